@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark of the fused forward + backward charge+dipole PME on GB300.
+
+One step = pme_forward (energy, forces, dE/dq, field) + pme_backward (the gradient plus the
+Hessian-vector product a force-matching loss needs) on one 32768-ion molten-NaCl frame
+(L = 102 A, mesh 128^3, spline order 6, alpha 0.30 / A, rcut 9 A), with the inputs resident
+in HBM. The metric is ion-evaluations per second: ions / (t_forward + t_backward).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank runs an independent replica of the
+step on its own GPU ("replicas only": a single frame does not shard); value is the sum of the
+ions all ranks processed divided by the slowest rank's time.
+
+The reference arm (--impl reference) times the float64 CPU oracle (plain PME in torch CPU
+ops with autograd double backward), as it stands, on this machine's host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PME q+mu fwd+bwd Mion-evals/s @32k ions"
+UNIT = "Mion-evals/s"
+
+# Algorithmic bytes of each stage per call (N ions, M mesh points, Mh half-spectrum points):
+# the minimum the stage has to move -- ion inputs once, each mesh or spectrum value once per
+# pass, outputs once (float32 values, complex64 spectra).
+def stage_bytes(stage: str, N: int, M: int, Mh: int) -> float:
+    table = {
+        "fwd.spread": 28 * N + 4 * M,               # pos, q, mu in; rho out
+        "bwd.spread": 56 * N + 8 * M,               # + tangents; rho and d rho out
+        "fwd.influence": 16 * Mh,                   # spectrum read + write
+        "bwd.influence": 32 * Mh,                   # two spectra
+        "fwd.gather": 4 * M + 12 * N + 40 * N,      # Phi in, pos in, 10 floats out
+        "bwd.gather": 8 * M + 56 * N + 28 * N,      # Phi, dPhi, ion + tangents in, 7 out
+        "fwd.fft_r2c": 4 * M + 8 * Mh, "fwd.fft_c2r": 8 * Mh + 4 * M,
+        "bwd.fft_r2c": 8 * M + 16 * Mh, "bwd.fft_c2r": 16 * Mh + 8 * M,
+    }
+    return float(table.get(stage, 0.0))
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mp = json.load(f)
+        return float(mp["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling every 200 ms while the benchmark runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.lines: list[str] = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def build_frame(name: str):
+    import workloads as W
+    fr, cfg = W.workload(name)
+    return fr, cfg
+
+
+def cpu_baseline(fr, cfg, max_seconds: float = 20.0, max_steps: int = 5):
+    """Time the float64 oracle (plain PME, autograd double backward) as it stands."""
+    import numpy as np
+    import torch
+    from oracle import pme as O2
+    import workloads as W
+    pos, q, mu = (np.asarray(np.float32(x), np.float64) for x in (fr.pos, fr.q, fr.mu))
+    gF, gphi, gfield = W.tangent(fr.n, seed=99)
+    o = O2.PMEOracle(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"])
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        o.evaluate(pos, q, mu, field_grad=False)
+        o.hvp(pos, q, mu, 0.5, gF, gphi, gfield)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= max_seconds * 0.5 or steps >= max_steps:
+            break
+    el = time.perf_counter() - t0
+    return {"value": fr.n * steps / el / 1e6, "unit": UNIT, "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": f"{steps} full fwd+bwd step(s) of the {fr.n}-ion frame (float64 torch CPU, "
+                      f"{el:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import torch
+    fr, cfg = build_frame(args.workload)
+    import numpy as np
+    import workloads as W
+    from oracle import pme as O2
+    pos, q, mu = (np.asarray(np.float32(x), np.float64) for x in (fr.pos, fr.q, fr.mu))
+    gF, gphi, gfield = W.tangent(fr.n, seed=99)
+    o = O2.PMEOracle(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"])
+
+    def step():
+        o.evaluate(pos, q, mu, field_grad=False)
+        o.hvp(pos, q, mu, 0.5, gF, gphi, gfield)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    ms = el * 1e3 / args.steps
+    val = fr.n / (ms / 1e3) / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(cfg, fr, ws),
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+                         "sample": f"each step one full fwd+bwd of the {fr.n}-ion frame"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def config_dict(cfg, fr, ws):
+    return {"workload": f"molten-NaCl {fr.n} ions, L={fr.box[0, 0]:.1f} A, mesh "
+                        f"{'x'.join(map(str, cfg['mesh']))}, order {cfg['order']}, alpha {cfg['alpha']}, "
+                        f"rcut {cfg['rcut']}, charges+dipoles, fwd+bwd (HVP)",
+            "ions": fr.n, "mesh": list(cfg["mesh"]), "order": cfg["order"], "alpha": cfg["alpha"],
+            "rcut": cfg["rcut"], "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+            "l2": "flushed between timed steps (256 MB write)"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_setup()
+    fr, cfg = build_frame(args.workload)
+    # the CPU baseline runs before any CUDA call (rank 0, N = 1 only)
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(fr, cfg)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2606_01598_gb300 as gb
+    import workloads as W
+
+    n = fr.n
+    plan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=n, device=dev)
+    c = lambda x: torch.tensor(np.float32(x), device=dev)
+    pos, q, mu = c(fr.pos), c(fr.q), c(fr.mu)
+    gF, gphi, gfield = (c(x) for x in W.tangent(n, seed=99))
+    gE = torch.tensor([0.5], dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def step():
+        plan.forward(pos, q, mu, energy=True, force=True, phi=True, field=True)
+        plan.backward(pos, q, mu, gE, gF, gphi, gfield)
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid).replace("GPU-", "")
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    # ---- timed region: K steps, device events, L2 flushed between steps --------------------
+    plan.profile(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    l0 = gb.launch_count()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record()
+        step()
+        stops[k].record()
+    torch.cuda.synchronize(dev)
+    launches = gb.launch_count() - l0
+    if ws > 1:
+        dist.barrier()
+    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, stops))
+    stages = plan.profile_read()
+    plan.profile(False)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_per_step = float(t.item()) / args.steps
+    value = ws * n / (ms_per_step / 1e3) / 1e6
+
+    # ---- end to end through the public API with pinned host buffers ------------------------
+    hp = [x.cpu().pin_memory() for x in (pos, q, mu, gF, gphi, gfield)]
+    hE = gE.cpu().pin_memory()
+    e_ms = 0.0
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        out = plan.forward(hp[0], hp[1], hp[2])
+        back = plan.backward(hp[0], hp[1], hp[2], hE, hp[3], hp[4], hp[5])
+        e_ms += (time.perf_counter() - t0) * 1e3
+    e_ms /= args.steps
+    e = torch.tensor([e_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(e, op=dist.ReduceOp.MAX)
+    e_value = ws * n / (float(e.item()) / 1e3) / 1e6
+    h2d = 2 * (12 + 4 + 12) * n + (12 + 4 + 12) * n + 8
+    d2h = 8 + (12 + 4 + 12) * n + (12 + 4 + 12) * n
+    clocks = sampler.stop()
+
+    if rank == 0:
+        # ---- roofline of the dominant kernel (stage timers of the timed region) ------------
+        M = int(np.prod(cfg["mesh"]))
+        Mh = cfg["mesh"][0] * cfg["mesh"][1] * (cfg["mesh"][2] // 2 + 1)
+        ours = {k: v for k, v in stages.items() if "fft" not in k}
+        dom = max(ours, key=lambda k: ours[k][0]) if ours else None
+        peak, peak_kind = load_peaks()
+        roof = None
+        if dom is not None:
+            avg_ms = ours[dom][0] / ours[dom][1]
+            by = stage_bytes(dom, n, M, Mh)
+            if by > 0:
+                ach = by / (avg_ms / 1e3) / 1e9
+                roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                        "frac": ach / peak, "traffic": None, "peak_source": peak_kind,
+                        "avg_launch_ms": avg_ms}
+            else:
+                roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None,
+                        "unit": "TFLOP/s", "frac": None, "traffic": None, "avg_launch_ms": avg_ms}
+        per_stage = {k: round(v[0] / v[1], 5) for k, v in sorted(stages.items())}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(cfg, fr, ws),
+            "roofline": roof,
+            "stage_ms": per_stage,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": e_ms},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="nacl32k")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,177 @@
+/*
+ * gbpme.h -- C ABI of the GB300 charge+dipole particle-mesh Ewald library (libgbpme.so).
+ *
+ * The library evaluates, for one periodic frame of N point charges q_i and point dipoles
+ * mu_i at positions r_i, the electrostatic energy of the Ewald-split Coulomb interaction
+ *
+ *   E = E_recip + E_pair + E_self + E_background                                  (1)
+ *
+ *   E_recip      particle-mesh reciprocal energy, Section 2.3 of the paper:
+ *                spline assignment of q and of the dipole bound charge (Eq.
+ *                charge_dipole_assign), R2C FFT (Eq. fft), deconvolved Green's function
+ *                G(k) C(n) (Eqs. green, Bk, influence), energy (Eq. energy_recip);
+ *   E_pair       real-space erfc(alpha r)/r charge-charge, charge-dipole and
+ *                dipole-dipole pair term over every periodic image within rcut (the
+ *                conventional-Ewald complement of the mesh term);
+ *   E_self       Eqs. self_q and self_mu;
+ *   E_background -pi Q^2 / (2 V alpha^2), Q = sum q (zero for neutral frames).
+ *
+ * and its derivatives, and the vector-Jacobian product (adjoint) of those derivatives that
+ * a force-matching loss (Eq. loss) needs.
+ *
+ * Conventions
+ *   - Lengths in the caller's unit (Angstrom in the tests), charges in e, dipoles in e*length.
+ *     Every energy and derivative is multiplied by opts.coulomb_k (default 1: Gaussian units).
+ *   - box[9] is row-major with ROWS the lattice vectors a_x, a_y, a_z (Section 2.3.1).
+ *   - Per-ion arrays are contiguous, in the caller's ion order: pos/mu/force/field [n][3]
+ *     float32, q/phi [n] float32, field_grad [n][6] float32 ordered xx, yy, zz, xy, xz, yz.
+ *   - Outputs are WRITTEN, never accumulated into.
+ *   - Pointers to per-ion arrays and to energies may be device pointers or host pointers
+ *     (pinned or pageable); the library asks the CUDA runtime which one it is and stages
+ *     host arrays through plan-owned device buffers with cudaMemcpyAsync on the call's
+ *     stream. Host outputs are complete when the stream is synchronised.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.
+ *     Calls are asynchronous on that stream. A plan must not be used by two calls that
+ *     overlap in time (its scratch buffers are shared); use one plan per stream.
+ *   - The plan owns all scratch (sorted ion records, meshes, spectra, cuFFT plans), sized
+ *     at creation for opts.max_ions ions. Nothing is allocated by the compute calls.
+ *
+ * Errors: every function returns a pme_status. No exception crosses the ABI. The text of
+ * the last error of a plan is returned by pme_last_error(). Non-finite inputs are detected
+ * on the device and reported by pme_sync_status().
+ */
+#ifndef GBPME_H
+#define GBPME_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PME_OK = 0,
+  PME_ERR_ARG = 1,          /* invalid argument: null handle, n > max_ions, order not in
+                               1..7, alpha <= 0, singular box, mesh dimension < order ... */
+  PME_ERR_CUDA = 2,         /* a CUDA runtime call or kernel launch failed */
+  PME_ERR_CUFFT = 3,        /* a cuFFT call failed */
+  PME_ERR_NONFINITE = 4,    /* a NaN or Inf appeared in pos, q or mu (device flag) */
+  PME_ERR_UNSUPPORTED = 5,  /* option combination not implemented (e.g. finite surface eps) */
+  PME_ERR_TIMEOUT = 6,      /* a bounded device-side wait expired */
+  PME_ERR_NOMEM = 7         /* device allocation failed at plan creation */
+} pme_status;
+
+typedef struct pme_plan_s* pme_plan_t;
+
+/* Options of a plan. Fill with pme_opts_default() and change what you need. */
+typedef struct {
+  double influence_power;  /* gamma of Eq. influence, C(n) = 1/|B(n)|^(2 gamma); default 1 */
+  int deconvolution;       /* 1: apply C(n) (default); 0: plain G(k) (the paper's ablation) */
+  double coulomb_k;        /* scale of every energy and derivative; 1 = Gaussian units,
+                              14.3996454784 for eV with Angstrom and e */
+  int include_pair;        /* 1: real-space erfc pair term (default); 0: mesh + self only */
+  int include_self;        /* 1: self terms (default) */
+  int include_background;  /* 1: neutralising background term (default) */
+  int max_ions;            /* capacity; default 1<<18 */
+  int brick[3];            /* spread/gather brick edge in mesh points; 0 = automatic */
+  int reserved[8];
+} pme_opts;
+
+void pme_opts_default(pme_opts* opts);
+
+/* Mesh-size rules of Section 2.3.1. rule 0: N = ceil(2 |a| / spacing + 1) (Eq. mesh_target
+ * as printed); rule 1: N = ceil(|a| / spacing). strategy 0: power of two; 1: smallest
+ * 2,3,5-smooth integer >= target (the paper's default); 2: the target itself. clamp_lo /
+ * clamp_hi bound the result when > 0. Writes mesh[3]. Host only; no GPU needed. */
+int pme_mesh_dims(const double box[9], double spacing, int rule, int strategy,
+                  int clamp_lo, int clamp_hi, int mesh[3]);
+
+/* Create a plan for one box, mesh, spline order p (1..7), Ewald alpha (> 0) and real-space
+ * cutoff rcut (> 0; ignored when include_pair = 0). mesh[3] = {Nx, Ny, Nz}, each >= order.
+ * opts may be NULL (defaults). Allocates all device scratch on the current CUDA device.
+ * Section 2.3.1 (cell, reciprocal basis, mesh), 2.3.3 (deconvolution). */
+int pme_plan_create(pme_plan_t* out, const double box[9], const int mesh[3], int order,
+                    double alpha, double rcut, const pme_opts* opts);
+
+/* Replace the box of an existing plan (same mesh, order, alpha, rcut). Not stream-ordered:
+ * the caller must make sure no call on the plan is in flight. */
+int pme_plan_set_box(pme_plan_t plan, const double box[9]);
+
+int pme_plan_destroy(pme_plan_t plan);
+
+/* Text of the last error recorded on the plan (never NULL). */
+const char* pme_last_error(pme_plan_t plan);
+const char* pme_status_string(int status);
+
+/* Synchronise `stream` and report device-detected errors (PME_ERR_NONFINITE, PME_ERR_TIMEOUT)
+ * raised since the previous pme_sync_status, clearing them. */
+int pme_sync_status(pme_plan_t plan, void* stream);
+
+/* Forward: energy and derivatives of Eq. (1).
+ *   energy     [1] float64: E                     (may be NULL)
+ *   force      [n][3]: F_i = -dE/dr_i             (may be NULL)
+ *   phi        [n]:    dE/dq_i                    (may be NULL)
+ *   field      [n][3]: -dE/dmu_i, the field of all other sources at r_i   (may be NULL)
+ *   field_grad [n][6]: gradient of that field at r_i (xx,yy,zz,xy,xz,yz)   (may be NULL)
+ * so that F_i = q_i field_i + field_grad_i mu_i. mu may be NULL (charges only).
+ * Forces follow Eq. forces (analytic derivative of the discrete mesh energy). */
+int pme_forward(pme_plan_t plan, void* stream, int n, const float* pos, const float* q,
+                const float* mu, double* energy, float* force, float* phi, float* field,
+                float* field_grad);
+
+/* Backward: vector-Jacobian product of the map (pos, q, mu) -> (E, force, phi, field) of
+ * pme_forward, for cotangents g_energy [1] float64, g_force [n][3], g_phi [n], g_field [n][3]
+ * (each may be NULL = zero):
+ *   grad_pos = g_E dE/dr + H v,  grad_q = g_E dE/dq + H v,  grad_mu = g_E dE/dmu + H v,
+ * with H the Hessian of E in (r, q, mu) and v = (-g_force, g_phi, -g_field). This is the
+ * double backward through Eq. forces that the force-matching loss of Eq. loss needs; it
+ * recomputes the mesh potential instead of storing it. Outputs may be NULL. */
+int pme_backward(pme_plan_t plan, void* stream, int n, const float* pos, const float* q,
+                 const float* mu, const double* g_energy, const float* g_force,
+                 const float* g_phi, const float* g_field, float* grad_pos, float* grad_q,
+                 float* grad_mu);
+
+/* ---- stage-level entry points (each runs one step of the pipeline on its own) ---------- */
+
+/* Mesh density rho_mesh of Eq. charge_dipole_assign, written to rho [Nx][Ny][Nz] float32
+ * (z fastest). Ions are sorted into mesh bricks and every mesh point is written once. */
+int pme_spread(pme_plan_t plan, void* stream, int n, const float* pos, const float* q,
+               const float* mu, float* rho);
+
+/* Potential mesh Phi = (1/V) IFFT_unnormalised[ G C FFT[rho] ] (Eqs. fft, potential_k, ifft)
+ * and E_recip = 1/2 sum rho Phi evaluated on the half spectrum in float64 (Eq.
+ * energy_recip), both WITHOUT the coulomb_k factor. rho is not modified. */
+int pme_solve(pme_plan_t plan, void* stream, const float* rho, float* phi_mesh,
+              double* e_recip);
+
+/* Interpolated potential of a mesh at the ions: out [n][10] = phi, d phi/dr (3),
+ * d^2 phi/dr dr (xx,yy,zz,xy,xz,yz), with the same assignment weights as the spread. */
+int pme_gather(pme_plan_t plan, void* stream, int n, const float* pos, const float* phi_mesh,
+               float* out);
+
+/* Real-space pair term alone: out [n][10] = pair potential at each ion and its first and
+ * second spatial derivatives (as pme_gather), e_pair [1] float64 = E_pair. No coulomb_k. */
+int pme_pair(pme_plan_t plan, void* stream, int n, const float* pos, const float* q,
+             const float* mu, float* out, double* e_pair);
+
+/* Number of the library's own kernels launched since the library was loaded (cuFFT's
+ * kernels are not counted). */
+long long pme_launch_count(void);
+
+/* ---- stage timers ------------------------------------------------------------------------
+ * When enabled, every stage of pme_forward / pme_backward is bracketed by CUDA events on
+ * the stream it runs on (the pair term runs on the plan's side stream). Stage index =
+ * stage + PME_STAGES_PER_PASS * pass, pass 0 = forward, 1 = backward, with stage
+ * 0 sort, 1 spread, 2 FFT R2C, 3 influence, 4 FFT C2R, 5 gather, 6 pair, 7 combine,
+ * 8 energy reduction. At most 4096 stage executions are recorded between two reads. */
+#define PME_STAGES_PER_PASS 9
+#define PME_NUM_STAGES 18
+int pme_profile_enable(pme_plan_t plan, int enable);
+/* Synchronises the plan's device, writes the summed milliseconds and the number of
+ * executions of each stage since the last read into ms[PME_NUM_STAGES] and
+ * calls[PME_NUM_STAGES] (either may be NULL), and resets the timers. */
+int pme_profile_read(pme_plan_t plan, double* ms, long long* calls);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBPME_H */

@@ -252,7 +252,7 @@ class PMEOracle:
             pairs = self._pairs(np.asarray(pos, np.float64))
         E, parts = self.energy(pos_t, q_t, mu_t, pairs, parts=True)
         gr, gq, gm = torch.autograd.grad(E, (pos_t, q_t, mu_t))
-        out = dict(energy=float(E), force=(-gr).numpy(), phi=gq.numpy(), field=(-gm).numpy())
+        out = dict(energy=float(E.detach()), force=(-gr).numpy(), phi=gq.numpy(), field=(-gm).numpy())
         out.update({k: float(v) for k, v in parts.items()})
         if field_grad:
             out["field_grad"] = self.field_gradient(np.asarray(pos, np.float64), np.asarray(q, np.float64),

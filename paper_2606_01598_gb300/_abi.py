@@ -1,0 +1,86 @@
+"""ctypes declarations of the libgbpme C ABI (include/gbpme.h). Argument marshalling only."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from .build import ROOT, lib_path
+
+c_int = ctypes.c_int
+c_double = ctypes.c_double
+c_void_p = ctypes.c_void_p
+c_float_p = ctypes.POINTER(ctypes.c_float)
+c_double_p = ctypes.POINTER(ctypes.c_double)
+c_int_p = ctypes.POINTER(ctypes.c_int)
+
+HEADER = os.path.join(ROOT, "include", "gbpme.h")
+
+STATUS = {0: "PME_OK", 1: "PME_ERR_ARG", 2: "PME_ERR_CUDA", 3: "PME_ERR_CUFFT",
+          4: "PME_ERR_NONFINITE", 5: "PME_ERR_UNSUPPORTED", 6: "PME_ERR_TIMEOUT",
+          7: "PME_ERR_NOMEM"}
+
+
+class PMEOpts(ctypes.Structure):
+    _fields_ = [("influence_power", c_double), ("deconvolution", c_int), ("coulomb_k", c_double),
+                ("include_pair", c_int), ("include_self", c_int), ("include_background", c_int),
+                ("max_ions", c_int), ("brick", c_int * 3), ("reserved", c_int * 8)]
+
+
+_SIGS = {
+    "pme_opts_default": (None, [ctypes.POINTER(PMEOpts)]),
+    "pme_mesh_dims": (c_int, [c_double_p, c_double, c_int, c_int, c_int, c_int, c_int_p]),
+    "pme_plan_create": (c_int, [ctypes.POINTER(c_void_p), c_double_p, c_int_p, c_int, c_double,
+                                c_double, ctypes.POINTER(PMEOpts)]),
+    "pme_plan_set_box": (c_int, [c_void_p, c_double_p]),
+    "pme_plan_destroy": (c_int, [c_void_p]),
+    "pme_last_error": (ctypes.c_char_p, [c_void_p]),
+    "pme_status_string": (ctypes.c_char_p, [c_int]),
+    "pme_sync_status": (c_int, [c_void_p, c_void_p]),
+    "pme_forward": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 8),
+    "pme_backward": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 10),
+    "pme_spread": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 4),
+    "pme_solve": (c_int, [c_void_p, c_void_p] + [c_void_p] * 3),
+    "pme_gather": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 3),
+    "pme_pair": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 5),
+    "pme_launch_count": (ctypes.c_longlong, []),
+    "pme_profile_enable": (c_int, [c_void_p, c_int]),
+    "pme_profile_read": (c_int, [c_void_p, c_double_p, ctypes.POINTER(ctypes.c_longlong)]),
+}
+
+NUM_STAGES = 18
+STAGE_NAMES = ["sort", "spread", "fft_r2c", "influence", "fft_c2r", "gather", "pair",
+               "combine", "energy"]
+
+_LIB = None
+
+
+def header_functions() -> list[str]:
+    """Names of every function the public header declares."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pme_[a-z_]+)\s*\(", src)))
+
+
+def load():
+    """Load libgbpme.so (built in-tree). Raises if it is missing: there is no fallback."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "(the CUDA library is required; there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+class PMEError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}" + (f" ({detail})" if detail else ""))

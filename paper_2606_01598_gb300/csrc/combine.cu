@@ -1,0 +1,222 @@
+// Per-ion assembly of the outputs from the mesh and pair parts, plus the self terms
+// (Eqs. self_q, self_mu) and the neutralising background -pi Q^2 / (2 V alpha^2).
+//
+// Forward, per ion (k = coulomb_k, c = 4 alpha^3 / (3 sqrt(pi))):
+//   phi        = k (phi_mesh + phi_pair - 2 alpha q / sqrt(pi) - pi Q / (V alpha^2))
+//   field      = k (-grad phi_mesh - grad phi_pair + c mu)              (= -dE/dmu)
+//   field_grad = k (-hess phi_mesh - hess phi_pair - c q I)
+//   force      = q field + field_grad mu                               (= -dE/dr)
+// where the c terms remove the ion's own screening cloud (for mu they are the derivative of
+// Eq. self_mu; for the field gradient the analogous part of the reciprocal sum), so field
+// and field_grad are those of all other sources. Energy partials per block (float64):
+// 1/2 (q phi_pair + mu . grad phi_pair) + self energies.
+//
+// Backward, per ion: grad = k (mesh part + pair part) + the self and background terms of
+// the g_E-weighted gradient and of the Hessian-vector product.
+#include "kernels.h"
+
+namespace gbpme {
+
+namespace {
+
+constexpr int kCombThreads = 256;
+
+struct CombineArgs {
+  const float* mesh_out;
+  const float* pair_out;
+  int with_mesh, with_pair;
+  IonInputs in;
+  const double* qsum;
+  const double* g_energy;
+  double* epart;
+  float* force;
+  float* phi;
+  float* field;
+  float* field_grad;
+  float* grad_pos;
+  float* grad_q;
+  float* grad_mu;
+  float k;
+  float self_phi;     // 2 alpha / sqrt(pi)     (0 when self terms are off)
+  float self_c;       // 4 alpha^3 / (3 sqrt(pi))
+  float bg;           // pi / (V alpha^2)       (0 when background is off)
+  double e_self_q;    // alpha / sqrt(pi)
+  double e_self_mu;   // 2 alpha^3 / (3 sqrt(pi))
+};
+
+__global__ void __launch_bounds__(kCombThreads) k_combine_forward(CombineArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double e = 0.0;
+  if (i < a.in.n) {
+    float qi = a.in.q[i];
+    float mu[3] = {0.f, 0.f, 0.f};
+    if (a.in.mu) {
+      mu[0] = a.in.mu[3 * i];
+      mu[1] = a.in.mu[3 * i + 1];
+      mu[2] = a.in.mu[3 * i + 2];
+    }
+    float v[10], w[10];
+#pragma unroll
+    for (int t = 0; t < 10; ++t) {
+      v[t] = a.with_mesh ? a.mesh_out[size_t(i) * 10 + t] : 0.f;
+      w[t] = a.with_pair ? a.pair_out[size_t(i) * 10 + t] : 0.f;
+    }
+    const float Q = float(a.qsum[0]);
+    const float k = a.k;
+    const float ph = k * (v[0] + w[0] - a.self_phi * qi - a.bg * Q);
+    float fld[3], fg[6];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) fld[c] = k * (-(v[1 + c] + w[1 + c]) + a.self_c * mu[c]);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) fg[c] = k * (-(v[4 + c] + w[4 + c]) - (c < 3 ? a.self_c * qi : 0.f));
+    // force = q field + field_grad mu ; field_grad order xx yy zz xy xz yz
+    const float F0 = qi * fld[0] + fg[0] * mu[0] + fg[3] * mu[1] + fg[4] * mu[2];
+    const float F1 = qi * fld[1] + fg[3] * mu[0] + fg[1] * mu[1] + fg[5] * mu[2];
+    const float F2 = qi * fld[2] + fg[4] * mu[0] + fg[5] * mu[1] + fg[2] * mu[2];
+    if (a.phi) a.phi[i] = ph;
+    if (a.field) {
+      a.field[3 * i] = fld[0];
+      a.field[3 * i + 1] = fld[1];
+      a.field[3 * i + 2] = fld[2];
+    }
+    if (a.field_grad) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) a.field_grad[6 * i + c] = fg[c];
+    }
+    if (a.force) {
+      a.force[3 * i] = F0;
+      a.force[3 * i + 1] = F1;
+      a.force[3 * i + 2] = F2;
+    }
+    const double mu2 = double(mu[0]) * mu[0] + double(mu[1]) * mu[1] + double(mu[2]) * mu[2];
+    e = 0.5 * (double(qi) * w[0] + double(mu[0]) * w[1] + double(mu[1]) * w[2] +
+               double(mu[2]) * w[3]) -
+        a.e_self_q * double(qi) * qi - a.e_self_mu * mu2;
+  }
+  const double t = block_sum_d(e);
+  if (threadIdx.x == 0) a.epart[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kCombThreads) k_combine_backward(CombineArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.in.n) return;
+  const float qi = a.in.q[i];
+  float mu[3] = {0.f, 0.f, 0.f}, dmu[3] = {0.f, 0.f, 0.f};
+  if (a.in.mu) {
+    mu[0] = a.in.mu[3 * i];
+    mu[1] = a.in.mu[3 * i + 1];
+    mu[2] = a.in.mu[3 * i + 2];
+  }
+  if (a.in.gfield) {
+    dmu[0] = -a.in.gfield[3 * i];
+    dmu[1] = -a.in.gfield[3 * i + 1];
+    dmu[2] = -a.in.gfield[3 * i + 2];
+  }
+  const float dq = a.in.gphi ? a.in.gphi[i] : 0.f;
+  const float gE = a.g_energy ? float(*a.g_energy) : 0.f;
+  float v[8], w[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    v[t] = a.with_mesh ? a.mesh_out[size_t(i) * 8 + t] : 0.f;
+    w[t] = a.with_pair ? a.pair_out[size_t(i) * 8 + t] : 0.f;
+  }
+  const float Q = float(a.qsum[0]), dQ = float(a.qsum[1]);
+  const float k = a.k;
+  if (a.grad_pos) {
+    a.grad_pos[3 * i] = k * (v[0] + w[0]);
+    a.grad_pos[3 * i + 1] = k * (v[1] + w[1]);
+    a.grad_pos[3 * i + 2] = k * (v[2] + w[2]);
+  }
+  if (a.grad_q)
+    a.grad_q[i] = k * (v[3] + w[3] - a.self_phi * (gE * qi + dq) - a.bg * (gE * Q + dQ));
+  if (a.grad_mu) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      a.grad_mu[3 * i + c] = k * (v[4 + c] + w[4 + c] - a.self_c * (gE * mu[c] + dmu[c]));
+  }
+}
+
+__global__ void __launch_bounds__(kCombThreads)
+k_pair_energy(int n, const float* q, const float* mu, const float* pair_out, double* epart) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double e = 0.0;
+  if (i < n) {
+    const float* w = pair_out + size_t(i) * 10;
+    e = 0.5 * double(q[i]) * w[0];
+    if (mu)
+      e += 0.5 * (double(mu[3 * i]) * w[1] + double(mu[3 * i + 1]) * w[2] +
+                  double(mu[3 * i + 2]) * w[3]);
+  }
+  const double t = block_sum_d(e);
+  if (threadIdx.x == 0) epart[blockIdx.x] = t;
+}
+
+CombineArgs base_args(pme_plan_t p, const IonInputs& in) {
+  CombineArgs a = {};
+  a.in = in;
+  a.qsum = p->sb.qsum;
+  a.k = float(p->opts.coulomb_k);
+  const double sp = 1.7724538509055160273;
+  const double al = p->alpha;
+  const bool self = p->opts.include_self != 0;
+  a.self_phi = self ? float(2.0 * al / sp) : 0.f;
+  a.self_c = self ? float(4.0 * al * al * al / (3.0 * sp)) : 0.f;
+  a.bg = p->opts.include_background ? float(kPi / (p->g.volume * al * al)) : 0.f;
+  a.e_self_q = self ? al / sp : 0.0;
+  a.e_self_mu = self ? 2.0 * al * al * al / (3.0 * sp) : 0.0;
+  return a;
+}
+
+}  // namespace
+
+int launch_combine_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool with_mesh,
+                           bool with_pair, double* e_parts, float* force, float* phi,
+                           float* field, float* field_grad) {
+  CombineArgs a = base_args(p, in);
+  a.mesh_out = p->mesh_out;
+  a.pair_out = p->pair_out;
+  a.with_mesh = with_mesh;
+  a.with_pair = with_pair;
+  a.epart = e_parts;
+  a.force = force;
+  a.phi = phi;
+  a.field = field;
+  a.field_grad = field_grad;
+  const int grid = (in.n + kCombThreads - 1) / kCombThreads;
+  if (grid == 0) return PME_OK;
+  k_combine_forward<<<grid, kCombThreads, 0, s>>>(a);
+  count_launch();
+  return check_launch(p, "k_combine_forward");
+}
+
+int launch_combine_backward(pme_plan_t p, cudaStream_t s, const IonInputs& in,
+                            const double* g_energy, float* grad_pos, float* grad_q,
+                            float* grad_mu) {
+  CombineArgs a = base_args(p, in);
+  a.mesh_out = p->mesh_out;
+  a.pair_out = p->pair_out;
+  a.with_mesh = 1;
+  a.with_pair = p->opts.include_pair != 0;
+  a.g_energy = g_energy;
+  a.grad_pos = grad_pos;
+  a.grad_q = grad_q;
+  a.grad_mu = grad_mu;
+  const int grid = (in.n + kCombThreads - 1) / kCombThreads;
+  if (grid == 0) return PME_OK;
+  k_combine_backward<<<grid, kCombThreads, 0, s>>>(a);
+  count_launch();
+  return check_launch(p, "k_combine_backward");
+}
+
+int launch_pair_energy(pme_plan_t p, cudaStream_t s, int n, const IonInputs& in,
+                       const float* pair_out, double* e_pair) {
+  const int grid = (n + kCombThreads - 1) / kCombThreads;
+  if (grid == 0) return PME_OK;
+  k_pair_energy<<<grid, kCombThreads, 0, s>>>(n, in.q, in.mu, pair_out, e_pair);
+  count_launch();
+  return check_launch(p, "k_pair_energy");
+}
+
+int combine_blocks(int n) { return (n + kCombThreads - 1) / kCombThreads; }
+
+}  // namespace gbpme

@@ -1,0 +1,248 @@
+// Internal declarations of libgbpme: the plan, launch bookkeeping and device helpers that
+// several kernels share (B-spline weights, mesh and cell coordinates, reductions).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "../../include/gbpme.h"
+
+namespace gbpme {
+
+constexpr int kMaxOrder = 7;
+constexpr int kMaxCandPerDim = 4;   // bricks along one axis that can feed one brick's stencils
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kProfCap = 4096;
+
+// ----------------------------------------------------------------------------------------
+// launch bookkeeping
+// ----------------------------------------------------------------------------------------
+void count_launch();
+
+// ----------------------------------------------------------------------------------------
+// geometry shared by all kernels of one plan (passed by value)
+// ----------------------------------------------------------------------------------------
+struct Geometry {
+  double cinv[9];   // C^{-1}, row-major: s_b = sum_a r_a cinv[a*3+b]
+  float D[9];       // D[a*3+b] = N_b cinv[a*3+b]: d/dr_a = sum_b D[a][b] d/dx_b
+  float H[9];       // pair cells: rows a_b / ncell_b, r = sum_b u_b H[b]
+  int N[3];         // mesh
+  int brick[3];     // brick edge per axis
+  int nb[3];        // bricks per axis
+  int ncell[3];     // pair cells per axis (1 = all images brute force along that axis)
+  int kimg[3];      // neighbour cell / image range per axis
+  int order;
+  float alpha;
+  float rcut2;
+  double volume;
+};
+
+// Per-ion records in brick (mesh) order.
+struct MeshRecords {
+  int4* idx;     // m0x, m0y, m0z (wrapped into [0,N)), original index
+  float4* fq;    // fractional offsets fx, fy, fz in [0,1), q
+  float4* dm;    // N_b (mu . C^{-1}_{:b}) for b = x,y,z ; w unused
+  float4* tq;    // tangent: dq, projected d' = N_b((dmu + q dr) . C^{-1}_{:b})
+  float4* tt;    // tangent: t = N_b (dr . C^{-1}_{:b}); w unused
+};
+
+// Per-ion records in pair-cell order.
+struct PairRecords {
+  int4* idx;     // cell x, y, z, original index
+  float4* fq;    // offsets inside the cell in cell units fx, fy, fz in [0,1), q
+  float4* mu;    // mu (r-space), w unused
+  float4* tq;    // tangent: dq, d' = dmu + q dr (r-space)
+  float4* dr;    // tangent: dr (r-space); w unused
+};
+
+struct SortBuffers {
+  int* key_b;     // [max_ions] brick key per caller-order ion
+  int* key_c;     // [max_ions] pair cell key
+  int* slot_b;    // [max_ions] arrival slot inside the brick
+  int* slot_c;
+  int* count_b;   // [nbricks + 1]
+  int* count_c;   // [ncells + 1]
+  int* start_b;   // [nbricks + 1] exclusive scan
+  int* start_c;   // [ncells + 1]
+  int* perm_b;    // [max_ions] unsorted placement (sorted slot -> caller index)
+  int* perm_c;
+  double* qpart;  // [2 * max_blocks] per-block sums of q and dq
+  double* qsum;   // [2] Q and dQ
+};
+
+}  // namespace gbpme
+
+struct pme_plan_s {
+  gbpme::Geometry g;
+  double box[9];
+  double alpha, rcut;
+  pme_opts opts;
+  int M, Mh;            // mesh points, half-spectrum points
+  int nbricks, ncells;
+  int max_ions;
+  int max_blocks;       // ion blocks of 256 for max_ions
+  int device;
+  // device scratch
+  float* rho;           // [2][M]   primal and tangent mesh densities
+  cufftComplex* spec;   // [2][Mh]
+  float* phi;           // [2][M]   primal and tangent potential meshes
+  float* dconv[3];      // per-axis deconvolution factors 1/sinc^(2 p gamma) (or 1)
+  int* cand;            // [3][max nb][1 + kMaxCandPerDim] candidate bricks per axis
+  int max_nb;
+  gbpme::SortBuffers sb;
+  gbpme::MeshRecords mr;
+  gbpme::PairRecords pr;
+  float* mesh_out;      // [max_ions][10] per-ion mesh results (caller order)
+  float* pair_out;      // [max_ions][10] per-ion pair results
+  double* epart;        // energy partials: [0, nspec_blocks) recip, then per-ion blocks
+  int nspec_blocks;
+  int* flags;           // device error flags
+  // host-pointer staging
+  float* stage_f;       // device staging for host arrays, 24 floats per ion
+  double* stage_d;      // [4]
+  // cuFFT
+  cufftHandle r2c1, c2r1, r2c2, c2r2;
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_join;
+  std::string last_error;
+  // stage timers
+  bool prof = false;
+  cudaEvent_t* prof_ev = nullptr;   // [2 * kProfCap]
+  int* prof_stage = nullptr;        // [kProfCap]
+  int prof_used = 0;
+};
+
+namespace gbpme {
+
+int set_error(pme_plan_t plan, int status, const std::string& what);
+// Stage timer bracket: returns a slot (or -1 when timers are off or full).
+int prof_begin(pme_plan_t plan, int stage, cudaStream_t s);
+void prof_end(pme_plan_t plan, int slot, cudaStream_t s);
+int check_cuda(pme_plan_t plan, cudaError_t e, const char* what);
+int check_launch(pme_plan_t plan, const char* what);
+
+// ----------------------------------------------------------------------------------------
+// device helpers
+// ----------------------------------------------------------------------------------------
+
+// Uniform cardinal B-spline weights. For the offset f in [0,1) of a mesh coordinate from its
+// first stencil point m0 (x = m0 + P/2 - 1 + f), w[d][j] is the d-th derivative (d <= DMAX)
+// of the centred spline W^(P) at t_j = x - (m0 + j). Built from the recursion
+// N_k(y) = (y N_{k-1}(y) + (k - y) N_{k-1}(y - 1)) / (k - 1) on y = f + i, and
+// d^d/dy^d N_P(y) = sum_s (-1)^s binom(d, s) N_{P-d}(y - s).
+template <int P, int DMAX>
+__device__ __forceinline__ void spline_weights(float f, float (&w)[DMAX + 1][P]) {
+  float lv[DMAX + 1][P];   // lv[d][i] = N_{P-d}(f + i), zero when P - d < 1
+  float b[P];              // running N_k(f + i)
+#pragma unroll
+  for (int d = 0; d <= DMAX; ++d)
+#pragma unroll
+    for (int i = 0; i < P; ++i) lv[d][i] = 0.f;
+#pragma unroll
+  for (int i = 0; i < P; ++i) b[i] = (i == 0) ? 1.f : 0.f;   // N_1(f + i), f in [0,1)
+#pragma unroll
+  for (int d = 0; d <= DMAX; ++d)
+    if (P - d == 1) {
+#pragma unroll
+      for (int i = 0; i < P; ++i) lv[d][i] = b[i];
+    }
+#pragma unroll
+  for (int k = 2; k <= P; ++k) {
+    const float inv = 1.f / float(k - 1);
+#pragma unroll
+    for (int i = P - 1; i >= 0; --i) {
+      if (i <= k - 1) {
+        const float left = (i <= k - 2) ? b[i] : 0.f;
+        const float right = (i >= 1) ? b[i - 1] : 0.f;
+        b[i] = ((f + float(i)) * left + (float(k) - f - float(i)) * right) * inv;
+      }
+    }
+#pragma unroll
+    for (int d = 0; d <= DMAX; ++d)
+      if (k == P - d) {
+#pragma unroll
+        for (int i = 0; i < P; ++i) lv[d][i] = b[i];
+      }
+  }
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    const int i = P - 1 - j;
+    w[0][j] = lv[0][i];
+    if constexpr (DMAX >= 1)
+      w[1][j] = lv[1][i] - ((i >= 1) ? lv[1][i - 1] : 0.f);
+    if constexpr (DMAX >= 2)
+      w[2][j] = lv[2][i] - 2.f * ((i >= 1) ? lv[2][i - 1] : 0.f) + ((i >= 2) ? lv[2][i - 2] : 0.f);
+    if constexpr (DMAX >= 3)
+      w[3][j] = lv[3][i] - 3.f * ((i >= 1) ? lv[3][i - 1] : 0.f) +
+                3.f * ((i >= 2) ? lv[3][i - 2] : 0.f) - ((i >= 3) ? lv[3][i - 3] : 0.f);
+  }
+}
+
+// Fractional coordinate s = r C^{-1} wrapped into [0,1), in float64.
+__device__ __forceinline__ void frac_coords(const Geometry& g, double rx, double ry, double rz,
+                                            double s[3]) {
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    double v = rx * g.cinv[0 * 3 + b] + ry * g.cinv[1 * 3 + b] + rz * g.cinv[2 * 3 + b];
+    v -= floor(v);
+    if (v >= 1.0) v -= 1.0;
+    if (!(v >= 0.0)) v = 0.0;   // NaN guard; the caller flags non-finite inputs
+    s[b] = v;
+  }
+}
+
+// First stencil point m0 (wrapped) and offset f of mesh coordinate x = N s (Eq. w3d):
+// m0 = floor(x - P/2) + 1, f = x - P/2 + 1 - floor(x - P/2 + 1).
+__device__ __forceinline__ void stencil_origin(double s, int N, int order, int& m0, float& f) {
+  const double y = s * double(N) - 0.5 * double(order) + 1.0;
+  const double fl = floor(y);
+  int m = int(fl);
+  float fr = float(y - fl);
+  if (fr >= 1.f) { fr = 0.f; m += 1; }   // keep the float offset inside [0,1)
+  if (m < 0) m += N;
+  if (m >= N) m -= N;
+  m0 = m;
+  f = fr;
+}
+
+// Pair cell and in-cell offset of fractional coordinate s along one axis.
+__device__ __forceinline__ void cell_origin(double s, int nc, int& c, float& f) {
+  const double u = s * double(nc);
+  double fl = floor(u);
+  if (fl > double(nc - 1)) fl = double(nc - 1);
+  if (fl < 0.0) fl = 0.0;
+  c = int(fl);
+  f = float(u - fl);
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide float64 sum (blockDim.x a multiple of 32, <= 1024). Result valid in thread 0.
+__device__ __forceinline__ double block_sum_d(double v) {
+  __shared__ double part[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum_d(v);
+  __syncthreads();
+  if (lane == 0) part[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (wid == 0) {
+    r = (lane < int(blockDim.x >> 5)) ? part[lane] : 0.0;
+    r = warp_sum_d(r);
+  }
+  return r;
+}
+
+// Device error flag bits.
+constexpr int kFlagNonFinite = 1;
+constexpr int kFlagTimeout = 2;
+
+}  // namespace gbpme

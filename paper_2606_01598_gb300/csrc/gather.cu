@@ -1,0 +1,270 @@
+// Gather of the potential mesh at the ions (the interpolation that is the adjoint of the
+// spread of Eq. charge_dipole_assign; forces follow Eq. forces).
+//
+// For an ion with first stencil point m0 and offsets f, the interpolated potential
+// phi(x) = sum_m W(x - m) Phi(m) has mesh-coordinate derivatives
+//   M_abc = sum_{jx,jy,jz} Phi(m0 + j) W^(a)(t_jx) W^(b)(t_jy) W^(c)(t_jz),
+// and r-space derivatives follow with D[a][b] = N_b C^{-1}[a][b] (d/dr = D d/dx).
+//
+// Work split: a group of 8 lanes per ion, lane l owning stencil z-offset l (l < p), so each
+// mesh row segment is read by consecutive lanes. Each lane forms the y- and x-moments of its
+// z-column, scales them by its own z-weights, and the group sums the moments with warp
+// shuffles. Forward mode keeps orders <= 2 (potential, gradient, Hessian). Tangent mode
+// (backward pass) keeps orders <= 3 of Phi and <= 2 of the tangent potential dPhi and
+// evaluates the mesh part of the Hessian-vector product in mesh coordinates.
+#include "kernels.h"
+
+namespace gbpme {
+
+namespace {
+
+constexpr int kGatherThreads = 256;
+constexpr int kGroup = 8;
+
+struct GatherArgs {
+  Geometry g;
+  MeshRecords mr;
+  const float* phi;
+  const float* dphi;
+  const double* g_energy;
+  float* out;
+  int n;
+};
+
+__device__ __forceinline__ float group_sum(float v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v;
+}
+
+// y = D x
+__device__ __forceinline__ void apply_D(const float* D, const float x[3], float y[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) y[a] = D[a * 3 + 0] * x[0] + D[a * 3 + 1] * x[1] + D[a * 3 + 2] * x[2];
+}
+
+template <int P, bool TAN>
+__global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
+  constexpr int DM = TAN ? 3 : 2;
+  const Geometry& g = a.g;
+  const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / kGroup;
+  const int l = threadIdx.x & (kGroup - 1);
+  const bool valid = gid < a.n;
+  const int ion = valid ? gid : 0;
+  const int4 m = a.mr.idx[ion];
+  const float4 fq = a.mr.fq[ion];
+  float wx[DM + 1][P], wy[DM + 1][P], wzall[DM + 1][P];
+  spline_weights<P, DM>(fq.x, wx);
+  spline_weights<P, DM>(fq.y, wy);
+  spline_weights<P, DM>(fq.z, wzall);
+  const bool act = valid && (l < P);
+  float wz[DM + 1];
+#pragma unroll
+  for (int c = 0; c <= DM; ++c) {
+    float v = 0.f;
+#pragma unroll
+    for (int j = 0; j < P; ++j) v = (j == l) ? wzall[c][j] : v;
+    wz[c] = act ? v : 0.f;
+  }
+  int z = m.z + l;
+  if (z >= g.N[2]) z -= g.N[2];
+  const int Ny = g.N[1], Nz = g.N[2];
+
+  // S[a][b]: sum over (jx, jy) of Phi * W^(a)_x * W^(b)_y for this lane's z, a + b <= DM
+  float S[DM + 1][DM + 1];
+  float T[3][3];   // same for the tangent mesh, a + b <= 2
+#pragma unroll
+  for (int i = 0; i <= DM; ++i)
+#pragma unroll
+    for (int j = 0; j <= DM; ++j) S[i][j] = 0.f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) T[i][j] = 0.f;
+
+  if (act) {
+#pragma unroll
+    for (int jx = 0; jx < P; ++jx) {
+      int x = m.x + jx;
+      if (x >= g.N[0]) x -= g.N[0];
+      float r[DM + 1], rt[3];
+#pragma unroll
+      for (int b = 0; b <= DM; ++b) r[b] = 0.f;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) rt[b] = 0.f;
+#pragma unroll
+      for (int jy = 0; jy < P; ++jy) {
+        int y = m.y + jy;
+        if (y >= Ny) y -= Ny;
+        const size_t off = (size_t(x) * Ny + y) * Nz + z;
+        const float v = __ldg(a.phi + off);
+#pragma unroll
+        for (int b = 0; b <= DM; ++b) r[b] += v * wy[b][jy];
+        if (TAN) {
+          const float dv = __ldg(a.dphi + off);
+#pragma unroll
+          for (int b = 0; b < 3; ++b) rt[b] += dv * wy[b][jy];
+        }
+      }
+#pragma unroll
+      for (int ia = 0; ia <= DM; ++ia)
+#pragma unroll
+        for (int ib = 0; ib <= DM; ++ib)
+          if (ia + ib <= DM) S[ia][ib] += r[ib] * wx[ia][jx];
+      if (TAN) {
+#pragma unroll
+        for (int ia = 0; ia < 3; ++ia)
+#pragma unroll
+          for (int ib = 0; ib < 3; ++ib)
+            if (ia + ib <= 2) T[ia][ib] += rt[ib] * wx[ia][jx];
+      }
+    }
+  }
+  // moments M_abc, reduced over the group's z-lanes
+#define MOM(ia, ib, ic) group_sum(S[ia][ib] * wz[ic])
+#define TMOM(ia, ib, ic) group_sum(T[ia][ib] * wz[ic])
+  const float m000 = MOM(0, 0, 0);
+  const float m100 = MOM(1, 0, 0), m010 = MOM(0, 1, 0), m001 = MOM(0, 0, 1);
+  const float m200 = MOM(2, 0, 0), m020 = MOM(0, 2, 0), m002 = MOM(0, 0, 2);
+  const float m110 = MOM(1, 1, 0), m101 = MOM(1, 0, 1), m011 = MOM(0, 1, 1);
+  if (!TAN) {
+    if (!valid || l != 0) return;
+    const float gx[3] = {m100, m010, m001};
+    const float Hx[3][3] = {{m200, m110, m101}, {m110, m020, m011}, {m101, m011, m002}};
+    float gr[3];
+    apply_D(g.D, gx, gr);
+    float HD[3][3];   // Hx D^T
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        HD[i][b] = Hx[i][0] * g.D[b * 3 + 0] + Hx[i][1] * g.D[b * 3 + 1] + Hx[i][2] * g.D[b * 3 + 2];
+    float Hr[3][3];   // D Hx D^T
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        Hr[i][b] = g.D[i * 3 + 0] * HD[0][b] + g.D[i * 3 + 1] * HD[1][b] + g.D[i * 3 + 2] * HD[2][b];
+    float* o = a.out + size_t(m.w) * 10;
+    o[0] = m000;
+    o[1] = gr[0];
+    o[2] = gr[1];
+    o[3] = gr[2];
+    o[4] = Hr[0][0];
+    o[5] = Hr[1][1];
+    o[6] = Hr[2][2];
+    o[7] = Hr[0][1];
+    o[8] = Hr[0][2];
+    o[9] = Hr[1][2];
+    return;
+  }
+  if constexpr (TAN) {
+    const float m300 = MOM(3, 0, 0), m030 = MOM(0, 3, 0), m003 = MOM(0, 0, 3);
+    const float m210 = MOM(2, 1, 0), m201 = MOM(2, 0, 1), m120 = MOM(1, 2, 0);
+    const float m021 = MOM(0, 2, 1), m102 = MOM(1, 0, 2), m012 = MOM(0, 1, 2);
+    const float m111 = MOM(1, 1, 1);
+    const float t000 = TMOM(0, 0, 0);
+    const float t100 = TMOM(1, 0, 0), t010 = TMOM(0, 1, 0), t001 = TMOM(0, 0, 1);
+    const float t200 = TMOM(2, 0, 0), t020 = TMOM(0, 2, 0), t002 = TMOM(0, 0, 2);
+    const float t110 = TMOM(1, 1, 0), t101 = TMOM(1, 0, 1), t011 = TMOM(0, 1, 1);
+    if (!valid || l != 0) return;
+    const float gE = a.g_energy ? float(*a.g_energy) : 0.f;
+    const float4 dm = a.mr.dm[ion];   // m = D^T mu
+    const float4 tq = a.mr.tq[ion];   // dq, dd = D^T (dmu + q dr)
+    const float4 tt = a.mr.tt[ion];   // t = D^T dr
+    const float q = fq.w, dq = tq.x;
+    const float mv[3] = {dm.x, dm.y, dm.z};
+    const float dd[3] = {tq.y, tq.z, tq.w};
+    const float tv[3] = {tt.x, tt.y, tt.z};
+    const float gx[3] = {m100, m010, m001};
+    const float Hx[3][3] = {{m200, m110, m101}, {m110, m020, m011}, {m101, m011, m002}};
+    const float dgx[3] = {t100, t010, t001};
+    const float dHx[3][3] = {{t200, t110, t101}, {t110, t020, t011}, {t101, t011, t002}};
+    // third-derivative tensor T3[a][b][c] of the potential in mesh coordinates
+    float T3[3][3][3];
+    T3[0][0][0] = m300; T3[1][1][1] = m030; T3[2][2][2] = m003;
+    T3[0][0][1] = T3[0][1][0] = T3[1][0][0] = m210;
+    T3[0][0][2] = T3[0][2][0] = T3[2][0][0] = m201;
+    T3[0][1][1] = T3[1][0][1] = T3[1][1][0] = m120;
+    T3[1][1][2] = T3[1][2][1] = T3[2][1][1] = m021;
+    T3[0][2][2] = T3[2][0][2] = T3[2][2][0] = m102;
+    T3[1][2][2] = T3[2][1][2] = T3[2][2][1] = m012;
+    T3[0][1][2] = T3[0][2][1] = T3[1][0][2] = T3[1][2][0] = T3[2][0][1] = T3[2][1][0] = m111;
+    // D^T w with w = gE mu + dmu + q dr  ->  gE m + dd
+    const float wv[3] = {gE * mv[0] + dd[0], gE * mv[1] + dd[1], gE * mv[2] + dd[2]};
+    float xr[3], xm[3];
+    const float cq = gE * q + dq;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      float Hw = 0.f, Ht = 0.f, dHm = 0.f, T3mt = 0.f;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        Hw += Hx[i][j] * wv[j];
+        Ht += Hx[i][j] * tv[j];
+        dHm += dHx[i][j] * mv[j];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) T3mt += T3[i][j][k] * mv[j] * tv[k];
+      }
+      // grad_r (mesh coords) = (gE q + dq) g + H w + q dg + dH m + T3[m, t]
+      xr[i] = cq * gx[i] + Hw + q * dgx[i] + dHm + T3mt;
+      // grad_mu (mesh coords) = gE g + dg + H t
+      xm[i] = gE * gx[i] + dgx[i] + Ht;
+    }
+    float gr[3], gm[3];
+    apply_D(g.D, xr, gr);
+    apply_D(g.D, xm, gm);
+    // grad_q = gE phi + dphi + g . t
+    const float gq = gE * m000 + t000 + gx[0] * tv[0] + gx[1] * tv[1] + gx[2] * tv[2];
+    float* o = a.out + size_t(m.w) * 8;
+    o[0] = gr[0];
+    o[1] = gr[1];
+    o[2] = gr[2];
+    o[3] = gq;
+    o[4] = gm[0];
+    o[5] = gm[1];
+    o[6] = gm[2];
+    o[7] = 0.f;
+  }
+#undef MOM
+#undef TMOM
+}
+
+template <bool TAN>
+int launch_t(pme_plan_t p, cudaStream_t s, int n, const float* phi, const float* dphi,
+             const double* g_energy, float* out) {
+  GatherArgs a;
+  a.g = p->g;
+  a.mr = p->mr;
+  a.phi = phi;
+  a.dphi = dphi;
+  a.g_energy = g_energy;
+  a.out = out;
+  a.n = n;
+  const int grid = int((size_t(n) * kGroup + kGatherThreads - 1) / kGatherThreads);
+  if (grid == 0) return PME_OK;
+  switch (p->g.order) {
+    case 1: k_gather<1, TAN><<<grid, kGatherThreads, 0, s>>>(a); break;
+    case 2: k_gather<2, TAN><<<grid, kGatherThreads, 0, s>>>(a); break;
+    case 3: k_gather<3, TAN><<<grid, kGatherThreads, 0, s>>>(a); break;
+    case 4: k_gather<4, TAN><<<grid, kGatherThreads, 0, s>>>(a); break;
+    case 5: k_gather<5, TAN><<<grid, kGatherThreads, 0, s>>>(a); break;
+    case 6: k_gather<6, TAN><<<grid, kGatherThreads, 0, s>>>(a); break;
+    case 7: k_gather<7, TAN><<<grid, kGatherThreads, 0, s>>>(a); break;
+    default: return set_error(p, PME_ERR_ARG, "spline order out of range");
+  }
+  count_launch();
+  return check_launch(p, "k_gather");
+}
+
+}  // namespace
+
+int launch_gather(pme_plan_t p, cudaStream_t s, int n, const float* phi_mesh,
+                  const float* dphi_mesh, bool tangent, const IonInputs& in,
+                  const double* g_energy, float* out) {
+  (void)in;
+  return tangent ? launch_t<true>(p, s, n, phi_mesh, dphi_mesh, g_energy, out)
+                 : launch_t<false>(p, s, n, phi_mesh, nullptr, nullptr, out);
+}
+
+}  // namespace gbpme

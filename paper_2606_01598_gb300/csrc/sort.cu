@@ -1,0 +1,248 @@
+// Sorting ions into mesh bricks and pair cells.
+//
+// Every ion gets two keys in one pass: the brick holding its first stencil point m0
+// (Section 2.3.2, Eq. w3d) and the pair cell holding its position. A counting sort orders
+// them: k_bin counts (one integer atomic per ion and key, never per stencil point), k_scan
+// turns the counts into segment starts, k_scatter places ions in arrival order, and
+// k_rank_records re-ranks each segment by caller index, which makes the order -- and hence
+// every later sum -- deterministic, while writing the per-ion records both orders need.
+#include "kernels.h"
+
+namespace gbpme {
+
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kRankMaxSegment = 2048;   // longer segments keep arrival order
+
+__global__ void __launch_bounds__(kSortThreads)
+k_bin(Geometry g, IonInputs in, SortBuffers sb, int* flags, int tangent, int max_blocks) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double qv = 0.0, dqv = 0.0;
+  if (i < in.n) {
+    const float rx = in.pos[3 * i], ry = in.pos[3 * i + 1], rz = in.pos[3 * i + 2];
+    const float qi = in.q ? in.q[i] : 0.f;
+    bool ok = isfinite(rx) && isfinite(ry) && isfinite(rz) && isfinite(qi);
+    if (in.mu) ok = ok && isfinite(in.mu[3 * i]) && isfinite(in.mu[3 * i + 1]) &&
+                    isfinite(in.mu[3 * i + 2]);
+    if (!ok) atomicOr(flags, kFlagNonFinite);
+    double s[3];
+    frac_coords(g, rx, ry, rz, s);
+    int m0[3], c[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      float f;
+      stencil_origin(s[b], g.N[b], g.order, m0[b], f);
+      cell_origin(s[b], g.ncell[b], c[b], f);
+    }
+    const int kb = ((m0[0] / g.brick[0]) * g.nb[1] + m0[1] / g.brick[1]) * g.nb[2] +
+                   m0[2] / g.brick[2];
+    const int kc = (c[0] * g.ncell[1] + c[1]) * g.ncell[2] + c[2];
+    sb.key_b[i] = kb;
+    sb.key_c[i] = kc;
+    sb.slot_b[i] = atomicAdd(&sb.count_b[kb], 1);
+    sb.slot_c[i] = atomicAdd(&sb.count_c[kc], 1);
+    qv = ok ? double(qi) : 0.0;
+    if (tangent && in.gphi) dqv = double(in.gphi[i]);
+  }
+  const double a = block_sum_d(qv);
+  const double b = block_sum_d(dqv);
+  if (threadIdx.x == 0) {
+    sb.qpart[blockIdx.x] = a;
+    sb.qpart[max_blocks + blockIdx.x] = b;
+  }
+}
+
+// Exclusive scan of one count array by one block of 1024 threads; start[n] = total.
+__device__ void block_exclusive_scan(const int* count, int* start, int n) {
+  __shared__ int warp_tot[32];
+  const int T = blockDim.x;
+  const int chunk = (n + T - 1) / T;
+  const int lo = min(n, threadIdx.x * chunk), hi = min(n, lo + chunk);
+  int local = 0;
+  for (int k = lo; k < hi; ++k) local += count[k];
+  // inclusive warp scan of the per-thread totals
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int v = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  if (lane == 31) warp_tot[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    int w = (lane < (T >> 5)) ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += u;
+    }
+    warp_tot[lane] = w;   // inclusive prefix over warps
+  }
+  __syncthreads();
+  int run = v - local + (wid > 0 ? warp_tot[wid - 1] : 0);
+  for (int k = lo; k < hi; ++k) {
+    start[k] = run;
+    run += count[k];
+  }
+  if (threadIdx.x == T - 1) start[n] = run;
+}
+
+__global__ void __launch_bounds__(1024)
+k_scan(SortBuffers sb, int nbricks, int ncells, int nblocks, int max_blocks) {
+  if (blockIdx.x == 0) {
+    block_exclusive_scan(sb.count_b, sb.start_b, nbricks);
+  } else if (blockIdx.x == 1) {
+    block_exclusive_scan(sb.count_c, sb.start_c, ncells);
+  } else {
+    // Q and dQ in a fixed order: thread t sums partials t, t + T, ...
+    double a = 0.0, b = 0.0;
+    for (int k = threadIdx.x; k < nblocks; k += blockDim.x) {
+      a += sb.qpart[k];
+      b += sb.qpart[max_blocks + k];
+    }
+    a = block_sum_d(a);
+    b = block_sum_d(b);
+    if (threadIdx.x == 0) {
+      sb.qsum[0] = a;
+      sb.qsum[1] = b;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+k_scatter(int n, SortBuffers sb, int need_mesh, int need_pair) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (need_mesh) sb.perm_b[sb.start_b[sb.key_b[i]] + sb.slot_b[i]] = i;
+  if (need_pair) sb.perm_c[sb.start_c[sb.key_c[i]] + sb.slot_c[i]] = i;
+}
+
+__device__ __forceinline__ int stable_rank(const int* perm, int seg_lo, int seg_hi, int self,
+                                           int fallback) {
+  if (seg_hi - seg_lo > kRankMaxSegment) return fallback;
+  int r = 0;
+  for (int u = seg_lo; u < seg_hi; ++u) r += (perm[u] < self) ? 1 : 0;
+  return seg_lo + r;
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+k_rank_records(Geometry g, IonInputs in, SortBuffers sb, MeshRecords mr, PairRecords pr,
+               int tangent, int need_mesh, int need_pair) {
+  const int n = in.n;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool mesh_side = t < n;
+  if (!mesh_side) t -= n;
+  if (t >= n) return;
+  if (mesh_side && !need_mesh) return;
+  if (!mesh_side && !need_pair) return;
+  const int i = mesh_side ? sb.perm_b[t] : sb.perm_c[t];
+  int dest;
+  if (mesh_side) {
+    const int k = sb.key_b[i];
+    dest = stable_rank(sb.perm_b, sb.start_b[k], sb.start_b[k + 1], i, t);
+  } else {
+    const int k = sb.key_c[i];
+    dest = stable_rank(sb.perm_c, sb.start_c[k], sb.start_c[k + 1], i, t);
+  }
+  const float rx = in.pos[3 * i], ry = in.pos[3 * i + 1], rz = in.pos[3 * i + 2];
+  float qi = in.q ? in.q[i] : 0.f;
+  float mu[3] = {0.f, 0.f, 0.f};
+  if (in.mu) {
+    mu[0] = in.mu[3 * i];
+    mu[1] = in.mu[3 * i + 1];
+    mu[2] = in.mu[3 * i + 2];
+  }
+  if (!isfinite(qi)) qi = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (!isfinite(mu[a])) mu[a] = 0.f;
+  double s[3];
+  frac_coords(g, rx, ry, rz, s);
+  float dq = 0.f, dr[3] = {0.f, 0.f, 0.f}, dmu[3] = {0.f, 0.f, 0.f};
+  if (tangent) {
+    if (in.gphi) dq = in.gphi[i];
+    if (in.gforce) {
+      dr[0] = -in.gforce[3 * i];
+      dr[1] = -in.gforce[3 * i + 1];
+      dr[2] = -in.gforce[3 * i + 2];
+    }
+    if (in.gfield) {
+      dmu[0] = -in.gfield[3 * i];
+      dmu[1] = -in.gfield[3 * i + 1];
+      dmu[2] = -in.gfield[3 * i + 2];
+    }
+  }
+  // tangent dipole source d' = dmu + q dr
+  const float dp[3] = {dmu[0] + qi * dr[0], dmu[1] + qi * dr[1], dmu[2] + qi * dr[2]};
+  if (mesh_side) {
+    int m0[3];
+    float f[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) stencil_origin(s[b], g.N[b], g.order, m0[b], f[b]);
+    float pm[3], pd[3], pt[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      pm[b] = mu[0] * g.D[0 * 3 + b] + mu[1] * g.D[1 * 3 + b] + mu[2] * g.D[2 * 3 + b];
+      pd[b] = dp[0] * g.D[0 * 3 + b] + dp[1] * g.D[1 * 3 + b] + dp[2] * g.D[2 * 3 + b];
+      pt[b] = dr[0] * g.D[0 * 3 + b] + dr[1] * g.D[1 * 3 + b] + dr[2] * g.D[2 * 3 + b];
+    }
+    mr.idx[dest] = make_int4(m0[0], m0[1], m0[2], i);
+    mr.fq[dest] = make_float4(f[0], f[1], f[2], qi);
+    mr.dm[dest] = make_float4(pm[0], pm[1], pm[2], 0.f);
+    if (tangent) {
+      mr.tq[dest] = make_float4(dq, pd[0], pd[1], pd[2]);
+      mr.tt[dest] = make_float4(pt[0], pt[1], pt[2], 0.f);
+    }
+  } else {
+    int c[3];
+    float f[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) cell_origin(s[b], g.ncell[b], c[b], f[b]);
+    pr.idx[dest] = make_int4(c[0], c[1], c[2], i);
+    pr.fq[dest] = make_float4(f[0], f[1], f[2], qi);
+    pr.mu[dest] = make_float4(mu[0], mu[1], mu[2], 0.f);
+    if (tangent) {
+      pr.tq[dest] = make_float4(dq, dp[0], dp[1], dp[2]);
+      pr.dr[dest] = make_float4(dr[0], dr[1], dr[2], 0.f);
+    }
+  }
+}
+
+}  // namespace
+
+int launch_sort(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent, bool need_mesh,
+                bool need_pair) {
+  const int n = in.n;
+  const int nblk = (n + kSortThreads - 1) / kSortThreads;
+  int st = check_cuda(p, cudaMemsetAsync(p->sb.count_b, 0, sizeof(int) * (p->nbricks + 1), s),
+                      "memset brick counts");
+  if (st) return st;
+  st = check_cuda(p, cudaMemsetAsync(p->sb.count_c, 0, sizeof(int) * (p->ncells + 1), s),
+                  "memset cell counts");
+  if (st) return st;
+  if (nblk > 0) {
+    k_bin<<<nblk, kSortThreads, 0, s>>>(p->g, in, p->sb, p->flags, tangent ? 1 : 0,
+                                        p->max_blocks);
+    count_launch();
+    if ((st = check_launch(p, "k_bin"))) return st;
+  }
+  k_scan<<<3, 1024, 0, s>>>(p->sb, p->nbricks, p->ncells, nblk, p->max_blocks);
+  count_launch();
+  if ((st = check_launch(p, "k_scan"))) return st;
+  if (nblk > 0) {
+    k_scatter<<<nblk, kSortThreads, 0, s>>>(n, p->sb, need_mesh ? 1 : 0, need_pair ? 1 : 0);
+    count_launch();
+    if ((st = check_launch(p, "k_scatter"))) return st;
+    const int nblk2 = (2 * n + kSortThreads - 1) / kSortThreads;
+    k_rank_records<<<nblk2, kSortThreads, 0, s>>>(p->g, in, p->sb, p->mr, p->pr,
+                                                  tangent ? 1 : 0, need_mesh ? 1 : 0,
+                                                  need_pair ? 1 : 0);
+    count_launch();
+    if ((st = check_launch(p, "k_rank_records"))) return st;
+  }
+  return PME_OK;
+}
+
+}  // namespace gbpme

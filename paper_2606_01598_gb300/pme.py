@@ -1,0 +1,293 @@
+"""Python face of libgbpme: a plan object over the C ABI and a differentiable energy.
+
+Every step of the computation runs in the library's CUDA kernels (and cuFFT for the two 3D
+transforms); this module only allocates output tensors, passes pointers and the current CUDA
+stream, and wires the adjoint into torch.autograd:
+
+  E = PMEEnergy.apply(plan, pos, q, mu)
+  F = -torch.autograd.grad(E, pos, create_graph=True)[0]      # Eq. forces
+  loss = ((F - F_ref) ** 2).mean(); loss.backward()           # Eq. loss: double backward
+
+The first derivatives come from pme_forward; the derivative of those derivatives (the
+Hessian-vector product the force-matching loss needs) from pme_backward, which recomputes
+the mesh potential instead of storing it.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import PMEError, PMEOpts
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(device):
+    if device.type != "cuda":
+        return None
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _f32(t, device):
+    if t is None:
+        return None
+    t = torch.as_tensor(t)
+    if device.type == "cuda":
+        t = t.to(device=device)
+    return t.to(torch.float32).contiguous()
+
+
+def mesh_dims(box, spacing: float, rule: int = 0, strategy: int = 1, clamp=(0, 0)):
+    """Mesh-size rules of Section 2.3.1 (see pme_mesh_dims in include/gbpme.h)."""
+    lib = _abi.load()
+    b = (ctypes.c_double * 9)(*np.asarray(box, np.float64).reshape(9))
+    m = (ctypes.c_int * 3)()
+    st = lib.pme_mesh_dims(b, float(spacing), int(rule), int(strategy), int(clamp[0]), int(clamp[1]), m)
+    if st:
+        raise PMEError(st, "pme_mesh_dims")
+    return [m[0], m[1], m[2]]
+
+
+def launch_count() -> int:
+    return int(_abi.load().pme_launch_count())
+
+
+class Plan:
+    """One box, mesh, spline order, alpha and cutoff; owns all device scratch."""
+
+    def __init__(self, box, mesh, order: int, alpha: float, rcut: float, *,
+                 influence_power: float = 1.0, deconvolution: bool = True,
+                 coulomb_k: float = 1.0, include_pair: bool = True, include_self: bool = True,
+                 include_background: bool = True, max_ions: int = 1 << 18, device=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("gbpme needs a CUDA device; there is no CPU fallback")
+        self.lib = _abi.load()
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        if dev.type != "cuda":
+            raise ValueError("a plan lives on a CUDA device")
+        if dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        torch.cuda.init()
+        opts = PMEOpts()
+        self.lib.pme_opts_default(ctypes.byref(opts))
+        opts.influence_power = float(influence_power)
+        opts.deconvolution = int(bool(deconvolution))
+        opts.coulomb_k = float(coulomb_k)
+        opts.include_pair = int(bool(include_pair))
+        opts.include_self = int(bool(include_self))
+        opts.include_background = int(bool(include_background))
+        opts.max_ions = int(max_ions)
+        self.box = np.asarray(box, np.float64).reshape(3, 3).copy()
+        self.mesh = tuple(int(x) for x in mesh)
+        self.order = int(order)
+        self.alpha = float(alpha)
+        self.rcut = float(rcut)
+        self.coulomb_k = float(coulomb_k)
+        self.max_ions = int(max_ions)
+        b = (ctypes.c_double * 9)(*self.box.reshape(9))
+        m = (ctypes.c_int * 3)(*self.mesh)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self.lib.pme_plan_create(ctypes.byref(h), b, m, self.order, self.alpha, self.rcut,
+                                          ctypes.byref(opts))
+        if st:
+            raise PMEError(st, "pme_plan_create")
+        self.handle = h
+
+    # -- helpers ---------------------------------------------------------------------------
+    def _check(self, st, where):
+        if st:
+            raise PMEError(st, where, self.lib.pme_last_error(self.handle).decode())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.pme_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_box(self, box):
+        self.box = np.asarray(box, np.float64).reshape(3, 3).copy()
+        b = (ctypes.c_double * 9)(*self.box.reshape(9))
+        self._check(self.lib.pme_plan_set_box(self.handle, b), "pme_plan_set_box")
+
+    def sync_status(self):
+        with torch.cuda.device(self.device):
+            self._check(self.lib.pme_sync_status(self.handle, _stream_handle(self.device)),
+                        "pme_sync_status")
+
+    def profile(self, enable: bool = True):
+        """Turn the per-stage CUDA-event timers on or off (see pme_profile_enable)."""
+        self._check(self.lib.pme_profile_enable(self.handle, int(bool(enable))), "pme_profile_enable")
+
+    def profile_read(self):
+        """{'fwd.spread': (ms_total, calls), ...} since the last read; resets the timers."""
+        ms = (ctypes.c_double * _abi.NUM_STAGES)()
+        calls = (ctypes.c_longlong * _abi.NUM_STAGES)()
+        with torch.cuda.device(self.device):
+            self._check(self.lib.pme_profile_read(self.handle, ms, calls), "pme_profile_read")
+        out = {}
+        for k in range(_abi.NUM_STAGES):
+            name = ("fwd." if k < 9 else "bwd.") + _abi.STAGE_NAMES[k % 9]
+            if calls[k]:
+                out[name] = (float(ms[k]), int(calls[k]))
+        return out
+
+    @property
+    def M(self):
+        return int(np.prod(self.mesh))
+
+    # -- full passes -----------------------------------------------------------------------
+    def forward(self, pos, q, mu=None, *, energy=True, force=True, phi=True, field=True,
+                field_grad=False):
+        """Energy and derivatives. Device tensors stay on the device; CPU tensors are passed as
+        host pointers (the library stages them). Returns a dict of tensors."""
+        dev = pos.device if isinstance(pos, torch.Tensor) else torch.device("cpu")
+        on_dev = dev.type == "cuda"
+        pos = _f32(pos, dev)
+        q = _f32(q, dev)
+        mu = _f32(mu, dev)
+        n = int(pos.shape[0])
+        pin = (not on_dev)
+        alloc = dict(device=dev, pin_memory=pin) if pin else dict(device=dev)
+        out = {}
+        if energy:
+            out["energy"] = torch.empty(1, dtype=torch.float64, **alloc)
+        if force:
+            out["force"] = torch.empty((n, 3), dtype=torch.float32, **alloc)
+        if phi:
+            out["phi"] = torch.empty(n, dtype=torch.float32, **alloc)
+        if field:
+            out["field"] = torch.empty((n, 3), dtype=torch.float32, **alloc)
+        if field_grad:
+            out["field_grad"] = torch.empty((n, 6), dtype=torch.float32, **alloc)
+        with torch.cuda.device(self.device):
+            st = self.lib.pme_forward(self.handle, _stream_handle(self.device), n, _ptr(pos), _ptr(q),
+                                      _ptr(mu), _ptr(out.get("energy")), _ptr(out.get("force")),
+                                      _ptr(out.get("phi")), _ptr(out.get("field")),
+                                      _ptr(out.get("field_grad")))
+            self._check(st, "pme_forward")
+            if not on_dev:
+                torch.cuda.current_stream(self.device).synchronize()
+        return out
+
+    def backward(self, pos, q, mu=None, g_energy=None, g_force=None, g_phi=None, g_field=None):
+        """Vector-Jacobian product of (pos, q, mu) -> (E, force, phi, field)."""
+        dev = pos.device if isinstance(pos, torch.Tensor) else torch.device("cpu")
+        on_dev = dev.type == "cuda"
+        pos = _f32(pos, dev)
+        q = _f32(q, dev)
+        mu = _f32(mu, dev)
+        g_force = _f32(g_force, dev)
+        g_phi = _f32(g_phi, dev)
+        g_field = _f32(g_field, dev)
+        if g_energy is not None:
+            g_energy = torch.as_tensor(g_energy, dtype=torch.float64).reshape(1)
+            g_energy = g_energy.to(dev).contiguous()
+        n = int(pos.shape[0])
+        alloc = dict(device=dev, pin_memory=True) if not on_dev else dict(device=dev)
+        gp = torch.empty((n, 3), dtype=torch.float32, **alloc)
+        gq = torch.empty(n, dtype=torch.float32, **alloc)
+        gm = torch.empty((n, 3), dtype=torch.float32, **alloc)
+        with torch.cuda.device(self.device):
+            st = self.lib.pme_backward(self.handle, _stream_handle(self.device), n, _ptr(pos), _ptr(q),
+                                       _ptr(mu), _ptr(g_energy), _ptr(g_force), _ptr(g_phi),
+                                       _ptr(g_field), _ptr(gp), _ptr(gq), _ptr(gm))
+            self._check(st, "pme_backward")
+            if not on_dev:
+                torch.cuda.current_stream(self.device).synchronize()
+        return gp, gq, gm
+
+    # -- stage-level entry points (device tensors) -------------------------------------------
+    def spread(self, pos, q, mu=None):
+        pos, q, mu = (_f32(t, self.device) for t in (pos, q, mu))
+        rho = torch.empty(self.mesh, dtype=torch.float32, device=self.device)
+        with torch.cuda.device(self.device):
+            self._check(self.lib.pme_spread(self.handle, _stream_handle(self.device), int(pos.shape[0]),
+                                            _ptr(pos), _ptr(q), _ptr(mu), _ptr(rho)), "pme_spread")
+        return rho
+
+    def solve(self, rho):
+        rho = _f32(rho, self.device)
+        phi = torch.empty(self.mesh, dtype=torch.float32, device=self.device)
+        e = torch.empty(1, dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            self._check(self.lib.pme_solve(self.handle, _stream_handle(self.device), _ptr(rho), _ptr(phi),
+                                           _ptr(e)), "pme_solve")
+        return phi, e
+
+    def gather(self, pos, phi_mesh):
+        pos = _f32(pos, self.device)
+        phi_mesh = _f32(phi_mesh, self.device)
+        out = torch.empty((pos.shape[0], 10), dtype=torch.float32, device=self.device)
+        with torch.cuda.device(self.device):
+            self._check(self.lib.pme_gather(self.handle, _stream_handle(self.device), int(pos.shape[0]),
+                                            _ptr(pos), _ptr(phi_mesh), _ptr(out)), "pme_gather")
+        return out
+
+    def pair(self, pos, q, mu=None):
+        pos, q, mu = (_f32(t, self.device) for t in (pos, q, mu))
+        out = torch.empty((pos.shape[0], 10), dtype=torch.float32, device=self.device)
+        e = torch.empty(1, dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            self._check(self.lib.pme_pair(self.handle, _stream_handle(self.device), int(pos.shape[0]),
+                                          _ptr(pos), _ptr(q), _ptr(mu), _ptr(out), _ptr(e)), "pme_pair")
+        return out, e
+
+
+# ------------------------------------------------------------------------------------------
+# autograd
+# ------------------------------------------------------------------------------------------
+
+class _PMEGrad(torch.autograd.Function):
+    """(pos, q, mu) -> (dE/dr, dE/dq, dE/dmu); its VJP is the Hessian-vector product."""
+
+    @staticmethod
+    def forward(ctx, plan, pos, q, mu, dEdr, dEdq, dEdmu):
+        ctx.plan = plan
+        ctx.save_for_backward(pos, q, mu)
+        return dEdr.clone(), dEdq.clone(), dEdmu.clone()
+
+    @staticmethod
+    def backward(ctx, v_r, v_q, v_mu):
+        pos, q, mu = ctx.saved_tensors
+        z = lambda t, like: torch.zeros_like(like) if t is None else t
+        v_r, v_q, v_mu = z(v_r, pos), z(v_q, q), z(v_mu, mu)
+        gp, gq, gm = ctx.plan.backward(pos.detach(), q.detach(), mu.detach(), None,
+                                       -v_r.detach(), v_q.detach(), -v_mu.detach())
+        return None, gp, gq, gm, None, None, None
+
+
+class PMEEnergy(torch.autograd.Function):
+    """Differentiable total energy of Eq. (1) of include/gbpme.h, twice differentiable."""
+
+    @staticmethod
+    def forward(ctx, plan, pos, q, mu):
+        out = plan.forward(pos.detach(), q.detach(), mu.detach(), energy=True, force=True,
+                           phi=True, field=True)
+        ctx.plan = plan
+        ctx.save_for_backward(pos, q, mu, out["force"], out["phi"], out["field"])
+        return out["energy"].reshape(())
+
+    @staticmethod
+    def backward(ctx, gE):
+        pos, q, mu, F, phi, field = ctx.saved_tensors
+        dEdr, dEdq, dEdmu = _PMEGrad.apply(ctx.plan, pos, q, mu, -F, phi, -field)
+        g = gE.to(torch.float32)
+        return None, g * dEdr, g * dEdq, g * dEdmu
+
+
+def pme_energy(plan: Plan, pos, q, mu=None):
+    if mu is None:
+        mu = torch.zeros_like(pos)
+    return PMEEnergy.apply(plan, pos, q, mu)

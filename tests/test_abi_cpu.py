@@ -1,0 +1,60 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports every function
+the public header declares, and its host-only mesh-size rule agrees with the oracle's."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import meshdims
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2606_01598_gb300 as g
+    from paper_2606_01598_gb300 import build as b
+    b.build()
+    return g.load_library()
+
+
+def test_every_header_symbol_is_exported(lib):
+    import paper_2606_01598_gb300 as g
+    names = g.header_functions()
+    assert len(names) >= 14
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    for s in range(8):
+        assert lib.pme_status_string(s)
+    assert lib.pme_last_error(None) == b"null plan"
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+@pytest.mark.parametrize("strategy", [0, 1, 2])
+def test_mesh_dims_matches_oracle(lib, rule, strategy):
+    import paper_2606_01598_gb300 as g
+    names = {0: "pow2", 1: "smooth", 2: "ceil"}
+    rules = {0: "paper", 1: "spacing"}
+    rng = np.random.default_rng(rule * 3 + strategy)
+    for _ in range(50):
+        box = np.diag(rng.uniform(5, 120, size=3))
+        box[1, 0] = rng.uniform(-3, 3)
+        sp = rng.uniform(0.2, 1.5)
+        got = g.mesh_dims(box, sp, rule, strategy)
+        ref = meshdims.mesh_dims(box, sp, names[strategy], rules[rule])
+        assert got == ref
+
+
+def test_mesh_dims_rejects_bad_arguments(lib):
+    m = (ctypes.c_int * 3)()
+    b = (ctypes.c_double * 9)(*np.eye(3).reshape(9))
+    assert lib.pme_mesh_dims(b, 0.0, 0, 1, 0, 0, m) == 1
+    assert lib.pme_mesh_dims(b, 0.5, 2, 1, 0, 0, m) == 1
+    assert lib.pme_mesh_dims(b, 0.5, 0, 3, 0, 0, m) == 1
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.pme_plan_destroy(None) == 1
+    assert lib.pme_forward(None, None, 0, *([None] * 8)) == 1
+    assert lib.pme_backward(None, None, 0, *([None] * 10)) == 1

@@ -1,0 +1,111 @@
+"""Parity of pme_backward (the vector-Jacobian product of (pos, q, mu) -> (E, F, phi, field),
+i.e. the gradient plus the Hessian-vector product) against O2's double backward, and of the
+autograd wrapper (double backward through forces) against the same loss on the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import pme as O2
+
+from gpu_util import TOL_HVP, f32, prepared, relrmse
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2606_01598_gb300 as g
+    return g
+
+
+CASES = {
+    "nacl512_p6": lambda: (W.molten_nacl(512, seed=201), (32, 32, 32), 6, 0.30, 9.0),
+    "nacl64_images_p5": lambda: (W.molten_nacl(64, seed=202), (16, 16, 16), 5, 0.30, 9.0),
+    "nacl1000_ragged_p7": lambda: (W.molten_nacl(1000, seed=203), (27, 30, 25), 7, 0.35, 8.0),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("gE", [0.0, 0.7])
+def test_backward_matches_double_backward(gb, name, gE):
+    fr, mesh, p, a, rc = CASES[name]()
+    pos, q, mu = prepared(fr)
+    gF, gphi, gfield = (f32(x) for x in W.tangent(fr.n, scale=1.0, seed=9))
+    o = O2.PMEOracle(fr.box, mesh, p, a, rc)
+    ref = o.hvp(pos, q, mu, gE, gF, gphi, gfield)
+    plan = gb.Plan(fr.box, mesh, p, a, rc, max_ions=max(1024, fr.n))
+    c = lambda x: torch.tensor(np.float32(x), device="cuda")
+    got = plan.backward(c(pos), c(q), c(mu), torch.tensor([gE], dtype=torch.float64, device="cuda"),
+                        c(gF), c(gphi), c(gfield))
+    for g, r, what in zip(got, ref, ("grad_pos", "grad_q", "grad_mu")):
+        err = relrmse(g.cpu().numpy(), r)
+        assert err < TOL_HVP, (what, err)
+
+
+def test_backward_single_cotangents(gb):
+    # each cotangent alone (force, phi, field), so no term hides behind another
+    fr, mesh, p, a, rc = CASES["nacl512_p6"]()
+    pos, q, mu = prepared(fr)
+    gF, gphi, gfield = (f32(x) for x in W.tangent(fr.n, seed=11))
+    z3, z1 = np.zeros_like(gF), np.zeros_like(gphi)
+    o = O2.PMEOracle(fr.box, mesh, p, a, rc)
+    plan = gb.Plan(fr.box, mesh, p, a, rc, max_ions=1024)
+    c = lambda x: torch.tensor(np.float32(x), device="cuda")
+    for args in ((gF, z1, z3), (z3, gphi, z3), (z3, z1, gfield)):
+        ref = o.hvp(pos, q, mu, 0.0, *args)
+        got = plan.backward(c(pos), c(q), c(mu), None, *(c(x) for x in args))
+        for g, r in zip(got, ref):
+            assert relrmse(g.cpu().numpy(), r) < TOL_HVP
+
+
+def test_backward_energy_only_is_gradient(gb):
+    fr, mesh, p, a, rc = CASES["nacl512_p6"]()
+    pos, q, mu = prepared(fr)
+    plan = gb.Plan(fr.box, mesh, p, a, rc, max_ions=1024)
+    c = lambda x: torch.tensor(np.float32(x), device="cuda")
+    fw = plan.forward(c(pos), c(q), c(mu))
+    gp, gq, gm = plan.backward(c(pos), c(q), c(mu), torch.tensor([2.0], dtype=torch.float64, device="cuda"))
+    assert relrmse(gp.cpu().numpy(), -2 * fw["force"].cpu().numpy()) < 1e-6
+    assert relrmse(gq.cpu().numpy(), 2 * fw["phi"].cpu().numpy()) < 1e-6
+    assert relrmse(gm.cpu().numpy(), -2 * fw["field"].cpu().numpy()) < 1e-6
+
+
+def test_autograd_force_matching_double_backward(gb):
+    fr, mesh, p, a, rc = CASES["nacl512_p6"]()
+    pos, q, mu = prepared(fr)
+    Fref = f32(np.random.default_rng(4).normal(0, 0.05, size=(fr.n, 3)))
+    plan = gb.Plan(fr.box, mesh, p, a, rc, max_ions=1024)
+
+    def loss_of(pos_t, q_t, mu_t, energy_fn):
+        E = energy_fn(pos_t, q_t, mu_t)
+        F = -torch.autograd.grad(E, pos_t, create_graph=True)[0]
+        return E, ((F - torch.as_tensor(Fref, dtype=F.dtype, device=F.device)) ** 2).sum()
+
+    dev = [torch.tensor(np.float32(x), device="cuda", requires_grad=True) for x in (pos, q, mu)]
+    E, L = loss_of(*dev, lambda a_, b_, c_: gb.pme_energy(plan, a_, b_, c_))
+    L.backward()
+    o = O2.PMEOracle(fr.box, mesh, p, a, rc)
+    cpu = [torch.tensor(x, dtype=torch.float64, requires_grad=True) for x in (pos, q, mu)]
+    pairs = o._pairs(pos)
+    E2, L2 = loss_of(*cpu, lambda a_, b_, c_: o.energy(a_, b_, c_, pairs))
+    L2.backward()
+    assert abs(L.item() - L2.item()) < 1e-4 * abs(L2.item())
+    for t_gpu, t_cpu in zip(dev, cpu):
+        assert relrmse(t_gpu.grad.cpu().numpy(), t_cpu.grad.numpy()) < TOL_HVP
+
+
+def test_backward_host_pointer_path(gb):
+    fr, mesh, p, a, rc = CASES["nacl64_images_p5"]()
+    pos, q, mu = prepared(fr)
+    gF, gphi, gfield = (f32(x) for x in W.tangent(fr.n, seed=3))
+    plan = gb.Plan(fr.box, mesh, p, a, rc, max_ions=256)
+    c = lambda x: torch.tensor(np.float32(x), device="cuda")
+    gE = torch.tensor([0.3], dtype=torch.float64)
+    d = plan.backward(c(pos), c(q), c(mu), gE.cuda(), c(gF), c(gphi), c(gfield))
+    h = plan.backward(*(c(x).cpu().pin_memory() for x in (pos, q, mu)), gE.pin_memory(),
+                      *(c(x).cpu().pin_memory() for x in (gF, gphi, gfield)))
+    for x, y in zip(d, h):
+        assert torch.equal(x.cpu(), y)
