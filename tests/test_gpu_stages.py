@@ -133,7 +133,10 @@ def test_pair_matches_oracle(gb, name):
     plan = gb.Plan(box, (16, 16, 16), 4, 0.3, rc, max_ions=2048)
     out, E = plan.pair(*_cuda(pos, q, mu))
     out = out.cpu().numpy()
-    assert abs(E.item() - E_ref) < 1e-6 * abs(E_ref)
+    # the pair energy alone is a sum of terms of both signs that nearly cancel; its error is
+    # measured against the size of those terms, 1/2 sum |q phi| + |mu . grad phi|
+    scale = 0.5 * np.sum(np.abs(q * phi) + np.abs(np.einsum("ik,ik->i", mu, g)))
+    assert abs(E.item() - E_ref) < TOL_E * scale
     assert relmax(out[:, 0], phi) < TOL_MESH
     assert relmax(out[:, 1:4], g) < TOL_MESH
     assert relmax(out[:, 4:], sym6(H)) < TOL_MESH
