@@ -46,7 +46,11 @@ _SIGS = {
     "pme_launch_count": (ctypes.c_longlong, []),
     "pme_profile_enable": (c_int, [c_void_p, c_int]),
     "pme_profile_read": (c_int, [c_void_p, c_double_p, ctypes.POINTER(ctypes.c_longlong)]),
+    "pme_spread_noalloc": (c_int, [c_void_p, c_double_p, c_int_p, c_int, c_int] + [c_void_p] * 4),
 }
+
+NOALLOC_MAX_IONS = 32768
+NOALLOC_MAX_MESH = 128
 
 NUM_STAGES = 18
 STAGE_NAMES = ["sort", "spread", "fft_r2c", "influence", "fft_c2r", "gather", "pair",

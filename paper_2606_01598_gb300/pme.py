@@ -53,6 +53,28 @@ def mesh_dims(box, spacing: float, rule: int = 0, strategy: int = 1, clamp=(0, 0
     return [m[0], m[1], m[2]]
 
 
+def spread_noalloc(box, mesh, order: int, pos, q, mu=None):
+    """pme_spread_noalloc: the mesh density without a plan and without any device allocation
+    (for callers that cannot allocate; see include/gbpme.h). Device tensors in; rho is
+    allocated here by torch only because this helper returns a new tensor -- callers that
+    cannot allocate pass their own output through the C ABI."""
+    lib = _abi.load()
+    dev = pos.device
+    pos, q, mu = (_f32(t, dev) for t in (pos, q, mu))
+    if pos.shape[0] > _abi.NOALLOC_MAX_IONS or max(mesh) > _abi.NOALLOC_MAX_MESH:
+        raise ValueError(f"pme_spread_noalloc takes at most {_abi.NOALLOC_MAX_IONS} ions and "
+                         f"mesh dimensions up to {_abi.NOALLOC_MAX_MESH}")
+    rho = torch.empty(tuple(int(m) for m in mesh), dtype=torch.float32, device=dev)
+    b = (ctypes.c_double * 9)(*np.asarray(box, np.float64).reshape(9))
+    m = (ctypes.c_int * 3)(*[int(x) for x in mesh])
+    with torch.cuda.device(dev):
+        st = lib.pme_spread_noalloc(_stream_handle(dev), b, m, int(order), int(pos.shape[0]),
+                                    _ptr(pos), _ptr(q), _ptr(mu), _ptr(rho))
+    if st:
+        raise PMEError(st, "pme_spread_noalloc")
+    return rho
+
+
 def launch_count() -> int:
     return int(_abi.load().pme_launch_count())
 
