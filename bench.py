@@ -50,6 +50,22 @@ def stage_bytes(stage: str, N: int, M: int, Mh: int) -> float:
     return float(table.get(stage, 0.0))
 
 
+# Pair term (ALU bound): float32 operations per pair inside rcut, counted from the formulas
+# in csrc/pair.cu (a fused multiply-add counts 2, each reciprocal, square root, exponential
+# or erfc evaluation counts 1): forward 80 (radial functions B0..B3, phi, grad phi, the
+# 6-component Hessian), backward 450 (B0..B4, the g2 / g3 / g4 contractions of the primal
+# and tangent potentials, and the folding into the seven outputs). Candidate tests outside
+# rcut are not counted.
+PAIR_FLOPS = {"fwd.pair": 80.0, "bwd.pair": 450.0}
+# FP32 peak for the ALU bound: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def pairs_per_ion(n: int, volume: float, rcut: float) -> float:
+    """Expected partners inside rcut at uniform density (the molten-NaCl generator's)."""
+    return (n - 1) / volume * 4.0 / 3.0 * math.pi * rcut ** 3
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -60,7 +76,7 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling every 200 ms while the benchmark runs."""
+    """nvidia-smi clock / throttle sampling every 50 ms while the benchmark runs."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -73,7 +89,7 @@ class ClockSampler:
         self.thread = None
 
     def start(self):
-        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50"]
         if self.uuid:
             cmd += ["-i", self.uuid]
         try:
@@ -261,13 +277,37 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
     total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, stops))
-    stages = plan.profile_read()
     plan.profile(False)
+    plan.profile_read()
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     if ws > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_per_step = float(t.item()) / args.steps
     value = ws * n / (ms_per_step / 1e3) / 1e6
+
+    # ---- per-kernel times: the same K steps with the pair term on the call's stream ---------
+    # (stage events then bracket one kernel at a time; the overlapped run above is the value)
+    splan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=n,
+                    device=dev, overlap_pair=False)
+
+    def sstep():
+        splan.forward(pos, q, mu, energy=True, force=True, phi=True, field=True)
+        splan.backward(pos, q, mu, gE, gF, gphi, gfield)
+
+    for _ in range(args.warmup):
+        sstep()
+    splan.profile(True)
+    s_ms = 0.0
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record()
+        sstep()
+        stops[k].record()
+    torch.cuda.synchronize(dev)
+    s_ms = sum(a.elapsed_time(b) for a, b in zip(starts, stops)) / args.steps
+    stages = splan.profile_read()
+    splan.profile(False)
+    splan.close()
 
     # ---- end to end through the public API with pinned host buffers ------------------------
     hp = [x.cpu().pin_memory() for x in (pos, q, mu, gF, gphi, gfield)]
@@ -296,18 +336,27 @@ def run_ours(args):
         ours = {k: v for k, v in stages.items() if "fft" not in k}
         dom = max(ours, key=lambda k: ours[k][0]) if ours else None
         peak, peak_kind = load_peaks()
-        roof = None
-        if dom is not None:
-            avg_ms = ours[dom][0] / ours[dom][1]
-            by = stage_bytes(dom, n, M, Mh)
-            if by > 0:
-                ach = by / (avg_ms / 1e3) / 1e9
-                roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                        "frac": ach / peak, "traffic": None, "peak_source": peak_kind,
-                        "avg_launch_ms": avg_ms}
-            else:
-                roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None,
-                        "unit": "TFLOP/s", "frac": None, "traffic": None, "avg_launch_ms": avg_ms}
+        vol = abs(float(np.linalg.det(fr.box)))
+        ppi = pairs_per_ion(n, vol, cfg["rcut"])
+
+        def roofline(stage):
+            avg_ms = stages[stage][0] / stages[stage][1]
+            if stage in PAIR_FLOPS:
+                fl = n * ppi * PAIR_FLOPS[stage]
+                ach = fl / (avg_ms / 1e3) / 1e12
+                return {"kernel": stage, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+                        "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                        "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
+                        "avg_launch_ms": avg_ms, "flops_per_launch": fl}
+            by = stage_bytes(stage, n, M, Mh)
+            ach = by / (avg_ms / 1e3) / 1e9
+            return {"kernel": stage, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "traffic": None, "peak_source": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)",
+                    "avg_launch_ms": avg_ms, "bytes_per_launch": by}
+
+        roof = roofline(dom) if dom is not None else None
+        mesh_kernels = {k: roofline(k) for k in ("fwd.spread", "bwd.spread", "fwd.gather", "bwd.gather",
+                                                  "fwd.influence", "bwd.influence") if k in stages}
         per_stage = {k: round(v[0] / v[1], 5) for k, v in sorted(stages.items())}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -316,6 +365,10 @@ def run_ours(args):
             "config": config_dict(cfg, fr, ws),
             "roofline": roof,
             "stage_ms": per_stage,
+            "serial_ms_per_step": s_ms,
+            "mesh_rooflines": {k: {"achieved": round(v["achieved"], 1), "frac": round(v["frac"], 4),
+                                   "avg_launch_ms": round(v["avg_launch_ms"], 5)}
+                               for k, v in mesh_kernels.items()},
             "cpu_baseline": cpu,
             "e2e": {"value": e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e_ms},

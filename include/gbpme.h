@@ -72,7 +72,10 @@ typedef struct {
   int include_background;  /* 1: neutralising background term (default) */
   int max_ions;            /* capacity; default 1<<18 */
   int brick[3];            /* spread/gather brick edge in mesh points; 0 = automatic */
-  int reserved[8];
+  int overlap_pair;        /* 1: run the pair term on a plan-owned side stream, concurrently
+                              with the mesh stages (default); 0: everything on the call's
+                              stream, one stage after the other (per-kernel timing) */
+  int reserved[7];
 } pme_opts;
 
 void pme_opts_default(pme_opts* opts);

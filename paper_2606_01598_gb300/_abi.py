@@ -24,7 +24,8 @@ STATUS = {0: "PME_OK", 1: "PME_ERR_ARG", 2: "PME_ERR_CUDA", 3: "PME_ERR_CUFFT",
 class PMEOpts(ctypes.Structure):
     _fields_ = [("influence_power", c_double), ("deconvolution", c_int), ("coulomb_k", c_double),
                 ("include_pair", c_int), ("include_self", c_int), ("include_background", c_int),
-                ("max_ions", c_int), ("brick", c_int * 3), ("reserved", c_int * 8)]
+                ("max_ions", c_int), ("brick", c_int * 3), ("overlap_pair", c_int),
+                ("reserved", c_int * 7)]
 
 
 _SIGS = {

@@ -57,6 +57,7 @@ struct PairRecords {
   float4* mu;    // mu (r-space), w unused
   float4* tq;    // tangent: dq, d' = dmu + q dr (r-space)
   float4* dr;    // tangent: dr (r-space); w unused
+  int* cz;       // cell z index (for the z offset of a candidate inside a z-run)
 };
 
 struct SortBuffers {

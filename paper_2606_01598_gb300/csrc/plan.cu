@@ -249,7 +249,7 @@ static void free_plan(pme_plan_t p) {
                   p->sb.key_b, p->sb.key_c, p->sb.slot_b, p->sb.slot_c, p->sb.count_b,
                   p->sb.count_c, p->sb.start_b, p->sb.start_c, p->sb.perm_b, p->sb.perm_c,
                   p->sb.qpart, p->sb.qsum, p->mr.idx, p->mr.fq, p->mr.dm, p->mr.tq, p->mr.tt,
-                  p->pr.idx, p->pr.fq, p->pr.mu, p->pr.tq, p->pr.dr, p->mesh_out, p->pair_out,
+                  p->pr.idx, p->pr.fq, p->pr.mu, p->pr.tq, p->pr.dr, p->pr.cz, p->mesh_out, p->pair_out,
                   p->epart, p->flags, p->stage_f, p->stage_d};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -298,6 +298,7 @@ void pme_opts_default(pme_opts* o) {
   o->include_self = 1;
   o->include_background = 1;
   o->max_ions = 1 << 18;
+  o->overlap_pair = 1;
 }
 
 const char* pme_status_string(int s) {
@@ -426,6 +427,7 @@ int pme_plan_create(pme_plan_t* out, const double box[9], const int mesh[3], int
   A(&p->pr.mu, ni);
   A(&p->pr.tq, ni);
   A(&p->pr.dr, ni);
+  A(&p->pr.cz, ni);
   A(&p->mesh_out, ni * 10);
   A(&p->pair_out, ni * 10);
   p->nspec_blocks = influence_grid(p);
@@ -536,11 +538,12 @@ int pme_forward(pme_plan_t p, void* stream, int n, const float* pos, const float
   prof_end(p, t, s);
   // the pair term runs on the plan's side stream, concurrently with the mesh stages
   const bool fork = pair && n > 0;
+  cudaStream_t ps = p->opts.overlap_pair ? p->side : s;
   if (fork) {
-    if ((st = fork_side(p, s))) return st;
-    t = prof_begin(p, 6, p->side);
-    if ((st = launch_pair(p, p->side, n, false, in, nullptr, p->pair_out))) return st;
-    prof_end(p, t, p->side);
+    if (p->opts.overlap_pair && (st = fork_side(p, s))) return st;
+    t = prof_begin(p, 6, ps);
+    if ((st = launch_pair(p, ps, n, false, in, nullptr, p->pair_out))) return st;
+    prof_end(p, t, ps);
   }
   t = prof_begin(p, 1, s);
   if ((st = launch_spread(p, s, n, false, p->rho, nullptr))) return st;
@@ -559,7 +562,7 @@ int pme_forward(pme_plan_t p, void* stream, int n, const float* pos, const float
   t = prof_begin(p, 5, s);
   if ((st = launch_gather(p, s, n, p->phi, nullptr, false, in, nullptr, p->mesh_out))) return st;
   prof_end(p, t, s);
-  if (fork && (st = join_side(p, s))) return st;
+  if (fork && p->opts.overlap_pair && (st = join_side(p, s))) return st;
   t = prof_begin(p, 7, s);
   if ((st = launch_combine_forward(p, s, in, true, pair && n > 0, p->epart + p->nspec_blocks,
                                    f_out, p_out, fl_out, fg_out)))
@@ -605,11 +608,12 @@ int pme_backward(pme_plan_t p, void* stream, int n, const float* pos, const floa
   t = prof_begin(p, B + 0, s);
   if ((st = launch_sort(p, s, in, true, true, pair))) return st;
   prof_end(p, t, s);
+  cudaStream_t ps = p->opts.overlap_pair ? p->side : s;
   if (pair) {
-    if ((st = fork_side(p, s))) return st;
-    t = prof_begin(p, B + 6, p->side);
-    if ((st = launch_pair(p, p->side, n, true, in, gE, p->pair_out))) return st;
-    prof_end(p, t, p->side);
+    if (p->opts.overlap_pair && (st = fork_side(p, s))) return st;
+    t = prof_begin(p, B + 6, ps);
+    if ((st = launch_pair(p, ps, n, true, in, gE, p->pair_out))) return st;
+    prof_end(p, t, ps);
   }
   t = prof_begin(p, B + 1, s);
   if ((st = launch_spread(p, s, n, true, p->rho, p->rho + p->M))) return st;
@@ -628,7 +632,7 @@ int pme_backward(pme_plan_t p, void* stream, int n, const float* pos, const floa
   t = prof_begin(p, B + 5, s);
   if ((st = launch_gather(p, s, n, p->phi, p->phi + p->M, true, in, gE, p->mesh_out))) return st;
   prof_end(p, t, s);
-  if (pair && (st = join_side(p, s))) return st;
+  if (pair && p->opts.overlap_pair && (st = join_side(p, s))) return st;
   t = prof_begin(p, B + 7, s);
   if ((st = launch_combine_backward(p, s, in, gE, o_pos, o_q, o_mu))) return st;
   prof_end(p, t, s);

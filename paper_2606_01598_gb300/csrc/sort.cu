@@ -201,6 +201,7 @@ k_rank_records(Geometry g, IonInputs in, SortBuffers sb, MeshRecords mr, PairRec
 #pragma unroll
     for (int b = 0; b < 3; ++b) cell_origin(s[b], g.ncell[b], c[b], f[b]);
     pr.idx[dest] = make_int4(c[0], c[1], c[2], i);
+    pr.cz[dest] = c[2];
     pr.fq[dest] = make_float4(f[0], f[1], f[2], qi);
     pr.mu[dest] = make_float4(mu[0], mu[1], mu[2], 0.f);
     if (tangent) {

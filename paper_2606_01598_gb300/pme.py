@@ -85,7 +85,8 @@ class Plan:
     def __init__(self, box, mesh, order: int, alpha: float, rcut: float, *,
                  influence_power: float = 1.0, deconvolution: bool = True,
                  coulomb_k: float = 1.0, include_pair: bool = True, include_self: bool = True,
-                 include_background: bool = True, max_ions: int = 1 << 18, device=None):
+                 include_background: bool = True, max_ions: int = 1 << 18,
+                 overlap_pair: bool = True, device=None):
         if not torch.cuda.is_available():
             raise RuntimeError("gbpme needs a CUDA device; there is no CPU fallback")
         self.lib = _abi.load()
@@ -105,6 +106,7 @@ class Plan:
         opts.include_self = int(bool(include_self))
         opts.include_background = int(bool(include_background))
         opts.max_ions = int(max_ions)
+        opts.overlap_pair = int(bool(overlap_pair))
         self.box = np.asarray(box, np.float64).reshape(3, 3).copy()
         self.mesh = tuple(int(x) for x in mesh)
         self.order = int(order)
