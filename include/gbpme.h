@@ -75,7 +75,12 @@ typedef struct {
   int overlap_pair;        /* 1: run the pair term on a plan-owned side stream, concurrently
                               with the mesh stages (default); 0: everything on the call's
                               stream, one stage after the other (per-kernel timing) */
-  int reserved[7];
+  int recip_method;        /* 0: particle mesh (default). 1: explicit Ewald k-sum over the half
+                              space |k| <= ewald_kmax instead of the mesh (the conventional
+                              baseline of the paper's timing crossover; forward only) */
+  double ewald_kmax;       /* |k| cutoff in 1/length for recip_method 1; <= 0 selects
+                              2 alpha sqrt(ln 1e8), where exp(-k^2/4 alpha^2) = 1e-8 */
+  int reserved[6];
 } pme_opts;
 
 void pme_opts_default(pme_opts* opts);
@@ -119,6 +124,11 @@ int pme_sync_status(pme_plan_t plan, void* stream);
 int pme_forward(pme_plan_t plan, void* stream, int n, const float* pos, const float* q,
                 const float* mu, double* energy, float* force, float* phi, float* field,
                 float* field_grad);
+
+/* With opts.recip_method = 1 the reciprocal part is the explicit Ewald sum
+ *   E_recip = (2 pi / V) sum_{0 < |k| <= kmax} exp(-k^2/4 alpha^2)/k^2 |sum_j (q_j + i mu_j.k) e^{i k.r_j}|^2
+ * (O(N K) work) and every output keeps its meaning; pme_backward then returns
+ * PME_ERR_UNSUPPORTED. */
 
 /* Backward: vector-Jacobian product of the map (pos, q, mu) -> (E, force, phi, field) of
  * pme_forward, for cotangents g_energy [1] float64, g_force [n][3], g_phi [n], g_field [n][3]

@@ -110,6 +110,14 @@ struct pme_plan_s {
   cudaStream_t side;
   cudaEvent_t ev_fork, ev_join;
   std::string last_error;
+  // explicit Ewald k-sum (recip_method = 1)
+  double opts_kmax = 0.0;
+  int ew_K = 0;
+  int4* ew_kn = nullptr;      // [K] n vector, A(k) in .w
+  float4* ew_kv = nullptr;    // [K] k vector
+  float2* ew_S = nullptr;     // [K] structure factor
+  uint4* ew_fx = nullptr;     // [max_ions] fixed-point fractional coordinates
+  float4* ew_qm = nullptr;    // [max_ions] q, mu
   // stage timers
   bool prof = false;
   cudaEvent_t* prof_ev = nullptr;   // [2 * kProfCap]

@@ -1,6 +1,8 @@
 // Host-side launchers of the libgbpme kernels (one translation unit per pipeline stage).
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace gbpme {
@@ -54,6 +56,13 @@ int launch_combine_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, bo
 int launch_combine_backward(pme_plan_t p, cudaStream_t s, const IonInputs& in,
                             const double* g_energy, float* grad_pos, float* grad_q,
                             float* grad_mu);
+// ewald.cu: explicit Ewald reciprocal sum (structure factor, then per-ion potential
+// derivatives in the gather's [n][10] layout); energy partials sum A |S|^2 over the half space.
+int ewald_build_kvectors(pme_plan_t p, std::vector<int4>& kn, std::vector<float4>& kv);
+int launch_ewald_recip(pme_plan_t p, cudaStream_t s, const IonInputs& in, double* partials,
+                       float* out);
+int ewald_partial_blocks(pme_plan_t p);
+
 // Sum of per-ion pair energies 1/2 (q phi + mu . dphi/dr) of a pair_out buffer.
 int launch_pair_energy(pme_plan_t p, cudaStream_t s, int n, const IonInputs& in,
                        const float* pair_out, double* e_pair);

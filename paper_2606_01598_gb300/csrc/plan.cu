@@ -250,7 +250,8 @@ static void free_plan(pme_plan_t p) {
                   p->sb.count_c, p->sb.start_b, p->sb.start_c, p->sb.perm_b, p->sb.perm_c,
                   p->sb.qpart, p->sb.qsum, p->mr.idx, p->mr.fq, p->mr.dm, p->mr.tq, p->mr.tt,
                   p->pr.idx, p->pr.fq, p->pr.mu, p->pr.tq, p->pr.dr, p->pr.cz, p->mesh_out, p->pair_out,
-                  p->epart, p->flags, p->stage_f, p->stage_d};
+                  p->epart, p->flags, p->stage_f, p->stage_d, p->ew_kn, p->ew_kv, p->ew_S,
+                  p->ew_fx, p->ew_qm};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p->r2c1) cufftDestroy(p->r2c1);
@@ -282,6 +283,72 @@ static int alloc_cells(pme_plan_t p) {
   return PME_OK;
 }
 
+// (Re)build the explicit-Ewald k-vector tables for the current box.
+static int setup_kvectors(pme_plan_t p) {
+  std::vector<int4> kn;
+  std::vector<float4> kv;
+  ewald_build_kvectors(p, kn, kv);
+  cudaFree(p->ew_kn);
+  cudaFree(p->ew_kv);
+  cudaFree(p->ew_S);
+  p->ew_kn = nullptr;
+  p->ew_kv = nullptr;
+  p->ew_S = nullptr;
+  p->ew_K = int(kn.size());
+  int st;
+  if ((st = dalloc(p, &p->ew_kn, kn.size()))) return st;
+  if ((st = dalloc(p, &p->ew_kv, kv.size()))) return st;
+  if ((st = dalloc(p, &p->ew_S, kn.size()))) return st;
+  if (!kn.empty()) {
+    if ((st = check_cuda(p, cudaMemcpy(p->ew_kn, kn.data(), sizeof(int4) * kn.size(), cudaMemcpyHostToDevice),
+                         "copy k-vectors")))
+      return st;
+    if ((st = check_cuda(p, cudaMemcpy(p->ew_kv, kv.data(), sizeof(float4) * kv.size(), cudaMemcpyHostToDevice),
+                         "copy k-vectors")))
+      return st;
+  }
+  // the energy partials array must hold one slot per k block
+  cudaFree(p->epart);
+  p->epart = nullptr;
+  const int na = std::max(p->nspec_blocks, ewald_partial_blocks(p));
+  return dalloc(p, &p->epart, size_t(na) + p->max_blocks);
+}
+
+// Forward with the explicit k-sum in place of the mesh stages.
+static int forward_ewald(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool pair, double* e_out,
+                         float* f_out, float* p_out, float* fl_out, float* fg_out, Staging& sg) {
+  const int n = in.n;
+  int st, t;
+  t = prof_begin(p, 0, s);
+  if ((st = launch_sort(p, s, in, false, false, pair))) return st;
+  prof_end(p, t, s);
+  const bool fork = pair && n > 0;
+  cudaStream_t ps = p->opts.overlap_pair ? p->side : s;
+  if (fork) {
+    if (p->opts.overlap_pair && (st = fork_side(p, s))) return st;
+    t = prof_begin(p, 6, ps);
+    if ((st = launch_pair(p, ps, n, false, in, nullptr, p->pair_out))) return st;
+    prof_end(p, t, ps);
+  }
+  t = prof_begin(p, 3, s);
+  if ((st = launch_ewald_recip(p, s, in, p->epart, p->mesh_out))) return st;
+  prof_end(p, t, s);
+  if (fork && p->opts.overlap_pair && (st = join_side(p, s))) return st;
+  const int na = ewald_partial_blocks(p);
+  t = prof_begin(p, 7, s);
+  if ((st = launch_combine_forward(p, s, in, true, fork, p->epart + na, f_out, p_out, fl_out, fg_out)))
+    return st;
+  prof_end(p, t, s);
+  if (e_out) {
+    const double bgfac =
+        p->opts.include_background ? -kPi / (2.0 * p->g.volume * p->alpha * p->alpha) : 0.0;
+    if ((st = launch_energy_final(p, s, p->epart, na, combine_blocks(n), 4.0 * kPi / p->g.volume,
+                                  p->opts.coulomb_k, bgfac, p->sb.qsum, e_out)))
+      return st;
+  }
+  return sg.finish();
+}
+
 }  // namespace gbpme
 
 using namespace gbpme;
@@ -299,6 +366,8 @@ void pme_opts_default(pme_opts* o) {
   o->include_background = 1;
   o->max_ions = 1 << 18;
   o->overlap_pair = 1;
+  o->recip_method = 0;
+  o->ewald_kmax = 0.0;
 }
 
 const char* pme_status_string(int s) {
@@ -374,6 +443,8 @@ int pme_plan_create(pme_plan_t* out, const double box[9], const int mesh[3], int
   for (int a = 0; a < 3; ++a)
     if (mesh[a] < order || mesh[a] > 4096) return fail(PME_ERR_ARG, "mesh dimension < order");
   if (!(p->opts.influence_power >= 0.0)) return fail(PME_ERR_ARG, "influence_power < 0");
+  if (p->opts.recip_method < 0 || p->opts.recip_method > 1) return fail(PME_ERR_ARG, "recip_method");
+  p->opts_kmax = p->opts.ewald_kmax > 0.0 ? p->opts.ewald_kmax : 2.0 * alpha * std::sqrt(std::log(1e8));
   Geometry& g = p->g;
   for (int a = 0; a < 3; ++a) g.N[a] = mesh[a];
   g.order = order;
@@ -436,6 +507,11 @@ int pme_plan_create(pme_plan_t* out, const double box[9], const int mesh[3], int
   A(&p->stage_f, ni * kStageFloats);
   A(&p->stage_d, 4);
   if (st == PME_OK) st = alloc_cells(p);
+  if (p->opts.recip_method == 1) {
+    A(&p->ew_fx, ni);
+    A(&p->ew_qm, ni);
+    if (st == PME_OK) st = setup_kvectors(p);
+  }
   if (st) return fail(st, p->last_error);
   if ((st = check_cuda(p, cudaMemset(p->flags, 0, sizeof(int)), "memset"))) return fail(st, p->last_error);
   if ((st = check_cuda(p, cudaMemcpy(p->cand, cand.data(), sizeof(int) * cand.size(),
@@ -488,6 +564,11 @@ int pme_plan_set_box(pme_plan_t p, const double box[9]) {
     p->sb.count_c = p->sb.start_c = nullptr;
     if ((st = alloc_cells(p))) return st;
   }
+  if (p->opts.recip_method == 1) {
+    int st = check_cuda(p, cudaDeviceSynchronize(), "synchronize");
+    if (st) return st;
+    return setup_kvectors(p);
+  }
   return PME_OK;
 }
 
@@ -533,6 +614,7 @@ int pme_forward(pme_plan_t p, void* stream, int n, const float* pos, const float
   if (sg.status) return sg.status;
   const bool pair = p->opts.include_pair != 0;
   int t;
+  if (p->opts.recip_method == 1) return forward_ewald(p, s, in, pair, e_out, f_out, p_out, fl_out, fg_out, sg);
   t = prof_begin(p, 0, s);
   if ((st = launch_sort(p, s, in, false, true, pair))) return st;
   prof_end(p, t, s);
@@ -586,6 +668,8 @@ int pme_backward(pme_plan_t p, void* stream, int n, const float* pos, const floa
                  float* grad_mu) {
   int st = check_common(p, n, pos, q);
   if (st) return st;
+  if (p->opts.recip_method != 0)
+    return set_error(p, PME_ERR_UNSUPPORTED, "pme_backward needs the particle-mesh reciprocal method");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Staging sg(p, s, n);
   IonInputs in{};

@@ -86,7 +86,8 @@ class Plan:
                  influence_power: float = 1.0, deconvolution: bool = True,
                  coulomb_k: float = 1.0, include_pair: bool = True, include_self: bool = True,
                  include_background: bool = True, max_ions: int = 1 << 18,
-                 overlap_pair: bool = True, device=None):
+                 overlap_pair: bool = True, recip_method: str = "mesh", ewald_kmax: float = 0.0,
+                 device=None):
         if not torch.cuda.is_available():
             raise RuntimeError("gbpme needs a CUDA device; there is no CPU fallback")
         self.lib = _abi.load()
@@ -107,6 +108,10 @@ class Plan:
         opts.include_background = int(bool(include_background))
         opts.max_ions = int(max_ions)
         opts.overlap_pair = int(bool(overlap_pair))
+        if recip_method not in ("mesh", "ewald"):
+            raise ValueError("recip_method is 'mesh' or 'ewald'")
+        opts.recip_method = 0 if recip_method == "mesh" else 1
+        opts.ewald_kmax = float(ewald_kmax)
         self.box = np.asarray(box, np.float64).reshape(3, 3).copy()
         self.mesh = tuple(int(x) for x in mesh)
         self.order = int(order)
