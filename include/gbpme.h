@@ -142,6 +142,33 @@ int pme_backward(pme_plan_t plan, void* stream, int n, const float* pos, const f
                  const float* g_phi, const float* g_field, float* grad_pos, float* grad_q,
                  float* grad_mu);
 
+/* ---- batched frames ----------------------------------------------------------------------
+ * One plan over F frames stored back to back in the per-ion arrays: frame f owns ions
+ * [offsets[f], offsets[f+1]) (offsets[0] = 0, host array of F+1), with its own box
+ * (boxes + 9 f, rows = lattice vectors), mesh (meshes + 3 f) and spline order (orders[f]);
+ * alpha, rcut and opts are shared (opts.max_ions is ignored: the plan holds offsets[F] ions;
+ * opts.recip_method must be 0). Every stage runs as one launch over the whole batch (spread
+ * and gather: one launch per distinct spline order; the FFTs: one batched cuFFT call per
+ * distinct mesh shape), so a batch of small frames costs a handful of launches instead of
+ * a handful per frame. The handle is a pme_plan_t: destroy it with pme_plan_destroy; the
+ * single-frame calls reject it and the batch calls reject single-frame plans. */
+int pme_batch_create(pme_plan_t* out, int nframes, const int* offsets, const double* boxes,
+                     const int* meshes, const int* orders, double alpha, double rcut,
+                     const pme_opts* opts);
+int pme_batch_frames(pme_plan_t plan);
+
+/* As pme_forward for every frame: energy [F] float64 (per frame), per-ion outputs over all
+ * offsets[F] ions in the caller's order. Pointers follow the same host/device rule. */
+int pme_batch_forward(pme_plan_t plan, void* stream, const float* pos, const float* q,
+                      const float* mu, double* energy, float* force, float* phi, float* field,
+                      float* field_grad);
+
+/* As pme_backward for every frame; g_energy is [F] float64 (one cotangent per frame). */
+int pme_batch_backward(pme_plan_t plan, void* stream, const float* pos, const float* q,
+                       const float* mu, const double* g_energy, const float* g_force,
+                       const float* g_phi, const float* g_field, float* grad_pos, float* grad_q,
+                       float* grad_mu);
+
 /* ---- stage-level entry points (each runs one step of the pipeline on its own) ---------- */
 
 /* Mesh density rho_mesh of Eq. charge_dipole_assign, written to rho [Nx][Ny][Nz] float32

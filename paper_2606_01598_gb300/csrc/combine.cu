@@ -8,8 +8,8 @@
 //   force      = q field + field_grad mu                               (= -dE/dr)
 // where the c terms remove the ion's own screening cloud (for mu they are the derivative of
 // Eq. self_mu; for the field gradient the analogous part of the reciprocal sum), so field
-// and field_grad are those of all other sources. Energy partials per block (float64):
-// 1/2 (q phi_pair + mu . grad phi_pair) + self energies.
+// and field_grad are those of all other sources. Per-ion float64 energy contributions
+// 1/2 (q phi_pair + mu . grad phi_pair) + self energies are summed per frame afterwards.
 //
 // Backward, per ion: grad = k (mesh part + pair part) + the self and background terms of
 // the g_E-weighted gradient and of the Hessian-vector product.
@@ -22,13 +22,15 @@ namespace {
 constexpr int kCombThreads = 256;
 
 struct CombineArgs {
+  FrameDesc one;
+  FrameMaps maps;
   const float* mesh_out;
   const float* pair_out;
   int with_mesh, with_pair;
   IonInputs in;
-  const double* qsum;
-  const double* g_energy;
-  double* epart;
+  const double* qsum;       // Q, dQ per frame
+  const double* g_energy;   // per frame
+  double* e_ion;            // per-ion energy contributions (forward)
   float* force;
   float* phi;
   float* field;
@@ -39,15 +41,24 @@ struct CombineArgs {
   float k;
   float self_phi;     // 2 alpha / sqrt(pi)     (0 when self terms are off)
   float self_c;       // 4 alpha^3 / (3 sqrt(pi))
-  float bg;           // pi / (V alpha^2)       (0 when background is off)
+  int with_bg;        // background term on
+  float alpha;
   double e_self_q;    // alpha / sqrt(pi)
   double e_self_mu;   // 2 alpha^3 / (3 sqrt(pi))
 };
 
+// pi / (V alpha^2) of the ion's frame, or 0 without the background term
+__device__ __forceinline__ float bg_factor(const CombineArgs& a, const FrameDesc& F) {
+  return a.with_bg ? float(kPi / (F.g.volume * double(a.alpha) * double(a.alpha))) : 0.f;
+}
+
+template <bool BATCH>
 __global__ void __launch_bounds__(kCombThreads) k_combine_forward(CombineArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double e = 0.0;
   if (i < a.in.n) {
+    const int f = BATCH ? a.maps.ion_frame[i] : 0;
+    const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, f);
+    const float bg = bg_factor(a, F);
     float qi = a.in.q[i];
     float mu[3] = {0.f, 0.f, 0.f};
     if (a.in.mu) {
@@ -61,9 +72,9 @@ __global__ void __launch_bounds__(kCombThreads) k_combine_forward(CombineArgs a)
       v[t] = a.with_mesh ? a.mesh_out[size_t(i) * 10 + t] : 0.f;
       w[t] = a.with_pair ? a.pair_out[size_t(i) * 10 + t] : 0.f;
     }
-    const float Q = float(a.qsum[0]);
+    const float Q = float(a.qsum[2 * f]);
     const float k = a.k;
-    const float ph = k * (v[0] + w[0] - a.self_phi * qi - a.bg * Q);
+    const float ph = k * (v[0] + w[0] - a.self_phi * qi - bg * Q);
     float fld[3], fg[6];
 #pragma unroll
     for (int c = 0; c < 3; ++c) fld[c] = k * (-(v[1 + c] + w[1 + c]) + a.self_c * mu[c]);
@@ -89,17 +100,19 @@ __global__ void __launch_bounds__(kCombThreads) k_combine_forward(CombineArgs a)
       a.force[3 * i + 2] = F2;
     }
     const double mu2 = double(mu[0]) * mu[0] + double(mu[1]) * mu[1] + double(mu[2]) * mu[2];
-    e = 0.5 * (double(qi) * w[0] + double(mu[0]) * w[1] + double(mu[1]) * w[2] +
-               double(mu[2]) * w[3]) -
-        a.e_self_q * double(qi) * qi - a.e_self_mu * mu2;
+    a.e_ion[i] = 0.5 * (double(qi) * w[0] + double(mu[0]) * w[1] + double(mu[1]) * w[2] +
+                        double(mu[2]) * w[3]) -
+                 a.e_self_q * double(qi) * qi - a.e_self_mu * mu2;
   }
-  const double t = block_sum_d(e);
-  if (threadIdx.x == 0) a.epart[blockIdx.x] = t;
 }
 
+template <bool BATCH>
 __global__ void __launch_bounds__(kCombThreads) k_combine_backward(CombineArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.in.n) return;
+  const int f = BATCH ? a.maps.ion_frame[i] : 0;
+  const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, f);
+  const float bg = bg_factor(a, F);
   const float qi = a.in.q[i];
   float mu[3] = {0.f, 0.f, 0.f}, dmu[3] = {0.f, 0.f, 0.f};
   if (a.in.mu) {
@@ -113,14 +126,14 @@ __global__ void __launch_bounds__(kCombThreads) k_combine_backward(CombineArgs a
     dmu[2] = -a.in.gfield[3 * i + 2];
   }
   const float dq = a.in.gphi ? a.in.gphi[i] : 0.f;
-  const float gE = a.g_energy ? float(*a.g_energy) : 0.f;
+  const float gE = a.g_energy ? float(a.g_energy[f]) : 0.f;
   float v[8], w[8];
 #pragma unroll
   for (int t = 0; t < 8; ++t) {
     v[t] = a.with_mesh ? a.mesh_out[size_t(i) * 8 + t] : 0.f;
     w[t] = a.with_pair ? a.pair_out[size_t(i) * 8 + t] : 0.f;
   }
-  const float Q = float(a.qsum[0]), dQ = float(a.qsum[1]);
+  const float Q = float(a.qsum[2 * f]), dQ = float(a.qsum[2 * f + 1]);
   const float k = a.k;
   if (a.grad_pos) {
     a.grad_pos[3 * i] = k * (v[0] + w[0]);
@@ -128,7 +141,7 @@ __global__ void __launch_bounds__(kCombThreads) k_combine_backward(CombineArgs a
     a.grad_pos[3 * i + 2] = k * (v[2] + w[2]);
   }
   if (a.grad_q)
-    a.grad_q[i] = k * (v[3] + w[3] - a.self_phi * (gE * qi + dq) - a.bg * (gE * Q + dQ));
+    a.grad_q[i] = k * (v[3] + w[3] - a.self_phi * (gE * qi + dq) - bg * (gE * Q + dQ));
   if (a.grad_mu) {
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -137,31 +150,31 @@ __global__ void __launch_bounds__(kCombThreads) k_combine_backward(CombineArgs a
 }
 
 __global__ void __launch_bounds__(kCombThreads)
-k_pair_energy(int n, const float* q, const float* mu, const float* pair_out, double* epart) {
+k_pair_energy(int n, const float* q, const float* mu, const float* pair_out, double* e_ion) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double e = 0.0;
-  if (i < n) {
-    const float* w = pair_out + size_t(i) * 10;
-    e = 0.5 * double(q[i]) * w[0];
-    if (mu)
-      e += 0.5 * (double(mu[3 * i]) * w[1] + double(mu[3 * i + 1]) * w[2] +
-                  double(mu[3 * i + 2]) * w[3]);
-  }
-  const double t = block_sum_d(e);
-  if (threadIdx.x == 0) epart[blockIdx.x] = t;
+  if (i >= n) return;
+  const float* w = pair_out + size_t(i) * 10;
+  double e = 0.5 * double(q[i]) * w[0];
+  if (mu)
+    e += 0.5 * (double(mu[3 * i]) * w[1] + double(mu[3 * i + 1]) * w[2] + double(mu[3 * i + 2]) * w[3]);
+  e_ion[i] = e;
 }
 
 CombineArgs base_args(pme_plan_t p, const IonInputs& in) {
   CombineArgs a = {};
+  a.one = p->frames_h[0];
+  a.maps = p->maps;
   a.in = in;
   a.qsum = p->sb.qsum;
+  a.e_ion = p->e_ion;
+  a.alpha = float(p->alpha);
   a.k = float(p->opts.coulomb_k);
   const double sp = 1.7724538509055160273;
   const double al = p->alpha;
   const bool self = p->opts.include_self != 0;
   a.self_phi = self ? float(2.0 * al / sp) : 0.f;
   a.self_c = self ? float(4.0 * al * al * al / (3.0 * sp)) : 0.f;
-  a.bg = p->opts.include_background ? float(kPi / (p->g.volume * al * al)) : 0.f;
+  a.with_bg = p->opts.include_background ? 1 : 0;
   a.e_self_q = self ? al / sp : 0.0;
   a.e_self_mu = self ? 2.0 * al * al * al / (3.0 * sp) : 0.0;
   return a;
@@ -170,21 +183,21 @@ CombineArgs base_args(pme_plan_t p, const IonInputs& in) {
 }  // namespace
 
 int launch_combine_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool with_mesh,
-                           bool with_pair, double* e_parts, float* force, float* phi,
-                           float* field, float* field_grad) {
+                           bool with_pair, float* force, float* phi, float* field,
+                           float* field_grad) {
   CombineArgs a = base_args(p, in);
   a.mesh_out = p->mesh_out;
   a.pair_out = p->pair_out;
   a.with_mesh = with_mesh;
   a.with_pair = with_pair;
-  a.epart = e_parts;
   a.force = force;
   a.phi = phi;
   a.field = field;
   a.field_grad = field_grad;
   const int grid = (in.n + kCombThreads - 1) / kCombThreads;
   if (grid == 0) return PME_OK;
-  k_combine_forward<<<grid, kCombThreads, 0, s>>>(a);
+  if (p->batch) k_combine_forward<true><<<grid, kCombThreads, 0, s>>>(a);
+  else k_combine_forward<false><<<grid, kCombThreads, 0, s>>>(a);
   count_launch();
   return check_launch(p, "k_combine_forward");
 }
@@ -203,20 +216,20 @@ int launch_combine_backward(pme_plan_t p, cudaStream_t s, const IonInputs& in,
   a.grad_mu = grad_mu;
   const int grid = (in.n + kCombThreads - 1) / kCombThreads;
   if (grid == 0) return PME_OK;
-  k_combine_backward<<<grid, kCombThreads, 0, s>>>(a);
+  if (p->batch) k_combine_backward<true><<<grid, kCombThreads, 0, s>>>(a);
+  else k_combine_backward<false><<<grid, kCombThreads, 0, s>>>(a);
   count_launch();
   return check_launch(p, "k_combine_backward");
 }
 
 int launch_pair_energy(pme_plan_t p, cudaStream_t s, int n, const IonInputs& in,
-                       const float* pair_out, double* e_pair) {
+                       const float* pair_out) {
   const int grid = (n + kCombThreads - 1) / kCombThreads;
   if (grid == 0) return PME_OK;
-  k_pair_energy<<<grid, kCombThreads, 0, s>>>(n, in.q, in.mu, pair_out, e_pair);
+  k_pair_energy<<<grid, kCombThreads, 0, s>>>(n, in.q, in.mu, pair_out, p->e_ion);
   count_launch();
   return check_launch(p, "k_pair_energy");
 }
 
-int combine_blocks(int n) { return (n + kCombThreads - 1) / kCombThreads; }
 
 }  // namespace gbpme

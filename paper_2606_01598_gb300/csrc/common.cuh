@@ -61,52 +61,110 @@ struct PairRecords {
 };
 
 struct SortBuffers {
-  int* key_b;     // [max_ions] brick key per caller-order ion
-  int* key_c;     // [max_ions] pair cell key
+  int* key_b;     // [max_ions] global brick key per caller-order ion
+  int* key_c;     // [max_ions] global pair cell key
   int* slot_b;    // [max_ions] arrival slot inside the brick
   int* slot_c;
-  int* count_b;   // [nbricks + 1]
-  int* count_c;   // [ncells + 1]
-  int* start_b;   // [nbricks + 1] exclusive scan
-  int* start_c;   // [ncells + 1]
+  int* count_b;   // [total bricks + 1]
+  int* count_c;   // [total cells + 1]
+  int* start_b;   // [total bricks + 1] exclusive scan
+  int* start_c;   // [total cells + 1]
   int* perm_b;    // [max_ions] unsorted placement (sorted slot -> caller index)
   int* perm_c;
-  double* qpart;  // [2 * max_blocks] per-block sums of q and dq
-  double* qsum;   // [2] Q and dQ
+  double* qpart;  // unused (kept for the fixed scratch layout of the allocation-free spread)
+  double* qsum;   // [2 * frames] Q and dQ of each frame
+};
+
+// One frame of a plan: its geometry and where its data lives in the plan's arrays. A single-
+// frame plan passes its one descriptor as a kernel argument; a batched plan keeps a table of
+// them in device memory and maps ions / bricks / blocks to frames with the FrameMaps arrays.
+struct FrameDesc {
+  Geometry g;
+  int ion_off, n;           // caller-order ion range
+  int sorted_off;           // first position of the frame's ions in both sorted orders
+  int brick_off, nbricks;   // global brick keys [brick_off, brick_off + nbricks)
+  int cell_off, ncells;     // global pair-cell keys
+  long long mesh_off;       // first float of rho / Phi
+  long long tmesh_off;      // first float of d rho / d Phi (backward)
+  long long spec_off;       // first complex of the spectrum
+  long long tspec_off;      // first complex of the tangent spectrum
+  int cand_off, max_nb;     // candidate-brick table [3][max_nb][1 + kMaxCandPerDim]
+  int dconv_off;            // deconvolution tables: x at dconv_off, y at +Nx, z at +Nx+Ny
+  int infl_blk_off, infl_nblk;  // influence / energy blocks of this frame
+};
+
+struct FrameMaps {
+  const FrameDesc* desc;    // [frames]
+  const int* ion_frame;     // caller ion -> frame
+  const int* sorted_frame;  // sorted position -> frame
+  const int* brick_frame;   // global brick key -> frame
+  const int* blk_frame;     // influence block -> frame
+};
+
+template <bool BATCH>
+__device__ __forceinline__ const FrameDesc& frame_at(const FrameDesc& one, const FrameMaps& m, int f) {
+  if constexpr (BATCH) return m.desc[f];
+  else return one;
+}
+
+// Spread / gather launch range of one spline order: frames of that order own the contiguous
+// global brick keys [brick_lo, brick_hi) and sorted ion positions [sorted_lo, sorted_hi).
+struct OrderGroup {
+  int order;
+  int brick_lo, brick_hi;
+  int sorted_lo, sorted_hi;
+};
+
+// Frames sharing one mesh shape and order, transformed by one batched cuFFT call: rho of the
+// group's frames back to back, then their d rho (and likewise for spectra and potentials).
+struct FFTGroup {
+  int N[3];
+  int count;
+  long long mesh_off, spec_off;
+  cufftHandle r2c, c2r, r2c2, c2r2;
 };
 
 }  // namespace gbpme
 
 struct pme_plan_s {
-  gbpme::Geometry g;
-  double box[9];
+  gbpme::Geometry g;         // geometry of frame 0 (single-frame plans)
+  int nframes = 1;
+  bool batch = false;
+  gbpme::FrameDesc* frames_h = nullptr;   // [nframes] host copy
+  gbpme::FrameDesc* frames_d = nullptr;   // [nframes] device table (batched plans)
+  gbpme::FrameMaps maps = {};
+  int* map_buf = nullptr;                 // device storage of the maps
+  gbpme::OrderGroup ogroups[8];
+  int nogroups = 0;
+  gbpme::FFTGroup* fgroups = nullptr;
+  int nfgroups = 0;
+  void* fft_work = nullptr;
+  double* e_ion = nullptr;                // [max_ions] per-ion energy contributions
+  int total_bricks = 0, total_cells = 0, total_blocks = 0;
+  long long total_mesh = 0, total_spec = 0;
+  int* frame_offsets = nullptr;           // host copy [nframes + 1]
+  double box[9];             // box of frame 0
   double alpha, rcut;
   pme_opts opts;
-  int M, Mh;            // mesh points, half-spectrum points
-  int nbricks, ncells;
-  int max_ions;
-  int max_blocks;       // ion blocks of 256 for max_ions
+  int M, Mh;                 // mesh / half-spectrum points of frame 0
+  int max_ions;              // ions the buffers hold (batched plans: all frames)
   int device;
   // device scratch
-  float* rho;           // [2][M]   primal and tangent mesh densities
-  cufftComplex* spec;   // [2][Mh]
-  float* phi;           // [2][M]   primal and tangent potential meshes
-  float* dconv[3];      // per-axis deconvolution factors 1/sinc^(2 p gamma) (or 1)
-  int* cand;            // [3][max nb][1 + kMaxCandPerDim] candidate bricks per axis
-  int max_nb;
+  float* rho;                // meshes of every frame: rho at mesh_off, d rho at tmesh_off
+  cufftComplex* spec;        // spectra (same layout with spec_off / tspec_off)
+  float* phi;                // potential meshes (layout of rho)
+  float* dconv_all;          // per-frame, per-axis deconvolution factors 1/sinc^(2 p gamma)
+  int* cand;                 // per-frame candidate-brick tables
   gbpme::SortBuffers sb;
   gbpme::MeshRecords mr;
   gbpme::PairRecords pr;
-  float* mesh_out;      // [max_ions][10] per-ion mesh results (caller order)
-  float* pair_out;      // [max_ions][10] per-ion pair results
-  double* epart;        // energy partials: [0, nspec_blocks) recip, then per-ion blocks
-  int nspec_blocks;
-  int* flags;           // device error flags
+  float* mesh_out;           // [max_ions][10] per-ion mesh results (caller order)
+  float* pair_out;           // [max_ions][10] per-ion pair results
+  double* epart;             // reciprocal energy partials, one per influence (or k) block
+  int* flags;                // device error flags
   // host-pointer staging
-  float* stage_f;       // device staging for host arrays, 24 floats per ion
-  double* stage_d;      // [4]
-  // cuFFT
-  cufftHandle r2c1, c2r1, r2c2, c2r2;
+  float* stage_f;            // device staging for host arrays, 34 floats per ion
+  double* stage_d;           // [2 frames + 2]
   cudaStream_t side;
   cudaEvent_t ev_fork, ev_join;
   std::string last_error;

@@ -6,6 +6,7 @@
 //   M_abc = sum_{jx,jy,jz} Phi(m0 + j) W^(a)(t_jx) W^(b)(t_jy) W^(c)(t_jz),
 // and r-space derivatives follow with D[a][b] = N_b C^{-1}[a][b] (d/dr = D d/dx).
 //
+// One launch per spline order covers the ions of every frame of that order.
 // Work split: a group of 8 lanes per ion, lane l owning stencil z-offset l (l < p), so each
 // mesh row segment is read by consecutive lanes. Each lane forms the y- and x-moments of its
 // z-column, scales them by its own z-weights, and the group sums the moments with warp
@@ -22,13 +23,13 @@ constexpr int kGatherThreads = 256;
 constexpr int kGroup = 8;
 
 struct GatherArgs {
-  Geometry g;
+  FrameDesc one;
+  FrameMaps maps;
   MeshRecords mr;
-  const float* phi;
-  const float* dphi;
-  const double* g_energy;
+  const float* mesh;      // Phi of frame f at mesh_off, d Phi at tmesh_off
+  const double* g_energy; // per frame
   float* out;
-  int n;
+  int t_lo, t_hi;         // sorted positions of this launch
 };
 
 __device__ __forceinline__ float group_sum(float v) {
@@ -44,14 +45,18 @@ __device__ __forceinline__ void apply_D(const float* D, const float x[3], float 
   for (int a = 0; a < 3; ++a) y[a] = D[a * 3 + 0] * x[0] + D[a * 3 + 1] * x[1] + D[a * 3 + 2] * x[2];
 }
 
-template <int P, bool TAN>
+template <int P, bool TAN, bool BATCH>
 __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
   constexpr int DM = TAN ? 3 : 2;
-  const Geometry& g = a.g;
-  const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / kGroup;
+  const int gid = a.t_lo + (blockIdx.x * blockDim.x + threadIdx.x) / kGroup;
   const int l = threadIdx.x & (kGroup - 1);
-  const bool valid = gid < a.n;
-  const int ion = valid ? gid : 0;
+  const bool valid = gid < a.t_hi;
+  const int ion = valid ? gid : a.t_lo;
+  const int frame = BATCH ? a.maps.sorted_frame[ion] : 0;
+  const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, frame);
+  const Geometry& g = F.g;
+  const float* phi_mesh = a.mesh + F.mesh_off;
+  const float* dphi_mesh = a.mesh + F.tmesh_off;
   const int4 m = a.mr.idx[ion];
   const float4 fq = a.mr.fq[ion];
   float wx[DM + 1][P], wy[DM + 1][P], wzall[DM + 1][P];
@@ -98,11 +103,11 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
         int y = m.y + jy;
         if (y >= Ny) y -= Ny;
         const size_t off = (size_t(x) * Ny + y) * Nz + z;
-        const float v = __ldg(a.phi + off);
+        const float v = __ldg(phi_mesh + off);
 #pragma unroll
         for (int b = 0; b <= DM; ++b) r[b] += v * wy[b][jy];
         if (TAN) {
-          const float dv = __ldg(a.dphi + off);
+          const float dv = __ldg(dphi_mesh + off);
 #pragma unroll
           for (int b = 0; b < 3; ++b) rt[b] += dv * wy[b][jy];
         }
@@ -169,7 +174,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
     const float t200 = TMOM(2, 0, 0), t020 = TMOM(0, 2, 0), t002 = TMOM(0, 0, 2);
     const float t110 = TMOM(1, 1, 0), t101 = TMOM(1, 0, 1), t011 = TMOM(0, 1, 1);
     if (!valid || l != 0) return;
-    const float gE = a.g_energy ? float(*a.g_energy) : 0.f;
+    const float gE = a.g_energy ? float(a.g_energy[frame]) : 0.f;
     const float4 dm = a.mr.dm[ion];   // m = D^T mu
     const float4 tq = a.mr.tq[ion];   // dq, dd = D^T (dmu + q dr)
     const float4 tt = a.mr.tt[ion];   // t = D^T dr
@@ -230,41 +235,48 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
 #undef TMOM
 }
 
-template <bool TAN>
-int launch_t(pme_plan_t p, cudaStream_t s, int n, const float* phi, const float* dphi,
-             const double* g_energy, float* out) {
+template <bool TAN, bool BATCH>
+int launch_t(pme_plan_t p, cudaStream_t s, int n, const float* mesh, const double* g_energy,
+             float* out) {
   GatherArgs a;
-  a.g = p->g;
+  a.one = p->frames_h[0];
+  a.maps = p->maps;
   a.mr = p->mr;
-  a.phi = phi;
-  a.dphi = dphi;
+  a.mesh = mesh;
   a.g_energy = g_energy;
   a.out = out;
-  a.n = n;
-  const int grid = int((size_t(n) * kGroup + kGatherThreads - 1) / kGatherThreads);
-  if (grid == 0) return PME_OK;
-  switch (p->g.order) {
-    case 1: k_gather<1, TAN><<<grid, kGatherThreads, 0, s>>>(a); break;
-    case 2: k_gather<2, TAN><<<grid, kGatherThreads, 0, s>>>(a); break;
-    case 3: k_gather<3, TAN><<<grid, kGatherThreads, 0, s>>>(a); break;
-    case 4: k_gather<4, TAN><<<grid, kGatherThreads, 0, s>>>(a); break;
-    case 5: k_gather<5, TAN><<<grid, kGatherThreads, 0, s>>>(a); break;
-    case 6: k_gather<6, TAN><<<grid, kGatherThreads, 0, s>>>(a); break;
-    case 7: k_gather<7, TAN><<<grid, kGatherThreads, 0, s>>>(a); break;
-    default: return set_error(p, PME_ERR_ARG, "spline order out of range");
+  for (int gi = 0; gi < p->nogroups; ++gi) {
+    const OrderGroup& G = p->ogroups[gi];
+    a.t_lo = BATCH ? G.sorted_lo : 0;
+    a.t_hi = BATCH ? G.sorted_hi : n;
+    const int grid = int((size_t(a.t_hi - a.t_lo) * kGroup + kGatherThreads - 1) / kGatherThreads);
+    if (grid <= 0) continue;
+    switch (G.order) {
+      case 1: k_gather<1, TAN, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
+      case 2: k_gather<2, TAN, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
+      case 3: k_gather<3, TAN, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
+      case 4: k_gather<4, TAN, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
+      case 5: k_gather<5, TAN, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
+      case 6: k_gather<6, TAN, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
+      case 7: k_gather<7, TAN, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
+      default: return set_error(p, PME_ERR_ARG, "spline order out of range");
+    }
+    count_launch();
+    int st = check_launch(p, "k_gather");
+    if (st) return st;
   }
-  count_launch();
-  return check_launch(p, "k_gather");
+  return PME_OK;
 }
 
 }  // namespace
 
-int launch_gather(pme_plan_t p, cudaStream_t s, int n, const float* phi_mesh,
-                  const float* dphi_mesh, bool tangent, const IonInputs& in,
+int launch_gather(pme_plan_t p, cudaStream_t s, int n, const float* mesh, bool tangent,
                   const double* g_energy, float* out) {
-  (void)in;
-  return tangent ? launch_t<true>(p, s, n, phi_mesh, dphi_mesh, g_energy, out)
-                 : launch_t<false>(p, s, n, phi_mesh, nullptr, nullptr, out);
+  if (p->batch)
+    return tangent ? launch_t<true, true>(p, s, n, mesh, g_energy, out)
+                   : launch_t<false, true>(p, s, n, mesh, nullptr, out);
+  return tangent ? launch_t<true, false>(p, s, n, mesh, g_energy, out)
+                 : launch_t<false, false>(p, s, n, mesh, nullptr, out);
 }
 
 }  // namespace gbpme

@@ -22,27 +22,26 @@ struct IonInputs {
 int launch_sort(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent, bool need_mesh,
                 bool need_pair);
 
-// spread.cu: owner-computes spread of rho (and, with tangent, of the tangent density).
-int launch_spread(pme_plan_t p, cudaStream_t s, int n, bool tangent, float* rho_out,
-                  float* drho_out);
+// spread.cu: owner-computes spread of rho (and, with tangent, of the tangent density) of every
+// frame; frame f writes mesh + mesh_off (and mesh + tmesh_off).
+int launch_spread(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh);
 
-// influence.cu: in-place G C / V multiply of nspec half spectra and the float64 energy
-// partials of the first; energy_final reduces all partials into one float64 value.
-int launch_influence(pme_plan_t p, cudaStream_t s, cufftComplex* spec, int nspec,
+// influence.cu: in-place G C / V multiply of every frame's spectrum (and tangent spectrum)
+// and the float64 energy partials (one per block, blocks grouped by frame).
+int launch_influence(pme_plan_t p, cudaStream_t s, cufftComplex* spec, bool tangent,
                      double* partials);
-// out = scale * (coef_a * sum parts[0, na) + sum parts[na, na + nb) + bgfac * Q^2)
-int launch_energy_final(pme_plan_t p, cudaStream_t s, const double* parts, int na, int nb,
-                        double coef_a, double scale, double bgfac, const double* qsum,
-                        double* out);
-int influence_grid(pme_plan_t p);
+// Per-frame energies: out[f] = k (recip_coef(f) * sum of f's block partials + sum of f's
+// per-ion energies e_ion + background(Q_f)); recip_coef = 1/(2V) for the mesh, 4 pi / V for
+// the explicit k-sum, 0 without a reciprocal part.
+int launch_energy_final(pme_plan_t p, cudaStream_t s, const double* parts, int recip_kind,
+                        bool with_ions, bool with_bg, double scale, int n_single, double* out);
+int influence_blocks(const Geometry& g);
 void spread_brick_shape(int shape[3]);
-int combine_blocks(int n);
 
 // gather.cu: per-ion interpolation of the potential mesh(es).
 //   forward: out[orig][10] = phi, dphi/dr (3), d2phi/drdr (6)
 //   tangent: out[orig][8]  = mesh part of (grad_r (3), grad_q, grad_mu (3)) of the backward
-int launch_gather(pme_plan_t p, cudaStream_t s, int n, const float* phi_mesh,
-                  const float* dphi_mesh, bool tangent, const IonInputs& in,
+int launch_gather(pme_plan_t p, cudaStream_t s, int n, const float* mesh, bool tangent,
                   const double* g_energy, float* out);
 
 // pair.cu: real-space erfc pair term over the cell list, same output layouts as gather.
@@ -51,8 +50,8 @@ int launch_pair(pme_plan_t p, cudaStream_t s, int n, bool tangent, const IonInpu
 
 // combine.cu: add the parts, the self and background terms, apply coulomb_k, write outputs.
 int launch_combine_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool with_mesh,
-                           bool with_pair, double* e_parts, float* force, float* phi,
-                           float* field, float* field_grad);
+                           bool with_pair, float* force, float* phi, float* field,
+                           float* field_grad);
 int launch_combine_backward(pme_plan_t p, cudaStream_t s, const IonInputs& in,
                             const double* g_energy, float* grad_pos, float* grad_q,
                             float* grad_mu);
@@ -65,6 +64,6 @@ int ewald_partial_blocks(pme_plan_t p);
 
 // Sum of per-ion pair energies 1/2 (q phi + mu . dphi/dr) of a pair_out buffer.
 int launch_pair_energy(pme_plan_t p, cudaStream_t s, int n, const IonInputs& in,
-                       const float* pair_out, double* e_pair);
+                       const float* pair_out);
 
 }  // namespace gbpme

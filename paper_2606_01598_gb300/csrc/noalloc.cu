@@ -138,9 +138,10 @@ extern "C" int pme_spread_noalloc(void* stream, const double box[9], const int m
   if (scratch_address(dev, &base) != cudaSuccess) return PME_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-  // a plan-shaped view of the scratch (host struct only; no device memory is allocated)
+  // a plan-shaped view of the scratch (host structs only; no device memory is allocated)
   pme_plan_s v{};
-  Geometry& g = v.g;
+  FrameDesc fd{};
+  Geometry& g = fd.g;
   double inv[9], det;
   if (!na_invert(box, inv, &det)) return PME_ERR_ARG;
   for (int k = 0; k < 9; ++k) g.cinv[k] = inv[k];
@@ -158,16 +159,24 @@ extern "C" int pme_spread_noalloc(void* stream, const double box[9], const int m
   g.rcut2 = 0.f;
   spread_brick_shape(g.brick);
   for (int a = 0; a < 3; ++a) g.nb[a] = (mesh[a] + g.brick[a] - 1) / g.brick[a];
-  v.nbricks = g.nb[0] * g.nb[1] * g.nb[2];
-  v.ncells = 1;
+  fd.n = n;
+  fd.nbricks = g.nb[0] * g.nb[1] * g.nb[2];
+  fd.ncells = 1;
+  fd.max_nb = std::max(g.nb[0], std::max(g.nb[1], g.nb[2]));
+  if (fd.max_nb > kNaMaxNb) return PME_ERR_ARG;
+  v.g = g;
+  v.frames_h = &fd;
+  v.nframes = 1;
+  v.batch = false;
+  v.total_bricks = fd.nbricks;
+  v.total_cells = 1;
   v.max_ions = kNaMaxIons;
-  v.max_blocks = kNaMaxBlocks;
-  v.max_nb = std::max(g.nb[0], std::max(g.nb[1], g.nb[2]));
-  if (v.max_nb > kNaMaxNb) return PME_ERR_ARG;
+  v.nogroups = 1;
+  v.ogroups[0] = OrderGroup{order, 0, fd.nbricks, 0, n};
   int cand[3 * kNaMaxNb * (1 + kMaxCandPerDim)];
   std::memset(cand, 0, sizeof(cand));
   for (int a = 0; a < 3; ++a)
-    if (!na_candidates(mesh[a], g.brick[a], order, g.nb[a], cand + a * v.max_nb * (1 + kMaxCandPerDim)))
+    if (!na_candidates(mesh[a], g.brick[a], order, g.nb[a], cand + a * fd.max_nb * (1 + kMaxCandPerDim)))
       return PME_ERR_UNSUPPORTED;
   v.sb.key_b = reinterpret_cast<int*>(base + kOffKeyB);
   v.sb.key_c = reinterpret_cast<int*>(base + kOffKeyC);
@@ -189,7 +198,7 @@ extern "C" int pme_spread_noalloc(void* stream, const double box[9], const int m
   v.cand = reinterpret_cast<int*>(base + kOffCand);
   v.flags = reinterpret_cast<int*>(base + kOffFlags);
   // the candidate table and the error flag are per call: rewrite / clear them first
-  if (cudaMemcpyAsync(v.cand, cand, sizeof(int) * 3 * v.max_nb * (1 + kMaxCandPerDim),
+  if (cudaMemcpyAsync(v.cand, cand, sizeof(int) * 3 * fd.max_nb * (1 + kMaxCandPerDim),
                       cudaMemcpyHostToDevice, s) != cudaSuccess)
     return PME_ERR_CUDA;
   if (cudaMemsetAsync(v.flags, 0, sizeof(int), s) != cudaSuccess) return PME_ERR_CUDA;
@@ -201,5 +210,7 @@ extern "C" int pme_spread_noalloc(void* stream, const double box[9], const int m
   // launch_sort clears the brick and cell counters on the stream before counting
   int st = launch_sort(&v, s, in, false, true, false);
   if (st) return st;
-  return launch_spread(&v, s, n, false, rho, nullptr);
+  const int rc = launch_spread(&v, s, false, rho);   // the frame's rho sits at offset 0
+  v.frames_h = nullptr;                               // host views only: nothing to release
+  return rc;
 }

@@ -12,10 +12,12 @@
 //                    + r ((u.v)(w.r) + (u.w)(v.r) + (v.w)(u.r))) B3 + r (u.r)(v.r)(w.r) B4
 // (the contractions of grad^k psi). The potential at i of source j is q_j psi - mu_j . grad psi.
 //
-// Work split: one warp per ion (ions in pair-cell order, cells at least rcut/2 wide). Its
-// candidates are the 5 x 5 neighbouring (x, y) cell columns, each holding the contiguous run
-// of the 5 z-cells around the ion (one or two ranges at the periodic wrap); axes too short for
-// five cells use every periodic image within rcut instead. The lanes describe the columns in
+// Work split: one warp per ion (ions in pair-cell order, cells at least rcut/2 wide, so a
+// partner is at most kimg = ceil(rcut / cell width) cells away per axis). Its candidates are
+// the (2 kimg + 1)^2 neighbouring (x, y) cell columns, each holding the contiguous run of the
+// 2 kimg + 1 z-cells around the ion (one or two ranges at the periodic wrap); when an axis has
+// too few cells for distinct offsets, each offset is its own segment and stands for its own
+// periodic image. The lanes describe the columns in
 // parallel and a warp scan turns them into one dense candidate stream, tested 32 at a time;
 // candidates inside rcut are compacted (ballot + popc) into a per-warp shared-memory buffer
 // and evaluated with all lanes busy once 32 or more are waiting. Each lane accumulates its share,
@@ -41,12 +43,14 @@ constexpr int kPairThreads = kPairWarps * 32;
 constexpr int kHitCap = 96;   // compacted hits buffered per warp
 
 struct PairArgs {
-  Geometry g;
+  FrameDesc one;
+  FrameMaps maps;
   PairRecords pr;
   const int* start_c;
-  const double* g_energy;
+  const double* g_energy;   // per frame
   float* out;
   int n;
+  float alpha;
   float c1, c2, c3, c4;   // (2 alpha^2)^l / (alpha sqrt(pi)), l = 1..4
 };
 
@@ -94,7 +98,7 @@ __device__ __forceinline__ void interact(const PairArgs& a, const Ion& I, int j,
   const float r2 = dot(r, r);
   const float rinv2 = 1.f / r2;
   const float rr = sqrtf(r2);
-  const float alpha = a.g.alpha;
+  const float alpha = a.alpha;
   const float ex = expf(-alpha * alpha * r2);
   const float B0 = erfcf(alpha * rr) / rr;
   const float B1 = (B0 + a.c1 * ex) * rinv2;
@@ -156,14 +160,16 @@ __device__ __forceinline__ void interact(const PairArgs& a, const Ion& I, int j,
   }
 }
 
-template <bool TAN>
+template <bool TAN, bool BATCH>
 __global__ void __launch_bounds__(kPairThreads) k_pair(PairArgs a) {
   __shared__ int s_j[kPairWarps][kHitCap];
   __shared__ float s_r[kPairWarps][3][kHitCap];
-  const Geometry& g = a.g;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int i = blockIdx.x * kPairWarps + w;
   if (i >= a.n) return;   // uniform per warp
+  const int frame = BATCH ? a.maps.sorted_frame[i] : 0;
+  const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, frame);
+  const Geometry& g = F.g;
   const int4 ci = a.pr.idx[i];
   const float4 fi = a.pr.fq[i];
   const float4 mi4 = a.pr.mu[i];
@@ -177,7 +183,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pair(PairArgs a) {
   if (TAN) {
     const float4 t = a.pr.tq[i];
     const float4 d = a.pr.dr[i];
-    I.gE = a.g_energy ? float(*a.g_energy) : 0.f;
+    I.gE = a.g_energy ? float(a.g_energy[frame]) : 0.f;
     I.dq = t.x;
     I.dr = mk(d.x, d.y, d.z);
     I.w = I.gE * I.mu + mk(t.y, t.z, t.w);   // gE mu + dmu + q dr
@@ -227,7 +233,8 @@ __global__ void __launch_bounds__(kPairThreads) k_pair(PairArgs a) {
   // concatenated ranges by a 5-step shuffle search, so each 32-wide chunk holds 32 candidates.
   const int ncx = g.ncell[0], ncy = g.ncell[1], ncz = g.ncell[2];
   const int kx = g.kimg[0], ky = g.kimg[1], kz = g.kimg[2];
-  const bool zrun = ncz >= 5;                       // z offsets come from the candidate's cell
+  const bool zrun = ncz >= 2 * kz + 1;              // the z-cells of a column are distinct:
+                                                    // z offsets come from the candidate's cell
   const int nzs = zrun ? 1 : 2 * kz + 1;            // segments per (ox, oy) column
   const int nseg = (2 * kx + 1) * (2 * ky + 1) * nzs;
   for (int g0 = 0; g0 < nseg; g0 += 32) {
@@ -238,12 +245,12 @@ __global__ void __launch_bounds__(kPairThreads) k_pair(PairArgs a) {
       const int t = sidx / nzs;
       const int oy = (t % (2 * ky + 1)) - ky;
       const int ox = (t / (2 * ky + 1)) - kx;
-      int cx = ci.x + ox, cy = ci.y + oy;
-      if (ncx == 1) cx = 0; else { if (cx < 0) cx += ncx; else if (cx >= ncx) cx -= ncx; }
-      if (ncy == 1) cy = 0; else { if (cy < 0) cy += ncy; else if (cy >= ncy) cy -= ncy; }
-      const int row = (cx * ncy + cy) * ncz;
+      int cx = (ci.x + ox) % ncx, cy = (ci.y + oy) % ncy;
+      if (cx < 0) cx += ncx;
+      if (cy < 0) cy += ncy;
+      const int row = F.cell_off + (cx * ncy + cy) * ncz;
       if (zrun) {
-        const int z0 = ci.z - 2, z1 = ci.z + 2;
+        const int z0 = ci.z - kz, z1 = ci.z + kz;
         if (z0 < 0) {
           loA = a.start_c[row + z0 + ncz]; lenA = a.start_c[row + ncz] - loA;
           loB = a.start_c[row]; lenB = a.start_c[row + z1 + 1] - loB;
@@ -254,7 +261,9 @@ __global__ void __launch_bounds__(kPairThreads) k_pair(PairArgs a) {
           loA = a.start_c[row + z0]; lenA = a.start_c[row + z1 + 1] - loA;
         }
       } else {
-        loA = a.start_c[row]; lenA = a.start_c[row + 1] - loA;
+        int cz = (ci.z + oz) % ncz;
+        if (cz < 0) cz += ncz;
+        loA = a.start_c[row + cz]; lenA = a.start_c[row + cz + 1] - loA;
       }
       // offsets packed in one int: 10 bits each, biased by 512
       code = ((ox + 512) << 20) | ((oy + 512) << 10) | (oz + 512);
@@ -290,8 +299,8 @@ __global__ void __launch_bounds__(kPairThreads) k_pair(PairArgs a) {
       int oz = (scode & 1023) - 512;
       if (zrun && valid) {
         oz = a.pr.cz[j] - ci.z;
-        if (oz > 2) oz -= ncz;
-        else if (oz < -2) oz += ncz;
+        if (oz > kz) oz -= ncz;
+        else if (oz < -kz) oz += ncz;
       }
       test(valid, j, ox, oy, oz);
     }
@@ -339,7 +348,9 @@ int launch_pair(pme_plan_t p, cudaStream_t s, int n, bool tangent, const IonInpu
   (void)in;
   if (n == 0) return PME_OK;
   PairArgs a;
-  a.g = p->g;
+  a.one = p->frames_h[0];
+  a.maps = p->maps;
+  a.alpha = float(p->alpha);
   a.pr = p->pr;
   a.start_c = p->sb.start_c;
   a.g_energy = g_energy;
@@ -358,10 +369,13 @@ int launch_pair(pme_plan_t p, cudaStream_t s, int n, bool tangent, const IonInpu
   a.c3 = float(cl[3]);
   a.c4 = float(cl[4]);
   const int grid = (n + kPairWarps - 1) / kPairWarps;
-  if (tangent)
-    k_pair<true><<<grid, kPairThreads, 0, s>>>(a);
-  else
-    k_pair<false><<<grid, kPairThreads, 0, s>>>(a);
+  if (p->batch) {
+    if (tangent) k_pair<true, true><<<grid, kPairThreads, 0, s>>>(a);
+    else k_pair<false, true><<<grid, kPairThreads, 0, s>>>(a);
+  } else {
+    if (tangent) k_pair<true, false><<<grid, kPairThreads, 0, s>>>(a);
+    else k_pair<false, false><<<grid, kPairThreads, 0, s>>>(a);
+  }
   count_launch();
   return check_launch(p, "k_pair");
 }

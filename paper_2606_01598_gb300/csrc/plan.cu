@@ -1,11 +1,18 @@
 // Plan construction (Section 2.3.1: cell, reciprocal basis, mesh; Section 2.3.3: the
 // deconvolution tables), host-pointer staging, and the stream orchestration of the forward
 // and backward passes behind the C ABI declared in include/gbpme.h.
+//
+// A plan holds one or more frames. A single-frame plan (pme_plan_create) passes its frame
+// descriptor to every kernel as an argument; a batched plan (pme_batch_create) keeps a table
+// of descriptors on the device plus maps from ions, bricks and influence blocks to frames,
+// so each pipeline stage is one launch for the whole batch (spread and gather: one launch
+// per spline order; FFT: one batched cuFFT call per distinct mesh shape).
 #include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <numeric>
 #include <vector>
 
 #include "kernels.h"
@@ -82,8 +89,7 @@ static double perp_width(const double* box, int ax, double V) {
 // Bricks along one axis whose ions' stencils can reach each brick: an ion with first stencil
 // point m0 covers m0 .. m0 + P - 1 (mod N), so brick [b0, b0 + ext) is fed by m0 in
 // [b0 - P + 1, b0 + ext - 1] (mod N).
-static bool build_candidates(int N, int B, int P, int nb, int max_nb, std::vector<int>& tab,
-                             int axis) {
+static bool build_candidates(int N, int B, int P, int nb, int max_nb, int* tab, int axis) {
   for (int b = 0; b < nb; ++b) {
     const int b0 = b * B, ext = std::min(B, N - b0);
     std::vector<int> list;
@@ -97,7 +103,7 @@ static bool build_candidates(int N, int B, int P, int nb, int max_nb, std::vecto
       }
     }
     if (int(list.size()) > kMaxCandPerDim) return false;
-    int* row = tab.data() + (axis * max_nb + b) * (1 + kMaxCandPerDim);
+    int* row = tab + (axis * max_nb + b) * (1 + kMaxCandPerDim);
     row[0] = int(list.size());
     for (size_t k = 0; k < list.size(); ++k) row[1 + k] = list[k];
   }
@@ -109,38 +115,35 @@ static double sinc(double x) {
   return std::sin(kPi * x) / (kPi * x);
 }
 
-// Geometry that depends on the box (cell matrices, pair cells). Returns false when the box is
-// singular.
-static bool set_geometry(pme_plan_t p, const double* box, std::string& why) {
+// Box-dependent geometry of one frame (cell matrices, pair cells). g.N, g.order, g.alpha,
+// g.rcut2 and the brick shape are set by the caller. Returns false for a singular box.
+static bool frame_geometry(Geometry& g, const double* box, double rcut, bool pair, int* ncells,
+                           std::string& why) {
   double inv[9], det;
   if (!invert3(box, inv, &det)) {
     why = "singular or non-finite box";
     return false;
   }
-  std::memcpy(p->box, box, sizeof(double) * 9);
-  Geometry& g = p->g;
   for (int k = 0; k < 9; ++k) g.cinv[k] = inv[k];
   g.volume = std::fabs(det);
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) g.D[a * 3 + b] = float(double(g.N[b]) * inv[a * 3 + b]);
-  // pair cells at least rcut/2 wide; axes too short for 5 cells loop over images instead
-  int ncell = 1;
+  // pair cells at least rcut/2 wide (at least one per axis); a candidate cell lies at most
+  // kimg = ceil(rcut / cell width) cells away along each axis. When an axis has fewer than
+  // 2 kimg + 1 cells the offsets wrap onto the same cells again: each offset then stands for
+  // a different periodic image, so every image inside rcut is visited exactly once.
+  int nc_tot = 1;
   for (int a = 0; a < 3; ++a) {
     const double w = perp_width(box, a, g.volume);
-    int nc = p->opts.include_pair ? int(std::floor(w / (0.5 * p->rcut))) : 1;
-    nc = std::min(nc, 512);
-    if (nc >= 5) {
-      g.ncell[a] = nc;
-      g.kimg[a] = 2;
-    } else {
-      g.ncell[a] = 1;
-      g.kimg[a] = p->opts.include_pair ? int(std::ceil(p->rcut / w)) + 1 : 0;
-    }
-    ncell *= g.ncell[a];
+    int nc = pair ? int(std::floor(w / (0.5 * rcut))) : 1;
+    nc = std::max(1, std::min(nc, 512));
+    g.ncell[a] = nc;
+    g.kimg[a] = pair ? std::max(1, int(std::ceil(rcut * nc / w - 1e-9))) : 0;
+    nc_tot *= nc;
   }
   for (int b = 0; b < 3; ++b)
     for (int c = 0; c < 3; ++c) g.H[b * 3 + c] = float(box[b * 3 + c] / g.ncell[b]);
-  p->ncells = ncell;
+  *ncells = nc_tot;
   return true;
 }
 
@@ -180,15 +183,15 @@ struct Staging {
     float* d = p->stage_f + size_t(slot) * p->max_ions;
     const size_t bytes = sizeof(float) * size_t(width) * n;
     if (bytes && status == PME_OK)
-      status = check_cuda(p, cudaMemcpyAsync(d, ptr, bytes, cudaMemcpyHostToDevice, s),
-                          "stage input");
+      status = check_cuda(p, cudaMemcpyAsync(d, ptr, bytes, cudaMemcpyHostToDevice, s), "stage input");
     return d;
   }
-  const double* in_d(const double* ptr, int slot) {
+  // count doubles (per-frame energies / cotangents); slot 0 = outputs, 1 = inputs
+  const double* in_d(const double* ptr, int count, int slot) {
     if (!ptr || is_device_pointer(ptr)) return ptr;
-    double* d = p->stage_d + slot;
+    double* d = p->stage_d + size_t(slot) * p->nframes;
     if (status == PME_OK)
-      status = check_cuda(p, cudaMemcpyAsync(d, ptr, sizeof(double), cudaMemcpyHostToDevice, s),
+      status = check_cuda(p, cudaMemcpyAsync(d, ptr, sizeof(double) * count, cudaMemcpyHostToDevice, s),
                           "stage input");
     return d;
   }
@@ -198,10 +201,10 @@ struct Staging {
     outs.push_back({ptr, d, sizeof(float) * size_t(width) * n});
     return d;
   }
-  double* out_d(double* ptr, int slot) {
+  double* out_d(double* ptr, int count, int slot) {
     if (!ptr || is_device_pointer(ptr)) return ptr;
-    double* d = p->stage_d + slot;
-    outs.push_back({ptr, d, sizeof(double)});
+    double* d = p->stage_d + size_t(slot) * p->nframes;
+    outs.push_back({ptr, d, sizeof(double) * count});
     return d;
   }
   int finish() {
@@ -215,20 +218,22 @@ struct Staging {
   }
 };
 
+static int set_device(pme_plan_t p) {
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != p->device) return check_cuda(p, cudaSetDevice(p->device), "cudaSetDevice");
+  return PME_OK;
+}
+
 static int check_common(pme_plan_t p, int n, const float* pos, const float* q) {
   if (!p) return PME_ERR_ARG;
+  if (p->batch) return set_error(p, PME_ERR_ARG, "batched plan: use the pme_batch_* calls");
   if (n < 0 || n > p->max_ions)
     return set_error(p, PME_ERR_ARG, "n = " + std::to_string(n) + " outside [0, max_ions = " +
                                          std::to_string(p->max_ions) + "]");
   if (n > 0 && !pos) return set_error(p, PME_ERR_ARG, "pos is NULL");
   if (n > 0 && !q) return set_error(p, PME_ERR_ARG, "q is NULL");
-  int dev = -1;
-  cudaGetDevice(&dev);
-  if (dev != p->device) {
-    int st = check_cuda(p, cudaSetDevice(p->device), "cudaSetDevice");
-    if (st) return st;
-  }
-  return PME_OK;
+  return set_device(p);
 }
 
 static int fork_side(pme_plan_t p, cudaStream_t s) {
@@ -245,19 +250,25 @@ static int join_side(pme_plan_t p, cudaStream_t s) {
 
 static void free_plan(pme_plan_t p) {
   if (!p) return;
-  void* bufs[] = {p->rho, p->spec, p->phi, p->dconv[0], p->dconv[1], p->dconv[2], p->cand,
-                  p->sb.key_b, p->sb.key_c, p->sb.slot_b, p->sb.slot_c, p->sb.count_b,
-                  p->sb.count_c, p->sb.start_b, p->sb.start_c, p->sb.perm_b, p->sb.perm_c,
-                  p->sb.qpart, p->sb.qsum, p->mr.idx, p->mr.fq, p->mr.dm, p->mr.tq, p->mr.tt,
-                  p->pr.idx, p->pr.fq, p->pr.mu, p->pr.tq, p->pr.dr, p->pr.cz, p->mesh_out, p->pair_out,
-                  p->epart, p->flags, p->stage_f, p->stage_d, p->ew_kn, p->ew_kv, p->ew_S,
-                  p->ew_fx, p->ew_qm};
+  void* bufs[] = {p->rho, p->spec, p->phi, p->dconv_all, p->cand, p->sb.key_b, p->sb.key_c,
+                  p->sb.slot_b, p->sb.slot_c, p->sb.count_b, p->sb.count_c, p->sb.start_b,
+                  p->sb.start_c, p->sb.perm_b, p->sb.perm_c, p->sb.qsum, p->mr.idx, p->mr.fq,
+                  p->mr.dm, p->mr.tq, p->mr.tt, p->pr.idx, p->pr.fq, p->pr.mu, p->pr.tq, p->pr.dr,
+                  p->pr.cz, p->mesh_out, p->pair_out, p->e_ion, p->epart, p->flags, p->stage_f,
+                  p->stage_d, p->ew_kn, p->ew_kv, p->ew_S, p->ew_fx, p->ew_qm, p->frames_d,
+                  p->map_buf, p->fft_work};
   for (void* b : bufs)
     if (b) cudaFree(b);
-  if (p->r2c1) cufftDestroy(p->r2c1);
-  if (p->c2r1) cufftDestroy(p->c2r1);
-  if (p->r2c2) cufftDestroy(p->r2c2);
-  if (p->c2r2) cufftDestroy(p->c2r2);
+  for (int g = 0; g < p->nfgroups; ++g) {
+    FFTGroup& G = p->fgroups[g];
+    if (G.r2c) cufftDestroy(G.r2c);
+    if (G.c2r) cufftDestroy(G.c2r);
+    if (G.r2c2) cufftDestroy(G.r2c2);
+    if (G.c2r2) cufftDestroy(G.c2r2);
+  }
+  delete[] p->fgroups;
+  delete[] p->frames_h;
+  delete[] p->frame_offsets;
   if (p->prof_ev) {
     for (int k = 0; k < 2 * kProfCap; ++k) cudaEventDestroy(p->prof_ev[k]);
     delete[] p->prof_ev;
@@ -278,12 +289,12 @@ static int dalloc(pme_plan_t p, T** ptr, size_t count) {
 
 static int alloc_cells(pme_plan_t p) {
   int st;
-  if ((st = dalloc(p, &p->sb.count_c, size_t(p->ncells) + 1))) return st;
-  if ((st = dalloc(p, &p->sb.start_c, size_t(p->ncells) + 1))) return st;
+  if ((st = dalloc(p, &p->sb.count_c, size_t(p->total_cells) + 1))) return st;
+  if ((st = dalloc(p, &p->sb.start_c, size_t(p->total_cells) + 1))) return st;
   return PME_OK;
 }
 
-// (Re)build the explicit-Ewald k-vector tables for the current box.
+// (Re)build the explicit-Ewald k-vector tables for the current box (single-frame plans).
 static int setup_kvectors(pme_plan_t p) {
   std::vector<int4> kn;
   std::vector<float4> kv;
@@ -307,16 +318,318 @@ static int setup_kvectors(pme_plan_t p) {
                          "copy k-vectors")))
       return st;
   }
-  // the energy partials array must hold one slot per k block
+  // the energy partials hold one slot per k block; frame 0's "influence blocks" are those
+  const int kb = ewald_partial_blocks(p);
+  p->frames_h[0].infl_blk_off = 0;
+  p->frames_h[0].infl_nblk = kb;
   cudaFree(p->epart);
   p->epart = nullptr;
-  const int na = std::max(p->nspec_blocks, ewald_partial_blocks(p));
-  return dalloc(p, &p->epart, size_t(na) + p->max_blocks);
+  return dalloc(p, &p->epart, size_t(std::max(kb, p->total_blocks)) + 1);
 }
 
-// Forward with the explicit k-sum in place of the mesh stages.
+// ---- plan construction ----------------------------------------------------------------------
+
+struct FrameInput {
+  const double* box;
+  int mesh[3];
+  int order;
+  int ion_off, n;
+};
+
+// Build a plan over the given frames. single: one frame whose ion count is chosen per call.
+static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double alpha, double rcut,
+                      bool single) {
+  const int F = int(fin.size());
+  p->nframes = F;
+  p->batch = !single;
+  p->alpha = alpha;
+  p->rcut = rcut;
+  p->frames_h = new (std::nothrow) FrameDesc[F];
+  p->frame_offsets = new (std::nothrow) int[F + 1];
+  if (!p->frames_h || !p->frame_offsets) return set_error(p, PME_ERR_NOMEM, "host tables");
+  std::memset(p->frames_h, 0, sizeof(FrameDesc) * F);
+  const bool pair = p->opts.include_pair != 0;
+  int brick[3];
+  spread_brick_shape(brick);
+  std::vector<int> ncells(F);
+  for (int f = 0; f < F; ++f) {
+    FrameDesc& D = p->frames_h[f];
+    Geometry& g = D.g;
+    const FrameInput& in = fin[f];
+    if (in.order < 1 || in.order > kMaxOrder) return set_error(p, PME_ERR_ARG, "order outside 1..7");
+    for (int a = 0; a < 3; ++a)
+      if (in.mesh[a] < in.order || in.mesh[a] > 4096)
+        return set_error(p, PME_ERR_ARG, "mesh dimension < order (or > 4096)");
+    for (int a = 0; a < 3; ++a) {
+      g.N[a] = in.mesh[a];
+      g.brick[a] = brick[a];
+      g.nb[a] = (g.N[a] + brick[a] - 1) / brick[a];
+    }
+    g.order = in.order;
+    g.alpha = float(alpha);
+    g.rcut2 = float(rcut * rcut);
+    std::string why;
+    if (!frame_geometry(g, in.box, rcut, pair, &ncells[f], why)) return set_error(p, PME_ERR_ARG, why);
+    D.ion_off = in.ion_off;
+    D.n = in.n;
+    D.nbricks = g.nb[0] * g.nb[1] * g.nb[2];
+    D.ncells = ncells[f];
+    D.max_nb = std::max(g.nb[0], std::max(g.nb[1], g.nb[2]));
+    D.infl_nblk = influence_blocks(g);
+    p->frame_offsets[f] = in.ion_off;
+  }
+  p->frame_offsets[F] = single ? p->max_ions : fin[F - 1].ion_off + fin[F - 1].n;
+  p->g = p->frames_h[0].g;
+  std::memcpy(p->box, fin[0].box, sizeof(double) * 9);
+
+  // internal order of the frames: by spline order, then mesh shape (stable)
+  std::vector<int> ord(F);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+    const Geometry& ga = p->frames_h[a].g;
+    const Geometry& gb = p->frames_h[b].g;
+    if (ga.order != gb.order) return ga.order < gb.order;
+    for (int k = 0; k < 3; ++k)
+      if (ga.N[k] != gb.N[k]) return ga.N[k] < gb.N[k];
+    return false;
+  });
+  long long brick_off = 0, cell_off = 0, sorted_off = 0, cand_off = 0, dconv_off = 0, blk_off = 0;
+  for (int f : ord) {
+    FrameDesc& D = p->frames_h[f];
+    D.brick_off = int(brick_off);
+    D.cell_off = int(cell_off);
+    D.sorted_off = int(sorted_off);
+    D.cand_off = int(cand_off);
+    D.dconv_off = int(dconv_off);
+    D.infl_blk_off = int(blk_off);
+    brick_off += D.nbricks;
+    cell_off += D.ncells;
+    sorted_off += single ? 0 : D.n;
+    cand_off += 3LL * D.max_nb * (1 + kMaxCandPerDim);
+    dconv_off += D.g.N[0] + D.g.N[1] + D.g.N[2];
+    blk_off += D.infl_nblk;
+  }
+  if (brick_off > (1LL << 30) || cell_off > (1LL << 30)) return set_error(p, PME_ERR_UNSUPPORTED, "too many bricks");
+  p->total_bricks = int(brick_off);
+  p->total_cells = int(cell_off);
+  p->total_blocks = int(blk_off);
+  // spread / gather launch groups (one per spline order)
+  p->nogroups = 0;
+  for (int f : ord) {
+    const FrameDesc& D = p->frames_h[f];
+    if (p->nogroups == 0 || p->ogroups[p->nogroups - 1].order != D.g.order) {
+      OrderGroup& G = p->ogroups[p->nogroups++];
+      G.order = D.g.order;
+      G.brick_lo = D.brick_off;
+      G.sorted_lo = D.sorted_off;
+    }
+    OrderGroup& G = p->ogroups[p->nogroups - 1];
+    G.brick_hi = D.brick_off + D.nbricks;
+    G.sorted_hi = D.sorted_off + (single ? 0 : D.n);
+  }
+  // FFT groups (same order and mesh shape): rho of the members, then their d rho
+  std::vector<std::vector<int>> groups;
+  for (int f : ord) {
+    const Geometry& g = p->frames_h[f].g;
+    if (groups.empty()) {
+      groups.push_back({f});
+      continue;
+    }
+    const Geometry& h = p->frames_h[groups.back()[0]].g;
+    if (h.order == g.order && h.N[0] == g.N[0] && h.N[1] == g.N[1] && h.N[2] == g.N[2])
+      groups.back().push_back(f);
+    else
+      groups.push_back({f});
+  }
+  p->nfgroups = int(groups.size());
+  p->fgroups = new (std::nothrow) FFTGroup[p->nfgroups];
+  if (!p->fgroups) return set_error(p, PME_ERR_NOMEM, "host tables");
+  std::memset(p->fgroups, 0, sizeof(FFTGroup) * p->nfgroups);
+  long long mesh_off = 0, spec_off = 0;
+  for (int gi = 0; gi < p->nfgroups; ++gi) {
+    FFTGroup& G = p->fgroups[gi];
+    const Geometry& g = p->frames_h[groups[gi][0]].g;
+    const long long M = (long long)g.N[0] * g.N[1] * g.N[2];
+    const long long Mh = (long long)g.N[0] * g.N[1] * (g.N[2] / 2 + 1);
+    for (int k = 0; k < 3; ++k) G.N[k] = g.N[k];
+    G.count = int(groups[gi].size());
+    G.mesh_off = mesh_off;
+    G.spec_off = spec_off;
+    for (int k = 0; k < G.count; ++k) {
+      FrameDesc& D = p->frames_h[groups[gi][k]];
+      D.mesh_off = mesh_off + k * M;
+      D.tmesh_off = mesh_off + (G.count + k) * M;
+      D.spec_off = spec_off + k * Mh;
+      D.tspec_off = spec_off + (G.count + k) * Mh;
+    }
+    mesh_off += 2LL * G.count * M;
+    spec_off += 2LL * G.count * Mh;
+  }
+  p->total_mesh = mesh_off;
+  p->total_spec = spec_off;
+  {
+    const Geometry& g0 = p->frames_h[0].g;
+    p->M = g0.N[0] * g0.N[1] * g0.N[2];
+    p->Mh = g0.N[0] * g0.N[1] * (g0.N[2] / 2 + 1);
+  }
+
+  // ---- device buffers ----------------------------------------------------------------------
+  cudaGetDevice(&p->device);
+  int st = PME_OK;
+  auto A = [&](auto** ptr, size_t count) {
+    if (st == PME_OK) st = dalloc(p, ptr, count);
+  };
+  const size_t ni = size_t(p->max_ions);
+  A(&p->rho, size_t(p->total_mesh));
+  A(&p->spec, size_t(p->total_spec));
+  A(&p->phi, size_t(p->total_mesh));
+  A(&p->dconv_all, size_t(dconv_off));
+  A(&p->cand, size_t(cand_off));
+  A(&p->sb.key_b, ni);
+  A(&p->sb.key_c, ni);
+  A(&p->sb.slot_b, ni);
+  A(&p->sb.slot_c, ni);
+  A(&p->sb.perm_b, ni);
+  A(&p->sb.perm_c, ni);
+  A(&p->sb.count_b, size_t(p->total_bricks) + 1);
+  A(&p->sb.start_b, size_t(p->total_bricks) + 1);
+  A(&p->sb.qsum, size_t(2) * F);
+  A(&p->mr.idx, ni);
+  A(&p->mr.fq, ni);
+  A(&p->mr.dm, ni);
+  A(&p->mr.tq, ni);
+  A(&p->mr.tt, ni);
+  A(&p->pr.idx, ni);
+  A(&p->pr.fq, ni);
+  A(&p->pr.mu, ni);
+  A(&p->pr.tq, ni);
+  A(&p->pr.dr, ni);
+  A(&p->pr.cz, ni);
+  A(&p->mesh_out, ni * 10);
+  A(&p->pair_out, ni * 10);
+  A(&p->e_ion, ni);
+  A(&p->epart, size_t(p->total_blocks) + 1);
+  A(&p->flags, 1);
+  A(&p->stage_f, ni * kStageFloats);
+  A(&p->stage_d, size_t(2) * F + 2);
+  if (st == PME_OK) st = alloc_cells(p);
+  if (st) return st;
+  if ((st = check_cuda(p, cudaMemset(p->flags, 0, sizeof(int)), "memset"))) return st;
+  // candidate tables and deconvolution tables, frame by frame
+  {
+    std::vector<int> cand(size_t(cand_off), 0);
+    std::vector<float> dc(size_t(dconv_off), 1.f);
+    for (int f = 0; f < F; ++f) {
+      const FrameDesc& D = p->frames_h[f];
+      const Geometry& g = D.g;
+      for (int a = 0; a < 3; ++a)
+        if (!build_candidates(g.N[a], g.brick[a], g.order, g.nb[a], D.max_nb, cand.data() + D.cand_off, a))
+          return set_error(p, PME_ERR_UNSUPPORTED, "mesh / brick / order combination not supported");
+      // C(n) = 1 / sinc^(2 p gamma)(n / N) per axis (Eqs. Bk, influence)
+      int o = D.dconv_off;
+      for (int a = 0; a < 3; ++a)
+        for (int i = 0; i < g.N[a]; ++i) {
+          const int nsig = (i <= g.N[a] / 2) ? i : i - g.N[a];
+          const double b = std::pow(sinc(double(nsig) / g.N[a]), double(g.order));
+          dc[o++] = p->opts.deconvolution ? float(std::pow(b * b, -p->opts.influence_power)) : 1.f;
+        }
+    }
+    if ((st = check_cuda(p, cudaMemcpy(p->cand, cand.data(), sizeof(int) * cand.size(), cudaMemcpyHostToDevice),
+                         "copy candidates")))
+      return st;
+    if ((st = check_cuda(p, cudaMemcpy(p->dconv_all, dc.data(), sizeof(float) * dc.size(), cudaMemcpyHostToDevice),
+                         "copy deconvolution")))
+      return st;
+  }
+  // batched plans: descriptor table and frame maps on the device
+  if (!single) {
+    const long long Ntot = p->frame_offsets[F];
+    std::vector<int> maps(size_t(2 * Ntot + p->total_bricks + p->total_blocks));
+    int* ion_frame = maps.data();
+    int* sorted_frame = ion_frame + Ntot;
+    int* brick_frame = sorted_frame + Ntot;
+    int* blk_frame = brick_frame + p->total_bricks;
+    for (int f = 0; f < F; ++f) {
+      const FrameDesc& D = p->frames_h[f];
+      for (int k = 0; k < D.n; ++k) {
+        ion_frame[D.ion_off + k] = f;
+        sorted_frame[D.sorted_off + k] = f;
+      }
+      for (int k = 0; k < D.nbricks; ++k) brick_frame[D.brick_off + k] = f;
+      for (int k = 0; k < D.infl_nblk; ++k) blk_frame[D.infl_blk_off + k] = f;
+    }
+    if ((st = dalloc(p, &p->map_buf, maps.size()))) return st;
+    if ((st = dalloc(p, &p->frames_d, size_t(F)))) return st;
+    if ((st = check_cuda(p, cudaMemcpy(p->map_buf, maps.data(), sizeof(int) * maps.size(), cudaMemcpyHostToDevice),
+                         "copy maps")))
+      return st;
+    if ((st = check_cuda(p, cudaMemcpy(p->frames_d, p->frames_h, sizeof(FrameDesc) * F, cudaMemcpyHostToDevice),
+                         "copy frames")))
+      return st;
+    p->maps.desc = p->frames_d;
+    p->maps.ion_frame = p->map_buf;
+    p->maps.sorted_frame = p->map_buf + Ntot;
+    p->maps.brick_frame = p->map_buf + 2 * Ntot;
+    p->maps.blk_frame = p->map_buf + 2 * Ntot + p->total_bricks;
+  }
+  // cuFFT: four plans per group sharing one work area
+  size_t work = 0;
+  for (int gi = 0; gi < p->nfgroups; ++gi) {
+    FFTGroup& G = p->fgroups[gi];
+    int dims[3] = {G.N[0], G.N[1], G.N[2]};
+    cufftHandle* hs[4] = {&G.r2c, &G.c2r, &G.r2c2, &G.c2r2};
+    const cufftType ty[4] = {CUFFT_R2C, CUFFT_C2R, CUFFT_R2C, CUFFT_C2R};
+    const int batch[4] = {G.count, G.count, 2 * G.count, 2 * G.count};
+    for (int k = 0; k < 4; ++k) {
+      size_t ws = 0;
+      if ((st = check_fft(p, cufftCreate(hs[k]), "cufftCreate"))) return st;
+      if ((st = check_fft(p, cufftSetAutoAllocation(*hs[k], 0), "cufftSetAutoAllocation"))) return st;
+      if ((st = check_fft(p, cufftMakePlanMany(*hs[k], 3, dims, nullptr, 1, 0, nullptr, 1, 0, ty[k], batch[k], &ws),
+                          "cufftMakePlanMany")))
+        return st;
+      work = std::max(work, ws);
+    }
+  }
+  if ((st = check_cuda(p, cudaMalloc(&p->fft_work, std::max<size_t>(work, 16)), "cudaMalloc"))) return st;
+  for (int gi = 0; gi < p->nfgroups; ++gi) {
+    FFTGroup& G = p->fgroups[gi];
+    for (cufftHandle h : {G.r2c, G.c2r, G.r2c2, G.c2r2})
+      if ((st = check_fft(p, cufftSetWorkArea(h, p->fft_work), "cufftSetWorkArea"))) return st;
+  }
+  if ((st = check_cuda(p, cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking), "stream")) ||
+      (st = check_cuda(p, cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming), "event")) ||
+      (st = check_cuda(p, cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming), "event")))
+    return st;
+  return PME_OK;
+}
+
+// ---- the passes ----------------------------------------------------------------------------
+
+static int fft_forward(pme_plan_t p, cudaStream_t s, bool tangent) {
+  int st;
+  for (int gi = 0; gi < p->nfgroups; ++gi) {
+    FFTGroup& G = p->fgroups[gi];
+    cufftHandle h = tangent ? G.r2c2 : G.r2c;
+    if ((st = check_fft(p, cufftSetStream(h, s), "set stream"))) return st;
+    if ((st = check_fft(p, cufftExecR2C(h, p->rho + G.mesh_off, p->spec + G.spec_off), "exec r2c"))) return st;
+  }
+  return PME_OK;
+}
+
+static int fft_inverse(pme_plan_t p, cudaStream_t s, bool tangent) {
+  int st;
+  for (int gi = 0; gi < p->nfgroups; ++gi) {
+    FFTGroup& G = p->fgroups[gi];
+    cufftHandle h = tangent ? G.c2r2 : G.c2r;
+    if ((st = check_fft(p, cufftSetStream(h, s), "set stream"))) return st;
+    if ((st = check_fft(p, cufftExecC2R(h, p->spec + G.spec_off, p->phi + G.mesh_off), "exec c2r"))) return st;
+  }
+  return PME_OK;
+}
+
+// Forward with the explicit k-sum in place of the mesh stages (single-frame plans).
 static int forward_ewald(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool pair, double* e_out,
-                         float* f_out, float* p_out, float* fl_out, float* fg_out, Staging& sg) {
+                         float* f_out, float* p_out, float* fl_out, float* fg_out) {
   const int n = in.n;
   int st, t;
   t = prof_begin(p, 0, s);
@@ -334,19 +647,112 @@ static int forward_ewald(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool
   if ((st = launch_ewald_recip(p, s, in, p->epart, p->mesh_out))) return st;
   prof_end(p, t, s);
   if (fork && p->opts.overlap_pair && (st = join_side(p, s))) return st;
-  const int na = ewald_partial_blocks(p);
   t = prof_begin(p, 7, s);
-  if ((st = launch_combine_forward(p, s, in, true, fork, p->epart + na, f_out, p_out, fl_out, fg_out)))
+  if ((st = launch_combine_forward(p, s, in, true, fork, f_out, p_out, fl_out, fg_out))) return st;
+  prof_end(p, t, s);
+  if (e_out &&
+      (st = launch_energy_final(p, s, p->epart, 2, n > 0, p->opts.include_background != 0,
+                                p->opts.coulomb_k, n, e_out)))
     return st;
+  return PME_OK;
+}
+
+// Forward pass over every frame of the plan (in.n ions in total).
+static int run_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, double* e_out, float* f_out,
+                       float* p_out, float* fl_out, float* fg_out) {
+  const int n = in.n;
+  const bool pair = p->opts.include_pair != 0;
+  if (p->opts.recip_method == 1) return forward_ewald(p, s, in, pair, e_out, f_out, p_out, fl_out, fg_out);
+  int st, t;
+  t = prof_begin(p, 0, s);
+  if ((st = launch_sort(p, s, in, false, true, pair))) return st;
+  prof_end(p, t, s);
+  // the pair term runs on the plan's side stream, concurrently with the mesh stages
+  const bool fork = pair && n > 0;
+  cudaStream_t ps = p->opts.overlap_pair ? p->side : s;
+  if (fork) {
+    if (p->opts.overlap_pair && (st = fork_side(p, s))) return st;
+    t = prof_begin(p, 6, ps);
+    if ((st = launch_pair(p, ps, n, false, in, nullptr, p->pair_out))) return st;
+    prof_end(p, t, ps);
+  }
+  t = prof_begin(p, 1, s);
+  if ((st = launch_spread(p, s, false, p->rho))) return st;
+  prof_end(p, t, s);
+  t = prof_begin(p, 2, s);
+  if ((st = fft_forward(p, s, false))) return st;
+  prof_end(p, t, s);
+  t = prof_begin(p, 3, s);
+  if ((st = launch_influence(p, s, p->spec, false, p->epart))) return st;
+  prof_end(p, t, s);
+  t = prof_begin(p, 4, s);
+  if ((st = fft_inverse(p, s, false))) return st;
+  prof_end(p, t, s);
+  t = prof_begin(p, 5, s);
+  if ((st = launch_gather(p, s, n, p->phi, false, nullptr, p->mesh_out))) return st;
+  prof_end(p, t, s);
+  if (fork && p->opts.overlap_pair && (st = join_side(p, s))) return st;
+  t = prof_begin(p, 7, s);
+  if ((st = launch_combine_forward(p, s, in, true, fork, f_out, p_out, fl_out, fg_out))) return st;
   prof_end(p, t, s);
   if (e_out) {
-    const double bgfac =
-        p->opts.include_background ? -kPi / (2.0 * p->g.volume * p->alpha * p->alpha) : 0.0;
-    if ((st = launch_energy_final(p, s, p->epart, na, combine_blocks(n), 4.0 * kPi / p->g.volume,
-                                  p->opts.coulomb_k, bgfac, p->sb.qsum, e_out)))
+    t = prof_begin(p, 8, s);
+    if ((st = launch_energy_final(p, s, p->epart, 1, n > 0, p->opts.include_background != 0,
+                                  p->opts.coulomb_k, n, e_out)))
       return st;
+    prof_end(p, t, s);
   }
-  return sg.finish();
+  return PME_OK;
+}
+
+// Backward pass (gradient plus Hessian-vector product) over every frame of the plan.
+static int run_backward(pme_plan_t p, cudaStream_t s, const IonInputs& in, const double* gE,
+                        float* o_pos, float* o_q, float* o_mu) {
+  const int n = in.n;
+  if (n == 0) return PME_OK;
+  const bool pair = p->opts.include_pair != 0;
+  constexpr int B = PME_STAGES_PER_PASS;
+  int st, t;
+  t = prof_begin(p, B + 0, s);
+  if ((st = launch_sort(p, s, in, true, true, pair))) return st;
+  prof_end(p, t, s);
+  cudaStream_t ps = p->opts.overlap_pair ? p->side : s;
+  if (pair) {
+    if (p->opts.overlap_pair && (st = fork_side(p, s))) return st;
+    t = prof_begin(p, B + 6, ps);
+    if ((st = launch_pair(p, ps, n, true, in, gE, p->pair_out))) return st;
+    prof_end(p, t, ps);
+  }
+  t = prof_begin(p, B + 1, s);
+  if ((st = launch_spread(p, s, true, p->rho))) return st;
+  prof_end(p, t, s);
+  t = prof_begin(p, B + 2, s);
+  if ((st = fft_forward(p, s, true))) return st;
+  prof_end(p, t, s);
+  t = prof_begin(p, B + 3, s);
+  if ((st = launch_influence(p, s, p->spec, true, p->epart))) return st;
+  prof_end(p, t, s);
+  t = prof_begin(p, B + 4, s);
+  if ((st = fft_inverse(p, s, true))) return st;
+  prof_end(p, t, s);
+  t = prof_begin(p, B + 5, s);
+  if ((st = launch_gather(p, s, n, p->phi, true, gE, p->mesh_out))) return st;
+  prof_end(p, t, s);
+  if (pair && p->opts.overlap_pair && (st = join_side(p, s))) return st;
+  t = prof_begin(p, B + 7, s);
+  if ((st = launch_combine_backward(p, s, in, gE, o_pos, o_q, o_mu))) return st;
+  prof_end(p, t, s);
+  return PME_OK;
+}
+
+static int validate_opts(pme_plan_s* p, double alpha, double rcut) {
+  if (!(alpha > 0.0) || !std::isfinite(alpha)) return set_error(p, PME_ERR_ARG, "alpha must be > 0");
+  if (p->opts.include_pair && !(rcut > 0.0)) return set_error(p, PME_ERR_ARG, "rcut must be > 0");
+  if (p->opts.max_ions <= 0) return set_error(p, PME_ERR_ARG, "max_ions must be > 0");
+  if (!(p->opts.influence_power >= 0.0)) return set_error(p, PME_ERR_ARG, "influence_power < 0");
+  if (p->opts.recip_method < 0 || p->opts.recip_method > 1) return set_error(p, PME_ERR_ARG, "recip_method");
+  p->opts_kmax = p->opts.ewald_kmax > 0.0 ? p->opts.ewald_kmax : 2.0 * alpha * std::sqrt(std::log(1e8));
+  return PME_OK;
 }
 
 }  // namespace gbpme
@@ -431,144 +837,81 @@ int pme_plan_create(pme_plan_t* out, const double box[9], const int mesh[3], int
   if (!p) return PME_ERR_NOMEM;
   if (opts) p->opts = *opts;
   else pme_opts_default(&p->opts);
-  auto fail = [&](int st, const std::string& why) {
-    (void)why;   // the plan (and its error text) is released; only the status survives
-    free_plan(p);
+  int st = validate_opts(p, alpha, rcut);
+  if (st == PME_OK) {
+    p->max_ions = p->opts.max_ions;
+    FrameInput fi{box, {mesh[0], mesh[1], mesh[2]}, order, 0, p->max_ions};
+    st = build_plan(p, {fi}, alpha, rcut, true);
+  }
+  if (st == PME_OK && p->opts.recip_method == 1) {
+    const size_t ni = size_t(p->max_ions);
+    if ((st = dalloc(p, &p->ew_fx, ni)) == PME_OK && (st = dalloc(p, &p->ew_qm, ni)) == PME_OK)
+      st = setup_kvectors(p);
+  }
+  if (st) {
+    free_plan(p);   // the plan (and its error text) is released; only the status survives
     return st;
-  };
-  if (order < 1 || order > kMaxOrder) return fail(PME_ERR_ARG, "order outside 1..7");
-  if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(PME_ERR_ARG, "alpha must be > 0");
-  if (p->opts.include_pair && !(rcut > 0.0)) return fail(PME_ERR_ARG, "rcut must be > 0");
-  if (p->opts.max_ions <= 0) return fail(PME_ERR_ARG, "max_ions must be > 0");
-  for (int a = 0; a < 3; ++a)
-    if (mesh[a] < order || mesh[a] > 4096) return fail(PME_ERR_ARG, "mesh dimension < order");
-  if (!(p->opts.influence_power >= 0.0)) return fail(PME_ERR_ARG, "influence_power < 0");
-  if (p->opts.recip_method < 0 || p->opts.recip_method > 1) return fail(PME_ERR_ARG, "recip_method");
-  p->opts_kmax = p->opts.ewald_kmax > 0.0 ? p->opts.ewald_kmax : 2.0 * alpha * std::sqrt(std::log(1e8));
-  Geometry& g = p->g;
-  for (int a = 0; a < 3; ++a) g.N[a] = mesh[a];
-  g.order = order;
-  g.alpha = float(alpha);
-  g.rcut2 = float(rcut * rcut);
-  p->alpha = alpha;
-  p->rcut = rcut;
-  p->max_ions = p->opts.max_ions;
-  p->max_blocks = (p->max_ions + 255) / 256;
-  std::string why;
-  if (!set_geometry(p, box, why)) return fail(PME_ERR_ARG, why);
-  spread_brick_shape(g.brick);
-  for (int a = 0; a < 3; ++a) g.nb[a] = (g.N[a] + g.brick[a] - 1) / g.brick[a];
-  p->nbricks = g.nb[0] * g.nb[1] * g.nb[2];
-  p->max_nb = std::max(g.nb[0], std::max(g.nb[1], g.nb[2]));
-  std::vector<int> cand(size_t(3) * p->max_nb * (1 + kMaxCandPerDim), 0);
-  for (int a = 0; a < 3; ++a)
-    if (!build_candidates(g.N[a], g.brick[a], order, g.nb[a], p->max_nb, cand, a))
-      return fail(PME_ERR_UNSUPPORTED, "mesh / brick / order combination not supported");
-  p->M = g.N[0] * g.N[1] * g.N[2];
-  p->Mh = g.N[0] * g.N[1] * (g.N[2] / 2 + 1);
-  cudaGetDevice(&p->device);
-
-  int st = PME_OK;
-  auto A = [&](auto** ptr, size_t count) {
-    if (st == PME_OK) st = dalloc(p, ptr, count);
-  };
-  A(&p->rho, size_t(2) * p->M);
-  A(&p->spec, size_t(2) * p->Mh);
-  A(&p->phi, size_t(2) * p->M);
-  for (int a = 0; a < 3; ++a) A(&p->dconv[a], size_t(g.N[a]));
-  A(&p->cand, cand.size());
-  const size_t ni = size_t(p->max_ions);
-  A(&p->sb.key_b, ni);
-  A(&p->sb.key_c, ni);
-  A(&p->sb.slot_b, ni);
-  A(&p->sb.slot_c, ni);
-  A(&p->sb.perm_b, ni);
-  A(&p->sb.perm_c, ni);
-  A(&p->sb.count_b, size_t(p->nbricks) + 1);
-  A(&p->sb.start_b, size_t(p->nbricks) + 1);
-  A(&p->sb.qpart, size_t(2) * p->max_blocks);
-  A(&p->sb.qsum, 2);
-  A(&p->mr.idx, ni);
-  A(&p->mr.fq, ni);
-  A(&p->mr.dm, ni);
-  A(&p->mr.tq, ni);
-  A(&p->mr.tt, ni);
-  A(&p->pr.idx, ni);
-  A(&p->pr.fq, ni);
-  A(&p->pr.mu, ni);
-  A(&p->pr.tq, ni);
-  A(&p->pr.dr, ni);
-  A(&p->pr.cz, ni);
-  A(&p->mesh_out, ni * 10);
-  A(&p->pair_out, ni * 10);
-  p->nspec_blocks = influence_grid(p);
-  A(&p->epart, size_t(p->nspec_blocks) + p->max_blocks);
-  A(&p->flags, 1);
-  A(&p->stage_f, ni * kStageFloats);
-  A(&p->stage_d, 4);
-  if (st == PME_OK) st = alloc_cells(p);
-  if (p->opts.recip_method == 1) {
-    A(&p->ew_fx, ni);
-    A(&p->ew_qm, ni);
-    if (st == PME_OK) st = setup_kvectors(p);
   }
-  if (st) return fail(st, p->last_error);
-  if ((st = check_cuda(p, cudaMemset(p->flags, 0, sizeof(int)), "memset"))) return fail(st, p->last_error);
-  if ((st = check_cuda(p, cudaMemcpy(p->cand, cand.data(), sizeof(int) * cand.size(),
-                                     cudaMemcpyHostToDevice), "copy candidates")))
-    return fail(st, p->last_error);
-  // deconvolution C(n) = 1 / sinc^(2 p gamma)(n / N) per axis (Eqs. Bk, influence)
-  for (int a = 0; a < 3; ++a) {
-    std::vector<float> t(g.N[a]);
-    for (int i = 0; i < g.N[a]; ++i) {
-      const int nsig = (i <= g.N[a] / 2) ? i : i - g.N[a];
-      const double b = std::pow(sinc(double(nsig) / g.N[a]), double(order));
-      t[i] = p->opts.deconvolution ? float(std::pow(b * b, -p->opts.influence_power)) : 1.f;
-    }
-    if ((st = check_cuda(p, cudaMemcpy(p->dconv[a], t.data(), sizeof(float) * t.size(),
-                                       cudaMemcpyHostToDevice), "copy deconvolution")))
-      return fail(st, p->last_error);
-  }
-  int dims[3] = {g.N[0], g.N[1], g.N[2]};
-  if ((st = check_fft(p, cufftPlanMany(&p->r2c1, 3, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_R2C, 1), "plan r2c")) ||
-      (st = check_fft(p, cufftPlanMany(&p->c2r1, 3, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2R, 1), "plan c2r")) ||
-      (st = check_fft(p, cufftPlanMany(&p->r2c2, 3, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_R2C, 2), "plan r2c x2")) ||
-      (st = check_fft(p, cufftPlanMany(&p->c2r2, 3, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2R, 2), "plan c2r x2")))
-    return fail(st, p->last_error);
-  if ((st = check_cuda(p, cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking), "stream")) ||
-      (st = check_cuda(p, cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming), "event")) ||
-      (st = check_cuda(p, cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming), "event")))
-    return fail(st, p->last_error);
   *out = p;
   return PME_OK;
 }
 
+int pme_batch_create(pme_plan_t* out, int nframes, const int* offsets, const double* boxes,
+                     const int* meshes, const int* orders, double alpha, double rcut,
+                     const pme_opts* opts) {
+  if (!out) return PME_ERR_ARG;
+  *out = nullptr;
+  if (nframes <= 0 || !offsets || !boxes || !meshes || !orders) return PME_ERR_ARG;
+  if (offsets[0] != 0) return PME_ERR_ARG;
+  for (int f = 0; f < nframes; ++f)
+    if (offsets[f + 1] < offsets[f]) return PME_ERR_ARG;
+  pme_plan_s* p = new (std::nothrow) pme_plan_s();
+  if (!p) return PME_ERR_NOMEM;
+  if (opts) p->opts = *opts;
+  else pme_opts_default(&p->opts);
+  int st = validate_opts(p, alpha, rcut);
+  if (st == PME_OK && p->opts.recip_method != 0) st = PME_ERR_UNSUPPORTED;
+  if (st == PME_OK) {
+    p->max_ions = std::max(1, offsets[nframes]);
+    std::vector<FrameInput> fin(nframes);
+    for (int f = 0; f < nframes; ++f)
+      fin[f] = FrameInput{boxes + 9 * f, {meshes[3 * f], meshes[3 * f + 1], meshes[3 * f + 2]}, orders[f],
+                          offsets[f], offsets[f + 1] - offsets[f]};
+    st = build_plan(p, fin, alpha, rcut, false);
+  }
+  if (st) {
+    free_plan(p);
+    return st;
+  }
+  *out = p;
+  return PME_OK;
+}
+
+int pme_batch_frames(pme_plan_t p) { return p ? p->nframes : 0; }
+
 int pme_plan_set_box(pme_plan_t p, const double box[9]) {
   if (!p || !box) return PME_ERR_ARG;
-  const int old_cells = p->ncells;
-  Geometry saved = p->g;
-  double saved_box[9];
-  std::memcpy(saved_box, p->box, sizeof(saved_box));
+  if (p->batch) return set_error(p, PME_ERR_UNSUPPORTED, "pme_plan_set_box takes a single-frame plan");
+  FrameDesc& D = p->frames_h[0];
+  Geometry g = D.g;
+  int nc = 0;
   std::string why;
-  if (!set_geometry(p, box, why)) {
-    p->g = saved;
-    std::memcpy(p->box, saved_box, sizeof(saved_box));
-    p->ncells = old_cells;
-    return set_error(p, PME_ERR_ARG, why);
-  }
-  if (p->ncells > old_cells) {
-    int st = check_cuda(p, cudaDeviceSynchronize(), "synchronize");
-    if (st) return st;
+  if (!frame_geometry(g, box, p->rcut, p->opts.include_pair != 0, &nc, why)) return set_error(p, PME_ERR_ARG, why);
+  int st = check_cuda(p, cudaDeviceSynchronize(), "synchronize");
+  if (st) return st;
+  D.g = g;
+  D.ncells = nc;
+  p->g = g;
+  std::memcpy(p->box, box, sizeof(double) * 9);
+  if (nc > p->total_cells) {
     cudaFree(p->sb.count_c);
     cudaFree(p->sb.start_c);
     p->sb.count_c = p->sb.start_c = nullptr;
+    p->total_cells = nc;
     if ((st = alloc_cells(p))) return st;
   }
-  if (p->opts.recip_method == 1) {
-    int st = check_cuda(p, cudaDeviceSynchronize(), "synchronize");
-    if (st) return st;
-    return setup_kvectors(p);
-  }
+  p->total_cells = std::max(p->total_cells, nc);
+  if (p->opts.recip_method == 1) return setup_kvectors(p);
   return PME_OK;
 }
 
@@ -606,59 +949,13 @@ int pme_forward(pme_plan_t p, void* stream, int n, const float* pos, const float
   in.q = sg.in(q, 1, kQ);
   in.mu = sg.in(mu, 3, kMu);
   in.n = n;
-  double* e_out = sg.out_d(energy, 0);
+  double* e_out = sg.out_d(energy, 1, 0);
   float* f_out = sg.out(force, 3, kOF);
   float* p_out = sg.out(phi, 1, kOPhi);
   float* fl_out = sg.out(field, 3, kOField);
   float* fg_out = sg.out(field_grad, 6, kOFG);
   if (sg.status) return sg.status;
-  const bool pair = p->opts.include_pair != 0;
-  int t;
-  if (p->opts.recip_method == 1) return forward_ewald(p, s, in, pair, e_out, f_out, p_out, fl_out, fg_out, sg);
-  t = prof_begin(p, 0, s);
-  if ((st = launch_sort(p, s, in, false, true, pair))) return st;
-  prof_end(p, t, s);
-  // the pair term runs on the plan's side stream, concurrently with the mesh stages
-  const bool fork = pair && n > 0;
-  cudaStream_t ps = p->opts.overlap_pair ? p->side : s;
-  if (fork) {
-    if (p->opts.overlap_pair && (st = fork_side(p, s))) return st;
-    t = prof_begin(p, 6, ps);
-    if ((st = launch_pair(p, ps, n, false, in, nullptr, p->pair_out))) return st;
-    prof_end(p, t, ps);
-  }
-  t = prof_begin(p, 1, s);
-  if ((st = launch_spread(p, s, n, false, p->rho, nullptr))) return st;
-  prof_end(p, t, s);
-  t = prof_begin(p, 2, s);
-  if ((st = check_fft(p, cufftSetStream(p->r2c1, s), "set stream"))) return st;
-  if ((st = check_fft(p, cufftExecR2C(p->r2c1, p->rho, p->spec), "exec r2c"))) return st;
-  prof_end(p, t, s);
-  t = prof_begin(p, 3, s);
-  if ((st = launch_influence(p, s, p->spec, 1, p->epart))) return st;
-  prof_end(p, t, s);
-  t = prof_begin(p, 4, s);
-  if ((st = check_fft(p, cufftSetStream(p->c2r1, s), "set stream"))) return st;
-  if ((st = check_fft(p, cufftExecC2R(p->c2r1, p->spec, p->phi), "exec c2r"))) return st;
-  prof_end(p, t, s);
-  t = prof_begin(p, 5, s);
-  if ((st = launch_gather(p, s, n, p->phi, nullptr, false, in, nullptr, p->mesh_out))) return st;
-  prof_end(p, t, s);
-  if (fork && p->opts.overlap_pair && (st = join_side(p, s))) return st;
-  t = prof_begin(p, 7, s);
-  if ((st = launch_combine_forward(p, s, in, true, pair && n > 0, p->epart + p->nspec_blocks,
-                                   f_out, p_out, fl_out, fg_out)))
-    return st;
-  prof_end(p, t, s);
-  if (e_out) {
-    const double bgfac =
-        p->opts.include_background ? -kPi / (2.0 * p->g.volume * p->alpha * p->alpha) : 0.0;
-    t = prof_begin(p, 8, s);
-    if ((st = launch_energy_final(p, s, p->epart, p->nspec_blocks, combine_blocks(n),
-                                  0.5 / p->g.volume, p->opts.coulomb_k, bgfac, p->sb.qsum, e_out)))
-      return st;
-    prof_end(p, t, s);
-  }
+  if ((st = run_forward(p, s, in, e_out, f_out, p_out, fl_out, fg_out))) return st;
   return sg.finish();
 }
 
@@ -680,46 +977,66 @@ int pme_backward(pme_plan_t p, void* stream, int n, const float* pos, const floa
   in.gphi = sg.in(g_phi, 1, kGPhi);
   in.gfield = sg.in(g_field, 3, kGField);
   in.n = n;
-  const double* gE = sg.in_d(g_energy, 1);
+  const double* gE = sg.in_d(g_energy, 1, 1);
   float* o_pos = sg.out(grad_pos, 3, kOGPos);
   float* o_q = sg.out(grad_q, 1, kOGQ);
   float* o_mu = sg.out(grad_mu, 3, kOGMu);
   if (sg.status) return sg.status;
-  if (n == 0) return sg.finish();
-  const bool pair = p->opts.include_pair != 0;
-  constexpr int B = PME_STAGES_PER_PASS;
-  int t;
-  t = prof_begin(p, B + 0, s);
-  if ((st = launch_sort(p, s, in, true, true, pair))) return st;
-  prof_end(p, t, s);
-  cudaStream_t ps = p->opts.overlap_pair ? p->side : s;
-  if (pair) {
-    if (p->opts.overlap_pair && (st = fork_side(p, s))) return st;
-    t = prof_begin(p, B + 6, ps);
-    if ((st = launch_pair(p, ps, n, true, in, gE, p->pair_out))) return st;
-    prof_end(p, t, ps);
-  }
-  t = prof_begin(p, B + 1, s);
-  if ((st = launch_spread(p, s, n, true, p->rho, p->rho + p->M))) return st;
-  prof_end(p, t, s);
-  t = prof_begin(p, B + 2, s);
-  if ((st = check_fft(p, cufftSetStream(p->r2c2, s), "set stream"))) return st;
-  if ((st = check_fft(p, cufftExecR2C(p->r2c2, p->rho, p->spec), "exec r2c x2"))) return st;
-  prof_end(p, t, s);
-  t = prof_begin(p, B + 3, s);
-  if ((st = launch_influence(p, s, p->spec, 2, p->epart))) return st;
-  prof_end(p, t, s);
-  t = prof_begin(p, B + 4, s);
-  if ((st = check_fft(p, cufftSetStream(p->c2r2, s), "set stream"))) return st;
-  if ((st = check_fft(p, cufftExecC2R(p->c2r2, p->spec, p->phi), "exec c2r x2"))) return st;
-  prof_end(p, t, s);
-  t = prof_begin(p, B + 5, s);
-  if ((st = launch_gather(p, s, n, p->phi, p->phi + p->M, true, in, gE, p->mesh_out))) return st;
-  prof_end(p, t, s);
-  if (pair && p->opts.overlap_pair && (st = join_side(p, s))) return st;
-  t = prof_begin(p, B + 7, s);
-  if ((st = launch_combine_backward(p, s, in, gE, o_pos, o_q, o_mu))) return st;
-  prof_end(p, t, s);
+  if ((st = run_backward(p, s, in, gE, o_pos, o_q, o_mu))) return st;
+  return sg.finish();
+}
+
+static int check_batch(pme_plan_t p, const float* pos, const float* q) {
+  if (!p) return PME_ERR_ARG;
+  if (!p->batch) return set_error(p, PME_ERR_ARG, "single-frame plan: use pme_forward / pme_backward");
+  if (p->frame_offsets[p->nframes] > 0 && (!pos || !q)) return set_error(p, PME_ERR_ARG, "pos or q is NULL");
+  return set_device(p);
+}
+
+int pme_batch_forward(pme_plan_t p, void* stream, const float* pos, const float* q, const float* mu,
+                      double* energy, float* force, float* phi, float* field, float* field_grad) {
+  int st = check_batch(p, pos, q);
+  if (st) return st;
+  const int n = p->frame_offsets[p->nframes];
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Staging sg(p, s, n);
+  IonInputs in{};
+  in.pos = sg.in(pos, 3, kPos);
+  in.q = sg.in(q, 1, kQ);
+  in.mu = sg.in(mu, 3, kMu);
+  in.n = n;
+  double* e_out = sg.out_d(energy, p->nframes, 0);
+  float* f_out = sg.out(force, 3, kOF);
+  float* p_out = sg.out(phi, 1, kOPhi);
+  float* fl_out = sg.out(field, 3, kOField);
+  float* fg_out = sg.out(field_grad, 6, kOFG);
+  if (sg.status) return sg.status;
+  if ((st = run_forward(p, s, in, e_out, f_out, p_out, fl_out, fg_out))) return st;
+  return sg.finish();
+}
+
+int pme_batch_backward(pme_plan_t p, void* stream, const float* pos, const float* q, const float* mu,
+                       const double* g_energy, const float* g_force, const float* g_phi,
+                       const float* g_field, float* grad_pos, float* grad_q, float* grad_mu) {
+  int st = check_batch(p, pos, q);
+  if (st) return st;
+  const int n = p->frame_offsets[p->nframes];
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Staging sg(p, s, n);
+  IonInputs in{};
+  in.pos = sg.in(pos, 3, kPos);
+  in.q = sg.in(q, 1, kQ);
+  in.mu = sg.in(mu, 3, kMu);
+  in.gforce = sg.in(g_force, 3, kGF);
+  in.gphi = sg.in(g_phi, 1, kGPhi);
+  in.gfield = sg.in(g_field, 3, kGField);
+  in.n = n;
+  const double* gE = sg.in_d(g_energy, p->nframes, 1);
+  float* o_pos = sg.out(grad_pos, 3, kOGPos);
+  float* o_q = sg.out(grad_q, 1, kOGQ);
+  float* o_mu = sg.out(grad_mu, 3, kOGMu);
+  if (sg.status) return sg.status;
+  if ((st = run_backward(p, s, in, gE, o_pos, o_q, o_mu))) return st;
   return sg.finish();
 }
 
@@ -737,7 +1054,7 @@ int pme_spread(pme_plan_t p, void* stream, int n, const float* pos, const float*
   in.mu = mu;
   in.n = n;
   if ((st = launch_sort(p, s, in, false, true, false))) return st;
-  return launch_spread(p, s, n, false, rho, nullptr);
+  return launch_spread(p, s, false, rho);   // frame 0's rho sits at offset 0
 }
 
 int pme_solve(pme_plan_t p, void* stream, const float* rho, float* phi_mesh, double* e_recip) {
@@ -748,16 +1065,16 @@ int pme_solve(pme_plan_t p, void* stream, const float* rho, float* phi_mesh, dou
       !is_device_pointer(e_recip))
     return set_error(p, PME_ERR_ARG, "pme_solve takes device pointers");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if ((st = check_cuda(p, cudaMemcpyAsync(p->rho, rho, sizeof(float) * p->M, cudaMemcpyDeviceToDevice, s), "copy rho")))
+  const FFTGroup& G = p->fgroups[0];
+  if ((st = check_cuda(p, cudaMemcpyAsync(p->rho, rho, sizeof(float) * p->M, cudaMemcpyDeviceToDevice, s),
+                       "copy rho")))
     return st;
-  if ((st = check_fft(p, cufftSetStream(p->r2c1, s), "set stream"))) return st;
-  if ((st = check_fft(p, cufftExecR2C(p->r2c1, p->rho, p->spec), "exec r2c"))) return st;
-  if ((st = launch_influence(p, s, p->spec, 1, p->epart))) return st;
-  if ((st = check_fft(p, cufftSetStream(p->c2r1, s), "set stream"))) return st;
-  if ((st = check_fft(p, cufftExecC2R(p->c2r1, p->spec, phi_mesh), "exec c2r"))) return st;
-  if (e_recip)
-    return launch_energy_final(p, s, p->epart, p->nspec_blocks, 0, 0.5 / p->g.volume, 1.0, 0.0,
-                               nullptr, e_recip);
+  if ((st = check_fft(p, cufftSetStream(G.r2c, s), "set stream"))) return st;
+  if ((st = check_fft(p, cufftExecR2C(G.r2c, p->rho, p->spec), "exec r2c"))) return st;
+  if ((st = launch_influence(p, s, p->spec, false, p->epart))) return st;
+  if ((st = check_fft(p, cufftSetStream(G.c2r, s), "set stream"))) return st;
+  if ((st = check_fft(p, cufftExecC2R(G.c2r, p->spec, phi_mesh), "exec c2r"))) return st;
+  if (e_recip) return launch_energy_final(p, s, p->epart, 1, false, false, 1.0, 0, e_recip);
   return PME_OK;
 }
 
@@ -774,7 +1091,7 @@ int pme_gather(pme_plan_t p, void* stream, int n, const float* pos, const float*
   in.q = nullptr;
   in.n = n;
   if ((st = launch_sort(p, s, in, false, true, false))) return st;
-  return launch_gather(p, s, n, phi_mesh, nullptr, false, in, nullptr, out);
+  return launch_gather(p, s, n, phi_mesh, false, nullptr, out);
 }
 
 int pme_pair(pme_plan_t p, void* stream, int n, const float* pos, const float* q,
@@ -794,8 +1111,8 @@ int pme_pair(pme_plan_t p, void* stream, int n, const float* pos, const float* q
   if ((st = launch_sort(p, s, in, false, false, true))) return st;
   if ((st = launch_pair(p, s, n, false, in, nullptr, out))) return st;
   if (e_pair) {
-    if ((st = launch_pair_energy(p, s, n, in, out, p->epart))) return st;
-    return launch_energy_final(p, s, p->epart, 0, combine_blocks(n), 1.0, 1.0, 0.0, nullptr, e_pair);
+    if ((st = launch_pair_energy(p, s, n, in, out))) return st;
+    return launch_energy_final(p, s, p->epart, 0, true, false, 1.0, n, e_pair);
   }
   return PME_OK;
 }

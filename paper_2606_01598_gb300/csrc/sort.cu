@@ -1,11 +1,14 @@
 // Sorting ions into mesh bricks and pair cells.
 //
 // Every ion gets two keys in one pass: the brick holding its first stencil point m0
-// (Section 2.3.2, Eq. w3d) and the pair cell holding its position. A counting sort orders
-// them: k_bin counts (one integer atomic per ion and key, never per stencil point), k_scan
-// turns the counts into segment starts, k_scatter places ions in arrival order, and
-// k_rank_records re-ranks each segment by caller index, which makes the order -- and hence
-// every later sum -- deterministic, while writing the per-ion records both orders need.
+// (Section 2.3.2, Eq. w3d) and the pair cell holding its position, both offset by its
+// frame's first global key, so that one counting sort orders every frame of a batch and the
+// ions of a frame stay contiguous. k_bin counts (one integer atomic per ion and key, never
+// per stencil point), k_scan turns the counts into segment starts, k_scatter places ions in
+// arrival order, and k_rank_records re-ranks each segment by caller index, which makes the
+// order -- and hence every later sum -- deterministic, while writing the per-ion records both
+// orders need. k_frame_sums adds up the charges (and tangent charges) of each frame in a fixed
+// order for the background term.
 #include "kernels.h"
 
 namespace gbpme {
@@ -15,41 +18,54 @@ namespace {
 constexpr int kSortThreads = 256;
 constexpr int kRankMaxSegment = 2048;   // longer segments keep arrival order
 
+template <bool BATCH>
 __global__ void __launch_bounds__(kSortThreads)
-k_bin(Geometry g, IonInputs in, SortBuffers sb, int* flags, int tangent, int max_blocks) {
+k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int* flags) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double qv = 0.0, dqv = 0.0;
-  if (i < in.n) {
-    const float rx = in.pos[3 * i], ry = in.pos[3 * i + 1], rz = in.pos[3 * i + 2];
-    const float qi = in.q ? in.q[i] : 0.f;
-    bool ok = isfinite(rx) && isfinite(ry) && isfinite(rz) && isfinite(qi);
-    if (in.mu) ok = ok && isfinite(in.mu[3 * i]) && isfinite(in.mu[3 * i + 1]) &&
-                    isfinite(in.mu[3 * i + 2]);
-    if (!ok) atomicOr(flags, kFlagNonFinite);
-    double s[3];
-    frac_coords(g, rx, ry, rz, s);
-    int m0[3], c[3];
+  if (i >= in.n) return;
+  const int f = BATCH ? maps.ion_frame[i] : 0;
+  const FrameDesc& F = frame_at<BATCH>(one, maps, f);
+  const Geometry& g = F.g;
+  const float rx = in.pos[3 * i], ry = in.pos[3 * i + 1], rz = in.pos[3 * i + 2];
+  const float qi = in.q ? in.q[i] : 0.f;
+  bool ok = isfinite(rx) && isfinite(ry) && isfinite(rz) && isfinite(qi);
+  if (in.mu) ok = ok && isfinite(in.mu[3 * i]) && isfinite(in.mu[3 * i + 1]) && isfinite(in.mu[3 * i + 2]);
+  if (!ok) atomicOr(flags, kFlagNonFinite);
+  double s[3];
+  frac_coords(g, rx, ry, rz, s);
+  int m0[3], c[3];
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      float f;
-      stencil_origin(s[b], g.N[b], g.order, m0[b], f);
-      cell_origin(s[b], g.ncell[b], c[b], f);
-    }
-    const int kb = ((m0[0] / g.brick[0]) * g.nb[1] + m0[1] / g.brick[1]) * g.nb[2] +
-                   m0[2] / g.brick[2];
-    const int kc = (c[0] * g.ncell[1] + c[1]) * g.ncell[2] + c[2];
-    sb.key_b[i] = kb;
-    sb.key_c[i] = kc;
-    sb.slot_b[i] = atomicAdd(&sb.count_b[kb], 1);
-    sb.slot_c[i] = atomicAdd(&sb.count_c[kc], 1);
-    qv = ok ? double(qi) : 0.0;
-    if (tangent && in.gphi) dqv = double(in.gphi[i]);
+  for (int b = 0; b < 3; ++b) {
+    float fr;
+    stencil_origin(s[b], g.N[b], g.order, m0[b], fr);
+    cell_origin(s[b], g.ncell[b], c[b], fr);
   }
-  const double a = block_sum_d(qv);
-  const double b = block_sum_d(dqv);
+  const int kb = F.brick_off + ((m0[0] / g.brick[0]) * g.nb[1] + m0[1] / g.brick[1]) * g.nb[2] +
+                 m0[2] / g.brick[2];
+  const int kc = F.cell_off + (c[0] * g.ncell[1] + c[1]) * g.ncell[2] + c[2];
+  sb.key_b[i] = kb;
+  sb.key_c[i] = kc;
+  sb.slot_b[i] = atomicAdd(&sb.count_b[kb], 1);
+  sb.slot_c[i] = atomicAdd(&sb.count_c[kc], 1);
+}
+
+// Q and dQ of every frame, one block per frame, in a fixed order.
+template <bool BATCH>
+__global__ void __launch_bounds__(kSortThreads)
+k_frame_sums(FrameDesc one, FrameMaps maps, IonInputs in, int tangent, double* qsum) {
+  const FrameDesc& F = frame_at<BATCH>(one, maps, blockIdx.x);
+  double a = 0.0, b = 0.0;
+  for (int k = threadIdx.x; k < F.n; k += blockDim.x) {
+    const int i = F.ion_off + k;
+    const float qi = in.q ? in.q[i] : 0.f;
+    if (isfinite(qi)) a += double(qi);
+    if (tangent && in.gphi) b += double(in.gphi[i]);
+  }
+  a = block_sum_d(a);
+  b = block_sum_d(b);
   if (threadIdx.x == 0) {
-    sb.qpart[blockIdx.x] = a;
-    sb.qpart[max_blocks + blockIdx.x] = b;
+    qsum[2 * blockIdx.x] = a;
+    qsum[2 * blockIdx.x + 1] = b;
   }
 }
 
@@ -61,7 +77,6 @@ __device__ void block_exclusive_scan(const int* count, int* start, int n) {
   const int lo = min(n, threadIdx.x * chunk), hi = min(n, lo + chunk);
   int local = 0;
   for (int k = lo; k < hi; ++k) local += count[k];
-  // inclusive warp scan of the per-thread totals
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int v = local;
 #pragma unroll
@@ -89,26 +104,11 @@ __device__ void block_exclusive_scan(const int* count, int* start, int n) {
   if (threadIdx.x == T - 1) start[n] = run;
 }
 
-__global__ void __launch_bounds__(1024)
-k_scan(SortBuffers sb, int nbricks, int ncells, int nblocks, int max_blocks) {
-  if (blockIdx.x == 0) {
+__global__ void __launch_bounds__(1024) k_scan(SortBuffers sb, int nbricks, int ncells) {
+  if (blockIdx.x == 0)
     block_exclusive_scan(sb.count_b, sb.start_b, nbricks);
-  } else if (blockIdx.x == 1) {
+  else
     block_exclusive_scan(sb.count_c, sb.start_c, ncells);
-  } else {
-    // Q and dQ in a fixed order: thread t sums partials t, t + T, ...
-    double a = 0.0, b = 0.0;
-    for (int k = threadIdx.x; k < nblocks; k += blockDim.x) {
-      a += sb.qpart[k];
-      b += sb.qpart[max_blocks + k];
-    }
-    a = block_sum_d(a);
-    b = block_sum_d(b);
-    if (threadIdx.x == 0) {
-      sb.qsum[0] = a;
-      sb.qsum[1] = b;
-    }
-  }
 }
 
 __global__ void __launch_bounds__(kSortThreads)
@@ -127,9 +127,10 @@ __device__ __forceinline__ int stable_rank(const int* perm, int seg_lo, int seg_
   return seg_lo + r;
 }
 
+template <bool BATCH>
 __global__ void __launch_bounds__(kSortThreads)
-k_rank_records(Geometry g, IonInputs in, SortBuffers sb, MeshRecords mr, PairRecords pr,
-               int tangent, int need_mesh, int need_pair) {
+k_rank_records(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, MeshRecords mr,
+               PairRecords pr, int tangent, int need_mesh, int need_pair) {
   const int n = in.n;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   const bool mesh_side = t < n;
@@ -146,6 +147,9 @@ k_rank_records(Geometry g, IonInputs in, SortBuffers sb, MeshRecords mr, PairRec
     const int k = sb.key_c[i];
     dest = stable_rank(sb.perm_c, sb.start_c[k], sb.start_c[k + 1], i, t);
   }
+  const int f = BATCH ? maps.ion_frame[i] : 0;
+  const FrameDesc& F = frame_at<BATCH>(one, maps, f);
+  const Geometry& g = F.g;
   const float rx = in.pos[3 * i], ry = in.pos[3 * i + 1], rz = in.pos[3 * i + 2];
   float qi = in.q ? in.q[i] : 0.f;
   float mu[3] = {0.f, 0.f, 0.f};
@@ -178,9 +182,9 @@ k_rank_records(Geometry g, IonInputs in, SortBuffers sb, MeshRecords mr, PairRec
   const float dp[3] = {dmu[0] + qi * dr[0], dmu[1] + qi * dr[1], dmu[2] + qi * dr[2]};
   if (mesh_side) {
     int m0[3];
-    float f[3];
+    float fr[3];
 #pragma unroll
-    for (int b = 0; b < 3; ++b) stencil_origin(s[b], g.N[b], g.order, m0[b], f[b]);
+    for (int b = 0; b < 3; ++b) stencil_origin(s[b], g.N[b], g.order, m0[b], fr[b]);
     float pm[3], pd[3], pt[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
@@ -189,7 +193,7 @@ k_rank_records(Geometry g, IonInputs in, SortBuffers sb, MeshRecords mr, PairRec
       pt[b] = dr[0] * g.D[0 * 3 + b] + dr[1] * g.D[1 * 3 + b] + dr[2] * g.D[2 * 3 + b];
     }
     mr.idx[dest] = make_int4(m0[0], m0[1], m0[2], i);
-    mr.fq[dest] = make_float4(f[0], f[1], f[2], qi);
+    mr.fq[dest] = make_float4(fr[0], fr[1], fr[2], qi);
     mr.dm[dest] = make_float4(pm[0], pm[1], pm[2], 0.f);
     if (tangent) {
       mr.tq[dest] = make_float4(dq, pd[0], pd[1], pd[2]);
@@ -197,12 +201,12 @@ k_rank_records(Geometry g, IonInputs in, SortBuffers sb, MeshRecords mr, PairRec
     }
   } else {
     int c[3];
-    float f[3];
+    float fr[3];
 #pragma unroll
-    for (int b = 0; b < 3; ++b) cell_origin(s[b], g.ncell[b], c[b], f[b]);
+    for (int b = 0; b < 3; ++b) cell_origin(s[b], g.ncell[b], c[b], fr[b]);
     pr.idx[dest] = make_int4(c[0], c[1], c[2], i);
     pr.cz[dest] = c[2];
-    pr.fq[dest] = make_float4(f[0], f[1], f[2], qi);
+    pr.fq[dest] = make_float4(fr[0], fr[1], fr[2], qi);
     pr.mu[dest] = make_float4(mu[0], mu[1], mu[2], 0.f);
     if (tangent) {
       pr.tq[dest] = make_float4(dq, dp[0], dp[1], dp[2]);
@@ -211,25 +215,28 @@ k_rank_records(Geometry g, IonInputs in, SortBuffers sb, MeshRecords mr, PairRec
   }
 }
 
-}  // namespace
-
-int launch_sort(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent, bool need_mesh,
-                bool need_pair) {
+template <bool BATCH>
+int launch_sort_t(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent, bool need_mesh,
+                  bool need_pair) {
   const int n = in.n;
   const int nblk = (n + kSortThreads - 1) / kSortThreads;
-  int st = check_cuda(p, cudaMemsetAsync(p->sb.count_b, 0, sizeof(int) * (p->nbricks + 1), s),
+  FrameDesc one = p->frames_h[0];
+  if (!BATCH) one.n = n;
+  int st = check_cuda(p, cudaMemsetAsync(p->sb.count_b, 0, sizeof(int) * (p->total_bricks + 1), s),
                       "memset brick counts");
   if (st) return st;
-  st = check_cuda(p, cudaMemsetAsync(p->sb.count_c, 0, sizeof(int) * (p->ncells + 1), s),
+  st = check_cuda(p, cudaMemsetAsync(p->sb.count_c, 0, sizeof(int) * (p->total_cells + 1), s),
                   "memset cell counts");
   if (st) return st;
   if (nblk > 0) {
-    k_bin<<<nblk, kSortThreads, 0, s>>>(p->g, in, p->sb, p->flags, tangent ? 1 : 0,
-                                        p->max_blocks);
+    k_bin<BATCH><<<nblk, kSortThreads, 0, s>>>(one, p->maps, in, p->sb, p->flags);
     count_launch();
     if ((st = check_launch(p, "k_bin"))) return st;
   }
-  k_scan<<<3, 1024, 0, s>>>(p->sb, p->nbricks, p->ncells, nblk, p->max_blocks);
+  k_frame_sums<BATCH><<<p->nframes, kSortThreads, 0, s>>>(one, p->maps, in, tangent ? 1 : 0, p->sb.qsum);
+  count_launch();
+  if ((st = check_launch(p, "k_frame_sums"))) return st;
+  k_scan<<<2, 1024, 0, s>>>(p->sb, p->total_bricks, p->total_cells);
   count_launch();
   if ((st = check_launch(p, "k_scan"))) return st;
   if (nblk > 0) {
@@ -237,13 +244,21 @@ int launch_sort(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent,
     count_launch();
     if ((st = check_launch(p, "k_scatter"))) return st;
     const int nblk2 = (2 * n + kSortThreads - 1) / kSortThreads;
-    k_rank_records<<<nblk2, kSortThreads, 0, s>>>(p->g, in, p->sb, p->mr, p->pr,
-                                                  tangent ? 1 : 0, need_mesh ? 1 : 0,
-                                                  need_pair ? 1 : 0);
+    k_rank_records<BATCH><<<nblk2, kSortThreads, 0, s>>>(one, p->maps, in, p->sb, p->mr, p->pr,
+                                                         tangent ? 1 : 0, need_mesh ? 1 : 0,
+                                                         need_pair ? 1 : 0);
     count_launch();
     if ((st = check_launch(p, "k_rank_records"))) return st;
   }
   return PME_OK;
+}
+
+}  // namespace
+
+int launch_sort(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent, bool need_mesh,
+                bool need_pair) {
+  return p->batch ? launch_sort_t<true>(p, s, in, tangent, need_mesh, need_pair)
+                  : launch_sort_t<false>(p, s, in, tangent, need_mesh, need_pair);
 }
 
 }  // namespace gbpme

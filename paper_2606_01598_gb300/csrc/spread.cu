@@ -1,7 +1,8 @@
 // Spread of charges and dipoles onto the mesh (Section 2.3.2, Eq. charge_dipole_assign).
 //
-// Owner-computes design: one CTA owns one brick of BX x BY x BZ mesh points and is the only
-// writer of those points, so the mesh needs no zeroing and no global atomics. The CTA walks
+// Owner-computes design: one CTA owns one brick of BX x BY x BZ mesh points of one frame and
+// is the only writer of those points, so the mesh needs no zeroing and no global atomics.
+// One launch covers every brick of every frame of one spline order. The CTA walks
 // the ions of the few bricks whose ions' stencils can reach it (ions are sorted by the brick
 // of their first stencil point), keeps those whose p^3 stencil really overlaps it (an
 // order-preserving compaction), stages their 1D spline weights in shared memory, and then
@@ -24,16 +25,16 @@ constexpr int NT = BX * BY;           // one thread per owned column
 constexpr int kMaxCand = kMaxCandPerDim * kMaxCandPerDim * kMaxCandPerDim;
 
 struct SpreadArgs {
-  Geometry g;
+  FrameDesc one;
+  FrameMaps maps;
+  int key_lo;           // first global brick of this launch
   MeshRecords mr;
   const int* start_b;
-  const int* cand;      // [3][max_nb][1 + kMaxCandPerDim]
-  int max_nb;
-  float* rho;
-  float* drho;
+  const int* cand;      // base of the candidate tables
+  float* mesh;          // base of the meshes: rho at mesh_off, d rho at tmesh_off
 };
 
-template <int P, bool TAN>
+template <int P, bool TAN, bool BATCH>
 __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
   constexpr int DW = TAN ? 3 : 2;                 // weight derivative orders kept
   constexpr int CAP = TAN ? NT : 2 * NT;          // staged ions per batch
@@ -51,9 +52,11 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
   __shared__ int warp_cnt[NT / 32];
   __shared__ int ncand_s;
 
-  const Geometry& g = a.g;
+  const int gkey = a.key_lo + blockIdx.x;
+  const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, BATCH ? a.maps.brick_frame[gkey] : 0);
+  const Geometry& g = F.g;
   const int tid = threadIdx.x;
-  const int bkey = blockIdx.x;
+  const int bkey = gkey - F.brick_off;
   const int bz = bkey % g.nb[2];
   const int by = (bkey / g.nb[2]) % g.nb[1];
   const int bx = bkey / (g.nb[2] * g.nb[1]);
@@ -66,14 +69,15 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
   }
   // candidate source bricks: product of the per-axis lists, in a fixed order
   if (tid == 0) {
-    const int* cx = a.cand + (0 * a.max_nb + bx) * (1 + kMaxCandPerDim);
-    const int* cy = a.cand + (1 * a.max_nb + by) * (1 + kMaxCandPerDim);
-    const int* cz = a.cand + (2 * a.max_nb + bz) * (1 + kMaxCandPerDim);
+    const int* ct = a.cand + F.cand_off;
+    const int* cx = ct + (0 * F.max_nb + bx) * (1 + kMaxCandPerDim);
+    const int* cy = ct + (1 * F.max_nb + by) * (1 + kMaxCandPerDim);
+    const int* cz = ct + (2 * F.max_nb + bz) * (1 + kMaxCandPerDim);
     int k = 0, cum = 0;
     for (int ix = 0; ix < cx[0]; ++ix)
       for (int iy = 0; iy < cy[0]; ++iy)
         for (int iz = 0; iz < cz[0]; ++iz) {
-          const int key = (cx[1 + ix] * g.nb[1] + cy[1 + iy]) * g.nb[2] + cz[1 + iz];
+          const int key = F.brick_off + (cx[1 + ix] * g.nb[1] + cy[1 + iy]) * g.nb[2] + cz[1 + iz];
           const int lo = a.start_b[key], hi = a.start_b[key + 1];
           cand_lo[k] = lo;
           cand_cum[k] = cum;
@@ -221,40 +225,48 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
   __syncthreads();
   // ---- flush: every owned mesh point written exactly once, z fastest ----------------
   const int Ny = g.N[1], Nz = g.N[2];
+  float* rho = a.mesh + F.mesh_off;
+  float* drho = a.mesh + F.tmesh_off;
   for (int e = tid; e < NT * BZ; e += NT) {
     const int Z = e % BZ, col = e / BZ;
     const int x = col / BY, y = col % BY;
     if (x < ex && y < ey && Z < ez) {
       const size_t off = (size_t(b0x + x) * Ny + (b0y + y)) * Nz + (b0z + Z);
-      a.rho[off] = tile[Z][col];
-      if (TAN) a.drho[off] = dtile[Z][col];
+      rho[off] = tile[Z][col];
+      if (TAN) drho[off] = dtile[Z][col];
     }
   }
 }
 
-template <bool TAN>
-int launch_t(pme_plan_t p, cudaStream_t s, float* rho, float* drho) {
+template <bool TAN, bool BATCH>
+int launch_t(pme_plan_t p, cudaStream_t s, float* mesh) {
   SpreadArgs a;
-  a.g = p->g;
+  a.one = p->frames_h[0];
+  a.maps = p->maps;
   a.mr = p->mr;
   a.start_b = p->sb.start_b;
   a.cand = p->cand;
-  a.max_nb = p->max_nb;
-  a.rho = rho;
-  a.drho = drho;
-  const int grid = p->nbricks;
-  switch (p->g.order) {
-    case 1: k_spread<1, TAN><<<grid, NT, 0, s>>>(a); break;
-    case 2: k_spread<2, TAN><<<grid, NT, 0, s>>>(a); break;
-    case 3: k_spread<3, TAN><<<grid, NT, 0, s>>>(a); break;
-    case 4: k_spread<4, TAN><<<grid, NT, 0, s>>>(a); break;
-    case 5: k_spread<5, TAN><<<grid, NT, 0, s>>>(a); break;
-    case 6: k_spread<6, TAN><<<grid, NT, 0, s>>>(a); break;
-    case 7: k_spread<7, TAN><<<grid, NT, 0, s>>>(a); break;
-    default: return set_error(p, PME_ERR_ARG, "spline order out of range");
+  a.mesh = mesh;
+  for (int gi = 0; gi < p->nogroups; ++gi) {
+    const OrderGroup& G = p->ogroups[gi];
+    const int grid = G.brick_hi - G.brick_lo;
+    if (grid <= 0) continue;
+    a.key_lo = G.brick_lo;
+    switch (G.order) {
+      case 1: k_spread<1, TAN, BATCH><<<grid, NT, 0, s>>>(a); break;
+      case 2: k_spread<2, TAN, BATCH><<<grid, NT, 0, s>>>(a); break;
+      case 3: k_spread<3, TAN, BATCH><<<grid, NT, 0, s>>>(a); break;
+      case 4: k_spread<4, TAN, BATCH><<<grid, NT, 0, s>>>(a); break;
+      case 5: k_spread<5, TAN, BATCH><<<grid, NT, 0, s>>>(a); break;
+      case 6: k_spread<6, TAN, BATCH><<<grid, NT, 0, s>>>(a); break;
+      case 7: k_spread<7, TAN, BATCH><<<grid, NT, 0, s>>>(a); break;
+      default: return set_error(p, PME_ERR_ARG, "spline order out of range");
+    }
+    count_launch();
+    int st = check_launch(p, "k_spread");
+    if (st) return st;
   }
-  count_launch();
-  return check_launch(p, "k_spread");
+  return PME_OK;
 }
 
 }  // namespace
@@ -265,10 +277,10 @@ void spread_brick_shape(int shape[3]) {
   shape[2] = BZ;
 }
 
-int launch_spread(pme_plan_t p, cudaStream_t s, int n, bool tangent, float* rho_out,
-                  float* drho_out) {
-  (void)n;
-  return tangent ? launch_t<true>(p, s, rho_out, drho_out) : launch_t<false>(p, s, rho_out, nullptr);
+int launch_spread(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh) {
+  if (p->batch)
+    return tangent ? launch_t<true, true>(p, s, mesh) : launch_t<false, true>(p, s, mesh);
+  return tangent ? launch_t<true, false>(p, s, mesh) : launch_t<false, false>(p, s, mesh);
 }
 
 }  // namespace gbpme

@@ -274,6 +274,103 @@ class Plan:
         return out, e
 
 
+class BatchPlan(Plan):
+    """Many frames of uneven sizes in one plan (pme_batch_create): every stage is one launch
+    over the whole batch. Frame f owns ions [offsets[f], offsets[f+1]) of the batch arrays."""
+
+    def __init__(self, boxes, meshes, orders, offsets, alpha: float, rcut: float, *,
+                 influence_power: float = 1.0, deconvolution: bool = True,
+                 coulomb_k: float = 1.0, include_pair: bool = True, include_self: bool = True,
+                 include_background: bool = True, overlap_pair: bool = True, device=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("gbpme needs a CUDA device; there is no CPU fallback")
+        self.lib = _abi.load()
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        if dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        torch.cuda.init()
+        opts = PMEOpts()
+        self.lib.pme_opts_default(ctypes.byref(opts))
+        opts.influence_power = float(influence_power)
+        opts.deconvolution = int(bool(deconvolution))
+        opts.coulomb_k = float(coulomb_k)
+        opts.include_pair = int(bool(include_pair))
+        opts.include_self = int(bool(include_self))
+        opts.include_background = int(bool(include_background))
+        opts.overlap_pair = int(bool(overlap_pair))
+        boxes = np.asarray(boxes, np.float64).reshape(-1, 9)
+        meshes = np.asarray(meshes, np.int32).reshape(-1, 3)
+        orders = np.asarray(orders, np.int32).reshape(-1)
+        offsets = np.asarray(offsets, np.int32).reshape(-1)
+        F = len(orders)
+        if not (len(boxes) == len(meshes) == F and len(offsets) == F + 1):
+            raise ValueError("boxes, meshes, orders need one entry per frame and offsets F + 1")
+        self.nframes = F
+        self.offsets = offsets.copy()
+        self.n = int(offsets[-1])
+        self.coulomb_k = float(coulomb_k)
+        b = (ctypes.c_double * (9 * F))(*boxes.reshape(-1))
+        m = (ctypes.c_int * (3 * F))(*meshes.reshape(-1).tolist())
+        o = (ctypes.c_int * F)(*orders.tolist())
+        off = (ctypes.c_int * (F + 1))(*offsets.tolist())
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self.lib.pme_batch_create(ctypes.byref(h), F, off, b, m, o, float(alpha), float(rcut),
+                                           ctypes.byref(opts))
+        if st:
+            raise PMEError(st, "pme_batch_create")
+        self.handle = h
+
+    def forward(self, pos, q, mu=None, *, energy=True, force=True, phi=True, field=True,
+                field_grad=False):
+        dev = pos.device if isinstance(pos, torch.Tensor) else torch.device("cpu")
+        on_dev = dev.type == "cuda"
+        pos, q, mu = (_f32(t, dev) for t in (pos, q, mu))
+        n = self.n
+        alloc = dict(device=dev, pin_memory=True) if not on_dev else dict(device=dev)
+        out = {}
+        if energy:
+            out["energy"] = torch.empty(self.nframes, dtype=torch.float64, **alloc)
+        if force:
+            out["force"] = torch.empty((n, 3), dtype=torch.float32, **alloc)
+        if phi:
+            out["phi"] = torch.empty(n, dtype=torch.float32, **alloc)
+        if field:
+            out["field"] = torch.empty((n, 3), dtype=torch.float32, **alloc)
+        if field_grad:
+            out["field_grad"] = torch.empty((n, 6), dtype=torch.float32, **alloc)
+        with torch.cuda.device(self.device):
+            st = self.lib.pme_batch_forward(self.handle, _stream_handle(self.device), _ptr(pos), _ptr(q),
+                                            _ptr(mu), _ptr(out.get("energy")), _ptr(out.get("force")),
+                                            _ptr(out.get("phi")), _ptr(out.get("field")),
+                                            _ptr(out.get("field_grad")))
+            self._check(st, "pme_batch_forward")
+            if not on_dev:
+                torch.cuda.current_stream(self.device).synchronize()
+        return out
+
+    def backward(self, pos, q, mu=None, g_energy=None, g_force=None, g_phi=None, g_field=None):
+        dev = pos.device if isinstance(pos, torch.Tensor) else torch.device("cpu")
+        on_dev = dev.type == "cuda"
+        pos, q, mu, g_force, g_phi, g_field = (_f32(t, dev) for t in (pos, q, mu, g_force, g_phi, g_field))
+        if g_energy is not None:
+            g_energy = torch.as_tensor(g_energy, dtype=torch.float64).reshape(self.nframes).to(dev).contiguous()
+        n = self.n
+        alloc = dict(device=dev, pin_memory=True) if not on_dev else dict(device=dev)
+        gp = torch.empty((n, 3), dtype=torch.float32, **alloc)
+        gq = torch.empty(n, dtype=torch.float32, **alloc)
+        gm = torch.empty((n, 3), dtype=torch.float32, **alloc)
+        with torch.cuda.device(self.device):
+            st = self.lib.pme_batch_backward(self.handle, _stream_handle(self.device), _ptr(pos), _ptr(q),
+                                             _ptr(mu), _ptr(g_energy), _ptr(g_force), _ptr(g_phi),
+                                             _ptr(g_field), _ptr(gp), _ptr(gq), _ptr(gm))
+            self._check(st, "pme_batch_backward")
+            if not on_dev:
+                torch.cuda.current_stream(self.device).synchronize()
+        return gp, gq, gm
+
+
 # ------------------------------------------------------------------------------------------
 # autograd
 # ------------------------------------------------------------------------------------------

@@ -78,9 +78,16 @@ def test_mesh_and_ksum_agree(gb):
                  max_ions=1024).forward(*t)
     o2 = O2.PMEOracle(fr.box, (40, 40, 40), 7, 0.30, 9.0).evaluate(pos, q, mu, field_grad=False)
     o1 = O1.ewald(pos, q, mu, fr.box, 0.30, rcut=9.0, kmax=3.5)
+    # float32 rounding scales with the parts of the Ewald split, not with their near-cancelling
+    # total (here |E| ~ 38 against |E_self| ~ 110), so the relative bar is taken on their sum
+    E = sum(abs(o2[k]) for k in ("e_recip", "e_pair", "e_self", "e_bg"))
+    err_mesh = mesh["energy"].item() - o2["energy"]
+    err_ks = ks["energy"].item() - o1["energy"]
+    assert abs(err_mesh) < TOL_E * E, ("mesh vs plain PME", err_mesh / E)
+    assert abs(err_ks) < TOL_E * E, ("k-sum vs explicit Ewald", err_ks / E)
     gap_gpu = mesh["energy"].item() - ks["energy"].item()
     gap_ref = o2["energy"] - o1["energy"]
-    assert abs(gap_gpu - gap_ref) < TOL_E * abs(o1["energy"])
+    assert abs(gap_gpu - gap_ref) < 2 * TOL_E * E
     fg = relrmse(mesh["force"].cpu().numpy(), ks["force"].cpu().numpy())
     fr_ = relrmse(o2["force"], o1["force"])
     assert abs(fg - fr_) < 0.1 * fr_ + TOL_F
