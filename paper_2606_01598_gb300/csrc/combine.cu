@@ -49,7 +49,7 @@ struct CombineArgs {
 
 // pi / (V alpha^2) of the ion's frame, or 0 without the background term
 __device__ __forceinline__ float bg_factor(const CombineArgs& a, const FrameDesc& F) {
-  return a.with_bg ? float(kPi / (F.g.volume * double(a.alpha) * double(a.alpha))) : 0.f;
+  return a.with_bg ? F.g.bg_fac : 0.f;
 }
 
 template <bool BATCH>

@@ -17,6 +17,9 @@ constexpr int kMaxOrder = 7;
 constexpr int kMaxCandPerDim = 4;   // bricks along one axis that can feed one brick's stencils
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kProfCap = 4096;
+// Ions per item of the per-frame float64 sums (charges, energies): a frame of n ions is split
+// into max(1, ceil(n / kRedItem)) items, one block each.
+constexpr int kRedItem = 2048;
 
 // ----------------------------------------------------------------------------------------
 // launch bookkeeping
@@ -39,6 +42,9 @@ struct Geometry {
   float alpha;
   float rcut2;
   double volume;
+  float bk[9];        // reciprocal basis, rows b_r = 2 pi C^{-T}: bk[r*3+c] = 2 pi cinv[c*3+r]
+  float inv_volume;   // 1 / V
+  float bg_fac;       // pi / (V alpha^2), the background potential per unit net charge
 };
 
 // Per-ion records in brick (mesh) order.
@@ -71,9 +77,33 @@ struct SortBuffers {
   int* start_c;   // [total cells + 1]
   int* perm_b;    // [max_ions] unsorted placement (sorted slot -> caller index)
   int* perm_c;
-  double* qpart;  // unused (kept for the fixed scratch layout of the allocation-free spread)
+  double* qpart;  // [2 * items] Q and dQ of each reduction item
+  int* qcount;    // [frames] items finished (reset by the last one); null: no charge sums wanted
   double* qsum;   // [2 * frames] Q and dQ of each frame
 };
+
+// Division by an invariant divisor d >= 1 with a multiply-high and a shift (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", PLDI 1994): with
+// l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1, floor(x / d) = (umulhi(m, x) + x) >> l
+// for 0 <= x < 2^31 (the sum cannot overflow there).
+struct FastDiv {
+  unsigned m;
+  int l;
+  int d;
+};
+
+inline FastDiv make_fastdiv(int d) {
+  FastDiv f;
+  f.d = d;
+  f.l = 0;
+  while ((1ll << f.l) < d) ++f.l;
+  f.m = unsigned(((1ull << 32) * ((1ull << f.l) - unsigned(d))) / unsigned(d) + 1ull);
+  return f;
+}
+
+__device__ __forceinline__ int fdiv(int x, const FastDiv& f) {
+  return int((__umulhi(f.m, unsigned(x)) + unsigned(x)) >> f.l);
+}
 
 // One frame of a plan: its geometry and where its data lives in the plan's arrays. A single-
 // frame plan passes its one descriptor as a kernel argument; a batched plan keeps a table of
@@ -91,6 +121,8 @@ struct FrameDesc {
   int cand_off, max_nb;     // candidate-brick table [3][max_nb][1 + kMaxCandPerDim]
   int dconv_off;            // deconvolution tables: x at dconv_off, y at +Nx, z at +Nx+Ny
   int infl_blk_off, infl_nblk;  // influence / energy blocks of this frame
+  int item_off, nitems;     // items of the per-frame float64 sums
+  FastDiv div_zh, div_y;    // division by Nz/2 + 1 and by Ny (half-spectrum index -> n)
 };
 
 struct FrameMaps {
@@ -99,6 +131,7 @@ struct FrameMaps {
   const int* sorted_frame;  // sorted position -> frame
   const int* brick_frame;   // global brick key -> frame
   const int* blk_frame;     // influence block -> frame
+  const int* item_frame;    // reduction item -> frame
 };
 
 template <bool BATCH>
@@ -140,7 +173,7 @@ struct pme_plan_s {
   int nfgroups = 0;
   void* fft_work = nullptr;
   double* e_ion = nullptr;                // [max_ions] per-ion energy contributions
-  int total_bricks = 0, total_cells = 0, total_blocks = 0;
+  int total_bricks = 0, total_cells = 0, total_blocks = 0, total_items = 0;
   long long total_mesh = 0, total_spec = 0;
   int* frame_offsets = nullptr;           // host copy [nframes + 1]
   double box[9];             // box of frame 0
@@ -161,6 +194,8 @@ struct pme_plan_s {
   float* mesh_out;           // [max_ions][10] per-ion mesh results (caller order)
   float* pair_out;           // [max_ions][10] per-ion pair results
   double* epart;             // reciprocal energy partials, one per influence (or k) block
+  double* eitem;             // [items] per-ion energy partials
+  int* ecount;               // [frames] energy items finished (reset by the last one)
   int* flags;                // device error flags
   // host-pointer staging
   float* stage_f;            // device staging for host arrays, 34 floats per ion
@@ -306,6 +341,30 @@ __device__ __forceinline__ double block_sum_d(double v) {
     r = warp_sum_d(r);
   }
   return r;
+}
+
+// Two-level deterministic sum, second level: after thread 0 has stored its block's partial,
+// every thread calls this; it returns true in the block that finished last among the nitems
+// blocks counting on *count (an atomic ticket). That block alone then adds all partials in
+// item order (reading them with __ldcg) and resets *count, so the result does not depend on
+// which block came last.
+__device__ __forceinline__ bool last_item_done(int* count, int nitems) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(count, 1) == nitems - 1;
+  }
+  __syncthreads();
+  const bool last = s_last != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+// Ion range [lo, hi) of reduction item `item` of frame F.
+__device__ __forceinline__ void item_range(const FrameDesc& F, int item, int& lo, int& hi) {
+  lo = F.ion_off + (item - F.item_off) * kRedItem;
+  hi = min(F.ion_off + F.n, lo + kRedItem);
 }
 
 // Device error flag bits.

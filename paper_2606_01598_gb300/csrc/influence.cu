@@ -6,10 +6,12 @@
 // the separable deconvolution C(n) = prod_a 1/sinc^(2 p gamma)(n_a / N_a) (per-axis tables
 // built on the host). The energy (1/2V) sum_{n != 0} G C |rho_hat|^2 over the full spectrum
 // is accumulated on the half spectrum with weight 2 for the planes that stand for their
-// mirror images (0 < n_z < Nz/2) and 1 otherwise; per-thread float sums go to float64 block
-// partials. Each spectrum (and, in the backward pass, the tangent spectrum) is then multiplied
-// in place by G C / V, so the C2R transform that follows yields Phi with
-// E_recip = 1/2 sum_m rho(m) Phi(m). A batched plan gives every frame its own run of blocks.
+// mirror images (0 < n_z < Nz/2) and 1 otherwise; compensated (Neumaier) float sums per
+// thread and per warp go to float64 block partials. Each spectrum (and, in the backward pass,
+// the tangent spectrum) is then multiplied in place by G C / V, so the C2R transform that
+// follows yields Phi with E_recip = 1/2 sum_m rho(m) Phi(m). A batched plan gives every frame
+// its own run of blocks. All per-element arithmetic is float32 (the float64 rate of the part
+// is a small fraction of its float32 rate), with the constants precomputed on the host.
 #include "kernels.h"
 
 namespace gbpme {
@@ -17,7 +19,14 @@ namespace gbpme {
 namespace {
 
 constexpr int kInflThreads = 256;
-constexpr int kInflMaxBlocks = 152 * 8;
+constexpr int kInflMaxBlocks = 152 * 4;
+
+// Neumaier-compensated float accumulation (sum s, running correction c)
+__device__ __forceinline__ void comp_add(float& s, float& c, float v) {
+  const float t = s + v;
+  c += fabsf(s) >= fabsf(v) ? (s - t) + v : (v - t) + s;
+  s = t;
+}
 
 template <bool BATCH>
 __global__ void __launch_bounds__(kInflThreads)
@@ -27,72 +36,95 @@ k_influence(FrameDesc one, FrameMaps maps, float2* spec, int tangent, const floa
   const Geometry& g = F.g;
   const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2];
   const int Nzh = N2 / 2 + 1;
-  const long long Mh = (long long)N0 * N1 * Nzh;
-  float b[9];   // rows b_x, b_y, b_z of 2 pi C^{-T}: b_r[c] = 2 pi cinv[c][r]
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) b[r * 3 + c] = float(2.0 * kPi * g.cinv[c * 3 + r]);
-  const float inv_volume = float(1.0 / g.volume);
+  const int Mh = N0 * N1 * Nzh;   // < 2^30 (checked when the plan is made)
   const float* cx = dconv + F.dconv_off;
   const float* cy = cx + N0;
   const float* cz = cy + N1;
+  const float four_pi = 12.566370614359172f;
   float2* sp = spec + F.spec_off;
   float2* tp = spec + F.tspec_off;
-  float e = 0.f;
-  const long long step = (long long)F.infl_nblk * blockDim.x;
-  for (long long idx = (long long)(blockIdx.x - F.infl_blk_off) * blockDim.x + threadIdx.x; idx < Mh;
-       idx += step) {
-    const int iz = int(idx % Nzh);
-    const long long r = idx / Nzh;
-    const int iy = int(r % N1);
-    const int ix = int(r / N1);
+  float e = 0.f, ec = 0.f;
+  const int step = F.infl_nblk * blockDim.x;
+  for (int idx = (blockIdx.x - F.infl_blk_off) * blockDim.x + threadIdx.x; idx < Mh; idx += step) {
+    const int r = fdiv(idx, F.div_zh);
+    const int iz = idx - r * Nzh;
+    const int ix = fdiv(r, F.div_y);
+    const int iy = r - ix * N1;
     const float nx = float(ix <= N0 / 2 ? ix : ix - N0);
     const float ny = float(iy <= N1 / 2 ? iy : iy - N1);
     const float nz = float(iz);
-    const float kx = nx * b[0] + ny * b[3] + nz * b[6];
-    const float ky = nx * b[1] + ny * b[4] + nz * b[7];
-    const float kz = nx * b[2] + ny * b[5] + nz * b[8];
+    const float kx = nx * g.bk[0] + ny * g.bk[3] + nz * g.bk[6];
+    const float ky = nx * g.bk[1] + ny * g.bk[4] + nz * g.bk[7];
+    const float kz = nx * g.bk[2] + ny * g.bk[5] + nz * g.bk[8];
     const float k2 = kx * kx + ky * ky + kz * kz;
     float gc = 0.f;
-    if (k2 > 0.f) gc = 4.f * 3.14159265358979f * expf(-k2 * inv4a2) / k2 * cx[ix] * cy[iy] * cz[iz];
+    if (k2 > 0.f) gc = four_pi * expf(-k2 * inv4a2) / k2 * cx[ix] * cy[iy] * cz[iz];
     const float2 v = sp[idx];
     const float w = (iz == 0 || (2 * iz == N2)) ? 1.f : 2.f;
-    e += w * gc * (v.x * v.x + v.y * v.y);
-    const float f = gc * inv_volume;
+    comp_add(e, ec, w * gc * (v.x * v.x + v.y * v.y));
+    const float f = gc * g.inv_volume;
     sp[idx] = make_float2(v.x * f, v.y * f);
     if (tangent) {
       const float2 u = tp[idx];
       tp[idx] = make_float2(u.x * f, u.y * f);
     }
   }
-  const double t = block_sum_d(double(e));
-  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  // warp sums of the compensated pairs in float, then float64 over the block's warps
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float e2 = __shfl_xor_sync(0xffffffffu, e, o);
+    const float c2 = __shfl_xor_sync(0xffffffffu, ec, o);
+    ec += c2;
+    comp_add(e, ec, e2);
+  }
+  __shared__ double wsum[kInflThreads / 32];
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = double(e) + double(ec);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kInflThreads / 32; ++w) t += wsum[w];
+    partials[blockIdx.x] = t;
+  }
 }
 
-// One block per frame: reciprocal partials, per-ion energies and background, times k.
+// Frame energies: one block per reduction item sums the item's per-ion energies; the last item
+// of each frame to finish adds the reciprocal partials, the item partials (both in a fixed
+// order) and the background term, times k.
+constexpr int kEnergyThreads = 256;
+
 template <bool BATCH>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(kEnergyThreads)
 k_energy_final(FrameDesc one, FrameMaps maps, const double* parts, int recip_kind,
                const double* e_ion, const double* qsum, int with_bg, double alpha, double scale,
-               double* out) {
-  const FrameDesc& F = frame_at<BATCH>(one, maps, blockIdx.x);
-  double a = 0.0, b = 0.0;
+               double* eitem, int* ecount, double* out) {
+  const int item = blockIdx.x;
+  const int f = BATCH ? maps.item_frame[item] : 0;
+  const FrameDesc& F = frame_at<BATCH>(one, maps, f);
+  int lo, hi;
+  item_range(F, item, lo, hi);
+  double b = 0.0;
+  if (e_ion)
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) b += e_ion[i];
+  b = block_sum_d(b);
+  if (threadIdx.x == 0) eitem[item] = b;
+  if (!last_item_done(ecount + f, F.nitems)) return;
+  double a = 0.0, e = 0.0;
   if (recip_kind)
     for (int k = threadIdx.x; k < F.infl_nblk; k += blockDim.x) a += parts[F.infl_blk_off + k];
-  if (e_ion)
-    for (int k = threadIdx.x; k < F.n; k += blockDim.x) b += e_ion[F.ion_off + k];
+  for (int k = threadIdx.x; k < F.nitems; k += blockDim.x) e += __ldcg(eitem + F.item_off + k);
   a = block_sum_d(a);
-  b = block_sum_d(b);
+  e = block_sum_d(e);
   if (threadIdx.x == 0) {
     const double V = F.g.volume;
     const double coef = recip_kind == 1 ? 0.5 / V : (recip_kind == 2 ? 4.0 * kPi / V : 0.0);
     double bg = 0.0;
     if (with_bg) {
-      const double Q = qsum[2 * blockIdx.x];
+      const double Q = qsum[2 * f];
       bg = -kPi * Q * Q / (2.0 * V * alpha * alpha);
     }
-    out[blockIdx.x] = scale * (coef * a + b + bg);
+    out[f] = scale * (coef * a + e + bg);
+    ecount[f] = 0;
   }
 }
 
@@ -121,14 +153,21 @@ int launch_influence(pme_plan_t p, cudaStream_t s, cufftComplex* spec, bool tang
 int launch_energy_final(pme_plan_t p, cudaStream_t s, const double* parts, int recip_kind,
                         bool with_ions, bool with_bg, double scale, int n_single, double* out) {
   FrameDesc one = p->frames_h[0];
-  if (!p->batch) one.n = n_single;
+  if (!p->batch) {
+    one.n = n_single;
+    one.item_off = 0;
+    one.nitems = n_single > kRedItem ? (n_single + kRedItem - 1) / kRedItem : 1;
+  }
   const double* e_ion = with_ions ? p->e_ion : nullptr;
+  const int items = p->batch ? p->total_items : one.nitems;
   if (p->batch)
-    k_energy_final<true><<<p->nframes, 1024, 0, s>>>(one, p->maps, parts, recip_kind, e_ion, p->sb.qsum,
-                                                     with_bg ? 1 : 0, p->alpha, scale, out);
+    k_energy_final<true><<<items, kEnergyThreads, 0, s>>>(one, p->maps, parts, recip_kind, e_ion, p->sb.qsum,
+                                                          with_bg ? 1 : 0, p->alpha, scale, p->eitem,
+                                                          p->ecount, out);
   else
-    k_energy_final<false><<<1, 1024, 0, s>>>(one, p->maps, parts, recip_kind, e_ion, p->sb.qsum,
-                                             with_bg ? 1 : 0, p->alpha, scale, out);
+    k_energy_final<false><<<items, kEnergyThreads, 0, s>>>(one, p->maps, parts, recip_kind, e_ion, p->sb.qsum,
+                                                           with_bg ? 1 : 0, p->alpha, scale, p->eitem,
+                                                           p->ecount, out);
   count_launch();
   return check_launch(p, "k_energy_final");
 }

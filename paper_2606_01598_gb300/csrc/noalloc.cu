@@ -189,6 +189,7 @@ extern "C" int pme_spread_noalloc(void* stream, const double box[9], const int m
   v.sb.count_c = reinterpret_cast<int*>(base + kOffCountC);
   v.sb.start_c = reinterpret_cast<int*>(base + kOffStartC);
   v.sb.qpart = reinterpret_cast<double*>(base + kOffQpart);
+  v.sb.qcount = nullptr;   // the spread needs no charge sums: the sort skips them
   v.sb.qsum = reinterpret_cast<double*>(base + kOffQsum);
   v.mr.idx = reinterpret_cast<int4*>(base + kOffIdx);
   v.mr.fq = reinterpret_cast<float4*>(base + kOffFq);

@@ -128,6 +128,10 @@ static bool frame_geometry(Geometry& g, const double* box, double rcut, bool pai
   g.volume = std::fabs(det);
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) g.D[a * 3 + b] = float(double(g.N[b]) * inv[a * 3 + b]);
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) g.bk[r * 3 + c] = float(2.0 * kPi * inv[c * 3 + r]);
+  g.inv_volume = float(1.0 / g.volume);
+  g.bg_fac = float(kPi / (g.volume * double(g.alpha) * double(g.alpha)));
   // pair cells at least rcut/2 wide (at least one per axis); a candidate cell lies at most
   // kimg = ceil(rcut / cell width) cells away along each axis. When an axis has fewer than
   // 2 kimg + 1 cells the offsets wrap onto the same cells again: each offset then stands for
@@ -256,7 +260,7 @@ static void free_plan(pme_plan_t p) {
                   p->mr.dm, p->mr.tq, p->mr.tt, p->pr.idx, p->pr.fq, p->pr.mu, p->pr.tq, p->pr.dr,
                   p->pr.cz, p->mesh_out, p->pair_out, p->e_ion, p->epart, p->flags, p->stage_f,
                   p->stage_d, p->ew_kn, p->ew_kv, p->ew_S, p->ew_fx, p->ew_qm, p->frames_d,
-                  p->map_buf, p->fft_work};
+                  p->map_buf, p->fft_work, p->sb.qpart, p->sb.qcount, p->eitem, p->ecount};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int g = 0; g < p->nfgroups; ++g) {
@@ -287,10 +291,14 @@ static int dalloc(pme_plan_t p, T** ptr, size_t count) {
                     "cudaMalloc");
 }
 
+// Count / start arrays of the sort: n + 1 entries padded to a multiple of 4 (the scan moves
+// them 16 bytes at a time).
+static size_t scan_entries(int n) { return (size_t(n) + 1 + 3) & ~size_t(3); }
+
 static int alloc_cells(pme_plan_t p) {
   int st;
-  if ((st = dalloc(p, &p->sb.count_c, size_t(p->total_cells) + 1))) return st;
-  if ((st = dalloc(p, &p->sb.start_c, size_t(p->total_cells) + 1))) return st;
+  if ((st = dalloc(p, &p->sb.count_c, scan_entries(p->total_cells)))) return st;
+  if ((st = dalloc(p, &p->sb.start_c, scan_entries(p->total_cells)))) return st;
   return PME_OK;
 }
 
@@ -375,7 +383,13 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
     D.nbricks = g.nb[0] * g.nb[1] * g.nb[2];
     D.ncells = ncells[f];
     D.max_nb = std::max(g.nb[0], std::max(g.nb[1], g.nb[2]));
+    if ((long long)g.N[0] * g.N[1] * (g.N[2] / 2 + 1) >= (1LL << 30))
+      return set_error(p, PME_ERR_UNSUPPORTED, "half spectrum of a frame above 2^30 points");
     D.infl_nblk = influence_blocks(g);
+    D.div_zh = make_fastdiv(g.N[2] / 2 + 1);
+    D.div_y = make_fastdiv(g.N[1]);
+    D.nitems = single ? std::max(1, (p->max_ions + kRedItem - 1) / kRedItem)
+                      : std::max(1, (in.n + kRedItem - 1) / kRedItem);
     p->frame_offsets[f] = in.ion_off;
   }
   p->frame_offsets[F] = single ? p->max_ions : fin[F - 1].ion_off + fin[F - 1].n;
@@ -393,7 +407,8 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
       if (ga.N[k] != gb.N[k]) return ga.N[k] < gb.N[k];
     return false;
   });
-  long long brick_off = 0, cell_off = 0, sorted_off = 0, cand_off = 0, dconv_off = 0, blk_off = 0;
+  long long brick_off = 0, cell_off = 0, sorted_off = 0, cand_off = 0, dconv_off = 0, blk_off = 0,
+            item_off = 0;
   for (int f : ord) {
     FrameDesc& D = p->frames_h[f];
     D.brick_off = int(brick_off);
@@ -402,6 +417,8 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
     D.cand_off = int(cand_off);
     D.dconv_off = int(dconv_off);
     D.infl_blk_off = int(blk_off);
+    D.item_off = int(item_off);
+    item_off += D.nitems;
     brick_off += D.nbricks;
     cell_off += D.ncells;
     sorted_off += single ? 0 : D.n;
@@ -413,6 +430,7 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
   p->total_bricks = int(brick_off);
   p->total_cells = int(cell_off);
   p->total_blocks = int(blk_off);
+  p->total_items = int(item_off);
   // spread / gather launch groups (one per spline order)
   p->nogroups = 0;
   for (int f : ord) {
@@ -491,9 +509,13 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
   A(&p->sb.slot_c, ni);
   A(&p->sb.perm_b, ni);
   A(&p->sb.perm_c, ni);
-  A(&p->sb.count_b, size_t(p->total_bricks) + 1);
-  A(&p->sb.start_b, size_t(p->total_bricks) + 1);
+  A(&p->sb.count_b, scan_entries(p->total_bricks));
+  A(&p->sb.start_b, scan_entries(p->total_bricks));
   A(&p->sb.qsum, size_t(2) * F);
+  A(&p->sb.qpart, size_t(2) * p->total_items);
+  A(&p->sb.qcount, size_t(F));
+  A(&p->eitem, size_t(p->total_items));
+  A(&p->ecount, size_t(F));
   A(&p->mr.idx, ni);
   A(&p->mr.fq, ni);
   A(&p->mr.dm, ni);
@@ -515,6 +537,8 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
   if (st == PME_OK) st = alloc_cells(p);
   if (st) return st;
   if ((st = check_cuda(p, cudaMemset(p->flags, 0, sizeof(int)), "memset"))) return st;
+  if ((st = check_cuda(p, cudaMemset(p->sb.qcount, 0, sizeof(int) * F), "memset"))) return st;
+  if ((st = check_cuda(p, cudaMemset(p->ecount, 0, sizeof(int) * F), "memset"))) return st;
   // candidate tables and deconvolution tables, frame by frame
   {
     std::vector<int> cand(size_t(cand_off), 0);
@@ -544,11 +568,12 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
   // batched plans: descriptor table and frame maps on the device
   if (!single) {
     const long long Ntot = p->frame_offsets[F];
-    std::vector<int> maps(size_t(2 * Ntot + p->total_bricks + p->total_blocks));
+    std::vector<int> maps(size_t(2 * Ntot + p->total_bricks + p->total_blocks + p->total_items));
     int* ion_frame = maps.data();
     int* sorted_frame = ion_frame + Ntot;
     int* brick_frame = sorted_frame + Ntot;
     int* blk_frame = brick_frame + p->total_bricks;
+    int* item_frame = blk_frame + p->total_blocks;
     for (int f = 0; f < F; ++f) {
       const FrameDesc& D = p->frames_h[f];
       for (int k = 0; k < D.n; ++k) {
@@ -557,6 +582,7 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
       }
       for (int k = 0; k < D.nbricks; ++k) brick_frame[D.brick_off + k] = f;
       for (int k = 0; k < D.infl_nblk; ++k) blk_frame[D.infl_blk_off + k] = f;
+      for (int k = 0; k < D.nitems; ++k) item_frame[D.item_off + k] = f;
     }
     if ((st = dalloc(p, &p->map_buf, maps.size()))) return st;
     if ((st = dalloc(p, &p->frames_d, size_t(F)))) return st;
@@ -571,6 +597,7 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
     p->maps.sorted_frame = p->map_buf + Ntot;
     p->maps.brick_frame = p->map_buf + 2 * Ntot;
     p->maps.blk_frame = p->map_buf + 2 * Ntot + p->total_bricks;
+    p->maps.item_frame = p->map_buf + 2 * Ntot + p->total_bricks + p->total_blocks;
   }
   // cuFFT: four plans per group sharing one work area
   size_t work = 0;

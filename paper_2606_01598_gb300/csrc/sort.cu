@@ -8,7 +8,10 @@
 // arrival order, and k_rank_records re-ranks each segment by caller index, which makes the
 // order -- and hence every later sum -- deterministic, while writing the per-ion records both
 // orders need. k_frame_sums adds up the charges (and tangent charges) of each frame in a fixed
-// order for the background term.
+// order for the background term (the allocation-free spread, which has no use for them,
+// skips it).
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace gbpme {
@@ -49,14 +52,18 @@ k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int* flags) {
   sb.slot_c[i] = atomicAdd(&sb.count_c[kc], 1);
 }
 
-// Q and dQ of every frame, one block per frame, in a fixed order.
+// Q and dQ of every frame in a fixed order: one block per reduction item, and the last item
+// of each frame to finish adds the item partials in order.
 template <bool BATCH>
 __global__ void __launch_bounds__(kSortThreads)
-k_frame_sums(FrameDesc one, FrameMaps maps, IonInputs in, int tangent, double* qsum) {
-  const FrameDesc& F = frame_at<BATCH>(one, maps, blockIdx.x);
+k_frame_sums(FrameDesc one, FrameMaps maps, IonInputs in, int tangent, SortBuffers sb) {
+  const int item = blockIdx.x;
+  const int f = BATCH ? maps.item_frame[item] : 0;
+  const FrameDesc& F = frame_at<BATCH>(one, maps, f);
+  int lo, hi;
+  item_range(F, item, lo, hi);
   double a = 0.0, b = 0.0;
-  for (int k = threadIdx.x; k < F.n; k += blockDim.x) {
-    const int i = F.ion_off + k;
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     const float qi = in.q ? in.q[i] : 0.f;
     if (isfinite(qi)) a += double(qi);
     if (tangent && in.gphi) b += double(in.gphi[i]);
@@ -64,19 +71,35 @@ k_frame_sums(FrameDesc one, FrameMaps maps, IonInputs in, int tangent, double* q
   a = block_sum_d(a);
   b = block_sum_d(b);
   if (threadIdx.x == 0) {
-    qsum[2 * blockIdx.x] = a;
-    qsum[2 * blockIdx.x + 1] = b;
+    sb.qpart[2 * item] = a;
+    sb.qpart[2 * item + 1] = b;
   }
+  if (!last_item_done(sb.qcount + f, F.nitems) || threadIdx.x != 0) return;
+  double A = 0.0, B = 0.0;
+  for (int k = 0; k < F.nitems; ++k) {
+    A += __ldcg(sb.qpart + 2 * (F.item_off + k));
+    B += __ldcg(sb.qpart + 2 * (F.item_off + k) + 1);
+  }
+  sb.qsum[2 * f] = A;
+  sb.qsum[2 * f + 1] = B;
+  sb.qcount[f] = 0;
 }
 
-// Exclusive scan of one count array by one block of 1024 threads; start[n] = total.
+// Exclusive scan of one count array by one block of 1024 threads; start[n] = total. Each
+// thread owns a chunk of a multiple of 4 entries and moves it with 16-byte loads and stores,
+// so both arrays are allocated padded to a multiple of 4 entries past n + 1 (entries past n
+// are read but ignored, and written with scratch values before start[n] is set).
 __device__ void block_exclusive_scan(const int* count, int* start, int n) {
   __shared__ int warp_tot[32];
   const int T = blockDim.x;
-  const int chunk = (n + T - 1) / T;
+  const int chunk = ((n + T - 1) / T + 3) & ~3;
   const int lo = min(n, threadIdx.x * chunk), hi = min(n, lo + chunk);
   int local = 0;
-  for (int k = lo; k < hi; ++k) local += count[k];
+#pragma unroll 4
+  for (int k = lo; k < hi; k += 4) {
+    const int4 c = *reinterpret_cast<const int4*>(count + k);
+    local += c.x + (k + 1 < hi ? c.y : 0) + (k + 2 < hi ? c.z : 0) + (k + 3 < hi ? c.w : 0);
+  }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int v = local;
 #pragma unroll
@@ -97,11 +120,19 @@ __device__ void block_exclusive_scan(const int* count, int* start, int n) {
   }
   __syncthreads();
   int run = v - local + (wid > 0 ? warp_tot[wid - 1] : 0);
-  for (int k = lo; k < hi; ++k) {
-    start[k] = run;
-    run += count[k];
+#pragma unroll 4
+  for (int k = lo; k < hi; k += 4) {
+    const int4 c = *reinterpret_cast<const int4*>(count + k);
+    int4 o;
+    o.x = run;
+    o.y = o.x + c.x;
+    o.z = o.y + (k + 1 < hi ? c.y : 0);
+    o.w = o.z + (k + 2 < hi ? c.z : 0);
+    run = o.w + (k + 3 < hi ? c.w : 0);
+    *reinterpret_cast<int4*>(start + k) = o;
   }
-  if (threadIdx.x == T - 1) start[n] = run;
+  __syncthreads();
+  if (threadIdx.x == 0) start[n] = warp_tot[31];
 }
 
 __global__ void __launch_bounds__(1024) k_scan(SortBuffers sb, int nbricks, int ncells) {
@@ -221,7 +252,11 @@ int launch_sort_t(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangen
   const int n = in.n;
   const int nblk = (n + kSortThreads - 1) / kSortThreads;
   FrameDesc one = p->frames_h[0];
-  if (!BATCH) one.n = n;
+  if (!BATCH) {
+    one.n = n;
+    one.item_off = 0;
+    one.nitems = std::max(1, (n + kRedItem - 1) / kRedItem);
+  }
   int st = check_cuda(p, cudaMemsetAsync(p->sb.count_b, 0, sizeof(int) * (p->total_bricks + 1), s),
                       "memset brick counts");
   if (st) return st;
@@ -233,9 +268,12 @@ int launch_sort_t(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangen
     count_launch();
     if ((st = check_launch(p, "k_bin"))) return st;
   }
-  k_frame_sums<BATCH><<<p->nframes, kSortThreads, 0, s>>>(one, p->maps, in, tangent ? 1 : 0, p->sb.qsum);
-  count_launch();
-  if ((st = check_launch(p, "k_frame_sums"))) return st;
+  if (p->sb.qcount) {
+    const int items = BATCH ? p->total_items : one.nitems;
+    k_frame_sums<BATCH><<<items, kSortThreads, 0, s>>>(one, p->maps, in, tangent ? 1 : 0, p->sb);
+    count_launch();
+    if ((st = check_launch(p, "k_frame_sums"))) return st;
+  }
   k_scan<<<2, 1024, 0, s>>>(p->sb, p->total_bricks, p->total_cells);
   count_launch();
   if ((st = check_launch(p, "k_scan"))) return st;

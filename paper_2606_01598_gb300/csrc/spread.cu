@@ -2,13 +2,18 @@
 //
 // Owner-computes design: one CTA owns one brick of BX x BY x BZ mesh points of one frame and
 // is the only writer of those points, so the mesh needs no zeroing and no global atomics.
-// One launch covers every brick of every frame of one spline order. The CTA walks
-// the ions of the few bricks whose ions' stencils can reach it (ions are sorted by the brick
-// of their first stencil point), keeps those whose p^3 stencil really overlaps it (an
-// order-preserving compaction), stages their 1D spline weights in shared memory, and then
-// each thread accumulates the z-column (X, Y) it owns inside a shared-memory tile. Ions are
-// visited in a fixed order, so the result is bitwise reproducible. The finished tile is
-// flushed with coalesced stores along z (the fastest mesh axis).
+// One launch covers every brick of every frame of one spline order. Each of the 256 threads
+// owns one z-segment of ZS points of one (X, Y) column of the brick and keeps it in registers.
+//
+// The CTA (1) lists the few source bricks whose ions' stencils can reach it (ions are sorted by
+// the brick of their first stencil point), one thread per source brick; (2) walks their ions
+// 256 at a time and keeps, in order, those whose p^3 stencil overlaps the brick (ballot
+// compaction); (3) stages the kept ions' 1D spline weights and coefficients in shared memory;
+// (4) builds separable coverage bitmasks -- bit l of xmask[X] is set when staged ion l's
+// stencil covers plane X, likewise for Y and for each z-segment -- so that each thread visits
+// only the ions whose stencil touches its segment (xmask[X] & ymask[Y] & zmask[seg]), in
+// staged order; (5) writes its points once. Every sum runs in a fixed order, so the result is
+// bitwise reproducible.
 //
 // Tangent mode (backward pass) spreads, in the same sweep, the tangent density
 //   d rho = sum_i [dq_i + (dmu_i + q_i dr_i) . grad + (mu_i . grad)(dr_i . grad)] W(x_i - m)
@@ -21,7 +26,12 @@ namespace gbpme {
 namespace {
 
 constexpr int BX = 8, BY = 8, BZ = 32;
-constexpr int NT = BX * BY;           // one thread per owned column
+constexpr int ZS = 8;                     // z points per thread
+constexpr int NSEG = BZ / ZS;             // z-segments per column
+constexpr int NT = BX * BY * NSEG;        // 256 threads
+constexpr int CAP = NT;                   // ions staged at once
+constexpr int NW = CAP / 32;              // mask words
+constexpr int SL = 2 * NT;                // listed (overlapping) ions held before staging
 constexpr int kMaxCand = kMaxCandPerDim * kMaxCandPerDim * kMaxCandPerDim;
 
 struct SpreadArgs {
@@ -34,87 +44,110 @@ struct SpreadArgs {
   float* mesh;          // base of the meshes: rho at mesh_off, d rho at tmesh_off
 };
 
+template <int P, bool TAN>
+constexpr int spread_smem_bytes() {
+  return CAP * (3 * (TAN ? 3 : 2) * P + (TAN ? 11 : 4)) * 4 + SL * 4 * 4;
+}
+
+// distance from a to b going up the periodic axis of length n (a, b in [0, n))
+__device__ __forceinline__ int up_dist(int a, int b, int n) {
+  const int d = b - a;
+  return d < 0 ? d + n : d;
+}
+
 template <int P, bool TAN, bool BATCH>
 __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
   constexpr int DW = TAN ? 3 : 2;                 // weight derivative orders kept
-  constexpr int CAP = TAN ? NT : 2 * NT;          // staged ions per batch
   constexpr int WSTRIDE = 3 * DW * P;             // floats of weights per staged ion
   constexpr int NC = TAN ? 11 : 4;                // coefficients per staged ion
 
-  __shared__ float tile[BZ][NT + 1];
-  __shared__ float dtile[TAN ? BZ : 1][NT + 1];
-  __shared__ float sw[CAP * WSTRIDE];
-  __shared__ float sc[CAP * NC];
-  __shared__ int sm0[CAP * 3];
-  __shared__ int slist[CAP];
+  extern __shared__ __align__(16) float dyn[];
+  float* sw = dyn;                                        // [CAP][WSTRIDE]
+  float* sc = sw + CAP * WSTRIDE;                         // [CAP][NC]
+  int* slist = reinterpret_cast<int*>(sc + CAP * NC);     // [SL] listed ions
+  int* sm0 = slist + SL;                                  // [SL][3] their first stencil points
+  __shared__ unsigned xmask[BX][NW], ymask[BY][NW], zmask[NSEG][NW];
   __shared__ int cand_lo[kMaxCand];
+  __shared__ int cand_cnt[kMaxCand];
   __shared__ int cand_cum[kMaxCand + 1];
   __shared__ int warp_cnt[NT / 32];
-  __shared__ int ncand_s;
 
   const int gkey = a.key_lo + blockIdx.x;
   const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, BATCH ? a.maps.brick_frame[gkey] : 0);
   const Geometry& g = F.g;
   const int tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
   const int bkey = gkey - F.brick_off;
   const int bz = bkey % g.nb[2];
   const int by = (bkey / g.nb[2]) % g.nb[1];
   const int bx = bkey / (g.nb[2] * g.nb[1]);
   const int b0x = bx * BX, b0y = by * BY, b0z = bz * BZ;
   const int ex = min(BX, g.N[0] - b0x), ey = min(BY, g.N[1] - b0y), ez = min(BZ, g.N[2] - b0z);
+  const int Nx = g.N[0], Ny = g.N[1], Nz = g.N[2];
 
-  for (int e = tid; e < BZ * (NT + 1); e += NT) {
-    (&tile[0][0])[e] = 0.f;
-    if (TAN) (&dtile[0][0])[e] = 0.f;
-  }
-  // candidate source bricks: product of the per-axis lists, in a fixed order
-  if (tid == 0) {
-    const int* ct = a.cand + F.cand_off;
-    const int* cx = ct + (0 * F.max_nb + bx) * (1 + kMaxCandPerDim);
-    const int* cy = ct + (1 * F.max_nb + by) * (1 + kMaxCandPerDim);
-    const int* cz = ct + (2 * F.max_nb + bz) * (1 + kMaxCandPerDim);
-    int k = 0, cum = 0;
-    for (int ix = 0; ix < cx[0]; ++ix)
-      for (int iy = 0; iy < cy[0]; ++iy)
-        for (int iz = 0; iz < cz[0]; ++iz) {
-          const int key = F.brick_off + (cx[1 + ix] * g.nb[1] + cy[1 + iy]) * g.nb[2] + cz[1 + iz];
-          const int lo = a.start_b[key], hi = a.start_b[key + 1];
-          cand_lo[k] = lo;
-          cand_cum[k] = cum;
-          cum += hi - lo;
-          ++k;
-        }
-    cand_cum[k] = cum;
-    ncand_s = k;
+  // ---- (1) candidate source bricks: product of the per-axis lists, in a fixed order ----
+  const int* ct = a.cand + F.cand_off;
+  const int* cx = ct + (0 * F.max_nb + bx) * (1 + kMaxCandPerDim);
+  const int* cy = ct + (1 * F.max_nb + by) * (1 + kMaxCandPerDim);
+  const int* cz = ct + (2 * F.max_nb + bz) * (1 + kMaxCandPerDim);
+  const int ncx = cx[0], ncy = cy[0], ncz = cz[0];
+  const int ncand = ncx * ncy * ncz;
+  if (tid < kMaxCand) {
+    int lo = 0, c = 0;
+    if (tid < ncand) {
+      const int iz = tid % ncz, iy = (tid / ncz) % ncy, ix = tid / (ncz * ncy);
+      const int key = F.brick_off + (cx[1 + ix] * g.nb[1] + cy[1 + iy]) * g.nb[2] + cz[1 + iz];
+      lo = a.start_b[key];
+      c = a.start_b[key + 1] - lo;
+    }
+    cand_lo[tid] = lo;
+    cand_cnt[tid] = c;
   }
   __syncthreads();
-  const int ncand = ncand_s;
-  const int total = cand_cum[ncand];
+  if (wid == 0) {
+    // exclusive scan of the 64 counts, two per lane
+    const int c0 = cand_cnt[2 * lane], c1 = cand_cnt[2 * lane + 1];
+    int v = c0 + c1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    const int excl = v - c0 - c1;
+    cand_cum[2 * lane] = excl;
+    cand_cum[2 * lane + 1] = excl + c0;
+    if (lane == 31) cand_cum[kMaxCand] = v;
+  }
+  __syncthreads();
+  const int total = cand_cum[kMaxCand];
 
-  const int X = tid / BY, Y = tid % BY;
-  const bool own = (X < ex) && (Y < ey);
-  const int gx = b0x + X, gy = b0y + Y;
-  const int lane = tid & 31, wid = tid >> 5;
+  // this thread's points: column (X, Y), z-segment seg
+  const int seg = tid & (NSEG - 1), col = tid / NSEG;
+  const int X = col / BY, Y = col % BY;
+  const int gx = b0x + X, gy = b0y + Y, zs0 = b0z + seg * ZS;
+  float acc[ZS], dacc[TAN ? ZS : 1];
+#pragma unroll
+  for (int z = 0; z < ZS; ++z) acc[z] = 0.f;
+#pragma unroll
+  for (int z = 0; z < (TAN ? ZS : 1); ++z) dacc[z] = 0.f;
 
   int cnt = 0;
   for (int cursor = 0; cursor < total; cursor += NT) {
-    // ---- fill: test NT candidates, append the overlapping ones in order --------------
+    // ---- (2) test NT candidates, append the overlapping ones in order -----------------
     const int gi = cursor + tid;
-    int ion = -1;
     bool take = false;
+    int ion = 0;
+    int4 m = make_int4(0, 0, 0, 0);
     if (gi < total) {
       int k = 0;
-      while (k + 1 < ncand && cand_cum[k + 1] <= gi) ++k;
+#pragma unroll
+      for (int st = 32; st >= 1; st >>= 1)
+        if (k + st < ncand && cand_cum[k + st] <= gi) k += st;
       ion = cand_lo[k] + (gi - cand_cum[k]);
-      const int4 m = a.mr.idx[ion];
-      int d;
-      d = b0x - m.x; if (d < 0) d += g.N[0];
-      const bool okx = (d <= P - 1) || (d >= g.N[0] - ex + 1);
-      d = b0y - m.y; if (d < 0) d += g.N[1];
-      const bool oky = (d <= P - 1) || (d >= g.N[1] - ey + 1);
-      d = b0z - m.z; if (d < 0) d += g.N[2];
-      const bool okz = (d <= P - 1) || (d >= g.N[2] - ez + 1);
-      take = okx && oky && okz;
+      m = a.mr.idx[ion];
+      const int dx = up_dist(m.x, b0x, Nx), dy = up_dist(m.y, b0y, Ny), dz = up_dist(m.z, b0z, Nz);
+      take = (dx <= P - 1 || dx >= Nx - ex + 1) && (dy <= P - 1 || dy >= Ny - ey + 1) &&
+             (dz <= P - 1 || dz >= Nz - ez + 1);
     }
     const unsigned bal = __ballot_sync(0xffffffffu, take);
     if (lane == 0) warp_cnt[wid] = __popc(bal);
@@ -122,22 +155,30 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
     int before = 0, tot = 0;
 #pragma unroll
     for (int w = 0; w < NT / 32; ++w) {
-      if (w < wid) before += warp_cnt[w];
+      before += (w < wid) ? warp_cnt[w] : 0;
       tot += warp_cnt[w];
     }
-    if (take) slist[cnt + before + __popc(bal & ((1u << lane) - 1u))] = ion;
+    if (take) {
+      const int l = cnt + before + __popc(bal & ((1u << lane) - 1u));
+      slist[l] = ion;
+      sm0[3 * l] = m.x;
+      sm0[3 * l + 1] = m.y;
+      sm0[3 * l + 2] = m.z;
+    }
     cnt += tot;
     __syncthreads();
-    const bool last = cursor + NT >= total;
-    if (cnt > CAP - NT || last) {
-      // ---- stage weights and coefficients of the listed ions -----------------------
-      for (int l = tid; l < cnt; l += NT) {
+    if (cnt <= SL - NT && cursor + NT < total) continue;
+
+    for (int base = 0; base < cnt; base += CAP) {
+      const int nst = min(CAP, cnt - base);
+      // ---- (3) stage weights and coefficients ---------------------------------------
+      if (tid < nst) {
+        const int l = base + tid;
         const int src = slist[l];
-        const int4 m = a.mr.idx[src];
         const float4 fq = a.mr.fq[src];
         const float4 dm = a.mr.dm[src];
         float w[DW][P];
-        float* dst = sw + l * WSTRIDE;
+        float* dst = sw + tid * WSTRIDE;
         spline_weights<P, DW - 1>(fq.x, w);
 #pragma unroll
         for (int d = 0; d < DW; ++d)
@@ -153,10 +194,7 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
         for (int d = 0; d < DW; ++d)
 #pragma unroll
           for (int j = 0; j < P; ++j) dst[(2 * DW + d) * P + j] = w[d][j];
-        sm0[3 * l] = m.x;
-        sm0[3 * l + 1] = m.y;
-        sm0[3 * l + 2] = m.z;
-        float* c = sc + l * NC;
+        float* c = sc + tid * NC;
         c[0] = fq.w;
         c[1] = dm.x;
         c[2] = dm.y;
@@ -173,27 +211,55 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
           c[10] = tt.z;
         }
       }
+      // ---- (4) coverage masks: warp w builds word w -----------------------------------
+      if (wid < NW) {
+        const int l = base + wid * 32 + lane;
+        const bool in = wid * 32 + lane < nst;
+        const int mx = in ? sm0[3 * l] : 0, my = in ? sm0[3 * l + 1] : 0, mz = in ? sm0[3 * l + 2] : 0;
+#pragma unroll
+        for (int t = 0; t < BX; ++t) {
+          const bool cov = in && t < ex && up_dist(mx, b0x + t, Nx) < P;
+          const unsigned b = __ballot_sync(0xffffffffu, cov);
+          if (lane == 0) xmask[t][wid] = b;
+        }
+#pragma unroll
+        for (int t = 0; t < BY; ++t) {
+          const bool cov = in && t < ey && up_dist(my, b0y + t, Ny) < P;
+          const unsigned b = __ballot_sync(0xffffffffu, cov);
+          if (lane == 0) ymask[t][wid] = b;
+        }
+#pragma unroll
+        for (int t = 0; t < NSEG; ++t) {
+          const int s0 = b0z + t * ZS, ext = min(ZS, ez - t * ZS);
+          const bool cov = in && ext > 0 &&
+                           (up_dist(mz, s0, Nz) < P || up_dist(s0, mz, Nz) < ext);
+          const unsigned b = __ballot_sync(0xffffffffu, cov);
+          if (lane == 0) zmask[t][wid] = b;
+        }
+      }
       __syncthreads();
-      // ---- accumulate the owned column ----------------------------------------------
-      if (own) {
-        for (int l = 0; l < cnt; ++l) {
-          int dx = gx - sm0[3 * l];
-          if (dx < 0) dx += g.N[0];
-          if (dx >= P) continue;
-          int dy = gy - sm0[3 * l + 1];
-          if (dy < 0) dy += g.N[1];
-          if (dy >= P) continue;
-          const float* w = sw + l * WSTRIDE;
-          const float* c = sc + l * NC;
-          const float wx = w[(0 * DW + 0) * P + dx], wx1 = w[(0 * DW + 1) * P + dx];
-          const float wy = w[(1 * DW + 0) * P + dy], wy1 = w[(1 * DW + 1) * P + dy];
+      // ---- accumulate this thread's points over the ions that touch them --------------
+      const int nw = (nst + 31) >> 5;
+      for (int w = 0; w < nw; ++w) {
+        unsigned bits = xmask[X][w] & ymask[Y][w] & zmask[seg][w];
+        while (bits) {
+          const int t = w * 32 + __ffs(bits) - 1;
+          bits &= bits - 1;
+          const int l = base + t;
+          const int dx = up_dist(sm0[3 * l], gx, Nx);
+          const int dy = up_dist(sm0[3 * l + 1], gy, Ny);
+          const int dz0 = up_dist(sm0[3 * l + 2], zs0, Nz);   // stencil index of z = zs0
+          const float* wt = sw + t * WSTRIDE;
+          const float* c = sc + t * NC;
+          const float wx = wt[(0 * DW + 0) * P + dx], wx1 = wt[(0 * DW + 1) * P + dx];
+          const float wy = wt[(1 * DW + 0) * P + dy], wy1 = wt[(1 * DW + 1) * P + dy];
           const float wxy = wx * wy;
           // rho: coefficient of W_z and of W'_z
           const float A = c[0] * wxy + c[1] * wx1 * wy + c[2] * wx * wy1;
           const float B = c[3] * wxy;
           float A0 = 0.f, A1 = 0.f, A2 = 0.f;
           if (TAN) {
-            const float wx2 = w[(0 * DW + 2) * P + dx], wy2 = w[(1 * DW + 2) * P + dy];
+            const float wx2 = wt[(0 * DW + 2) * P + dx], wy2 = wt[(1 * DW + 2) * P + dy];
             const float mx = c[1], my = c[2], mz = c[3];
             const float tx = c[8], ty = c[9], tz = c[10];
             A0 = c[4] * wxy + c[5] * wx1 * wy + c[6] * wx * wy1 + mx * tx * wx2 * wy +
@@ -201,41 +267,54 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
             A1 = c[7] * wxy + (mx * tz + mz * tx) * wx1 * wy + (my * tz + mz * ty) * wx * wy1;
             A2 = mz * tz * wxy;
           }
-          const int mz0 = sm0[3 * l + 2];
+          const float* wz = wt + (2 * DW + 0) * P;
 #pragma unroll
-          for (int jz = 0; jz < P; ++jz) {
-            int Z = mz0 + jz - b0z;
-            if (Z < 0) Z += g.N[2];
-            else if (Z >= g.N[2]) Z -= g.N[2];
-            if (Z < ez) {
-              const float wz = w[(2 * DW + 0) * P + jz], wz1 = w[(2 * DW + 1) * P + jz];
-              tile[Z][tid] += A * wz + B * wz1;
-              if (TAN) {
-                const float wz2 = w[(2 * DW + 2) * P + jz];
-                dtile[Z][tid] += A0 * wz + A1 * wz1 + A2 * wz2;
-              }
+          for (int z = 0; z < ZS; ++z) {
+            int j = dz0 + z;
+            if (j >= Nz) j -= Nz;
+            if (j < P) {
+              acc[z] += A * wz[j] + B * wz[P + j];
+              if (TAN) dacc[z] += A0 * wz[j] + A1 * wz[P + j] + A2 * wz[2 * P + j];
             }
           }
         }
       }
       __syncthreads();
-      cnt = 0;
     }
+    cnt = 0;
   }
-  __syncthreads();
-  // ---- flush: every owned mesh point written exactly once, z fastest ----------------
-  const int Ny = g.N[1], Nz = g.N[2];
-  float* rho = a.mesh + F.mesh_off;
-  float* drho = a.mesh + F.tmesh_off;
-  for (int e = tid; e < NT * BZ; e += NT) {
-    const int Z = e % BZ, col = e / BZ;
-    const int x = col / BY, y = col % BY;
-    if (x < ex && y < ey && Z < ez) {
-      const size_t off = (size_t(b0x + x) * Ny + (b0y + y)) * Nz + (b0z + Z);
-      rho[off] = tile[Z][col];
-      if (TAN) drho[off] = dtile[Z][col];
-    }
+
+  // ---- (5) write: every owned mesh point exactly once ---------------------------------
+  if (X < ex && Y < ey) {
+    const size_t off = (size_t(gx) * Ny + gy) * Nz + zs0;
+    float* rho = a.mesh + F.mesh_off + off;
+    float* drho = a.mesh + F.tmesh_off + off;
+    const int nz = min(ZS, ez - seg * ZS);
+#pragma unroll
+    for (int z = 0; z < ZS; ++z)
+      if (z < nz) {
+        rho[z] = acc[z];
+        if (TAN) drho[z] = dacc[z];
+      }
   }
+}
+
+// One instantiation's launch; the first use on a device raises its dynamic shared-memory limit.
+template <int P, bool TAN, bool BATCH>
+int launch_order(pme_plan_t p, cudaStream_t s, int grid, const SpreadArgs& a) {
+  constexpr int bytes = spread_smem_bytes<P, TAN>();
+  static int done_mask = 0;   // devices 0..31 already configured (idempotent if raced)
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 32 || !(done_mask & (1 << dev))) {
+    const int st = check_cuda(p, cudaFuncSetAttribute(k_spread<P, TAN, BATCH>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
+                              "cudaFuncSetAttribute");
+    if (st) return st;
+    if (dev < 32) done_mask |= 1 << dev;
+  }
+  k_spread<P, TAN, BATCH><<<grid, NT, bytes, s>>>(a);
+  return PME_OK;
 }
 
 template <bool TAN, bool BATCH>
@@ -252,19 +331,19 @@ int launch_t(pme_plan_t p, cudaStream_t s, float* mesh) {
     const int grid = G.brick_hi - G.brick_lo;
     if (grid <= 0) continue;
     a.key_lo = G.brick_lo;
+    int st = PME_OK;
     switch (G.order) {
-      case 1: k_spread<1, TAN, BATCH><<<grid, NT, 0, s>>>(a); break;
-      case 2: k_spread<2, TAN, BATCH><<<grid, NT, 0, s>>>(a); break;
-      case 3: k_spread<3, TAN, BATCH><<<grid, NT, 0, s>>>(a); break;
-      case 4: k_spread<4, TAN, BATCH><<<grid, NT, 0, s>>>(a); break;
-      case 5: k_spread<5, TAN, BATCH><<<grid, NT, 0, s>>>(a); break;
-      case 6: k_spread<6, TAN, BATCH><<<grid, NT, 0, s>>>(a); break;
-      case 7: k_spread<7, TAN, BATCH><<<grid, NT, 0, s>>>(a); break;
+      case 1: st = launch_order<1, TAN, BATCH>(p, s, grid, a); break;
+      case 2: st = launch_order<2, TAN, BATCH>(p, s, grid, a); break;
+      case 3: st = launch_order<3, TAN, BATCH>(p, s, grid, a); break;
+      case 4: st = launch_order<4, TAN, BATCH>(p, s, grid, a); break;
+      case 5: st = launch_order<5, TAN, BATCH>(p, s, grid, a); break;
+      case 6: st = launch_order<6, TAN, BATCH>(p, s, grid, a); break;
+      case 7: st = launch_order<7, TAN, BATCH>(p, s, grid, a); break;
       default: return set_error(p, PME_ERR_ARG, "spline order out of range");
     }
-    count_launch();
-    int st = check_launch(p, "k_spread");
     if (st) return st;
+    if ((st = check_launch(p, "k_spread"))) return st;
   }
   return PME_OK;
 }
