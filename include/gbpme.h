@@ -70,7 +70,7 @@ typedef struct {
   int include_pair;        /* 1: real-space erfc pair term (default); 0: mesh + self only */
   int include_self;        /* 1: self terms (default) */
   int include_background;  /* 1: neutralising background term (default) */
-  int max_ions;            /* capacity; default 1<<18 */
+  int max_ions;            /* capacity; default 1<<18, at most 1<<27 (PME_ERR_UNSUPPORTED) */
   int brick[3];            /* spread/gather brick edge in mesh points; 0 = automatic */
   int overlap_pair;        /* 1: run the pair term on a plan-owned side stream, concurrently
                               with the mesh stages (default); 0: everything on the call's

@@ -59,11 +59,11 @@ struct MeshRecords {
 // Per-ion records in pair-cell order.
 struct PairRecords {
   int4* idx;     // cell x, y, z, original index
-  float4* fq;    // offsets inside the cell in cell units fx, fy, fz in [0,1), q
-  float4* mu;    // mu (r-space), w unused
+  float4* fq;    // offsets inside the cell in cell units fx, fy, fz in [0,1); w = cell z index
+                 // (int bits), which gives a candidate's z offset inside a z-run
+  float4* mu;    // mu (r-space), w = q
   float4* tq;    // tangent: dq, d' = dmu + q dr (r-space)
   float4* dr;    // tangent: dr (r-space); w unused
-  int* cz;       // cell z index (for the z offset of a candidate inside a z-run)
 };
 
 struct SortBuffers {

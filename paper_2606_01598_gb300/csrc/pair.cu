@@ -12,18 +12,20 @@
 //                    + r ((u.v)(w.r) + (u.w)(v.r) + (v.w)(u.r))) B3 + r (u.r)(v.r)(w.r) B4
 // (the contractions of grad^k psi). The potential at i of source j is q_j psi - mu_j . grad psi.
 //
-// Work split: one warp per ion (ions in pair-cell order, cells at least rcut/2 wide, so a
-// partner is at most kimg = ceil(rcut / cell width) cells away per axis). Its candidates are
-// the (2 kimg + 1)^2 neighbouring (x, y) cell columns, each holding the contiguous run of the
-// 2 kimg + 1 z-cells around the ion (one or two ranges at the periodic wrap); when an axis has
-// too few cells for distinct offsets, each offset is its own segment and stands for its own
-// periodic image. The lanes describe the columns in
-// parallel and a warp scan turns them into one dense candidate stream, tested 32 at a time;
-// candidates inside rcut are compacted (ballot + popc) into a per-warp shared-memory buffer
-// and evaluated with all lanes busy once 32 or more are waiting. Each lane accumulates its share,
-// and a warp-shuffle reduction gives the ion's sums. Every pair is visited from both sides
-// (no atomics). Displacements are formed from in-cell offsets, which keeps them exact to float
-// rounding of a few Angstrom.
+// Work split: one warp per pair cell (cells at least rcut/2 wide, so a partner is at most
+// kimg = ceil(rcut / cell width) cells away per axis); the warp handles the cell's ions
+// kSlots at a time, and they share one candidate stream. The candidates are the
+// (2 kimg + 1)^2 neighbouring (x, y) cell columns, each holding the contiguous run of the
+// 2 kimg + 1 z-cells around the cell (one or two ranges at the periodic wrap); when an axis
+// has too few cells for distinct offsets, each offset is its own segment and stands for its
+// own periodic image. The lanes describe the columns in parallel and a warp scan turns them
+// into one dense candidate stream, loaded 32 at a time; each candidate is tested against
+// every ion of the group, and the ones inside rcut are compacted (ballot + popc) into that
+// ion's shared-memory hit list. Whenever a list holds 32 hits they are evaluated with all
+// lanes busy (the remainder waits for the next chunk). Each lane accumulates its share and a
+// warp-shuffle reduction gives each ion's sums. Every pair is visited from both sides (no
+// atomics), and every sum runs in a fixed order. Displacements are formed from in-cell
+// offsets, which keeps them exact to float rounding of a few Angstrom.
 //
 // Forward: out[orig][10] = phi, grad phi (3), grad grad phi (6) of the pair potential.
 // Tangent: out[orig][8] = pair part of the backward (grad_r, grad_q, grad_mu), i.e. the
@@ -40,7 +42,10 @@ namespace {
 
 constexpr int kPairWarps = 4;
 constexpr int kPairThreads = kPairWarps * 32;
-constexpr int kHitCap = 96;   // compacted hits buffered per warp
+constexpr int kSlots = 4;      // ions of one cell sharing a candidate stream
+constexpr int kSlotCap = 64;   // buffered hits per ion (< 32 wait between chunks)
+constexpr int kCandCap = 512;  // candidates listed per warp at a time
+constexpr int kSegShift = 27;  // candidate entry: (segment lane << 27) | sorted index
 
 struct PairArgs {
   FrameDesc one;
@@ -49,7 +54,7 @@ struct PairArgs {
   const int* start_c;
   const double* g_energy;   // per frame
   float* out;
-  int n;
+  int cell_lo, ncells;      // global cell keys handled by this launch
   float alpha;
   float c1, c2, c3, c4;   // (2 alpha^2)^l / (alpha sqrt(pi)), l = 1..4
 };
@@ -96,18 +101,18 @@ struct Ion {
 template <bool TAN>
 __device__ __forceinline__ void interact(const PairArgs& a, const Ion& I, int j, V3 r, Acc<TAN>& A) {
   const float r2 = dot(r, r);
-  const float rinv2 = 1.f / r2;
-  const float rr = sqrtf(r2);
+  const float rinv = rsqrtf(r2);
+  const float rinv2 = rinv * rinv;
+  const float rr = r2 * rinv;
   const float alpha = a.alpha;
   const float ex = expf(-alpha * alpha * r2);
-  const float B0 = erfcf(alpha * rr) / rr;
+  const float B0 = erfcf(alpha * rr) * rinv;
   const float B1 = (B0 + a.c1 * ex) * rinv2;
   const float B2 = (3.f * B1 + a.c2 * ex) * rinv2;
   const float B3 = (5.f * B2 + a.c3 * ex) * rinv2;
-  const float4 fj = a.pr.fq[j];
   const float4 mj4 = a.pr.mu[j];
   const V3 d = mk(mj4.x, mj4.y, mj4.z);
-  const float c = fj.w;
+  const float c = mj4.w;
   const float dr_ = dot(d, r);
   const float phi = c * B0 + dr_ * B1;
   // grad phi = c g1 - g2(d) = -(c B1 + (d.r) B2) r + B1 d
@@ -160,185 +165,279 @@ __device__ __forceinline__ void interact(const PairArgs& a, const Ion& I, int j,
   }
 }
 
-template <bool TAN, bool BATCH>
+// Accumulator floats per ion: phi, grad phi, grad grad phi (forward); grad_r, grad_q, grad_mu
+// (tangent).
+template <bool TAN>
+constexpr int kAccN = TAN ? 7 : 10;
+
+template <bool TAN>
+__device__ __forceinline__ void acc_load(Acc<TAN>& A, const float* p) {
+  if constexpr (!TAN) {
+    A.phi = p[0];
+    A.g = mk(p[32], p[64], p[96]);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) A.h[k] = p[32 * (4 + k)];
+  } else {
+    A.gr = mk(p[0], p[32], p[64]);
+    A.gq = p[96];
+    A.gm = mk(p[128], p[160], p[192]);
+  }
+}
+
+template <bool TAN>
+__device__ __forceinline__ void acc_store(const Acc<TAN>& A, float* p) {
+  if constexpr (!TAN) {
+    p[0] = A.phi;
+    p[32] = A.g.x;
+    p[64] = A.g.y;
+    p[96] = A.g.z;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) p[32 * (4 + k)] = A.h[k];
+  } else {
+    p[0] = A.gr.x;
+    p[32] = A.gr.y;
+    p[64] = A.gr.z;
+    p[96] = A.gq;
+    p[128] = A.gm.x;
+    p[160] = A.gm.y;
+    p[192] = A.gm.z;
+  }
+}
+
+__device__ __forceinline__ unsigned pack_counts(const int (&c)[kSlots]) {
+  unsigned p = 0;
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) p |= unsigned(c[s]) << (8 * s);
+  return p;
+}
+
+__device__ __forceinline__ void unpack_counts(unsigned p, int (&c)[kSlots]) {
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) c[s] = int((p >> (8 * s)) & 0xffu);
+}
+
+// ORTHO: every frame of the launch has a diagonal cell matrix (r = u . H needs 3 products).
+template <bool TAN, bool BATCH, bool ORTHO>
 __global__ void __launch_bounds__(kPairThreads) k_pair(PairArgs a) {
-  __shared__ int s_j[kPairWarps][kHitCap];
-  __shared__ float s_r[kPairWarps][3][kHitCap];
+  constexpr int NA = kAccN<TAN>;
+  __shared__ float4 s_hit[kPairWarps][kSlots][kSlotCap];   // r (x, y, z), w = j (int bits)
+  __shared__ float s_acc[kPairWarps][kSlots][NA][32];   // per-lane partial sums of each ion
+  __shared__ float4 s_fi[kPairWarps][kSlots];          // in-cell offsets, w = sorted index bits
+  __shared__ unsigned s_cand[kPairWarps][kCandCap];     // candidate stream of the segment group
+  __shared__ int s_code[kPairWarps][32];                // packed (ox, oy, oz) of each segment
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int i = blockIdx.x * kPairWarps + w;
-  if (i >= a.n) return;   // uniform per warp
-  const int frame = BATCH ? a.maps.sorted_frame[i] : 0;
+  const int cidx = blockIdx.x * kPairWarps + w;
+  if (cidx >= a.ncells) return;   // uniform per warp
+  const int cell = a.cell_lo + cidx;
+  const int c_lo = a.start_c[cell], c_hi = a.start_c[cell + 1];
+  if (c_lo == c_hi) return;
+  const int frame = BATCH ? a.maps.sorted_frame[c_lo] : 0;
   const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, frame);
   const Geometry& g = F.g;
-  const int4 ci = a.pr.idx[i];
-  const float4 fi = a.pr.fq[i];
-  const float4 mi4 = a.pr.mu[i];
-  Ion I;
-  I.mu = mk(mi4.x, mi4.y, mi4.z);
-  I.q = fi.w;
-  I.dq = 0.f;
-  I.gE = 0.f;
-  I.dr = mk(0.f, 0.f, 0.f);
-  I.w = mk(0.f, 0.f, 0.f);
-  if (TAN) {
-    const float4 t = a.pr.tq[i];
-    const float4 d = a.pr.dr[i];
-    I.gE = a.g_energy ? float(a.g_energy[frame]) : 0.f;
-    I.dq = t.x;
-    I.dr = mk(d.x, d.y, d.z);
-    I.w = I.gE * I.mu + mk(t.y, t.z, t.w);   // gE mu + dmu + q dr
-  }
-  Acc<TAN> A;
-  int cnt = 0;
-  int* sj = s_j[w];
-  float* sx = s_r[w][0];
-  float* sy = s_r[w][1];
-  float* sz = s_r[w][2];
-
-  auto flush = [&]() {
-    __syncwarp();
-    for (int k = lane; k < cnt; k += 32) interact<TAN>(a, I, sj[k], mk(sx[k], sy[k], sz[k]), A);
-    __syncwarp();
-    cnt = 0;
-  };
-  // test candidate j (valid lanes only) with cell offsets (ox, oy, oz); append the hits
-  auto test = [&](bool valid, int j, int ox, int oy, int oz) {
-    bool hit = false;
-    V3 r = mk(0.f, 0.f, 0.f);
-    if (valid) {
-      const float4 fj = a.pr.fq[j];
-      const float ux = fi.x - fj.x - float(ox);
-      const float uy = fi.y - fj.y - float(oy);
-      const float uz = fi.z - fj.z - float(oz);
-      r = mk(ux * g.H[0] + uy * g.H[3] + uz * g.H[6], ux * g.H[1] + uy * g.H[4] + uz * g.H[7],
-             ux * g.H[2] + uy * g.H[5] + uz * g.H[8]);
-      hit = dot(r, r) < g.rcut2 && !(j == i && ox == 0 && oy == 0 && oz == 0);
-    }
-    const unsigned bal = __ballot_sync(0xffffffffu, hit);
-    if (hit) {
-      const int k = cnt + __popc(bal & ((1u << lane) - 1u));
-      sj[k] = j;
-      sx[k] = r.x;
-      sy[k] = r.y;
-      sz[k] = r.z;
-    }
-    cnt += __popc(bal);
-    if (cnt > kHitCap - 32) flush();
-  };
-
-  // ---- dense candidate stream ---------------------------------------------------------
-  // A segment is one (ox, oy[, oz]) neighbour column: the ions of one or two contiguous
-  // ranges of the cell order. Lane l describes segment (32 g + l) of group g; a warp scan of
-  // the lengths lets every lane pick its candidate c = base + lane of the group's
-  // concatenated ranges by a 5-step shuffle search, so each 32-wide chunk holds 32 candidates.
   const int ncx = g.ncell[0], ncy = g.ncell[1], ncz = g.ncell[2];
   const int kx = g.kimg[0], ky = g.kimg[1], kz = g.kimg[2];
+  const int lc = cell - F.cell_off;
+  const int ciz = lc % ncz, ciy = (lc / ncz) % ncy, cix = lc / (ncz * ncy);
+  const unsigned lane_lt = (1u << lane) - 1u;
+  const float gE = (TAN && a.g_energy) ? float(a.g_energy[frame]) : 0.f;
+
   const bool zrun = ncz >= 2 * kz + 1;              // the z-cells of a column are distinct:
                                                     // z offsets come from the candidate's cell
   const int nzs = zrun ? 1 : 2 * kz + 1;            // segments per (ox, oy) column
   const int nseg = (2 * kx + 1) * (2 * ky + 1) * nzs;
-  for (int g0 = 0; g0 < nseg; g0 += 32) {
-    const int sidx = g0 + lane;
-    int loA = 0, lenA = 0, loB = 0, lenB = 0, code = 0;
-    if (sidx < nseg) {
-      const int oz = zrun ? 0 : (sidx % nzs) - kz;
-      const int t = sidx / nzs;
-      const int oy = (t % (2 * ky + 1)) - ky;
-      const int ox = (t / (2 * ky + 1)) - kx;
-      int cx = (ci.x + ox) % ncx, cy = (ci.y + oy) % ncy;
-      if (cx < 0) cx += ncx;
-      if (cy < 0) cy += ncy;
-      const int row = F.cell_off + (cx * ncy + cy) * ncz;
-      if (zrun) {
-        const int z0 = ci.z - kz, z1 = ci.z + kz;
-        if (z0 < 0) {
-          loA = a.start_c[row + z0 + ncz]; lenA = a.start_c[row + ncz] - loA;
-          loB = a.start_c[row]; lenB = a.start_c[row + z1 + 1] - loB;
-        } else if (z1 >= ncz) {
-          loA = a.start_c[row + z0]; lenA = a.start_c[row + ncz] - loA;
-          loB = a.start_c[row]; lenB = a.start_c[row + z1 - ncz + 1] - loB;
-        } else {
-          loA = a.start_c[row + z0]; lenA = a.start_c[row + z1 + 1] - loA;
-        }
-      } else {
-        int cz = (ci.z + oz) % ncz;
-        if (cz < 0) cz += ncz;
-        loA = a.start_c[row + cz]; lenA = a.start_c[row + cz + 1] - loA;
-      }
-      // offsets packed in one int: 10 bits each, biased by 512
-      code = ((ox + 512) << 20) | ((oy + 512) << 10) | (oz + 512);
-    }
-    const int len = lenA + lenB;
-    int pre = len;   // inclusive scan over the group's segments
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int u = __shfl_up_sync(0xffffffffu, pre, o);
-      if (lane >= o) pre += u;
-    }
-    const int total = __shfl_sync(0xffffffffu, pre, 31);
-    for (int base = 0; base < total; base += 32) {
-      const int c = base + lane;
-      // smallest segment s with pre[s] > c
-      int sl = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int v = __shfl_sync(0xffffffffu, pre, sl + step - 1);
-        if (v <= c) sl += step;
-      }
-      const int sp = __shfl_sync(0xffffffffu, pre, sl);
-      const int sl_len = __shfl_sync(0xffffffffu, len, sl);
-      const int sa = __shfl_sync(0xffffffffu, loA, sl);
-      const int sla = __shfl_sync(0xffffffffu, lenA, sl);
-      const int sb = __shfl_sync(0xffffffffu, loB, sl);
-      const int scode = __shfl_sync(0xffffffffu, code, sl);
-      const bool valid = c < total;
-      const int off = c - (sp - sl_len);
-      const int j = valid ? ((off < sla) ? sa + off : sb + (off - sla)) : 0;
-      const int ox = ((scode >> 20) & 1023) - 512;
-      const int oy = ((scode >> 10) & 1023) - 512;
-      int oz = (scode & 1023) - 512;
-      if (zrun && valid) {
-        oz = a.pr.cz[j] - ci.z;
-        if (oz > kz) oz -= ncz;
-        else if (oz < -kz) oz += ncz;
-      }
-      test(valid, j, ox, oy, oz);
-    }
-  }
-  if (cnt > 0) flush();
 
-  const int orig = ci.w;
-  if constexpr (!TAN) {
-    const float phi = warp_sum(A.phi);
-    const float gx = warp_sum(A.g.x), gy = warp_sum(A.g.y), gz = warp_sum(A.g.z);
-    float h[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) h[k] = warp_sum(A.h[k]);
-    if (lane == 0) {
-      float* o = a.out + size_t(orig) * 10;
-      o[0] = phi;
-      o[1] = gx;
-      o[2] = gy;
-      o[3] = gz;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) o[4 + k] = h[k];
+  for (int i0 = c_lo; i0 < c_hi; i0 += kSlots) {
+    const int ni = min(kSlots, c_hi - i0);
+    if (lane < ni) {
+      const float4 f = a.pr.fq[i0 + lane];
+      s_fi[w][lane] = make_float4(f.x, f.y, f.z, __int_as_float(i0 + lane));
     }
-  } else {
-    const float rx = warp_sum(A.gr.x), ry = warp_sum(A.gr.y), rz = warp_sum(A.gr.z);
-    const float q = warp_sum(A.gq);
-    const float mx = warp_sum(A.gm.x), my = warp_sum(A.gm.y), mz = warp_sum(A.gm.z);
-    if (lane == 0) {
-      float* o = a.out + size_t(orig) * 8;
-      o[0] = rx;
-      o[1] = ry;
-      o[2] = rz;
-      o[3] = q;
-      o[4] = mx;
-      o[5] = my;
-      o[6] = mz;
-      o[7] = 0.f;
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s)
+#pragma unroll
+      for (int k = 0; k < NA; ++k) s_acc[w][s][k][lane] = 0.f;
+    __syncwarp();
+    int cnt[kSlots];     // hits waiting per slot (< 64)
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s) cnt[s] = 0;
+    unsigned cnts = 0;   // the same, packed 8 bits per slot, for the flush loop
+
+    // Evaluate, for every slot, its waiting hits in whole 32-wide chunks (all of them when
+    // `last`), keeping the remainder at the front of the list.
+    auto flush = [&](bool last) {
+      for (int s = 0; s < ni; ++s) {
+        const int c = int((cnts >> (8 * s)) & 0xffu);
+        const int upto = last ? c : (c & ~31);
+        if (upto == 0) continue;   // uniform
+        const int i = i0 + s;
+        Ion I;
+        const float4 mi4 = a.pr.mu[i];
+        I.mu = mk(mi4.x, mi4.y, mi4.z);
+        I.q = mi4.w;
+        I.dq = 0.f;
+        I.gE = gE;
+        I.dr = mk(0.f, 0.f, 0.f);
+        I.w = mk(0.f, 0.f, 0.f);
+        if (TAN) {
+          const float4 t = a.pr.tq[i];
+          const float4 d = a.pr.dr[i];
+          I.dq = t.x;
+          I.dr = mk(d.x, d.y, d.z);
+          I.w = gE * I.mu + mk(t.y, t.z, t.w);   // gE mu + dmu + q dr
+        }
+        Acc<TAN> A;
+        float* ap = &s_acc[w][s][0][lane];
+        acc_load<TAN>(A, ap);
+        for (int k = lane; k < upto; k += 32) {
+          const float4 h = s_hit[w][s][k];
+          interact<TAN>(a, I, __float_as_int(h.w), mk(h.x, h.y, h.z), A);
+        }
+        acc_store<TAN>(A, ap);
+        __syncwarp();
+        const int rest = c - upto;
+        if (lane < rest) {   // [0, rest) and [upto, c) do not overlap: upto >= 32 > rest
+          s_hit[w][s][lane] = s_hit[w][s][upto + lane];
+        }
+        __syncwarp();
+        cnts = (cnts & ~(0xffu << (8 * s))) | (unsigned(rest) << (8 * s));
+      }
+    };
+
+    // ---- dense candidate stream ---------------------------------------------------------
+    // A segment is one (ox, oy[, oz]) neighbour column: the ions of one or two contiguous
+    // ranges of the cell order. Lane l describes segment (32 g + l) of group g; a warp scan of
+    // the lengths places the segments back to back, each lane lists its own segment's ions
+    // (tagged with the lane) in shared memory, and the warp then walks the list 32 candidates
+    // at a time, loading the next chunk's records while it tests the current one.
+    for (int g0 = 0; g0 < nseg; g0 += 32) {
+      const int sidx = g0 + lane;
+      int loA = 0, lenA = 0, loB = 0, lenB = 0, code = 0;
+      if (sidx < nseg) {
+        const int oz = zrun ? 0 : (sidx % nzs) - kz;
+        const int t = sidx / nzs;
+        const int oy = (t % (2 * ky + 1)) - ky;
+        const int ox = (t / (2 * ky + 1)) - kx;
+        int cx = (cix + ox) % ncx, cy = (ciy + oy) % ncy;
+        if (cx < 0) cx += ncx;
+        if (cy < 0) cy += ncy;
+        const int row = F.cell_off + (cx * ncy + cy) * ncz;
+        if (zrun) {
+          const int z0 = ciz - kz, z1 = ciz + kz;
+          if (z0 < 0) {
+            loA = a.start_c[row + z0 + ncz]; lenA = a.start_c[row + ncz] - loA;
+            loB = a.start_c[row]; lenB = a.start_c[row + z1 + 1] - loB;
+          } else if (z1 >= ncz) {
+            loA = a.start_c[row + z0]; lenA = a.start_c[row + ncz] - loA;
+            loB = a.start_c[row]; lenB = a.start_c[row + z1 - ncz + 1] - loB;
+          } else {
+            loA = a.start_c[row + z0]; lenA = a.start_c[row + z1 + 1] - loA;
+          }
+        } else {
+          int cz = (ciz + oz) % ncz;
+          if (cz < 0) cz += ncz;
+          loA = a.start_c[row + cz]; lenA = a.start_c[row + cz + 1] - loA;
+        }
+        // offsets packed in one int: 10 bits each, biased by 512
+        code = ((ox + 512) << 20) | ((oy + 512) << 10) | (oz + 512);
+      }
+      s_code[w][lane] = code;
+      const int len = lenA + lenB;
+      int pre = len;   // inclusive scan over the group's segments
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += u;
+      }
+      const int total = __shfl_sync(0xffffffffu, pre, 31);
+      for (int piece = 0; piece < total; piece += kCandCap) {
+        const int npc = min(kCandCap, total - piece);
+        {
+          const int first = pre - len;
+          const int lo = max(first, piece), hi = min(pre, piece + kCandCap);
+          const unsigned tag = unsigned(lane) << kSegShift;
+          for (int c = lo; c < hi; ++c) {
+            const int off = c - first;
+            s_cand[w][c - piece] = tag | unsigned(off < lenA ? loA + off : loB + (off - lenA));
+          }
+        }
+        __syncwarp();
+        unsigned e = lane < npc ? s_cand[w][lane] : 0u;
+        float4 fj = lane < npc ? a.pr.fq[e & ((1u << kSegShift) - 1u)] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int base = 0; base < npc; base += 32) {
+          // records of the next chunk, in flight while this one is tested
+          const int kn = base + 32 + lane;
+          const unsigned en = kn < npc ? s_cand[w][kn] : 0u;
+          const float4 fjn = kn < npc ? a.pr.fq[en & ((1u << kSegShift) - 1u)] : make_float4(0.f, 0.f, 0.f, 0.f);
+          const bool valid = base + lane < npc;
+          const int j = int(e & ((1u << kSegShift) - 1u));
+          const int scode = s_code[w][e >> kSegShift];
+          const int ox = ((scode >> 20) & 1023) - 512;
+          const int oy = ((scode >> 10) & 1023) - 512;
+          int oz = (scode & 1023) - 512;
+          if (zrun) {
+            oz = __float_as_int(fj.w) - ciz;
+            if (oz > kz) oz -= ncz;
+            else if (oz < -kz) oz += ncz;
+          }
+          // u = (offset of i) - (offset of j) - (cell offset), in cell units
+          const float bx = -fj.x - float(ox), by = -fj.y - float(oy), bz = -fj.z - float(oz);
+          const bool self_cell = ox == 0 && oy == 0 && oz == 0;
+          bool any_full = false;
+#pragma unroll
+          for (int s = 0; s < kSlots; ++s) {
+            const float4 fi = s_fi[w][s];
+            const float ux = fi.x + bx, uy = fi.y + by, uz = fi.z + bz;
+            V3 r;
+            if constexpr (ORTHO) {
+              r = mk(ux * g.H[0], uy * g.H[4], uz * g.H[8]);
+            } else {
+              r = mk(ux * g.H[0] + uy * g.H[3] + uz * g.H[6], ux * g.H[1] + uy * g.H[4] + uz * g.H[7],
+                     ux * g.H[2] + uy * g.H[5] + uz * g.H[8]);
+            }
+            const bool hit = valid && s < ni && dot(r, r) < g.rcut2 &&
+                             !(self_cell && j == __float_as_int(fi.w));
+            const unsigned bal = __ballot_sync(0xffffffffu, hit);
+            if (hit) s_hit[w][s][cnt[s] + __popc(bal & lane_lt)] = make_float4(r.x, r.y, r.z, __int_as_float(j));
+            cnt[s] += __popc(bal);
+            any_full |= cnt[s] >= 32;
+          }
+          if (any_full) {
+            __syncwarp();
+            cnts = pack_counts(cnt);
+            flush(false);
+            unpack_counts(cnts, cnt);
+          }
+          e = en;
+          fj = fjn;
+        }
+        __syncwarp();
+      }
     }
+    __syncwarp();
+    cnts = pack_counts(cnt);
+    flush(true);
+
+    for (int s = 0; s < ni; ++s) {
+      const int orig = a.pr.idx[i0 + s].w;
+      const float* ap = &s_acc[w][s][0][0];
+      float v[NA];
+#pragma unroll
+      for (int k = 0; k < NA; ++k) v[k] = warp_sum(ap[32 * k + lane]);
+      if (lane == 0) {
+        float* o = a.out + size_t(orig) * (TAN ? 8 : 10);
+#pragma unroll
+        for (int k = 0; k < NA; ++k) o[k] = v[k];
+        if (TAN) o[7] = 0.f;
+      }
+    }
+    __syncwarp();
   }
+}
+
+template <bool TAN, bool BATCH>
+void launch_k(bool ortho, int grid, cudaStream_t s, const PairArgs& a) {
+  if (ortho) k_pair<TAN, BATCH, true><<<grid, kPairThreads, 0, s>>>(a);
+  else k_pair<TAN, BATCH, false><<<grid, kPairThreads, 0, s>>>(a);
 }
 
 }  // namespace
@@ -355,7 +454,13 @@ int launch_pair(pme_plan_t p, cudaStream_t s, int n, bool tangent, const IonInpu
   a.start_c = p->sb.start_c;
   a.g_energy = g_energy;
   a.out = out;
-  a.n = n;
+  if (p->batch) {
+    a.cell_lo = 0;
+    a.ncells = p->total_cells;
+  } else {
+    a.cell_lo = p->frames_h[0].cell_off;
+    a.ncells = p->frames_h[0].ncells;
+  }
   const double al = p->alpha;
   const double sp = 1.7724538509055160273;   // sqrt(pi)
   double t = 1.0 / (al * sp);
@@ -368,13 +473,19 @@ int launch_pair(pme_plan_t p, cudaStream_t s, int n, bool tangent, const IonInpu
   a.c2 = float(cl[2]);
   a.c3 = float(cl[3]);
   a.c4 = float(cl[4]);
-  const int grid = (n + kPairWarps - 1) / kPairWarps;
+  const int grid = (a.ncells + kPairWarps - 1) / kPairWarps;
+  if (grid == 0) return PME_OK;
+  bool ortho = true;
+  for (int f = 0; f < p->nframes && ortho; ++f) {
+    const float* H = p->frames_h[f].g.H;
+    ortho = H[1] == 0.f && H[2] == 0.f && H[3] == 0.f && H[5] == 0.f && H[6] == 0.f && H[7] == 0.f;
+  }
   if (p->batch) {
-    if (tangent) k_pair<true, true><<<grid, kPairThreads, 0, s>>>(a);
-    else k_pair<false, true><<<grid, kPairThreads, 0, s>>>(a);
+    if (tangent) launch_k<true, true>(ortho, grid, s, a);
+    else launch_k<false, true>(ortho, grid, s, a);
   } else {
-    if (tangent) k_pair<true, false><<<grid, kPairThreads, 0, s>>>(a);
-    else k_pair<false, false><<<grid, kPairThreads, 0, s>>>(a);
+    if (tangent) launch_k<true, false>(ortho, grid, s, a);
+    else launch_k<false, false>(ortho, grid, s, a);
   }
   count_launch();
   return check_launch(p, "k_pair");

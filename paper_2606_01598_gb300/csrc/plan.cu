@@ -258,7 +258,7 @@ static void free_plan(pme_plan_t p) {
                   p->sb.slot_b, p->sb.slot_c, p->sb.count_b, p->sb.count_c, p->sb.start_b,
                   p->sb.start_c, p->sb.perm_b, p->sb.perm_c, p->sb.qsum, p->mr.idx, p->mr.fq,
                   p->mr.dm, p->mr.tq, p->mr.tt, p->pr.idx, p->pr.fq, p->pr.mu, p->pr.tq, p->pr.dr,
-                  p->pr.cz, p->mesh_out, p->pair_out, p->e_ion, p->epart, p->flags, p->stage_f,
+                  p->mesh_out, p->pair_out, p->e_ion, p->epart, p->flags, p->stage_f,
                   p->stage_d, p->ew_kn, p->ew_kv, p->ew_S, p->ew_fx, p->ew_qm, p->frames_d,
                   p->map_buf, p->fft_work, p->sb.qpart, p->sb.qcount, p->eitem, p->ecount};
   for (void* b : bufs)
@@ -357,6 +357,7 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
   if (!p->frames_h || !p->frame_offsets) return set_error(p, PME_ERR_NOMEM, "host tables");
   std::memset(p->frames_h, 0, sizeof(FrameDesc) * F);
   const bool pair = p->opts.include_pair != 0;
+  if (p->max_ions > (1 << 27)) return set_error(p, PME_ERR_UNSUPPORTED, "more than 2^27 ions in one plan");
   int brick[3];
   spread_brick_shape(brick);
   std::vector<int> ncells(F);
@@ -526,7 +527,6 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
   A(&p->pr.mu, ni);
   A(&p->pr.tq, ni);
   A(&p->pr.dr, ni);
-  A(&p->pr.cz, ni);
   A(&p->mesh_out, ni * 10);
   A(&p->pair_out, ni * 10);
   A(&p->e_ion, ni);

@@ -236,9 +236,8 @@ k_rank_records(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, Mesh
 #pragma unroll
     for (int b = 0; b < 3; ++b) cell_origin(s[b], g.ncell[b], c[b], fr[b]);
     pr.idx[dest] = make_int4(c[0], c[1], c[2], i);
-    pr.cz[dest] = c[2];
-    pr.fq[dest] = make_float4(fr[0], fr[1], fr[2], qi);
-    pr.mu[dest] = make_float4(mu[0], mu[1], mu[2], 0.f);
+    pr.fq[dest] = make_float4(fr[0], fr[1], fr[2], __int_as_float(c[2]));
+    pr.mu[dest] = make_float4(mu[0], mu[1], mu[2], qi);
     if (tangent) {
       pr.tq[dest] = make_float4(dq, dp[0], dp[1], dp[2]);
       pr.dr[dest] = make_float4(dr[0], dr[1], dr[2], 0.f);
