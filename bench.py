@@ -14,6 +14,13 @@ ions all ranks processed divided by the slowest rank's time.
 
 The reference arm (--impl reference) times the float64 CPU oracle (plain PME in torch CPU
 ops with autograd double backward), as it stands, on this machine's host cores.
+
+Beside the value the line carries: the dominant kernel's roofline; per-stage times from a
+serialised pass; "vs_plain", the mesh-only step of this library against the paper's own
+formulation written in PyTorch ops (index_put_ scatter, rfftn, autograd and double backward)
+on the same GPU; "mesh_rooflines_batch16", spread / gather / influence over 16 frames of
+the 32k workload in one batched launch per stage (working set above L2); the end-to-end
+number through host buffers; and the CPU oracle baseline.
 """
 from __future__ import annotations
 
@@ -216,6 +223,201 @@ def config_dict(cfg, fr, ws):
             "l2": "flushed between timed steps (256 MB write)"}
 
 
+def plain_pme(box, mesh, order, alpha, dev):
+    """The "plain" comparator: the paper's own formulation in PyTorch ops on the GPU, float32,
+    mesh part only (the paper's network has no pair term). B-spline weights come from the
+    recursion, the charge + dipole density (Eq. charge_dipole_assign) is scattered with
+    index_put_(accumulate=True), then rfftn, the deconvolved influence function and
+    Eq. energy_recip; forces, dE/dq and the field come from autograd and the backward of a
+    force-matching loss from the double backward. Returns step(pos, q, mu, gE, gF, gphi,
+    gfield) -> (E, F, phi, field, grad_pos, grad_q, grad_mu). Measurement only: it is not part
+    of the library."""
+    import numpy as np
+    import torch
+
+    p = int(order)
+    Nx, Ny, Nz = (int(v) for v in mesh)
+    C = np.asarray(box, dtype=np.float64)
+    Ci = np.linalg.inv(C)
+    V = abs(float(np.linalg.det(C)))
+    Cinv = torch.tensor(Ci, dtype=torch.float32, device=dev)
+    Nvec = torch.tensor([Nx, Ny, Nz], dtype=torch.float32, device=dev)
+    D = torch.tensor(Ci * np.array([Nx, Ny, Nz])[None, :], dtype=torch.float32, device=dev)
+    # influence G C with half-spectrum weights, on the rfft grid [Nx][Ny][Nz/2+1]
+    def signed(n):
+        return np.where(np.arange(n) <= n // 2, np.arange(n), np.arange(n) - n).astype(np.float64)
+    nx, ny, nz = signed(Nx), signed(Ny), np.arange(Nz // 2 + 1, dtype=np.float64)
+    n3 = np.stack(np.meshgrid(nx, ny, nz, indexing="ij"), -1)
+    k = 2 * np.pi * n3 @ Ci.T
+    k2 = (k * k).sum(-1)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        G = np.where(k2 > 0, 4 * np.pi * np.exp(-k2 / (4 * alpha * alpha)) / k2, 0.0)
+    def sinc(x):
+        return np.where(x == 0, 1.0, np.sin(np.pi * x) / np.where(x == 0, 1.0, np.pi * x))
+    B = (sinc(nx / Nx)[:, None, None] * sinc(ny / Ny)[None, :, None] * sinc(nz / Nz)[None, None, :]) ** p
+    w = np.where((nz == 0) | (2 * nz == Nz), 1.0, 2.0)[None, None, :]
+    GCw = torch.tensor(G / (B * B) * w, dtype=torch.float32, device=dev)
+    ar = torch.arange(p, device=dev)
+    sp = math.sqrt(math.pi)
+
+    def weights(f):
+        # M_k(f + i), i = 0..k-1, by M_k(y) = (y M_{k-1}(y) + (k - y) M_{k-1}(y - 1)) / (k - 1)
+        m = torch.ones_like(f).unsqueeze(-1)
+        dm = None
+        for kk in range(2, p + 1):
+            z = torch.zeros_like(f).unsqueeze(-1)
+            a, b = torch.cat([m, z], -1), torch.cat([z, m], -1)
+            y = f.unsqueeze(-1) + torch.arange(kk, device=dev, dtype=f.dtype)
+            if kk == p:
+                dm = a - b
+            m = (y * a + (kk - y) * b) / (kk - 1)
+        if p == 1:
+            dm = torch.zeros_like(m)
+        # stencil point j sits at t_j = f + p/2 - 1 - j: W(t_j) = M_p(f + p - 1 - j)
+        return m.flip(-1), dm.flip(-1)
+
+    def energy(pos, q, mu):
+        s = pos @ Cinv
+        s = s - torch.floor(s)
+        x = s * Nvec
+        u = x - 0.5 * p + 1.0
+        m0 = torch.floor(u)
+        f = u - m0
+        W, dW = weights(f)                                   # [n, 3, p]
+        pm = mu @ D                                          # N_a (mu . C^-1_{:a})
+        Wx, Wy, Wz = W[:, 0, :, None, None], W[:, 1, None, :, None], W[:, 2, None, None, :]
+        dWx, dWy, dWz = dW[:, 0, :, None, None], dW[:, 1, None, :, None], dW[:, 2, None, None, :]
+        vals = (q[:, None, None, None] * Wx * Wy * Wz + pm[:, 0, None, None, None] * dWx * Wy * Wz
+                + pm[:, 1, None, None, None] * Wx * dWy * Wz + pm[:, 2, None, None, None] * Wx * Wy * dWz)
+        mi = m0.long()
+        ix = (mi[:, 0, None] + ar) % Nx
+        iy = (mi[:, 1, None] + ar) % Ny
+        iz = (mi[:, 2, None] + ar) % Nz
+        flat = (ix[:, :, None, None] * Ny + iy[:, None, :, None]) * Nz + iz[:, None, None, :]
+        rho = torch.zeros(Nx * Ny * Nz, dtype=pos.dtype, device=dev)
+        rho = rho.index_put((flat.reshape(-1),), vals.reshape(-1), accumulate=True)
+        rh = torch.fft.rfftn(rho.view(Nx, Ny, Nz))
+        e_rec = (GCw * (rh.real * rh.real + rh.imag * rh.imag)).sum() / (2 * V)
+        e_self = -alpha / sp * (q * q).sum() - 2 * alpha ** 3 / (3 * sp) * (mu * mu).sum()
+        Q = q.sum()
+        return e_rec + e_self - math.pi * Q * Q / (2 * V * alpha * alpha)
+
+    def step(pos, q, mu, gE, gF, gphi, gfield):
+        pos = pos.detach().requires_grad_(True)
+        q = q.detach().requires_grad_(True)
+        mu = mu.detach().requires_grad_(True)
+        E = energy(pos, q, mu)
+        gr, gq, gm = torch.autograd.grad(E, (pos, q, mu), create_graph=True)
+        F, phi, field = -gr, gq, -gm
+        L = gE * E + (gF * F).sum() + (gphi * phi).sum() + (gfield * field).sum()
+        g = torch.autograd.grad(L, (pos, q, mu))
+        return (E.detach(), F.detach(), phi.detach(), field.detach()) + tuple(g)
+
+    return step
+
+
+def time_steps(torch, fn, steps, warmup, dev, flush):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize(dev)
+    a = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    b = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        a[k].record()
+        fn()
+        b[k].record()
+    torch.cuda.synchronize(dev)
+    return sum(x.elapsed_time(y) for x, y in zip(a, b)) / steps
+
+
+def vs_plain(gb, fr, cfg, dev, pos, q, mu, gE, gF, gphi, gfield, flush, steps):
+    """Mesh-only forward + backward: this library (pair term off) against the plain PyTorch-ops
+    formulation of the paper on the same GPU and frame."""
+    import torch
+    plan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=fr.n, device=dev,
+                   include_pair=False)
+    plain = plain_pme(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], dev)
+    gE32 = gE.float()
+
+    def ours():
+        plan.forward(pos, q, mu, energy=True, force=True, phi=True, field=True)
+        plan.backward(pos, q, mu, gE, gF, gphi, gfield)
+
+    def theirs():
+        plain(pos, q, mu, gE32, gF, gphi, gfield)
+
+    k = max(3, steps // 4)
+    t_ours = time_steps(torch, ours, k, 3, dev, flush)
+    t_plain = time_steps(torch, theirs, k, 2, dev, flush)
+    e_ours = plan.forward(pos, q, mu)["energy"].item()
+    e_plain = float(plain(pos, q, mu, gE32, gF, gphi, gfield)[0])
+    plan.close()
+    n = fr.n
+    return {"what": "mesh part only (pair term off), fwd + bwd on the same frame and GPU",
+            "plain": "PyTorch ops in the paper's formulation (index_put_ scatter, rfftn, autograd "
+                     "forces and double backward), float32",
+            "plain_ms_per_step": t_plain, "ours_ms_per_step": t_ours,
+            "plain_Mion_evals_per_s": n / (t_plain / 1e3) / 1e6,
+            "ours_Mion_evals_per_s": n / (t_ours / 1e3) / 1e6,
+            "speedup": t_plain / t_ours, "energy_rel_diff": abs(e_ours - e_plain) / abs(e_plain),
+            "steps": k}
+
+
+def batch16_rooflines(gb, fr, cfg, dev, steps):
+    """Spread / gather / influence rooflines over 16 frames of the 32k workload in one batched
+    launch per stage (working set well above L2). The frames are translated, axis-permuted
+    copies of the benchmark frame: same statistics, different ion-to-brick layouts."""
+    import numpy as np
+    import torch
+    import workloads as W
+
+    F = 16
+    rng = np.random.default_rng(4242)
+    L = np.diag(fr.box)
+    pos, q, mu = [], [], []
+    for f in range(F):
+        perm = rng.permutation(3)
+        pf = (fr.pos[:, perm] + rng.uniform(0, 1, 3) * L) % L
+        pos.append(pf)
+        q.append(fr.q)
+        mu.append(fr.mu[:, perm])
+    n = fr.n
+    offsets = np.arange(F + 1, dtype=np.int64) * n
+    c = lambda x: torch.tensor(np.float32(np.concatenate(x)), device=dev)
+    P, Qv, MU = c(pos), c(q), c(mu)
+    gF, gphi, gfield = (torch.tensor(np.float32(x), device=dev) for x in W.tangent(F * n, seed=17))
+    gE = torch.full((F,), 0.5, dtype=torch.float64, device=dev)
+    bp = gb.BatchPlan([fr.box] * F, [cfg["mesh"]] * F, [cfg["order"]] * F, offsets, cfg["alpha"], cfg["rcut"],
+                      device=dev, overlap_pair=False)
+    for _ in range(2):
+        bp.forward(P, Qv, MU)
+        bp.backward(P, Qv, MU, gE, gF, gphi, gfield)
+    torch.cuda.synchronize(dev)
+    bp.profile(True)
+    k = max(3, steps // 4)
+    for _ in range(k):
+        bp.forward(P, Qv, MU)
+        bp.backward(P, Qv, MU, gE, gF, gphi, gfield)
+    torch.cuda.synchronize(dev)
+    st = bp.profile_read()
+    bp.profile(False)
+    bp.close()
+    peak, kind = load_peaks()
+    M = int(np.prod(cfg["mesh"]))
+    Mh = cfg["mesh"][0] * cfg["mesh"][1] * (cfg["mesh"][2] // 2 + 1)
+    out = {}
+    for stage in ("fwd.spread", "bwd.spread", "fwd.gather", "bwd.gather", "fwd.influence", "bwd.influence"):
+        if stage not in st:
+            continue
+        avg = st[stage][0] / st[stage][1]
+        by = F * stage_bytes(stage, n, M, Mh)
+        ach = by / (avg / 1e3) / 1e9
+        out[stage] = {"avg_launch_ms": round(avg, 5), "bytes_per_launch": by, "achieved": round(ach, 1),
+                      "frac": round(ach / peak, 4)}
+    return {"frames": F, "ions_per_frame": n, "peak_gbs": peak, "peak_source": kind, "stages": out}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -328,6 +530,10 @@ def run_ours(args):
     h2d = 2 * (12 + 4 + 12) * n + (12 + 4 + 12) * n + 8
     d2h = 8 + (12 + 4 + 12) * n + (12 + 4 + 12) * n
     clocks = sampler.stop()
+    plain = b16 = None
+    if rank == 0 and not args.no_extras:
+        plain = vs_plain(gb, fr, cfg, dev, pos, q, mu, gE, gF, gphi, gfield, flush, args.steps)
+        b16 = batch16_rooflines(gb, fr, cfg, dev, args.steps)
 
     if rank == 0:
         # ---- roofline of the dominant kernel (stage timers of the timed region) ------------
@@ -369,6 +575,8 @@ def run_ours(args):
             "mesh_rooflines": {k: {"achieved": round(v["achieved"], 1), "frac": round(v["frac"], 4),
                                    "avg_launch_ms": round(v["avg_launch_ms"], 5)}
                                for k, v in mesh_kernels.items()},
+            "mesh_rooflines_batch16": b16,
+            "vs_plain": plain,
             "cpu_baseline": cpu,
             "e2e": {"value": e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e_ms},
@@ -542,6 +750,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="nacl32k")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the plain-PyTorch comparator and the 16-frame roofline")
     ap.add_argument("--crossover", action="store_true", help="Ewald vs PME timing sweep")
     ap.add_argument("--batch", action="store_true", help="uneven batch vs per-frame loop")
     ap.add_argument("--frames", type=int, default=256)

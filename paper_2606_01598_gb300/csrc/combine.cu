@@ -8,11 +8,15 @@
 //   force      = q field + field_grad mu                               (= -dE/dr)
 // where the c terms remove the ion's own screening cloud (for mu they are the derivative of
 // Eq. self_mu; for the field gradient the analogous part of the reciprocal sum), so field
-// and field_grad are those of all other sources. Per-ion float64 energy contributions
-// 1/2 (q phi_pair + mu . grad phi_pair) + self energies are summed per frame afterwards.
+// and field_grad are those of all other sources. The per-ion float64 energy contributions
+// 1/2 (q phi_pair + mu . grad phi_pair) + self energies are summed per reduction item (one
+// block of kRedItem ions), and the item of each frame that finishes last adds the item sums,
+// the frame's reciprocal-space partials and the background energy in a fixed order.
 //
 // Backward, per ion: grad = k (mesh part + pair part) + the self and background terms of
 // the g_E-weighted gradient and of the Hessian-vector product.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace gbpme {
@@ -45,6 +49,13 @@ struct CombineArgs {
   float alpha;
   double e_self_q;    // alpha / sqrt(pi)
   double e_self_mu;   // 2 alpha^3 / (3 sqrt(pi))
+  // frame energies (forward; energy_out null: not wanted)
+  double* energy_out;
+  const double* recip_parts;
+  int recip_kind;     // 0 none, 1 mesh (1/2V), 2 explicit k-sum (4 pi / V)
+  double kd;          // coulomb_k
+  double* eitem;
+  int* ecount;
 };
 
 // pi / (V alpha^2) of the ion's frame, or 0 without the background term
@@ -54,10 +65,15 @@ __device__ __forceinline__ float bg_factor(const CombineArgs& a, const FrameDesc
 
 template <bool BATCH>
 __global__ void __launch_bounds__(kCombThreads) k_combine_forward(CombineArgs a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < a.in.n) {
-    const int f = BATCH ? a.maps.ion_frame[i] : 0;
-    const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, f);
+  static_assert(kRedItem == kCombThreads, "one ion per thread");
+  const int item = blockIdx.x;
+  const int f = BATCH ? a.maps.item_frame[item] : 0;
+  const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, f);
+  int lo, hi;
+  item_range(F, item, lo, hi);
+  const int i = lo + int(threadIdx.x);
+  double e_i = 0.0;
+  if (i < hi) {
     const float bg = bg_factor(a, F);
     float qi = a.in.q[i];
     float mu[3] = {0.f, 0.f, 0.f};
@@ -100,9 +116,30 @@ __global__ void __launch_bounds__(kCombThreads) k_combine_forward(CombineArgs a)
       a.force[3 * i + 2] = F2;
     }
     const double mu2 = double(mu[0]) * mu[0] + double(mu[1]) * mu[1] + double(mu[2]) * mu[2];
-    a.e_ion[i] = 0.5 * (double(qi) * w[0] + double(mu[0]) * w[1] + double(mu[1]) * w[2] +
-                        double(mu[2]) * w[3]) -
-                 a.e_self_q * double(qi) * qi - a.e_self_mu * mu2;
+    e_i = 0.5 * (double(qi) * w[0] + double(mu[0]) * w[1] + double(mu[1]) * w[2] +
+                 double(mu[2]) * w[3]) -
+          a.e_self_q * double(qi) * qi - a.e_self_mu * mu2;
+  }
+  if (!a.energy_out) return;   // uniform
+  const double e_item = block_sum_d(e_i);
+  if (threadIdx.x == 0) a.eitem[item] = e_item;
+  if (!last_item_done(a.ecount + f, F.nitems)) return;
+  double rp = 0.0, ep = 0.0;
+  if (a.recip_kind)
+    for (int k = threadIdx.x; k < F.infl_nblk; k += blockDim.x) rp += a.recip_parts[F.infl_blk_off + k];
+  for (int k = threadIdx.x; k < F.nitems; k += blockDim.x) ep += __ldcg(a.eitem + F.item_off + k);
+  rp = block_sum_d(rp);
+  ep = block_sum_d(ep);
+  if (threadIdx.x == 0) {
+    const double V = F.g.volume;
+    const double coef = a.recip_kind == 1 ? 0.5 / V : (a.recip_kind == 2 ? 4.0 * kPi / V : 0.0);
+    double e_bg = 0.0;
+    if (a.with_bg) {
+      const double Q = a.qsum[2 * f];
+      e_bg = -kPi * Q * Q / (2.0 * V * double(a.alpha) * double(a.alpha));
+    }
+    a.energy_out[f] = a.kd * (coef * rp + ep + e_bg);
+    a.ecount[f] = 0;
   }
 }
 
@@ -184,7 +221,7 @@ CombineArgs base_args(pme_plan_t p, const IonInputs& in) {
 
 int launch_combine_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool with_mesh,
                            bool with_pair, float* force, float* phi, float* field,
-                           float* field_grad) {
+                           float* field_grad, double* energy, int recip_kind) {
   CombineArgs a = base_args(p, in);
   a.mesh_out = p->mesh_out;
   a.pair_out = p->pair_out;
@@ -194,10 +231,23 @@ int launch_combine_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, bo
   a.phi = phi;
   a.field = field;
   a.field_grad = field_grad;
-  const int grid = (in.n + kCombThreads - 1) / kCombThreads;
-  if (grid == 0) return PME_OK;
-  if (p->batch) k_combine_forward<true><<<grid, kCombThreads, 0, s>>>(a);
-  else k_combine_forward<false><<<grid, kCombThreads, 0, s>>>(a);
+  a.energy_out = energy;
+  a.recip_parts = p->epart;
+  a.recip_kind = recip_kind;
+  a.kd = p->opts.coulomb_k;
+  a.eitem = p->eitem;
+  a.ecount = p->ecount;
+  int items;
+  if (p->batch) {
+    items = p->total_items;
+  } else {
+    a.one.n = in.n;
+    a.one.item_off = 0;
+    a.one.nitems = std::max(1, (in.n + kRedItem - 1) / kRedItem);
+    items = a.one.nitems;
+  }
+  if (p->batch) k_combine_forward<true><<<items, kCombThreads, 0, s>>>(a);
+  else k_combine_forward<false><<<items, kCombThreads, 0, s>>>(a);
   count_launch();
   return check_launch(p, "k_combine_forward");
 }

@@ -17,9 +17,9 @@ constexpr int kMaxOrder = 7;
 constexpr int kMaxCandPerDim = 4;   // bricks along one axis that can feed one brick's stencils
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kProfCap = 4096;
-// Ions per item of the per-frame float64 sums (charges, energies): a frame of n ions is split
-// into max(1, ceil(n / kRedItem)) items, one block each.
-constexpr int kRedItem = 2048;
+// Ions per item of the per-frame sums (charges, energies): a frame of n ions is split into
+// max(1, ceil(n / kRedItem)) items, one 256-thread block each (one ion per thread).
+constexpr int kRedItem = 256;
 
 // ----------------------------------------------------------------------------------------
 // launch bookkeeping
@@ -79,6 +79,7 @@ struct SortBuffers {
   int* perm_c;
   double* qpart;  // [2 * items] Q and dQ of each reduction item
   int* qcount;    // [frames] items finished (reset by the last one); null: no charge sums wanted
+  int* gcount;    // [1] blocks of the binning pass finished (reset by the last one)
   double* qsum;   // [2 * frames] Q and dQ of each frame
 };
 
@@ -359,6 +360,28 @@ __device__ __forceinline__ bool last_item_done(int* count, int nitems) {
   const bool last = s_last != 0;
   if (last) __threadfence();
   return last;
+}
+
+// Sum of one float per thread over the block: Neumaier-compensated within each warp, float64
+// across the warps; fixed order; valid in thread 0. (blockDim.x a multiple of 32, <= 1024)
+__device__ __forceinline__ double block_sum_f(float v) {
+  __shared__ double wpart[32];
+  float c = 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
+    const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    const float t = v + v2;
+    c += c2 + (fabsf(v) >= fabsf(v2) ? (v - t) + v2 : (v2 - t) + v);
+    v = t;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) wpart[threadIdx.x >> 5] = double(v) + double(c);
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) r += wpart[w];
+  return r;
 }
 
 // Ion range [lo, hi) of reduction item `item` of frame F.

@@ -48,10 +48,12 @@ int launch_gather(pme_plan_t p, cudaStream_t s, int n, const float* mesh, bool t
 int launch_pair(pme_plan_t p, cudaStream_t s, int n, bool tangent, const IonInputs& in,
                 const double* g_energy, float* out);
 
-// combine.cu: add the parts, the self and background terms, apply coulomb_k, write outputs.
+// combine.cu: add the parts, the self and background terms, apply coulomb_k, write outputs;
+// with energy non-null also the frame energies, as launch_energy_final with the per-ion
+// energies of this pass (recip_kind as there).
 int launch_combine_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool with_mesh,
                            bool with_pair, float* force, float* phi, float* field,
-                           float* field_grad);
+                           float* field_grad, double* energy, int recip_kind);
 int launch_combine_backward(pme_plan_t p, cudaStream_t s, const IonInputs& in,
                             const double* g_energy, float* grad_pos, float* grad_q,
                             float* grad_mu);

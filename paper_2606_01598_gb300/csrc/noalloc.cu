@@ -198,11 +198,12 @@ extern "C" int pme_spread_noalloc(void* stream, const double box[9], const int m
   v.mr.tt = nullptr;
   v.cand = reinterpret_cast<int*>(base + kOffCand);
   v.flags = reinterpret_cast<int*>(base + kOffFlags);
+  v.sb.gcount = v.flags + 1;   // the binning pass's block counter shares the flag's 256 bytes
   // the candidate table and the error flag are per call: rewrite / clear them first
   if (cudaMemcpyAsync(v.cand, cand, sizeof(int) * 3 * fd.max_nb * (1 + kMaxCandPerDim),
                       cudaMemcpyHostToDevice, s) != cudaSuccess)
     return PME_ERR_CUDA;
-  if (cudaMemsetAsync(v.flags, 0, sizeof(int), s) != cudaSuccess) return PME_ERR_CUDA;
+  if (cudaMemsetAsync(v.flags, 0, 2 * sizeof(int), s) != cudaSuccess) return PME_ERR_CUDA;
   IonInputs in{};
   in.pos = pos;
   in.q = q;

@@ -260,7 +260,7 @@ static void free_plan(pme_plan_t p) {
                   p->mr.dm, p->mr.tq, p->mr.tt, p->pr.idx, p->pr.fq, p->pr.mu, p->pr.tq, p->pr.dr,
                   p->mesh_out, p->pair_out, p->e_ion, p->epart, p->flags, p->stage_f,
                   p->stage_d, p->ew_kn, p->ew_kv, p->ew_S, p->ew_fx, p->ew_qm, p->frames_d,
-                  p->map_buf, p->fft_work, p->sb.qpart, p->sb.qcount, p->eitem, p->ecount};
+                  p->map_buf, p->fft_work, p->sb.qpart, p->sb.qcount, p->eitem, p->ecount, p->sb.gcount};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int g = 0; g < p->nfgroups; ++g) {
@@ -515,6 +515,7 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
   A(&p->sb.qsum, size_t(2) * F);
   A(&p->sb.qpart, size_t(2) * p->total_items);
   A(&p->sb.qcount, size_t(F));
+  A(&p->sb.gcount, 1);
   A(&p->eitem, size_t(p->total_items));
   A(&p->ecount, size_t(F));
   A(&p->mr.idx, ni);
@@ -538,6 +539,7 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
   if (st) return st;
   if ((st = check_cuda(p, cudaMemset(p->flags, 0, sizeof(int)), "memset"))) return st;
   if ((st = check_cuda(p, cudaMemset(p->sb.qcount, 0, sizeof(int) * F), "memset"))) return st;
+  if ((st = check_cuda(p, cudaMemset(p->sb.gcount, 0, sizeof(int)), "memset"))) return st;
   if ((st = check_cuda(p, cudaMemset(p->ecount, 0, sizeof(int) * F), "memset"))) return st;
   // candidate tables and deconvolution tables, frame by frame
   {
@@ -675,12 +677,8 @@ static int forward_ewald(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool
   prof_end(p, t, s);
   if (fork && p->opts.overlap_pair && (st = join_side(p, s))) return st;
   t = prof_begin(p, 7, s);
-  if ((st = launch_combine_forward(p, s, in, true, fork, f_out, p_out, fl_out, fg_out))) return st;
+  if ((st = launch_combine_forward(p, s, in, true, fork, f_out, p_out, fl_out, fg_out, e_out, 2))) return st;
   prof_end(p, t, s);
-  if (e_out &&
-      (st = launch_energy_final(p, s, p->epart, 2, n > 0, p->opts.include_background != 0,
-                                p->opts.coulomb_k, n, e_out)))
-    return st;
   return PME_OK;
 }
 
@@ -720,15 +718,8 @@ static int run_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, double
   prof_end(p, t, s);
   if (fork && p->opts.overlap_pair && (st = join_side(p, s))) return st;
   t = prof_begin(p, 7, s);
-  if ((st = launch_combine_forward(p, s, in, true, fork, f_out, p_out, fl_out, fg_out))) return st;
+  if ((st = launch_combine_forward(p, s, in, true, fork, f_out, p_out, fl_out, fg_out, e_out, 1))) return st;
   prof_end(p, t, s);
-  if (e_out) {
-    t = prof_begin(p, 8, s);
-    if ((st = launch_energy_final(p, s, p->epart, 1, n > 0, p->opts.include_background != 0,
-                                  p->opts.coulomb_k, n, e_out)))
-      return st;
-    prof_end(p, t, s);
-  }
   return PME_OK;
 }
 

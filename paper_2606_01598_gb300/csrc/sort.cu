@@ -4,12 +4,12 @@
 // (Section 2.3.2, Eq. w3d) and the pair cell holding its position, both offset by its
 // frame's first global key, so that one counting sort orders every frame of a batch and the
 // ions of a frame stay contiguous. k_bin counts (one integer atomic per ion and key, never
-// per stencil point), k_scan turns the counts into segment starts, k_scatter places ions in
-// arrival order, and k_rank_records re-ranks each segment by caller index, which makes the
-// order -- and hence every later sum -- deterministic, while writing the per-ion records both
-// orders need. k_frame_sums adds up the charges (and tangent charges) of each frame in a fixed
-// order for the background term (the allocation-free spread, which has no use for them,
-// skips it).
+// per stencil point), adds up each frame's charges (and tangent charges) in a fixed order
+// for the background term, and its last block turns the counts into segment starts;
+// k_scatter places ions in arrival order, and k_rank_records re-ranks each segment by caller
+// index, which makes the order -- and hence every later sum -- deterministic, while writing
+// the per-ion records both orders need. (The allocation-free spread, which needs no charge
+// sums, skips them.)
 #include <algorithm>
 
 #include "kernels.h"
@@ -20,70 +20,6 @@ namespace {
 
 constexpr int kSortThreads = 256;
 constexpr int kRankMaxSegment = 2048;   // longer segments keep arrival order
-
-template <bool BATCH>
-__global__ void __launch_bounds__(kSortThreads)
-k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int* flags) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= in.n) return;
-  const int f = BATCH ? maps.ion_frame[i] : 0;
-  const FrameDesc& F = frame_at<BATCH>(one, maps, f);
-  const Geometry& g = F.g;
-  const float rx = in.pos[3 * i], ry = in.pos[3 * i + 1], rz = in.pos[3 * i + 2];
-  const float qi = in.q ? in.q[i] : 0.f;
-  bool ok = isfinite(rx) && isfinite(ry) && isfinite(rz) && isfinite(qi);
-  if (in.mu) ok = ok && isfinite(in.mu[3 * i]) && isfinite(in.mu[3 * i + 1]) && isfinite(in.mu[3 * i + 2]);
-  if (!ok) atomicOr(flags, kFlagNonFinite);
-  double s[3];
-  frac_coords(g, rx, ry, rz, s);
-  int m0[3], c[3];
-#pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    float fr;
-    stencil_origin(s[b], g.N[b], g.order, m0[b], fr);
-    cell_origin(s[b], g.ncell[b], c[b], fr);
-  }
-  const int kb = F.brick_off + ((m0[0] / g.brick[0]) * g.nb[1] + m0[1] / g.brick[1]) * g.nb[2] +
-                 m0[2] / g.brick[2];
-  const int kc = F.cell_off + (c[0] * g.ncell[1] + c[1]) * g.ncell[2] + c[2];
-  sb.key_b[i] = kb;
-  sb.key_c[i] = kc;
-  sb.slot_b[i] = atomicAdd(&sb.count_b[kb], 1);
-  sb.slot_c[i] = atomicAdd(&sb.count_c[kc], 1);
-}
-
-// Q and dQ of every frame in a fixed order: one block per reduction item, and the last item
-// of each frame to finish adds the item partials in order.
-template <bool BATCH>
-__global__ void __launch_bounds__(kSortThreads)
-k_frame_sums(FrameDesc one, FrameMaps maps, IonInputs in, int tangent, SortBuffers sb) {
-  const int item = blockIdx.x;
-  const int f = BATCH ? maps.item_frame[item] : 0;
-  const FrameDesc& F = frame_at<BATCH>(one, maps, f);
-  int lo, hi;
-  item_range(F, item, lo, hi);
-  double a = 0.0, b = 0.0;
-  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const float qi = in.q ? in.q[i] : 0.f;
-    if (isfinite(qi)) a += double(qi);
-    if (tangent && in.gphi) b += double(in.gphi[i]);
-  }
-  a = block_sum_d(a);
-  b = block_sum_d(b);
-  if (threadIdx.x == 0) {
-    sb.qpart[2 * item] = a;
-    sb.qpart[2 * item + 1] = b;
-  }
-  if (!last_item_done(sb.qcount + f, F.nitems) || threadIdx.x != 0) return;
-  double A = 0.0, B = 0.0;
-  for (int k = 0; k < F.nitems; ++k) {
-    A += __ldcg(sb.qpart + 2 * (F.item_off + k));
-    B += __ldcg(sb.qpart + 2 * (F.item_off + k) + 1);
-  }
-  sb.qsum[2 * f] = A;
-  sb.qsum[2 * f + 1] = B;
-  sb.qcount[f] = 0;
-}
 
 // Exclusive scan of one count array by one block of 1024 threads; start[n] = total. Each
 // thread owns a chunk of a multiple of 4 entries and moves it with 16-byte loads and stores,
@@ -97,7 +33,7 @@ __device__ void block_exclusive_scan(const int* count, int* start, int n) {
   int local = 0;
 #pragma unroll 4
   for (int k = lo; k < hi; k += 4) {
-    const int4 c = *reinterpret_cast<const int4*>(count + k);
+    const int4 c = __ldcg(reinterpret_cast<const int4*>(count + k));
     local += c.x + (k + 1 < hi ? c.y : 0) + (k + 2 < hi ? c.z : 0) + (k + 3 < hi ? c.w : 0);
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -122,7 +58,7 @@ __device__ void block_exclusive_scan(const int* count, int* start, int n) {
   int run = v - local + (wid > 0 ? warp_tot[wid - 1] : 0);
 #pragma unroll 4
   for (int k = lo; k < hi; k += 4) {
-    const int4 c = *reinterpret_cast<const int4*>(count + k);
+    const int4 c = __ldcg(reinterpret_cast<const int4*>(count + k));
     int4 o;
     o.x = run;
     o.y = o.x + c.x;
@@ -135,11 +71,75 @@ __device__ void block_exclusive_scan(const int* count, int* start, int n) {
   if (threadIdx.x == 0) start[n] = warp_tot[31];
 }
 
-__global__ void __launch_bounds__(1024) k_scan(SortBuffers sb, int nbricks, int ncells) {
-  if (blockIdx.x == 0)
+// One block per reduction item (kRedItem = kSortThreads ions of one frame, one per thread):
+// the ion's brick key and pair-cell key with one counting atomic each, the item's charge
+// sums (the last item of a frame adds the item partials in order), and -- in the block that
+// finishes last -- the exclusive scans that turn the final counts into segment starts.
+template <bool BATCH>
+__global__ void __launch_bounds__(kSortThreads)
+k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int tangent, int* flags,
+      int nbricks, int ncells) {
+  static_assert(kRedItem == kSortThreads, "one ion per thread");
+  const int item = blockIdx.x;
+  const int f = BATCH ? maps.item_frame[item] : 0;
+  const FrameDesc& F = frame_at<BATCH>(one, maps, f);
+  int lo, hi;
+  item_range(F, item, lo, hi);
+  const int i = lo + int(threadIdx.x);
+  float qa = 0.f, qb = 0.f;
+  if (i < hi) {
+    const Geometry& g = F.g;
+    const float rx = in.pos[3 * i], ry = in.pos[3 * i + 1], rz = in.pos[3 * i + 2];
+    const float qi = in.q ? in.q[i] : 0.f;
+    bool ok = isfinite(rx) && isfinite(ry) && isfinite(rz) && isfinite(qi);
+    if (in.mu) ok = ok && isfinite(in.mu[3 * i]) && isfinite(in.mu[3 * i + 1]) && isfinite(in.mu[3 * i + 2]);
+    if (!ok) atomicOr(flags, kFlagNonFinite);
+    double s[3];
+    frac_coords(g, rx, ry, rz, s);
+    int m0[3], c[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      float fr;
+      stencil_origin(s[b], g.N[b], g.order, m0[b], fr);
+      cell_origin(s[b], g.ncell[b], c[b], fr);
+    }
+    const int kb = F.brick_off + ((m0[0] / g.brick[0]) * g.nb[1] + m0[1] / g.brick[1]) * g.nb[2] +
+                   m0[2] / g.brick[2];
+    const int kc = F.cell_off + (c[0] * g.ncell[1] + c[1]) * g.ncell[2] + c[2];
+    sb.key_b[i] = kb;
+    sb.key_c[i] = kc;
+    sb.slot_b[i] = atomicAdd(&sb.count_b[kb], 1);
+    sb.slot_c[i] = atomicAdd(&sb.count_c[kc], 1);
+    qa = isfinite(qi) ? qi : 0.f;
+    qb = (tangent && in.gphi) ? in.gphi[i] : 0.f;
+  }
+  if (sb.qcount) {
+    const double A = block_sum_f(qa), B = block_sum_f(qb);
+    if (threadIdx.x == 0) {
+      sb.qpart[2 * item] = A;
+      sb.qpart[2 * item + 1] = B;
+    }
+    if (last_item_done(sb.qcount + f, F.nitems)) {
+      double a = 0.0, b = 0.0;
+      for (int k = threadIdx.x; k < F.nitems; k += blockDim.x) {
+        a += __ldcg(sb.qpart + 2 * (F.item_off + k));
+        b += __ldcg(sb.qpart + 2 * (F.item_off + k) + 1);
+      }
+      a = block_sum_d(a);
+      b = block_sum_d(b);
+      if (threadIdx.x == 0) {
+        sb.qsum[2 * f] = a;
+        sb.qsum[2 * f + 1] = b;
+        sb.qcount[f] = 0;
+      }
+    }
+  }
+  if (last_item_done(sb.gcount, int(gridDim.x))) {
     block_exclusive_scan(sb.count_b, sb.start_b, nbricks);
-  else
+    __syncthreads();
     block_exclusive_scan(sb.count_c, sb.start_c, ncells);
+    if (threadIdx.x == 0) *sb.gcount = 0;
+  }
 }
 
 __global__ void __launch_bounds__(kSortThreads)
@@ -262,20 +262,13 @@ int launch_sort_t(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangen
   st = check_cuda(p, cudaMemsetAsync(p->sb.count_c, 0, sizeof(int) * (p->total_cells + 1), s),
                   "memset cell counts");
   if (st) return st;
-  if (nblk > 0) {
-    k_bin<BATCH><<<nblk, kSortThreads, 0, s>>>(one, p->maps, in, p->sb, p->flags);
+  {
+    const int items = BATCH ? p->total_items : one.nitems;
+    k_bin<BATCH><<<items, kSortThreads, 0, s>>>(one, p->maps, in, p->sb, tangent ? 1 : 0, p->flags,
+                                                p->total_bricks, p->total_cells);
     count_launch();
     if ((st = check_launch(p, "k_bin"))) return st;
   }
-  if (p->sb.qcount) {
-    const int items = BATCH ? p->total_items : one.nitems;
-    k_frame_sums<BATCH><<<items, kSortThreads, 0, s>>>(one, p->maps, in, tangent ? 1 : 0, p->sb);
-    count_launch();
-    if ((st = check_launch(p, "k_frame_sums"))) return st;
-  }
-  k_scan<<<2, 1024, 0, s>>>(p->sb, p->total_bricks, p->total_cells);
-  count_launch();
-  if ((st = check_launch(p, "k_scan"))) return st;
   if (nblk > 0) {
     k_scatter<<<nblk, kSortThreads, 0, s>>>(n, p->sb, need_mesh ? 1 : 0, need_pair ? 1 : 0);
     count_launch();

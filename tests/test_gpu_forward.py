@@ -9,7 +9,7 @@ import workloads as W
 from oracle import ewald as O1
 from oracle import pme as O2
 
-from gpu_util import TOL_E, TOL_F, prepared, relrmse, sym6
+from gpu_util import TOL_E, TOL_F, f32, prepared, relrmse, sym6
 
 pytestmark = pytest.mark.gpu
 
@@ -134,3 +134,47 @@ def test_triclinic_cell(gb):
     assert abs(out["energy"].item() - ref["energy"]) < TOL_E * abs(ref["energy"])
     assert relrmse(out["force"].cpu().numpy(), ref["force"]) < TOL_F
     assert relrmse(out["field_grad"].cpu().numpy(), sym6(ref["field_grad"])) < TOL_F
+
+
+def test_nonfinite_inputs_are_flagged(gb):
+    # a NaN position and an infinite charge are wrapped / zeroed on the device (no fault) and
+    # reported as PME_ERR_NONFINITE (4) by the next status check; the plan then keeps working
+    fr, mesh, p, a, rc = CASES["nacl1000_ragged"]()
+    pos, q, mu = prepared(fr)
+    plan = gb.Plan(fr.box, mesh, p, a, rc, max_ions=1024)
+    c = lambda x: torch.tensor(np.float32(x), device="cuda")
+    for bad_pos, bad_q in ((True, False), (False, True)):
+        P, Q = np.array(pos), np.array(q)
+        if bad_pos:
+            P[17, 1] = np.nan
+        if bad_q:
+            Q[5] = np.inf
+        plan.forward(c(P), c(Q), c(mu))
+        with pytest.raises(gb.PMEError) as e:
+            plan.sync_status()
+        assert e.value.status == 4
+    out = plan.forward(c(pos), c(q), c(mu))
+    plan.sync_status()
+    ref = O2.PMEOracle(fr.box, mesh, p, a, rc).evaluate(pos, q, mu, field_grad=False)
+    assert abs(out["energy"].item() - ref["energy"]) < TOL_E * abs(ref["energy"])
+
+
+def test_single_ion(gb):
+    # one charged dipole in a 12 A box: only its own mesh images and self terms act
+    box = np.diag([12.0, 12.0, 12.0])
+    pos = np.array([[3.1, 7.7, 5.2]])
+    q = np.array([0.8])
+    mu = np.array([[0.05, -0.02, 0.04]])
+    pos, q, mu = f32(pos), f32(q), f32(mu)
+    plan = gb.Plan(box, (16, 16, 16), 6, 0.35, 9.0, max_ions=64)
+    out = plan.forward(*[torch.tensor(np.float32(x), device="cuda") for x in (pos, q, mu)])
+    ref = O2.PMEOracle(box, (16, 16, 16), 6, 0.35, 9.0).evaluate(pos, q, mu, field_grad=False)
+    # the mesh self-interaction nearly cancels the self term: bar on the parts' magnitudes
+    scale = sum(abs(ref[k]) for k in ("e_recip", "e_pair", "e_self", "e_bg"))
+    assert abs(out["energy"].item() - ref["energy"]) < TOL_E * scale
+    assert relrmse(out["phi"].cpu().numpy(), ref["phi"]) < TOL_F
+    # the field of the ion's own images is what remains of its mesh field after the own-cloud
+    # term (4 alpha^3 / 3 sqrt(pi)) mu is removed: the bar scales with that term
+    own = 4 * 0.35 ** 3 / (3 * np.sqrt(np.pi)) * np.linalg.norm(mu)
+    err = np.linalg.norm(out["field"].cpu().numpy() - ref["field"])
+    assert err < TOL_F * max(np.linalg.norm(ref["field"]), own)

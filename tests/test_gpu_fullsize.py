@@ -1,0 +1,126 @@
+"""Full-size parity in the launch configurations the benchmark times.
+
+* The 32768-ion molten-NaCl frame (L = 102 A, 128^3 mesh, order 6, alpha 0.30 / A,
+  rcut 9 A) through a default plan (pair term on the plan's second stream), forward and
+  backward against the float64 plain PME on the same mesh.
+* The 256-frame uneven batch built exactly as the benchmark builds it (64-1024 ions per
+  frame, spacing 0.8 A rounded to 2,3,5-smooth meshes in [16, 48], orders 4 and 6), with
+  sampled frames against the same oracle, and every frame's energy against a single-frame
+  plan.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import pme as O2
+
+from gpu_util import TOL_E, TOL_F, TOL_HVP, f32, prepared, relrmse, sym6
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2606_01598_gb300 as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def frame32k():
+    fr, cfg = W.workload("nacl32k")
+    return fr, cfg
+
+
+def _c(x):
+    return torch.tensor(np.float32(x), device="cuda")
+
+
+def test_32k_forward_matches_plain_pme(gb, frame32k):
+    fr, cfg = frame32k
+    pos, q, mu = prepared(fr)
+    plan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=fr.n)
+    out = plan.forward(_c(pos), _c(q), _c(mu), field_grad=True)
+    o = O2.PMEOracle(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"])
+    ref = o.evaluate(pos, q, mu)
+    # |E| ~ 370 is a tenth of |E_self| ~ 3500: the bar is on the parts' magnitudes (float32
+    # rounding of the transforms and sums scales with them)
+    scale = sum(abs(ref[k]) for k in ("e_recip", "e_pair", "e_self", "e_bg"))
+    assert abs(out["energy"].item() - ref["energy"]) < TOL_E * scale
+    for k in ("force", "phi", "field"):
+        assert relrmse(out[k].cpu().numpy(), ref[k]) < TOL_F, k
+    assert relrmse(out["field_grad"].cpu().numpy(), sym6(ref["field_grad"])) < TOL_F
+    plan.close()
+
+
+def test_32k_backward_matches_double_backward(gb, frame32k):
+    fr, cfg = frame32k
+    pos, q, mu = prepared(fr)
+    gF, gphi, gfield = (f32(x) for x in W.tangent(fr.n, seed=99))
+    plan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=fr.n)
+    got = plan.backward(_c(pos), _c(q), _c(mu), torch.tensor([0.5], dtype=torch.float64, device="cuda"),
+                        _c(gF), _c(gphi), _c(gfield))
+    o = O2.PMEOracle(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"])
+    ref = o.hvp(pos, q, mu, 0.5, gF, gphi, gfield)
+    for g_, r_ in zip(got, ref):
+        assert relrmse(g_.cpu().numpy(), r_) < TOL_HVP
+    plan.close()
+
+
+@pytest.fixture(scope="module")
+def batch256(gb):
+    specs = W.uneven_frames(n_frames=256, seed=1002)
+    frames = [s.frame for s in specs]
+    meshes = [gb.mesh_dims(fr.box, s.spacing, rule=1, strategy=1, clamp=(16, 48)) for fr, s in zip(frames, specs)]
+    orders = [s.order for s in specs]
+    offsets = np.concatenate([[0], np.cumsum([fr.n for fr in frames])]).astype(np.int64)
+    pos = np.concatenate([f32(fr.pos) for fr in frames])
+    q = np.concatenate([f32(fr.q) for fr in frames])
+    mu = np.concatenate([f32(fr.mu) for fr in frames])
+    return dict(frames=frames, meshes=meshes, orders=orders, offsets=offsets, pos=pos, q=q, mu=mu)
+
+
+def test_batch256_sampled_frames_match_oracle(gb, batch256):
+    B = batch256
+    bp = gb.BatchPlan([fr.box for fr in B["frames"]], B["meshes"], B["orders"], B["offsets"], 0.30, 9.0)
+    out = bp.forward(_c(B["pos"]), _c(B["q"]), _c(B["mu"]))
+    n = int(B["offsets"][-1])
+    gF, gphi, gfield = (f32(x) for x in W.tangent(n, seed=7))
+    gE = np.full(len(B["frames"]), 0.3)
+    got = bp.backward(_c(B["pos"]), _c(B["q"]), _c(B["mu"]), torch.tensor(gE, device="cuda"),
+                      _c(gF), _c(gphi), _c(gfield))
+    # the smallest and the largest frame of each order, and two in between
+    sizes = np.array([fr.n for fr in B["frames"]])
+    picks = set()
+    for order in (4, 6):
+        idx = [f for f in range(len(B["frames"])) if B["orders"][f] == order]
+        idx.sort(key=lambda f: sizes[f])
+        picks.update([idx[0], idx[-1], idx[len(idx) // 2]])
+    for f in sorted(picks):
+        fr = B["frames"][f]
+        lo, hi = B["offsets"][f], B["offsets"][f + 1]
+        o = O2.PMEOracle(fr.box, B["meshes"][f], B["orders"][f], 0.30, 9.0)
+        ref = o.evaluate(B["pos"][lo:hi], B["q"][lo:hi], B["mu"][lo:hi], field_grad=False)
+        scale = sum(abs(ref[k]) for k in ("e_recip", "e_pair", "e_self", "e_bg"))
+        assert abs(out["energy"][f].item() - ref["energy"]) < TOL_E * scale, f
+        assert relrmse(out["force"][lo:hi].cpu().numpy(), ref["force"]) < TOL_F, f
+        assert relrmse(out["phi"][lo:hi].cpu().numpy(), ref["phi"]) < TOL_F, f
+        hv = o.hvp(B["pos"][lo:hi], B["q"][lo:hi], B["mu"][lo:hi], 0.3, gF[lo:hi], gphi[lo:hi], gfield[lo:hi])
+        for g_, r_ in zip(got, hv):
+            assert relrmse(g_[lo:hi].cpu().numpy(), r_) < TOL_HVP, f
+    bp.close()
+
+
+def test_batch256_energies_match_single_frame_plans(gb, batch256):
+    B = batch256
+    bp = gb.BatchPlan([fr.box for fr in B["frames"]], B["meshes"], B["orders"], B["offsets"], 0.30, 9.0)
+    e_b = bp.forward(_c(B["pos"]), _c(B["q"]), _c(B["mu"]))["energy"].cpu().numpy()
+    for f, fr in enumerate(B["frames"]):
+        lo, hi = B["offsets"][f], B["offsets"][f + 1]
+        sp = gb.Plan(fr.box, B["meshes"][f], B["orders"][f], 0.30, 9.0, max_ions=max(fr.n, 64))
+        e = sp.forward(_c(B["pos"][lo:hi]), _c(B["q"][lo:hi]), _c(B["mu"][lo:hi]))["energy"].item()
+        assert abs(e_b[f] - e) < 1e-6 * abs(e), f
+        sp.close()
+    bp.close()
