@@ -29,7 +29,7 @@ constexpr int BX = 8, BY = 8, BZ = 32;
 constexpr int ZS = 8;                     // z points per thread
 constexpr int NSEG = BZ / ZS;             // z-segments per column
 constexpr int NT = BX * BY * NSEG;        // 256 threads
-constexpr int CAP = NT;                   // ions staged at once
+constexpr int CAP = NT / 2;               // ions staged at once
 constexpr int NW = CAP / 32;              // mask words
 constexpr int SL = 2 * NT;                // listed (overlapping) ions held before staging
 constexpr int kMaxCand = kMaxCandPerDim * kMaxCandPerDim * kMaxCandPerDim;
@@ -44,9 +44,28 @@ struct SpreadArgs {
   float* mesh;          // base of the meshes: rho at mesh_off, d rho at tmesh_off
 };
 
+// z weight rows are padded with ZS - 1 zeros on both sides, so a segment reads its ZS weights
+// from one window without range tests
+template <int P>
+__host__ __device__ constexpr int zrow() {
+  return P + 2 * (ZS - 1);
+}
+
+// Per-ion strides in shared memory (floats), odd so that threads reading the same entry of
+// different ions fall in different banks.
+template <int P, bool TAN>
+__host__ __device__ constexpr int wstride() {
+  return ((TAN ? 3 : 2) * (2 * P + zrow<P>())) | 1;
+}
+
+template <bool TAN>
+__host__ __device__ constexpr int cstride() {
+  return TAN ? 11 : 5;
+}
+
 template <int P, bool TAN>
 constexpr int spread_smem_bytes() {
-  return CAP * (3 * (TAN ? 3 : 2) * P + (TAN ? 11 : 4)) * 4 + SL * 4 * 4;
+  return CAP * (wstride<P, TAN>() + cstride<TAN>()) * 4 + SL * (4 + 8);
 }
 
 // distance from a to b going up the periodic axis of length n (a, b in [0, n))
@@ -58,14 +77,17 @@ __device__ __forceinline__ int up_dist(int a, int b, int n) {
 template <int P, bool TAN, bool BATCH>
 __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
   constexpr int DW = TAN ? 3 : 2;                 // weight derivative orders kept
-  constexpr int WSTRIDE = 3 * DW * P;             // floats of weights per staged ion
-  constexpr int NC = TAN ? 11 : 4;                // coefficients per staged ion
+  constexpr int ZP = zrow<P>();
+  constexpr int WZ = 2 * DW * P;                  // start of the padded z rows
+  constexpr int WSTRIDE = wstride<P, TAN>();      // floats of weights per staged ion
+  constexpr int NC = cstride<TAN>();              // coefficients per staged ion (4 or 11 used)
 
   extern __shared__ __align__(16) float dyn[];
   float* sw = dyn;                                        // [CAP][WSTRIDE]
   float* sc = sw + CAP * WSTRIDE;                         // [CAP][NC]
-  int* slist = reinterpret_cast<int*>(sc + CAP * NC);     // [SL] listed ions
-  int* sm0 = slist + SL;                                  // [SL][3] their first stencil points
+  int2* srel = reinterpret_cast<int2*>(sc + CAP * NC);    // [SL] stencil index of the brick
+                                                          // origin: x | y << 16, z
+  int* slist = reinterpret_cast<int*>(srel + SL);         // [SL] listed ions
   __shared__ unsigned xmask[BX][NW], ymask[BY][NW], zmask[NSEG][NW];
   __shared__ int cand_lo[kMaxCand];
   __shared__ int cand_cnt[kMaxCand];
@@ -148,6 +170,7 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
       const int dx = up_dist(m.x, b0x, Nx), dy = up_dist(m.y, b0y, Ny), dz = up_dist(m.z, b0z, Nz);
       take = (dx <= P - 1 || dx >= Nx - ex + 1) && (dy <= P - 1 || dy >= Ny - ey + 1) &&
              (dz <= P - 1 || dz >= Nz - ez + 1);
+      m = make_int4(dx, dy, dz, 0);
     }
     const unsigned bal = __ballot_sync(0xffffffffu, take);
     if (lane == 0) warp_cnt[wid] = __popc(bal);
@@ -161,9 +184,7 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
     if (take) {
       const int l = cnt + before + __popc(bal & ((1u << lane) - 1u));
       slist[l] = ion;
-      sm0[3 * l] = m.x;
-      sm0[3 * l + 1] = m.y;
-      sm0[3 * l + 2] = m.z;
+      srel[l] = make_int2(m.x | (m.y << 16), m.z);
     }
     cnt += tot;
     __syncthreads();
@@ -191,9 +212,16 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
           for (int j = 0; j < P; ++j) dst[(1 * DW + d) * P + j] = w[d][j];
         spline_weights<P, DW - 1>(fq.z, w);
 #pragma unroll
-        for (int d = 0; d < DW; ++d)
+        for (int d = 0; d < DW; ++d) {
+          float* row = dst + WZ + d * ZP;
 #pragma unroll
-          for (int j = 0; j < P; ++j) dst[(2 * DW + d) * P + j] = w[d][j];
+          for (int j = 0; j < ZS - 1; ++j) {
+            row[j] = 0.f;
+            row[ZS - 1 + P + j] = 0.f;
+          }
+#pragma unroll
+          for (int j = 0; j < P; ++j) row[ZS - 1 + j] = w[d][j];
+        }
         float* c = sc + tid * NC;
         c[0] = fq.w;
         c[1] = dm.x;
@@ -215,40 +243,49 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
       if (wid < NW) {
         const int l = base + wid * 32 + lane;
         const bool in = wid * 32 + lane < nst;
-        const int mx = in ? sm0[3 * l] : 0, my = in ? sm0[3 * l + 1] : 0, mz = in ? sm0[3 * l + 2] : 0;
+        const int2 rl = in ? srel[l] : make_int2(0, 0);
+        const int rx = rl.x & 0xffff, ry = rl.x >> 16, rz = rl.y;
 #pragma unroll
         for (int t = 0; t < BX; ++t) {
-          const bool cov = in && t < ex && up_dist(mx, b0x + t, Nx) < P;
-          const unsigned b = __ballot_sync(0xffffffffu, cov);
+          int d = rx + t;
+          if (d >= Nx) d -= Nx;
+          const unsigned b = __ballot_sync(0xffffffffu, in && t < ex && d < P);
           if (lane == 0) xmask[t][wid] = b;
         }
 #pragma unroll
         for (int t = 0; t < BY; ++t) {
-          const bool cov = in && t < ey && up_dist(my, b0y + t, Ny) < P;
-          const unsigned b = __ballot_sync(0xffffffffu, cov);
+          int d = ry + t;
+          if (d >= Ny) d -= Ny;
+          const unsigned b = __ballot_sync(0xffffffffu, in && t < ey && d < P);
           if (lane == 0) ymask[t][wid] = b;
         }
 #pragma unroll
         for (int t = 0; t < NSEG; ++t) {
-          const int s0 = b0z + t * ZS, ext = min(ZS, ez - t * ZS);
-          const bool cov = in && ext > 0 &&
-                           (up_dist(mz, s0, Nz) < P || up_dist(s0, mz, Nz) < ext);
-          const unsigned b = __ballot_sync(0xffffffffu, cov);
+          // stencil index of the segment's first point, and the segment start's distance to
+          // the ion's first point
+          const int ext = min(ZS, ez - t * ZS);
+          int d = (rz + t * ZS) % Nz;
+          const int back = d == 0 ? 0 : Nz - d;
+          const unsigned b = __ballot_sync(0xffffffffu, in && ext > 0 && (d < P || back < ext));
           if (lane == 0) zmask[t][wid] = b;
         }
       }
       __syncthreads();
       // ---- accumulate this thread's points over the ions that touch them --------------
       const int nw = (nst + 31) >> 5;
+      const bool padded = Nz >= P + ZS - 1;   // no stencil wraps inside one segment
       for (int w = 0; w < nw; ++w) {
         unsigned bits = xmask[X][w] & ymask[Y][w] & zmask[seg][w];
         while (bits) {
           const int t = w * 32 + __ffs(bits) - 1;
           bits &= bits - 1;
-          const int l = base + t;
-          const int dx = up_dist(sm0[3 * l], gx, Nx);
-          const int dy = up_dist(sm0[3 * l + 1], gy, Ny);
-          const int dz0 = up_dist(sm0[3 * l + 2], zs0, Nz);   // stencil index of z = zs0
+          const int2 rl = srel[base + t];
+          int dx = (rl.x & 0xffff) + X;
+          if (dx >= Nx) dx -= Nx;
+          int dy = (rl.x >> 16) + Y;
+          if (dy >= Ny) dy -= Ny;
+          int dz = rl.y + seg * ZS;   // stencil index of z = zs0
+          if (dz >= Nz) dz -= Nz;
           const float* wt = sw + t * WSTRIDE;
           const float* c = sc + t * NC;
           const float wx = wt[(0 * DW + 0) * P + dx], wx1 = wt[(0 * DW + 1) * P + dx];
@@ -267,14 +304,25 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
             A1 = c[7] * wxy + (mx * tz + mz * tx) * wx1 * wy + (my * tz + mz * ty) * wx * wy1;
             A2 = mz * tz * wxy;
           }
-          const float* wz = wt + (2 * DW + 0) * P;
+          const float* wz = wt + WZ + (ZS - 1);   // wz[j], j in [-(ZS-1), P + ZS - 1)
+          if (padded) {
+            // the stencil meets this segment either from below (dz < P) or from above
+            // (dz > Nz - ZS, i.e. index dz - Nz of the window)
+            const float* wzs = wz + (dz < P ? dz : dz - Nz);
 #pragma unroll
-          for (int z = 0; z < ZS; ++z) {
-            int j = dz0 + z;
-            if (j >= Nz) j -= Nz;
-            if (j < P) {
-              acc[z] += A * wz[j] + B * wz[P + j];
-              if (TAN) dacc[z] += A0 * wz[j] + A1 * wz[P + j] + A2 * wz[2 * P + j];
+            for (int z = 0; z < ZS; ++z) {
+              acc[z] += A * wzs[z] + B * wzs[ZP + z];
+              if (TAN) dacc[z] += A0 * wzs[z] + A1 * wzs[ZP + z] + A2 * wzs[2 * ZP + z];
+            }
+          } else {
+#pragma unroll
+            for (int z = 0; z < ZS; ++z) {
+              int j = dz + z;
+              if (j >= Nz) j -= Nz;
+              if (j < P) {
+                acc[z] += A * wz[j] + B * wz[ZP + j];
+                if (TAN) dacc[z] += A0 * wz[j] + A1 * wz[ZP + j] + A2 * wz[2 * ZP + j];
+              }
             }
           }
         }
