@@ -196,6 +196,13 @@ struct pme_plan_s {
   float* pair_out;           // [max_ions][10] per-ion pair results
   double* epart;             // reciprocal energy partials, one per influence (or k) block
   double* eitem;             // [items] per-ion energy partials
+  // pair lists recorded by the forward for a backward on the same positions
+  float4* plist = nullptr;   // [max_ions][plist_cap] (r, j) per hit, pair-cell order
+  int* plist_cnt = nullptr;  // [max_ions] hits per ion, -1 when more than plist_cap
+  int plist_cap = 0;
+  float* pos_saved = nullptr;  // [3 max_ions] positions of that forward
+  int* cache_bad = nullptr;    // [1] result of the check in the backward
+  int fwd_list_n = -1;         // ions of the forward that recorded the lists (-1: none)
   int* ecount;               // [frames] energy items finished (reset by the last one)
   int* flags;                // device error flags
   // host-pointer staging

@@ -55,6 +55,14 @@ struct PairArgs {
   const double* g_energy;   // per frame
   float* out;
   int cell_lo, ncells;      // global cell keys handled by this launch
+  // forward: every ion's hits (r, j) in evaluation order, for a later backward on the same
+  // positions (list null: not recorded); list_cnt = hits, or -1 when more than list_cap
+  float4* list;
+  int* list_cnt;
+  int list_cap;
+  // backward: *cache_bad == 0 means the recorded lists hold for these positions, and this
+  // kernel leaves the work to the list-driven one (null: always run)
+  const int* cache_bad;
   float alpha;
   float c1, c2, c3, c4;   // (2 alpha^2)^l / (alpha sqrt(pi)), l = 1..4
 };
@@ -228,6 +236,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pair(PairArgs a) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int cidx = blockIdx.x * kPairWarps + w;
   if (cidx >= a.ncells) return;   // uniform per warp
+  if (a.cache_bad && *a.cache_bad == 0) return;
   const int cell = a.cell_lo + cidx;
   const int c_lo = a.start_c[cell], c_hi = a.start_c[cell + 1];
   if (c_lo == c_hi) return;
@@ -261,6 +270,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pair(PairArgs a) {
 #pragma unroll
     for (int s = 0; s < kSlots; ++s) cnt[s] = 0;
     unsigned cnts = 0;   // the same, packed 8 bits per slot, for the flush loop
+    unsigned long long done = 0;   // hits already evaluated per slot, 16 bits each (saturating)
 
     // Evaluate, for every slot, its waiting hits in whole 32-wide chunks (all of them when
     // `last`), keeping the remainder at the front of the list.
@@ -288,11 +298,15 @@ __global__ void __launch_bounds__(kPairThreads) k_pair(PairArgs a) {
         Acc<TAN> A;
         float* ap = &s_acc[w][s][0][lane];
         acc_load<TAN>(A, ap);
+        const int d0 = int((done >> (16 * s)) & 0xffffull);
         for (int k = lane; k < upto; k += 32) {
           const float4 h = s_hit[w][s][k];
+          if (!TAN && a.list && d0 + k < a.list_cap) a.list[size_t(i) * a.list_cap + d0 + k] = h;
           interact<TAN>(a, I, __float_as_int(h.w), mk(h.x, h.y, h.z), A);
         }
         acc_store<TAN>(A, ap);
+        const unsigned long long d1 = (unsigned long long)min(d0 + upto, 0xffff);
+        done = (done & ~(0xffffull << (16 * s))) | (d1 << (16 * s));
         __syncwarp();
         const int rest = c - upto;
         if (lane < rest) {   // [0, rest) and [upto, c) do not overlap: upto >= 32 > rest
@@ -419,6 +433,10 @@ __global__ void __launch_bounds__(kPairThreads) k_pair(PairArgs a) {
 
     for (int s = 0; s < ni; ++s) {
       const int orig = a.pr.idx[i0 + s].w;
+      if (!TAN && a.list && lane == 0) {
+        const int d = int((done >> (16 * s)) & 0xffffull);
+        a.list_cnt[i0 + s] = d < a.list_cap ? d : -1;
+      }
       const float* ap = &s_acc[w][s][0][0];
       float v[NA];
 #pragma unroll
@@ -434,19 +452,71 @@ __global__ void __launch_bounds__(kPairThreads) k_pair(PairArgs a) {
   }
 }
 
+// Backward from the lists the forward recorded: one warp per ion (pair-cell order); lane l
+// takes hits l, l + 32, ... in order -- the same per-lane order as the fused kernel, so the
+// two paths give bitwise equal results. Runs only when *cache_bad == 0.
+template <bool BATCH>
+__global__ void __launch_bounds__(kPairThreads) k_pair_listed(PairArgs a, int n) {
+  if (*a.cache_bad != 0) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = blockIdx.x * kPairWarps + w;
+  if (i >= n) return;   // uniform per warp
+  const int frame = BATCH ? a.maps.sorted_frame[i] : 0;
+  const float gE = a.g_energy ? float(a.g_energy[frame]) : 0.f;
+  Ion I;
+  const float4 mi4 = a.pr.mu[i];
+  const float4 t = a.pr.tq[i];
+  const float4 d = a.pr.dr[i];
+  I.mu = mk(mi4.x, mi4.y, mi4.z);
+  I.q = mi4.w;
+  I.gE = gE;
+  I.dq = t.x;
+  I.dr = mk(d.x, d.y, d.z);
+  I.w = gE * I.mu + mk(t.y, t.z, t.w);   // gE mu + dmu + q dr
+  Acc<true> A;
+  const int c = a.list_cnt[i];
+  const float4* li = a.list + size_t(i) * a.list_cap;
+  for (int k = lane; k < c; k += 32) {
+    const float4 h = li[k];
+    interact<true>(a, I, __float_as_int(h.w), mk(h.x, h.y, h.z), A);
+  }
+  const float rx = warp_sum(A.gr.x), ry = warp_sum(A.gr.y), rz = warp_sum(A.gr.z);
+  const float q = warp_sum(A.gq);
+  const float mx = warp_sum(A.gm.x), my = warp_sum(A.gm.y), mz = warp_sum(A.gm.z);
+  if (lane == 0) {
+    float* o = a.out + size_t(a.pr.idx[i].w) * 8;
+    o[0] = rx;
+    o[1] = ry;
+    o[2] = rz;
+    o[3] = q;
+    o[4] = mx;
+    o[5] = my;
+    o[6] = mz;
+    o[7] = 0.f;
+  }
+}
+
+// *bad = 1 unless pos equals the positions of the forward that recorded the lists (bit for
+// bit) and no list overflowed; *bad must be 0 on entry.
+__global__ void __launch_bounds__(256) k_pair_cache_check(int n, const float* pos, const float* saved,
+                                                          const int* cnt, int* bad) {
+  bool ok = true;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 3 * n; k += gridDim.x * blockDim.x)
+    ok = ok && __float_as_int(pos[k]) == __float_as_int(saved[k]);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    ok = ok && cnt[k] >= 0;
+  if (__any_sync(0xffffffffu, !ok) && (threadIdx.x & 31) == 0) *bad = 1;
+}
+
 template <bool TAN, bool BATCH>
 void launch_k(bool ortho, int grid, cudaStream_t s, const PairArgs& a) {
   if (ortho) k_pair<TAN, BATCH, true><<<grid, kPairThreads, 0, s>>>(a);
   else k_pair<TAN, BATCH, false><<<grid, kPairThreads, 0, s>>>(a);
 }
 
-}  // namespace
-
-int launch_pair(pme_plan_t p, cudaStream_t s, int n, bool tangent, const IonInputs& in,
-                const double* g_energy, float* out) {
-  (void)in;
-  if (n == 0) return PME_OK;
-  PairArgs a;
+// Arguments shared by the pair launches.
+PairArgs pair_args(pme_plan_t p, const double* g_energy, float* out) {
+  PairArgs a = {};
   a.one = p->frames_h[0];
   a.maps = p->maps;
   a.alpha = float(p->alpha);
@@ -473,6 +543,21 @@ int launch_pair(pme_plan_t p, cudaStream_t s, int n, bool tangent, const IonInpu
   a.c2 = float(cl[2]);
   a.c3 = float(cl[3]);
   a.c4 = float(cl[4]);
+  a.list = p->plist;
+  a.list_cnt = p->plist_cnt;
+  a.list_cap = p->plist_cap;
+  return a;
+}
+
+}  // namespace
+
+int launch_pair(pme_plan_t p, cudaStream_t s, int n, bool tangent, const IonInputs& in,
+                const double* g_energy, float* out, bool record, const int* cache_bad) {
+  (void)in;
+  if (n == 0) return PME_OK;
+  PairArgs a = pair_args(p, g_energy, out);
+  if (!record || tangent) a.list = nullptr;
+  a.cache_bad = tangent ? cache_bad : nullptr;
   const int grid = (a.ncells + kPairWarps - 1) / kPairWarps;
   if (grid == 0) return PME_OK;
   bool ortho = true;
@@ -489,6 +574,28 @@ int launch_pair(pme_plan_t p, cudaStream_t s, int n, bool tangent, const IonInpu
   }
   count_launch();
   return check_launch(p, "k_pair");
+}
+
+int launch_pair_cache_check(pme_plan_t p, cudaStream_t s, int n, const float* pos, int* bad) {
+  const int st = check_cuda(p, cudaMemsetAsync(bad, 0, sizeof(int), s), "memset");
+  if (st) return st;
+  if (n == 0) return PME_OK;
+  const int grid = std::min(152 * 4, (3 * n + 255) / 256);
+  k_pair_cache_check<<<grid, 256, 0, s>>>(n, pos, p->pos_saved, p->plist_cnt, bad);
+  count_launch();
+  return check_launch(p, "k_pair_cache_check");
+}
+
+int launch_pair_listed(pme_plan_t p, cudaStream_t s, int n, const double* g_energy, float* out,
+                       const int* cache_bad) {
+  if (n == 0) return PME_OK;
+  PairArgs a = pair_args(p, g_energy, out);
+  a.cache_bad = cache_bad;
+  const int grid = (n + kPairWarps - 1) / kPairWarps;
+  if (p->batch) k_pair_listed<true><<<grid, kPairThreads, 0, s>>>(a, n);
+  else k_pair_listed<false><<<grid, kPairThreads, 0, s>>>(a, n);
+  count_launch();
+  return check_launch(p, "k_pair_listed");
 }
 
 }  // namespace gbpme

@@ -260,7 +260,8 @@ static void free_plan(pme_plan_t p) {
                   p->mr.dm, p->mr.tq, p->mr.tt, p->pr.idx, p->pr.fq, p->pr.mu, p->pr.tq, p->pr.dr,
                   p->mesh_out, p->pair_out, p->e_ion, p->epart, p->flags, p->stage_f,
                   p->stage_d, p->ew_kn, p->ew_kv, p->ew_S, p->ew_fx, p->ew_qm, p->frames_d,
-                  p->map_buf, p->fft_work, p->sb.qpart, p->sb.qcount, p->eitem, p->ecount, p->sb.gcount};
+                  p->map_buf, p->fft_work, p->sb.qpart, p->sb.qcount, p->eitem, p->ecount, p->sb.gcount,
+                  p->plist, p->plist_cnt, p->pos_saved, p->cache_bad};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int g = 0; g < p->nfgroups; ++g) {
@@ -536,6 +537,27 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
   A(&p->stage_f, ni * kStageFloats);
   A(&p->stage_d, size_t(2) * F + 2);
   if (st == PME_OK) st = alloc_cells(p);
+  // pair lists for backward passes on the forward's positions: room for 1.5x the mean number
+  // of partners inside rcut (density from the plan's largest n / V) + 64, when that fits in
+  // 1 GiB; an ion with more partners marks the lists invalid and the backward recomputes
+  if (st == PME_OK && pair) {
+    double dens = 0.0;
+    for (int f = 0; f < F; ++f) {
+      const FrameDesc& D = p->frames_h[f];
+      const double nf = single ? double(p->max_ions) : double(D.n);
+      dens = std::max(dens, nf / D.g.volume);
+    }
+    const double mean = 4.0 / 3.0 * kPi * rcut * rcut * rcut * dens;
+    int cap = int(std::ceil((1.5 * mean + 64.0) / 32.0)) * 32;
+    cap = std::max(64, std::min(cap, 2048));
+    if (double(p->max_ions) * cap * sizeof(float4) <= double(1ull << 30)) {
+      p->plist_cap = cap;
+      A(&p->plist, ni * size_t(cap));
+      A(&p->plist_cnt, ni);
+      A(&p->pos_saved, 3 * ni);
+      A(&p->cache_bad, 1);
+    }
+  }
   if (st) return st;
   if ((st = check_cuda(p, cudaMemset(p->flags, 0, sizeof(int)), "memset"))) return st;
   if ((st = check_cuda(p, cudaMemset(p->sb.qcount, 0, sizeof(int) * F), "memset"))) return st;
@@ -669,7 +691,7 @@ static int forward_ewald(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool
   if (fork) {
     if (p->opts.overlap_pair && (st = fork_side(p, s))) return st;
     t = prof_begin(p, 6, ps);
-    if ((st = launch_pair(p, ps, n, false, in, nullptr, p->pair_out))) return st;
+    if ((st = launch_pair(p, ps, n, false, in, nullptr, p->pair_out, false, nullptr))) return st;
     prof_end(p, t, ps);
   }
   t = prof_begin(p, 3, s);
@@ -689,18 +711,25 @@ static int run_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, double
   const bool pair = p->opts.include_pair != 0;
   if (p->opts.recip_method == 1) return forward_ewald(p, s, in, pair, e_out, f_out, p_out, fl_out, fg_out);
   int st, t;
+  p->fwd_list_n = -1;
   t = prof_begin(p, 0, s);
   if ((st = launch_sort(p, s, in, false, true, pair))) return st;
   prof_end(p, t, s);
-  // the pair term runs on the plan's side stream, concurrently with the mesh stages
+  // the pair term runs on the plan's side stream, concurrently with the mesh stages; it also
+  // records each ion's hits for a backward on the same positions
   const bool fork = pair && n > 0;
+  const bool record = fork && p->plist;
   cudaStream_t ps = p->opts.overlap_pair ? p->side : s;
   if (fork) {
     if (p->opts.overlap_pair && (st = fork_side(p, s))) return st;
     t = prof_begin(p, 6, ps);
-    if ((st = launch_pair(p, ps, n, false, in, nullptr, p->pair_out))) return st;
+    if ((st = launch_pair(p, ps, n, false, in, nullptr, p->pair_out, record, nullptr))) return st;
     prof_end(p, t, ps);
   }
+  if (record &&
+      (st = check_cuda(p, cudaMemcpyAsync(p->pos_saved, in.pos, sizeof(float) * 3 * size_t(n),
+                                          cudaMemcpyDeviceToDevice, s), "copy positions")))
+    return st;
   t = prof_begin(p, 1, s);
   if ((st = launch_spread(p, s, false, p->rho))) return st;
   prof_end(p, t, s);
@@ -720,6 +749,7 @@ static int run_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, double
   t = prof_begin(p, 7, s);
   if ((st = launch_combine_forward(p, s, in, true, fork, f_out, p_out, fl_out, fg_out, e_out, 1))) return st;
   prof_end(p, t, s);
+  if (record) p->fwd_list_n = n;
   return PME_OK;
 }
 
@@ -738,7 +768,13 @@ static int run_backward(pme_plan_t p, cudaStream_t s, const IonInputs& in, const
   if (pair) {
     if (p->opts.overlap_pair && (st = fork_side(p, s))) return st;
     t = prof_begin(p, B + 6, ps);
-    if ((st = launch_pair(p, ps, n, true, in, gE, p->pair_out))) return st;
+    // positions bit for bit those of the last forward: the recorded hit lists drive the
+    // pair term; otherwise the full cell-list pass runs
+    const bool cached = p->plist && p->fwd_list_n == n;
+    if (cached && (st = launch_pair_cache_check(p, ps, n, in.pos, p->cache_bad))) return st;
+    if ((st = launch_pair(p, ps, n, true, in, gE, p->pair_out, false, cached ? p->cache_bad : nullptr)))
+      return st;
+    if (cached && (st = launch_pair_listed(p, ps, n, gE, p->pair_out, p->cache_bad))) return st;
     prof_end(p, t, ps);
   }
   t = prof_begin(p, B + 1, s);
@@ -920,6 +956,7 @@ int pme_plan_set_box(pme_plan_t p, const double box[9]) {
   D.g = g;
   D.ncells = nc;
   p->g = g;
+  p->fwd_list_n = -1;   // recorded pair lists belong to the old box
   std::memcpy(p->box, box, sizeof(double) * 9);
   if (nc > p->total_cells) {
     cudaFree(p->sb.count_c);
@@ -1127,7 +1164,7 @@ int pme_pair(pme_plan_t p, void* stream, int n, const float* pos, const float* q
   in.mu = mu;
   in.n = n;
   if ((st = launch_sort(p, s, in, false, false, true))) return st;
-  if ((st = launch_pair(p, s, n, false, in, nullptr, out))) return st;
+  if ((st = launch_pair(p, s, n, false, in, nullptr, out, false, nullptr))) return st;
   if (e_pair) {
     if ((st = launch_pair_energy(p, s, n, in, out))) return st;
     return launch_energy_final(p, s, p->epart, 0, true, false, 1.0, n, e_pair);

@@ -109,3 +109,31 @@ def test_backward_host_pointer_path(gb):
                       *(c(x).cpu().pin_memory() for x in (gF, gphi, gfield)))
     for x, y in zip(d, h):
         assert torch.equal(x.cpu(), y)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_backward_after_forward_reuses_pair_lists_bitwise(gb, name):
+    # a backward on the positions of the plan's last forward evaluates the pair term from the
+    # hit lists that forward recorded; it must equal the full cell-list pass bit for bit, and
+    # any change of the positions (here one coordinate by one ulp) must fall back to that pass
+    fr, mesh, p, a, rc = CASES[name]()
+    pos, q, mu = prepared(fr)
+    gF, gphi, gfield = (f32(x) for x in W.tangent(fr.n, scale=1.0, seed=19))
+    c = lambda x: torch.tensor(np.float32(x), device="cuda")
+    gE = torch.tensor([0.4], dtype=torch.float64, device="cuda")
+    args = (c(pos), c(q), c(mu), gE, c(gF), c(gphi), c(gfield))
+    warm = gb.Plan(fr.box, mesh, p, a, rc, max_ions=1024)
+    warm.forward(*args[:3])
+    listed = warm.backward(*args)
+    fresh = gb.Plan(fr.box, mesh, p, a, rc, max_ions=1024).backward(*args)
+    for x, y in zip(listed, fresh):
+        assert torch.equal(x, y)
+    pos2 = np.float32(pos).copy()
+    pos2[3, 0] = np.nextafter(pos2[3, 0], np.float32(np.inf))
+    args2 = (torch.tensor(pos2, device="cuda"),) + args[1:]
+    warm.forward(*args[:3])          # lists recorded for the original positions
+    moved = warm.backward(*args2)
+    fresh2 = gb.Plan(fr.box, mesh, p, a, rc, max_ions=1024).backward(*args2)
+    for x, y in zip(moved, fresh2):
+        assert torch.equal(x, y)
+    warm.close()

@@ -115,3 +115,18 @@ def test_batch_host_pointers_and_rejections(gb, batch):
     sp = gb.Plan(B["frames"][0].box, B["meshes"][0], B["orders"][0], 0.30, 9.0, max_ions=2048)
     assert sp.lib.pme_batch_forward(sp.handle, None, p_(pos), p_(q), *([None] * 6)) == 1
     assert bp.lib.pme_batch_frames(bp.handle) == len(B["frames"])
+
+
+def test_batch_backward_after_forward_is_bitwise_the_same(gb, batch):
+    B = batch
+    n = int(B["offsets"][-1])
+    gF, gphi, gfield = (f32(x) for x in W.tangent(n, seed=23))
+    gE = torch.tensor(np.linspace(0.2, 0.6, len(B["frames"])), device="cuda")
+    args = (_c(B["pos"]), _c(B["q"]), _c(B["mu"]), gE, _c(gF), _c(gphi), _c(gfield))
+    mk = lambda: gb.BatchPlan([fr.box for fr in B["frames"]], B["meshes"], B["orders"], B["offsets"], 0.30, 9.0)
+    bp = mk()
+    bp.forward(*args[:3])
+    listed = bp.backward(*args)
+    fresh = mk().backward(*args)
+    for x, y in zip(listed, fresh):
+        assert torch.equal(x, y)
