@@ -60,7 +60,7 @@ NOALLOC_MAX_MESH = 128
 
 NUM_STAGES = 18
 STAGE_NAMES = ["sort", "spread", "fft_r2c", "influence", "fft_c2r", "gather", "pair",
-               "combine", "energy"]
+               "combine", "pair_eval"]
 
 _LIB = None
 

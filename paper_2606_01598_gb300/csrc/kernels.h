@@ -45,15 +45,16 @@ int launch_gather(pme_plan_t p, cudaStream_t s, int n, const float* mesh, bool t
                   const double* g_energy, float* out);
 
 // pair.cu: real-space erfc pair term over the cell list, same output layouts as gather.
-//   record (forward): also write every ion's hits to the plan's pair lists;
-//   cache_bad (backward, nullable): skip the launch when *cache_bad == 0 (lists valid).
+// The fused pass; skip (nullable): return at once when *skip == 0.
 int launch_pair(pme_plan_t p, cudaStream_t s, int n, bool tangent, const IonInputs& in,
-                const double* g_energy, float* out, bool record, const int* cache_bad);
-// *bad = 0 when pos is bit for bit the recorded forward's and no list overflowed, else 1.
+                const double* g_energy, float* out, const int* skip);
+// Write every ion's hits to the plan's pair lists; *overflow = 1 when a list is too short.
+int launch_pair_build(pme_plan_t p, cudaStream_t s, int n, int* overflow);
+// *bad = 0 when pos is bit for bit the listed forward's and no list overflowed, else 1.
 int launch_pair_cache_check(pme_plan_t p, cudaStream_t s, int n, const float* pos, int* bad);
-// Backward pair term from the recorded lists (runs only when *cache_bad == 0).
-int launch_pair_listed(pme_plan_t p, cudaStream_t s, int n, const double* g_energy, float* out,
-                       const int* cache_bad);
+// Pair term from the lists (runs only when *flag == 0).
+int launch_pair_listed(pme_plan_t p, cudaStream_t s, int n, bool tangent, const double* g_energy,
+                       float* out, const int* flag);
 
 // combine.cu: add the parts, the self and background terms, apply coulomb_k, write outputs;
 // with energy non-null also the frame energies, as launch_energy_final with the per-ion

@@ -55,13 +55,13 @@ struct PairArgs {
   const double* g_energy;   // per frame
   float* out;
   int cell_lo, ncells;      // global cell keys handled by this launch
-  // forward: every ion's hits (r, j) in evaluation order, for a later backward on the same
-  // positions (list null: not recorded); list_cnt = hits, or -1 when more than list_cap
+  // per-ion hit lists (r, j) in stream order, pair-cell order; list_cnt = hits, or -1 when
+  // more than list_cap
   float4* list;
   int* list_cnt;
   int list_cap;
-  // backward: *cache_bad == 0 means the recorded lists hold for these positions, and this
-  // kernel leaves the work to the list-driven one (null: always run)
+  // *cache_bad == 0: the lists hold for this pass -- the fused kernel returns at once and
+  // the list-driven one runs (fused kernel: null means always run)
   const int* cache_bad;
   float alpha;
   float c1, c2, c3, c4;   // (2 alpha^2)^l / (alpha sqrt(pi)), l = 1..4
@@ -224,7 +224,162 @@ __device__ __forceinline__ void unpack_counts(unsigned p, int (&c)[kSlots]) {
   for (int s = 0; s < kSlots; ++s) c[s] = int((p >> (8 * s)) & 0xffu);
 }
 
-// ORTHO: every frame of the launch has a diagonal cell matrix (r = u . H needs 3 products).
+// Geometry of one pair cell and its neighbourhood.
+struct CellCtx {
+  int cix, ciy, ciz;         // the cell
+  int ncx, ncy, ncz;         // cells per axis
+  int kx, ky, kz;            // neighbour range per axis
+  bool zrun;                 // the z-cells of a column are distinct: z offsets come from the
+                             // candidate's own cell
+  int nzs, nseg;             // segments per (ox, oy) column, segments in all
+  int cell_off;              // first global cell key of the frame
+};
+
+__device__ __forceinline__ CellCtx cell_ctx(const Geometry& g, int lc, int cell_off) {
+  CellCtx c;
+  c.ncx = g.ncell[0];
+  c.ncy = g.ncell[1];
+  c.ncz = g.ncell[2];
+  c.kx = g.kimg[0];
+  c.ky = g.kimg[1];
+  c.kz = g.kimg[2];
+  c.ciz = lc % c.ncz;
+  c.ciy = (lc / c.ncz) % c.ncy;
+  c.cix = lc / (c.ncz * c.ncy);
+  c.zrun = c.ncz >= 2 * c.kz + 1;
+  c.nzs = c.zrun ? 1 : 2 * c.kz + 1;
+  c.nseg = (2 * c.kx + 1) * (2 * c.ky + 1) * c.nzs;
+  c.cell_off = cell_off;
+  return c;
+}
+
+// The dense candidate stream of one cell, 32 candidates at a time. A segment is one
+// (ox, oy[, oz]) neighbour column: the ions of one or two contiguous ranges of the cell order.
+// Lane l describes segment (32 g + l) of group g; a warp scan of the lengths places the
+// segments back to back, each lane lists its own segment's ions (tagged with the lane) in
+// shared memory (cand: this warp's kCandCap entries, code: its 32 segment codes), and the warp
+// walks the list, loading the next chunk's records while fn(valid, j, bx, by, bz, self_cell)
+// handles the current one: candidate j (sorted index), b = -(offset of j) - (cell offset) in
+// cell units, self_cell when the offset is zero. fn is called by the whole warp.
+template <class Fn>
+__device__ __forceinline__ void walk_candidates(const PairArgs& a, const CellCtx& c, unsigned* cand,
+                                                int* code_s, int lane, Fn&& fn) {
+  for (int g0 = 0; g0 < c.nseg; g0 += 32) {
+    const int sidx = g0 + lane;
+    int loA = 0, lenA = 0, loB = 0, lenB = 0, code = 0;
+    if (sidx < c.nseg) {
+      const int oz = c.zrun ? 0 : (sidx % c.nzs) - c.kz;
+      const int t = sidx / c.nzs;
+      const int oy = (t % (2 * c.ky + 1)) - c.ky;
+      const int ox = (t / (2 * c.ky + 1)) - c.kx;
+      int cx = (c.cix + ox) % c.ncx, cy = (c.ciy + oy) % c.ncy;
+      if (cx < 0) cx += c.ncx;
+      if (cy < 0) cy += c.ncy;
+      const int row = c.cell_off + (cx * c.ncy + cy) * c.ncz;
+      if (c.zrun) {
+        const int z0 = c.ciz - c.kz, z1 = c.ciz + c.kz;
+        if (z0 < 0) {
+          loA = a.start_c[row + z0 + c.ncz]; lenA = a.start_c[row + c.ncz] - loA;
+          loB = a.start_c[row]; lenB = a.start_c[row + z1 + 1] - loB;
+        } else if (z1 >= c.ncz) {
+          loA = a.start_c[row + z0]; lenA = a.start_c[row + c.ncz] - loA;
+          loB = a.start_c[row]; lenB = a.start_c[row + z1 - c.ncz + 1] - loB;
+        } else {
+          loA = a.start_c[row + z0]; lenA = a.start_c[row + z1 + 1] - loA;
+        }
+      } else {
+        int cz = (c.ciz + oz) % c.ncz;
+        if (cz < 0) cz += c.ncz;
+        loA = a.start_c[row + cz]; lenA = a.start_c[row + cz + 1] - loA;
+      }
+      // offsets packed in one int: 10 bits each, biased by 512
+      code = ((ox + 512) << 20) | ((oy + 512) << 10) | (oz + 512);
+    }
+    code_s[lane] = code;
+    const int len = lenA + lenB;
+    int pre = len;   // inclusive scan over the group's segments
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, pre, o);
+      if (lane >= o) pre += u;
+    }
+    const int total = __shfl_sync(0xffffffffu, pre, 31);
+    for (int piece = 0; piece < total; piece += kCandCap) {
+      const int npc = min(kCandCap, total - piece);
+      {
+        const int first = pre - len;
+        const int lo = max(first, piece), hi = min(pre, piece + kCandCap);
+        const unsigned tag = unsigned(lane) << kSegShift;
+        for (int q = lo; q < hi; ++q) {
+          const int off = q - first;
+          cand[q - piece] = tag | unsigned(off < lenA ? loA + off : loB + (off - lenA));
+        }
+      }
+      __syncwarp();
+      constexpr unsigned kIdx = (1u << kSegShift) - 1u;
+      unsigned e = lane < npc ? cand[lane] : 0u;
+      float4 fj = lane < npc ? a.pr.fq[e & kIdx] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int base = 0; base < npc; base += 32) {
+        // records of the next chunk, in flight while this one is tested
+        const int kn = base + 32 + lane;
+        const unsigned en = kn < npc ? cand[kn] : 0u;
+        const float4 fjn = kn < npc ? a.pr.fq[en & kIdx] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool valid = base + lane < npc;
+        const int j = int(e & kIdx);
+        const int scode = code_s[e >> kSegShift];
+        const int ox = ((scode >> 20) & 1023) - 512;
+        const int oy = ((scode >> 10) & 1023) - 512;
+        int oz = (scode & 1023) - 512;
+        if (c.zrun) {
+          oz = __float_as_int(fj.w) - c.ciz;
+          if (oz > c.kz) oz -= c.ncz;
+          else if (oz < -c.kz) oz += c.ncz;
+        }
+        fn(valid, j, -fj.x - float(ox), -fj.y - float(oy), -fj.z - float(oz), ox == 0 && oy == 0 && oz == 0);
+        e = en;
+        fj = fjn;
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// r = u . H for u = (offset of i) + b in cell units; ORTHO: diagonal cell matrix
+template <bool ORTHO>
+__device__ __forceinline__ V3 cell_to_r(const Geometry& g, float ux, float uy, float uz) {
+  if constexpr (ORTHO) {
+    return mk(ux * g.H[0], uy * g.H[4], uz * g.H[8]);
+  } else {
+    return mk(ux * g.H[0] + uy * g.H[3] + uz * g.H[6], ux * g.H[1] + uy * g.H[4] + uz * g.H[7],
+              ux * g.H[2] + uy * g.H[5] + uz * g.H[8]);
+  }
+}
+
+// Ion-side data of sorted ion i for pair contributions.
+template <bool TAN>
+__device__ __forceinline__ Ion load_ion(const PairArgs& a, int i, float gE) {
+  Ion I;
+  const float4 mi4 = a.pr.mu[i];
+  I.mu = mk(mi4.x, mi4.y, mi4.z);
+  I.q = mi4.w;
+  I.dq = 0.f;
+  I.gE = gE;
+  I.dr = mk(0.f, 0.f, 0.f);
+  I.w = mk(0.f, 0.f, 0.f);
+  if (TAN) {
+    const float4 t = a.pr.tq[i];
+    const float4 d = a.pr.dr[i];
+    I.dq = t.x;
+    I.dr = mk(d.x, d.y, d.z);
+    I.w = gE * I.mu + mk(t.y, t.z, t.w);   // gE mu + dmu + q dr
+  }
+  return I;
+}
+
+// Fused pass (used when no valid lists exist): one warp per pair cell; the cell's ions
+// (kSlots at a time) share the candidate stream, each keeps its own hit list in shared memory,
+// evaluated whenever it holds 32 hits (the remainder waits for the next chunk).
+// skip (nullable): return at once when *skip == 0 (the list-driven kernels do the work).
 template <bool TAN, bool BATCH, bool ORTHO>
 __global__ void __launch_bounds__(kPairThreads) k_pair(PairArgs a) {
   constexpr int NA = kAccN<TAN>;
@@ -243,17 +398,9 @@ __global__ void __launch_bounds__(kPairThreads) k_pair(PairArgs a) {
   const int frame = BATCH ? a.maps.sorted_frame[c_lo] : 0;
   const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, frame);
   const Geometry& g = F.g;
-  const int ncx = g.ncell[0], ncy = g.ncell[1], ncz = g.ncell[2];
-  const int kx = g.kimg[0], ky = g.kimg[1], kz = g.kimg[2];
-  const int lc = cell - F.cell_off;
-  const int ciz = lc % ncz, ciy = (lc / ncz) % ncy, cix = lc / (ncz * ncy);
+  const CellCtx cc = cell_ctx(g, cell - F.cell_off, F.cell_off);
   const unsigned lane_lt = (1u << lane) - 1u;
   const float gE = (TAN && a.g_energy) ? float(a.g_energy[frame]) : 0.f;
-
-  const bool zrun = ncz >= 2 * kz + 1;              // the z-cells of a column are distinct:
-                                                    // z offsets come from the candidate's cell
-  const int nzs = zrun ? 1 : 2 * kz + 1;            // segments per (ox, oy) column
-  const int nseg = (2 * kx + 1) * (2 * ky + 1) * nzs;
 
   for (int i0 = c_lo; i0 < c_hi; i0 += kSlots) {
     const int ni = min(kSlots, c_hi - i0);
@@ -270,7 +417,6 @@ __global__ void __launch_bounds__(kPairThreads) k_pair(PairArgs a) {
 #pragma unroll
     for (int s = 0; s < kSlots; ++s) cnt[s] = 0;
     unsigned cnts = 0;   // the same, packed 8 bits per slot, for the flush loop
-    unsigned long long done = 0;   // hits already evaluated per slot, 16 bits each (saturating)
 
     // Evaluate, for every slot, its waiting hits in whole 32-wide chunks (all of them when
     // `last`), keeping the remainder at the front of the list.
@@ -279,164 +425,51 @@ __global__ void __launch_bounds__(kPairThreads) k_pair(PairArgs a) {
         const int c = int((cnts >> (8 * s)) & 0xffu);
         const int upto = last ? c : (c & ~31);
         if (upto == 0) continue;   // uniform
-        const int i = i0 + s;
-        Ion I;
-        const float4 mi4 = a.pr.mu[i];
-        I.mu = mk(mi4.x, mi4.y, mi4.z);
-        I.q = mi4.w;
-        I.dq = 0.f;
-        I.gE = gE;
-        I.dr = mk(0.f, 0.f, 0.f);
-        I.w = mk(0.f, 0.f, 0.f);
-        if (TAN) {
-          const float4 t = a.pr.tq[i];
-          const float4 d = a.pr.dr[i];
-          I.dq = t.x;
-          I.dr = mk(d.x, d.y, d.z);
-          I.w = gE * I.mu + mk(t.y, t.z, t.w);   // gE mu + dmu + q dr
-        }
+        const Ion I = load_ion<TAN>(a, i0 + s, gE);
         Acc<TAN> A;
         float* ap = &s_acc[w][s][0][lane];
         acc_load<TAN>(A, ap);
-        const int d0 = int((done >> (16 * s)) & 0xffffull);
         for (int k = lane; k < upto; k += 32) {
           const float4 h = s_hit[w][s][k];
-          if (!TAN && a.list && d0 + k < a.list_cap) a.list[size_t(i) * a.list_cap + d0 + k] = h;
           interact<TAN>(a, I, __float_as_int(h.w), mk(h.x, h.y, h.z), A);
         }
         acc_store<TAN>(A, ap);
-        const unsigned long long d1 = (unsigned long long)min(d0 + upto, 0xffff);
-        done = (done & ~(0xffffull << (16 * s))) | (d1 << (16 * s));
         __syncwarp();
         const int rest = c - upto;
-        if (lane < rest) {   // [0, rest) and [upto, c) do not overlap: upto >= 32 > rest
+        if (lane < rest)   // [0, rest) and [upto, c) do not overlap: upto >= 32 > rest
           s_hit[w][s][lane] = s_hit[w][s][upto + lane];
-        }
         __syncwarp();
         cnts = (cnts & ~(0xffu << (8 * s))) | (unsigned(rest) << (8 * s));
       }
     };
 
-    // ---- dense candidate stream ---------------------------------------------------------
-    // A segment is one (ox, oy[, oz]) neighbour column: the ions of one or two contiguous
-    // ranges of the cell order. Lane l describes segment (32 g + l) of group g; a warp scan of
-    // the lengths places the segments back to back, each lane lists its own segment's ions
-    // (tagged with the lane) in shared memory, and the warp then walks the list 32 candidates
-    // at a time, loading the next chunk's records while it tests the current one.
-    for (int g0 = 0; g0 < nseg; g0 += 32) {
-      const int sidx = g0 + lane;
-      int loA = 0, lenA = 0, loB = 0, lenB = 0, code = 0;
-      if (sidx < nseg) {
-        const int oz = zrun ? 0 : (sidx % nzs) - kz;
-        const int t = sidx / nzs;
-        const int oy = (t % (2 * ky + 1)) - ky;
-        const int ox = (t / (2 * ky + 1)) - kx;
-        int cx = (cix + ox) % ncx, cy = (ciy + oy) % ncy;
-        if (cx < 0) cx += ncx;
-        if (cy < 0) cy += ncy;
-        const int row = F.cell_off + (cx * ncy + cy) * ncz;
-        if (zrun) {
-          const int z0 = ciz - kz, z1 = ciz + kz;
-          if (z0 < 0) {
-            loA = a.start_c[row + z0 + ncz]; lenA = a.start_c[row + ncz] - loA;
-            loB = a.start_c[row]; lenB = a.start_c[row + z1 + 1] - loB;
-          } else if (z1 >= ncz) {
-            loA = a.start_c[row + z0]; lenA = a.start_c[row + ncz] - loA;
-            loB = a.start_c[row]; lenB = a.start_c[row + z1 - ncz + 1] - loB;
-          } else {
-            loA = a.start_c[row + z0]; lenA = a.start_c[row + z1 + 1] - loA;
-          }
-        } else {
-          int cz = (ciz + oz) % ncz;
-          if (cz < 0) cz += ncz;
-          loA = a.start_c[row + cz]; lenA = a.start_c[row + cz + 1] - loA;
-        }
-        // offsets packed in one int: 10 bits each, biased by 512
-        code = ((ox + 512) << 20) | ((oy + 512) << 10) | (oz + 512);
-      }
-      s_code[w][lane] = code;
-      const int len = lenA + lenB;
-      int pre = len;   // inclusive scan over the group's segments
+    walk_candidates(a, cc, s_cand[w], s_code[w], lane,
+                    [&](bool valid, int j, float bx, float by, float bz, bool self_cell) {
+      bool any_full = false;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, pre, o);
-        if (lane >= o) pre += u;
+      for (int s = 0; s < kSlots; ++s) {
+        const float4 fi = s_fi[w][s];
+        const V3 r = cell_to_r<ORTHO>(g, fi.x + bx, fi.y + by, fi.z + bz);
+        const bool hit = valid && s < ni && dot(r, r) < g.rcut2 &&
+                         !(self_cell && j == __float_as_int(fi.w));
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        if (hit) s_hit[w][s][cnt[s] + __popc(bal & lane_lt)] = make_float4(r.x, r.y, r.z, __int_as_float(j));
+        cnt[s] += __popc(bal);
+        any_full |= cnt[s] >= 32;
       }
-      const int total = __shfl_sync(0xffffffffu, pre, 31);
-      for (int piece = 0; piece < total; piece += kCandCap) {
-        const int npc = min(kCandCap, total - piece);
-        {
-          const int first = pre - len;
-          const int lo = max(first, piece), hi = min(pre, piece + kCandCap);
-          const unsigned tag = unsigned(lane) << kSegShift;
-          for (int c = lo; c < hi; ++c) {
-            const int off = c - first;
-            s_cand[w][c - piece] = tag | unsigned(off < lenA ? loA + off : loB + (off - lenA));
-          }
-        }
+      if (any_full) {
         __syncwarp();
-        unsigned e = lane < npc ? s_cand[w][lane] : 0u;
-        float4 fj = lane < npc ? a.pr.fq[e & ((1u << kSegShift) - 1u)] : make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int base = 0; base < npc; base += 32) {
-          // records of the next chunk, in flight while this one is tested
-          const int kn = base + 32 + lane;
-          const unsigned en = kn < npc ? s_cand[w][kn] : 0u;
-          const float4 fjn = kn < npc ? a.pr.fq[en & ((1u << kSegShift) - 1u)] : make_float4(0.f, 0.f, 0.f, 0.f);
-          const bool valid = base + lane < npc;
-          const int j = int(e & ((1u << kSegShift) - 1u));
-          const int scode = s_code[w][e >> kSegShift];
-          const int ox = ((scode >> 20) & 1023) - 512;
-          const int oy = ((scode >> 10) & 1023) - 512;
-          int oz = (scode & 1023) - 512;
-          if (zrun) {
-            oz = __float_as_int(fj.w) - ciz;
-            if (oz > kz) oz -= ncz;
-            else if (oz < -kz) oz += ncz;
-          }
-          // u = (offset of i) - (offset of j) - (cell offset), in cell units
-          const float bx = -fj.x - float(ox), by = -fj.y - float(oy), bz = -fj.z - float(oz);
-          const bool self_cell = ox == 0 && oy == 0 && oz == 0;
-          bool any_full = false;
-#pragma unroll
-          for (int s = 0; s < kSlots; ++s) {
-            const float4 fi = s_fi[w][s];
-            const float ux = fi.x + bx, uy = fi.y + by, uz = fi.z + bz;
-            V3 r;
-            if constexpr (ORTHO) {
-              r = mk(ux * g.H[0], uy * g.H[4], uz * g.H[8]);
-            } else {
-              r = mk(ux * g.H[0] + uy * g.H[3] + uz * g.H[6], ux * g.H[1] + uy * g.H[4] + uz * g.H[7],
-                     ux * g.H[2] + uy * g.H[5] + uz * g.H[8]);
-            }
-            const bool hit = valid && s < ni && dot(r, r) < g.rcut2 &&
-                             !(self_cell && j == __float_as_int(fi.w));
-            const unsigned bal = __ballot_sync(0xffffffffu, hit);
-            if (hit) s_hit[w][s][cnt[s] + __popc(bal & lane_lt)] = make_float4(r.x, r.y, r.z, __int_as_float(j));
-            cnt[s] += __popc(bal);
-            any_full |= cnt[s] >= 32;
-          }
-          if (any_full) {
-            __syncwarp();
-            cnts = pack_counts(cnt);
-            flush(false);
-            unpack_counts(cnts, cnt);
-          }
-          e = en;
-          fj = fjn;
-        }
-        __syncwarp();
+        cnts = pack_counts(cnt);
+        flush(false);
+        unpack_counts(cnts, cnt);
       }
-    }
+    });
     __syncwarp();
     cnts = pack_counts(cnt);
     flush(true);
 
     for (int s = 0; s < ni; ++s) {
       const int orig = a.pr.idx[i0 + s].w;
-      if (!TAN && a.list && lane == 0) {
-        const int d = int((done >> (16 * s)) & 0xffffull);
-        a.list_cnt[i0 + s] = d < a.list_cap ? d : -1;
-      }
       const float* ap = &s_acc[w][s][0][0];
       float v[NA];
 #pragma unroll
@@ -452,47 +485,106 @@ __global__ void __launch_bounds__(kPairThreads) k_pair(PairArgs a) {
   }
 }
 
-// Backward from the lists the forward recorded: one warp per ion (pair-cell order); lane l
-// takes hits l, l + 32, ... in order -- the same per-lane order as the fused kernel, so the
-// two paths give bitwise equal results. Runs only when *cache_bad == 0.
-template <bool BATCH>
+// List pass: one warp per pair cell walks the same candidate stream and writes every ion's
+// hits (r, j), in stream order, to its list in global memory; list_cnt = hits, or -1 (and
+// *overflow = 1) when an ion has more than list_cap.
+template <bool BATCH, bool ORTHO>
+__global__ void __launch_bounds__(kPairThreads) k_pair_build(PairArgs a, int* overflow) {
+  __shared__ float4 s_fi[kPairWarps][kSlots];
+  __shared__ unsigned s_cand[kPairWarps][kCandCap];
+  __shared__ int s_code[kPairWarps][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int cidx = blockIdx.x * kPairWarps + w;
+  if (cidx >= a.ncells) return;   // uniform per warp
+  const int cell = a.cell_lo + cidx;
+  const int c_lo = a.start_c[cell], c_hi = a.start_c[cell + 1];
+  if (c_lo == c_hi) return;
+  const int frame = BATCH ? a.maps.sorted_frame[c_lo] : 0;
+  const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, frame);
+  const Geometry& g = F.g;
+  const CellCtx cc = cell_ctx(g, cell - F.cell_off, F.cell_off);
+  const unsigned lane_lt = (1u << lane) - 1u;
+  const int cap = a.list_cap;
+  for (int i0 = c_lo; i0 < c_hi; i0 += kSlots) {
+    const int ni = min(kSlots, c_hi - i0);
+    if (lane < ni) {
+      const float4 f = a.pr.fq[i0 + lane];
+      s_fi[w][lane] = make_float4(f.x, f.y, f.z, __int_as_float(i0 + lane));
+    }
+    __syncwarp();
+    int cnt[kSlots];
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s) cnt[s] = 0;
+    walk_candidates(a, cc, s_cand[w], s_code[w], lane,
+                    [&](bool valid, int j, float bx, float by, float bz, bool self_cell) {
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s) {
+        const float4 fi = s_fi[w][s];
+        const V3 r = cell_to_r<ORTHO>(g, fi.x + bx, fi.y + by, fi.z + bz);
+        const bool hit = valid && s < ni && dot(r, r) < g.rcut2 &&
+                         !(self_cell && j == __float_as_int(fi.w));
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        const int k = cnt[s] + __popc(bal & lane_lt);
+        if (hit && k < cap)
+          a.list[size_t(i0 + s) * cap + k] = make_float4(r.x, r.y, r.z, __int_as_float(j));
+        cnt[s] += __popc(bal);
+      }
+    });
+    if (lane < ni) {
+      int c = 0;
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s) c = (s == lane) ? cnt[s] : c;
+      a.list_cnt[i0 + lane] = c <= cap ? c : -1;
+      if (c > cap) atomicOr(overflow, 1);
+    }
+    __syncwarp();
+  }
+}
+
+// Pair term from the lists: one warp per ion (pair-cell order); lane l takes hits l, l + 32,
+// ... in order -- the same per-lane order as the fused kernel, so the two paths give bitwise
+// equal results. Runs only when *cache_bad == 0.
+template <bool TAN, bool BATCH>
 __global__ void __launch_bounds__(kPairThreads) k_pair_listed(PairArgs a, int n) {
   if (*a.cache_bad != 0) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int i = blockIdx.x * kPairWarps + w;
   if (i >= n) return;   // uniform per warp
   const int frame = BATCH ? a.maps.sorted_frame[i] : 0;
-  const float gE = a.g_energy ? float(a.g_energy[frame]) : 0.f;
-  Ion I;
-  const float4 mi4 = a.pr.mu[i];
-  const float4 t = a.pr.tq[i];
-  const float4 d = a.pr.dr[i];
-  I.mu = mk(mi4.x, mi4.y, mi4.z);
-  I.q = mi4.w;
-  I.gE = gE;
-  I.dq = t.x;
-  I.dr = mk(d.x, d.y, d.z);
-  I.w = gE * I.mu + mk(t.y, t.z, t.w);   // gE mu + dmu + q dr
-  Acc<true> A;
+  const float gE = (TAN && a.g_energy) ? float(a.g_energy[frame]) : 0.f;
+  const Ion I = load_ion<TAN>(a, i, gE);
+  Acc<TAN> A;
   const int c = a.list_cnt[i];
   const float4* li = a.list + size_t(i) * a.list_cap;
   for (int k = lane; k < c; k += 32) {
     const float4 h = li[k];
-    interact<true>(a, I, __float_as_int(h.w), mk(h.x, h.y, h.z), A);
+    interact<TAN>(a, I, __float_as_int(h.w), mk(h.x, h.y, h.z), A);
   }
-  const float rx = warp_sum(A.gr.x), ry = warp_sum(A.gr.y), rz = warp_sum(A.gr.z);
-  const float q = warp_sum(A.gq);
-  const float mx = warp_sum(A.gm.x), my = warp_sum(A.gm.y), mz = warp_sum(A.gm.z);
+  constexpr int NA = kAccN<TAN>;
+  float v[NA];
+  if constexpr (!TAN) {
+    v[0] = A.phi;
+    v[1] = A.g.x;
+    v[2] = A.g.y;
+    v[3] = A.g.z;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[4 + k] = A.h[k];
+  } else {
+    v[0] = A.gr.x;
+    v[1] = A.gr.y;
+    v[2] = A.gr.z;
+    v[3] = A.gq;
+    v[4] = A.gm.x;
+    v[5] = A.gm.y;
+    v[6] = A.gm.z;
+  }
+#pragma unroll
+  for (int k = 0; k < NA; ++k) v[k] = warp_sum(v[k]);
   if (lane == 0) {
-    float* o = a.out + size_t(a.pr.idx[i].w) * 8;
-    o[0] = rx;
-    o[1] = ry;
-    o[2] = rz;
-    o[3] = q;
-    o[4] = mx;
-    o[5] = my;
-    o[6] = mz;
-    o[7] = 0.f;
+    float* o = a.out + size_t(a.pr.idx[i].w) * (TAN ? 8 : 10);
+#pragma unroll
+    for (int k = 0; k < NA; ++k) o[k] = v[k];
+    if (TAN) o[7] = 0.f;
   }
 }
 
@@ -551,20 +643,25 @@ PairArgs pair_args(pme_plan_t p, const double* g_energy, float* out) {
 
 }  // namespace
 
+// every frame of the plan has a diagonal cell matrix
+static bool plan_ortho(pme_plan_t p) {
+  for (int f = 0; f < p->nframes; ++f) {
+    const float* H = p->frames_h[f].g.H;
+    if (!(H[1] == 0.f && H[2] == 0.f && H[3] == 0.f && H[5] == 0.f && H[6] == 0.f && H[7] == 0.f))
+      return false;
+  }
+  return true;
+}
+
 int launch_pair(pme_plan_t p, cudaStream_t s, int n, bool tangent, const IonInputs& in,
-                const double* g_energy, float* out, bool record, const int* cache_bad) {
+                const double* g_energy, float* out, const int* skip) {
   (void)in;
   if (n == 0) return PME_OK;
   PairArgs a = pair_args(p, g_energy, out);
-  if (!record || tangent) a.list = nullptr;
-  a.cache_bad = tangent ? cache_bad : nullptr;
+  a.cache_bad = skip;
   const int grid = (a.ncells + kPairWarps - 1) / kPairWarps;
   if (grid == 0) return PME_OK;
-  bool ortho = true;
-  for (int f = 0; f < p->nframes && ortho; ++f) {
-    const float* H = p->frames_h[f].g.H;
-    ortho = H[1] == 0.f && H[2] == 0.f && H[3] == 0.f && H[5] == 0.f && H[6] == 0.f && H[7] == 0.f;
-  }
+  const bool ortho = plan_ortho(p);
   if (p->batch) {
     if (tangent) launch_k<true, true>(ortho, grid, s, a);
     else launch_k<false, true>(ortho, grid, s, a);
@@ -574,6 +671,24 @@ int launch_pair(pme_plan_t p, cudaStream_t s, int n, bool tangent, const IonInpu
   }
   count_launch();
   return check_launch(p, "k_pair");
+}
+
+int launch_pair_build(pme_plan_t p, cudaStream_t s, int n, int* overflow) {
+  int st = check_cuda(p, cudaMemsetAsync(overflow, 0, sizeof(int), s), "memset");
+  if (st || n == 0) return st;
+  PairArgs a = pair_args(p, nullptr, nullptr);
+  const int grid = (a.ncells + kPairWarps - 1) / kPairWarps;
+  if (grid == 0) return PME_OK;
+  const bool ortho = plan_ortho(p);
+  if (p->batch) {
+    if (ortho) k_pair_build<true, true><<<grid, kPairThreads, 0, s>>>(a, overflow);
+    else k_pair_build<true, false><<<grid, kPairThreads, 0, s>>>(a, overflow);
+  } else {
+    if (ortho) k_pair_build<false, true><<<grid, kPairThreads, 0, s>>>(a, overflow);
+    else k_pair_build<false, false><<<grid, kPairThreads, 0, s>>>(a, overflow);
+  }
+  count_launch();
+  return check_launch(p, "k_pair_build");
 }
 
 int launch_pair_cache_check(pme_plan_t p, cudaStream_t s, int n, const float* pos, int* bad) {
@@ -586,14 +701,19 @@ int launch_pair_cache_check(pme_plan_t p, cudaStream_t s, int n, const float* po
   return check_launch(p, "k_pair_cache_check");
 }
 
-int launch_pair_listed(pme_plan_t p, cudaStream_t s, int n, const double* g_energy, float* out,
-                       const int* cache_bad) {
+int launch_pair_listed(pme_plan_t p, cudaStream_t s, int n, bool tangent, const double* g_energy,
+                       float* out, const int* flag) {
   if (n == 0) return PME_OK;
   PairArgs a = pair_args(p, g_energy, out);
-  a.cache_bad = cache_bad;
+  a.cache_bad = flag;
   const int grid = (n + kPairWarps - 1) / kPairWarps;
-  if (p->batch) k_pair_listed<true><<<grid, kPairThreads, 0, s>>>(a, n);
-  else k_pair_listed<false><<<grid, kPairThreads, 0, s>>>(a, n);
+  if (p->batch) {
+    if (tangent) k_pair_listed<true, true><<<grid, kPairThreads, 0, s>>>(a, n);
+    else k_pair_listed<false, true><<<grid, kPairThreads, 0, s>>>(a, n);
+  } else {
+    if (tangent) k_pair_listed<true, false><<<grid, kPairThreads, 0, s>>>(a, n);
+    else k_pair_listed<false, false><<<grid, kPairThreads, 0, s>>>(a, n);
+  }
   count_launch();
   return check_launch(p, "k_pair_listed");
 }

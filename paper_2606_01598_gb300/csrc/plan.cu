@@ -691,7 +691,7 @@ static int forward_ewald(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool
   if (fork) {
     if (p->opts.overlap_pair && (st = fork_side(p, s))) return st;
     t = prof_begin(p, 6, ps);
-    if ((st = launch_pair(p, ps, n, false, in, nullptr, p->pair_out, false, nullptr))) return st;
+    if ((st = launch_pair(p, ps, n, false, in, nullptr, p->pair_out, nullptr))) return st;
     prof_end(p, t, ps);
   }
   t = prof_begin(p, 3, s);
@@ -715,15 +715,24 @@ static int run_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, double
   t = prof_begin(p, 0, s);
   if ((st = launch_sort(p, s, in, false, true, pair))) return st;
   prof_end(p, t, s);
-  // the pair term runs on the plan's side stream, concurrently with the mesh stages; it also
-  // records each ion's hits for a backward on the same positions
+  // the pair term runs on the plan's side stream, concurrently with the mesh stages: a list
+  // pass writes each ion's hits (kept for a backward on the same positions), then the
+  // list-driven evaluation; if a list overflowed, the fused pass does the work instead
   const bool fork = pair && n > 0;
   const bool record = fork && p->plist;
   cudaStream_t ps = p->opts.overlap_pair ? p->side : s;
   if (fork) {
     if (p->opts.overlap_pair && (st = fork_side(p, s))) return st;
     t = prof_begin(p, 6, ps);
-    if ((st = launch_pair(p, ps, n, false, in, nullptr, p->pair_out, record, nullptr))) return st;
+    if (record) {
+      if ((st = launch_pair_build(p, ps, n, p->cache_bad))) return st;
+      if ((st = launch_pair(p, ps, n, false, in, nullptr, p->pair_out, p->cache_bad))) return st;
+      const int te = prof_begin(p, 8, ps);
+      if ((st = launch_pair_listed(p, ps, n, false, nullptr, p->pair_out, p->cache_bad))) return st;
+      prof_end(p, te, ps);
+    } else if ((st = launch_pair(p, ps, n, false, in, nullptr, p->pair_out, nullptr))) {
+      return st;
+    }
     prof_end(p, t, ps);
   }
   if (record &&
@@ -772,9 +781,13 @@ static int run_backward(pme_plan_t p, cudaStream_t s, const IonInputs& in, const
     // pair term; otherwise the full cell-list pass runs
     const bool cached = p->plist && p->fwd_list_n == n;
     if (cached && (st = launch_pair_cache_check(p, ps, n, in.pos, p->cache_bad))) return st;
-    if ((st = launch_pair(p, ps, n, true, in, gE, p->pair_out, false, cached ? p->cache_bad : nullptr)))
+    if ((st = launch_pair(p, ps, n, true, in, gE, p->pair_out, cached ? p->cache_bad : nullptr)))
       return st;
-    if (cached && (st = launch_pair_listed(p, ps, n, gE, p->pair_out, p->cache_bad))) return st;
+    if (cached) {
+      const int te = prof_begin(p, B + 8, ps);
+      if ((st = launch_pair_listed(p, ps, n, true, gE, p->pair_out, p->cache_bad))) return st;
+      prof_end(p, te, ps);
+    }
     prof_end(p, t, ps);
   }
   t = prof_begin(p, B + 1, s);
@@ -1164,7 +1177,7 @@ int pme_pair(pme_plan_t p, void* stream, int n, const float* pos, const float* q
   in.mu = mu;
   in.n = n;
   if ((st = launch_sort(p, s, in, false, false, true))) return st;
-  if ((st = launch_pair(p, s, n, false, in, nullptr, out, false, nullptr))) return st;
+  if ((st = launch_pair(p, s, n, false, in, nullptr, out, nullptr))) return st;
   if (e_pair) {
     if ((st = launch_pair_energy(p, s, n, in, out))) return st;
     return launch_energy_final(p, s, p->epart, 0, true, false, 1.0, n, e_pair);

@@ -8,7 +8,7 @@ import torch
 import workloads as W
 from oracle import pme as O2
 
-from gpu_util import TOL_HVP, f32, prepared, relrmse
+from gpu_util import TOL_E, TOL_F, TOL_HVP, f32, prepared, relrmse
 
 pytestmark = pytest.mark.gpu
 
@@ -137,3 +137,51 @@ def test_backward_after_forward_reuses_pair_lists_bitwise(gb, name):
     for x, y in zip(moved, fresh2):
         assert torch.equal(x, y)
     warm.close()
+
+
+def test_pair_lists_disabled_and_overflowing_paths(gb):
+    # a plan whose lists would need more than 1 GiB has none (fused pass only); a clustered
+    # frame overflows the lists sized from the plan's mean density (fused fallback); both give
+    # the same forward and backward as the list path, bit for bit, and match the oracle
+    fr, mesh, p, a, rc = CASES["nacl512_p6"]()
+    pos, q, mu = prepared(fr)
+    gF, gphi, gfield = (f32(x) for x in W.tangent(fr.n, scale=1.0, seed=29))
+    c = lambda x: torch.tensor(np.float32(x), device="cuda")
+    gE = torch.tensor([0.3], dtype=torch.float64, device="cuda")
+    args = (c(pos), c(q), c(mu), gE, c(gF), c(gphi), c(gfield))
+    outs = []
+    for max_ions in (1024, 1 << 18):
+        plan = gb.Plan(fr.box, mesh, p, a, rc, max_ions=max_ions)
+        f = plan.forward(*args[:3], field_grad=True)
+        b = plan.backward(*args)
+        outs.append((f, b))
+        plan.close()
+    for k in outs[0][0]:
+        assert torch.equal(outs[0][0][k], outs[1][0][k]), k
+    for x, y in zip(outs[0][1], outs[1][1]):
+        assert torch.equal(x, y)
+    # 200 ions (at least 1 A apart) inside a 7 A ball in a 40 A box: each has 199 partners
+    # against lists sized for the mean density of 1024 ions in that box (160 entries)
+    rng = np.random.default_rng(31)
+    box = np.diag([40.0, 40.0, 40.0])
+    pts = []
+    while len(pts) < 200:
+        x = rng.uniform(-7.0, 7.0, 3)
+        if np.linalg.norm(x) < 7.0 and all(np.linalg.norm(x - y) > 1.0 for y in pts):
+            pts.append(x)
+    pts = 20.0 + np.array(pts)
+    qc = np.where(np.arange(200) % 2 == 0, 0.5, -0.5)
+    muc = rng.normal(0, 0.05, (200, 3))
+    pc, qc, muc = f32(pts), f32(qc), f32(muc)
+    plan = gb.Plan(box, (40, 40, 40), 6, 0.30, 9.0, max_ions=1024)
+    out = plan.forward(c(pc), c(qc), c(muc))
+    ref = O2.PMEOracle(box, (40, 40, 40), 6, 0.30, 9.0).evaluate(pc, qc, muc, field_grad=False)
+    scale = sum(abs(ref[k]) for k in ("e_recip", "e_pair", "e_self", "e_bg"))
+    assert abs(out["energy"].item() - ref["energy"]) < TOL_E * scale
+    assert relrmse(out["force"].cpu().numpy(), ref["force"]) < TOL_F
+    gFc, gphic, gfieldc = (f32(x) for x in W.tangent(200, seed=37))
+    got = plan.backward(c(pc), c(qc), c(muc), gE, c(gFc), c(gphic), c(gfieldc))
+    hv = O2.PMEOracle(box, (40, 40, 40), 6, 0.30, 9.0).hvp(pc, qc, muc, 0.3, gFc, gphic, gfieldc)
+    for g_, r_ in zip(got, hv):
+        assert relrmse(g_.cpu().numpy(), r_) < TOL_HVP
+    plan.close()
