@@ -200,9 +200,13 @@ struct pme_plan_s {
   float4* plist = nullptr;   // [max_ions][plist_cap] (r, j) per hit, pair-cell order
   int* plist_cnt = nullptr;  // [max_ions] hits per ion, -1 when more than plist_cap
   int plist_cap = 0;
-  float* pos_saved = nullptr;  // [3 max_ions] positions of that forward
-  int* cache_bad = nullptr;    // [1] result of the check in the backward
-  int fwd_list_n = -1;         // ions of the forward that recorded the lists (-1: none)
+  // inputs of the last forward, kept with its sorted order and records for the backward
+  float* in_saved = nullptr;   // [7 max_ions]: positions, then q at 3 max_ions, mu at 4 max_ions
+  int* in_flags = nullptr;     // [2]: in_diff, cache_bad (see launch_input_check)
+  int* in_diff = nullptr;
+  int* cache_bad = nullptr;
+  int fwd_n = -1;              // ions of that forward (-1: nothing saved / no longer valid)
+  bool fwd_lists = false;      // that forward recorded the pair lists
   int* ecount;               // [frames] energy items finished (reset by the last one)
   int* flags;                // device error flags
   // host-pointer staging

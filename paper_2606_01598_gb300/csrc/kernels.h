@@ -19,8 +19,16 @@ struct IonInputs {
 };
 
 // sort.cu: brick and pair-cell counting sorts (4 kernels), records in both orders.
+// reuse (nullable): when *reuse == 0 the plan's sorted order and primal records are those of
+// these inputs (a forward on them) and are kept; only charge sums and tangent records are
+// formed. A sort without reuse clears the plan's saved-forward state.
 int launch_sort(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent, bool need_mesh,
-                bool need_pair);
+                bool need_pair, const int* reuse);
+// Save the forward's inputs (positions, charges, dipoles) for a later backward.
+int save_inputs(pme_plan_t p, cudaStream_t s, const IonInputs& in);
+// *in_diff = 1 unless the inputs equal the saved ones bit for bit; *cache_bad = 1 when
+// *in_diff or (with_lists) a recorded pair list overflowed; both 0 otherwise.
+int launch_input_check(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool with_lists);
 
 // spread.cu: owner-computes spread of rho (and, with tangent, of the tangent density) of every
 // frame; frame f writes mesh + mesh_off (and mesh + tmesh_off).
@@ -50,8 +58,6 @@ int launch_pair(pme_plan_t p, cudaStream_t s, int n, bool tangent, const IonInpu
                 const double* g_energy, float* out, const int* skip);
 // Write every ion's hits to the plan's pair lists; *overflow = 1 when a list is too short.
 int launch_pair_build(pme_plan_t p, cudaStream_t s, int n, int* overflow);
-// *bad = 0 when pos is bit for bit the listed forward's and no list overflowed, else 1.
-int launch_pair_cache_check(pme_plan_t p, cudaStream_t s, int n, const float* pos, int* bad);
 // Pair term from the lists (runs only when *flag == 0).
 int launch_pair_listed(pme_plan_t p, cudaStream_t s, int n, bool tangent, const double* g_energy,
                        float* out, const int* flag);

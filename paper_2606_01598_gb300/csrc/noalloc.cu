@@ -210,7 +210,7 @@ extern "C" int pme_spread_noalloc(void* stream, const double box[9], const int m
   in.mu = mu;
   in.n = n;
   // launch_sort clears the brick and cell counters on the stream before counting
-  int st = launch_sort(&v, s, in, false, true, false);
+  int st = launch_sort(&v, s, in, false, true, false, nullptr);
   if (st) return st;
   const int rc = launch_spread(&v, s, false, rho);   // the frame's rho sits at offset 0
   v.frames_h = nullptr;                               // host views only: nothing to release

@@ -588,18 +588,6 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_listed(PairArgs a, int n)
   }
 }
 
-// *bad = 1 unless pos equals the positions of the forward that recorded the lists (bit for
-// bit) and no list overflowed; *bad must be 0 on entry.
-__global__ void __launch_bounds__(256) k_pair_cache_check(int n, const float* pos, const float* saved,
-                                                          const int* cnt, int* bad) {
-  bool ok = true;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 3 * n; k += gridDim.x * blockDim.x)
-    ok = ok && __float_as_int(pos[k]) == __float_as_int(saved[k]);
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
-    ok = ok && cnt[k] >= 0;
-  if (__any_sync(0xffffffffu, !ok) && (threadIdx.x & 31) == 0) *bad = 1;
-}
-
 template <bool TAN, bool BATCH>
 void launch_k(bool ortho, int grid, cudaStream_t s, const PairArgs& a) {
   if (ortho) k_pair<TAN, BATCH, true><<<grid, kPairThreads, 0, s>>>(a);
@@ -689,16 +677,6 @@ int launch_pair_build(pme_plan_t p, cudaStream_t s, int n, int* overflow) {
   }
   count_launch();
   return check_launch(p, "k_pair_build");
-}
-
-int launch_pair_cache_check(pme_plan_t p, cudaStream_t s, int n, const float* pos, int* bad) {
-  const int st = check_cuda(p, cudaMemsetAsync(bad, 0, sizeof(int), s), "memset");
-  if (st) return st;
-  if (n == 0) return PME_OK;
-  const int grid = std::min(152 * 4, (3 * n + 255) / 256);
-  k_pair_cache_check<<<grid, 256, 0, s>>>(n, pos, p->pos_saved, p->plist_cnt, bad);
-  count_launch();
-  return check_launch(p, "k_pair_cache_check");
 }
 
 int launch_pair_listed(pme_plan_t p, cudaStream_t s, int n, bool tangent, const double* g_energy,

@@ -261,7 +261,7 @@ static void free_plan(pme_plan_t p) {
                   p->mesh_out, p->pair_out, p->e_ion, p->epart, p->flags, p->stage_f,
                   p->stage_d, p->ew_kn, p->ew_kv, p->ew_S, p->ew_fx, p->ew_qm, p->frames_d,
                   p->map_buf, p->fft_work, p->sb.qpart, p->sb.qcount, p->eitem, p->ecount, p->sb.gcount,
-                  p->plist, p->plist_cnt, p->pos_saved, p->cache_bad};
+                  p->plist, p->plist_cnt, p->in_saved, p->in_flags};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int g = 0; g < p->nfgroups; ++g) {
@@ -554,9 +554,13 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
       p->plist_cap = cap;
       A(&p->plist, ni * size_t(cap));
       A(&p->plist_cnt, ni);
-      A(&p->pos_saved, 3 * ni);
-      A(&p->cache_bad, 1);
     }
+  }
+  A(&p->in_saved, 7 * ni);
+  A(&p->in_flags, 2);
+  if (st == PME_OK) {
+    p->in_diff = p->in_flags;
+    p->cache_bad = p->in_flags + 1;
   }
   if (st) return st;
   if ((st = check_cuda(p, cudaMemset(p->flags, 0, sizeof(int)), "memset"))) return st;
@@ -684,7 +688,7 @@ static int forward_ewald(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool
   const int n = in.n;
   int st, t;
   t = prof_begin(p, 0, s);
-  if ((st = launch_sort(p, s, in, false, false, pair))) return st;
+  if ((st = launch_sort(p, s, in, false, false, pair, nullptr))) return st;
   prof_end(p, t, s);
   const bool fork = pair && n > 0;
   cudaStream_t ps = p->opts.overlap_pair ? p->side : s;
@@ -711,9 +715,8 @@ static int run_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, double
   const bool pair = p->opts.include_pair != 0;
   if (p->opts.recip_method == 1) return forward_ewald(p, s, in, pair, e_out, f_out, p_out, fl_out, fg_out);
   int st, t;
-  p->fwd_list_n = -1;
   t = prof_begin(p, 0, s);
-  if ((st = launch_sort(p, s, in, false, true, pair))) return st;
+  if ((st = launch_sort(p, s, in, false, true, pair, nullptr))) return st;   // clears fwd_n
   prof_end(p, t, s);
   // the pair term runs on the plan's side stream, concurrently with the mesh stages: a list
   // pass writes each ion's hits (kept for a backward on the same positions), then the
@@ -735,10 +738,8 @@ static int run_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, double
     }
     prof_end(p, t, ps);
   }
-  if (record &&
-      (st = check_cuda(p, cudaMemcpyAsync(p->pos_saved, in.pos, sizeof(float) * 3 * size_t(n),
-                                          cudaMemcpyDeviceToDevice, s), "copy positions")))
-    return st;
+  // the inputs, with the sort and the lists made from them, serve a backward on the same inputs
+  if (n > 0 && (st = save_inputs(p, s, in))) return st;
   t = prof_begin(p, 1, s);
   if ((st = launch_spread(p, s, false, p->rho))) return st;
   prof_end(p, t, s);
@@ -758,7 +759,8 @@ static int run_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, double
   t = prof_begin(p, 7, s);
   if ((st = launch_combine_forward(p, s, in, true, fork, f_out, p_out, fl_out, fg_out, e_out, 1))) return st;
   prof_end(p, t, s);
-  if (record) p->fwd_list_n = n;
+  p->fwd_n = n > 0 ? n : -1;
+  p->fwd_lists = record;
   return PME_OK;
 }
 
@@ -770,17 +772,19 @@ static int run_backward(pme_plan_t p, cudaStream_t s, const IonInputs& in, const
   const bool pair = p->opts.include_pair != 0;
   constexpr int B = PME_STAGES_PER_PASS;
   int st, t;
+  // inputs bit for bit those of the plan's last forward (checked on the device): that
+  // forward's sorted order, records and pair lists are reused; otherwise everything is redone
+  const bool reuse = p->fwd_n == n;
+  const bool cached = reuse && pair && p->fwd_lists;
+  p->fwd_n = -1;   // a backward leaves nothing for a later one
   t = prof_begin(p, B + 0, s);
-  if ((st = launch_sort(p, s, in, true, true, pair))) return st;
+  if (reuse && (st = launch_input_check(p, s, in, cached))) return st;
+  if ((st = launch_sort(p, s, in, true, true, pair, reuse ? p->in_diff : nullptr))) return st;
   prof_end(p, t, s);
   cudaStream_t ps = p->opts.overlap_pair ? p->side : s;
   if (pair) {
     if (p->opts.overlap_pair && (st = fork_side(p, s))) return st;
     t = prof_begin(p, B + 6, ps);
-    // positions bit for bit those of the last forward: the recorded hit lists drive the
-    // pair term; otherwise the full cell-list pass runs
-    const bool cached = p->plist && p->fwd_list_n == n;
-    if (cached && (st = launch_pair_cache_check(p, ps, n, in.pos, p->cache_bad))) return st;
     if ((st = launch_pair(p, ps, n, true, in, gE, p->pair_out, cached ? p->cache_bad : nullptr)))
       return st;
     if (cached) {
@@ -969,7 +973,7 @@ int pme_plan_set_box(pme_plan_t p, const double box[9]) {
   D.g = g;
   D.ncells = nc;
   p->g = g;
-  p->fwd_list_n = -1;   // recorded pair lists belong to the old box
+  p->fwd_n = -1;   // the saved forward belongs to the old box
   std::memcpy(p->box, box, sizeof(double) * 9);
   if (nc > p->total_cells) {
     cudaFree(p->sb.count_c);
@@ -1121,7 +1125,7 @@ int pme_spread(pme_plan_t p, void* stream, int n, const float* pos, const float*
   in.q = q;
   in.mu = mu;
   in.n = n;
-  if ((st = launch_sort(p, s, in, false, true, false))) return st;
+  if ((st = launch_sort(p, s, in, false, true, false, nullptr))) return st;
   return launch_spread(p, s, false, rho);   // frame 0's rho sits at offset 0
 }
 
@@ -1158,7 +1162,7 @@ int pme_gather(pme_plan_t p, void* stream, int n, const float* pos, const float*
   in.pos = pos;
   in.q = nullptr;
   in.n = n;
-  if ((st = launch_sort(p, s, in, false, true, false))) return st;
+  if ((st = launch_sort(p, s, in, false, true, false, nullptr))) return st;
   return launch_gather(p, s, n, phi_mesh, false, nullptr, out);
 }
 
@@ -1176,7 +1180,7 @@ int pme_pair(pme_plan_t p, void* stream, int n, const float* pos, const float* q
   in.q = q;
   in.mu = mu;
   in.n = n;
-  if ((st = launch_sort(p, s, in, false, false, true))) return st;
+  if ((st = launch_sort(p, s, in, false, false, true, nullptr))) return st;
   if ((st = launch_pair(p, s, n, false, in, nullptr, out, nullptr))) return st;
   if (e_pair) {
     if ((st = launch_pair_energy(p, s, n, in, out))) return st;

@@ -9,7 +9,9 @@
 // k_scatter places ions in arrival order, and k_rank_records re-ranks each segment by caller
 // index, which makes the order -- and hence every later sum -- deterministic, while writing
 // the per-ion records both orders need. (The allocation-free spread, which needs no charge
-// sums, skips them.)
+// sums, skips them.) A backward whose inputs are bit for bit those of the plan's last forward
+// (checked on the device first) keeps that forward's order and records and only adds the
+// charge sums and the tangent records.
 #include <algorithm>
 
 #include "kernels.h"
@@ -78,7 +80,7 @@ __device__ void block_exclusive_scan(const int* count, int* start, int n) {
 template <bool BATCH>
 __global__ void __launch_bounds__(kSortThreads)
 k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int tangent, int* flags,
-      int nbricks, int ncells) {
+      int nbricks, int ncells, const int* reuse) {
   static_assert(kRedItem == kSortThreads, "one ion per thread");
   const int item = blockIdx.x;
   const int f = BATCH ? maps.item_frame[item] : 0;
@@ -86,8 +88,15 @@ k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int tangent, 
   int lo, hi;
   item_range(F, item, lo, hi);
   const int i = lo + int(threadIdx.x);
+  // reuse: the inputs are those of the forward whose sort is still in place; only the charge
+  // sums are formed
+  const bool re = reuse && *reuse == 0;
   float qa = 0.f, qb = 0.f;
-  if (i < hi) {
+  if (re && i < hi) {
+    const float qi = in.q ? in.q[i] : 0.f;
+    qa = isfinite(qi) ? qi : 0.f;
+    qb = (tangent && in.gphi) ? in.gphi[i] : 0.f;
+  } else if (i < hi) {
     const Geometry& g = F.g;
     const float rx = in.pos[3 * i], ry = in.pos[3 * i + 1], rz = in.pos[3 * i + 2];
     const float qi = in.q ? in.q[i] : 0.f;
@@ -134,7 +143,7 @@ k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int tangent, 
       }
     }
   }
-  if (last_item_done(sb.gcount, int(gridDim.x))) {
+  if (!re && last_item_done(sb.gcount, int(gridDim.x))) {
     block_exclusive_scan(sb.count_b, sb.start_b, nbricks);
     __syncthreads();
     block_exclusive_scan(sb.count_c, sb.start_c, ncells);
@@ -143,9 +152,9 @@ k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int tangent, 
 }
 
 __global__ void __launch_bounds__(kSortThreads)
-k_scatter(int n, SortBuffers sb, int need_mesh, int need_pair) {
+k_scatter(int n, SortBuffers sb, int need_mesh, int need_pair, const int* reuse) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || (reuse && *reuse == 0)) return;
   if (need_mesh) sb.perm_b[sb.start_b[sb.key_b[i]] + sb.slot_b[i]] = i;
   if (need_pair) sb.perm_c[sb.start_c[sb.key_c[i]] + sb.slot_c[i]] = i;
 }
@@ -161,7 +170,7 @@ __device__ __forceinline__ int stable_rank(const int* perm, int seg_lo, int seg_
 template <bool BATCH>
 __global__ void __launch_bounds__(kSortThreads)
 k_rank_records(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, MeshRecords mr,
-               PairRecords pr, int tangent, int need_mesh, int need_pair) {
+               PairRecords pr, int tangent, int need_mesh, int need_pair, const int* reuse) {
   const int n = in.n;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   const bool mesh_side = t < n;
@@ -169,12 +178,19 @@ k_rank_records(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, Mesh
   if (t >= n) return;
   if (mesh_side && !need_mesh) return;
   if (!mesh_side && !need_pair) return;
-  const int i = mesh_side ? sb.perm_b[t] : sb.perm_c[t];
-  int dest;
-  if (mesh_side) {
+  // reuse: the forward's records stay; only the tangent records are written, at the sorted
+  // slot the forward gave each ion
+  const bool re = reuse && *reuse == 0;
+  int i, dest;
+  if (re) {
+    dest = t;
+    i = mesh_side ? mr.idx[t].w : pr.idx[t].w;
+  } else if (mesh_side) {
+    i = sb.perm_b[t];
     const int k = sb.key_b[i];
     dest = stable_rank(sb.perm_b, sb.start_b[k], sb.start_b[k + 1], i, t);
   } else {
+    i = sb.perm_c[t];
     const int k = sb.key_c[i];
     dest = stable_rank(sb.perm_c, sb.start_c[k], sb.start_c[k + 1], i, t);
   }
@@ -193,8 +209,6 @@ k_rank_records(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, Mesh
 #pragma unroll
   for (int a = 0; a < 3; ++a)
     if (!isfinite(mu[a])) mu[a] = 0.f;
-  double s[3];
-  frac_coords(g, rx, ry, rz, s);
   float dq = 0.f, dr[3] = {0.f, 0.f, 0.f}, dmu[3] = {0.f, 0.f, 0.f};
   if (tangent) {
     if (in.gphi) dq = in.gphi[i];
@@ -211,6 +225,24 @@ k_rank_records(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, Mesh
   }
   // tangent dipole source d' = dmu + q dr
   const float dp[3] = {dmu[0] + qi * dr[0], dmu[1] + qi * dr[1], dmu[2] + qi * dr[2]};
+  if (re) {
+    if (mesh_side) {
+      float pd[3], pt[3];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        pd[b] = dp[0] * g.D[0 * 3 + b] + dp[1] * g.D[1 * 3 + b] + dp[2] * g.D[2 * 3 + b];
+        pt[b] = dr[0] * g.D[0 * 3 + b] + dr[1] * g.D[1 * 3 + b] + dr[2] * g.D[2 * 3 + b];
+      }
+      mr.tq[dest] = make_float4(dq, pd[0], pd[1], pd[2]);
+      mr.tt[dest] = make_float4(pt[0], pt[1], pt[2], 0.f);
+    } else {
+      pr.tq[dest] = make_float4(dq, dp[0], dp[1], dp[2]);
+      pr.dr[dest] = make_float4(dr[0], dr[1], dr[2], 0.f);
+    }
+    return;
+  }
+  double s[3];
+  frac_coords(g, rx, ry, rz, s);
   if (mesh_side) {
     int m0[3];
     float fr[3];
@@ -245,9 +277,34 @@ k_rank_records(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, Mesh
   }
 }
 
+// Bitwise comparison of the backward's inputs with the saved forward inputs.
+__global__ void __launch_bounds__(256)
+k_input_check(int n, IonInputs in, const float* saved, int ld, const int* list_cnt, int* in_diff,
+              int* cache_bad) {
+  bool same = true, lists = true;
+  const int stride = gridDim.x * blockDim.x;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int k = t0; k < 3 * n; k += stride) {
+    same = same && __float_as_int(in.pos[k]) == __float_as_int(saved[k]);
+    const float m = in.mu ? in.mu[k] : 0.f;
+    same = same && __float_as_int(m) == __float_as_int(saved[4 * ld + k]);
+  }
+  for (int k = t0; k < n; k += stride) {
+    const float q = in.q ? in.q[k] : 0.f;
+    same = same && __float_as_int(q) == __float_as_int(saved[3 * ld + k]);
+    if (list_cnt) lists = lists && list_cnt[k] >= 0;
+  }
+  const bool diff = __any_sync(0xffffffffu, !same);
+  const bool bad = __any_sync(0xffffffffu, !lists);
+  if ((threadIdx.x & 31) == 0) {
+    if (diff) *in_diff = 1;
+    if (diff || bad) *cache_bad = 1;
+  }
+}
+
 template <bool BATCH>
 int launch_sort_t(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent, bool need_mesh,
-                  bool need_pair) {
+                  bool need_pair, const int* reuse) {
   const int n = in.n;
   const int nblk = (n + kSortThreads - 1) / kSortThreads;
   FrameDesc one = p->frames_h[0];
@@ -265,18 +322,18 @@ int launch_sort_t(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangen
   {
     const int items = BATCH ? p->total_items : one.nitems;
     k_bin<BATCH><<<items, kSortThreads, 0, s>>>(one, p->maps, in, p->sb, tangent ? 1 : 0, p->flags,
-                                                p->total_bricks, p->total_cells);
+                                                p->total_bricks, p->total_cells, reuse);
     count_launch();
     if ((st = check_launch(p, "k_bin"))) return st;
   }
   if (nblk > 0) {
-    k_scatter<<<nblk, kSortThreads, 0, s>>>(n, p->sb, need_mesh ? 1 : 0, need_pair ? 1 : 0);
+    k_scatter<<<nblk, kSortThreads, 0, s>>>(n, p->sb, need_mesh ? 1 : 0, need_pair ? 1 : 0, reuse);
     count_launch();
     if ((st = check_launch(p, "k_scatter"))) return st;
     const int nblk2 = (2 * n + kSortThreads - 1) / kSortThreads;
     k_rank_records<BATCH><<<nblk2, kSortThreads, 0, s>>>(one, p->maps, in, p->sb, p->mr, p->pr,
                                                          tangent ? 1 : 0, need_mesh ? 1 : 0,
-                                                         need_pair ? 1 : 0);
+                                                         need_pair ? 1 : 0, reuse);
     count_launch();
     if ((st = check_launch(p, "k_rank_records"))) return st;
   }
@@ -285,10 +342,35 @@ int launch_sort_t(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangen
 
 }  // namespace
 
+int save_inputs(pme_plan_t p, cudaStream_t s, const IonInputs& in) {
+  const size_t n = size_t(in.n), ld = size_t(p->max_ions);
+  float* sv = p->in_saved;
+  int st = check_cuda(p, cudaMemcpyAsync(sv, in.pos, sizeof(float) * 3 * n, cudaMemcpyDeviceToDevice, s),
+                      "save positions");
+  if (!st) st = in.q ? check_cuda(p, cudaMemcpyAsync(sv + 3 * ld, in.q, sizeof(float) * n,
+                                                     cudaMemcpyDeviceToDevice, s), "save charges")
+                     : check_cuda(p, cudaMemsetAsync(sv + 3 * ld, 0, sizeof(float) * n, s), "save charges");
+  if (!st) st = in.mu ? check_cuda(p, cudaMemcpyAsync(sv + 4 * ld, in.mu, sizeof(float) * 3 * n,
+                                                      cudaMemcpyDeviceToDevice, s), "save dipoles")
+                      : check_cuda(p, cudaMemsetAsync(sv + 4 * ld, 0, sizeof(float) * 3 * n, s), "save dipoles");
+  return st;
+}
+
+int launch_input_check(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool with_lists) {
+  int st = check_cuda(p, cudaMemsetAsync(p->in_flags, 0, 2 * sizeof(int), s), "memset");
+  if (st || in.n == 0) return st;
+  const int grid = std::min(152 * 4, (3 * in.n + 255) / 256);
+  k_input_check<<<grid, 256, 0, s>>>(in.n, in, p->in_saved, p->max_ions, with_lists ? p->plist_cnt : nullptr,
+                                      p->in_diff, p->cache_bad);
+  count_launch();
+  return check_launch(p, "k_input_check");
+}
+
 int launch_sort(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent, bool need_mesh,
-                bool need_pair) {
-  return p->batch ? launch_sort_t<true>(p, s, in, tangent, need_mesh, need_pair)
-                  : launch_sort_t<false>(p, s, in, tangent, need_mesh, need_pair);
+                bool need_pair, const int* reuse) {
+  if (!reuse) p->fwd_n = -1;   // the sorted records no longer belong to the saved inputs
+  return p->batch ? launch_sort_t<true>(p, s, in, tangent, need_mesh, need_pair, reuse)
+                  : launch_sort_t<false>(p, s, in, tangent, need_mesh, need_pair, reuse);
 }
 
 }  // namespace gbpme

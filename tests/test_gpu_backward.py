@@ -185,3 +185,39 @@ def test_pair_lists_disabled_and_overflowing_paths(gb):
     for g_, r_ in zip(got, hv):
         assert relrmse(g_.cpu().numpy(), r_) < TOL_HVP
     plan.close()
+
+
+def test_backward_reuse_is_invalidated_when_it_must_be(gb):
+    # the forward's sort, records and pair lists serve only the first backward on exactly the
+    # forward's inputs; every other sequence must give what a fresh plan gives, bit for bit
+    fr, mesh, p, a, rc = CASES["nacl1000_ragged_p7"]()
+    pos, q, mu = prepared(fr)
+    gF, gphi, gfield = (f32(x) for x in W.tangent(fr.n, scale=1.0, seed=41))
+    c = lambda x: torch.tensor(np.float32(x), device="cuda")
+    gE = torch.tensor([0.6], dtype=torch.float64, device="cuda")
+    P, Q, MU = c(pos), c(q), c(mu)
+    tang = (gE, c(gF), c(gphi), c(gfield))
+    fresh = lambda *x: gb.Plan(fr.box, mesh, p, a, rc, max_ions=1024).backward(*x)
+    ref = fresh(P, Q, MU, *tang)
+    plan = gb.Plan(fr.box, mesh, p, a, rc, max_ions=1024)
+    # a second backward after one forward
+    plan.forward(P, Q, MU)
+    for _ in range(2):
+        for x, y in zip(plan.backward(P, Q, MU, *tang), ref):
+            assert torch.equal(x, y)
+    # the charges changed between forward and backward
+    Q2 = Q.clone()
+    Q2[7] += 0.125
+    plan.forward(P, Q, MU)
+    for x, y in zip(plan.backward(P, Q2, MU, *tang), fresh(P, Q2, MU, *tang)):
+        assert torch.equal(x, y)
+    # a stage call on other positions between forward and backward
+    plan.forward(P, Q, MU)
+    plan.spread(P.flip(0), Q, MU)
+    for x, y in zip(plan.backward(P, Q, MU, *tang), ref):
+        assert torch.equal(x, y)
+    # dipoles given to the forward, none to the backward
+    plan.forward(P, Q, MU)
+    for x, y in zip(plan.backward(P, Q, None, *tang), fresh(P, Q, None, *tang)):
+        assert torch.equal(x, y)
+    plan.close()
