@@ -30,6 +30,12 @@ product that the force-matching loss (Eq. loss) needs. Field gradients at the io
 obtained by autograd of the interpolated potential at a probe point with the sources held
 fixed.
 
+The virial W_ab = -dE/d(eps_ab) under the homogeneous strain r -> (I + eps) r of positions
+and lattice vectors, with the dipoles held fixed (an extension: stress is not among the
+paper's outputs), is evaluated from its definition by central differences of the energy,
+and pinned against a term-by-term evaluation and the scaling identity
+tr W = E_qq + 2 E_qmu + 3 E_mumu of the exact (O1) Ewald sum.
+
 Pins (tests/test_oracle_pme.py): agreement with O1 within the mesh error, which falls with
 mesh refinement and with order and is larger without deconvolution; the two forms of Eq.
 energy_recip; the dipole as the limit of a charge pair; exact invariance under whole-mesh-
@@ -239,6 +245,77 @@ class PMEOracle:
             return E, dict(e_recip=self.k * E_rec, e_pair=self.k * E_pair,
                            e_self=self.k * E_self, e_bg=self.k * E_bg)
         return E
+
+    # -- virial (stress), an extension beyond the paper's outputs ------------------------
+    def strained(self, eps):
+        """The same PME on the homogeneously strained cell, lattice rows a_i -> (I + eps) a_i."""
+        F = np.eye(3) + np.asarray(eps, np.float64)
+        return PMEOracle(self.C @ F.T, self.N, self.p, self.alpha, self.rcut,
+                         influence_power=self.gamma, deconvolution=self.deconv, coulomb_k=self.k,
+                         include_pair=self.include_pair, include_self=self.include_self,
+                         include_background=self.include_bg)
+
+    def virial(self, pos, q, mu, h: float = 1e-5):
+        """W_ab = -dE/d(eps_ab) for the homogeneous strain r -> (I + eps) r, a_i -> (I + eps) a_i
+        with the dipoles held fixed: the definition, by central differences of the energy.
+        The pair list (with its image shifts, which strain as lattice vectors) is held fixed,
+        so no pair crosses the cutoff inside the difference stencil."""
+        pos = np.asarray(pos, np.float64)
+        q = np.asarray(q, np.float64)
+        mu = np.zeros_like(pos) if mu is None else np.asarray(mu, np.float64)
+        pairs = self._pairs(pos) if self.include_pair else None
+        W = np.zeros((3, 3))
+        for a in range(3):
+            for b in range(3):
+                E = []
+                for sgn in (1.0, -1.0):
+                    eps = np.zeros((3, 3))
+                    eps[a, b] = sgn * h
+                    F = np.eye(3) + eps
+                    pr = None if pairs is None else (pairs[0], pairs[1], pairs[2] @ F.T)
+                    E.append(float(self.strained(eps).energy(_t(pos @ F.T), _t(q), _t(mu), pairs=pr)))
+                W[a, b] = -(E[0] - E[1]) / (2 * h)
+        return W
+
+    def virial_terms(self, pos, q, mu):
+        """The same virial assembled term by term (a second evaluation that pins virial()):
+        reciprocal  E_rec I - (1/V) sum_n G C |rho_hat|^2 (1/k^2 + 1/(4 alpha^2)) k (x) k
+                    + sum_i (dE_rec/dmu_i) (x) mu_i        (the mesh sees mu through C^-1),
+        pair        -1/2 sum_(i,j) (du_ij/dr_ij) (x) r_ij  (each ordered pair),
+        background  E_bg I; the self terms do not depend on the cell. Times coulomb_k."""
+        pos_t = _t(pos)
+        q_t = _t(q)
+        mu_t = _t(np.zeros_like(pos) if mu is None else mu).requires_grad_(True)
+        rho = self.mesh_density(pos_t, q_t, mu_t)
+        E_rec = self.recip_energy(rho)
+        (gmu,) = torch.autograd.grad(E_rec, (mu_t,))
+        rho_hat = torch.fft.fftn(rho.detach().reshape(self.N)).numpy()
+        n = [np.fft.fftfreq(Na) * Na for Na in self.N]
+        nx, ny, nz = np.meshgrid(*n, indexing="ij")
+        kvec = (nx[..., None] * self.b[0] + ny[..., None] * self.b[1] + nz[..., None] * self.b[2])
+        k2 = np.einsum("...c,...c->...", kvec, kvec)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            wgt = np.where(k2 > 0, self.GC.numpy() * np.abs(rho_hat) ** 2
+                           * (1.0 / k2 + 1.0 / (4 * self.alpha ** 2)), 0.0)
+        S = np.einsum("xyz,xyza,xyzb->ab", wgt, kvec, kvec)
+        W = float(E_rec.detach()) * np.eye(3) - S / self.V + gmu.numpy().T @ mu_t.detach().numpy()
+        if self.include_pair:
+            i, j, sh = self._pairs(np.asarray(pos, np.float64))
+            i, j = torch.as_tensor(i), torch.as_tensor(j)
+            r = (pos_t[i] - pos_t[j] + _t(sh)).requires_grad_(True)
+            r2 = (r * r).sum(-1)
+            B0, B1, B2 = self._bfuncs(r2, self.alpha, 2)
+            m = mu_t.detach()
+            mir = (m[i] * r).sum(-1)
+            mjr = (m[j] * r).sum(-1)
+            u = (q_t[i] * q_t[j] * B0 + (q_t[i] * mjr - q_t[j] * mir) * B1
+                 + (m[i] * m[j]).sum(-1) * B1 - mir * mjr * B2)
+            (du,) = torch.autograd.grad(u.sum(), (r,))
+            W = W - 0.5 * (du.T @ r.detach()).numpy()
+        if self.include_bg:
+            Q = float(q_t.sum())
+            W = W - math.pi * Q * Q / (2 * self.V * self.alpha ** 2) * np.eye(3)
+        return self.k * W
 
     # -- public evaluation --------------------------------------------------------------
     def evaluate(self, pos, q, mu, *, field_grad: bool = True, pairs=None):
