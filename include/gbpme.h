@@ -142,6 +142,21 @@ int pme_backward(pme_plan_t plan, void* stream, int n, const float* pos, const f
                  const float* g_phi, const float* g_field, float* grad_pos, float* grad_q,
                  float* grad_mu);
 
+/* Forward plus the virial (an extension of the paper's outputs, for stress / NPT training):
+ *   virial [9] float64, row-major, W_ab = -dE/d(eps_ab) for the homogeneous strain
+ *   r -> (I + eps) r of the positions and the lattice vectors with the dipoles held fixed:
+ *   W = k (E_rec I - (1/V) sum_n G C |rho_hat|^2 (1/k^2 + 1/(4 alpha^2)) k (x) k
+ *          + sum_i (grad phi_mesh)_i (x) mu_i + 1/2 sum_(i,j) F_ij (x) r_ij + E_bg I)
+ *   (not symmetric when dipoles are present). energy and virial are required (device or
+ *   host pointers); the other outputs as in pme_forward.
+ * Needs the particle-mesh reciprocal method and, with the pair term on, the plan's pair-hit
+ * lists (PME_ERR_UNSUPPORTED for a plan too large to hold them). If a list overflows at run
+ * time the pair part of the virial cannot be formed: the next pme_sync_status reports
+ * PME_ERR_UNSUPPORTED. */
+int pme_forward_virial(pme_plan_t plan, void* stream, int n, const float* pos, const float* q,
+                       const float* mu, double* energy, float* force, float* phi, float* field,
+                       float* field_grad, double* virial);
+
 /* ---- batched frames ----------------------------------------------------------------------
  * One plan over F frames stored back to back in the per-ion arrays: frame f owns ions
  * [offsets[f], offsets[f+1]) (offsets[0] = 0, host array of F+1), with its own box
@@ -162,6 +177,11 @@ int pme_batch_frames(pme_plan_t plan);
 int pme_batch_forward(pme_plan_t plan, void* stream, const float* pos, const float* q,
                       const float* mu, double* energy, float* force, float* phi, float* field,
                       float* field_grad);
+
+/* As pme_forward_virial for every frame: virial [F][9] float64. */
+int pme_batch_forward_virial(pme_plan_t plan, void* stream, const float* pos, const float* q,
+                             const float* mu, double* energy, float* force, float* phi,
+                             float* field, float* field_grad, double* virial);
 
 /* As pme_backward for every frame; g_energy is [F] float64 (one cotangent per frame). */
 int pme_batch_backward(pme_plan_t plan, void* stream, const float* pos, const float* q,

@@ -39,6 +39,7 @@ _SIGS = {
     "pme_status_string": (ctypes.c_char_p, [c_int]),
     "pme_sync_status": (c_int, [c_void_p, c_void_p]),
     "pme_forward": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 8),
+    "pme_forward_virial": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 9),
     "pme_backward": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 10),
     "pme_spread": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 4),
     "pme_solve": (c_int, [c_void_p, c_void_p] + [c_void_p] * 3),
@@ -52,6 +53,7 @@ _SIGS = {
                                  c_double, c_double, ctypes.POINTER(PMEOpts)]),
     "pme_batch_frames": (c_int, [c_void_p]),
     "pme_batch_forward": (c_int, [c_void_p, c_void_p] + [c_void_p] * 8),
+    "pme_batch_forward_virial": (c_int, [c_void_p, c_void_p] + [c_void_p] * 9),
     "pme_batch_backward": (c_int, [c_void_p, c_void_p] + [c_void_p] * 10),
 }
 

@@ -56,6 +56,12 @@ struct CombineArgs {
   double kd;          // coulomb_k
   double* eitem;
   int* ecount;
+  // frame virials (forward; virial_out null: not wanted), row-major [9] per frame:
+  // W = k (E_rec I - S / V + sum_i grad phi_mesh,i (x) mu_i + W_pair + E_bg I)
+  double* virial_out;
+  const double* vparts;   // [6 * influence blocks] S_ab (xx yy zz xy xz yz)
+  const float* pvir;      // [n][9] per-ion pair virial (null without the pair term)
+  double* vitem;          // [9 * items]
 };
 
 // pi / (V alpha^2) of the ion's frame, or 0 without the background term
@@ -73,6 +79,7 @@ __global__ void __launch_bounds__(kCombThreads) k_combine_forward(CombineArgs a)
   item_range(F, item, lo, hi);
   const int i = lo + int(threadIdx.x);
   double e_i = 0.0;
+  float vi[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // virial terms of ion i
   if (i < hi) {
     const float bg = bg_factor(a, F);
     float qi = a.in.q[i];
@@ -119,6 +126,20 @@ __global__ void __launch_bounds__(kCombThreads) k_combine_forward(CombineArgs a)
     e_i = 0.5 * (double(qi) * w[0] + double(mu[0]) * w[1] + double(mu[1]) * w[2] +
                  double(mu[2]) * w[3]) -
           a.e_self_q * double(qi) * qi - a.e_self_mu * mu2;
+    if (a.virial_out) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          vi[3 * r + c] = v[1 + r] * mu[c] + (a.pvir ? a.pvir[size_t(i) * 9 + 3 * r + c] : 0.f);
+    }
+  }
+  if (a.virial_out) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      const double t = block_sum_f(vi[c]);
+      if (threadIdx.x == 0) a.vitem[9 * item + c] = t;
+    }
   }
   if (!a.energy_out) return;   // uniform
   const double e_item = block_sum_d(e_i);
@@ -130,6 +151,21 @@ __global__ void __launch_bounds__(kCombThreads) k_combine_forward(CombineArgs a)
   for (int k = threadIdx.x; k < F.nitems; k += blockDim.x) ep += __ldcg(a.eitem + F.item_off + k);
   rp = block_sum_d(rp);
   ep = block_sum_d(ep);
+  double W[9], S[6];
+  if (a.virial_out) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      double t = 0.0;
+      for (int k = threadIdx.x; k < F.nitems; k += blockDim.x) t += __ldcg(a.vitem + 9 * (F.item_off + k) + c);
+      W[c] = block_sum_d(t);
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      double t = 0.0;
+      for (int k = threadIdx.x; k < F.infl_nblk; k += blockDim.x) t += a.vparts[6 * (F.infl_blk_off + k) + c];
+      S[c] = block_sum_d(t);
+    }
+  }
   if (threadIdx.x == 0) {
     const double V = F.g.volume;
     const double coef = a.recip_kind == 1 ? 0.5 / V : (a.recip_kind == 2 ? 4.0 * kPi / V : 0.0);
@@ -139,6 +175,12 @@ __global__ void __launch_bounds__(kCombThreads) k_combine_forward(CombineArgs a)
       e_bg = -kPi * Q * Q / (2.0 * V * double(a.alpha) * double(a.alpha));
     }
     a.energy_out[f] = a.kd * (coef * rp + ep + e_bg);
+    if (a.virial_out) {
+      const int sidx[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};   // S_ab from xx yy zz xy xz yz
+      const double diag = coef * rp + e_bg;
+      for (int c = 0; c < 9; ++c)
+        a.virial_out[9 * f + c] = a.kd * (W[c] - S[sidx[c]] / V + ((c % 4) == 0 ? diag : 0.0));
+    }
     a.ecount[f] = 0;
   }
 }
@@ -221,7 +263,7 @@ CombineArgs base_args(pme_plan_t p, const IonInputs& in) {
 
 int launch_combine_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool with_mesh,
                            bool with_pair, float* force, float* phi, float* field,
-                           float* field_grad, double* energy, int recip_kind) {
+                           float* field_grad, double* energy, int recip_kind, double* virial) {
   CombineArgs a = base_args(p, in);
   a.mesh_out = p->mesh_out;
   a.pair_out = p->pair_out;
@@ -237,6 +279,10 @@ int launch_combine_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, bo
   a.kd = p->opts.coulomb_k;
   a.eitem = p->eitem;
   a.ecount = p->ecount;
+  a.virial_out = (virial && energy) ? virial : nullptr;
+  a.vparts = p->vpart;
+  a.pvir = with_pair ? p->pvir : nullptr;
+  a.vitem = p->vitem;
   int items;
   if (p->batch) {
     items = p->total_items;

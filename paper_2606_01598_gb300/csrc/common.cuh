@@ -206,6 +206,10 @@ struct pme_plan_s {
   int* in_diff = nullptr;
   int* cache_bad = nullptr;
   int fwd_n = -1;              // ions of that forward (-1: nothing saved / no longer valid)
+  // virial partial sums
+  double* vpart = nullptr;     // [6 * influence blocks] k-space sums S_ab
+  float* pvir = nullptr;       // [max_ions][9] per-ion pair virial
+  double* vitem = nullptr;     // [9 * items] per-item sums
   bool fwd_lists = false;      // that forward recorded the pair lists
   int* ecount;               // [frames] energy items finished (reset by the last one)
   int* flags;                // device error flags
@@ -404,5 +408,6 @@ __device__ __forceinline__ void item_range(const FrameDesc& F, int item, int& lo
 // Device error flag bits.
 constexpr int kFlagNonFinite = 1;
 constexpr int kFlagTimeout = 2;
+constexpr int kFlagVirialLost = 4;   // a virial pass fell back to the fused pair kernel
 
 }  // namespace gbpme

@@ -28,10 +28,12 @@ __device__ __forceinline__ void comp_add(float& s, float& c, float v) {
   s = t;
 }
 
-template <bool BATCH>
+// VIR: also the virial sums S_ab = sum_n w G C |rho_hat|^2 (1/k^2 + 1/(4 alpha^2)) k_a k_b
+// (xx yy zz xy xz yz) into vparts[6 * block + c].
+template <bool BATCH, bool VIR>
 __global__ void __launch_bounds__(kInflThreads)
 k_influence(FrameDesc one, FrameMaps maps, float2* spec, int tangent, const float* dconv,
-            float inv4a2, double* partials) {
+            float inv4a2, double* partials, double* vparts) {
   const FrameDesc& F = frame_at<BATCH>(one, maps, BATCH ? maps.blk_frame[blockIdx.x] : 0);
   const Geometry& g = F.g;
   const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2];
@@ -44,6 +46,7 @@ k_influence(FrameDesc one, FrameMaps maps, float2* spec, int tangent, const floa
   float2* sp = spec + F.spec_off;
   float2* tp = spec + F.tspec_off;
   float e = 0.f, ec = 0.f;
+  float sv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, sc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   const int step = F.infl_nblk * blockDim.x;
   for (int idx = (blockIdx.x - F.infl_blk_off) * blockDim.x + threadIdx.x; idx < Mh; idx += step) {
     const int r = fdiv(idx, F.div_zh);
@@ -61,7 +64,17 @@ k_influence(FrameDesc one, FrameMaps maps, float2* spec, int tangent, const floa
     if (k2 > 0.f) gc = four_pi * expf(-k2 * inv4a2) / k2 * cx[ix] * cy[iy] * cz[iz];
     const float2 v = sp[idx];
     const float w = (iz == 0 || (2 * iz == N2)) ? 1.f : 2.f;
-    comp_add(e, ec, w * gc * (v.x * v.x + v.y * v.y));
+    const float eg = w * gc * (v.x * v.x + v.y * v.y);
+    comp_add(e, ec, eg);
+    if (VIR && k2 > 0.f) {
+      const float t = eg * (1.f / k2 + inv4a2);
+      comp_add(sv[0], sc[0], t * kx * kx);
+      comp_add(sv[1], sc[1], t * ky * ky);
+      comp_add(sv[2], sc[2], t * kz * kz);
+      comp_add(sv[3], sc[3], t * kx * ky);
+      comp_add(sv[4], sc[4], t * kx * kz);
+      comp_add(sv[5], sc[5], t * ky * kz);
+    }
     const float f = gc * g.inv_volume;
     sp[idx] = make_float2(v.x * f, v.y * f);
     if (tangent) {
@@ -85,6 +98,28 @@ k_influence(FrameDesc one, FrameMaps maps, float2* spec, int tangent, const floa
 #pragma unroll
     for (int w = 0; w < kInflThreads / 32; ++w) t += wsum[w];
     partials[blockIdx.x] = t;
+  }
+  if (VIR) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      float v = sv[c], cc = sc[c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        const float c2 = __shfl_xor_sync(0xffffffffu, cc, o);
+        cc += c2;
+        comp_add(v, cc, v2);
+      }
+      __syncthreads();
+      if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = double(v) + double(cc);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kInflThreads / 32; ++w) t += wsum[w];
+        vparts[6 * blockIdx.x + c] = t;
+      }
+    }
   }
 }
 
@@ -137,15 +172,19 @@ int influence_blocks(const Geometry& g) {
 }
 
 int launch_influence(pme_plan_t p, cudaStream_t s, cufftComplex* spec, bool tangent,
-                     double* partials) {
+                     double* partials, double* vparts) {
   const float inv4a2 = float(1.0 / (4.0 * p->alpha * p->alpha));
   FrameDesc one = p->frames_h[0];
-  if (p->batch)
-    k_influence<true><<<p->total_blocks, kInflThreads, 0, s>>>(one, p->maps, reinterpret_cast<float2*>(spec),
-                                                              tangent ? 1 : 0, p->dconv_all, inv4a2, partials);
-  else
-    k_influence<false><<<one.infl_nblk, kInflThreads, 0, s>>>(one, p->maps, reinterpret_cast<float2*>(spec),
-                                                             tangent ? 1 : 0, p->dconv_all, inv4a2, partials);
+  float2* sp = reinterpret_cast<float2*>(spec);
+  const int grid = p->batch ? p->total_blocks : one.infl_nblk;
+  const int tg = tangent ? 1 : 0;
+  if (p->batch) {
+    if (vparts) k_influence<true, true><<<grid, kInflThreads, 0, s>>>(one, p->maps, sp, tg, p->dconv_all, inv4a2, partials, vparts);
+    else k_influence<true, false><<<grid, kInflThreads, 0, s>>>(one, p->maps, sp, tg, p->dconv_all, inv4a2, partials, vparts);
+  } else {
+    if (vparts) k_influence<false, true><<<grid, kInflThreads, 0, s>>>(one, p->maps, sp, tg, p->dconv_all, inv4a2, partials, vparts);
+    else k_influence<false, false><<<grid, kInflThreads, 0, s>>>(one, p->maps, sp, tg, p->dconv_all, inv4a2, partials, vparts);
+  }
   count_launch();
   return check_launch(p, "k_influence");
 }

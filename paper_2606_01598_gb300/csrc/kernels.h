@@ -37,7 +37,7 @@ int launch_spread(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh);
 // influence.cu: in-place G C / V multiply of every frame's spectrum (and tangent spectrum)
 // and the float64 energy partials (one per block, blocks grouped by frame).
 int launch_influence(pme_plan_t p, cudaStream_t s, cufftComplex* spec, bool tangent,
-                     double* partials);
+                     double* partials, double* vparts = nullptr);
 // Per-frame energies: out[f] = k (recip_coef(f) * sum of f's block partials + sum of f's
 // per-ion energies e_ion + background(Q_f)); recip_coef = 1/(2V) for the mesh, 4 pi / V for
 // the explicit k-sum, 0 without a reciprocal part.
@@ -54,20 +54,25 @@ int launch_gather(pme_plan_t p, cudaStream_t s, int n, const float* mesh, bool t
 
 // pair.cu: real-space erfc pair term over the cell list, same output layouts as gather.
 // The fused pass; skip (nullable): return at once when *skip == 0.
+// virial (forward): the fused pass cannot form the pair virial and sets the lost-virial flag.
 int launch_pair(pme_plan_t p, cudaStream_t s, int n, bool tangent, const IonInputs& in,
-                const double* g_energy, float* out, const int* skip);
+                const double* g_energy, float* out, const int* skip, bool virial = false);
 // Write every ion's hits to the plan's pair lists; *overflow = 1 when a list is too short.
 int launch_pair_build(pme_plan_t p, cudaStream_t s, int n, int* overflow);
 // Pair term from the lists (runs only when *flag == 0).
+// virial (forward): also each ion's 1/2 sum_j F_ij (x) r_ij into the plan's pvir [n][9].
 int launch_pair_listed(pme_plan_t p, cudaStream_t s, int n, bool tangent, const double* g_energy,
-                       float* out, const int* flag);
+                       float* out, const int* flag, bool virial = false);
 
 // combine.cu: add the parts, the self and background terms, apply coulomb_k, write outputs;
 // with energy non-null also the frame energies, as launch_energy_final with the per-ion
 // energies of this pass (recip_kind as there).
+// virial (nullable, needs energy): also the frame virials [9] per frame from the plan's
+// k-space sums (vpart) and per-ion pair virials (pvir).
 int launch_combine_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool with_mesh,
                            bool with_pair, float* force, float* phi, float* field,
-                           float* field_grad, double* energy, int recip_kind);
+                           float* field_grad, double* energy, int recip_kind,
+                           double* virial = nullptr);
 int launch_combine_backward(pme_plan_t p, cudaStream_t s, const IonInputs& in,
                             const double* g_energy, float* grad_pos, float* grad_q,
                             float* grad_mu);

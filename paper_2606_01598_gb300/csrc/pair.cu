@@ -63,6 +63,10 @@ struct PairArgs {
   // *cache_bad == 0: the lists hold for this pass -- the fused kernel returns at once and
   // the list-driven one runs (fused kernel: null means always run)
   const int* cache_bad;
+  // virial: per-ion 1/2 sum_j F_ij (x) r_ij [9] (caller order), forward list pass only
+  float* vir_out;
+  // fused fallback of a virial pass: it cannot form the pair virial, so it reports
+  int* vir_lost;
   float alpha;
   float c1, c2, c3, c4;   // (2 alpha^2)^l / (alpha sqrt(pi)), l = 1..4
 };
@@ -107,7 +111,10 @@ struct Ion {
 };
 
 template <bool TAN>
-__device__ __forceinline__ void interact(const PairArgs& a, const Ion& I, int j, V3 r, Acc<TAN>& A) {
+// vir (forward only, nullable): adds 1/2 F_ij (x) r_ij, with F_ij = -(q_i grad phi_ij +
+// (grad grad phi_ij) mu_i) the force on i from j, row-major [9].
+__device__ __forceinline__ void interact(const PairArgs& a, const Ion& I, int j, V3 r, Acc<TAN>& A,
+                                         float* vir = nullptr) {
   const float r2 = dot(r, r);
   const float rinv = rsqrtf(r2);
   const float rinv2 = rinv * rinv;
@@ -131,12 +138,30 @@ __device__ __forceinline__ void interact(const PairArgs& a, const Ion& I, int j,
     // grad grad phi = c (-I B1 + r r B2) - [(I (d.r) + r d + d r) B2 - r r (d.r) B3]
     const float s_rr = c * B2 + dr_ * B3;
     const float s_I = -c * B1 - dr_ * B2;
-    A.h[0] += s_I + s_rr * r.x * r.x - 2.f * B2 * d.x * r.x;
-    A.h[1] += s_I + s_rr * r.y * r.y - 2.f * B2 * d.y * r.y;
-    A.h[2] += s_I + s_rr * r.z * r.z - 2.f * B2 * d.z * r.z;
-    A.h[3] += s_rr * r.x * r.y - B2 * (r.x * d.y + d.x * r.y);
-    A.h[4] += s_rr * r.x * r.z - B2 * (r.x * d.z + d.x * r.z);
-    A.h[5] += s_rr * r.y * r.z - B2 * (r.y * d.z + d.y * r.z);
+    float h[6];
+    h[0] = s_I + s_rr * r.x * r.x - 2.f * B2 * d.x * r.x;
+    h[1] = s_I + s_rr * r.y * r.y - 2.f * B2 * d.y * r.y;
+    h[2] = s_I + s_rr * r.z * r.z - 2.f * B2 * d.z * r.z;
+    h[3] = s_rr * r.x * r.y - B2 * (r.x * d.y + d.x * r.y);
+    h[4] = s_rr * r.x * r.z - B2 * (r.x * d.z + d.x * r.z);
+    h[5] = s_rr * r.y * r.z - B2 * (r.y * d.z + d.y * r.z);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) A.h[k] += h[k];
+    if (vir) {
+      const V3 m = I.mu;
+      const float Fx = -(I.q * gphi.x + h[0] * m.x + h[3] * m.y + h[4] * m.z);
+      const float Fy = -(I.q * gphi.y + h[3] * m.x + h[1] * m.y + h[5] * m.z);
+      const float Fz = -(I.q * gphi.z + h[4] * m.x + h[5] * m.y + h[2] * m.z);
+      vir[0] += 0.5f * Fx * r.x;
+      vir[1] += 0.5f * Fx * r.y;
+      vir[2] += 0.5f * Fx * r.z;
+      vir[3] += 0.5f * Fy * r.x;
+      vir[4] += 0.5f * Fy * r.y;
+      vir[5] += 0.5f * Fy * r.z;
+      vir[6] += 0.5f * Fz * r.x;
+      vir[7] += 0.5f * Fz * r.y;
+      vir[8] += 0.5f * Fz * r.z;
+    }
   } else {
     const float B4 = (7.f * B3 + a.c4 * ex) * rinv2;
     const float4 tj = a.pr.tq[j];
@@ -392,6 +417,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pair(PairArgs a) {
   const int cidx = blockIdx.x * kPairWarps + w;
   if (cidx >= a.ncells) return;   // uniform per warp
   if (a.cache_bad && *a.cache_bad == 0) return;
+  if (a.vir_lost && cidx == 0 && lane == 0) atomicOr(a.vir_lost, kFlagVirialLost);
   const int cell = a.cell_lo + cidx;
   const int c_lo = a.start_c[cell], c_hi = a.start_c[cell + 1];
   if (c_lo == c_hi) return;
@@ -544,7 +570,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_build(PairArgs a, int* ov
 // Pair term from the lists: one warp per ion (pair-cell order); lane l takes hits l, l + 32,
 // ... in order -- the same per-lane order as the fused kernel, so the two paths give bitwise
 // equal results. Runs only when *cache_bad == 0.
-template <bool TAN, bool BATCH>
+template <bool TAN, bool BATCH, bool VIR = false>
 __global__ void __launch_bounds__(kPairThreads) k_pair_listed(PairArgs a, int n) {
   if (*a.cache_bad != 0) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -554,11 +580,21 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_listed(PairArgs a, int n)
   const float gE = (TAN && a.g_energy) ? float(a.g_energy[frame]) : 0.f;
   const Ion I = load_ion<TAN>(a, i, gE);
   Acc<TAN> A;
+  float vir[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   const int c = a.list_cnt[i];
   const float4* li = a.list + size_t(i) * a.list_cap;
   for (int k = lane; k < c; k += 32) {
     const float4 h = li[k];
-    interact<TAN>(a, I, __float_as_int(h.w), mk(h.x, h.y, h.z), A);
+    interact<TAN>(a, I, __float_as_int(h.w), mk(h.x, h.y, h.z), A, VIR ? vir : nullptr);
+  }
+  if (VIR) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) vir[k] = warp_sum(vir[k]);
+    if (lane == 0) {
+      float* o = a.vir_out + size_t(a.pr.idx[i].w) * 9;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) o[k] = vir[k];
+    }
   }
   constexpr int NA = kAccN<TAN>;
   float v[NA];
@@ -642,11 +678,12 @@ static bool plan_ortho(pme_plan_t p) {
 }
 
 int launch_pair(pme_plan_t p, cudaStream_t s, int n, bool tangent, const IonInputs& in,
-                const double* g_energy, float* out, const int* skip) {
+                const double* g_energy, float* out, const int* skip, bool virial) {
   (void)in;
   if (n == 0) return PME_OK;
   PairArgs a = pair_args(p, g_energy, out);
   a.cache_bad = skip;
+  if (virial && !tangent) a.vir_lost = p->flags;
   const int grid = (a.ncells + kPairWarps - 1) / kPairWarps;
   if (grid == 0) return PME_OK;
   const bool ortho = plan_ortho(p);
@@ -680,16 +717,20 @@ int launch_pair_build(pme_plan_t p, cudaStream_t s, int n, int* overflow) {
 }
 
 int launch_pair_listed(pme_plan_t p, cudaStream_t s, int n, bool tangent, const double* g_energy,
-                       float* out, const int* flag) {
+                       float* out, const int* flag, bool virial) {
   if (n == 0) return PME_OK;
   PairArgs a = pair_args(p, g_energy, out);
   a.cache_bad = flag;
+  a.vir_out = p->pvir;
   const int grid = (n + kPairWarps - 1) / kPairWarps;
+  const bool vir = virial && !tangent;
   if (p->batch) {
     if (tangent) k_pair_listed<true, true><<<grid, kPairThreads, 0, s>>>(a, n);
+    else if (vir) k_pair_listed<false, true, true><<<grid, kPairThreads, 0, s>>>(a, n);
     else k_pair_listed<false, true><<<grid, kPairThreads, 0, s>>>(a, n);
   } else {
     if (tangent) k_pair_listed<true, false><<<grid, kPairThreads, 0, s>>>(a, n);
+    else if (vir) k_pair_listed<false, false, true><<<grid, kPairThreads, 0, s>>>(a, n);
     else k_pair_listed<false, false><<<grid, kPairThreads, 0, s>>>(a, n);
   }
   count_launch();

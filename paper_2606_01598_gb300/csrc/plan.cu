@@ -190,7 +190,8 @@ struct Staging {
       status = check_cuda(p, cudaMemcpyAsync(d, ptr, bytes, cudaMemcpyHostToDevice, s), "stage input");
     return d;
   }
-  // count doubles (per-frame energies / cotangents); slot 0 = outputs, 1 = inputs
+  // count doubles (per-frame energies / cotangents / virials); slot 0 = outputs, 1 = inputs,
+  // 2 = virials (9 per frame)
   const double* in_d(const double* ptr, int count, int slot) {
     if (!ptr || is_device_pointer(ptr)) return ptr;
     double* d = p->stage_d + size_t(slot) * p->nframes;
@@ -261,7 +262,8 @@ static void free_plan(pme_plan_t p) {
                   p->mesh_out, p->pair_out, p->e_ion, p->epart, p->flags, p->stage_f,
                   p->stage_d, p->ew_kn, p->ew_kv, p->ew_S, p->ew_fx, p->ew_qm, p->frames_d,
                   p->map_buf, p->fft_work, p->sb.qpart, p->sb.qcount, p->eitem, p->ecount, p->sb.gcount,
-                  p->plist, p->plist_cnt, p->in_saved, p->in_flags};
+                  p->plist, p->plist_cnt, p->in_saved, p->in_flags, p->vpart,
+                  p->pvir, p->vitem};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int g = 0; g < p->nfgroups; ++g) {
@@ -535,7 +537,10 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
   A(&p->epart, size_t(p->total_blocks) + 1);
   A(&p->flags, 1);
   A(&p->stage_f, ni * kStageFloats);
-  A(&p->stage_d, size_t(2) * F + 2);
+  A(&p->stage_d, size_t(11) * F + 2);   // energies, cotangents, virials (9 per frame)
+  A(&p->vpart, size_t(6) * p->total_blocks + 6);
+  A(&p->pvir, 9 * ni);
+  A(&p->vitem, size_t(9) * p->total_items);
   if (st == PME_OK) st = alloc_cells(p);
   // pair lists for backward passes on the forward's positions: room for 1.5x the mean number
   // of partners inside rcut (density from the plan's largest n / V) + 64, when that fits in
@@ -709,8 +714,9 @@ static int forward_ewald(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool
 }
 
 // Forward pass over every frame of the plan (in.n ions in total).
+// v_out (nullable): also the frame virials, [9] per frame (needs e_out).
 static int run_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, double* e_out, float* f_out,
-                       float* p_out, float* fl_out, float* fg_out) {
+                       float* p_out, float* fl_out, float* fg_out, double* v_out = nullptr) {
   const int n = in.n;
   const bool pair = p->opts.include_pair != 0;
   if (p->opts.recip_method == 1) return forward_ewald(p, s, in, pair, e_out, f_out, p_out, fl_out, fg_out);
@@ -729,9 +735,11 @@ static int run_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, double
     t = prof_begin(p, 6, ps);
     if (record) {
       if ((st = launch_pair_build(p, ps, n, p->cache_bad))) return st;
-      if ((st = launch_pair(p, ps, n, false, in, nullptr, p->pair_out, p->cache_bad))) return st;
+      if ((st = launch_pair(p, ps, n, false, in, nullptr, p->pair_out, p->cache_bad, v_out != nullptr)))
+        return st;
       const int te = prof_begin(p, 8, ps);
-      if ((st = launch_pair_listed(p, ps, n, false, nullptr, p->pair_out, p->cache_bad))) return st;
+      if ((st = launch_pair_listed(p, ps, n, false, nullptr, p->pair_out, p->cache_bad, v_out != nullptr)))
+        return st;
       prof_end(p, te, ps);
     } else if ((st = launch_pair(p, ps, n, false, in, nullptr, p->pair_out, nullptr))) {
       return st;
@@ -747,7 +755,7 @@ static int run_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, double
   if ((st = fft_forward(p, s, false))) return st;
   prof_end(p, t, s);
   t = prof_begin(p, 3, s);
-  if ((st = launch_influence(p, s, p->spec, false, p->epart))) return st;
+  if ((st = launch_influence(p, s, p->spec, false, p->epart, v_out ? p->vpart : nullptr))) return st;
   prof_end(p, t, s);
   t = prof_begin(p, 4, s);
   if ((st = fft_inverse(p, s, false))) return st;
@@ -757,7 +765,8 @@ static int run_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, double
   prof_end(p, t, s);
   if (fork && p->opts.overlap_pair && (st = join_side(p, s))) return st;
   t = prof_begin(p, 7, s);
-  if ((st = launch_combine_forward(p, s, in, true, fork, f_out, p_out, fl_out, fg_out, e_out, 1))) return st;
+  if ((st = launch_combine_forward(p, s, in, true, fork, f_out, p_out, fl_out, fg_out, e_out, 1, v_out)))
+    return st;
   prof_end(p, t, s);
   p->fwd_n = n > 0 ? n : -1;
   p->fwd_lists = record;
@@ -1006,6 +1015,9 @@ int pme_sync_status(pme_plan_t p, void* stream) {
   if (flags) cudaMemset(p->flags, 0, sizeof(int));
   if (flags & kFlagNonFinite) return set_error(p, PME_ERR_NONFINITE, "non-finite value in pos, q or mu");
   if (flags & kFlagTimeout) return set_error(p, PME_ERR_TIMEOUT, "device wait timed out");
+  if (flags & kFlagVirialLost)
+    return set_error(p, PME_ERR_UNSUPPORTED,
+                     "virial: a pair-hit list overflowed, so the pair part of the virial is missing");
   return PME_OK;
 }
 
@@ -1028,6 +1040,34 @@ int pme_forward(pme_plan_t p, void* stream, int n, const float* pos, const float
   float* fg_out = sg.out(field_grad, 6, kOFG);
   if (sg.status) return sg.status;
   if ((st = run_forward(p, s, in, e_out, f_out, p_out, fl_out, fg_out))) return st;
+  return sg.finish();
+}
+
+int pme_forward_virial(pme_plan_t p, void* stream, int n, const float* pos, const float* q,
+                       const float* mu, double* energy, float* force, float* phi, float* field,
+                       float* field_grad, double* virial) {
+  int st = check_common(p, n, pos, q);
+  if (st) return st;
+  if (!energy || !virial) return set_error(p, PME_ERR_ARG, "pme_forward_virial needs energy and virial");
+  if (p->opts.recip_method != 0)
+    return set_error(p, PME_ERR_UNSUPPORTED, "the virial needs the particle-mesh reciprocal method");
+  if (p->opts.include_pair && !p->plist)
+    return set_error(p, PME_ERR_UNSUPPORTED, "the virial needs the plan's pair-hit lists (too large for this plan)");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Staging sg(p, s, n);
+  IonInputs in{};
+  in.pos = sg.in(pos, 3, kPos);
+  in.q = sg.in(q, 1, kQ);
+  in.mu = sg.in(mu, 3, kMu);
+  in.n = n;
+  double* e_out = sg.out_d(energy, 1, 0);
+  double* v_out = sg.out_d(virial, 9, 2);
+  float* f_out = sg.out(force, 3, kOF);
+  float* p_out = sg.out(phi, 1, kOPhi);
+  float* fl_out = sg.out(field, 3, kOField);
+  float* fg_out = sg.out(field_grad, 6, kOFG);
+  if (sg.status) return sg.status;
+  if ((st = run_forward(p, s, in, e_out, f_out, p_out, fl_out, fg_out, v_out))) return st;
   return sg.finish();
 }
 
@@ -1084,6 +1124,33 @@ int pme_batch_forward(pme_plan_t p, void* stream, const float* pos, const float*
   float* fg_out = sg.out(field_grad, 6, kOFG);
   if (sg.status) return sg.status;
   if ((st = run_forward(p, s, in, e_out, f_out, p_out, fl_out, fg_out))) return st;
+  return sg.finish();
+}
+
+int pme_batch_forward_virial(pme_plan_t p, void* stream, const float* pos, const float* q,
+                             const float* mu, double* energy, float* force, float* phi,
+                             float* field, float* field_grad, double* virial) {
+  int st = check_batch(p, pos, q);
+  if (st) return st;
+  if (!energy || !virial) return set_error(p, PME_ERR_ARG, "pme_batch_forward_virial needs energy and virial");
+  if (p->opts.include_pair && !p->plist)
+    return set_error(p, PME_ERR_UNSUPPORTED, "the virial needs the plan's pair-hit lists (too large for this plan)");
+  const int n = p->frame_offsets[p->nframes];
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Staging sg(p, s, n);
+  IonInputs in{};
+  in.pos = sg.in(pos, 3, kPos);
+  in.q = sg.in(q, 1, kQ);
+  in.mu = sg.in(mu, 3, kMu);
+  in.n = n;
+  double* e_out = sg.out_d(energy, p->nframes, 0);
+  double* v_out = sg.out_d(virial, 9 * p->nframes, 2);
+  float* f_out = sg.out(force, 3, kOF);
+  float* p_out = sg.out(phi, 1, kOPhi);
+  float* fl_out = sg.out(field, 3, kOField);
+  float* fg_out = sg.out(field_grad, 6, kOFG);
+  if (sg.status) return sg.status;
+  if ((st = run_forward(p, s, in, e_out, f_out, p_out, fl_out, fg_out, v_out))) return st;
   return sg.finish();
 }
 

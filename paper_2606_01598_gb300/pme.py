@@ -178,8 +178,9 @@ class Plan:
 
     # -- full passes -----------------------------------------------------------------------
     def forward(self, pos, q, mu=None, *, energy=True, force=True, phi=True, field=True,
-                field_grad=False):
-        """Energy and derivatives. Device tensors stay on the device; CPU tensors are passed as
+                field_grad=False, virial=False):
+        """Energy and derivatives (and, with virial=True, the 3x3 virial -dE/d strain; see
+        pme_forward_virial). Device tensors stay on the device; CPU tensors are passed as
         host pointers (the library stages them). Returns a dict of tensors."""
         dev = pos.device if isinstance(pos, torch.Tensor) else torch.device("cpu")
         on_dev = dev.type == "cuda"
@@ -200,12 +201,19 @@ class Plan:
             out["field"] = torch.empty((n, 3), dtype=torch.float32, **alloc)
         if field_grad:
             out["field_grad"] = torch.empty((n, 6), dtype=torch.float32, **alloc)
+        if virial:
+            out.setdefault("energy", torch.empty(1, dtype=torch.float64, **alloc))
+            out["virial"] = torch.empty((3, 3), dtype=torch.float64, **alloc)
         with torch.cuda.device(self.device):
-            st = self.lib.pme_forward(self.handle, _stream_handle(self.device), n, _ptr(pos), _ptr(q),
-                                      _ptr(mu), _ptr(out.get("energy")), _ptr(out.get("force")),
-                                      _ptr(out.get("phi")), _ptr(out.get("field")),
-                                      _ptr(out.get("field_grad")))
-            self._check(st, "pme_forward")
+            args = (self.handle, _stream_handle(self.device), n, _ptr(pos), _ptr(q),
+                    _ptr(mu), _ptr(out.get("energy")), _ptr(out.get("force")),
+                    _ptr(out.get("phi")), _ptr(out.get("field")), _ptr(out.get("field_grad")))
+            if virial:
+                st = self.lib.pme_forward_virial(*args, _ptr(out["virial"]))
+                self._check(st, "pme_forward_virial")
+            else:
+                st = self.lib.pme_forward(*args)
+                self._check(st, "pme_forward")
             if not on_dev:
                 torch.cuda.current_stream(self.device).synchronize()
         return out
@@ -323,7 +331,7 @@ class BatchPlan(Plan):
         self.handle = h
 
     def forward(self, pos, q, mu=None, *, energy=True, force=True, phi=True, field=True,
-                field_grad=False):
+                field_grad=False, virial=False):
         dev = pos.device if isinstance(pos, torch.Tensor) else torch.device("cpu")
         on_dev = dev.type == "cuda"
         pos, q, mu = (_f32(t, dev) for t in (pos, q, mu))
@@ -340,12 +348,19 @@ class BatchPlan(Plan):
             out["field"] = torch.empty((n, 3), dtype=torch.float32, **alloc)
         if field_grad:
             out["field_grad"] = torch.empty((n, 6), dtype=torch.float32, **alloc)
+        if virial:
+            out.setdefault("energy", torch.empty(self.nframes, dtype=torch.float64, **alloc))
+            out["virial"] = torch.empty((self.nframes, 3, 3), dtype=torch.float64, **alloc)
         with torch.cuda.device(self.device):
-            st = self.lib.pme_batch_forward(self.handle, _stream_handle(self.device), _ptr(pos), _ptr(q),
-                                            _ptr(mu), _ptr(out.get("energy")), _ptr(out.get("force")),
-                                            _ptr(out.get("phi")), _ptr(out.get("field")),
-                                            _ptr(out.get("field_grad")))
-            self._check(st, "pme_batch_forward")
+            args = (self.handle, _stream_handle(self.device), _ptr(pos), _ptr(q),
+                    _ptr(mu), _ptr(out.get("energy")), _ptr(out.get("force")),
+                    _ptr(out.get("phi")), _ptr(out.get("field")), _ptr(out.get("field_grad")))
+            if virial:
+                st = self.lib.pme_batch_forward_virial(*args, _ptr(out["virial"]))
+                self._check(st, "pme_batch_forward_virial")
+            else:
+                st = self.lib.pme_batch_forward(*args)
+                self._check(st, "pme_batch_forward")
             if not on_dev:
                 torch.cuda.current_stream(self.device).synchronize()
         return out
