@@ -368,6 +368,17 @@ def vs_plain(gb, fr, cfg, dev, pos, q, mu, gE, gF, gphi, gfield, flush, steps):
             "steps": k}
 
 
+def virial_cost(gb, fr, cfg, dev, pos, q, mu, flush, steps):
+    """Forward with and without the virial on the benchmark frame (CUDA events)."""
+    import torch
+    plan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=fr.n, device=dev)
+    k = max(3, steps // 4)
+    t_f = time_steps(torch, lambda: plan.forward(pos, q, mu), k, 3, dev, flush)
+    t_v = time_steps(torch, lambda: plan.forward(pos, q, mu, virial=True), k, 3, dev, flush)
+    plan.close()
+    return {"forward_ms": t_f, "forward_with_virial_ms": t_v, "steps": k}
+
+
 def batch16_rooflines(gb, fr, cfg, dev, steps):
     """Spread / gather / influence rooflines over 16 frames of the 32k workload in one batched
     launch per stage (working set well above L2). The frames are translated, axis-permuted
@@ -534,9 +545,10 @@ def run_ours(args):
     h2d = 2 * (12 + 4 + 12) * n + (12 + 4 + 12) * n + 8
     d2h = 8 + (12 + 4 + 12) * n + (12 + 4 + 12) * n
     clocks = sampler.stop()
-    plain = b16 = None
+    plain = b16 = vir = None
     if rank == 0 and not args.no_extras:
         plain = vs_plain(gb, fr, cfg, dev, pos, q, mu, gE, gF, gphi, gfield, flush, args.steps)
+        vir = virial_cost(gb, fr, cfg, dev, pos, q, mu, flush, args.steps)
         b16 = batch16_rooflines(gb, fr, cfg, dev, args.steps)
 
     if rank == 0:
@@ -583,6 +595,7 @@ def run_ours(args):
                                for k, v in mesh_kernels.items()},
             "mesh_rooflines_batch16": b16,
             "vs_plain": plain,
+            "virial": vir,
             "cpu_baseline": cpu,
             "e2e": {"value": e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e_ms},
