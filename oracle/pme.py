@@ -120,8 +120,11 @@ class PMEOracle:
     def __init__(self, box, mesh, order: int, alpha: float, rcut: float, *,
                  influence_power: float = 1.0, deconvolution: bool = True,
                  coulomb_k: float = 1.0, include_pair: bool = True,
-                 include_self: bool = True, include_background: bool = True):
+                 include_self: bool = True, include_background: bool = True,
+                 influence_kind: str = "deconvolution", alias_range: int = 2):
         self.C = np.asarray(box, np.float64).reshape(3, 3)
+        self.influence_kind = influence_kind
+        self.alias_range = int(alias_range)
         self.Cinv = np.linalg.inv(self.C)
         self.b = 2.0 * math.pi * self.Cinv.T            # rows b_alpha
         self.V = abs(np.linalg.det(self.C))
@@ -139,6 +142,8 @@ class PMEOracle:
 
     # -- Section 2.3.3 / 2.3.4: influence function on the full signed spectrum ----------
     def influence(self) -> np.ndarray:
+        if self.influence_kind == "p3m":
+            return self.influence_p3m(self.alias_range)
         Nx, Ny, Nz = self.N
         n = [np.fft.fftfreq(Na) * Na for Na in self.N]
         nx, ny, nz = np.meshgrid(*n, indexing="ij")
@@ -154,6 +159,41 @@ class PMEOracle:
         else:
             Cn = np.ones_like(G)
         return G * Cn
+
+    # -- alternative (not the paper's): the P3M influence function ------------------------
+    def influence_p3m(self, mrange: int) -> np.ndarray:
+        """Influence function that minimises the mean-square error of the forces obtained by
+        differentiating the interpolated potential (analytical differentiation), for this
+        assignment function, in the least-squares sense of Hockney and Eastwood: with the
+        aliases k_m = sum_a (n_a + m_a N_a) b_a of the signed frequency n and
+        U(k_m) = prod_a sinc^(2p)(n_a / N_a + m_a),
+            G(n) = sum_m k_m^2 U(k_m) phi(k_m) / [(sum_m U(k_m)) (sum_m k_m^2 U(k_m))],
+        phi(k) = 4 pi e^{-k^2/4 alpha^2}/k^2, G(0) = 0, sums over |m_a| <= mrange. Keeping only
+        m = 0 gives phi / U, the sinc deconvolution with gamma = 1."""
+        n = [np.fft.fftfreq(Na) * Na for Na in self.N]
+        nx, ny, nz = np.meshgrid(*n, indexing="ij")
+        num = np.zeros(nx.shape)
+        s1 = np.zeros(nx.shape)
+        s2 = np.zeros(nx.shape)
+        for mx in range(-mrange, mrange + 1):
+            ux = np.sinc(nx / self.N[0] + mx) ** (2 * self.p)
+            for my in range(-mrange, mrange + 1):
+                uy = np.sinc(ny / self.N[1] + my) ** (2 * self.p)
+                for mz in range(-mrange, mrange + 1):
+                    uz = np.sinc(nz / self.N[2] + mz) ** (2 * self.p)
+                    kv = ((nx + mx * self.N[0])[..., None] * self.b[0] + (ny + my * self.N[1])[..., None] * self.b[1]
+                          + (nz + mz * self.N[2])[..., None] * self.b[2])
+                    k2 = np.einsum("...c,...c->...", kv, kv)
+                    with np.errstate(divide="ignore", invalid="ignore"):
+                        ph = np.where(k2 > 0, 4 * math.pi * np.exp(-k2 / (4 * self.alpha ** 2)) / k2, 0.0)
+                    U = ux * uy * uz
+                    num += k2 * U * ph
+                    s1 += U
+                    s2 += k2 * U
+        with np.errstate(divide="ignore", invalid="ignore"):
+            G = np.where(s2 > 0, num / (s1 * s2), 0.0)
+        G[0, 0, 0] = 0.0
+        return G
 
     # -- Section 2.3.2: spline assignment of charges and dipoles ------------------------
     def _stencils(self, pos):
@@ -253,7 +293,8 @@ class PMEOracle:
         return PMEOracle(self.C @ F.T, self.N, self.p, self.alpha, self.rcut,
                          influence_power=self.gamma, deconvolution=self.deconv, coulomb_k=self.k,
                          include_pair=self.include_pair, include_self=self.include_self,
-                         include_background=self.include_bg)
+                         include_background=self.include_bg, influence_kind=self.influence_kind,
+                         alias_range=self.alias_range)
 
     def virial(self, pos, q, mu, h: float = 1e-5):
         """W_ab = -dE/d(eps_ab) for the homogeneous strain r -> (I + eps) r, a_i -> (I + eps) a_i
