@@ -80,7 +80,14 @@ typedef struct {
                               baseline of the paper's timing crossover; forward only) */
   double ewald_kmax;       /* |k| cutoff in 1/length for recip_method 1; <= 0 selects
                               2 alpha sqrt(ln 1e8), where exp(-k^2/4 alpha^2) = 1e-8 */
-  int reserved[6];
+  int influence_kind;      /* 0: G(k) C(n), the sinc deconvolution of Eq. influence (default).
+                              1: the P3M influence function that minimises the mean-square
+                              force error for analytical differentiation (Hockney-Eastwood
+                              least squares), with alias sums |m| <= 2: G(n) = sum_m k_m^2 U_m
+                              phi(k_m) / [(sum_m U_m)(sum_m k_m^2 U_m)], U_m = prod sinc^(2p);
+                              deconvolution and influence_power are then unused, and
+                              pme_forward_virial reports PME_ERR_UNSUPPORTED */
+  int reserved[5];
 } pme_opts;
 
 void pme_opts_default(pme_opts* opts);

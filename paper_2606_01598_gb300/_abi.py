@@ -25,7 +25,8 @@ class PMEOpts(ctypes.Structure):
     _fields_ = [("influence_power", c_double), ("deconvolution", c_int), ("coulomb_k", c_double),
                 ("include_pair", c_int), ("include_self", c_int), ("include_background", c_int),
                 ("max_ions", c_int), ("brick", c_int * 3), ("overlap_pair", c_int),
-                ("recip_method", c_int), ("ewald_kmax", c_double), ("reserved", c_int * 6)]
+                ("recip_method", c_int), ("ewald_kmax", c_double), ("influence_kind", c_int),
+                ("reserved", c_int * 5)]
 
 
 _SIGS = {

@@ -119,6 +119,7 @@ struct FrameDesc {
   long long tmesh_off;      // first float of d rho / d Phi (backward)
   long long spec_off;       // first complex of the spectrum
   long long tspec_off;      // first complex of the tangent spectrum
+  long long gtab_off;       // first entry of the frame's P3M influence table
   int cand_off, max_nb;     // candidate-brick table [3][max_nb][1 + kMaxCandPerDim]
   int dconv_off;            // deconvolution tables: x at dconv_off, y at +Nx, z at +Nx+Ny
   int infl_blk_off, infl_nblk;  // influence / energy blocks of this frame
@@ -188,6 +189,7 @@ struct pme_plan_s {
   cufftComplex* spec;        // spectra (same layout with spec_off / tspec_off)
   float* phi;                // potential meshes (layout of rho)
   float* dconv_all;          // per-frame, per-axis deconvolution factors 1/sinc^(2 p gamma)
+  float* gtab = nullptr;     // P3M influence tables (influence_kind 1), [half spectrum] per frame
   int* cand;                 // per-frame candidate-brick tables
   gbpme::SortBuffers sb;
   gbpme::MeshRecords mr;

@@ -12,6 +12,8 @@
 // follows yields Phi with E_recip = 1/2 sum_m rho(m) Phi(m). A batched plan gives every frame
 // its own run of blocks. All per-element arithmetic is float32 (the float64 rate of the part
 // is a small fraction of its float32 rate), with the constants precomputed on the host.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace gbpme {
@@ -33,7 +35,7 @@ __device__ __forceinline__ void comp_add(float& s, float& c, float v) {
 template <bool BATCH, bool VIR>
 __global__ void __launch_bounds__(kInflThreads)
 k_influence(FrameDesc one, FrameMaps maps, float2* spec, int tangent, const float* dconv,
-            float inv4a2, double* partials, double* vparts) {
+            float inv4a2, double* partials, double* vparts, const float* gtab) {
   const FrameDesc& F = frame_at<BATCH>(one, maps, BATCH ? maps.blk_frame[blockIdx.x] : 0);
   const Geometry& g = F.g;
   const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2];
@@ -61,7 +63,8 @@ k_influence(FrameDesc one, FrameMaps maps, float2* spec, int tangent, const floa
     const float kz = nx * g.bk[2] + ny * g.bk[5] + nz * g.bk[8];
     const float k2 = kx * kx + ky * ky + kz * kz;
     float gc = 0.f;
-    if (k2 > 0.f) gc = four_pi * expf(-k2 * inv4a2) / k2 * cx[ix] * cy[iy] * cz[iz];
+    if (gtab) gc = gtab[F.gtab_off + idx];
+    else if (k2 > 0.f) gc = four_pi * expf(-k2 * inv4a2) / k2 * cx[ix] * cy[iy] * cz[iz];
     const float2 v = sp[idx];
     const float w = (iz == 0 || (2 * iz == N2)) ? 1.f : 2.f;
     const float eg = w * gc * (v.x * v.x + v.y * v.y);
@@ -163,7 +166,69 @@ k_energy_final(FrameDesc one, FrameMaps maps, const double* parts, int recip_kin
   }
 }
 
+// P3M influence table of one frame (influence_kind 1): for every half-spectrum point,
+// G(n) = sum_m k_m^2 U_m phi(k_m) / [(sum_m U_m)(sum_m k_m^2 U_m)] with U_m = prod_a
+// sinc^(2p)(n_a / N_a + m_a), |m_a| <= kAlias, phi(k) = 4 pi e^{-k^2/4 alpha^2}/k^2 (so
+// k_m^2 phi(k_m) = 4 pi e^{-k_m^2/4 alpha^2}); G(0) = 0. Float32 sums of positive terms.
+constexpr int kAlias = 2;
+
+__device__ __forceinline__ float sinc_pow2p(float x, int p) {
+  const float s = (x == 0.f) ? 1.f : sinpif(x) / (3.14159265358979f * x);
+  const float s2 = s * s;
+  float r = 1.f;
+  for (int k = 0; k < p; ++k) r *= s2;
+  return r;
+}
+
+__global__ void __launch_bounds__(kInflThreads) k_p3m_table(FrameDesc F, float inv4a2, float* tab) {
+  const Geometry& g = F.g;
+  const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2];
+  const int Nzh = N2 / 2 + 1;
+  const int Mh = N0 * N1 * Nzh;
+  const float four_pi = 12.566370614359172f;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < Mh; idx += gridDim.x * blockDim.x) {
+    const int r = fdiv(idx, F.div_zh);
+    const int iz = idx - r * Nzh;
+    const int ix = fdiv(r, F.div_y);
+    const int iy = r - ix * N1;
+    const int n[3] = {ix <= N0 / 2 ? ix : ix - N0, iy <= N1 / 2 ? iy : iy - N1, iz};
+    float U[3][2 * kAlias + 1];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int m = -kAlias; m <= kAlias; ++m) U[a][m + kAlias] = sinc_pow2p(float(n[a]) / float(g.N[a]) + float(m), g.order);
+    float num = 0.f, s1 = 0.f, s2 = 0.f;
+    for (int mx = -kAlias; mx <= kAlias; ++mx)
+      for (int my = -kAlias; my <= kAlias; ++my)
+        for (int mz = -kAlias; mz <= kAlias; ++mz) {
+          const float u = U[0][mx + kAlias] * U[1][my + kAlias] * U[2][mz + kAlias];
+          const float fx = float(n[0] + mx * N0), fy = float(n[1] + my * N1), fz = float(n[2] + mz * N2);
+          const float kx = fx * g.bk[0] + fy * g.bk[3] + fz * g.bk[6];
+          const float ky = fx * g.bk[1] + fy * g.bk[4] + fz * g.bk[7];
+          const float kz = fx * g.bk[2] + fy * g.bk[5] + fz * g.bk[8];
+          const float k2 = kx * kx + ky * ky + kz * kz;
+          num += u * four_pi * expf(-k2 * inv4a2);
+          s1 += u;
+          s2 += u * k2;
+        }
+    tab[F.gtab_off + idx] = (idx == 0 || s2 <= 0.f) ? 0.f : num / (s1 * s2);
+  }
+}
+
 }  // namespace
+
+int launch_p3m_tables(pme_plan_t p, cudaStream_t s) {
+  const float inv4a2 = float(1.0 / (4.0 * p->alpha * p->alpha));
+  for (int f = 0; f < p->nframes; ++f) {
+    const FrameDesc& F = p->frames_h[f];
+    const long long Mh = (long long)F.g.N[0] * F.g.N[1] * (F.g.N[2] / 2 + 1);
+    const int grid = int(std::min<long long>((Mh + kInflThreads - 1) / kInflThreads, 152 * 8));
+    k_p3m_table<<<grid, kInflThreads, 0, s>>>(F, inv4a2, p->gtab);
+    const int st = check_launch(p, "k_p3m_table");
+    if (st) return st;
+  }
+  return PME_OK;
+}
 
 int influence_blocks(const Geometry& g) {
   const long long Mh = (long long)g.N[0] * g.N[1] * (g.N[2] / 2 + 1);
@@ -179,11 +244,11 @@ int launch_influence(pme_plan_t p, cudaStream_t s, cufftComplex* spec, bool tang
   const int grid = p->batch ? p->total_blocks : one.infl_nblk;
   const int tg = tangent ? 1 : 0;
   if (p->batch) {
-    if (vparts) k_influence<true, true><<<grid, kInflThreads, 0, s>>>(one, p->maps, sp, tg, p->dconv_all, inv4a2, partials, vparts);
-    else k_influence<true, false><<<grid, kInflThreads, 0, s>>>(one, p->maps, sp, tg, p->dconv_all, inv4a2, partials, vparts);
+    if (vparts) k_influence<true, true><<<grid, kInflThreads, 0, s>>>(one, p->maps, sp, tg, p->dconv_all, inv4a2, partials, vparts, p->gtab);
+    else k_influence<true, false><<<grid, kInflThreads, 0, s>>>(one, p->maps, sp, tg, p->dconv_all, inv4a2, partials, vparts, p->gtab);
   } else {
-    if (vparts) k_influence<false, true><<<grid, kInflThreads, 0, s>>>(one, p->maps, sp, tg, p->dconv_all, inv4a2, partials, vparts);
-    else k_influence<false, false><<<grid, kInflThreads, 0, s>>>(one, p->maps, sp, tg, p->dconv_all, inv4a2, partials, vparts);
+    if (vparts) k_influence<false, true><<<grid, kInflThreads, 0, s>>>(one, p->maps, sp, tg, p->dconv_all, inv4a2, partials, vparts, p->gtab);
+    else k_influence<false, false><<<grid, kInflThreads, 0, s>>>(one, p->maps, sp, tg, p->dconv_all, inv4a2, partials, vparts, p->gtab);
   }
   count_launch();
   return check_launch(p, "k_influence");

@@ -44,6 +44,8 @@ int launch_influence(pme_plan_t p, cudaStream_t s, cufftComplex* spec, bool tang
 int launch_energy_final(pme_plan_t p, cudaStream_t s, const double* parts, int recip_kind,
                         bool with_ions, bool with_bg, double scale, int n_single, double* out);
 int influence_blocks(const Geometry& g);
+// Fill the P3M influence table of every frame (influence_kind 1; plan creation, set_box).
+int launch_p3m_tables(pme_plan_t p, cudaStream_t s);
 void spread_brick_shape(int shape[3]);
 
 // gather.cu: per-ion interpolation of the potential mesh(es).

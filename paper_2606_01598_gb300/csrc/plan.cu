@@ -263,7 +263,7 @@ static void free_plan(pme_plan_t p) {
                   p->stage_d, p->ew_kn, p->ew_kv, p->ew_S, p->ew_fx, p->ew_qm, p->frames_d,
                   p->map_buf, p->fft_work, p->sb.qpart, p->sb.qcount, p->eitem, p->ecount, p->sb.gcount,
                   p->plist, p->plist_cnt, p->in_saved, p->in_flags, p->vpart,
-                  p->pvir, p->vitem};
+                  p->pvir, p->vitem, p->gtab};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int g = 0; g < p->nfgroups; ++g) {
@@ -488,6 +488,12 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
     spec_off += 2LL * G.count * Mh;
   }
   p->total_mesh = mesh_off;
+  long long gtab_total = 0;   // P3M influence tables, one half spectrum per frame
+  for (int f = 0; f < F; ++f) {
+    FrameDesc& D = p->frames_h[f];
+    D.gtab_off = gtab_total;
+    gtab_total += (long long)D.g.N[0] * D.g.N[1] * (D.g.N[2] / 2 + 1);
+  }
   p->total_spec = spec_off;
   {
     const Geometry& g0 = p->frames_h[0].g;
@@ -561,6 +567,7 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
       A(&p->plist_cnt, ni);
     }
   }
+  if (p->opts.influence_kind == 1) A(&p->gtab, size_t(gtab_total));
   A(&p->in_saved, 7 * ni);
   A(&p->in_flags, 2);
   if (st == PME_OK) {
@@ -656,6 +663,8 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
     for (cufftHandle h : {G.r2c, G.c2r, G.r2c2, G.c2r2})
       if ((st = check_fft(p, cufftSetWorkArea(h, p->fft_work), "cufftSetWorkArea"))) return st;
   }
+  if (p->gtab && ((st = launch_p3m_tables(p, 0)) || (st = check_cuda(p, cudaDeviceSynchronize(), "synchronize"))))
+    return st;
   if ((st = check_cuda(p, cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking), "stream")) ||
       (st = check_cuda(p, cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming), "event")) ||
       (st = check_cuda(p, cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming), "event")))
@@ -831,6 +840,7 @@ static int validate_opts(pme_plan_s* p, double alpha, double rcut) {
   if (p->opts.max_ions <= 0) return set_error(p, PME_ERR_ARG, "max_ions must be > 0");
   if (!(p->opts.influence_power >= 0.0)) return set_error(p, PME_ERR_ARG, "influence_power < 0");
   if (p->opts.recip_method < 0 || p->opts.recip_method > 1) return set_error(p, PME_ERR_ARG, "recip_method");
+  if (p->opts.influence_kind < 0 || p->opts.influence_kind > 1) return set_error(p, PME_ERR_ARG, "influence_kind");
   p->opts_kmax = p->opts.ewald_kmax > 0.0 ? p->opts.ewald_kmax : 2.0 * alpha * std::sqrt(std::log(1e8));
   return PME_OK;
 }
@@ -984,6 +994,8 @@ int pme_plan_set_box(pme_plan_t p, const double box[9]) {
   p->g = g;
   p->fwd_n = -1;   // the saved forward belongs to the old box
   std::memcpy(p->box, box, sizeof(double) * 9);
+  if (p->gtab && ((st = launch_p3m_tables(p, 0)) || (st = check_cuda(p, cudaDeviceSynchronize(), "synchronize"))))
+    return st;
   if (nc > p->total_cells) {
     cudaFree(p->sb.count_c);
     cudaFree(p->sb.start_c);
@@ -1049,8 +1061,9 @@ int pme_forward_virial(pme_plan_t p, void* stream, int n, const float* pos, cons
   int st = check_common(p, n, pos, q);
   if (st) return st;
   if (!energy || !virial) return set_error(p, PME_ERR_ARG, "pme_forward_virial needs energy and virial");
-  if (p->opts.recip_method != 0)
-    return set_error(p, PME_ERR_UNSUPPORTED, "the virial needs the particle-mesh reciprocal method");
+  if (p->opts.recip_method != 0 || p->opts.influence_kind != 0)
+    return set_error(p, PME_ERR_UNSUPPORTED,
+                     "the virial needs the particle-mesh method with the sinc-deconvolution influence");
   if (p->opts.include_pair && !p->plist)
     return set_error(p, PME_ERR_UNSUPPORTED, "the virial needs the plan's pair-hit lists (too large for this plan)");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1133,6 +1146,8 @@ int pme_batch_forward_virial(pme_plan_t p, void* stream, const float* pos, const
   int st = check_batch(p, pos, q);
   if (st) return st;
   if (!energy || !virial) return set_error(p, PME_ERR_ARG, "pme_batch_forward_virial needs energy and virial");
+  if (p->opts.influence_kind != 0)
+    return set_error(p, PME_ERR_UNSUPPORTED, "the virial needs the sinc-deconvolution influence");
   if (p->opts.include_pair && !p->plist)
     return set_error(p, PME_ERR_UNSUPPORTED, "the virial needs the plan's pair-hit lists (too large for this plan)");
   const int n = p->frame_offsets[p->nframes];

@@ -87,7 +87,7 @@ class Plan:
                  coulomb_k: float = 1.0, include_pair: bool = True, include_self: bool = True,
                  include_background: bool = True, max_ions: int = 1 << 18,
                  overlap_pair: bool = True, recip_method: str = "mesh", ewald_kmax: float = 0.0,
-                 device=None):
+                 influence: str = "deconvolution", device=None):
         if not torch.cuda.is_available():
             raise RuntimeError("gbpme needs a CUDA device; there is no CPU fallback")
         self.lib = _abi.load()
@@ -110,6 +110,9 @@ class Plan:
         opts.overlap_pair = int(bool(overlap_pair))
         if recip_method not in ("mesh", "ewald"):
             raise ValueError("recip_method is 'mesh' or 'ewald'")
+        if influence not in ("deconvolution", "p3m"):
+            raise ValueError("influence is 'deconvolution' or 'p3m'")
+        opts.influence_kind = 0 if influence == "deconvolution" else 1
         opts.recip_method = 0 if recip_method == "mesh" else 1
         opts.ewald_kmax = float(ewald_kmax)
         self.box = np.asarray(box, np.float64).reshape(3, 3).copy()
@@ -289,7 +292,8 @@ class BatchPlan(Plan):
     def __init__(self, boxes, meshes, orders, offsets, alpha: float, rcut: float, *,
                  influence_power: float = 1.0, deconvolution: bool = True,
                  coulomb_k: float = 1.0, include_pair: bool = True, include_self: bool = True,
-                 include_background: bool = True, overlap_pair: bool = True, device=None):
+                 include_background: bool = True, overlap_pair: bool = True,
+                 influence: str = "deconvolution", device=None):
         if not torch.cuda.is_available():
             raise RuntimeError("gbpme needs a CUDA device; there is no CPU fallback")
         self.lib = _abi.load()
@@ -304,6 +308,9 @@ class BatchPlan(Plan):
         opts.deconvolution = int(bool(deconvolution))
         opts.coulomb_k = float(coulomb_k)
         opts.include_pair = int(bool(include_pair))
+        if influence not in ("deconvolution", "p3m"):
+            raise ValueError("influence is 'deconvolution' or 'p3m'")
+        opts.influence_kind = 0 if influence == "deconvolution" else 1
         opts.include_self = int(bool(include_self))
         opts.include_background = int(bool(include_background))
         opts.overlap_pair = int(bool(overlap_pair))
