@@ -166,35 +166,61 @@ __device__ __forceinline__ void interact(const PairArgs& a, const Ion& I, int j,
     const float B4 = (7.f * B3 + a.c4 * ex) * rinv2;
     const float4 tj = a.pr.tq[j];
     const float4 drj4 = a.pr.dr[j];
-    const float cp = tj.x;
-    const V3 dp = mk(tj.y, tj.z, tj.w);
-    const V3 drj = mk(drj4.x, drj4.y, drj4.z);
-    auto g2 = [&](V3 u) { return (-B1) * u + (dot(r, u) * B2) * r; };
-    auto g3 = [&](V3 u, V3 v) {
-      const float ur = dot(u, r), vr = dot(v, r);
-      return B2 * (vr * u + ur * v + dot(u, v) * r) - (ur * vr * B3) * r;
-    };
-    auto g4 = [&](V3 u, V3 v, V3 w) {
-      const float ur = dot(u, r), vr = dot(v, r), wr = dot(w, r);
-      const float uv = dot(u, v), uw = dot(u, w), vw = dot(v, w);
-      V3 o = B2 * (vw * u + uw * v + uv * w);
-      o = o - B3 * ((vr * wr) * u + (ur * wr) * v + (ur * vr) * w + (uv * wr + uw * vr + vw * ur) * r);
-      return o + (B4 * ur * vr * wr) * r;
-    };
-    // primal potential: Hessian and third-derivative contractions
-    const V3 Hdr = c * g2(I.dr) - g3(d, I.dr);
-    const V3 Hw = c * g2(I.w) - g3(d, I.w);
-    const V3 T3 = c * g3(I.mu, I.dr) - g4(d, I.mu, I.dr);
-    // tangent potential of sources cp, dp, mu_j (x) dr_j
-    const float djr = dot(drj, r);
-    const float dphi = cp * B0 + dot(dp, r) * B1 - dot(d, drj) * B1 + dr_ * djr * B2;
-    const V3 gdphi = (-cp * B1) * r - g2(dp) + g3(d, drj);
-    const V3 Hdmu = cp * g2(I.mu) - g3(dp, I.mu) + g4(d, drj, I.mu);
-    // grad_q = gE phi + dphi + grad phi . dr ; grad_mu = gE grad phi + grad dphi + H dr
-    // grad_r = (gE q + dq) grad phi + H w + q grad dphi + (grad grad dphi) mu + T3[mu, dr]
-    A.gq += I.gE * phi + dphi + dot(gphi, I.dr);
-    acc(A.gm, I.gE * gphi + gdphi + Hdr);
-    acc(A.gr, (I.gE * I.q + I.dq) * gphi + Hw + I.q * gdphi + Hdmu + T3);
+    const float cp = tj.x;                       // tangent charge of j
+    const V3 dp = mk(tj.y, tj.z, tj.w);          // tangent dipole d'_j = dmu_j + q_j dr_j
+    const V3 drj = mk(drj4.x, drj4.y, drj4.z);   // dr_j
+    const V3 m = I.mu, t = I.dr, w = I.w;
+    // Every term below is a contraction of grad^k psi (k <= 4) with the vectors r, d = mu_j,
+    // d', dr_j, mu_i, dr_i, w_i; it is written as a combination of those vectors with scalar
+    // coefficients built from their dot products:
+    //   H(u)      = (grad grad phi) u            = alpha u + (ru s_rr - B2 du) r - B2 ru d
+    //   T3        = (grad^3 phi)[mu_i, dr_i]
+    //   gdphi     = grad of the potential of the tangent sources (cp, d', mu_j (x) dr_j)
+    //   Hdmu      = (grad grad dphi) mu_i
+    // with alpha = -(c B1 + rd B2), s_rr = c B2 + rd B3 (the coefficients of g2 / g3 / g4
+    // contractions of the header, expanded).
+    const float rd = dr_, rm = dot(r, m), rt = dot(r, t), rw = dot(r, w);
+    const float rdp = dot(r, dp), rdj = dot(r, drj);
+    const float d_t = dot(d, t), d_w = dot(d, w), d_m = dot(d, m), m_t = dot(m, t);
+    const float dp_m = dot(dp, m), dj_m = dot(drj, m), d_dj = dot(d, drj);
+    const float al = -c * B1 - rd * B2;          // gphi = al r + B1 d
+    const float s_rr = c * B2 + rd * B3;
+    const float dphi = cp * B0 + (rdp - d_dj) * B1 + rd * rdj * B2;
+    const float gd_r = -cp * B1 - rdp * B2 + d_dj * B2 - rd * rdj * B3;   // gdphi = gd_r r + B1 d'
+                                                                          //   + B2 rdj d + B2 rd dr_j
+    // T3 on m, t, d, r
+    const float T_m = c * B2 * rt - B2 * d_t + B3 * rd * rt;
+    const float T_t = c * B2 * rm - B2 * d_m + B3 * rd * rm;
+    const float T_d = -B2 * m_t + B3 * rm * rt;
+    const float T_r = c * B2 * m_t - c * rm * rt * B3 + B3 * (d_m * rt + d_t * rm + m_t * rd) - B4 * rd * rm * rt;
+    // Hdmu on m, r, d', d, dr_j
+    const float D_m = -cp * B1 - B2 * rdp + B2 * d_dj - B3 * rd * rdj;
+    const float D_r = cp * rm * B2 - B2 * dp_m + rdp * rm * B3 - B3 * (d_dj * rm + d_m * rdj + dj_m * rd) +
+                      B4 * rd * rdj * rm;
+    const float D_dp = -B2 * rm;
+    const float D_d = B2 * dj_m - B3 * rdj * rm;
+    const float D_dj = B2 * d_m - B3 * rd * rm;
+    // grad_q = gE phi + dphi + gphi . dr_i
+    A.gq += I.gE * phi + dphi + al * rt + B1 * d_t;
+    // grad_mu = gE gphi + gdphi + H(dr_i)
+    {
+      const float cr = I.gE * al + gd_r + (rt * s_rr - B2 * d_t);
+      const float cd = I.gE * B1 + B2 * rdj - B2 * rt;
+      const float cdp = B1, cdj = B2 * rd, ct = al;
+      acc(A.gm, cr * r + cd * d + cdp * dp + cdj * drj + ct * t);
+    }
+    // grad_r = (gE q + dq) gphi + H(w_i) + q gdphi + Hdmu + T3
+    {
+      const float k1 = I.gE * I.q + I.dq;
+      const float cr = k1 * al + (rw * s_rr - B2 * d_w) + I.q * gd_r + D_r + T_r;
+      const float cd = k1 * B1 - B2 * rw + I.q * B2 * rdj + D_d + T_d;
+      const float cw = al;
+      const float cdp = I.q * B1 + D_dp;
+      const float cdj = I.q * B2 * rd + D_dj;
+      const float cm = D_m + T_m;
+      const float ct = T_t;
+      acc(A.gr, cr * r + cd * d + cw * w + cdp * dp + cdj * drj + cm * m + ct * t);
+    }
   }
 }
 
