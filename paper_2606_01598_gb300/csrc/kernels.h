@@ -32,7 +32,9 @@ int launch_input_check(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool w
 
 // spread.cu: owner-computes spread of rho (and, with tangent, of the tangent density) of every
 // frame; frame f writes mesh + mesh_off (and mesh + tmesh_off).
-int launch_spread(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh);
+// keep_rho (tangent pass, nullable): *keep_rho == 0 means rho is in place from the forward on
+// the same inputs; only d rho is formed and written.
+int launch_spread(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh, const int* keep_rho = nullptr);
 
 // influence.cu: in-place G C / V multiply of every frame's spectrum (and tangent spectrum)
 // and the float64 energy partials (one per block, blocks grouped by frame).

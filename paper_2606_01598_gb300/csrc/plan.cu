@@ -813,7 +813,7 @@ static int run_backward(pme_plan_t p, cudaStream_t s, const IonInputs& in, const
     prof_end(p, t, ps);
   }
   t = prof_begin(p, B + 1, s);
-  if ((st = launch_spread(p, s, true, p->rho))) return st;
+  if ((st = launch_spread(p, s, true, p->rho, reuse ? p->in_diff : nullptr))) return st;
   prof_end(p, t, s);
   t = prof_begin(p, B + 2, s);
   if ((st = fft_forward(p, s, true))) return st;

@@ -42,6 +42,9 @@ struct SpreadArgs {
   const int* start_b;
   const int* cand;      // base of the candidate tables
   float* mesh;          // base of the meshes: rho at mesh_off, d rho at tmesh_off
+  // tangent pass: *keep_rho == 0 means rho is still in place from the forward on the same
+  // inputs, so only d rho is formed and written (null: form both)
+  const int* keep_rho;
 };
 
 // z weight rows are padded with ZS - 1 zeros on both sides, so a segment reads its ZS weights
@@ -106,6 +109,7 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
   const int b0x = bx * BX, b0y = by * BY, b0z = bz * BZ;
   const int ex = min(BX, g.N[0] - b0x), ey = min(BY, g.N[1] - b0y), ez = min(BZ, g.N[2] - b0z);
   const int Nx = g.N[0], Ny = g.N[1], Nz = g.N[2];
+  const bool with_rho = !TAN || !a.keep_rho || *a.keep_rho != 0;
 
   // ---- (1) candidate source bricks: product of the per-axis lists, in a fixed order ----
   const int* ct = a.cand + F.cand_off;
@@ -292,8 +296,8 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
           const float wy = wt[(1 * DW + 0) * P + dy], wy1 = wt[(1 * DW + 1) * P + dy];
           const float wxy = wx * wy;
           // rho: coefficient of W_z and of W'_z
-          const float A = c[0] * wxy + c[1] * wx1 * wy + c[2] * wx * wy1;
-          const float B = c[3] * wxy;
+          const float A = with_rho ? c[0] * wxy + c[1] * wx1 * wy + c[2] * wx * wy1 : 0.f;
+          const float B = with_rho ? c[3] * wxy : 0.f;
           float A0 = 0.f, A1 = 0.f, A2 = 0.f;
           if (TAN) {
             const float wx2 = wt[(0 * DW + 2) * P + dx], wy2 = wt[(1 * DW + 2) * P + dy];
@@ -309,10 +313,15 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
             // the stencil meets this segment either from below (dz < P) or from above
             // (dz > Nz - ZS, i.e. index dz - Nz of the window)
             const float* wzs = wz + (dz < P ? dz : dz - Nz);
+            if (!TAN || with_rho) {
 #pragma unroll
-            for (int z = 0; z < ZS; ++z) {
-              acc[z] += A * wzs[z] + B * wzs[ZP + z];
-              if (TAN) dacc[z] += A0 * wzs[z] + A1 * wzs[ZP + z] + A2 * wzs[2 * ZP + z];
+              for (int z = 0; z < ZS; ++z) {
+                acc[z] += A * wzs[z] + B * wzs[ZP + z];
+                if (TAN) dacc[z] += A0 * wzs[z] + A1 * wzs[ZP + z] + A2 * wzs[2 * ZP + z];
+              }
+            } else {
+#pragma unroll
+              for (int z = 0; z < ZS; ++z) dacc[z] += A0 * wzs[z] + A1 * wzs[ZP + z] + A2 * wzs[2 * ZP + z];
             }
           } else {
 #pragma unroll
@@ -341,7 +350,7 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
 #pragma unroll
     for (int z = 0; z < ZS; ++z)
       if (z < nz) {
-        rho[z] = acc[z];
+        if (with_rho) rho[z] = acc[z];
         if (TAN) drho[z] = dacc[z];
       }
   }
@@ -366,8 +375,9 @@ int launch_order(pme_plan_t p, cudaStream_t s, int grid, const SpreadArgs& a) {
 }
 
 template <bool TAN, bool BATCH>
-int launch_t(pme_plan_t p, cudaStream_t s, float* mesh) {
+int launch_t(pme_plan_t p, cudaStream_t s, float* mesh, const int* keep_rho) {
   SpreadArgs a;
+  a.keep_rho = TAN ? keep_rho : nullptr;
   a.one = p->frames_h[0];
   a.maps = p->maps;
   a.mr = p->mr;
@@ -404,10 +414,10 @@ void spread_brick_shape(int shape[3]) {
   shape[2] = BZ;
 }
 
-int launch_spread(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh) {
+int launch_spread(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh, const int* keep_rho) {
   if (p->batch)
-    return tangent ? launch_t<true, true>(p, s, mesh) : launch_t<false, true>(p, s, mesh);
-  return tangent ? launch_t<true, false>(p, s, mesh) : launch_t<false, false>(p, s, mesh);
+    return tangent ? launch_t<true, true>(p, s, mesh, keep_rho) : launch_t<false, true>(p, s, mesh, keep_rho);
+  return tangent ? launch_t<true, false>(p, s, mesh, keep_rho) : launch_t<false, false>(p, s, mesh, keep_rho);
 }
 
 }  // namespace gbpme
