@@ -23,7 +23,7 @@ namespace gbpme {
 
 namespace {
 
-constexpr int kCombThreads = 256;
+constexpr int kCombThreads = kRedItem;   // one block per reduction item
 
 struct CombineArgs {
   FrameDesc one;

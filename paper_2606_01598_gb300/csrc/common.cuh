@@ -18,8 +18,8 @@ constexpr int kMaxCandPerDim = 4;   // bricks along one axis that can feed one b
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kProfCap = 4096;
 // Ions per item of the per-frame sums (charges, energies): a frame of n ions is split into
-// max(1, ceil(n / kRedItem)) items, one 256-thread block each (one ion per thread).
-constexpr int kRedItem = 256;
+// max(1, ceil(n / kRedItem)) items, one kRedItem-thread block each (one ion per thread).
+constexpr int kRedItem = 128;
 
 // ----------------------------------------------------------------------------------------
 // launch bookkeeping
@@ -79,7 +79,14 @@ struct SortBuffers {
   int* perm_c;
   double* qpart;  // [2 * items] Q and dQ of each reduction item
   int* qcount;    // [frames] items finished (reset by the last one); null: no charge sums wanted
-  int* gcount;    // [1] blocks of the binning pass finished (reset by the last one)
+  // per-ion records formed by the binning pass in caller order (null: the rank pass forms
+  // them itself), copied to their sorted slots by the rank pass
+  int4* t_bidx;
+  float4* t_bfq;
+  float4* t_bdm;
+  int4* t_cidx;
+  float4* t_cfq;
+  float4* t_cmu;
   double* qsum;   // [2 * frames] Q and dQ of each frame
 };
 

@@ -190,6 +190,7 @@ extern "C" int pme_spread_noalloc(void* stream, const double box[9], const int m
   v.sb.start_c = reinterpret_cast<int*>(base + kOffStartC);
   v.sb.qpart = reinterpret_cast<double*>(base + kOffQpart);
   v.sb.qcount = nullptr;   // the spread needs no charge sums: the sort skips them
+  v.sb.t_bidx = nullptr;   // no room for caller-order records: the rank pass forms them
   v.sb.qsum = reinterpret_cast<double*>(base + kOffQsum);
   v.mr.idx = reinterpret_cast<int4*>(base + kOffIdx);
   v.mr.fq = reinterpret_cast<float4*>(base + kOffFq);
@@ -198,12 +199,11 @@ extern "C" int pme_spread_noalloc(void* stream, const double box[9], const int m
   v.mr.tt = nullptr;
   v.cand = reinterpret_cast<int*>(base + kOffCand);
   v.flags = reinterpret_cast<int*>(base + kOffFlags);
-  v.sb.gcount = v.flags + 1;   // the binning pass's block counter shares the flag's 256 bytes
   // the candidate table and the error flag are per call: rewrite / clear them first
   if (cudaMemcpyAsync(v.cand, cand, sizeof(int) * 3 * fd.max_nb * (1 + kMaxCandPerDim),
                       cudaMemcpyHostToDevice, s) != cudaSuccess)
     return PME_ERR_CUDA;
-  if (cudaMemsetAsync(v.flags, 0, 2 * sizeof(int), s) != cudaSuccess) return PME_ERR_CUDA;
+  if (cudaMemsetAsync(v.flags, 0, sizeof(int), s) != cudaSuccess) return PME_ERR_CUDA;
   IonInputs in{};
   in.pos = pos;
   in.q = q;

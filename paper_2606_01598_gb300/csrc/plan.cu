@@ -261,9 +261,10 @@ static void free_plan(pme_plan_t p) {
                   p->mr.dm, p->mr.tq, p->mr.tt, p->pr.idx, p->pr.fq, p->pr.mu, p->pr.tq, p->pr.dr,
                   p->mesh_out, p->pair_out, p->e_ion, p->epart, p->flags, p->stage_f,
                   p->stage_d, p->ew_kn, p->ew_kv, p->ew_S, p->ew_fx, p->ew_qm, p->frames_d,
-                  p->map_buf, p->fft_work, p->sb.qpart, p->sb.qcount, p->eitem, p->ecount, p->sb.gcount,
+                  p->map_buf, p->fft_work, p->sb.qpart, p->sb.qcount, p->eitem, p->ecount,
                   p->plist, p->plist_cnt, p->in_saved, p->in_flags, p->vpart,
-                  p->pvir, p->vitem, p->gtab};
+                  p->pvir, p->vitem, p->gtab, p->sb.t_bidx, p->sb.t_bfq,
+                  p->sb.t_bdm, p->sb.t_cidx, p->sb.t_cfq, p->sb.t_cmu};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int g = 0; g < p->nfgroups; ++g) {
@@ -522,9 +523,14 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
   A(&p->sb.count_b, scan_entries(p->total_bricks));
   A(&p->sb.start_b, scan_entries(p->total_bricks));
   A(&p->sb.qsum, size_t(2) * F);
+  A(&p->sb.t_bidx, ni);
+  A(&p->sb.t_bfq, ni);
+  A(&p->sb.t_bdm, ni);
+  A(&p->sb.t_cidx, ni);
+  A(&p->sb.t_cfq, ni);
+  A(&p->sb.t_cmu, ni);
   A(&p->sb.qpart, size_t(2) * p->total_items);
   A(&p->sb.qcount, size_t(F));
-  A(&p->sb.gcount, 1);
   A(&p->eitem, size_t(p->total_items));
   A(&p->ecount, size_t(F));
   A(&p->mr.idx, ni);
@@ -577,7 +583,6 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
   if (st) return st;
   if ((st = check_cuda(p, cudaMemset(p->flags, 0, sizeof(int)), "memset"))) return st;
   if ((st = check_cuda(p, cudaMemset(p->sb.qcount, 0, sizeof(int) * F), "memset"))) return st;
-  if ((st = check_cuda(p, cudaMemset(p->sb.gcount, 0, sizeof(int)), "memset"))) return st;
   if ((st = check_cuda(p, cudaMemset(p->ecount, 0, sizeof(int) * F), "memset"))) return st;
   // candidate tables and deconvolution tables, frame by frame
   {

@@ -4,8 +4,9 @@
 // (Section 2.3.2, Eq. w3d) and the pair cell holding its position, both offset by its
 // frame's first global key, so that one counting sort orders every frame of a batch and the
 // ions of a frame stay contiguous. k_bin counts (one integer atomic per ion and key, never
-// per stencil point), adds up each frame's charges (and tangent charges) in a fixed order
-// for the background term, and its last block turns the counts into segment starts;
+// per stencil point), forms each ion's records and adds up each frame's charges (and tangent
+// charges) in a fixed order for the background term; k_scan turns the counts into segment
+// starts;
 // k_scatter places ions in arrival order, and k_rank_records re-ranks each segment by caller
 // index, which makes the order -- and hence every later sum -- deterministic, while writing
 // the per-ion records both orders need. (The allocation-free spread, which needs no charge
@@ -20,7 +21,7 @@ namespace gbpme {
 
 namespace {
 
-constexpr int kSortThreads = 256;
+constexpr int kSortThreads = kRedItem;   // binning: one block per reduction item
 constexpr int kRankMaxSegment = 2048;   // longer segments keep arrival order
 
 // Exclusive scan of one count array by one block of 1024 threads; start[n] = total. Each
@@ -74,9 +75,9 @@ __device__ void block_exclusive_scan(const int* count, int* start, int n) {
 }
 
 // One block per reduction item (kRedItem = kSortThreads ions of one frame, one per thread):
-// the ion's brick key and pair-cell key with one counting atomic each, the item's charge
-// sums (the last item of a frame adds the item partials in order), and -- in the block that
-// finishes last -- the exclusive scans that turn the final counts into segment starts.
+// the ion's brick key and pair-cell key with one counting atomic each, its records in caller
+// order, and the item's charge sums (the last item of a frame adds the item partials in
+// order).
 template <bool BATCH>
 __global__ void __launch_bounds__(kSortThreads)
 k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int tangent, int* flags,
@@ -106,11 +107,11 @@ k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int tangent, 
     double s[3];
     frac_coords(g, rx, ry, rz, s);
     int m0[3], c[3];
+    float fb[3], fc[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      float fr;
-      stencil_origin(s[b], g.N[b], g.order, m0[b], fr);
-      cell_origin(s[b], g.ncell[b], c[b], fr);
+      stencil_origin(s[b], g.N[b], g.order, m0[b], fb[b]);
+      cell_origin(s[b], g.ncell[b], c[b], fc[b]);
     }
     const int kb = F.brick_off + ((m0[0] / g.brick[0]) * g.nb[1] + m0[1] / g.brick[1]) * g.nb[2] +
                    m0[2] / g.brick[2];
@@ -119,6 +120,27 @@ k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int tangent, 
     sb.key_c[i] = kc;
     sb.slot_b[i] = atomicAdd(&sb.count_b[kb], 1);
     sb.slot_c[i] = atomicAdd(&sb.count_c[kc], 1);
+    if (sb.t_bidx) {
+      // the primal records of both orders, in caller order (the rank pass moves them)
+      const float qs = isfinite(qi) ? qi : 0.f;
+      float mu[3] = {0.f, 0.f, 0.f};
+      if (in.mu) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          mu[a] = in.mu[3 * i + a];
+          if (!isfinite(mu[a])) mu[a] = 0.f;
+        }
+      }
+      float pm[3];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) pm[b] = mu[0] * g.D[0 * 3 + b] + mu[1] * g.D[1 * 3 + b] + mu[2] * g.D[2 * 3 + b];
+      sb.t_bidx[i] = make_int4(m0[0], m0[1], m0[2], i);
+      sb.t_bfq[i] = make_float4(fb[0], fb[1], fb[2], qs);
+      sb.t_bdm[i] = make_float4(pm[0], pm[1], pm[2], 0.f);
+      sb.t_cidx[i] = make_int4(c[0], c[1], c[2], i);
+      sb.t_cfq[i] = make_float4(fc[0], fc[1], fc[2], __int_as_float(c[2]));
+      sb.t_cmu[i] = make_float4(mu[0], mu[1], mu[2], qs);
+    }
     qa = isfinite(qi) ? qi : 0.f;
     qb = (tangent && in.gphi) ? in.gphi[i] : 0.f;
   }
@@ -143,12 +165,16 @@ k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int tangent, 
       }
     }
   }
-  if (!re && last_item_done(sb.gcount, int(gridDim.x))) {
-    block_exclusive_scan(sb.count_b, sb.start_b, nbricks);
-    __syncthreads();
-    block_exclusive_scan(sb.count_c, sb.start_c, ncells);
-    if (threadIdx.x == 0) *sb.gcount = 0;
-  }
+  (void)nbricks;
+  (void)ncells;
+}
+
+// Segment starts from the final counts: block 0 scans the brick counts, block 1 the cell
+// counts (1024 threads each). Skipped on reuse.
+__global__ void __launch_bounds__(1024) k_scan(SortBuffers sb, int nbricks, int ncells, const int* reuse) {
+  if (reuse && *reuse == 0) return;
+  if (blockIdx.x == 0) block_exclusive_scan(sb.count_b, sb.start_b, nbricks);
+  else block_exclusive_scan(sb.count_c, sb.start_c, ncells);
 }
 
 __global__ void __launch_bounds__(kSortThreads)
@@ -241,6 +267,33 @@ k_rank_records(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, Mesh
     }
     return;
   }
+  if (sb.t_bidx) {
+    // primal records from the binning pass; tangent records formed here
+    if (mesh_side) {
+      mr.idx[dest] = sb.t_bidx[i];
+      mr.fq[dest] = sb.t_bfq[i];
+      mr.dm[dest] = sb.t_bdm[i];
+      if (tangent) {
+        float pd[3], pt[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          pd[b] = dp[0] * g.D[0 * 3 + b] + dp[1] * g.D[1 * 3 + b] + dp[2] * g.D[2 * 3 + b];
+          pt[b] = dr[0] * g.D[0 * 3 + b] + dr[1] * g.D[1 * 3 + b] + dr[2] * g.D[2 * 3 + b];
+        }
+        mr.tq[dest] = make_float4(dq, pd[0], pd[1], pd[2]);
+        mr.tt[dest] = make_float4(pt[0], pt[1], pt[2], 0.f);
+      }
+    } else {
+      pr.idx[dest] = sb.t_cidx[i];
+      pr.fq[dest] = sb.t_cfq[i];
+      pr.mu[dest] = sb.t_cmu[i];
+      if (tangent) {
+        pr.tq[dest] = make_float4(dq, dp[0], dp[1], dp[2]);
+        pr.dr[dest] = make_float4(dr[0], dr[1], dr[2], 0.f);
+      }
+    }
+    return;
+  }
   double s[3];
   frac_coords(g, rx, ry, rz, s);
   if (mesh_side) {
@@ -325,6 +378,9 @@ int launch_sort_t(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangen
                                                 p->total_bricks, p->total_cells, reuse);
     count_launch();
     if ((st = check_launch(p, "k_bin"))) return st;
+    k_scan<<<2, 1024, 0, s>>>(p->sb, p->total_bricks, p->total_cells, reuse);
+    count_launch();
+    if ((st = check_launch(p, "k_scan"))) return st;
   }
   if (nblk > 0) {
     k_scatter<<<nblk, kSortThreads, 0, s>>>(n, p->sb, need_mesh ? 1 : 0, need_pair ? 1 : 0, reuse);
