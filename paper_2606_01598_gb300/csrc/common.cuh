@@ -113,6 +113,31 @@ __device__ __forceinline__ int fdiv(int x, const FastDiv& f) {
   return int((__umulhi(f.m, unsigned(x)) + unsigned(x)) >> f.l);
 }
 
+// A pass (forward or backward) recorded as a CUDA graph: made on the second consecutive call
+// with the same arguments, replayed while they stay the same. The key holds every pointer and
+// size of the call and the host-side state the pass depends on; post_* is the host-side state
+// the pass leaves behind.
+struct PassKey {
+  unsigned long long v[24];
+  int len;
+  bool operator==(const PassKey& o) const {
+    if (len != o.len) return false;
+    for (int k = 0; k < len; ++k)
+      if (v[k] != o.v[k]) return false;
+    return true;
+  }
+};
+
+struct PassGraph {
+  PassKey key;
+  PassKey last;
+  bool have_last;
+  cudaGraphExec_t exec;
+  long long launches;   // kernels per replay (for pme_launch_count)
+  int post_fwd_n;
+  bool post_fwd_lists;
+};
+
 // One frame of a plan: its geometry and where its data lives in the plan's arrays. A single-
 // frame plan passes its one descriptor as a kernel argument; a batched plan keeps a table of
 // them in device memory and maps ions / bricks / blocks to frames with the FrameMaps arrays.
@@ -236,6 +261,9 @@ struct pme_plan_s {
   float2* ew_S = nullptr;     // [K] structure factor
   uint4* ew_fx = nullptr;     // [max_ions] fixed-point fractional coordinates
   float4* ew_qm = nullptr;    // [max_ions] q, mu
+  // CUDA graphs of repeated passes (0 forward, 1 backward)
+  gbpme::PassGraph* graphs = nullptr;
+  cudaStream_t cap_stream = nullptr;   // capture-only stream (nothing runs on it)
   // stage timers
   bool prof = false;
   cudaEvent_t* prof_ev = nullptr;   // [2 * kProfCap]

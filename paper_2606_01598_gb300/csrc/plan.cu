@@ -10,7 +10,9 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
+#include <initializer_list>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -179,11 +181,13 @@ struct Staging {
     size_t bytes;
   };
   std::vector<Pending> outs;
+  bool staged = false;   // some argument is a host pointer (the pass then runs without a graph)
 
   Staging(pme_plan_t p_, cudaStream_t s_, int n_) : p(p_), s(s_), n(n_) {}
 
   const float* in(const float* ptr, int width, int slot) {
     if (!ptr || is_device_pointer(ptr)) return ptr;
+    staged = true;
     float* d = p->stage_f + size_t(slot) * p->max_ions;
     const size_t bytes = sizeof(float) * size_t(width) * n;
     if (bytes && status == PME_OK)
@@ -194,6 +198,7 @@ struct Staging {
   // 2 = virials (9 per frame)
   const double* in_d(const double* ptr, int count, int slot) {
     if (!ptr || is_device_pointer(ptr)) return ptr;
+    staged = true;
     double* d = p->stage_d + size_t(slot) * p->nframes;
     if (status == PME_OK)
       status = check_cuda(p, cudaMemcpyAsync(d, ptr, sizeof(double) * count, cudaMemcpyHostToDevice, s),
@@ -202,12 +207,14 @@ struct Staging {
   }
   float* out(float* ptr, int width, int slot) {
     if (!ptr || is_device_pointer(ptr)) return ptr;
+    staged = true;
     float* d = p->stage_f + size_t(slot) * p->max_ions;
     outs.push_back({ptr, d, sizeof(float) * size_t(width) * n});
     return d;
   }
   double* out_d(double* ptr, int count, int slot) {
     if (!ptr || is_device_pointer(ptr)) return ptr;
+    staged = true;
     double* d = p->stage_d + size_t(slot) * p->nframes;
     outs.push_back({ptr, d, sizeof(double) * count});
     return d;
@@ -253,6 +260,8 @@ static int join_side(pme_plan_t p, cudaStream_t s) {
   return check_cuda(p, cudaStreamWaitEvent(s, p->ev_join, 0), "stream wait");
 }
 
+static void drop_graphs(pme_plan_t p);
+
 static void free_plan(pme_plan_t p) {
   if (!p) return;
   void* bufs[] = {p->rho, p->spec, p->phi, p->dconv_all, p->cand, p->sb.key_b, p->sb.key_c,
@@ -282,6 +291,9 @@ static void free_plan(pme_plan_t p) {
     delete[] p->prof_ev;
     delete[] p->prof_stage;
   }
+  drop_graphs(p);
+  delete[] p->graphs;
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   if (p->side) cudaStreamDestroy(p->side);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
@@ -670,6 +682,10 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
   }
   if (p->gtab && ((st = launch_p3m_tables(p, 0)) || (st = check_cuda(p, cudaDeviceSynchronize(), "synchronize"))))
     return st;
+  p->graphs = new (std::nothrow) PassGraph[2];
+  if (!p->graphs) return set_error(p, PME_ERR_NOMEM, "host tables");
+  std::memset(p->graphs, 0, sizeof(PassGraph) * 2);
+  if ((st = check_cuda(p, cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking), "stream"))) return st;
   if ((st = check_cuda(p, cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking), "stream")) ||
       (st = check_cuda(p, cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming), "event")) ||
       (st = check_cuda(p, cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming), "event")))
@@ -728,6 +744,85 @@ static int forward_ewald(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool
 }
 
 // Forward pass over every frame of the plan (in.n ions in total).
+// ---- CUDA graphs of repeated passes ------------------------------------------------------
+
+static PassKey make_key(std::initializer_list<unsigned long long> vals) {
+  PassKey k{};
+  for (unsigned long long v : vals) k.v[k.len++] = v;
+  return k;
+}
+
+static unsigned long long ptr_bits(const void* ptr) { return (unsigned long long)(uintptr_t)ptr; }
+
+static void drop_graphs(pme_plan_t p) {
+  if (!p->graphs) return;
+  for (int k = 0; k < 2; ++k) {
+    if (p->graphs[k].exec) cudaGraphExecDestroy(p->graphs[k].exec);
+    p->graphs[k].exec = nullptr;
+    p->graphs[k].have_last = false;
+  }
+}
+
+// Run a pass, through a CUDA graph when the same call (key) comes again: the second identical
+// call records the pass on the plan's capture stream and launches the graph; later identical
+// calls only launch it. eligible = false (host-pointer staging, stage timers on) runs directly.
+template <class Run>
+static int run_pass(pme_plan_t p, int which, cudaStream_t s, const PassKey& key, bool eligible, Run&& run) {
+  PassGraph& G = p->graphs[which];
+  if (!eligible || p->prof) {
+    G.have_last = false;
+    return run(s);
+  }
+  if (G.exec && G.key == key) {
+    int st = check_cuda(p, cudaGraphLaunch(G.exec, s), "graph launch");
+    if (st) return st;
+    for (long long k = 0; k < G.launches; ++k) count_launch();
+    p->fwd_n = G.post_fwd_n;
+    p->fwd_lists = G.post_fwd_lists;
+    return PME_OK;
+  }
+  if (!(G.have_last && G.last == key)) {
+    G.last = key;
+    G.have_last = true;
+    return run(s);
+  }
+  // second identical call: record the pass (nothing executes while capturing)
+  const long long before = pme_launch_count();
+  const int save_n = p->fwd_n;
+  const bool save_lists = p->fwd_lists;
+  cudaGraph_t graph = nullptr;
+  int st = check_cuda(p, cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+  if (!st) {
+    const int rs = run(p->cap_stream);
+    const cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &graph);
+    if (rs || ce != cudaSuccess || !graph) st = rs ? rs : check_cuda(p, ce, "end capture");
+  }
+  const long long captured = pme_launch_count() - before;
+  g_launches.fetch_sub(captured, std::memory_order_relaxed);   // recorded, not launched
+  cudaGraphExec_t exec = nullptr;
+  if (!st) st = check_cuda(p, cudaGraphInstantiate(&exec, graph, 0), "graph instantiate");
+  if (graph) cudaGraphDestroy(graph);
+  if (st) {
+    // fall back to a direct run with the host state as it was
+    cudaGetLastError();
+    p->last_error.clear();
+    p->fwd_n = save_n;
+    p->fwd_lists = save_lists;
+    G.have_last = false;
+    return run(s);
+  }
+  if (G.exec) cudaGraphExecDestroy(G.exec);
+  G.exec = exec;
+  G.key = key;
+  G.launches = captured;
+  G.post_fwd_n = p->fwd_n;
+  G.post_fwd_lists = p->fwd_lists;
+  st = check_cuda(p, cudaGraphLaunch(G.exec, s), "graph launch");
+  if (st) return st;
+  for (long long k = 0; k < G.launches; ++k) count_launch();
+  return PME_OK;
+}
+
 // v_out (nullable): also the frame virials, [9] per frame (needs e_out).
 static int run_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, double* e_out, float* f_out,
                        float* p_out, float* fl_out, float* fg_out, double* v_out = nullptr) {
@@ -998,6 +1093,7 @@ int pme_plan_set_box(pme_plan_t p, const double box[9]) {
   D.ncells = nc;
   p->g = g;
   p->fwd_n = -1;   // the saved forward belongs to the old box
+  drop_graphs(p);  // recorded passes carry the old geometry
   std::memcpy(p->box, box, sizeof(double) * 9);
   if (p->gtab && ((st = launch_p3m_tables(p, 0)) || (st = check_cuda(p, cudaDeviceSynchronize(), "synchronize"))))
     return st;
@@ -1056,7 +1152,12 @@ int pme_forward(pme_plan_t p, void* stream, int n, const float* pos, const float
   float* fl_out = sg.out(field, 3, kOField);
   float* fg_out = sg.out(field_grad, 6, kOFG);
   if (sg.status) return sg.status;
-  if ((st = run_forward(p, s, in, e_out, f_out, p_out, fl_out, fg_out))) return st;
+  const PassKey key = make_key({0ull, (unsigned long long)n, ptr_bits(in.pos), ptr_bits(in.q), ptr_bits(in.mu),
+                                ptr_bits(e_out), ptr_bits(f_out), ptr_bits(p_out), ptr_bits(fl_out),
+                                ptr_bits(fg_out)});
+  st = run_pass(p, 0, s, key, !sg.staged,
+                [&](cudaStream_t cs) { return run_forward(p, cs, in, e_out, f_out, p_out, fl_out, fg_out); });
+  if (st) return st;
   return sg.finish();
 }
 
@@ -1112,7 +1213,13 @@ int pme_backward(pme_plan_t p, void* stream, int n, const float* pos, const floa
   float* o_q = sg.out(grad_q, 1, kOGQ);
   float* o_mu = sg.out(grad_mu, 3, kOGMu);
   if (sg.status) return sg.status;
-  if ((st = run_backward(p, s, in, gE, o_pos, o_q, o_mu))) return st;
+  const PassKey key = make_key({1ull, (unsigned long long)n, ptr_bits(in.pos), ptr_bits(in.q), ptr_bits(in.mu),
+                                ptr_bits(gE), ptr_bits(in.gforce), ptr_bits(in.gphi), ptr_bits(in.gfield),
+                                ptr_bits(o_pos), ptr_bits(o_q), ptr_bits(o_mu),
+                                (unsigned long long)(long long)p->fwd_n, (unsigned long long)p->fwd_lists});
+  st = run_pass(p, 1, s, key, !sg.staged,
+                [&](cudaStream_t cs) { return run_backward(p, cs, in, gE, o_pos, o_q, o_mu); });
+  if (st) return st;
   return sg.finish();
 }
 
@@ -1141,7 +1248,12 @@ int pme_batch_forward(pme_plan_t p, void* stream, const float* pos, const float*
   float* fl_out = sg.out(field, 3, kOField);
   float* fg_out = sg.out(field_grad, 6, kOFG);
   if (sg.status) return sg.status;
-  if ((st = run_forward(p, s, in, e_out, f_out, p_out, fl_out, fg_out))) return st;
+  const PassKey key = make_key({0ull, (unsigned long long)n, ptr_bits(in.pos), ptr_bits(in.q), ptr_bits(in.mu),
+                                ptr_bits(e_out), ptr_bits(f_out), ptr_bits(p_out), ptr_bits(fl_out),
+                                ptr_bits(fg_out)});
+  st = run_pass(p, 0, s, key, !sg.staged,
+                [&](cudaStream_t cs) { return run_forward(p, cs, in, e_out, f_out, p_out, fl_out, fg_out); });
+  if (st) return st;
   return sg.finish();
 }
 
@@ -1195,7 +1307,13 @@ int pme_batch_backward(pme_plan_t p, void* stream, const float* pos, const float
   float* o_q = sg.out(grad_q, 1, kOGQ);
   float* o_mu = sg.out(grad_mu, 3, kOGMu);
   if (sg.status) return sg.status;
-  if ((st = run_backward(p, s, in, gE, o_pos, o_q, o_mu))) return st;
+  const PassKey key = make_key({1ull, (unsigned long long)n, ptr_bits(in.pos), ptr_bits(in.q), ptr_bits(in.mu),
+                                ptr_bits(gE), ptr_bits(in.gforce), ptr_bits(in.gphi), ptr_bits(in.gfield),
+                                ptr_bits(o_pos), ptr_bits(o_q), ptr_bits(o_mu),
+                                (unsigned long long)(long long)p->fwd_n, (unsigned long long)p->fwd_lists});
+  st = run_pass(p, 1, s, key, !sg.staged,
+                [&](cudaStream_t cs) { return run_backward(p, cs, in, gE, o_pos, o_q, o_mu); });
+  if (st) return st;
   return sg.finish();
 }
 

@@ -1,0 +1,91 @@
+"""Passes recorded as CUDA graphs: the second identical pme_forward / pme_backward call records
+the pass and later identical calls replay it. Replays must give the direct run's results bit
+for bit, keep pme_launch_count honest, follow the host-side reuse state, and be dropped when
+the box changes."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import pme as O2
+
+from gpu_util import TOL_F, f32, prepared, relrmse
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2606_01598_gb300 as g
+    return g
+
+
+def _c(x):
+    return torch.tensor(np.float32(x), device="cuda")
+
+
+def test_repeated_passes_replay_bitwise(gb):
+    fr = W.molten_nacl(700, seed=81)
+    pos, q, mu = prepared(fr)
+    gF, gphi, gfield = (f32(x) for x in W.tangent(fr.n, seed=83))
+    P, Q, MU = _c(pos), _c(q), _c(mu)
+    gE = torch.tensor([0.4], dtype=torch.float64, device="cuda")
+    T = (gE, _c(gF), _c(gphi), _c(gfield))
+    plan = gb.Plan(fr.box, (30, 30, 30), 6, 0.30, 9.0, max_ions=1024)
+    # preallocated outputs: the same pointers every call
+    n = fr.n
+    E = torch.empty(1, dtype=torch.float64, device="cuda")
+    F = torch.empty((n, 3), device="cuda")
+    PH = torch.empty(n, device="cuda")
+    FL = torch.empty((n, 3), device="cuda")
+    GP = torch.empty((n, 3), device="cuda")
+    GQ = torch.empty(n, device="cuda")
+    GM = torch.empty((n, 3), device="cuda")
+    lib, h = plan.lib, plan.handle
+    p_ = lambda t: None if t is None else t.data_ptr()
+    s = torch.cuda.current_stream().cuda_stream
+
+    def fwd():
+        assert lib.pme_forward(h, s, n, p_(P), p_(Q), p_(MU), p_(E), p_(F), p_(PH), p_(FL), None) == 0
+
+    def bwd():
+        assert lib.pme_backward(h, s, n, p_(P), p_(Q), p_(MU), p_(T[0]), p_(T[1]), p_(T[2]), p_(T[3]),
+                                p_(GP), p_(GQ), p_(GM)) == 0
+
+    ref = None
+    for k in range(5):   # direct, record + launch, then replays
+        c0 = gb.launch_count()
+        fwd()
+        bwd()
+        torch.cuda.synchronize()
+        launched = gb.launch_count() - c0
+        assert launched > 10
+        got = [x.clone() for x in (E, F, PH, FL, GP, GQ, GM)]
+        if ref is None:
+            ref = got
+            ref_launched = launched
+        else:
+            for a, b in zip(ref, got):
+                assert torch.equal(a, b), k
+            assert launched == ref_launched, k
+    # against a fresh plan (direct runs)
+    fresh = gb.Plan(fr.box, (30, 30, 30), 6, 0.30, 9.0, max_ions=1024)
+    out = fresh.forward(P, Q, MU)
+    assert torch.equal(out["force"], ref[1])
+    back = fresh.backward(P, Q, MU, *T)
+    for a, b in zip(back, ref[4:]):
+        assert torch.equal(a, b)
+    # a new box drops the recorded passes: the forces follow the new box
+    box2 = fr.box * 1.02
+    plan.set_box(box2)
+    P2 = P * 1.02
+    P.copy_(P2)   # same pointer, new contents
+    fwd()
+    fwd()
+    torch.cuda.synchronize()
+    o = O2.PMEOracle(box2, (30, 30, 30), 6, 0.30, 9.0).evaluate(P.cpu().double().numpy(), q, mu, field_grad=False)
+    assert relrmse(F.cpu().numpy(), o["force"]) < TOL_F
+    plan.close()
+    fresh.close()
