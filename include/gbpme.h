@@ -87,7 +87,14 @@ typedef struct {
                               phi(k_m) / [(sum_m U_m)(sum_m k_m^2 U_m)], U_m = prod sinc^(2p);
                               deconvolution and influence_power are then unused, and
                               pme_forward_virial reports PME_ERR_UNSUPPORTED */
-  int reserved[5];
+  int fft;                 /* transforms of the mesh convolution. The library's own apply when
+                              every mesh axis of every frame is 2,3,5-smooth and at most 256
+                              long and a mesh plane fits in one block's shared memory.
+                              0 (default): automatic, the library's own for batched plans
+                              where they apply (one launch per pass for all frames), cuFFT
+                              otherwise. 1: always cuFFT. 2: always the library's own
+                              (PME_ERR_UNSUPPORTED where they do not apply) */
+  int reserved[4];
 } pme_opts;
 
 void pme_opts_default(pme_opts* opts);
@@ -111,6 +118,11 @@ int pme_plan_create(pme_plan_t* out, const double box[9], const int mesh[3], int
 int pme_plan_set_box(pme_plan_t plan, const double box[9]);
 
 int pme_plan_destroy(pme_plan_t plan);
+
+/* Which transforms the plan's mesh convolution uses: *kind = 0 for the library's own
+ * (Stockham transforms in shared memory, the x transform fused with the influence multiply),
+ * 1 for cuFFT. */
+int pme_plan_fft_kind(pme_plan_t plan, int* kind);
 
 /* Text of the last error recorded on the plan (never NULL). */
 const char* pme_last_error(pme_plan_t plan);

@@ -26,7 +26,7 @@ class PMEOpts(ctypes.Structure):
                 ("include_pair", c_int), ("include_self", c_int), ("include_background", c_int),
                 ("max_ions", c_int), ("brick", c_int * 3), ("overlap_pair", c_int),
                 ("recip_method", c_int), ("ewald_kmax", c_double), ("influence_kind", c_int),
-                ("reserved", c_int * 5)]
+                ("fft", c_int), ("reserved", c_int * 4)]
 
 
 _SIGS = {
@@ -36,6 +36,7 @@ _SIGS = {
                                 c_double, ctypes.POINTER(PMEOpts)]),
     "pme_plan_set_box": (c_int, [c_void_p, c_double_p]),
     "pme_plan_destroy": (c_int, [c_void_p]),
+    "pme_plan_fft_kind": (c_int, [c_void_p, c_int_p]),
     "pme_last_error": (ctypes.c_char_p, [c_void_p]),
     "pme_status_string": (ctypes.c_char_p, [c_int]),
     "pme_sync_status": (c_int, [c_void_p, c_void_p]),

@@ -155,6 +155,8 @@ struct FrameDesc {
   int cand_off, max_nb;     // candidate-brick table [3][max_nb][1 + kMaxCandPerDim]
   int dconv_off;            // deconvolution tables: x at dconv_off, y at +Nx, z at +Nx+Ny
   int infl_blk_off, infl_nblk;  // influence / energy blocks of this frame
+  int tw_off[3];            // hand-written transforms: twiddle tables of the x, y, z lengths
+  int conv_ntile, conv_kz;  // pass-B tiles per n_y row and their n_z width
   int item_off, nitems;     // items of the per-frame float64 sums
   FastDiv div_zh, div_y;    // division by Nz/2 + 1 and by Ny (half-spectrum index -> n)
 };
@@ -204,6 +206,14 @@ struct pme_plan_s {
   gbpme::OrderGroup ogroups[8];
   int nogroups = 0;
   gbpme::FFTGroup* fgroups = nullptr;
+  // hand-written transforms (every axis 2,3,5-smooth and short enough): no cuFFT plans
+  bool conv = false;
+  float2* conv_tw = nullptr;               // twiddle tables
+  int2* conv_planes1 = nullptr;            // batched plans: pass A / C block -> (frame, plane)
+  int2* conv_planes2 = nullptr;            //   the same with the tangent meshes
+  int conv_nplanes1 = 0, conv_nplanes2 = 0;
+  int conv_cap = 0, conv_threads = 0;
+  size_t conv_smem_plane = 0, conv_smem_x = 0;
   int nfgroups = 0;
   void* fft_work = nullptr;
   double* e_ion = nullptr;                // [max_ions] per-ion energy contributions

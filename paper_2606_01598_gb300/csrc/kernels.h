@@ -50,6 +50,23 @@ int influence_blocks(const Geometry& g);
 int launch_p3m_tables(pme_plan_t p, cudaStream_t s);
 void spread_brick_shape(int shape[3]);
 
+// conv.cu: the mesh convolution by hand-written transforms (meshes whose axes are all
+// 2,3,5-smooth and at most kConvMaxLen long, planes within shared memory).
+//   forward: R2C of every rho (and, tangent, d rho) in mesh into the plan's spectra
+//   influence: x transform, G C / V multiply with the energy (virial) partials, inverse x
+//   inverse: C2R of the spectra into mesh (Phi, and d Phi)
+constexpr int kConvMaxLen = 256;
+bool conv_axis_ok(int L);
+void conv_tiles(int Nz, int* ntile, int* kz);
+size_t conv_plane_cap(const int N[3]);
+size_t conv_plane_smem(const int N[3], size_t cap);
+size_t conv_x_smem(const int N[3]);
+void conv_twiddles(int L, std::vector<float2>& out);
+int launch_conv_forward(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh);
+int launch_conv_influence(pme_plan_t p, cudaStream_t s, bool tangent, double* partials,
+                          double* vparts = nullptr);
+int launch_conv_inverse(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh);
+
 // gather.cu: per-ion interpolation of the potential mesh(es).
 //   forward: out[orig][10] = phi, dphi/dr (3), d2phi/drdr (6)
 //   tangent: out[orig][8]  = mesh part of (grad_r (3), grad_q, grad_mu (3)) of the backward

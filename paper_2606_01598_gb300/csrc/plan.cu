@@ -273,7 +273,8 @@ static void free_plan(pme_plan_t p) {
                   p->map_buf, p->fft_work, p->sb.qpart, p->sb.qcount, p->eitem, p->ecount,
                   p->plist, p->plist_cnt, p->in_saved, p->in_flags, p->vpart,
                   p->pvir, p->vitem, p->gtab, p->sb.t_bidx, p->sb.t_bfq,
-                  p->sb.t_bdm, p->sb.t_cidx, p->sb.t_cfq, p->sb.t_cmu};
+                  p->sb.t_bdm, p->sb.t_cidx, p->sb.t_cfq, p->sb.t_cmu, p->conv_tw,
+                  p->conv_planes1};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int g = 0; g < p->nfgroups; ++g) {
@@ -360,6 +361,13 @@ struct FrameInput {
   int ion_off, n;
 };
 
+// Whether the options ask for the hand-written transforms: fft 2 always; fft 0 (automatic)
+// for batched plans, whose frames then share one launch per pass instead of a cuFFT plan per
+// mesh shape. The axis lengths and shared-memory sizes are checked by the caller.
+static bool conv_wanted(const pme_plan_s* p, bool single) {
+  return p->opts.fft == 2 || (p->opts.fft == 0 && !single);
+}
+
 // Build a plan over the given frames. single: one frame whose ion count is chosen per call.
 static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double alpha, double rcut,
                       bool single) {
@@ -376,6 +384,37 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
   if (p->max_ions > (1 << 27)) return set_error(p, PME_ERR_UNSUPPORTED, "more than 2^27 ions in one plan");
   int brick[3];
   spread_brick_shape(brick);
+  // the mesh convolution runs on the hand-written transforms when the options ask for them,
+  // every axis of every frame is 2,3,5-smooth and short enough, and a plane (pass A / C) and
+  // a pass-B tile fit in shared memory
+  {
+    bool conv = conv_wanted(p, single);
+    size_t cap = 0, smem_plane = 0, smem_x = 0, biggest = 0;
+    for (int f = 0; f < F && conv; ++f) {
+      for (int a = 0; a < 3; ++a) conv = conv && conv_axis_ok(fin[f].mesh[a]);
+      if (!conv) break;
+      cap = std::max(cap, conv_plane_cap(fin[f].mesh));
+      smem_x = std::max(smem_x, conv_x_smem(fin[f].mesh));
+      biggest = std::max(biggest, size_t(fin[f].mesh[1]) * (fin[f].mesh[2] / 2 + 1));
+    }
+    if (conv) {
+      for (int f = 0; f < F; ++f) smem_plane = std::max(smem_plane, conv_plane_smem(fin[f].mesh, cap));
+      int dev = 0, optin = 0;
+      cudaGetDevice(&dev);
+      if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        optin = 0;
+      }
+      conv = smem_plane + 1024 <= size_t(optin) && smem_x + 1024 <= size_t(optin);
+    }
+    if (!conv && p->opts.fft == 2)
+      return set_error(p, PME_ERR_UNSUPPORTED, "fft = 2: a mesh the library's transforms do not take");
+    p->conv = conv;
+    p->conv_cap = int(cap);
+    p->conv_smem_plane = smem_plane;
+    p->conv_smem_x = smem_x;
+    p->conv_threads = biggest >= 8192 ? 1024 : (biggest >= 2048 ? 512 : 256);
+  }
   std::vector<int> ncells(F);
   for (int f = 0; f < F; ++f) {
     FrameDesc& D = p->frames_h[f];
@@ -402,7 +441,12 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
     D.max_nb = std::max(g.nb[0], std::max(g.nb[1], g.nb[2]));
     if ((long long)g.N[0] * g.N[1] * (g.N[2] / 2 + 1) >= (1LL << 30))
       return set_error(p, PME_ERR_UNSUPPORTED, "half spectrum of a frame above 2^30 points");
-    D.infl_nblk = influence_blocks(g);
+    if (p->conv) {
+      conv_tiles(g.N[2], &D.conv_ntile, &D.conv_kz);
+      D.infl_nblk = g.N[1] * D.conv_ntile;
+    } else {
+      D.infl_nblk = influence_blocks(g);
+    }
     D.div_zh = make_fastdiv(g.N[2] / 2 + 1);
     D.div_y = make_fastdiv(g.N[1]);
     D.nitems = single ? std::max(1, (p->max_ions + kRedItem - 1) / kRedItem)
@@ -622,6 +666,40 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
                          "copy deconvolution")))
       return st;
   }
+  if (p->conv) {
+    // twiddle tables, one per distinct axis length
+    std::vector<float2> tw;
+    std::vector<int> tw_at(kConvMaxLen + 1, -1);
+    for (int f = 0; f < F; ++f)
+      for (int a = 0; a < 3; ++a) {
+        const int L = p->frames_h[f].g.N[a];
+        if (tw_at[L] < 0) {
+          tw_at[L] = int(tw.size());
+          conv_twiddles(L, tw);
+        }
+        p->frames_h[f].tw_off[a] = tw_at[L];
+      }
+    if ((st = dalloc(p, &p->conv_tw, tw.size()))) return st;
+    if ((st = check_cuda(p, cudaMemcpy(p->conv_tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice),
+                         "copy twiddles")))
+      return st;
+    if (!single) {
+      // pass A / C blocks: (frame, plane) without and with the tangent meshes
+      std::vector<int2> planes;
+      for (int f : ord)
+        for (int x = 0; x < p->frames_h[f].g.N[0]; ++x) planes.push_back(make_int2(f, x));
+      p->conv_nplanes1 = int(planes.size());
+      for (int f : ord)
+        for (int x = 0; x < 2 * p->frames_h[f].g.N[0]; ++x) planes.push_back(make_int2(f, x));
+      p->conv_nplanes2 = int(planes.size()) - p->conv_nplanes1;
+      if ((st = dalloc(p, &p->conv_planes1, planes.size()))) return st;
+      if ((st = check_cuda(p, cudaMemcpy(p->conv_planes1, planes.data(), sizeof(int2) * planes.size(),
+                                         cudaMemcpyHostToDevice),
+                           "copy plane maps")))
+        return st;
+      p->conv_planes2 = p->conv_planes1 + p->conv_nplanes1;
+    }
+  }
   // batched plans: descriptor table and frame maps on the device
   if (!single) {
     const long long Ntot = p->frame_offsets[F];
@@ -658,7 +736,7 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
   }
   // cuFFT: four plans per group sharing one work area
   size_t work = 0;
-  for (int gi = 0; gi < p->nfgroups; ++gi) {
+  for (int gi = 0; gi < p->nfgroups && !p->conv; ++gi) {
     FFTGroup& G = p->fgroups[gi];
     int dims[3] = {G.N[0], G.N[1], G.N[2]};
     cufftHandle* hs[4] = {&G.r2c, &G.c2r, &G.r2c2, &G.c2r2};
@@ -674,8 +752,9 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
       work = std::max(work, ws);
     }
   }
-  if ((st = check_cuda(p, cudaMalloc(&p->fft_work, std::max<size_t>(work, 16)), "cudaMalloc"))) return st;
-  for (int gi = 0; gi < p->nfgroups; ++gi) {
+  if (!p->conv && (st = check_cuda(p, cudaMalloc(&p->fft_work, std::max<size_t>(work, 16)), "cudaMalloc")))
+    return st;
+  for (int gi = 0; gi < p->nfgroups && !p->conv; ++gi) {
     FFTGroup& G = p->fgroups[gi];
     for (cufftHandle h : {G.r2c, G.c2r, G.r2c2, G.c2r2})
       if ((st = check_fft(p, cufftSetWorkArea(h, p->fft_work), "cufftSetWorkArea"))) return st;
@@ -696,6 +775,7 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
 // ---- the passes ----------------------------------------------------------------------------
 
 static int fft_forward(pme_plan_t p, cudaStream_t s, bool tangent) {
+  if (p->conv) return launch_conv_forward(p, s, tangent, p->rho);
   int st;
   for (int gi = 0; gi < p->nfgroups; ++gi) {
     FFTGroup& G = p->fgroups[gi];
@@ -707,6 +787,7 @@ static int fft_forward(pme_plan_t p, cudaStream_t s, bool tangent) {
 }
 
 static int fft_inverse(pme_plan_t p, cudaStream_t s, bool tangent) {
+  if (p->conv) return launch_conv_inverse(p, s, tangent, p->phi);
   int st;
   for (int gi = 0; gi < p->nfgroups; ++gi) {
     FFTGroup& G = p->fgroups[gi];
@@ -715,6 +796,14 @@ static int fft_inverse(pme_plan_t p, cudaStream_t s, bool tangent) {
     if ((st = check_fft(p, cufftExecC2R(h, p->spec + G.spec_off, p->phi + G.mesh_off), "exec c2r"))) return st;
   }
   return PME_OK;
+}
+
+// The influence stage: with the hand-written transforms, the x transforms and the multiply
+// in one pass (the spectra are then transformed along z and y only); otherwise in place on
+// cuFFT's full spectra.
+static int multiply_influence(pme_plan_t p, cudaStream_t s, bool tangent, double* vparts) {
+  if (p->conv) return launch_conv_influence(p, s, tangent, p->epart, vparts);
+  return launch_influence(p, s, p->spec, tangent, p->epart, vparts);
 }
 
 // Forward with the explicit k-sum in place of the mesh stages (single-frame plans).
@@ -864,7 +953,7 @@ static int run_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, double
   if ((st = fft_forward(p, s, false))) return st;
   prof_end(p, t, s);
   t = prof_begin(p, 3, s);
-  if ((st = launch_influence(p, s, p->spec, false, p->epart, v_out ? p->vpart : nullptr))) return st;
+  if ((st = multiply_influence(p, s, false, v_out ? p->vpart : nullptr))) return st;
   prof_end(p, t, s);
   t = prof_begin(p, 4, s);
   if ((st = fft_inverse(p, s, false))) return st;
@@ -919,7 +1008,7 @@ static int run_backward(pme_plan_t p, cudaStream_t s, const IonInputs& in, const
   if ((st = fft_forward(p, s, true))) return st;
   prof_end(p, t, s);
   t = prof_begin(p, B + 3, s);
-  if ((st = launch_influence(p, s, p->spec, true, p->epart))) return st;
+  if ((st = multiply_influence(p, s, true, nullptr))) return st;
   prof_end(p, t, s);
   t = prof_begin(p, B + 4, s);
   if ((st = fft_inverse(p, s, true))) return st;
@@ -941,6 +1030,7 @@ static int validate_opts(pme_plan_s* p, double alpha, double rcut) {
   if (!(p->opts.influence_power >= 0.0)) return set_error(p, PME_ERR_ARG, "influence_power < 0");
   if (p->opts.recip_method < 0 || p->opts.recip_method > 1) return set_error(p, PME_ERR_ARG, "recip_method");
   if (p->opts.influence_kind < 0 || p->opts.influence_kind > 1) return set_error(p, PME_ERR_ARG, "influence_kind");
+  if (p->opts.fft < 0 || p->opts.fft > 2) return set_error(p, PME_ERR_ARG, "fft");
   p->opts_kmax = p->opts.ewald_kmax > 0.0 ? p->opts.ewald_kmax : 2.0 * alpha * std::sqrt(std::log(1e8));
   return PME_OK;
 }
@@ -1114,6 +1204,12 @@ int pme_plan_destroy(pme_plan_t p) {
   cudaSetDevice(p->device);
   cudaDeviceSynchronize();
   free_plan(p);
+  return PME_OK;
+}
+
+int pme_plan_fft_kind(pme_plan_t p, int* kind) {
+  if (!p || !kind) return PME_ERR_ARG;
+  *kind = p->conv ? 0 : 1;
   return PME_OK;
 }
 
@@ -1346,11 +1442,17 @@ int pme_solve(pme_plan_t p, void* stream, const float* rho, float* phi_mesh, dou
   if ((st = check_cuda(p, cudaMemcpyAsync(p->rho, rho, sizeof(float) * p->M, cudaMemcpyDeviceToDevice, s),
                        "copy rho")))
     return st;
-  if ((st = check_fft(p, cufftSetStream(G.r2c, s), "set stream"))) return st;
-  if ((st = check_fft(p, cufftExecR2C(G.r2c, p->rho, p->spec), "exec r2c"))) return st;
-  if ((st = launch_influence(p, s, p->spec, false, p->epart))) return st;
-  if ((st = check_fft(p, cufftSetStream(G.c2r, s), "set stream"))) return st;
-  if ((st = check_fft(p, cufftExecC2R(G.c2r, p->spec, phi_mesh), "exec c2r"))) return st;
+  if (p->conv) {
+    if ((st = launch_conv_forward(p, s, false, p->rho)) || (st = multiply_influence(p, s, false, nullptr)) ||
+        (st = launch_conv_inverse(p, s, false, phi_mesh)))
+      return st;
+  } else {
+    if ((st = check_fft(p, cufftSetStream(G.r2c, s), "set stream"))) return st;
+    if ((st = check_fft(p, cufftExecR2C(G.r2c, p->rho, p->spec), "exec r2c"))) return st;
+    if ((st = launch_influence(p, s, p->spec, false, p->epart))) return st;
+    if ((st = check_fft(p, cufftSetStream(G.c2r, s), "set stream"))) return st;
+    if ((st = check_fft(p, cufftExecC2R(G.c2r, p->spec, phi_mesh), "exec c2r"))) return st;
+  }
   if (e_recip) return launch_energy_final(p, s, p->epart, 1, false, false, 1.0, 0, e_recip);
   return PME_OK;
 }

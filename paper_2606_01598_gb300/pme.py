@@ -79,6 +79,9 @@ def launch_count() -> int:
     return int(_abi.load().pme_launch_count())
 
 
+_FFT_KINDS = {"auto": 0, "cufft": 1, "own": 2}
+
+
 class Plan:
     """One box, mesh, spline order, alpha and cutoff; owns all device scratch."""
 
@@ -87,7 +90,7 @@ class Plan:
                  coulomb_k: float = 1.0, include_pair: bool = True, include_self: bool = True,
                  include_background: bool = True, max_ions: int = 1 << 18,
                  overlap_pair: bool = True, recip_method: str = "mesh", ewald_kmax: float = 0.0,
-                 influence: str = "deconvolution", device=None):
+                 influence: str = "deconvolution", fft: str = "auto", device=None):
         if not torch.cuda.is_available():
             raise RuntimeError("gbpme needs a CUDA device; there is no CPU fallback")
         self.lib = _abi.load()
@@ -113,6 +116,9 @@ class Plan:
         if influence not in ("deconvolution", "p3m"):
             raise ValueError("influence is 'deconvolution' or 'p3m'")
         opts.influence_kind = 0 if influence == "deconvolution" else 1
+        if fft not in _FFT_KINDS:
+            raise ValueError("fft is 'auto', 'cufft' or 'own'")
+        opts.fft = _FFT_KINDS[fft]
         opts.recip_method = 0 if recip_method == "mesh" else 1
         opts.ewald_kmax = float(ewald_kmax)
         self.box = np.asarray(box, np.float64).reshape(3, 3).copy()
@@ -152,6 +158,13 @@ class Plan:
         self.box = np.asarray(box, np.float64).reshape(3, 3).copy()
         b = (ctypes.c_double * 9)(*self.box.reshape(9))
         self._check(self.lib.pme_plan_set_box(self.handle, b), "pme_plan_set_box")
+
+    @property
+    def fft_kind(self) -> str:
+        """'own' (the library's transforms) or 'cufft' (pme_plan_fft_kind)."""
+        k = ctypes.c_int(-1)
+        self._check(self.lib.pme_plan_fft_kind(self.handle, ctypes.byref(k)), "pme_plan_fft_kind")
+        return "own" if k.value == 0 else "cufft"
 
     def sync_status(self):
         with torch.cuda.device(self.device):
@@ -293,7 +306,7 @@ class BatchPlan(Plan):
                  influence_power: float = 1.0, deconvolution: bool = True,
                  coulomb_k: float = 1.0, include_pair: bool = True, include_self: bool = True,
                  include_background: bool = True, overlap_pair: bool = True,
-                 influence: str = "deconvolution", device=None):
+                 influence: str = "deconvolution", fft: str = "auto", device=None):
         if not torch.cuda.is_available():
             raise RuntimeError("gbpme needs a CUDA device; there is no CPU fallback")
         self.lib = _abi.load()
@@ -311,6 +324,9 @@ class BatchPlan(Plan):
         if influence not in ("deconvolution", "p3m"):
             raise ValueError("influence is 'deconvolution' or 'p3m'")
         opts.influence_kind = 0 if influence == "deconvolution" else 1
+        if fft not in _FFT_KINDS:
+            raise ValueError("fft is 'auto', 'cufft' or 'own'")
+        opts.fft = _FFT_KINDS[fft]
         opts.include_self = int(bool(include_self))
         opts.include_background = int(bool(include_background))
         opts.overlap_pair = int(bool(overlap_pair))
