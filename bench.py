@@ -37,6 +37,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# transforms of the mesh convolution for every plan the bench makes (--fft, pme_opts.fft)
+FFT = "auto"
+
 METRIC = "PME q+mu fwd+bwd Mion-evals/s @32k ions"
 UNIT = "Mion-evals/s"
 
@@ -339,7 +342,7 @@ def vs_plain(gb, fr, cfg, dev, pos, q, mu, gE, gF, gphi, gfield, flush, steps):
     """Mesh-only forward + backward: this library (pair term off) against the plain PyTorch-ops
     formulation of the paper on the same GPU and frame."""
     import torch
-    plan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=fr.n, device=dev,
+    plan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=fr.n, device=dev, fft=FFT,
                    include_pair=False)
     plain = plain_pme(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], dev)
     gE32 = gE.float()
@@ -371,7 +374,7 @@ def vs_plain(gb, fr, cfg, dev, pos, q, mu, gE, gF, gphi, gfield, flush, steps):
 def virial_cost(gb, fr, cfg, dev, pos, q, mu, flush, steps):
     """Forward with and without the virial on the benchmark frame (CUDA events)."""
     import torch
-    plan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=fr.n, device=dev)
+    plan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=fr.n, device=dev, fft=FFT)
     k = max(3, steps // 4)
     t_f = time_steps(torch, lambda: plan.forward(pos, q, mu), k, 3, dev, flush)
     t_v = time_steps(torch, lambda: plan.forward(pos, q, mu, virial=True), k, 3, dev, flush)
@@ -404,7 +407,7 @@ def batch16_rooflines(gb, fr, cfg, dev, steps):
     gF, gphi, gfield = (torch.tensor(np.float32(x), device=dev) for x in W.tangent(F * n, seed=17))
     gE = torch.full((F,), 0.5, dtype=torch.float64, device=dev)
     bp = gb.BatchPlan([fr.box] * F, [cfg["mesh"]] * F, [cfg["order"]] * F, offsets, cfg["alpha"], cfg["rcut"],
-                      device=dev, overlap_pair=False)
+                      device=dev, fft=FFT, overlap_pair=False)
     for _ in range(2):
         bp.forward(P, Qv, MU)
         bp.backward(P, Qv, MU, gE, gF, gphi, gfield)
@@ -454,7 +457,7 @@ def run_ours(args):
     import workloads as W
 
     n = fr.n
-    plan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=n, device=dev)
+    plan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=n, device=dev, fft=FFT)
     c = lambda x: torch.tensor(np.float32(x), device=dev)
     pos, q, mu = c(fr.pos), c(fr.q), c(fr.mu)
     gF, gphi, gfield = (c(x) for x in W.tangent(n, seed=99))
@@ -505,7 +508,7 @@ def run_ours(args):
     # ---- per-kernel times: the same K steps with the pair term on the call's stream ---------
     # (stage events then bracket one kernel at a time; the overlapped run above is the value)
     splan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=n,
-                    device=dev, overlap_pair=False)
+                    device=dev, fft=FFT, overlap_pair=False)
 
     def sstep():
         splan.forward(pos, q, mu, energy=True, force=True, phi=True, field=True)
@@ -586,7 +589,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_dict(cfg, fr, ws),
+            "config": dict(config_dict(cfg, fr, ws), transforms=plan.fft_kind),
             "roofline": roof,
             "stage_ms": per_stage,
             "serial_ms_per_step": s_ms,
@@ -625,8 +628,8 @@ def run_crossover(args):
         mesh = gb.mesh_dims(fr.box, 0.8, rule=1, strategy=1)
         c = lambda x: torch.tensor(np.float32(x), device=dev)
         pos, q, mu = c(fr.pos), c(fr.q), c(fr.mu)
-        plans = {"pme": gb.Plan(fr.box, mesh, 6, 0.30, 9.0, max_ions=n, device=dev),
-                 "ewald": gb.Plan(fr.box, (8, 8, 8), 6, 0.30, 9.0, max_ions=n, device=dev,
+        plans = {"pme": gb.Plan(fr.box, mesh, 6, 0.30, 9.0, max_ions=n, device=dev, fft=FFT),
+                 "ewald": gb.Plan(fr.box, (8, 8, 8), 6, 0.30, 9.0, max_ions=n, device=dev, fft=FFT,
                                   recip_method="ewald")}
         res = {}
         outs = {}
@@ -681,7 +684,7 @@ def run_batch(args):
     mu = c(np.concatenate([fr.mu for fr in frames]))
     gF, gphi, gfield = (c(x) for x in W.tangent(N, seed=99))
     gE = torch.full((len(frames),), 0.5, dtype=torch.float64, device=dev)
-    bp = gb.BatchPlan([fr.box for fr in frames], meshes, orders, offsets, 0.30, 9.0, device=dev)
+    bp = gb.BatchPlan([fr.box for fr in frames], meshes, orders, offsets, 0.30, 9.0, device=dev, fft=FFT)
 
     def bstep():
         bp.forward(pos, q, mu)
@@ -723,7 +726,7 @@ def run_batch(args):
     singles = []
     for f, fr in enumerate(frames):
         lo, hi = int(offsets[f]), int(offsets[f + 1])
-        sp = gb.Plan(fr.box, meshes[f], orders[f], 0.30, 9.0, max_ions=max(fr.n, 64), device=dev)
+        sp = gb.Plan(fr.box, meshes[f], orders[f], 0.30, 9.0, max_ions=max(fr.n, 64), device=dev, fft=FFT)
         singles.append((sp, lo, hi))
     gE1 = torch.tensor([0.5], dtype=torch.float64, device=dev)
 
@@ -734,7 +737,7 @@ def run_batch(args):
 
     t_loop = timed(loop, max(2, args.steps // 4))
     # per-stage times of the batched step (pair term serialised so each event pair brackets one stage)
-    sp_ = gb.BatchPlan([fr.box for fr in frames], meshes, orders, offsets, 0.30, 9.0, device=dev,
+    sp_ = gb.BatchPlan([fr.box for fr in frames], meshes, orders, offsets, 0.30, 9.0, device=dev, fft=FFT,
                        overlap_pair=False)
     for _ in range(2):
         sp_.forward(pos, q, mu)
@@ -774,7 +777,11 @@ def main():
     ap.add_argument("--crossover", action="store_true", help="Ewald vs PME timing sweep")
     ap.add_argument("--batch", action="store_true", help="uneven batch vs per-frame loop")
     ap.add_argument("--frames", type=int, default=256)
+    ap.add_argument("--fft", default="auto", choices=["auto", "cufft", "own"],
+                    help="transforms of the mesh convolution (pme_opts.fft)")
     args = ap.parse_args()
+    global FFT
+    FFT = args.fft
     if args.batch:
         return run_batch(args)
     if args.crossover:

@@ -156,7 +156,7 @@ struct FrameDesc {
   int dconv_off;            // deconvolution tables: x at dconv_off, y at +Nx, z at +Nx+Ny
   int infl_blk_off, infl_nblk;  // influence / energy blocks of this frame
   int tw_off[3];            // hand-written transforms: twiddle tables of the x, y, z lengths
-  int conv_ntile, conv_kz;  // pass-B tiles per n_y row and their n_z width
+  int conv_cols;            // pass-B tile width in (n_y, n_z) columns
   int item_off, nitems;     // items of the per-frame float64 sums
   FastDiv div_zh, div_y;    // division by Nz/2 + 1 and by Ny (half-spectrum index -> n)
 };

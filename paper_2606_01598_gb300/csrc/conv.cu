@@ -7,10 +7,12 @@
 //     z, separated into the two half spectra (X_k = (Z_k + conj Z_{N-k}) / 2 and
 //     Y_k = (Z_k - conj Z_{N-k}) / 2i), transformed along y and stored as plane x of the
 //     [Nx][Ny][Nz/2+1] spectrum.
-//   pass B (k_conv_x), one CTA per (n_y, run of n_z columns) of a frame: transform along x,
-//     the influence multiply G C / V of every point with the energy (and virial) sums of the
-//     stand-alone influence pass, inverse transform along x. The backward's tangent spectrum
-//     rides in the same CTA as extra columns.
+//   pass B (k_conv_x), one CTA per run of C consecutive (n_y, n_z) columns of a frame (for a
+//     fixed x they are contiguous in the spectrum; C grows for short x axes so that a tile
+//     holds at least 1024 points): transform along x, the influence multiply G C / V of every
+//     point with the energy (and virial) sums of the stand-alone influence pass, inverse
+//     transform along x. The backward's tangent spectrum rides in the same CTA as extra
+//     columns.
 //   pass C (k_conv_c2r), one CTA per x-plane: inverse along y, Hermitian extension of each
 //     pair of half rows into one complex row, inverse along z, real and imaginary parts
 //     stored as two rows of Phi.
@@ -37,7 +39,8 @@ namespace gbpme {
 
 namespace {
 
-constexpr int kConvKZ = 16;              // widest run of n_z columns of one pass-B CTA
+constexpr int kConvMinCols = 16;         // narrowest pass-B tile (columns)
+constexpr int kConvMaxCols = 64;         // widest pass-B tile
 constexpr int kConvBThreads = 256;
 constexpr int kConvPlaneThreads = 1024;  // upper bound of the pass A / C block size
 constexpr int kLoadBatch = 8;            // global loads a thread keeps in flight
@@ -389,18 +392,17 @@ __global__ void __launch_bounds__(kConvBThreads) k_conv_x(ConvArgs a) {
   const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, BATCH ? a.maps.blk_frame[blockIdx.x] : 0);
   const Geometry& g = F.g;
   const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2], Nzh = N2 / 2 + 1;
-  const int local = blockIdx.x - F.infl_blk_off;
-  const int ky = local / F.conv_ntile;
-  const int kz0 = (local - ky * F.conv_ntile) * F.conv_kz;
-  const int kw = min(F.conv_kz, Nzh - kz0);
+  const int ncols = N1 * Nzh;   // (n_y, n_z) columns of a plane, contiguous for a fixed x
+  const int c0 = (blockIdx.x - F.infl_blk_off) * F.conv_cols;
+  const int kw = min(F.conv_cols, ncols - c0);
   const int nc = a.tangent ? 2 * kw : kw;
-  const float rnc = 1.f / float(nc), rkw = 1.f / float(kw);
+  const float rnc = 1.f / float(nc), rkw = 1.f / float(kw), rzh = 1.f / float(Nzh);
   float2* tw = csm;
   float2* b0 = csm + ((N0 + 1) & ~1);
   float2* b1 = b0 + N0 * nc;
   for (int k = threadIdx.x; k < N0; k += blockDim.x) tw[k] = a.tw[F.tw_off[0] + k];
-  float2* sp = a.spec + F.spec_off;
-  float2* tp = a.spec + F.tspec_off;
+  float2* sp = a.spec + F.spec_off + c0;
+  float2* tp = a.spec + F.tspec_off + c0;
   // tile [x][c]: columns [0, kw) of the spectrum, then (tangent) [kw, 2 kw) of the tangent one
   for (int t0 = threadIdx.x; t0 < N0 * nc; t0 += kLoadBatch * blockDim.x) {
     float2 v[kLoadBatch];
@@ -410,8 +412,7 @@ __global__ void __launch_bounds__(kConvBThreads) k_conv_x(ConvArgs a) {
       if (t < N0 * nc) {
         int x, c;
         split_rc(t, nc, rnc, x, c);
-        const float2* base = c < kw ? sp : tp;
-        v[u] = base[(size_t(x) * N1 + ky) * Nzh + kz0 + (c < kw ? c : c - kw)];
+        v[u] = c < kw ? sp[size_t(x) * ncols + c] : tp[size_t(x) * ncols + c - kw];
       }
     }
 #pragma unroll
@@ -426,22 +427,21 @@ __global__ void __launch_bounds__(kConvBThreads) k_conv_x(ConvArgs a) {
   const float* cy = cx + N0;
   const float* cz = cy + N1;
   const float four_pi = 12.566370614359172f;
-  const int iy = ky;
-  const float ny = float(iy <= N1 / 2 ? iy : iy - N1);
   float e = 0.f, ec = 0.f;
   float sv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, sc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int t = threadIdx.x; t < N0 * kw; t += blockDim.x) {
-    int ix, c;
+    int ix, c, iy, iz;
     split_rc(t, kw, rkw, ix, c);
-    const int iz = kz0 + c;
+    split_rc(c0 + c, Nzh, rzh, iy, iz);
     const float nx = float(ix <= N0 / 2 ? ix : ix - N0);
+    const float ny = float(iy <= N1 / 2 ? iy : iy - N1);
     const float nz = float(iz);
     const float kx = nx * g.bk[0] + ny * g.bk[3] + nz * g.bk[6];
     const float kyv = nx * g.bk[1] + ny * g.bk[4] + nz * g.bk[7];
     const float kz = nx * g.bk[2] + ny * g.bk[5] + nz * g.bk[8];
     const float k2 = kx * kx + kyv * kyv + kz * kz;
     float gc = 0.f;
-    if (a.gtab) gc = a.gtab[F.gtab_off + (size_t(ix) * N1 + iy) * Nzh + iz];
+    if (a.gtab) gc = a.gtab[F.gtab_off + size_t(ix) * ncols + c0 + c];
     else if (k2 > 0.f) gc = four_pi * expf(-k2 * a.inv4a2) / k2 * cx[ix] * cy[iy] * cz[iz];
     float2* pv = r + ix * nc + c;
     const float2 v = *pv;
@@ -469,8 +469,8 @@ __global__ void __launch_bounds__(kConvBThreads) k_conv_x(ConvArgs a) {
   for (int t = threadIdx.x; t < N0 * nc; t += blockDim.x) {
     int x, c;
     split_rc(t, nc, rnc, x, c);
-    float2* base = c < kw ? sp : tp;
-    base[(size_t(x) * N1 + ky) * Nzh + kz0 + (c < kw ? c : c - kw)] = o[t];
+    if (c < kw) sp[size_t(x) * ncols + c] = o[t];
+    else tp[size_t(x) * ncols + c - kw] = o[t];
   }
   __shared__ double wsum[kConvBThreads / 32];
   const double et = block_comp_sum(e, ec, wsum);
@@ -524,10 +524,12 @@ bool conv_axis_ok(int L) {
   return L == 1;
 }
 
-void conv_tiles(int Nz, int* ntile, int* kz) {
-  const int Nzh = Nz / 2 + 1;
-  *ntile = (Nzh + kConvKZ - 1) / kConvKZ;
-  *kz = (Nzh + *ntile - 1) / *ntile;
+void conv_tiles(const int N[3], int* ntile, int* cols) {
+  int c = kConvMinCols;
+  while (c < kConvMaxCols && N[0] * c < 1024) c *= 2;
+  const int ncols = N[1] * (N[2] / 2 + 1);
+  *cols = c;
+  *ntile = (ncols + c - 1) / c;
 }
 
 size_t conv_plane_cap(const int N[3]) {
@@ -540,9 +542,9 @@ size_t conv_plane_smem(const int N[3], size_t cap) {
 }
 
 size_t conv_x_smem(const int N[3]) {
-  int nt, kz;
-  conv_tiles(N[2], &nt, &kz);
-  return (size_t((N[0] + 1) & ~1) + 2 * size_t(N[0]) * 2 * kz) * sizeof(float2);
+  int nt, cols;
+  conv_tiles(N, &nt, &cols);
+  return (size_t((N[0] + 1) & ~1) + 2 * size_t(N[0]) * 2 * cols) * sizeof(float2);
 }
 
 void conv_twiddles(int L, std::vector<float2>& out) {

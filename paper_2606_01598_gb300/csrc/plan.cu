@@ -442,8 +442,7 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
     if ((long long)g.N[0] * g.N[1] * (g.N[2] / 2 + 1) >= (1LL << 30))
       return set_error(p, PME_ERR_UNSUPPORTED, "half spectrum of a frame above 2^30 points");
     if (p->conv) {
-      conv_tiles(g.N[2], &D.conv_ntile, &D.conv_kz);
-      D.infl_nblk = g.N[1] * D.conv_ntile;
+      conv_tiles(g.N, &D.infl_nblk, &D.conv_cols);
     } else {
       D.infl_nblk = influence_blocks(g);
     }
