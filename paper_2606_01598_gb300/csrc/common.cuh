@@ -157,6 +157,7 @@ struct FrameDesc {
   int infl_blk_off, infl_nblk;  // influence / energy blocks of this frame
   int tw_off[3];            // hand-written transforms: twiddle tables of the x, y, z lengths
   int conv_cols;            // pass-B tile width in (n_y, n_z) columns
+  int conv_pp;              // pass A / C: consecutive x-planes per block
   int item_off, nitems;     // items of the per-frame float64 sums
   FastDiv div_zh, div_y;    // division by Nz/2 + 1 and by Ny (half-spectrum index -> n)
 };

@@ -2,7 +2,8 @@
 // energy_recip): the R2C transform of every rho (and d rho), the influence multiply with the
 // reciprocal energy, and the C2R transform back to Phi (and d Phi), in three passes.
 //
-//   pass A (k_conv_r2c), one CTA per x-plane of a mesh: the plane's real rows are packed two
+//   pass A (k_conv_r2c), one CTA per x-plane of a mesh (several consecutive planes when they
+//     are small, transformed together as more lines): the plane's real rows are packed two
 //     to a complex row (row 2p as real part, row 2p+1 as imaginary part), transformed along
 //     z, separated into the two half spectra (X_k = (Z_k + conj Z_{N-k}) / 2 and
 //     Y_k = (Z_k - conj Z_{N-k}) / 2i), transformed along y and stored as plane x of the
@@ -13,7 +14,7 @@
 //     point with the energy (and virial) sums of the stand-alone influence pass, inverse
 //     transform along x. The backward's tangent spectrum rides in the same CTA as extra
 //     columns.
-//   pass C (k_conv_c2r), one CTA per x-plane: inverse along y, Hermitian extension of each
+//   pass C (k_conv_c2r), one CTA per x-plane (or several): inverse along y, Hermitian extension of each
 //     pair of half rows into one complex row, inverse along z, real and imaginary parts
 //     stored as two rows of Phi.
 //
@@ -44,6 +45,7 @@ constexpr int kConvMaxCols = 64;         // widest pass-B tile
 constexpr int kConvBThreads = 256;
 constexpr int kConvPlaneThreads = 1024;  // upper bound of the pass A / C block size
 constexpr int kLoadBatch = 8;            // global loads a thread keeps in flight
+constexpr size_t kConvPlaneTarget = 4096;  // small planes are grouped up to this many entries
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -258,9 +260,10 @@ __device__ __forceinline__ void plane_setup(const ConvArgs& a, const FrameDesc& 
   for (int k = threadIdx.x; k < Ny; k += blockDim.x) twy[k] = a.tw[F.tw_off[1] + k];
 }
 
+// Pass A / C block: frame, mesh copy (0: rho / Phi, 1: the tangent one), first plane x0 and
+// plane count pc (F.conv_pp consecutive x-planes per block, fewer in the last one).
 template <bool BATCH>
-__global__ void __launch_bounds__(kConvPlaneThreads) k_conv_r2c(ConvArgs a) {
-  extern __shared__ __align__(16) float2 csm[];
+__device__ __forceinline__ const FrameDesc& plane_block(const ConvArgs& a, int& copy, int& x0, int& pc) {
   int f = 0, local = blockIdx.x;
   if (BATCH) {
     const int2 m = a.planes[blockIdx.x];
@@ -268,19 +271,34 @@ __global__ void __launch_bounds__(kConvPlaneThreads) k_conv_r2c(ConvArgs a) {
     local = m.y;
   }
   const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, f);
-  const int Nx = F.g.N[0], Ny = F.g.N[1], Nz = F.g.N[2], Nzh = Nz / 2 + 1;
-  const int copy = local >= Nx ? 1 : 0;
-  const int x = local - copy * Nx;
+  const int Nx = F.g.N[0], P = F.conv_pp;
+  const int per_copy = (Nx + P - 1) / P;
+  copy = local >= per_copy ? 1 : 0;
+  x0 = (local - copy * per_copy) * P;
+  pc = min(P, Nx - x0);
+  return F;
+}
+
+// Shared-memory layouts of a block's pc planes (np = ceil(Ny / 2) row pairs, Zs = Nz | 1):
+//   Z: complex row pp of plane p at (p np + pp) Zs (rows 2pp, 2pp+1 as real, imaginary parts)
+//   S: half spectrum entry (y, k) of plane p at y Sw + p Nzh + k, Sw = pc Nzh (the columns of
+//      all planes side by side, so one transform along y covers them)
+template <bool BATCH>
+__global__ void __launch_bounds__(kConvPlaneThreads) k_conv_r2c(ConvArgs a) {
+  extern __shared__ __align__(16) float2 csm[];
+  int copy, x0, pc;
+  const FrameDesc& F = plane_block<BATCH>(a, copy, x0, pc);
+  const int Ny = F.g.N[1], Nz = F.g.N[2], Nzh = Nz / 2 + 1;
   float2 *twz, *twy, *b0, *b1;
   plane_setup(a, F, csm, twz, twy, b0, b1);
-  const int np = (Ny + 1) >> 1, Zs = Nz | 1;
+  const int np = (Ny + 1) >> 1, Zs = Nz | 1, Sw = pc * Nzh;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  // rows 2p and 2p+1 as the real and imaginary parts of complex row p (stride Zs)
-  const float* src = a.mesh + (copy ? F.tmesh_off : F.mesh_off) + size_t(x) * Ny * Nz;
+  const float rnz = 1.f / float(Nz), rny = 1.f / float(Ny), rnzh = 1.f / float(Nzh), rnp = 1.f / float(np);
+  const float* src = a.mesh + (copy ? F.tmesh_off : F.mesh_off) + size_t(x0) * Ny * Nz;
   float* zf = reinterpret_cast<float*>(b0);
   {
-    const int total = Ny * Nz;
-    const float rnz = 1.f / float(Nz);
+    // the pc planes are contiguous in the mesh; kLoadBatch loads in flight per thread
+    const int total = pc * Ny * Nz;
     for (int t0 = threadIdx.x; t0 < total; t0 += kLoadBatch * blockDim.x) {
       float v[kLoadBatch];
 #pragma unroll
@@ -292,72 +310,92 @@ __global__ void __launch_bounds__(kConvPlaneThreads) k_conv_r2c(ConvArgs a) {
       for (int u = 0; u < kLoadBatch; ++u) {
         const int t = t0 + u * blockDim.x;
         if (t < total) {
-          int y, z;
-          split_rc(t, Nz, rnz, y, z);
-          zf[2 * ((y >> 1) * Zs + z) + (y & 1)] = v[u];
+          int row, z, pl, y;
+          split_rc(t, Nz, rnz, row, z);
+          split_rc(row, Ny, rny, pl, y);
+          zf[2 * ((pl * np + (y >> 1)) * Zs + z) + (y & 1)] = v[u];
         }
       }
     }
-    if (Ny & 1)   // the unpaired last row's partner is zero
-      for (int z = threadIdx.x; z < Nz; z += blockDim.x) zf[2 * ((Ny >> 1) * Zs + z) + 1] = 0.f;
+    if (Ny & 1)   // each plane's unpaired last row has a zero partner
+      for (int t = threadIdx.x; t < pc * Nz; t += blockDim.x) {
+        int pl, z;
+        split_rc(t, Nz, rnz, pl, z);
+        zf[2 * ((pl * np + (Ny >> 1)) * Zs + z) + 1] = 0.f;
+      }
   }
   __syncthreads();
-  float2* r = fft_lines<false>(b0, b1, Nz, np, Zs, 1, twz);
+  float2* r = fft_lines<false>(b0, b1, Nz, pc * np, Zs, 1, twz);
   float2* o = r == b0 ? b1 : b0;
-  // separate the two real rows' half spectra: S[y][k], row stride Nzh
-  for (int pp = wid; pp < np; pp += nw)
+  // separate the two real rows' half spectra into S
+  for (int line = wid; line < pc * np; line += nw) {
+    int pl, pp;
+    split_rc(line, np, rnp, pl, pp);
+    const float2* zr = r + line * Zs;
+    float2* s0 = o + 2 * pp * Sw + pl * Nzh;
+    const bool has_b = 2 * pp + 1 < Ny;
     for (int k = lane; k < Nzh; k += 32) {
-      const float2 zk = r[pp * Zs + k];
-      const float2 zm = r[pp * Zs + (k == 0 ? 0 : Nz - k)];
-      o[2 * pp * Nzh + k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-      if (2 * pp + 1 < Ny) o[(2 * pp + 1) * Nzh + k] = make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
+      const float2 zk = zr[k];
+      const float2 zm = zr[k == 0 ? 0 : Nz - k];
+      s0[k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+      if (has_b) s0[Sw + k] = make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
     }
+  }
   __syncthreads();
-  const float2* s = fft_lines<false>(o, r, Ny, Nzh, 1, Nzh, twy);
-  float2* dst = a.spec + (copy ? F.tspec_off : F.spec_off) + size_t(x) * Ny * Nzh;
-  for (int t = threadIdx.x; t < Ny * Nzh; t += blockDim.x) dst[t] = s[t];
+  const float2* sres = fft_lines<false>(o, r, Ny, Sw, 1, Sw, twy);
+  // plane p's [ky][kz] block is contiguous in the spectrum, the pc planes one after another
+  float2* dst = a.spec + (copy ? F.tspec_off : F.spec_off) + size_t(x0) * Ny * Nzh;
+  for (int t = threadIdx.x; t < pc * Ny * Nzh; t += blockDim.x) {
+    int row, k, pl, y;
+    split_rc(t, Nzh, rnzh, row, k);
+    split_rc(row, Ny, rny, pl, y);
+    dst[t] = sres[y * Sw + pl * Nzh + k];
+  }
 }
 
 template <bool BATCH>
 __global__ void __launch_bounds__(kConvPlaneThreads) k_conv_c2r(ConvArgs a) {
   extern __shared__ __align__(16) float2 csm[];
-  int f = 0, local = blockIdx.x;
-  if (BATCH) {
-    const int2 m = a.planes[blockIdx.x];
-    f = m.x;
-    local = m.y;
-  }
-  const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, f);
-  const int Nx = F.g.N[0], Ny = F.g.N[1], Nz = F.g.N[2], Nzh = Nz / 2 + 1;
-  const int copy = local >= Nx ? 1 : 0;
-  const int x = local - copy * Nx;
+  int copy, x0, pc;
+  const FrameDesc& F = plane_block<BATCH>(a, copy, x0, pc);
+  const int Ny = F.g.N[1], Nz = F.g.N[2], Nzh = Nz / 2 + 1;
   float2 *twz, *twy, *b0, *b1;
   plane_setup(a, F, csm, twz, twy, b0, b1);
-  const int np = (Ny + 1) >> 1, Zs = Nz | 1;
+  const int np = (Ny + 1) >> 1, Zs = Nz | 1, Sw = pc * Nzh;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const float2* src = a.spec + (copy ? F.tspec_off : F.spec_off) + size_t(x) * Ny * Nzh;
-  for (int t0 = threadIdx.x; t0 < Ny * Nzh; t0 += kLoadBatch * blockDim.x) {
+  const float rnz = 1.f / float(Nz), rny = 1.f / float(Ny), rnzh = 1.f / float(Nzh), rnp = 1.f / float(np);
+  const float2* src = a.spec + (copy ? F.tspec_off : F.spec_off) + size_t(x0) * Ny * Nzh;
+  const int total = pc * Ny * Nzh;
+  for (int t0 = threadIdx.x; t0 < total; t0 += kLoadBatch * blockDim.x) {
     float2 v[kLoadBatch];
 #pragma unroll
     for (int u = 0; u < kLoadBatch; ++u) {
       const int t = t0 + u * blockDim.x;
-      if (t < Ny * Nzh) v[u] = src[t];
+      if (t < total) v[u] = src[t];
     }
 #pragma unroll
     for (int u = 0; u < kLoadBatch; ++u) {
       const int t = t0 + u * blockDim.x;
-      if (t < Ny * Nzh) b0[t] = v[u];
+      if (t < total) {
+        int row, k, pl, y;
+        split_rc(t, Nzh, rnzh, row, k);
+        split_rc(row, Ny, rny, pl, y);
+        b0[y * Sw + pl * Nzh + k] = v[u];
+      }
     }
   }
   __syncthreads();
-  float2* s = fft_lines<true>(b0, b1, Ny, Nzh, 1, Nzh, twy);
+  float2* s = fft_lines<true>(b0, b1, Ny, Sw, 1, Sw, twy);
   float2* o = s == b0 ? b1 : b0;
-  // complex row p = (half row 2p) + i (half row 2p+1), extended by Hermitian symmetry; the
-  // n_z = 0 and Nyquist entries of a real row's spectrum are real
-  for (int pp = wid; pp < np; pp += nw) {
-    const float2* ra = s + 2 * pp * Nzh;
-    const float2* rb = s + (2 * pp + 1) * Nzh;
+  // complex row (p, pp) = (half row 2pp) + i (half row 2pp+1), extended by Hermitian symmetry;
+  // the n_z = 0 and Nyquist entries of a real row's spectrum are real
+  for (int line = wid; line < pc * np; line += nw) {
+    int pl, pp;
+    split_rc(line, np, rnp, pl, pp);
+    const float2* ra = s + 2 * pp * Sw + pl * Nzh;
+    const float2* rb = ra + Sw;
     const bool has_b = 2 * pp + 1 < Ny;
+    float2* zr = o + line * Zs;
     for (int k = lane; k < Nz; k += 32) {
       float2 A, B = make_float2(0.f, 0.f);
       if (k < Nzh) {
@@ -375,15 +413,19 @@ __global__ void __launch_bounds__(kConvPlaneThreads) k_conv_c2r(ConvArgs a) {
           B.y = -B.y;
         }
       }
-      o[pp * Zs + k] = make_float2(A.x - B.y, A.y + B.x);
+      zr[k] = make_float2(A.x - B.y, A.y + B.x);
     }
   }
   __syncthreads();
-  const float2* z = fft_lines<true>(o, s, Nz, np, Zs, 1, twz);
+  const float2* z = fft_lines<true>(o, s, Nz, pc * np, Zs, 1, twz);
   const float* zf = reinterpret_cast<const float*>(z);
-  float* dst = a.mesh + (copy ? F.tmesh_off : F.mesh_off) + size_t(x) * Ny * Nz;
-  for (int y = wid; y < Ny; y += nw)
-    for (int k = lane; k < Nz; k += 32) dst[y * Nz + k] = zf[2 * ((y >> 1) * Zs + k) + (y & 1)];
+  float* dst = a.mesh + (copy ? F.tmesh_off : F.mesh_off) + size_t(x0) * Ny * Nz;
+  for (int t = threadIdx.x; t < pc * Ny * Nz; t += blockDim.x) {
+    int row, k, pl, y;
+    split_rc(t, Nz, rnz, row, k);
+    split_rc(row, Ny, rny, pl, y);
+    dst[t] = zf[2 * ((pl * np + (y >> 1)) * Zs + k) + (y & 1)];
+  }
 }
 
 template <bool BATCH, bool VIR>
@@ -532,10 +574,19 @@ void conv_tiles(const int N[3], int* ntile, int* cols) {
   *ntile = (ncols + c - 1) / c;
 }
 
-size_t conv_plane_cap(const int N[3]) {
+// Complex entries of one plane in either layout.
+static size_t plane_entries(const int N[3]) {
   const size_t np = size_t(N[1] + 1) / 2, Zs = size_t(N[2] | 1);
   return std::max(np * Zs, size_t(N[1]) * (N[2] / 2 + 1));
 }
+
+int conv_planes_per_block(const int N[3]) {
+  const size_t e = plane_entries(N);
+  const int p = int(std::max<size_t>(1, kConvPlaneTarget / e));
+  return std::min(p, N[0]);
+}
+
+size_t conv_plane_cap(const int N[3]) { return conv_planes_per_block(N) * plane_entries(N); }
 
 size_t conv_plane_smem(const int N[3], size_t cap) {
   return (size_t((N[1] + N[2] + 1) & ~1) + 2 * cap) * sizeof(float2);
@@ -559,8 +610,9 @@ int launch_conv_forward(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh)
   a.mesh = mesh;
   a.spec = reinterpret_cast<float2*>(p->spec);
   a.tangent = tangent ? 1 : 0;
+  const FrameDesc& F0 = p->frames_h[0];
   const int grid = p->batch ? (tangent ? p->conv_nplanes2 : p->conv_nplanes1)
-                            : (tangent ? 2 : 1) * p->frames_h[0].g.N[0];
+                            : (tangent ? 2 : 1) * ((F0.g.N[0] + F0.conv_pp - 1) / F0.conv_pp);
   a.planes = tangent ? p->conv_planes2 : p->conv_planes1;
   int st;
   if (p->batch) {
@@ -581,8 +633,9 @@ int launch_conv_inverse(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh)
   a.mesh = mesh;
   a.spec = reinterpret_cast<float2*>(p->spec);
   a.tangent = tangent ? 1 : 0;
+  const FrameDesc& F0 = p->frames_h[0];
   const int grid = p->batch ? (tangent ? p->conv_nplanes2 : p->conv_nplanes1)
-                            : (tangent ? 2 : 1) * p->frames_h[0].g.N[0];
+                            : (tangent ? 2 : 1) * ((F0.g.N[0] + F0.conv_pp - 1) / F0.conv_pp);
   a.planes = tangent ? p->conv_planes2 : p->conv_planes1;
   int st;
   if (p->batch) {

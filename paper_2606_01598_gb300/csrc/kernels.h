@@ -58,6 +58,7 @@ void spread_brick_shape(int shape[3]);
 constexpr int kConvMaxLen = 256;
 bool conv_axis_ok(int L);
 void conv_tiles(const int N[3], int* ntile, int* cols);
+int conv_planes_per_block(const int N[3]);
 size_t conv_plane_cap(const int N[3]);
 size_t conv_plane_smem(const int N[3], size_t cap);
 size_t conv_x_smem(const int N[3]);

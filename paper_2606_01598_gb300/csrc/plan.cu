@@ -395,7 +395,7 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
       if (!conv) break;
       cap = std::max(cap, conv_plane_cap(fin[f].mesh));
       smem_x = std::max(smem_x, conv_x_smem(fin[f].mesh));
-      biggest = std::max(biggest, size_t(fin[f].mesh[1]) * (fin[f].mesh[2] / 2 + 1));
+      biggest = std::max(biggest, conv_plane_cap(fin[f].mesh));
     }
     if (conv) {
       for (int f = 0; f < F; ++f) smem_plane = std::max(smem_plane, conv_plane_smem(fin[f].mesh, cap));
@@ -443,6 +443,7 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
       return set_error(p, PME_ERR_UNSUPPORTED, "half spectrum of a frame above 2^30 points");
     if (p->conv) {
       conv_tiles(g.N, &D.infl_nblk, &D.conv_cols);
+      D.conv_pp = conv_planes_per_block(g.N);
     } else {
       D.infl_nblk = influence_blocks(g);
     }
@@ -685,11 +686,15 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
     if (!single) {
       // pass A / C blocks: (frame, plane) without and with the tangent meshes
       std::vector<int2> planes;
+      auto per_copy = [&](int f) {
+        const FrameDesc& D = p->frames_h[f];
+        return (D.g.N[0] + D.conv_pp - 1) / D.conv_pp;
+      };
       for (int f : ord)
-        for (int x = 0; x < p->frames_h[f].g.N[0]; ++x) planes.push_back(make_int2(f, x));
+        for (int b = 0; b < per_copy(f); ++b) planes.push_back(make_int2(f, b));
       p->conv_nplanes1 = int(planes.size());
       for (int f : ord)
-        for (int x = 0; x < 2 * p->frames_h[f].g.N[0]; ++x) planes.push_back(make_int2(f, x));
+        for (int b = 0; b < 2 * per_copy(f); ++b) planes.push_back(make_int2(f, b));
       p->conv_nplanes2 = int(planes.size()) - p->conv_nplanes1;
       if ((st = dalloc(p, &p->conv_planes1, planes.size()))) return st;
       if ((st = check_cuda(p, cudaMemcpy(p->conv_planes1, planes.data(), sizeof(int2) * planes.size(),
