@@ -310,9 +310,10 @@ __global__ void __launch_bounds__(kConvPlaneThreads) k_conv_r2c(ConvArgs a) {
       for (int u = 0; u < kLoadBatch; ++u) {
         const int t = t0 + u * blockDim.x;
         if (t < total) {
-          int row, z, pl, y;
+          int row, z, pl = 0, y;
           split_rc(t, Nz, rnz, row, z);
-          split_rc(row, Ny, rny, pl, y);
+          if (pc > 1) split_rc(row, Ny, rny, pl, y);
+          else y = row;
           zf[2 * ((pl * np + (y >> 1)) * Zs + z) + (y & 1)] = v[u];
         }
       }
@@ -345,11 +346,15 @@ __global__ void __launch_bounds__(kConvPlaneThreads) k_conv_r2c(ConvArgs a) {
   const float2* sres = fft_lines<false>(o, r, Ny, Sw, 1, Sw, twy);
   // plane p's [ky][kz] block is contiguous in the spectrum, the pc planes one after another
   float2* dst = a.spec + (copy ? F.tspec_off : F.spec_off) + size_t(x0) * Ny * Nzh;
-  for (int t = threadIdx.x; t < pc * Ny * Nzh; t += blockDim.x) {
-    int row, k, pl, y;
-    split_rc(t, Nzh, rnzh, row, k);
-    split_rc(row, Ny, rny, pl, y);
-    dst[t] = sres[y * Sw + pl * Nzh + k];
+  if (pc == 1) {   // one plane: S is the plane's [ky][kz] block itself
+    for (int t = threadIdx.x; t < Ny * Nzh; t += blockDim.x) dst[t] = sres[t];
+  } else {
+    for (int t = threadIdx.x; t < pc * Ny * Nzh; t += blockDim.x) {
+      int row, k, pl, y;
+      split_rc(t, Nzh, rnzh, row, k);
+      split_rc(row, Ny, rny, pl, y);
+      dst[t] = sres[y * Sw + pl * Nzh + k];
+    }
   }
 }
 
@@ -377,10 +382,14 @@ __global__ void __launch_bounds__(kConvPlaneThreads) k_conv_c2r(ConvArgs a) {
     for (int u = 0; u < kLoadBatch; ++u) {
       const int t = t0 + u * blockDim.x;
       if (t < total) {
-        int row, k, pl, y;
-        split_rc(t, Nzh, rnzh, row, k);
-        split_rc(row, Ny, rny, pl, y);
-        b0[y * Sw + pl * Nzh + k] = v[u];
+        if (pc == 1) {   // one plane: S is the plane's [ky][kz] block itself
+          b0[t] = v[u];
+        } else {
+          int row, k, pl, y;
+          split_rc(t, Nzh, rnzh, row, k);
+          split_rc(row, Ny, rny, pl, y);
+          b0[y * Sw + pl * Nzh + k] = v[u];
+        }
       }
     }
   }
@@ -420,11 +429,12 @@ __global__ void __launch_bounds__(kConvPlaneThreads) k_conv_c2r(ConvArgs a) {
   const float2* z = fft_lines<true>(o, s, Nz, pc * np, Zs, 1, twz);
   const float* zf = reinterpret_cast<const float*>(z);
   float* dst = a.mesh + (copy ? F.tmesh_off : F.mesh_off) + size_t(x0) * Ny * Nz;
-  for (int t = threadIdx.x; t < pc * Ny * Nz; t += blockDim.x) {
-    int row, k, pl, y;
-    split_rc(t, Nz, rnz, row, k);
-    split_rc(row, Ny, rny, pl, y);
-    dst[t] = zf[2 * ((pl * np + (y >> 1)) * Zs + k) + (y & 1)];
+  for (int row = wid; row < pc * Ny; row += nw) {
+    int pl = 0, y = row;
+    if (pc > 1) split_rc(row, Ny, rny, pl, y);
+    const float* zr = zf + 2 * (pl * np + (y >> 1)) * Zs + (y & 1);
+    float* dr = dst + size_t(row) * Nz;
+    for (int k = lane; k < Nz; k += 32) dr[k] = zr[2 * k];
   }
 }
 
