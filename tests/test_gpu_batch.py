@@ -41,13 +41,16 @@ def _c(x):
     return torch.tensor(np.float32(x), device="cuda")
 
 
-def test_batch_forward_matches_single_frames(gb, batch):
+@pytest.mark.parametrize("fft", ["auto", "cufft"])
+def test_batch_forward_matches_single_frames(gb, batch, fft):
     B = batch
-    bp = gb.BatchPlan([fr.box for fr in B["frames"]], B["meshes"], B["orders"], B["offsets"], 0.30, 9.0)
+    bp = gb.BatchPlan([fr.box for fr in B["frames"]], B["meshes"], B["orders"], B["offsets"], 0.30, 9.0,
+                      fft=fft)
     out = bp.forward(_c(B["pos"]), _c(B["q"]), _c(B["mu"]), field_grad=True)
     for f, fr in enumerate(B["frames"]):
         lo, hi = B["offsets"][f], B["offsets"][f + 1]
-        sp = gb.Plan(fr.box, B["meshes"][f], B["orders"][f], 0.30, 9.0, max_ions=max(fr.n, 64))
+        sp = gb.Plan(fr.box, B["meshes"][f], B["orders"][f], 0.30, 9.0, max_ions=max(fr.n, 64),
+                     fft=bp.fft_kind)   # the batch's transforms: like for like
         ref = sp.forward(_c(B["pos"][lo:hi]), _c(B["q"][lo:hi]), _c(B["mu"][lo:hi]), field_grad=True)
         e = ref["energy"].item()
         assert abs(out["energy"][f].item() - e) < 1e-6 * abs(e), f
@@ -66,7 +69,8 @@ def test_batch_backward_matches_single_frames(gb, batch):
                       _c(gF), _c(gphi), _c(gfield))
     for f, fr in enumerate(B["frames"]):
         lo, hi = B["offsets"][f], B["offsets"][f + 1]
-        sp = gb.Plan(fr.box, B["meshes"][f], B["orders"][f], 0.30, 9.0, max_ions=max(fr.n, 64))
+        sp = gb.Plan(fr.box, B["meshes"][f], B["orders"][f], 0.30, 9.0, max_ions=max(fr.n, 64),
+                     fft=bp.fft_kind)   # the batch's transforms: like for like
         ref = sp.backward(_c(B["pos"][lo:hi]), _c(B["q"][lo:hi]), _c(B["mu"][lo:hi]),
                           torch.tensor([gE[f]], dtype=torch.float64, device="cuda"),
                           _c(gF[lo:hi]), _c(gphi[lo:hi]), _c(gfield[lo:hi]))

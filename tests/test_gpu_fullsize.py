@@ -119,7 +119,8 @@ def test_batch256_energies_match_single_frame_plans(gb, batch256):
     e_b = bp.forward(_c(B["pos"]), _c(B["q"]), _c(B["mu"]))["energy"].cpu().numpy()
     for f, fr in enumerate(B["frames"]):
         lo, hi = B["offsets"][f], B["offsets"][f + 1]
-        sp = gb.Plan(fr.box, B["meshes"][f], B["orders"][f], 0.30, 9.0, max_ions=max(fr.n, 64))
+        sp = gb.Plan(fr.box, B["meshes"][f], B["orders"][f], 0.30, 9.0, max_ions=max(fr.n, 64),
+                     fft=bp.fft_kind)   # the batch's transforms: like for like
         e = sp.forward(_c(B["pos"][lo:hi]), _c(B["q"][lo:hi]), _c(B["mu"][lo:hi]))["energy"].item()
         assert abs(e_b[f] - e) < 1e-6 * abs(e), f
         sp.close()
