@@ -132,6 +132,13 @@ const char* pme_status_string(int status);
  * raised since the previous pme_sync_status, clearing them. */
 int pme_sync_status(pme_plan_t plan, void* stream);
 
+/* Repeated calls. pme_forward, pme_backward and their pme_batch_* forms keep one CUDA graph
+ * per pass kind: the second call with the same n and the same pointers (host arguments count
+ * by the plan's staging buffers, so any host pointers qualify) records the pass once on a
+ * plan-owned stream, and that call and every later identical call launch the recorded graph
+ * on `stream`, with the same results. A different call runs directly; pme_plan_set_box drops
+ * the graphs, and calls made while the stage timers are on always run directly. */
+
 /* Forward: energy and derivatives of Eq. (1).
  *   energy     [1] float64: E                     (may be NULL)
  *   force      [n][3]: F_i = -dE/dr_i             (may be NULL)

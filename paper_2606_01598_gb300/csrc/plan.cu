@@ -181,7 +181,7 @@ struct Staging {
     size_t bytes;
   };
   std::vector<Pending> outs;
-  bool staged = false;   // some argument is a host pointer (the pass then runs without a graph)
+  bool staged = false;   // some argument is a host pointer
 
   Staging(pme_plan_t p_, cudaStream_t s_, int n_) : p(p_), s(s_), n(n_) {}
 
@@ -858,7 +858,9 @@ static void drop_graphs(pme_plan_t p) {
 
 // Run a pass, through a CUDA graph when the same call (key) comes again: the second identical
 // call records the pass on the plan's capture stream and launches the graph; later identical
-// calls only launch it. eligible = false (host-pointer staging, stage timers on) runs directly.
+// calls only launch it. The pass sees device pointers only (host arguments are copied to and
+// from the plan's staging buffers on the stream before and after it), so staged calls replay
+// too. eligible = false, or stage timers on, runs directly.
 template <class Run>
 static int run_pass(pme_plan_t p, int which, cudaStream_t s, const PassKey& key, bool eligible, Run&& run) {
   PassGraph& G = p->graphs[which];
@@ -1255,7 +1257,7 @@ int pme_forward(pme_plan_t p, void* stream, int n, const float* pos, const float
   const PassKey key = make_key({0ull, (unsigned long long)n, ptr_bits(in.pos), ptr_bits(in.q), ptr_bits(in.mu),
                                 ptr_bits(e_out), ptr_bits(f_out), ptr_bits(p_out), ptr_bits(fl_out),
                                 ptr_bits(fg_out)});
-  st = run_pass(p, 0, s, key, !sg.staged,
+  st = run_pass(p, 0, s, key, true,
                 [&](cudaStream_t cs) { return run_forward(p, cs, in, e_out, f_out, p_out, fl_out, fg_out); });
   if (st) return st;
   return sg.finish();
@@ -1317,7 +1319,7 @@ int pme_backward(pme_plan_t p, void* stream, int n, const float* pos, const floa
                                 ptr_bits(gE), ptr_bits(in.gforce), ptr_bits(in.gphi), ptr_bits(in.gfield),
                                 ptr_bits(o_pos), ptr_bits(o_q), ptr_bits(o_mu),
                                 (unsigned long long)(long long)p->fwd_n, (unsigned long long)p->fwd_lists});
-  st = run_pass(p, 1, s, key, !sg.staged,
+  st = run_pass(p, 1, s, key, true,
                 [&](cudaStream_t cs) { return run_backward(p, cs, in, gE, o_pos, o_q, o_mu); });
   if (st) return st;
   return sg.finish();
@@ -1351,7 +1353,7 @@ int pme_batch_forward(pme_plan_t p, void* stream, const float* pos, const float*
   const PassKey key = make_key({0ull, (unsigned long long)n, ptr_bits(in.pos), ptr_bits(in.q), ptr_bits(in.mu),
                                 ptr_bits(e_out), ptr_bits(f_out), ptr_bits(p_out), ptr_bits(fl_out),
                                 ptr_bits(fg_out)});
-  st = run_pass(p, 0, s, key, !sg.staged,
+  st = run_pass(p, 0, s, key, true,
                 [&](cudaStream_t cs) { return run_forward(p, cs, in, e_out, f_out, p_out, fl_out, fg_out); });
   if (st) return st;
   return sg.finish();
@@ -1411,7 +1413,7 @@ int pme_batch_backward(pme_plan_t p, void* stream, const float* pos, const float
                                 ptr_bits(gE), ptr_bits(in.gforce), ptr_bits(in.gphi), ptr_bits(in.gfield),
                                 ptr_bits(o_pos), ptr_bits(o_q), ptr_bits(o_mu),
                                 (unsigned long long)(long long)p->fwd_n, (unsigned long long)p->fwd_lists});
-  st = run_pass(p, 1, s, key, !sg.staged,
+  st = run_pass(p, 1, s, key, true,
                 [&](cudaStream_t cs) { return run_backward(p, cs, in, gE, o_pos, o_q, o_mu); });
   if (st) return st;
   return sg.finish();

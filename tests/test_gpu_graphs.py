@@ -89,3 +89,31 @@ def test_repeated_passes_replay_bitwise(gb):
     assert relrmse(F.cpu().numpy(), o["force"]) < TOL_F
     plan.close()
     fresh.close()
+
+
+def test_host_pointer_calls_replay_with_fresh_inputs(gb):
+    # pinned host arguments go through the plan's staging buffers, so repeated calls replay the
+    # recorded pass; each call must still see its own inputs and fill its own outputs
+    fr = W.molten_nacl(600, seed=91)
+    pos, q, mu = prepared(fr)
+    n = fr.n
+    plan = gb.Plan(fr.box, (30, 30, 30), 6, 0.30, 9.0, max_ions=1024)
+    hp = [torch.tensor(np.float32(x)).pin_memory() for x in (pos, q, mu)]
+    E = torch.empty(1, dtype=torch.float64).pin_memory()
+    F = torch.empty((n, 3)).pin_memory()
+    lib, h = plan.lib, plan.handle
+    s = torch.cuda.current_stream().cuda_stream
+    rng = np.random.default_rng(5)
+    for k in range(5):
+        # new positions in the same host buffer: a replay must not reuse the old ones
+        shifted = np.float32(pos + 0.05 * k * rng.normal(size=pos.shape))
+        hp[0].copy_(torch.from_numpy(shifted))
+        c0 = gb.launch_count()
+        assert lib.pme_forward(h, s, n, hp[0].data_ptr(), hp[1].data_ptr(), hp[2].data_ptr(), E.data_ptr(),
+                               F.data_ptr(), None, None, None) == 0
+        torch.cuda.synchronize()
+        assert gb.launch_count() > c0
+        ref = plan.forward(_c(shifted), _c(q), _c(mu))
+        assert E.item() == ref["energy"].item(), k
+        assert torch.equal(F, ref["force"].cpu()), k
+    plan.close()
