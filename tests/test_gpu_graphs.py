@@ -98,6 +98,7 @@ def test_host_pointer_calls_replay_with_fresh_inputs(gb):
     pos, q, mu = prepared(fr)
     n = fr.n
     plan = gb.Plan(fr.box, (30, 30, 30), 6, 0.30, 9.0, max_ions=1024)
+    ref_plan = gb.Plan(fr.box, (30, 30, 30), 6, 0.30, 9.0, max_ions=1024)   # direct device calls
     hp = [torch.tensor(np.float32(x)).pin_memory() for x in (pos, q, mu)]
     E = torch.empty(1, dtype=torch.float64).pin_memory()
     F = torch.empty((n, 3)).pin_memory()
@@ -113,7 +114,8 @@ def test_host_pointer_calls_replay_with_fresh_inputs(gb):
                                F.data_ptr(), None, None, None) == 0
         torch.cuda.synchronize()
         assert gb.launch_count() > c0
-        ref = plan.forward(_c(shifted), _c(q), _c(mu))
+        ref = ref_plan.forward(_c(shifted), _c(q), _c(mu))
         assert E.item() == ref["energy"].item(), k
         assert torch.equal(F, ref["force"].cpu()), k
     plan.close()
+    ref_plan.close()
