@@ -91,8 +91,8 @@ typedef struct {
                               every mesh axis of every frame is 2,3,5-smooth and at most 256
                               long and a mesh plane fits in one block's shared memory.
                               0 (default): automatic, the library's own for batched plans
-                              where they apply (one launch per pass for all frames), cuFFT
-                              otherwise. 1: always cuFFT. 2: always the library's own
+                              whose meshes have no axis above 64 points (one launch per pass
+                              for all frames; faster there on GB300), cuFFT otherwise. 1: always cuFFT. 2: always the library's own
                               (PME_ERR_UNSUPPORTED where they do not apply) */
   int reserved[4];
 } pme_opts;

@@ -362,10 +362,20 @@ struct FrameInput {
 };
 
 // Whether the options ask for the hand-written transforms: fft 2 always; fft 0 (automatic)
-// for batched plans, whose frames then share one launch per pass instead of a cuFFT plan per
-// mesh shape. The axis lengths and shared-memory sizes are checked by the caller.
-static bool conv_wanted(const pme_plan_s* p, bool single) {
-  return p->opts.fft == 2 || (p->opts.fft == 0 && !single);
+// for batched plans of small meshes (no axis above kConvAutoMaxAxis), whose frames then share
+// one launch per pass instead of a cuFFT plan per mesh shape. On GB300 these passes beat
+// cuFFT on batches of 16-48 point meshes and lose to it at 128^3, where the spectrum stays in
+// L2 and cuFFT's per-point cost is lower. The axis lengths and shared-memory sizes are
+// checked by the caller.
+constexpr int kConvAutoMaxAxis = 64;
+
+static bool conv_wanted(const pme_plan_s* p, bool single, const std::vector<FrameInput>& fin) {
+  if (p->opts.fft == 2) return true;
+  if (p->opts.fft != 0 || single) return false;
+  for (const FrameInput& f : fin)
+    for (int a = 0; a < 3; ++a)
+      if (f.mesh[a] > kConvAutoMaxAxis) return false;
+  return true;
 }
 
 // Build a plan over the given frames. single: one frame whose ion count is chosen per call.
@@ -388,7 +398,7 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
   // every axis of every frame is 2,3,5-smooth and short enough, and a plane (pass A / C) and
   // a pass-B tile fit in shared memory
   {
-    bool conv = conv_wanted(p, single);
+    bool conv = conv_wanted(p, single, fin);
     size_t cap = 0, smem_plane = 0, smem_x = 0, biggest = 0;
     for (int f = 0; f < F && conv; ++f) {
       for (int a = 0; a < 3; ++a) conv = conv && conv_axis_ok(fin[f].mesh[a]);
