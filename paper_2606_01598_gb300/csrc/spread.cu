@@ -8,12 +8,18 @@
 // The CTA (1) lists the few source bricks whose ions' stencils can reach it (ions are sorted by
 // the brick of their first stencil point), one thread per source brick; (2) walks their ions
 // 256 at a time and keeps, in order, those whose p^3 stencil overlaps the brick (ballot
-// compaction); (3) stages the kept ions' 1D spline weights and coefficients in shared memory;
-// (4) builds separable coverage bitmasks -- bit l of xmask[X] is set when staged ion l's
-// stencil covers plane X, likewise for Y and for each z-segment -- so that each thread visits
-// only the ions whose stencil touches its segment (xmask[X] & ymask[Y] & zmask[seg]), in
-// staged order; (5) writes its points once. Every sum runs in a fixed order, so the result is
-// bitwise reproducible.
+// compaction); (3) stages per kept ion, two threads to an ion, what a visit needs in shared
+// memory: for each brick column X the coefficient combinations times the x weights (the
+// density at a point is a sum over the weight-derivative orders of x, y and z, and the x and
+// coefficient factors of every term are folded per column), for each row Y the y weights,
+// and for each z-segment the aligned window of the z weights its 8 points see (zeros where
+// the stencil does not reach); (4) builds separable coverage bitmasks -- bit l of xmask[X] is
+// set when staged ion l's stencil covers plane X, likewise for Y and for each z-segment -- so
+// that each thread visits only the ions whose stencil touches its segment
+// (xmask[X] & ymask[Y] & zmask[seg]), in staged order; a visit is two table reads, a few
+// multiply-adds for the y combination, vector window reads and the 8-point updates; (5)
+// writes its points once. Every sum runs in a fixed order, so the result is bitwise
+// reproducible.
 //
 // Tangent mode (backward pass) spreads, in the same sweep, the tangent density
 //   d rho = sum_i [dq_i + (dmu_i + q_i dr_i) . grad + (mu_i . grad)(dr_i . grad)] W(x_i - m)
@@ -47,28 +53,32 @@ struct SpreadArgs {
   const int* keep_rho;
 };
 
-// z weight rows are padded with ZS - 1 zeros on both sides, so a segment reads its ZS weights
-// from one window without range tests
-template <int P>
-__host__ __device__ constexpr int zrow() {
-  return P + 2 * (ZS - 1);
-}
-
-// Per-ion strides in shared memory (floats), odd so that threads reading the same entry of
-// different ions fall in different banks.
-template <int P, bool TAN>
-__host__ __device__ constexpr int wstride() {
-  return ((TAN ? 3 : 2) * (2 * P + zrow<P>())) | 1;
-}
-
+// Shared-memory record of one staged ion (floats), DW = weight-derivative orders kept:
+//   [ZOFF, ...)  z windows: for segment g and order d, 8 floats at ZOFF + (g DW + d) 8
+//   [XOFF, ...)  per brick column X, NXV floats at XOFF + X NXV:
+//                forward: (u, v, b, 0), A = u wy0 + v wy1 and B = b wy0 being the
+//                coefficients of W_z and W'_z in rho;
+//                tangent: (p0, p1, p2, q0, q1, r0, u, v, b), the coefficients of W_z, W'_z,
+//                W''_z in d rho being A0 = p0 wy0 + p1 wy1 + p2 wy2, A1 = q0 wy0 + q1 wy1,
+//                A2 = r0 wy0 (and A, B as above for rho)
+//   [YOFF, ...)  per brick row Y, the y weights wy0, wy1 (and wy2), NYV floats
+// The stride is a multiple of 4 with an odd quotient, so 16-byte reads of different ions
+// spread over the banks.
 template <bool TAN>
-__host__ __device__ constexpr int cstride() {
-  return TAN ? 11 : 5;
-}
+struct Rec {
+  static constexpr int DW = TAN ? 3 : 2;
+  static constexpr int ZOFF = 0;
+  static constexpr int XOFF = NSEG * DW * ZS;
+  static constexpr int NXV = TAN ? 9 : 4;
+  static constexpr int YOFF = XOFF + BX * NXV;
+  static constexpr int NYV = TAN ? 3 : 2;
+  static constexpr int LEN = YOFF + BY * NYV;
+  static constexpr int STR = ((LEN + 3) / 4) % 2 == 0 ? (LEN + 3) / 4 * 4 + 4 : (LEN + 3) / 4 * 4;
+};
 
 template <int P, bool TAN>
 constexpr int spread_smem_bytes() {
-  return CAP * (wstride<P, TAN>() + cstride<TAN>()) * 4 + SL * (4 + 8);
+  return CAP * Rec<TAN>::STR * 4 + SL * (4 + 8);
 }
 
 // distance from a to b going up the periodic axis of length n (a, b in [0, n))
@@ -79,17 +89,13 @@ __device__ __forceinline__ int up_dist(int a, int b, int n) {
 
 template <int P, bool TAN, bool BATCH>
 __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
-  constexpr int DW = TAN ? 3 : 2;                 // weight derivative orders kept
-  constexpr int ZP = zrow<P>();
-  constexpr int WZ = 2 * DW * P;                  // start of the padded z rows
-  constexpr int WSTRIDE = wstride<P, TAN>();      // floats of weights per staged ion
-  constexpr int NC = cstride<TAN>();              // coefficients per staged ion (4 or 11 used)
+  using RC = Rec<TAN>;
+  constexpr int DW = RC::DW;                      // weight derivative orders kept
 
   extern __shared__ __align__(16) float dyn[];
-  float* sw = dyn;                                        // [CAP][WSTRIDE]
-  float* sc = sw + CAP * WSTRIDE;                         // [CAP][NC]
-  int2* srel = reinterpret_cast<int2*>(sc + CAP * NC);    // [SL] stencil index of the brick
-                                                          // origin: x | y << 16, z
+  float* sw = dyn;                                        // [CAP][RC::STR] staged records
+  int2* srel = reinterpret_cast<int2*>(sw + CAP * RC::STR);   // [SL] stencil index of the brick
+                                                              // origin: x | y << 16, z
   int* slist = reinterpret_cast<int*>(srel + SL);         // [SL] listed ions
   __shared__ unsigned xmask[BX][NW], ymask[BY][NW], zmask[NSEG][NW];
   __shared__ int cand_lo[kMaxCand];
@@ -196,51 +202,94 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
 
     for (int base = 0; base < cnt; base += CAP) {
       const int nst = min(CAP, cnt - base);
-      // ---- (3) stage weights and coefficients ---------------------------------------
-      if (tid < nst) {
+      // ---- (3) stage: threads [0, CAP) the x / y tables, [CAP, 2 CAP) the z windows ----
+      if (tid < CAP && tid < nst) {
         const int l = base + tid;
         const int src = slist[l];
+        const int2 rl = srel[l];
+        const int rx = rl.x & 0xffff, ry = rl.x >> 16;
         const float4 fq = a.mr.fq[src];
         const float4 dm = a.mr.dm[src];
+        float* rec = sw + tid * RC::STR;
         float w[DW][P];
-        float* dst = sw + tid * WSTRIDE;
         spline_weights<P, DW - 1>(fq.x, w);
 #pragma unroll
-        for (int d = 0; d < DW; ++d)
-#pragma unroll
-          for (int j = 0; j < P; ++j) dst[(0 * DW + d) * P + j] = w[d][j];
-        spline_weights<P, DW - 1>(fq.y, w);
-#pragma unroll
-        for (int d = 0; d < DW; ++d)
-#pragma unroll
-          for (int j = 0; j < P; ++j) dst[(1 * DW + d) * P + j] = w[d][j];
-        spline_weights<P, DW - 1>(fq.z, w);
-#pragma unroll
-        for (int d = 0; d < DW; ++d) {
-          float* row = dst + WZ + d * ZP;
-#pragma unroll
-          for (int j = 0; j < ZS - 1; ++j) {
-            row[j] = 0.f;
-            row[ZS - 1 + P + j] = 0.f;
-          }
-#pragma unroll
-          for (int j = 0; j < P; ++j) row[ZS - 1 + j] = w[d][j];
-        }
-        float* c = sc + tid * NC;
-        c[0] = fq.w;
-        c[1] = dm.x;
-        c[2] = dm.y;
-        c[3] = dm.z;
+        for (int k = 0; k < BX * RC::NXV; ++k) rec[RC::XOFF + k] = 0.f;
+        const float q = fq.w, mx = dm.x, my = dm.y, mz = dm.z;
+        float c4 = 0.f, c5 = 0.f, c6 = 0.f, c7 = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
         if (TAN) {
           const float4 tq = a.mr.tq[src];
           const float4 tt = a.mr.tt[src];
-          c[4] = tq.x;
-          c[5] = tq.y;
-          c[6] = tq.z;
-          c[7] = tq.w;
-          c[8] = tt.x;
-          c[9] = tt.y;
-          c[10] = tt.z;
+          c4 = tq.x;
+          c5 = tq.y;
+          c6 = tq.z;
+          c7 = tq.w;
+          tx = tt.x;
+          ty = tt.y;
+          tz = tt.z;
+        }
+        // stencil index j sits in brick column (j - rx) mod Nx
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          int X = j - rx;
+          if (X < 0) X += Nx;
+          if (X < BX) {
+            const float w0 = w[0][j], w1 = w[1][j];
+            float* e = rec + RC::XOFF + X * RC::NXV;
+            if (TAN) {
+              const float w2 = w[DW - 1][j];
+              e[0] = c4 * w0 + c5 * w1 + mx * tx * w2;
+              e[1] = c6 * w0 + (mx * ty + my * tx) * w1;
+              e[2] = my * ty * w0;
+              e[3] = c7 * w0 + (mx * tz + mz * tx) * w1;
+              e[4] = (my * tz + mz * ty) * w0;
+              e[5] = mz * tz * w0;
+              e[6] = q * w0 + mx * w1;
+              e[7] = my * w0;
+              e[8] = mz * w0;
+            } else {
+              *reinterpret_cast<float4*>(e) = make_float4(q * w0 + mx * w1, my * w0, mz * w0, 0.f);
+            }
+          }
+        }
+        spline_weights<P, DW - 1>(fq.y, w);
+#pragma unroll
+        for (int k = 0; k < BY * RC::NYV; ++k) rec[RC::YOFF + k] = 0.f;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          int Yr = j - ry;
+          if (Yr < 0) Yr += Ny;
+          if (Yr < BY) {
+            float* e = rec + RC::YOFF + Yr * RC::NYV;
+#pragma unroll
+            for (int d = 0; d < DW; ++d) e[d] = w[d][j];
+          }
+        }
+      } else if (tid >= CAP && tid - CAP < nst) {
+        const int k = tid - CAP;
+        const int l = base + k;
+        const int rz = srel[l].y;
+        const float4 fq = a.mr.fq[slist[l]];
+        float* rec = sw + k * RC::STR;
+        float w[DW][P];
+        spline_weights<P, DW - 1>(fq.z, w);
+#pragma unroll
+        for (int u = 0; u < NSEG * DW * ZS; u += 4)
+          *reinterpret_cast<float4*>(rec + RC::ZOFF + u) = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int g = 0; g < NSEG; ++g) {
+          // stencil index of the segment's first point; stencil index j lands on point
+          // (j - j0) mod Nz of the segment
+          const int j0 = (rz + g * ZS) % Nz;
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            int z = j - j0;
+            if (z < 0) z += Nz;
+            if (z < ZS) {
+#pragma unroll
+              for (int d = 0; d < DW; ++d) rec[RC::ZOFF + (g * DW + d) * ZS + z] = w[d][j];
+            }
+          }
         }
       }
       // ---- (4) coverage masks: warp w builds word w -----------------------------------
@@ -277,62 +326,41 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
       __syncthreads();
       // ---- accumulate this thread's points over the ions that touch them --------------
       const int nw = (nst + 31) >> 5;
-      const bool padded = Nz >= P + ZS - 1;   // no stencil wraps inside one segment
+      const int xo = RC::XOFF + X * RC::NXV, yo = RC::YOFF + Y * RC::NYV, zo = RC::ZOFF + seg * DW * ZS;
       for (int w = 0; w < nw; ++w) {
         unsigned bits = xmask[X][w] & ymask[Y][w] & zmask[seg][w];
         while (bits) {
           const int t = w * 32 + __ffs(bits) - 1;
           bits &= bits - 1;
-          const int2 rl = srel[base + t];
-          int dx = (rl.x & 0xffff) + X;
-          if (dx >= Nx) dx -= Nx;
-          int dy = (rl.x >> 16) + Y;
-          if (dy >= Ny) dy -= Ny;
-          int dz = rl.y + seg * ZS;   // stencil index of z = zs0
-          if (dz >= Nz) dz -= Nz;
-          const float* wt = sw + t * WSTRIDE;
-          const float* c = sc + t * NC;
-          const float wx = wt[(0 * DW + 0) * P + dx], wx1 = wt[(0 * DW + 1) * P + dx];
-          const float wy = wt[(1 * DW + 0) * P + dy], wy1 = wt[(1 * DW + 1) * P + dy];
-          const float wxy = wx * wy;
-          // rho: coefficient of W_z and of W'_z
-          const float A = with_rho ? c[0] * wxy + c[1] * wx1 * wy + c[2] * wx * wy1 : 0.f;
-          const float B = with_rho ? c[3] * wxy : 0.f;
-          float A0 = 0.f, A1 = 0.f, A2 = 0.f;
+          const float* rec = sw + t * RC::STR;
+          const float4* wz = reinterpret_cast<const float4*>(rec + zo);
           if (TAN) {
-            const float wx2 = wt[(0 * DW + 2) * P + dx], wy2 = wt[(1 * DW + 2) * P + dy];
-            const float mx = c[1], my = c[2], mz = c[3];
-            const float tx = c[8], ty = c[9], tz = c[10];
-            A0 = c[4] * wxy + c[5] * wx1 * wy + c[6] * wx * wy1 + mx * tx * wx2 * wy +
-                 my * ty * wx * wy2 + (mx * ty + my * tx) * wx1 * wy1;
-            A1 = c[7] * wxy + (mx * tz + mz * tx) * wx1 * wy + (my * tz + mz * ty) * wx * wy1;
-            A2 = mz * tz * wxy;
-          }
-          const float* wz = wt + WZ + (ZS - 1);   // wz[j], j in [-(ZS-1), P + ZS - 1)
-          if (padded) {
-            // the stencil meets this segment either from below (dz < P) or from above
-            // (dz > Nz - ZS, i.e. index dz - Nz of the window)
-            const float* wzs = wz + (dz < P ? dz : dz - Nz);
-            if (!TAN || with_rho) {
+            const float* xe = rec + xo;
+            const float* ye = rec + yo;
+            const float wy0 = ye[0], wy1 = ye[1], wy2 = ye[2];
+            const float A0 = xe[0] * wy0 + xe[1] * wy1 + xe[2] * wy2;
+            const float A1 = xe[3] * wy0 + xe[4] * wy1;
+            const float A2 = xe[5] * wy0;
+            const float4 z0a = wz[0], z0b = wz[1], z1a = wz[2], z1b = wz[3], z2a = wz[4], z2b = wz[5];
+            const float W0[ZS] = {z0a.x, z0a.y, z0a.z, z0a.w, z0b.x, z0b.y, z0b.z, z0b.w};
+            const float W1[ZS] = {z1a.x, z1a.y, z1a.z, z1a.w, z1b.x, z1b.y, z1b.z, z1b.w};
+            const float W2[ZS] = {z2a.x, z2a.y, z2a.z, z2a.w, z2b.x, z2b.y, z2b.z, z2b.w};
 #pragma unroll
-              for (int z = 0; z < ZS; ++z) {
-                acc[z] += A * wzs[z] + B * wzs[ZP + z];
-                if (TAN) dacc[z] += A0 * wzs[z] + A1 * wzs[ZP + z] + A2 * wzs[2 * ZP + z];
-              }
-            } else {
+            for (int z = 0; z < ZS; ++z) dacc[z] += A0 * W0[z] + A1 * W1[z] + A2 * W2[z];
+            if (with_rho) {
+              const float A = xe[6] * wy0 + xe[7] * wy1, B = xe[8] * wy0;
 #pragma unroll
-              for (int z = 0; z < ZS; ++z) dacc[z] += A0 * wzs[z] + A1 * wzs[ZP + z] + A2 * wzs[2 * ZP + z];
+              for (int z = 0; z < ZS; ++z) acc[z] += A * W0[z] + B * W1[z];
             }
           } else {
+            const float4 xe = *reinterpret_cast<const float4*>(rec + xo);
+            const float2 ye = *reinterpret_cast<const float2*>(rec + yo);
+            const float A = xe.x * ye.x + xe.y * ye.y, B = xe.z * ye.x;
+            const float4 z0a = wz[0], z0b = wz[1], z1a = wz[2], z1b = wz[3];
+            const float W0[ZS] = {z0a.x, z0a.y, z0a.z, z0a.w, z0b.x, z0b.y, z0b.z, z0b.w};
+            const float W1[ZS] = {z1a.x, z1a.y, z1a.z, z1a.w, z1b.x, z1b.y, z1b.z, z1b.w};
 #pragma unroll
-            for (int z = 0; z < ZS; ++z) {
-              int j = dz + z;
-              if (j >= Nz) j -= Nz;
-              if (j < P) {
-                acc[z] += A * wz[j] + B * wz[ZP + j];
-                if (TAN) dacc[z] += A0 * wz[j] + A1 * wz[ZP + j] + A2 * wz[2 * ZP + j];
-              }
-            }
+            for (int z = 0; z < ZS; ++z) acc[z] += A * W0[z] + B * W1[z];
           }
         }
       }
