@@ -332,60 +332,38 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
       const int xo = RC::XOFF + X * RC::NXV, yo = RC::YOFF + Y * RC::NYV, zo = RC::ZOFF + seg * RC::ZSEG;
       for (int w = 0; w < nw; ++w) {
         unsigned bits = xmask[X][w] & ymask[Y][w] & zmask[seg][w];
-        // two visits per trip, so their shared-memory reads overlap; a missing second visit
-        // repeats the first with zero coefficients
         while (bits) {
-          const int t1 = w * 32 + __ffs(bits) - 1;
+          const int t = w * 32 + __ffs(bits) - 1;
           bits &= bits - 1;
-          const bool two = bits != 0;
-          const int t2 = two ? w * 32 + __ffs(bits) - 1 : t1;
-          if (two) bits &= bits - 1;
-          const float keep = two ? 1.f : 0.f;
-          const float* r1 = sw + t1 * RC::STR;
-          const float* r2 = sw + t2 * RC::STR;
-          const float4* z1 = reinterpret_cast<const float4*>(r1 + zo);
-          const float4* z2 = reinterpret_cast<const float4*>(r2 + zo);
+          const float* rec = sw + t * RC::STR;
+          const float4* wz = reinterpret_cast<const float4*>(rec + zo);
           if (TAN) {
-            const float* x1 = r1 + xo;
-            const float* x2 = r2 + xo;
-            const float* y1 = r1 + yo;
-            const float* y2 = r2 + yo;
-            const float a0 = y1[0], a1 = y1[1], a2 = y1[2];
-            const float b0 = keep * y2[0], b1 = keep * y2[1], b2 = keep * y2[2];
-            const float4 p0 = z1[0], p1 = z1[1], p2 = z1[2], p3 = z1[3], p4 = z1[4], p5 = z1[5];
-            const float4 q0 = z2[0], q1 = z2[1], q2 = z2[2], q3 = z2[3], q4 = z2[4], q5 = z2[5];
-            const float A0 = x1[0] * a0 + x1[1] * a1 + x1[2] * a2, A1 = x1[3] * a0 + x1[4] * a1, A2 = x1[5] * a0;
-            const float B0 = x2[0] * b0 + x2[1] * b1 + x2[2] * b2, B1 = x2[3] * b0 + x2[4] * b1, B2 = x2[5] * b0;
-            const float U0[ZS] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
-            const float U1[ZS] = {p2.x, p2.y, p2.z, p2.w, p3.x, p3.y, p3.z, p3.w};
-            const float U2[ZS] = {p4.x, p4.y, p4.z, p4.w, p5.x, p5.y, p5.z, p5.w};
-            const float V0[ZS] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-            const float V1[ZS] = {q2.x, q2.y, q2.z, q2.w, q3.x, q3.y, q3.z, q3.w};
-            const float V2[ZS] = {q4.x, q4.y, q4.z, q4.w, q5.x, q5.y, q5.z, q5.w};
+            const float* xe = rec + xo;
+            const float* ye = rec + yo;
+            const float wy0 = ye[0], wy1 = ye[1], wy2 = ye[2];
+            const float A0 = xe[0] * wy0 + xe[1] * wy1 + xe[2] * wy2;
+            const float A1 = xe[3] * wy0 + xe[4] * wy1;
+            const float A2 = xe[5] * wy0;
+            const float4 z0a = wz[0], z0b = wz[1], z1a = wz[2], z1b = wz[3], z2a = wz[4], z2b = wz[5];
+            const float W0[ZS] = {z0a.x, z0a.y, z0a.z, z0a.w, z0b.x, z0b.y, z0b.z, z0b.w};
+            const float W1[ZS] = {z1a.x, z1a.y, z1a.z, z1a.w, z1b.x, z1b.y, z1b.z, z1b.w};
+            const float W2[ZS] = {z2a.x, z2a.y, z2a.z, z2a.w, z2b.x, z2b.y, z2b.z, z2b.w};
 #pragma unroll
-            for (int z = 0; z < ZS; ++z)
-              dacc[z] += A0 * U0[z] + A1 * U1[z] + A2 * U2[z] + (B0 * V0[z] + B1 * V1[z] + B2 * V2[z]);
+            for (int z = 0; z < ZS; ++z) dacc[z] += A0 * W0[z] + A1 * W1[z] + A2 * W2[z];
             if (with_rho) {
-              const float A = x1[6] * a0 + x1[7] * a1, B = x1[8] * a0;
-              const float C = x2[6] * b0 + x2[7] * b1, D = x2[8] * b0;
+              const float A = xe[6] * wy0 + xe[7] * wy1, B = xe[8] * wy0;
 #pragma unroll
-              for (int z = 0; z < ZS; ++z) acc[z] += A * U0[z] + B * U1[z] + (C * V0[z] + D * V1[z]);
+              for (int z = 0; z < ZS; ++z) acc[z] += A * W0[z] + B * W1[z];
             }
           } else {
-            const float4 x1 = *reinterpret_cast<const float4*>(r1 + xo);
-            const float4 x2 = *reinterpret_cast<const float4*>(r2 + xo);
-            const float2 y1 = *reinterpret_cast<const float2*>(r1 + yo);
-            const float2 y2 = *reinterpret_cast<const float2*>(r2 + yo);
-            const float4 p0 = z1[0], p1 = z1[1], p2 = z1[2], p3 = z1[3];
-            const float4 q0 = z2[0], q1 = z2[1], q2 = z2[2], q3 = z2[3];
-            const float A = x1.x * y1.x + x1.y * y1.y, B = x1.z * y1.x;
-            const float C = keep * (x2.x * y2.x + x2.y * y2.y), D = keep * (x2.z * y2.x);
-            const float U0[ZS] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
-            const float U1[ZS] = {p2.x, p2.y, p2.z, p2.w, p3.x, p3.y, p3.z, p3.w};
-            const float V0[ZS] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-            const float V1[ZS] = {q2.x, q2.y, q2.z, q2.w, q3.x, q3.y, q3.z, q3.w};
+            const float4 xe = *reinterpret_cast<const float4*>(rec + xo);
+            const float2 ye = *reinterpret_cast<const float2*>(rec + yo);
+            const float A = xe.x * ye.x + xe.y * ye.y, B = xe.z * ye.x;
+            const float4 z0a = wz[0], z0b = wz[1], z1a = wz[2], z1b = wz[3];
+            const float W0[ZS] = {z0a.x, z0a.y, z0a.z, z0a.w, z0b.x, z0b.y, z0b.z, z0b.w};
+            const float W1[ZS] = {z1a.x, z1a.y, z1a.z, z1a.w, z1b.x, z1b.y, z1b.z, z1b.w};
 #pragma unroll
-            for (int z = 0; z < ZS; ++z) acc[z] += A * U0[z] + B * U1[z] + (C * V0[z] + D * V1[z]);
+            for (int z = 0; z < ZS; ++z) acc[z] += A * W0[z] + B * W1[z];
           }
         }
       }
