@@ -250,6 +250,7 @@ struct pme_plan_s {
   int* in_flags = nullptr;     // [2]: in_diff, cache_bad (see launch_input_check)
   int* in_diff = nullptr;
   int* cache_bad = nullptr;
+  bool counts_clean = false;   // the sort's count arrays are zero (each scan re-zeroes them)
   int fwd_n = -1;              // ions of that forward (-1: nothing saved / no longer valid)
   // virial partial sums
   double* vpart = nullptr;     // [6 * influence blocks] k-space sums S_ab

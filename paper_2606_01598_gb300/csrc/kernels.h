@@ -22,10 +22,11 @@ struct IonInputs {
 // reuse (nullable): when *reuse == 0 the plan's sorted order and primal records are those of
 // these inputs (a forward on them) and are kept; only charge sums and tangent records are
 // formed. A sort without reuse clears the plan's saved-forward state.
+// save (nullable): the binning pass also copies the inputs there (positions at 0, charges at
+// 3 max_ions, dipoles at 4 max_ions) for a later backward's comparison.
+// The count arrays must be zero unless p->counts_clean is false (then they are cleared here).
 int launch_sort(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent, bool need_mesh,
-                bool need_pair, const int* reuse);
-// Save the forward's inputs (positions, charges, dipoles) for a later backward.
-int save_inputs(pme_plan_t p, cudaStream_t s, const IonInputs& in);
+                bool need_pair, const int* reuse, float* save = nullptr);
 // *in_diff = 1 unless the inputs equal the saved ones bit for bit; *cache_bad = 1 when
 // *in_diff or (with_lists) a recorded pair list overflowed; both 0 otherwise.
 int launch_input_check(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool with_lists);

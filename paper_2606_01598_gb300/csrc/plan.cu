@@ -312,11 +312,12 @@ static int dalloc(pme_plan_t p, T** ptr, size_t count) {
 // them 16 bytes at a time).
 static size_t scan_entries(int n) { return (size_t(n) + 1 + 3) & ~size_t(3); }
 
+// The cell counts start zero (each scan re-zeroes them).
 static int alloc_cells(pme_plan_t p) {
   int st;
   if ((st = dalloc(p, &p->sb.count_c, scan_entries(p->total_cells)))) return st;
   if ((st = dalloc(p, &p->sb.start_c, scan_entries(p->total_cells)))) return st;
-  return PME_OK;
+  return check_cuda(p, cudaMemset(p->sb.count_c, 0, sizeof(int) * scan_entries(p->total_cells)), "cudaMemset");
 }
 
 // (Re)build the explicit-Ewald k-vector tables for the current box (single-frame plans).
@@ -620,6 +621,9 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
   A(&p->pvir, 9 * ni);
   A(&p->vitem, size_t(9) * p->total_items);
   if (st == PME_OK) st = alloc_cells(p);
+  if (st == PME_OK)
+    st = check_cuda(p, cudaMemset(p->sb.count_b, 0, sizeof(int) * scan_entries(p->total_bricks)), "cudaMemset");
+  p->counts_clean = st == PME_OK;
   // pair lists for backward passes on the forward's positions: room for 1.5x the mean number
   // of partners inside rcut (density from the plan's largest n / V) + 64, when that fits in
   // 1 GiB; an ion with more partners marks the lists invalid and the backward recomputes
@@ -936,7 +940,8 @@ static int run_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, double
   if (p->opts.recip_method == 1) return forward_ewald(p, s, in, pair, e_out, f_out, p_out, fl_out, fg_out);
   int st, t;
   t = prof_begin(p, 0, s);
-  if ((st = launch_sort(p, s, in, false, true, pair, nullptr))) return st;   // clears fwd_n
+  // the binning pass also saves the inputs for a backward on the same ones
+  if ((st = launch_sort(p, s, in, false, true, pair, nullptr, n > 0 ? p->in_saved : nullptr))) return st;
   prof_end(p, t, s);
   // the pair term runs on the plan's side stream, concurrently with the mesh stages: a list
   // pass writes each ion's hits (kept for a backward on the same positions), then the
@@ -960,8 +965,6 @@ static int run_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, double
     }
     prof_end(p, t, ps);
   }
-  // the inputs, with the sort and the lists made from them, serve a backward on the same inputs
-  if (n > 0 && (st = save_inputs(p, s, in))) return st;
   t = prof_begin(p, 1, s);
   if ((st = launch_spread(p, s, false, p->rho))) return st;
   prof_end(p, t, s);

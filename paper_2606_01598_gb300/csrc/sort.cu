@@ -27,8 +27,9 @@ constexpr int kRankMaxSegment = 2048;   // longer segments keep arrival order
 // Exclusive scan of one count array by one block of 1024 threads; start[n] = total. Each
 // thread owns a chunk of a multiple of 4 entries and moves it with 16-byte loads and stores,
 // so both arrays are allocated padded to a multiple of 4 entries past n + 1 (entries past n
-// are read but ignored, and written with scratch values before start[n] is set).
-__device__ void block_exclusive_scan(const int* count, int* start, int n) {
+// are read but ignored, and written with scratch values before start[n] is set). The counts
+// are dead once scanned: the scan leaves them zero for the next sort.
+__device__ void block_exclusive_scan(int* count, int* start, int n) {
   __shared__ int warp_tot[32];
   const int T = blockDim.x;
   const int chunk = ((n + T - 1) / T + 3) & ~3;
@@ -69,6 +70,7 @@ __device__ void block_exclusive_scan(const int* count, int* start, int n) {
     o.w = o.z + (k + 2 < hi ? c.z : 0);
     run = o.w + (k + 3 < hi ? c.w : 0);
     *reinterpret_cast<int4*>(start + k) = o;
+    *reinterpret_cast<int4*>(count + k) = make_int4(0, 0, 0, 0);
   }
   __syncthreads();
   if (threadIdx.x == 0) start[n] = warp_tot[31];
@@ -81,7 +83,7 @@ __device__ void block_exclusive_scan(const int* count, int* start, int n) {
 template <bool BATCH>
 __global__ void __launch_bounds__(kSortThreads)
 k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int tangent, int* flags,
-      int nbricks, int ncells, const int* reuse) {
+      int nbricks, int ncells, const int* reuse, float* save, int ld) {
   static_assert(kRedItem == kSortThreads, "one ion per thread");
   const int item = blockIdx.x;
   const int f = BATCH ? maps.item_frame[item] : 0;
@@ -101,6 +103,15 @@ k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int tangent, 
     const Geometry& g = F.g;
     const float rx = in.pos[3 * i], ry = in.pos[3 * i + 1], rz = in.pos[3 * i + 2];
     const float qi = in.q ? in.q[i] : 0.f;
+    if (save) {
+      // the forward's inputs, bit for bit, for the comparison a later backward makes
+      save[3 * i] = rx;
+      save[3 * i + 1] = ry;
+      save[3 * i + 2] = rz;
+      save[3 * ld + i] = qi;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) save[4 * ld + 3 * i + a] = in.mu ? in.mu[3 * i + a] : 0.f;
+    }
     bool ok = isfinite(rx) && isfinite(ry) && isfinite(rz) && isfinite(qi);
     if (in.mu) ok = ok && isfinite(in.mu[3 * i]) && isfinite(in.mu[3 * i + 1]) && isfinite(in.mu[3 * i + 2]);
     if (!ok) atomicOr(flags, kFlagNonFinite);
@@ -357,7 +368,7 @@ k_input_check(int n, IonInputs in, const float* saved, int ld, const int* list_c
 
 template <bool BATCH>
 int launch_sort_t(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent, bool need_mesh,
-                  bool need_pair, const int* reuse) {
+                  bool need_pair, const int* reuse, float* save) {
   const int n = in.n;
   const int nblk = (n + kSortThreads - 1) / kSortThreads;
   FrameDesc one = p->frames_h[0];
@@ -366,21 +377,31 @@ int launch_sort_t(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangen
     one.item_off = 0;
     one.nitems = std::max(1, (n + kRedItem - 1) / kRedItem);
   }
-  int st = check_cuda(p, cudaMemsetAsync(p->sb.count_b, 0, sizeof(int) * (p->total_bricks + 1), s),
-                      "memset brick counts");
-  if (st) return st;
-  st = check_cuda(p, cudaMemsetAsync(p->sb.count_c, 0, sizeof(int) * (p->total_cells + 1), s),
-                  "memset cell counts");
-  if (st) return st;
+  int st = PME_OK;
+  if (!p->counts_clean) {
+    st = check_cuda(p, cudaMemsetAsync(p->sb.count_b, 0, sizeof(int) * (p->total_bricks + 1), s),
+                    "memset brick counts");
+    if (st) return st;
+    st = check_cuda(p, cudaMemsetAsync(p->sb.count_c, 0, sizeof(int) * (p->total_cells + 1), s),
+                    "memset cell counts");
+    if (st) return st;
+  }
   {
     const int items = BATCH ? p->total_items : one.nitems;
     k_bin<BATCH><<<items, kSortThreads, 0, s>>>(one, p->maps, in, p->sb, tangent ? 1 : 0, p->flags,
-                                                p->total_bricks, p->total_cells, reuse);
+                                                p->total_bricks, p->total_cells, reuse, save,
+                                                p->max_ions);
     count_launch();
-    if ((st = check_launch(p, "k_bin"))) return st;
+    if ((st = check_launch(p, "k_bin"))) {
+      p->counts_clean = false;
+      return st;
+    }
     k_scan<<<2, 1024, 0, s>>>(p->sb, p->total_bricks, p->total_cells, reuse);
     count_launch();
-    if ((st = check_launch(p, "k_scan"))) return st;
+    if ((st = check_launch(p, "k_scan"))) {
+      p->counts_clean = false;
+      return st;
+    }
   }
   if (nblk > 0) {
     k_scatter<<<nblk, kSortThreads, 0, s>>>(n, p->sb, need_mesh ? 1 : 0, need_pair ? 1 : 0, reuse);
@@ -398,20 +419,6 @@ int launch_sort_t(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangen
 
 }  // namespace
 
-int save_inputs(pme_plan_t p, cudaStream_t s, const IonInputs& in) {
-  const size_t n = size_t(in.n), ld = size_t(p->max_ions);
-  float* sv = p->in_saved;
-  int st = check_cuda(p, cudaMemcpyAsync(sv, in.pos, sizeof(float) * 3 * n, cudaMemcpyDeviceToDevice, s),
-                      "save positions");
-  if (!st) st = in.q ? check_cuda(p, cudaMemcpyAsync(sv + 3 * ld, in.q, sizeof(float) * n,
-                                                     cudaMemcpyDeviceToDevice, s), "save charges")
-                     : check_cuda(p, cudaMemsetAsync(sv + 3 * ld, 0, sizeof(float) * n, s), "save charges");
-  if (!st) st = in.mu ? check_cuda(p, cudaMemcpyAsync(sv + 4 * ld, in.mu, sizeof(float) * 3 * n,
-                                                      cudaMemcpyDeviceToDevice, s), "save dipoles")
-                      : check_cuda(p, cudaMemsetAsync(sv + 4 * ld, 0, sizeof(float) * 3 * n, s), "save dipoles");
-  return st;
-}
-
 int launch_input_check(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool with_lists) {
   int st = check_cuda(p, cudaMemsetAsync(p->in_flags, 0, 2 * sizeof(int), s), "memset");
   if (st || in.n == 0) return st;
@@ -423,10 +430,10 @@ int launch_input_check(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool w
 }
 
 int launch_sort(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent, bool need_mesh,
-                bool need_pair, const int* reuse) {
+                bool need_pair, const int* reuse, float* save) {
   if (!reuse) p->fwd_n = -1;   // the sorted records no longer belong to the saved inputs
-  return p->batch ? launch_sort_t<true>(p, s, in, tangent, need_mesh, need_pair, reuse)
-                  : launch_sort_t<false>(p, s, in, tangent, need_mesh, need_pair, reuse);
+  return p->batch ? launch_sort_t<true>(p, s, in, tangent, need_mesh, need_pair, reuse, save)
+                  : launch_sort_t<false>(p, s, in, tangent, need_mesh, need_pair, reuse, save);
 }
 
 }  // namespace gbpme
