@@ -145,26 +145,16 @@ __global__ void __launch_bounds__(kCombThreads) k_combine_forward(CombineArgs a)
   const double e_item = block_sum_d(e_i);
   if (threadIdx.x == 0) a.eitem[item] = e_item;
   if (!last_item_done(a.ecount + f, F.nitems)) return;
-  double rp = 0.0, ep = 0.0;
-  if (a.recip_kind)
-    for (int k = threadIdx.x; k < F.infl_nblk; k += blockDim.x) rp += a.recip_parts[F.infl_blk_off + k];
-  for (int k = threadIdx.x; k < F.nitems; k += blockDim.x) ep += __ldcg(a.eitem + F.item_off + k);
+  double rp = a.recip_kind ? strided_sum_d(a.recip_parts + F.infl_blk_off, F.infl_nblk) : 0.0;
+  double ep = strided_sum_d(a.eitem + F.item_off, F.nitems);
   rp = block_sum_d(rp);
   ep = block_sum_d(ep);
   double W[9], S[6];
   if (a.virial_out) {
 #pragma unroll
-    for (int c = 0; c < 9; ++c) {
-      double t = 0.0;
-      for (int k = threadIdx.x; k < F.nitems; k += blockDim.x) t += __ldcg(a.vitem + 9 * (F.item_off + k) + c);
-      W[c] = block_sum_d(t);
-    }
+    for (int c = 0; c < 9; ++c) W[c] = block_sum_d(strided_sum_d(a.vitem + 9 * F.item_off + c, F.nitems, 9));
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      double t = 0.0;
-      for (int k = threadIdx.x; k < F.infl_nblk; k += blockDim.x) t += a.vparts[6 * (F.infl_blk_off + k) + c];
-      S[c] = block_sum_d(t);
-    }
+    for (int c = 0; c < 6; ++c) S[c] = block_sum_d(strided_sum_d(a.vparts + 6 * F.infl_blk_off + c, F.infl_nblk, 6));
   }
   if (threadIdx.x == 0) {
     const double V = F.g.volume;

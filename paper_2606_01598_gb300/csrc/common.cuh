@@ -448,6 +448,22 @@ __device__ __forceinline__ double block_sum_f(float v) {
   return r;
 }
 
+// sum_{k = threadIdx.x; k < n; k += blockDim.x} src[k * stride] in that order, with eight loads
+// in flight at a time (the plain loop waits for each load before the next one). __ldcg reads
+// partials other blocks wrote in the same launch.
+__device__ __forceinline__ double strided_sum_d(const double* src, int n, int stride = 1) {
+  double acc = 0.0;
+  const int T = blockDim.x;
+  for (int k0 = threadIdx.x; k0 < n; k0 += 8 * T) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = (k0 + u * T < n) ? __ldcg(src + size_t(k0 + u * T) * stride) : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc += v[u];
+  }
+  return acc;
+}
+
 // Ion range [lo, hi) of reduction item `item` of frame F.
 __device__ __forceinline__ void item_range(const FrameDesc& F, int item, int& lo, int& hi) {
   lo = F.ion_off + (item - F.item_off) * kRedItem;

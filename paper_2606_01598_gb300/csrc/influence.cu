@@ -147,10 +147,8 @@ k_energy_final(FrameDesc one, FrameMaps maps, const double* parts, int recip_kin
   b = block_sum_d(b);
   if (threadIdx.x == 0) eitem[item] = b;
   if (!last_item_done(ecount + f, F.nitems)) return;
-  double a = 0.0, e = 0.0;
-  if (recip_kind)
-    for (int k = threadIdx.x; k < F.infl_nblk; k += blockDim.x) a += parts[F.infl_blk_off + k];
-  for (int k = threadIdx.x; k < F.nitems; k += blockDim.x) e += __ldcg(eitem + F.item_off + k);
+  double a = recip_kind ? strided_sum_d(parts + F.infl_blk_off, F.infl_nblk) : 0.0;
+  double e = strided_sum_d(eitem + F.item_off, F.nitems);
   a = block_sum_d(a);
   e = block_sum_d(e);
   if (threadIdx.x == 0) {

@@ -34,11 +34,31 @@ __device__ void block_exclusive_scan(int* count, int* start, int n) {
   const int T = blockDim.x;
   const int chunk = ((n + T - 1) / T + 3) & ~3;
   const int lo = min(n, threadIdx.x * chunk), hi = min(n, lo + chunk);
+  // chunks of up to 16 entries stay in registers between the two passes
+  constexpr int kHold = 4;
+  int4 held[kHold];
+  const bool hold = hi - lo <= 4 * kHold;
   int local = 0;
+  if (hold) {
+#pragma unroll
+    for (int u = 0; u < kHold; ++u) {
+      const int k = lo + 4 * u;
+      held[u] = k < hi ? __ldcg(reinterpret_cast<const int4*>(count + k)) : make_int4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < kHold; ++u) {
+      const int k = lo + 4 * u;
+      if (k < hi) {
+        const int4 c = held[u];
+        local += c.x + (k + 1 < hi ? c.y : 0) + (k + 2 < hi ? c.z : 0) + (k + 3 < hi ? c.w : 0);
+      }
+    }
+  } else {
 #pragma unroll 4
-  for (int k = lo; k < hi; k += 4) {
-    const int4 c = __ldcg(reinterpret_cast<const int4*>(count + k));
-    local += c.x + (k + 1 < hi ? c.y : 0) + (k + 2 < hi ? c.z : 0) + (k + 3 < hi ? c.w : 0);
+    for (int k = lo; k < hi; k += 4) {
+      const int4 c = __ldcg(reinterpret_cast<const int4*>(count + k));
+      local += c.x + (k + 1 < hi ? c.y : 0) + (k + 2 < hi ? c.z : 0) + (k + 3 < hi ? c.w : 0);
+    }
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int v = local;
@@ -62,7 +82,7 @@ __device__ void block_exclusive_scan(int* count, int* start, int n) {
   int run = v - local + (wid > 0 ? warp_tot[wid - 1] : 0);
 #pragma unroll 4
   for (int k = lo; k < hi; k += 4) {
-    const int4 c = __ldcg(reinterpret_cast<const int4*>(count + k));
+    const int4 c = hold ? held[(k - lo) >> 2] : __ldcg(reinterpret_cast<const int4*>(count + k));
     int4 o;
     o.x = run;
     o.y = o.x + c.x;
@@ -162,11 +182,8 @@ k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int tangent, 
       sb.qpart[2 * item + 1] = B;
     }
     if (last_item_done(sb.qcount + f, F.nitems)) {
-      double a = 0.0, b = 0.0;
-      for (int k = threadIdx.x; k < F.nitems; k += blockDim.x) {
-        a += __ldcg(sb.qpart + 2 * (F.item_off + k));
-        b += __ldcg(sb.qpart + 2 * (F.item_off + k) + 1);
-      }
+      double a = strided_sum_d(sb.qpart + 2 * F.item_off, F.nitems, 2);
+      double b = strided_sum_d(sb.qpart + 2 * F.item_off + 1, F.nitems, 2);
       a = block_sum_d(a);
       b = block_sum_d(b);
       if (threadIdx.x == 0) {
