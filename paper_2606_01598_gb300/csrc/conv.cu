@@ -246,6 +246,7 @@ struct ConvArgs {
   double* partials;
   double* vparts;
   const float* gtab;
+  const int* keep;      // tangent passes: *keep == 0 skips rho / Phi (the forward's stay)
 };
 
 // Plane buffers of pass A / C: twiddles of z and y, then two buffers of cap entries.
@@ -288,6 +289,7 @@ __global__ void __launch_bounds__(kConvPlaneThreads) k_conv_r2c(ConvArgs a) {
   extern __shared__ __align__(16) float2 csm[];
   int copy, x0, pc;
   const FrameDesc& F = plane_block<BATCH>(a, copy, x0, pc);
+  if (copy == 0 && a.keep && *a.keep == 0) return;   // rho's spectrum is not needed again
   const int Ny = F.g.N[1], Nz = F.g.N[2], Nzh = Nz / 2 + 1;
   float2 *twz, *twy, *b0, *b1;
   plane_setup(a, F, csm, twz, twy, b0, b1);
@@ -363,6 +365,7 @@ __global__ void __launch_bounds__(kConvPlaneThreads) k_conv_c2r(ConvArgs a) {
   extern __shared__ __align__(16) float2 csm[];
   int copy, x0, pc;
   const FrameDesc& F = plane_block<BATCH>(a, copy, x0, pc);
+  if (copy == 0 && a.keep && *a.keep == 0) return;   // the forward's Phi stays in place
   const int Ny = F.g.N[1], Nz = F.g.N[2], Nzh = Nz / 2 + 1;
   float2 *twz, *twy, *b0, *b1;
   plane_setup(a, F, csm, twz, twy, b0, b1);
@@ -447,7 +450,10 @@ __global__ void __launch_bounds__(kConvBThreads) k_conv_x(ConvArgs a) {
   const int ncols = N1 * Nzh;   // (n_y, n_z) columns of a plane, contiguous for a fixed x
   const int c0 = (blockIdx.x - F.infl_blk_off) * F.conv_cols;
   const int kw = min(F.conv_cols, ncols - c0);
-  const int nc = a.tangent ? 2 * kw : kw;
+  // tangent pass on the forward's inputs: rho's columns are not needed again
+  const bool rho_cols = !(a.tangent && a.keep && *a.keep == 0);
+  const int nrho = rho_cols ? kw : 0;
+  const int nc = a.tangent ? nrho + kw : kw;
   const float rnc = 1.f / float(nc), rkw = 1.f / float(kw), rzh = 1.f / float(Nzh);
   float2* tw = csm;
   float2* b0 = csm + ((N0 + 1) & ~1);
@@ -464,7 +470,7 @@ __global__ void __launch_bounds__(kConvBThreads) k_conv_x(ConvArgs a) {
       if (t < N0 * nc) {
         int x, c;
         split_rc(t, nc, rnc, x, c);
-        v[u] = c < kw ? sp[size_t(x) * ncols + c] : tp[size_t(x) * ncols + c - kw];
+        v[u] = c < nrho ? sp[size_t(x) * ncols + c] : tp[size_t(x) * ncols + c - nrho];
       }
     }
 #pragma unroll
@@ -496,6 +502,12 @@ __global__ void __launch_bounds__(kConvBThreads) k_conv_x(ConvArgs a) {
     if (a.gtab) gc = a.gtab[F.gtab_off + size_t(ix) * ncols + c0 + c];
     else if (k2 > 0.f) gc = four_pi * expf(-k2 * a.inv4a2) / k2 * cx[ix] * cy[iy] * cz[iz];
     float2* pv = r + ix * nc + c;
+    const float fac = gc * g.inv_volume;
+    if (!rho_cols) {   // tangent columns only; no energy
+      const float2 u = *pv;
+      *pv = make_float2(u.x * fac, u.y * fac);
+      continue;
+    }
     const float2 v = *pv;
     const float w = (iz == 0 || (2 * iz == N2)) ? 1.f : 2.f;
     const float eg = w * gc * (v.x * v.x + v.y * v.y);
@@ -509,7 +521,6 @@ __global__ void __launch_bounds__(kConvBThreads) k_conv_x(ConvArgs a) {
       comp_add(sv[4], sc[4], tt * kx * kz);
       comp_add(sv[5], sc[5], tt * kyv * kz);
     }
-    const float fac = gc * g.inv_volume;
     *pv = make_float2(v.x * fac, v.y * fac);
     if (a.tangent) {
       const float2 u = pv[kw];
@@ -521,8 +532,8 @@ __global__ void __launch_bounds__(kConvBThreads) k_conv_x(ConvArgs a) {
   for (int t = threadIdx.x; t < N0 * nc; t += blockDim.x) {
     int x, c;
     split_rc(t, nc, rnc, x, c);
-    if (c < kw) sp[size_t(x) * ncols + c] = o[t];
-    else tp[size_t(x) * ncols + c - kw] = o[t];
+    if (c < nrho) sp[size_t(x) * ncols + c] = o[t];
+    else tp[size_t(x) * ncols + c - nrho] = o[t];
   }
   __shared__ double wsum[kConvBThreads / 32];
   const double et = block_comp_sum(e, ec, wsum);
@@ -615,8 +626,9 @@ void conv_twiddles(int L, std::vector<float2>& out) {
   }
 }
 
-int launch_conv_forward(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh) {
+int launch_conv_forward(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh, const int* keep) {
   ConvArgs a = conv_args(p);
+  a.keep = tangent ? keep : nullptr;
   a.mesh = mesh;
   a.spec = reinterpret_cast<float2*>(p->spec);
   a.tangent = tangent ? 1 : 0;
@@ -638,8 +650,9 @@ int launch_conv_forward(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh)
   return check_launch(p, "k_conv_r2c");
 }
 
-int launch_conv_inverse(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh) {
+int launch_conv_inverse(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh, const int* keep) {
   ConvArgs a = conv_args(p);
+  a.keep = tangent ? keep : nullptr;
   a.mesh = mesh;
   a.spec = reinterpret_cast<float2*>(p->spec);
   a.tangent = tangent ? 1 : 0;
@@ -661,8 +674,10 @@ int launch_conv_inverse(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh)
   return check_launch(p, "k_conv_c2r");
 }
 
-int launch_conv_influence(pme_plan_t p, cudaStream_t s, bool tangent, double* partials, double* vparts) {
+int launch_conv_influence(pme_plan_t p, cudaStream_t s, bool tangent, double* partials, double* vparts,
+                          const int* keep) {
   ConvArgs a = conv_args(p);
+  a.keep = tangent ? keep : nullptr;
   a.spec = reinterpret_cast<float2*>(p->spec);
   a.tangent = tangent ? 1 : 0;
   a.partials = partials;

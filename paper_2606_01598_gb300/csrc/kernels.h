@@ -64,10 +64,12 @@ size_t conv_plane_cap(const int N[3]);
 size_t conv_plane_smem(const int N[3], size_t cap);
 size_t conv_x_smem(const int N[3]);
 void conv_twiddles(int L, std::vector<float2>& out);
-int launch_conv_forward(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh);
+// keep (tangent passes, nullable): *keep == 0 means the plan's rho and Phi are those of the
+// forward on the same inputs; the passes then skip them and transform the tangent mesh only.
+int launch_conv_forward(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh, const int* keep = nullptr);
 int launch_conv_influence(pme_plan_t p, cudaStream_t s, bool tangent, double* partials,
-                          double* vparts = nullptr);
-int launch_conv_inverse(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh);
+                          double* vparts = nullptr, const int* keep = nullptr);
+int launch_conv_inverse(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh, const int* keep = nullptr);
 
 // gather.cu: per-ion interpolation of the potential mesh(es).
 //   forward: out[orig][10] = phi, dphi/dr (3), d2phi/drdr (6)

@@ -792,8 +792,10 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
 
 // ---- the passes ----------------------------------------------------------------------------
 
-static int fft_forward(pme_plan_t p, cudaStream_t s, bool tangent) {
-  if (p->conv) return launch_conv_forward(p, s, tangent, p->rho);
+// keep (own transforms, backward, nullable): *keep == 0 means rho and Phi are the plan's
+// forward's, so only the tangent mesh is transformed (Phi stays in place)
+static int fft_forward(pme_plan_t p, cudaStream_t s, bool tangent, const int* keep = nullptr) {
+  if (p->conv) return launch_conv_forward(p, s, tangent, p->rho, keep);
   int st;
   for (int gi = 0; gi < p->nfgroups; ++gi) {
     FFTGroup& G = p->fgroups[gi];
@@ -804,8 +806,8 @@ static int fft_forward(pme_plan_t p, cudaStream_t s, bool tangent) {
   return PME_OK;
 }
 
-static int fft_inverse(pme_plan_t p, cudaStream_t s, bool tangent) {
-  if (p->conv) return launch_conv_inverse(p, s, tangent, p->phi);
+static int fft_inverse(pme_plan_t p, cudaStream_t s, bool tangent, const int* keep = nullptr) {
+  if (p->conv) return launch_conv_inverse(p, s, tangent, p->phi, keep);
   int st;
   for (int gi = 0; gi < p->nfgroups; ++gi) {
     FFTGroup& G = p->fgroups[gi];
@@ -819,8 +821,9 @@ static int fft_inverse(pme_plan_t p, cudaStream_t s, bool tangent) {
 // The influence stage: with the hand-written transforms, the x transforms and the multiply
 // in one pass (the spectra are then transformed along z and y only); otherwise in place on
 // cuFFT's full spectra.
-static int multiply_influence(pme_plan_t p, cudaStream_t s, bool tangent, double* vparts) {
-  if (p->conv) return launch_conv_influence(p, s, tangent, p->epart, vparts);
+static int multiply_influence(pme_plan_t p, cudaStream_t s, bool tangent, double* vparts,
+                              const int* keep = nullptr) {
+  if (p->conv) return launch_conv_influence(p, s, tangent, p->epart, vparts, keep);
   return launch_influence(p, s, p->spec, tangent, p->epart, vparts);
 }
 
@@ -1024,13 +1027,14 @@ static int run_backward(pme_plan_t p, cudaStream_t s, const IonInputs& in, const
   if ((st = launch_spread(p, s, true, p->rho, reuse ? p->in_diff : nullptr))) return st;
   prof_end(p, t, s);
   t = prof_begin(p, B + 2, s);
-  if ((st = fft_forward(p, s, true))) return st;
+  const int* keep = reuse ? p->in_diff : nullptr;
+  if ((st = fft_forward(p, s, true, keep))) return st;
   prof_end(p, t, s);
   t = prof_begin(p, B + 3, s);
-  if ((st = multiply_influence(p, s, true, nullptr))) return st;
+  if ((st = multiply_influence(p, s, true, nullptr, keep))) return st;
   prof_end(p, t, s);
   t = prof_begin(p, B + 4, s);
-  if ((st = fft_inverse(p, s, true))) return st;
+  if ((st = fft_inverse(p, s, true, keep))) return st;
   prof_end(p, t, s);
   t = prof_begin(p, B + 5, s);
   if ((st = launch_gather(p, s, n, p->phi, true, gE, p->mesh_out))) return st;
@@ -1458,6 +1462,7 @@ int pme_solve(pme_plan_t p, void* stream, const float* rho, float* phi_mesh, dou
     return set_error(p, PME_ERR_ARG, "pme_solve takes device pointers");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const FFTGroup& G = p->fgroups[0];
+  p->fwd_n = -1;   // the plan's rho is about to be replaced: nothing saved for a backward
   if ((st = check_cuda(p, cudaMemcpyAsync(p->rho, rho, sizeof(float) * p->M, cudaMemcpyDeviceToDevice, s),
                        "copy rho")))
     return st;
