@@ -6,13 +6,9 @@
 //   M_abc = sum_{jx,jy,jz} Phi(m0 + j) W^(a)(t_jx) W^(b)(t_jy) W^(c)(t_jz),
 // and r-space derivatives follow with D[a][b] = N_b C^{-1}[a][b] (d/dr = D d/dx).
 //
-// One launch per spline order covers the ions of every frame of that order, one block per
-// mesh brick (the bricks of the sort: an ion belongs to the brick holding its first stencil
-// point). The block loads the brick's tile of Phi (and d Phi) -- the brick plus p - 1 points
-// on the upper side of each axis, wrapped periodically -- into shared memory, eight loads in
-// flight per thread, and then evaluates the brick's ions from it, 32 at a time.
+// One launch per spline order covers the ions of every frame of that order.
 // Work split: a group of 8 lanes per ion, lane l owning stencil z-offset l (l < p), so each
-// tile row segment is read by consecutive lanes. Each lane forms the y- and x-moments of its
+// mesh row segment is read by consecutive lanes. Each lane forms the y- and x-moments of its
 // z-column, scales them by its own z-weights, and the group sums the moments with warp
 // shuffles. Forward mode keeps orders <= 2 (potential, gradient, Hessian). Tangent mode
 // (backward pass) keeps orders <= 3 of Phi and <= 2 of the tangent potential dPhi and
@@ -25,29 +21,16 @@ namespace {
 
 constexpr int kGatherThreads = 256;
 constexpr int kGroup = 8;
-constexpr int kTileLoads = 8;   // tile loads a thread keeps in flight
-constexpr int GBX = 8, GBY = 8, GBZ = 32;   // the sort's brick shape
 
 struct GatherArgs {
   FrameDesc one;
   FrameMaps maps;
   MeshRecords mr;
-  const int* start_b;     // sorted segment of each global brick
   const float* mesh;      // Phi of frame f at mesh_off, d Phi at tmesh_off
   const double* g_energy; // per frame
   float* out;
-  int key_lo;             // first global brick of this launch
+  int t_lo, t_hi;         // sorted positions of this launch
 };
-
-template <int P>
-struct Tile {
-  static constexpr int X = GBX + P - 1, Y = GBY + P - 1, Z = GBZ + P - 1, N = X * Y * Z;
-};
-
-template <int P, bool TAN>
-constexpr int gather_smem_bytes() {
-  return Tile<P>::N * (TAN ? 2 : 1) * 4;
-}
 
 __device__ __forceinline__ float group_sum(float v) {
   v += __shfl_xor_sync(0xffffffffu, v, 4);
@@ -65,58 +48,15 @@ __device__ __forceinline__ void apply_D(const float* D, const float x[3], float 
 template <int P, bool TAN, bool BATCH>
 __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
   constexpr int DM = TAN ? 3 : 2;
-  using TL = Tile<P>;
-  extern __shared__ __align__(16) float tile[];   // [TL::N] Phi, then [TL::N] d Phi
-  const int gkey = a.key_lo + blockIdx.x;
-  const int lo_ion = a.start_b[gkey], hi_ion = a.start_b[gkey + 1];
-  if (lo_ion == hi_ion) return;   // uniform: no ion starts its stencil in this brick
-  const int frame = BATCH ? a.maps.brick_frame[gkey] : 0;
+  const int gid = a.t_lo + (blockIdx.x * blockDim.x + threadIdx.x) / kGroup;
+  const int l = threadIdx.x & (kGroup - 1);
+  const bool valid = gid < a.t_hi;
+  const int ion = valid ? gid : a.t_lo;
+  const int frame = BATCH ? a.maps.sorted_frame[ion] : 0;
   const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, frame);
   const Geometry& g = F.g;
-  const int Nx = g.N[0], Ny = g.N[1], Nz = g.N[2];
-  const int bkey = gkey - F.brick_off;
-  const int b0z = (bkey % g.nb[2]) * GBZ;
-  const int b0y = ((bkey / g.nb[2]) % g.nb[1]) * GBY;
-  const int b0x = (bkey / (g.nb[2] * g.nb[1])) * GBX;
-  {
-    const float* phi_mesh = a.mesh + F.mesh_off;
-    const float* dphi_mesh = a.mesh + F.tmesh_off;
-    for (int t0 = threadIdx.x; t0 < TL::N; t0 += kTileLoads * blockDim.x) {
-      float v[kTileLoads], dv[kTileLoads];
-#pragma unroll
-      for (int u = 0; u < kTileLoads; ++u) {
-        const int t = t0 + u * blockDim.x;
-        v[u] = 0.f;
-        dv[u] = 0.f;
-        if (t < TL::N) {
-          const int tz = t % TL::Z, r = t / TL::Z;
-          const int ty = r % TL::Y, tx = r / TL::Y;
-          int x = b0x + tx, y = b0y + ty, z = b0z + tz;
-          while (x >= Nx) x -= Nx;
-          while (y >= Ny) y -= Ny;
-          while (z >= Nz) z -= Nz;
-          const size_t off = (size_t(x) * Ny + y) * Nz + z;
-          v[u] = __ldg(phi_mesh + off);
-          if (TAN) dv[u] = __ldg(dphi_mesh + off);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kTileLoads; ++u) {
-        const int t = t0 + u * blockDim.x;
-        if (t < TL::N) {
-          tile[t] = v[u];
-          if (TAN) tile[TL::N + t] = dv[u];
-        }
-      }
-    }
-  }
-  __syncthreads();
-  const float* dtile = tile + TL::N;
-  const int l = threadIdx.x & (kGroup - 1);
-  for (int base = lo_ion; base < hi_ion; base += kGatherThreads / kGroup) {
-  const int gid = base + int(threadIdx.x) / kGroup;
-  const bool valid = gid < hi_ion;
-  const int ion = valid ? gid : lo_ion;
+  const float* phi_mesh = a.mesh + F.mesh_off;
+  const float* dphi_mesh = a.mesh + F.tmesh_off;
   const int4 m = a.mr.idx[ion];
   const float4 fq = a.mr.fq[ion];
   float wx[DM + 1][P], wy[DM + 1][P], wzall[DM + 1][P];
@@ -132,8 +72,9 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
     for (int j = 0; j < P; ++j) v = (j == l) ? wzall[c][j] : v;
     wz[c] = act ? v : 0.f;
   }
-  // the ion's first stencil point lies in this brick: its stencil is inside the tile
-  const int lx = m.x - b0x, ly = m.y - b0y, lz = m.z - b0z + l;
+  int z = m.z + l;
+  if (z >= g.N[2]) z -= g.N[2];
+  const int Ny = g.N[1], Nz = g.N[2];
 
   // S[a][b]: sum over (jx, jy) of Phi * W^(a)_x * W^(b)_y for this lane's z, a + b <= DM
   float S[DM + 1][DM + 1];
@@ -150,6 +91,8 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
   if (act) {
 #pragma unroll
     for (int jx = 0; jx < P; ++jx) {
+      int x = m.x + jx;
+      if (x >= g.N[0]) x -= g.N[0];
       float r[DM + 1], rt[3];
 #pragma unroll
       for (int b = 0; b <= DM; ++b) r[b] = 0.f;
@@ -157,12 +100,14 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
       for (int b = 0; b < 3; ++b) rt[b] = 0.f;
 #pragma unroll
       for (int jy = 0; jy < P; ++jy) {
-        const int off = ((lx + jx) * TL::Y + (ly + jy)) * TL::Z + lz;
-        const float v = tile[off];
+        int y = m.y + jy;
+        if (y >= Ny) y -= Ny;
+        const size_t off = (size_t(x) * Ny + y) * Nz + z;
+        const float v = __ldg(phi_mesh + off);
 #pragma unroll
         for (int b = 0; b <= DM; ++b) r[b] += v * wy[b][jy];
         if (TAN) {
-          const float dv = dtile[off];
+          const float dv = __ldg(dphi_mesh + off);
 #pragma unroll
           for (int b = 0; b < 3; ++b) rt[b] += dv * wy[b][jy];
         }
@@ -189,7 +134,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
   const float m200 = MOM(2, 0, 0), m020 = MOM(0, 2, 0), m002 = MOM(0, 0, 2);
   const float m110 = MOM(1, 1, 0), m101 = MOM(1, 0, 1), m011 = MOM(0, 1, 1);
   if (!TAN) {
-    if (!valid || l != 0) continue;
+    if (!valid || l != 0) return;
     const float gx[3] = {m100, m010, m001};
     const float Hx[3][3] = {{m200, m110, m101}, {m110, m020, m011}, {m101, m011, m002}};
     float gr[3];
@@ -217,7 +162,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
     o[7] = Hr[0][1];
     o[8] = Hr[0][2];
     o[9] = Hr[1][2];
-    continue;
+    return;
   }
   if constexpr (TAN) {
     const float m300 = MOM(3, 0, 0), m030 = MOM(0, 3, 0), m003 = MOM(0, 0, 3);
@@ -228,7 +173,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
     const float t100 = TMOM(1, 0, 0), t010 = TMOM(0, 1, 0), t001 = TMOM(0, 0, 1);
     const float t200 = TMOM(2, 0, 0), t020 = TMOM(0, 2, 0), t002 = TMOM(0, 0, 2);
     const float t110 = TMOM(1, 1, 0), t101 = TMOM(1, 0, 1), t011 = TMOM(0, 1, 1);
-    if (!valid || l != 0) continue;
+    if (!valid || l != 0) return;
     const float gE = a.g_energy ? float(a.g_energy[frame]) : 0.f;
     const float4 dm = a.mr.dm[ion];   // m = D^T mu
     const float4 tq = a.mr.tq[ion];   // dq, dd = D^T (dmu + q dr)
@@ -286,27 +231,8 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
     o[6] = gm[2];
     o[7] = 0.f;
   }
-  }   // ions of the brick
 #undef MOM
 #undef TMOM
-}
-
-// One instantiation's launch; the first use on a device raises its dynamic shared-memory limit.
-template <int P, bool TAN, bool BATCH>
-int launch_order(pme_plan_t p, cudaStream_t s, int grid, const GatherArgs& a) {
-  constexpr int bytes = gather_smem_bytes<P, TAN>();
-  static unsigned done_mask = 0;   // devices 0..31 already configured (idempotent if raced)
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 32 || !(done_mask & (1u << dev))) {
-    const int st = check_cuda(p, cudaFuncSetAttribute(k_gather<P, TAN, BATCH>,
-                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
-                              "cudaFuncSetAttribute");
-    if (st) return st;
-    if (dev < 32) done_mask |= 1u << dev;
-  }
-  k_gather<P, TAN, BATCH><<<grid, kGatherThreads, bytes, s>>>(a);
-  return PME_OK;
 }
 
 template <bool TAN, bool BATCH>
@@ -316,30 +242,28 @@ int launch_t(pme_plan_t p, cudaStream_t s, int n, const float* mesh, const doubl
   a.one = p->frames_h[0];
   a.maps = p->maps;
   a.mr = p->mr;
-  a.start_b = p->sb.start_b;
   a.mesh = mesh;
   a.g_energy = g_energy;
   a.out = out;
-  if (n <= 0 && !BATCH) return PME_OK;
   for (int gi = 0; gi < p->nogroups; ++gi) {
     const OrderGroup& G = p->ogroups[gi];
-    const int grid = G.brick_hi - G.brick_lo;
+    a.t_lo = BATCH ? G.sorted_lo : 0;
+    a.t_hi = BATCH ? G.sorted_hi : n;
+    const int grid = int((size_t(a.t_hi - a.t_lo) * kGroup + kGatherThreads - 1) / kGatherThreads);
     if (grid <= 0) continue;
-    a.key_lo = G.brick_lo;
-    int st = PME_OK;
     switch (G.order) {
-      case 1: st = launch_order<1, TAN, BATCH>(p, s, grid, a); break;
-      case 2: st = launch_order<2, TAN, BATCH>(p, s, grid, a); break;
-      case 3: st = launch_order<3, TAN, BATCH>(p, s, grid, a); break;
-      case 4: st = launch_order<4, TAN, BATCH>(p, s, grid, a); break;
-      case 5: st = launch_order<5, TAN, BATCH>(p, s, grid, a); break;
-      case 6: st = launch_order<6, TAN, BATCH>(p, s, grid, a); break;
-      case 7: st = launch_order<7, TAN, BATCH>(p, s, grid, a); break;
+      case 1: k_gather<1, TAN, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
+      case 2: k_gather<2, TAN, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
+      case 3: k_gather<3, TAN, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
+      case 4: k_gather<4, TAN, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
+      case 5: k_gather<5, TAN, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
+      case 6: k_gather<6, TAN, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
+      case 7: k_gather<7, TAN, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
       default: return set_error(p, PME_ERR_ARG, "spline order out of range");
     }
-    if (st) return st;
     count_launch();
-    if ((st = check_launch(p, "k_gather"))) return st;
+    int st = check_launch(p, "k_gather");
+    if (st) return st;
   }
   return PME_OK;
 }
