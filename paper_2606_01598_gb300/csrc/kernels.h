@@ -27,14 +27,6 @@ struct IonInputs {
 // The count arrays must be zero unless p->counts_clean is false (then they are cleared here).
 int launch_sort(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent, bool need_mesh,
                 bool need_pair, const int* reuse, float* save = nullptr);
-// The same in two steps, so that the two orders can run on different streams: the binning
-// pass (keys of the orders asked for, records, charge sums), then for each order its scan,
-// scatter and re-rank (launch_sort_order may be called once per order, on any stream ordered
-// after the binning pass).
-int launch_sort_bin(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent, bool need_mesh,
-                    bool need_pair, const int* reuse, float* save = nullptr);
-int launch_sort_order(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent, bool mesh_side,
-                      bool pair_side, const int* reuse);
 // *in_diff = 1 unless the inputs equal the saved ones bit for bit; *cache_bad = 1 when
 // *in_diff or (with_lists) a recorded pair list overflowed; both 0 otherwise.
 int launch_input_check(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool with_lists);

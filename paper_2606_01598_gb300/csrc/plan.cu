@@ -944,20 +944,17 @@ static int run_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, double
   int st, t;
   t = prof_begin(p, 0, s);
   // the binning pass also saves the inputs for a backward on the same ones
-  if ((st = launch_sort_bin(p, s, in, false, true, pair, nullptr, n > 0 ? p->in_saved : nullptr))) return st;
-  // the pair term runs on the plan's side stream, concurrently with the mesh stages: the cell
-  // order, a list pass that writes each ion's hits (kept for a backward on the same
-  // positions), then the list-driven evaluation; if a list overflowed, the fused pass does the
-  // work instead. The mesh stages wait only for the brick order.
+  if ((st = launch_sort(p, s, in, false, true, pair, nullptr, n > 0 ? p->in_saved : nullptr))) return st;
+  prof_end(p, t, s);
+  // the pair term runs on the plan's side stream, concurrently with the mesh stages: a list
+  // pass writes each ion's hits (kept for a backward on the same positions), then the
+  // list-driven evaluation; if a list overflowed, the fused pass does the work instead
   const bool fork = pair && n > 0;
   const bool record = fork && p->plist;
   cudaStream_t ps = p->opts.overlap_pair ? p->side : s;
-  if (fork && p->opts.overlap_pair && (st = fork_side(p, s))) return st;
-  if ((st = launch_sort_order(p, s, in, false, true, false, nullptr))) return st;
-  prof_end(p, t, s);
   if (fork) {
+    if (p->opts.overlap_pair && (st = fork_side(p, s))) return st;
     t = prof_begin(p, 6, ps);
-    if ((st = launch_sort_order(p, ps, in, false, false, true, nullptr))) return st;
     if (record) {
       if ((st = launch_pair_build(p, ps, n, p->cache_bad))) return st;
       if ((st = launch_pair(p, ps, n, false, in, nullptr, p->pair_out, p->cache_bad, v_out != nullptr)))
@@ -1011,15 +1008,12 @@ static int run_backward(pme_plan_t p, cudaStream_t s, const IonInputs& in, const
   p->fwd_n = -1;   // a backward leaves nothing for a later one
   t = prof_begin(p, B + 0, s);
   if (reuse && (st = launch_input_check(p, s, in, cached))) return st;
-  const int* same = reuse ? p->in_diff : nullptr;
-  if ((st = launch_sort_bin(p, s, in, true, true, pair, same))) return st;
-  cudaStream_t ps = p->opts.overlap_pair ? p->side : s;
-  if (pair && p->opts.overlap_pair && (st = fork_side(p, s))) return st;
-  if ((st = launch_sort_order(p, s, in, true, true, false, same))) return st;
+  if ((st = launch_sort(p, s, in, true, true, pair, reuse ? p->in_diff : nullptr))) return st;
   prof_end(p, t, s);
+  cudaStream_t ps = p->opts.overlap_pair ? p->side : s;
   if (pair) {
+    if (p->opts.overlap_pair && (st = fork_side(p, s))) return st;
     t = prof_begin(p, B + 6, ps);
-    if ((st = launch_sort_order(p, ps, in, true, false, true, same))) return st;
     if ((st = launch_pair(p, ps, n, true, in, gE, p->pair_out, cached ? p->cache_bad : nullptr)))
       return st;
     if (cached) {

@@ -103,7 +103,7 @@ __device__ void block_exclusive_scan(int* count, int* start, int n) {
 template <bool BATCH>
 __global__ void __launch_bounds__(kSortThreads)
 k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int tangent, int* flags,
-      int need_mesh, int need_pair, const int* reuse, float* save, int ld) {
+      int nbricks, int ncells, const int* reuse, float* save, int ld) {
   static_assert(kRedItem == kSortThreads, "one ion per thread");
   const int item = blockIdx.x;
   const int f = BATCH ? maps.item_frame[item] : 0;
@@ -144,19 +144,13 @@ k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int tangent, 
       stencil_origin(s[b], g.N[b], g.order, m0[b], fb[b]);
       cell_origin(s[b], g.ncell[b], c[b], fc[b]);
     }
-    // only the keys this pass orders by are counted, so every count a scan does not see
-    // stays zero
-    if (need_mesh) {
-      const int kb = F.brick_off + ((m0[0] / g.brick[0]) * g.nb[1] + m0[1] / g.brick[1]) * g.nb[2] +
-                     m0[2] / g.brick[2];
-      sb.key_b[i] = kb;
-      sb.slot_b[i] = atomicAdd(&sb.count_b[kb], 1);
-    }
-    if (need_pair) {
-      const int kc = F.cell_off + (c[0] * g.ncell[1] + c[1]) * g.ncell[2] + c[2];
-      sb.key_c[i] = kc;
-      sb.slot_c[i] = atomicAdd(&sb.count_c[kc], 1);
-    }
+    const int kb = F.brick_off + ((m0[0] / g.brick[0]) * g.nb[1] + m0[1] / g.brick[1]) * g.nb[2] +
+                   m0[2] / g.brick[2];
+    const int kc = F.cell_off + (c[0] * g.ncell[1] + c[1]) * g.ncell[2] + c[2];
+    sb.key_b[i] = kb;
+    sb.key_c[i] = kc;
+    sb.slot_b[i] = atomicAdd(&sb.count_b[kb], 1);
+    sb.slot_c[i] = atomicAdd(&sb.count_c[kc], 1);
     if (sb.t_bidx) {
       // the primal records of both orders, in caller order (the rank pass moves them)
       const float qs = isfinite(qi) ? qi : 0.f;
@@ -171,16 +165,12 @@ k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int tangent, 
       float pm[3];
 #pragma unroll
       for (int b = 0; b < 3; ++b) pm[b] = mu[0] * g.D[0 * 3 + b] + mu[1] * g.D[1 * 3 + b] + mu[2] * g.D[2 * 3 + b];
-      if (need_mesh) {
-        sb.t_bidx[i] = make_int4(m0[0], m0[1], m0[2], i);
-        sb.t_bfq[i] = make_float4(fb[0], fb[1], fb[2], qs);
-        sb.t_bdm[i] = make_float4(pm[0], pm[1], pm[2], 0.f);
-      }
-      if (need_pair) {
-        sb.t_cidx[i] = make_int4(c[0], c[1], c[2], i);
-        sb.t_cfq[i] = make_float4(fc[0], fc[1], fc[2], __int_as_float(c[2]));
-        sb.t_cmu[i] = make_float4(mu[0], mu[1], mu[2], qs);
-      }
+      sb.t_bidx[i] = make_int4(m0[0], m0[1], m0[2], i);
+      sb.t_bfq[i] = make_float4(fb[0], fb[1], fb[2], qs);
+      sb.t_bdm[i] = make_float4(pm[0], pm[1], pm[2], 0.f);
+      sb.t_cidx[i] = make_int4(c[0], c[1], c[2], i);
+      sb.t_cfq[i] = make_float4(fc[0], fc[1], fc[2], __int_as_float(c[2]));
+      sb.t_cmu[i] = make_float4(mu[0], mu[1], mu[2], qs);
     }
     qa = isfinite(qi) ? qi : 0.f;
     qb = (tangent && in.gphi) ? in.gphi[i] : 0.f;
@@ -203,14 +193,15 @@ k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int tangent, 
       }
     }
   }
+  (void)nbricks;
+  (void)ncells;
 }
 
-// Segment starts from the final counts: block b scans the brick counts (side first + b = 0)
-// or the cell counts (side 1), 1024 threads each. Skipped on reuse.
-__global__ void __launch_bounds__(1024) k_scan(SortBuffers sb, int nbricks, int ncells, const int* reuse,
-                                               int first) {
+// Segment starts from the final counts: block 0 scans the brick counts, block 1 the cell
+// counts (1024 threads each). Skipped on reuse.
+__global__ void __launch_bounds__(1024) k_scan(SortBuffers sb, int nbricks, int ncells, const int* reuse) {
   if (reuse && *reuse == 0) return;
-  if (first + blockIdx.x == 0) block_exclusive_scan(sb.count_b, sb.start_b, nbricks);
+  if (blockIdx.x == 0) block_exclusive_scan(sb.count_b, sb.start_b, nbricks);
   else block_exclusive_scan(sb.count_c, sb.start_c, ncells);
 }
 
@@ -233,10 +224,9 @@ __device__ __forceinline__ int stable_rank(const int* perm, int seg_lo, int seg_
 template <bool BATCH>
 __global__ void __launch_bounds__(kSortThreads)
 k_rank_records(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, MeshRecords mr,
-               PairRecords pr, int tangent, int need_mesh, int need_pair, const int* reuse, int t_off) {
+               PairRecords pr, int tangent, int need_mesh, int need_pair, const int* reuse) {
   const int n = in.n;
-  // threads [0, n) the mesh order, [n, 2n) the pair order; t_off = n runs the pair order alone
-  int t = blockIdx.x * blockDim.x + threadIdx.x + t_off;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
   const bool mesh_side = t < n;
   if (!mesh_side) t -= n;
   if (t >= n) return;
@@ -393,15 +383,16 @@ k_input_check(int n, IonInputs in, const float* saved, int ld, const int* list_c
   }
 }
 
-// Binning pass (with the count memsets when the counts are not known to be zero).
 template <bool BATCH>
-int launch_bin_t(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent, bool need_mesh,
-                 bool need_pair, const int* reuse, float* save) {
+int launch_sort_t(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent, bool need_mesh,
+                  bool need_pair, const int* reuse, float* save) {
+  const int n = in.n;
+  const int nblk = (n + kSortThreads - 1) / kSortThreads;
   FrameDesc one = p->frames_h[0];
   if (!BATCH) {
-    one.n = in.n;
+    one.n = n;
     one.item_off = 0;
-    one.nitems = std::max(1, (in.n + kRedItem - 1) / kRedItem);
+    one.nitems = std::max(1, (n + kRedItem - 1) / kRedItem);
   }
   int st = PME_OK;
   if (!p->counts_clean) {
@@ -412,44 +403,31 @@ int launch_bin_t(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent
                     "memset cell counts");
     if (st) return st;
   }
-  const int items = BATCH ? p->total_items : one.nitems;
-  k_bin<BATCH><<<items, kSortThreads, 0, s>>>(one, p->maps, in, p->sb, tangent ? 1 : 0, p->flags,
-                                              need_mesh ? 1 : 0, need_pair ? 1 : 0, reuse, save,
-                                              p->max_ions);
-  count_launch();
-  if ((st = check_launch(p, "k_bin"))) p->counts_clean = false;
-  return st;
-}
-
-// Scan, scatter and re-rank of one order (mesh: bricks; pair: cells) or of both.
-template <bool BATCH>
-int launch_order_t(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent, bool mesh_side,
-                   bool pair_side, const int* reuse) {
-  const int n = in.n;
-  FrameDesc one = p->frames_h[0];
-  if (!BATCH) {
-    one.n = n;
-    one.item_off = 0;
-    one.nitems = std::max(1, (n + kRedItem - 1) / kRedItem);
+  {
+    const int items = BATCH ? p->total_items : one.nitems;
+    k_bin<BATCH><<<items, kSortThreads, 0, s>>>(one, p->maps, in, p->sb, tangent ? 1 : 0, p->flags,
+                                                p->total_bricks, p->total_cells, reuse, save,
+                                                p->max_ions);
+    count_launch();
+    if ((st = check_launch(p, "k_bin"))) {
+      p->counts_clean = false;
+      return st;
+    }
+    k_scan<<<2, 1024, 0, s>>>(p->sb, p->total_bricks, p->total_cells, reuse);
+    count_launch();
+    if ((st = check_launch(p, "k_scan"))) {
+      p->counts_clean = false;
+      return st;
+    }
   }
-  const int sides = (mesh_side ? 1 : 0) + (pair_side ? 1 : 0);
-  if (sides == 0) return PME_OK;
-  int st;
-  k_scan<<<sides, 1024, 0, s>>>(p->sb, p->total_bricks, p->total_cells, reuse, mesh_side ? 0 : 1);
-  count_launch();
-  if ((st = check_launch(p, "k_scan"))) {
-    p->counts_clean = false;
-    return st;
-  }
-  const int nblk = (n + kSortThreads - 1) / kSortThreads;
   if (nblk > 0) {
-    k_scatter<<<nblk, kSortThreads, 0, s>>>(n, p->sb, mesh_side ? 1 : 0, pair_side ? 1 : 0, reuse);
+    k_scatter<<<nblk, kSortThreads, 0, s>>>(n, p->sb, need_mesh ? 1 : 0, need_pair ? 1 : 0, reuse);
     count_launch();
     if ((st = check_launch(p, "k_scatter"))) return st;
-    const int nblk2 = int((size_t(sides) * n + kSortThreads - 1) / kSortThreads);
+    const int nblk2 = (2 * n + kSortThreads - 1) / kSortThreads;
     k_rank_records<BATCH><<<nblk2, kSortThreads, 0, s>>>(one, p->maps, in, p->sb, p->mr, p->pr,
-                                                         tangent ? 1 : 0, mesh_side ? 1 : 0,
-                                                         pair_side ? 1 : 0, reuse, mesh_side ? 0 : n);
+                                                         tangent ? 1 : 0, need_mesh ? 1 : 0,
+                                                         need_pair ? 1 : 0, reuse);
     count_launch();
     if ((st = check_launch(p, "k_rank_records"))) return st;
   }
@@ -468,24 +446,11 @@ int launch_input_check(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool w
   return check_launch(p, "k_input_check");
 }
 
-int launch_sort_bin(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent, bool need_mesh,
-                    bool need_pair, const int* reuse, float* save) {
-  if (!reuse) p->fwd_n = -1;   // the sorted records no longer belong to the saved inputs
-  return p->batch ? launch_bin_t<true>(p, s, in, tangent, need_mesh, need_pair, reuse, save)
-                  : launch_bin_t<false>(p, s, in, tangent, need_mesh, need_pair, reuse, save);
-}
-
-int launch_sort_order(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent, bool mesh_side,
-                      bool pair_side, const int* reuse) {
-  return p->batch ? launch_order_t<true>(p, s, in, tangent, mesh_side, pair_side, reuse)
-                  : launch_order_t<false>(p, s, in, tangent, mesh_side, pair_side, reuse);
-}
-
 int launch_sort(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent, bool need_mesh,
                 bool need_pair, const int* reuse, float* save) {
-  int st = launch_sort_bin(p, s, in, tangent, need_mesh, need_pair, reuse, save);
-  if (st) return st;
-  return launch_sort_order(p, s, in, tangent, need_mesh, need_pair, reuse);
+  if (!reuse) p->fwd_n = -1;   // the sorted records no longer belong to the saved inputs
+  return p->batch ? launch_sort_t<true>(p, s, in, tangent, need_mesh, need_pair, reuse, save)
+                  : launch_sort_t<false>(p, s, in, tangent, need_mesh, need_pair, reuse, save);
 }
 
 }  // namespace gbpme
