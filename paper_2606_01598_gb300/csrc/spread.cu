@@ -31,7 +31,7 @@ namespace gbpme {
 
 namespace {
 
-constexpr int BX = 8, BY = 8, BZ = 32;
+constexpr int BX = 8, BY = 8, BZ = 16;
 constexpr int ZS = 8;                     // z points per thread
 constexpr int NSEG = BZ / ZS;             // z-segments per column
 constexpr int NT = BX * BY * NSEG;        // 256 threads
