@@ -19,7 +19,7 @@ namespace gbpme {
 
 namespace {
 
-constexpr int kGatherThreads = 256;
+constexpr int kGatherThreads = 128;
 constexpr int kGroup = 8;
 
 struct GatherArgs {
