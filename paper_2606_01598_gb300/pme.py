@@ -1,16 +1,18 @@
 """Python face of libgbpme: a plan object over the C ABI and a differentiable energy.
 
-Every step of the computation runs in the library's CUDA kernels (and cuFFT for the two 3D
-transforms); this module only allocates output tensors, passes pointers and the current CUDA
-stream, and wires the adjoint into torch.autograd:
+Every step of the computation runs in the library's CUDA kernels (the 3D transforms in the
+library's own kernels or in cuFFT, see Plan(fft=...)); this module only allocates output
+tensors, passes pointers and the current CUDA stream, and wires the adjoint into
+torch.autograd:
 
   E = PMEEnergy.apply(plan, pos, q, mu)
   F = -torch.autograd.grad(E, pos, create_graph=True)[0]      # Eq. forces
   loss = ((F - F_ref) ** 2).mean(); loss.backward()           # Eq. loss: double backward
 
 The first derivatives come from pme_forward; the derivative of those derivatives (the
-Hessian-vector product the force-matching loss needs) from pme_backward, which recomputes
-the mesh potential instead of storing it.
+Hessian-vector product the force-matching loss needs) from pme_backward, which reuses what
+the plan kept from the forward when its inputs are the forward's (checked on the device) and
+recomputes everything otherwise.
 """
 from __future__ import annotations
 
@@ -36,10 +38,30 @@ def _stream_handle(device):
 def _f32(t, device):
     if t is None:
         return None
+    if (isinstance(t, torch.Tensor) and t.dtype == torch.float32 and t.device == device
+            and t.is_contiguous()):
+        return t   # the common case, without the conversion calls
     t = torch.as_tensor(t)
     if device.type == "cuda":
         t = t.to(device=device)
     return t.to(torch.float32).contiguous()
+
+
+class _on_device:
+    """torch.cuda.device(device), skipped when that device is already current."""
+
+    def __init__(self, device):
+        self.device = device
+        self.ctx = None
+
+    def __enter__(self):
+        if torch.cuda.current_device() != self.device.index:
+            self.ctx = torch.cuda.device(self.device)
+            self.ctx.__enter__()
+
+    def __exit__(self, *exc):
+        if self.ctx is not None:
+            self.ctx.__exit__(*exc)
 
 
 def mesh_dims(box, spacing: float, rule: int = 0, strategy: int = 1, clamp=(0, 0)):
@@ -131,7 +153,7 @@ class Plan:
         b = (ctypes.c_double * 9)(*self.box.reshape(9))
         m = (ctypes.c_int * 3)(*self.mesh)
         h = ctypes.c_void_p()
-        with torch.cuda.device(self.device):
+        with _on_device(self.device):
             st = self.lib.pme_plan_create(ctypes.byref(h), b, m, self.order, self.alpha, self.rcut,
                                           ctypes.byref(opts))
         if st:
@@ -167,7 +189,7 @@ class Plan:
         return "own" if k.value == 0 else "cufft"
 
     def sync_status(self):
-        with torch.cuda.device(self.device):
+        with _on_device(self.device):
             self._check(self.lib.pme_sync_status(self.handle, _stream_handle(self.device)),
                         "pme_sync_status")
 
@@ -179,7 +201,7 @@ class Plan:
         """{'fwd.spread': (ms_total, calls), ...} since the last read; resets the timers."""
         ms = (ctypes.c_double * _abi.NUM_STAGES)()
         calls = (ctypes.c_longlong * _abi.NUM_STAGES)()
-        with torch.cuda.device(self.device):
+        with _on_device(self.device):
             self._check(self.lib.pme_profile_read(self.handle, ms, calls), "pme_profile_read")
         out = {}
         for k in range(_abi.NUM_STAGES):
@@ -220,7 +242,7 @@ class Plan:
         if virial:
             out.setdefault("energy", torch.empty(1, dtype=torch.float64, **alloc))
             out["virial"] = torch.empty((3, 3), dtype=torch.float64, **alloc)
-        with torch.cuda.device(self.device):
+        with _on_device(self.device):
             args = (self.handle, _stream_handle(self.device), n, _ptr(pos), _ptr(q),
                     _ptr(mu), _ptr(out.get("energy")), _ptr(out.get("force")),
                     _ptr(out.get("phi")), _ptr(out.get("field")), _ptr(out.get("field_grad")))
@@ -252,7 +274,7 @@ class Plan:
         gp = torch.empty((n, 3), dtype=torch.float32, **alloc)
         gq = torch.empty(n, dtype=torch.float32, **alloc)
         gm = torch.empty((n, 3), dtype=torch.float32, **alloc)
-        with torch.cuda.device(self.device):
+        with _on_device(self.device):
             st = self.lib.pme_backward(self.handle, _stream_handle(self.device), n, _ptr(pos), _ptr(q),
                                        _ptr(mu), _ptr(g_energy), _ptr(g_force), _ptr(g_phi),
                                        _ptr(g_field), _ptr(gp), _ptr(gq), _ptr(gm))
@@ -265,7 +287,7 @@ class Plan:
     def spread(self, pos, q, mu=None):
         pos, q, mu = (_f32(t, self.device) for t in (pos, q, mu))
         rho = torch.empty(self.mesh, dtype=torch.float32, device=self.device)
-        with torch.cuda.device(self.device):
+        with _on_device(self.device):
             self._check(self.lib.pme_spread(self.handle, _stream_handle(self.device), int(pos.shape[0]),
                                             _ptr(pos), _ptr(q), _ptr(mu), _ptr(rho)), "pme_spread")
         return rho
@@ -274,7 +296,7 @@ class Plan:
         rho = _f32(rho, self.device)
         phi = torch.empty(self.mesh, dtype=torch.float32, device=self.device)
         e = torch.empty(1, dtype=torch.float64, device=self.device)
-        with torch.cuda.device(self.device):
+        with _on_device(self.device):
             self._check(self.lib.pme_solve(self.handle, _stream_handle(self.device), _ptr(rho), _ptr(phi),
                                            _ptr(e)), "pme_solve")
         return phi, e
@@ -283,7 +305,7 @@ class Plan:
         pos = _f32(pos, self.device)
         phi_mesh = _f32(phi_mesh, self.device)
         out = torch.empty((pos.shape[0], 10), dtype=torch.float32, device=self.device)
-        with torch.cuda.device(self.device):
+        with _on_device(self.device):
             self._check(self.lib.pme_gather(self.handle, _stream_handle(self.device), int(pos.shape[0]),
                                             _ptr(pos), _ptr(phi_mesh), _ptr(out)), "pme_gather")
         return out
@@ -292,7 +314,7 @@ class Plan:
         pos, q, mu = (_f32(t, self.device) for t in (pos, q, mu))
         out = torch.empty((pos.shape[0], 10), dtype=torch.float32, device=self.device)
         e = torch.empty(1, dtype=torch.float64, device=self.device)
-        with torch.cuda.device(self.device):
+        with _on_device(self.device):
             self._check(self.lib.pme_pair(self.handle, _stream_handle(self.device), int(pos.shape[0]),
                                           _ptr(pos), _ptr(q), _ptr(mu), _ptr(out), _ptr(e)), "pme_pair")
         return out, e
@@ -346,7 +368,7 @@ class BatchPlan(Plan):
         o = (ctypes.c_int * F)(*orders.tolist())
         off = (ctypes.c_int * (F + 1))(*offsets.tolist())
         h = ctypes.c_void_p()
-        with torch.cuda.device(self.device):
+        with _on_device(self.device):
             st = self.lib.pme_batch_create(ctypes.byref(h), F, off, b, m, o, float(alpha), float(rcut),
                                            ctypes.byref(opts))
         if st:
@@ -374,7 +396,7 @@ class BatchPlan(Plan):
         if virial:
             out.setdefault("energy", torch.empty(self.nframes, dtype=torch.float64, **alloc))
             out["virial"] = torch.empty((self.nframes, 3, 3), dtype=torch.float64, **alloc)
-        with torch.cuda.device(self.device):
+        with _on_device(self.device):
             args = (self.handle, _stream_handle(self.device), _ptr(pos), _ptr(q),
                     _ptr(mu), _ptr(out.get("energy")), _ptr(out.get("force")),
                     _ptr(out.get("phi")), _ptr(out.get("field")), _ptr(out.get("field_grad")))
@@ -399,7 +421,7 @@ class BatchPlan(Plan):
         gp = torch.empty((n, 3), dtype=torch.float32, **alloc)
         gq = torch.empty(n, dtype=torch.float32, **alloc)
         gm = torch.empty((n, 3), dtype=torch.float32, **alloc)
-        with torch.cuda.device(self.device):
+        with _on_device(self.device):
             st = self.lib.pme_batch_backward(self.handle, _stream_handle(self.device), _ptr(pos), _ptr(q),
                                              _ptr(mu), _ptr(g_energy), _ptr(g_force), _ptr(g_phi),
                                              _ptr(g_field), _ptr(gp), _ptr(gq), _ptr(gm))
