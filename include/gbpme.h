@@ -33,8 +33,9 @@
  *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.
  *     Calls are asynchronous on that stream. A plan must not be used by two calls that
  *     overlap in time (its scratch buffers are shared); use one plan per stream.
- *   - The plan owns all scratch (sorted ion records, meshes, spectra, cuFFT plans), sized
- *     at creation for opts.max_ions ions. Nothing is allocated by the compute calls.
+ *   - The plan owns all scratch (sorted ion records, meshes, spectra, cuFFT plans when it
+ *     uses cuFFT), sized at creation for opts.max_ions ions. Nothing is allocated on the
+ *     device by the compute calls.
  *
  * Errors: every function returns a pme_status. No exception crosses the ABI. The text of
  * the last error of a plan is returned by pme_last_error(). Non-finite inputs are detected
@@ -92,8 +93,11 @@ typedef struct {
                               long and a mesh plane fits in one block's shared memory.
                               0 (default): automatic, the library's own for batched plans
                               whose meshes have no axis above 64 points (one launch per pass
-                              for all frames; faster there on GB300), cuFFT otherwise. 1: always cuFFT. 2: always the library's own
-                              (PME_ERR_UNSUPPORTED where they do not apply) */
+                              for all frames; faster there on GB300), cuFFT otherwise.
+                              1: always cuFFT. 2: always the library's own
+                              (PME_ERR_UNSUPPORTED where they do not apply). With the own
+                              transforms the stage timers' "FFT R2C" and "FFT C2R" stages are
+                              the z/y passes and "influence" includes the x transforms */
   int reserved[4];
 } pme_opts;
 
@@ -189,9 +193,10 @@ int pme_forward_virial(pme_plan_t plan, void* stream, int n, const float* pos, c
  * (boxes + 9 f, rows = lattice vectors), mesh (meshes + 3 f) and spline order (orders[f]);
  * alpha, rcut and opts are shared (opts.max_ions is ignored: the plan holds offsets[F] ions;
  * opts.recip_method must be 0). Every stage runs as one launch over the whole batch (spread
- * and gather: one launch per distinct spline order; the FFTs: one batched cuFFT call per
- * distinct mesh shape), so a batch of small frames costs a handful of launches instead of
- * a handful per frame. The handle is a pme_plan_t: destroy it with pme_plan_destroy; the
+ * and gather: one launch per distinct spline order; the transforms: one launch per pass on
+ * the library's own transforms, or one batched cuFFT call per distinct mesh shape; see
+ * opts.fft), so a batch of small frames costs a handful of launches instead of a handful
+ * per frame. The handle is a pme_plan_t: destroy it with pme_plan_destroy; the
  * single-frame calls reject it and the batch calls reject single-frame plans. */
 int pme_batch_create(pme_plan_t* out, int nframes, const int* offsets, const double* boxes,
                      const int* meshes, const int* orders, double alpha, double rcut,
