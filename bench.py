@@ -7,6 +7,11 @@ Hessian-vector product a force-matching loss needs) on one 32768-ion molten-NaCl
 in HBM. The metric is ion-evaluations per second: ions / (t_forward + t_backward).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--fft auto|cufft|own] [--batch] [--crossover] [--no-extras]
+
+The timed steps repeat the same calls, so after the first two they replay the plan's recorded
+pass graphs, as any caller's repeated calls do. --fft picks the transforms of the mesh
+convolution (the automatic choice is cuFFT for this single frame).
 
 With N > 1 (launched by torch.distributed.run) every rank runs an independent replica of the
 step on its own GPU ("replicas only": a single frame does not shard); value is the sum of the
