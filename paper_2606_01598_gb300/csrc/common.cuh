@@ -232,7 +232,7 @@ struct pme_plan_s {
   cufftComplex* spec;        // spectra (same layout with spec_off / tspec_off)
   float* phi;                // potential meshes (layout of rho)
   float* dconv_all;          // per-frame, per-axis deconvolution factors 1/sinc^(2 p gamma)
-  float* gtab = nullptr;     // P3M influence tables (influence_kind 1), [half spectrum] per frame
+  float* gtab = nullptr;     // influence tables G C (or P3M), [half spectrum] per frame
   int* cand;                 // per-frame candidate-brick tables
   gbpme::SortBuffers sb;
   gbpme::MeshRecords mr;

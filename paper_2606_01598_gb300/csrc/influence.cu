@@ -4,7 +4,8 @@
 // One pass over each frame's R2C half spectrum [Nx][Ny][Nz/2+1]. For every signed frequency
 // n, k = n_x b_x + n_y b_y + n_z b_z, G(k) = 4 pi exp(-k^2 / 4 alpha^2) / k^2 (G(0) = 0) and
 // the separable deconvolution C(n) = prod_a 1/sinc^(2 p gamma)(n_a / N_a) (per-axis tables
-// built on the host). The energy (1/2V) sum_{n != 0} G C |rho_hat|^2 over the full spectrum
+// built on the host); G C itself depends only on the GPU machine and the mesh, so the plan keeps it
+// as a table per frame (k_gc_table, rebuilt when the box changes) and the pass reads it. The energy (1/2V) sum_{n != 0} G C |rho_hat|^2 over the full spectrum
 // is accumulated on the half spectrum with weight 2 for the planes that stand for their
 // mirror images (0 < n_z < Nz/2) and 1 otherwise; compensated (Neumaier) float sums per
 // thread and per warp go to float64 block partials. Each spectrum (and, in the backward pass,
@@ -213,7 +214,53 @@ __global__ void __launch_bounds__(kInflThreads) k_p3m_table(FrameDesc F, float i
   }
 }
 
+// Influence table of one frame for the default kind: G(k) C(n) at every half-spectrum point,
+// the same float expression the multiply would evaluate (G(0) = 0). It depends on the box and
+// the mesh only, so the plan builds it once (and again when the box changes) and the
+// multiply reads it instead of evaluating exp and a division per point on every call.
+__global__ void __launch_bounds__(kInflThreads) k_gc_table(FrameDesc F, const float* dconv, float inv4a2,
+                                                           float* tab) {
+  const Geometry& g = F.g;
+  const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2];
+  const int Nzh = N2 / 2 + 1;
+  const int Mh = N0 * N1 * Nzh;
+  const float* cx = dconv + F.dconv_off;
+  const float* cy = cx + N0;
+  const float* cz = cy + N1;
+  const float four_pi = 12.566370614359172f;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < Mh; idx += gridDim.x * blockDim.x) {
+    const int r = fdiv(idx, F.div_zh);
+    const int iz = idx - r * Nzh;
+    const int ix = fdiv(r, F.div_y);
+    const int iy = r - ix * N1;
+    const float nx = float(ix <= N0 / 2 ? ix : ix - N0);
+    const float ny = float(iy <= N1 / 2 ? iy : iy - N1);
+    const float nz = float(iz);
+    const float kx = nx * g.bk[0] + ny * g.bk[3] + nz * g.bk[6];
+    const float ky = nx * g.bk[1] + ny * g.bk[4] + nz * g.bk[7];
+    const float kz = nx * g.bk[2] + ny * g.bk[5] + nz * g.bk[8];
+    const float k2 = kx * kx + ky * ky + kz * kz;
+    float gc = 0.f;
+    if (k2 > 0.f) gc = four_pi * expf(-k2 * inv4a2) / k2 * cx[ix] * cy[iy] * cz[iz];
+    tab[F.gtab_off + idx] = gc;
+  }
+}
+
 }  // namespace
+
+int launch_influence_tables(pme_plan_t p, cudaStream_t s) {
+  if (p->opts.influence_kind == 1) return launch_p3m_tables(p, s);
+  const float inv4a2 = float(1.0 / (4.0 * p->alpha * p->alpha));
+  for (int f = 0; f < p->nframes; ++f) {
+    const FrameDesc& F = p->frames_h[f];
+    const long long Mh = (long long)F.g.N[0] * F.g.N[1] * (F.g.N[2] / 2 + 1);
+    const int grid = int(std::min<long long>((Mh + kInflThreads - 1) / kInflThreads, 152 * 8));
+    k_gc_table<<<grid, kInflThreads, 0, s>>>(F, p->dconv_all, inv4a2, p->gtab);
+    const int st = check_launch(p, "k_gc_table");
+    if (st) return st;
+  }
+  return PME_OK;
+}
 
 int launch_p3m_tables(pme_plan_t p, cudaStream_t s) {
   const float inv4a2 = float(1.0 / (4.0 * p->alpha * p->alpha));

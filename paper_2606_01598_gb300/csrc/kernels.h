@@ -49,6 +49,9 @@ int launch_energy_final(pme_plan_t p, cudaStream_t s, const double* parts, int r
 int influence_blocks(const Geometry& g);
 // Fill the P3M influence table of every frame (influence_kind 1; plan creation, set_box).
 int launch_p3m_tables(pme_plan_t p, cudaStream_t s);
+// Fill every frame's influence table for the plan's kind (G C for kind 0, P3M for kind 1):
+// plan creation and set_box; the multiply passes read it.
+int launch_influence_tables(pme_plan_t p, cudaStream_t s);
 void spread_brick_shape(int shape[3]);
 
 // conv.cu: the mesh convolution by hand-written transforms (meshes whose axes are all

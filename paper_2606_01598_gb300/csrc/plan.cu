@@ -556,7 +556,7 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
     spec_off += 2LL * G.count * Mh;
   }
   p->total_mesh = mesh_off;
-  long long gtab_total = 0;   // P3M influence tables, one half spectrum per frame
+  long long gtab_total = 0;   // influence tables, one half spectrum per frame
   for (int f = 0; f < F; ++f) {
     FrameDesc& D = p->frames_h[f];
     D.gtab_off = gtab_total;
@@ -643,7 +643,7 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
       A(&p->plist_cnt, ni);
     }
   }
-  if (p->opts.influence_kind == 1) A(&p->gtab, size_t(gtab_total));
+  if (p->opts.recip_method == 0) A(&p->gtab, size_t(gtab_total));
   A(&p->in_saved, 7 * ni);
   A(&p->in_flags, 2);
   if (st == PME_OK) {
@@ -777,7 +777,7 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
     for (cufftHandle h : {G.r2c, G.c2r, G.r2c2, G.c2r2})
       if ((st = check_fft(p, cufftSetWorkArea(h, p->fft_work), "cufftSetWorkArea"))) return st;
   }
-  if (p->gtab && ((st = launch_p3m_tables(p, 0)) || (st = check_cuda(p, cudaDeviceSynchronize(), "synchronize"))))
+  if (p->gtab && ((st = launch_influence_tables(p, 0)) || (st = check_cuda(p, cudaDeviceSynchronize(), "synchronize"))))
     return st;
   p->graphs = new (std::nothrow) PassGraph[2];
   if (!p->graphs) return set_error(p, PME_ERR_NOMEM, "host tables");
@@ -1208,7 +1208,7 @@ int pme_plan_set_box(pme_plan_t p, const double box[9]) {
   p->fwd_n = -1;   // the saved forward belongs to the old box
   drop_graphs(p);  // recorded passes carry the old geometry
   std::memcpy(p->box, box, sizeof(double) * 9);
-  if (p->gtab && ((st = launch_p3m_tables(p, 0)) || (st = check_cuda(p, cudaDeviceSynchronize(), "synchronize"))))
+  if (p->gtab && ((st = launch_influence_tables(p, 0)) || (st = check_cuda(p, cudaDeviceSynchronize(), "synchronize"))))
     return st;
   if (nc > p->total_cells) {
     cudaFree(p->sb.count_c);
