@@ -158,6 +158,22 @@ def dist_setup():
     return ws, rank, local
 
 
+def slowest_rank_ms(local_ms: float, ws: int, device) -> float:
+    """The largest of the ranks' times (the job ends when its slowest replica does)."""
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ions_per_rank: int, ws: int, ms_per_step: float) -> float:
+    """Whole-job throughput in Mion-evals/s: the ions all ranks processed per step over the
+    slowest rank's step time."""
+    return ws * ions_per_rank / (ms_per_step / 1e3) / 1e6
+
+
 def build_frame(name: str):
     import workloads as W
     fr, cfg = W.workload(name)
@@ -503,11 +519,8 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
     total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, stops))
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_per_step = float(t.item()) / args.steps
-    value = ws * n / (ms_per_step / 1e3) / 1e6
+    ms_per_step = slowest_rank_ms(total_ms, ws, dev) / args.steps
+    value = job_rate(n, ws, ms_per_step)
 
     # ---- per-kernel times: the same K steps with the pair term on the call's stream ---------
     # (stage events then bracket one kernel at a time; the overlapped run above is the value)
@@ -544,11 +557,8 @@ def run_ours(args):
         out = plan.forward(hp[0], hp[1], hp[2])
         back = plan.backward(hp[0], hp[1], hp[2], hE, hp[3], hp[4], hp[5])
         e_ms += (time.perf_counter() - t0) * 1e3
-    e_ms /= args.steps
-    e = torch.tensor([e_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(e, op=dist.ReduceOp.MAX)
-    e_value = ws * n / (float(e.item()) / 1e3) / 1e6
+    e_ms = slowest_rank_ms(e_ms / args.steps, ws, dev)
+    e_value = job_rate(n, ws, e_ms)
     h2d = 2 * (12 + 4 + 12) * n + (12 + 4 + 12) * n + 8
     d2h = 8 + (12 + 4 + 12) * n + (12 + 4 + 12) * n
     clocks = sampler.stop()
