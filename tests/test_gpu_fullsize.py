@@ -1,4 +1,4 @@
-"""Full-size parity in the launch configurations the benchmark times.
+"""Full-size parity in the launch configurations the benchmark times, and at 262144 ions.
 
 * The 32768-ion molten-NaCl frame (L = 102 A, 128^3 mesh, order 6, alpha 0.30 / A,
   rcut 9 A) through a default plan (pair term on the plan's second stream), forward and
@@ -15,7 +15,7 @@ import torch
 import workloads as W
 from oracle import pme as O2
 
-from gpu_util import TOL_E, TOL_F, TOL_HVP, f32, prepared, relrmse, sym6
+from gpu_util import TOL_E, TOL_F, TOL_HVP, TOL_MESH, f32, prepared, relmax, relrmse, sym6
 
 pytestmark = pytest.mark.gpu
 
@@ -125,3 +125,95 @@ def test_batch256_energies_match_single_frame_plans(gb, batch256):
         assert abs(e_b[f] - e) < 1e-6 * abs(e), f
         sp.close()
     bp.close()
+
+
+# ---- the 262144-ion frame (L = 204 A, 256^3, p = 6): the mesh stages over the whole mesh,
+# the gather and the pair term at sampled ions, and the backward through properties that
+# hold at any size (a Hessian is symmetric; the energy-only cotangent gives the gradient) ----
+
+@pytest.fixture(scope="module")
+def frame262k():
+    fr, cfg = W.workload("nacl262k")
+    pos, q, mu = prepared(fr)
+    return fr, cfg, pos, q, mu
+
+
+def _sampled_pairs(pos, L, rcut, sample):
+    """(i, j, shift) of every partner j within rcut of each sampled ion i (minimum image:
+    rcut < L / 2), in the oracle's pair convention r_ij = pos_i - pos_j + shift."""
+    I, J, S = [], [], []
+    for i in sample:
+        d = pos[i] - pos
+        sh = -L * np.round(d / L)
+        r2 = ((d + sh) ** 2).sum(1)
+        js = np.nonzero((r2 < rcut * rcut) & (np.arange(len(pos)) != i))[0]
+        I.append(np.full(len(js), i))
+        J.append(js)
+        S.append(sh[js])
+    return np.concatenate(I), np.concatenate(J), np.concatenate(S)
+
+
+def test_262k_mesh_stages_match_oracle(gb, frame262k):
+    fr, cfg, pos, q, mu = frame262k
+    plan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=fr.n)
+    o = O2.PMEOracle(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"])
+    # spread over the whole mesh
+    rho = plan.spread(_c(pos), _c(q), _c(mu)).cpu().numpy()
+    rho_ref = o.stage_mesh(pos, q, mu)
+    assert relmax(rho, rho_ref) < TOL_MESH
+    # solve over the whole mesh, from the same (float32) density
+    rho32 = np.asarray(np.float32(rho_ref), np.float64)
+    Phi_ref, E_ref = o.stage_solve(rho32)
+    Phi, E = plan.solve(torch.tensor(np.float32(rho_ref), device="cuda"))
+    assert relmax(Phi.cpu().numpy(), Phi_ref) < TOL_MESH
+    assert abs(E.item() - E_ref) < TOL_E * abs(E_ref)
+    # gather of that potential at sampled ions
+    sample = np.random.default_rng(7).choice(fr.n, 64, replace=False)
+    out = plan.gather(_c(pos), torch.tensor(np.float32(Phi_ref), device="cuda")).cpu().numpy()[sample]
+    phi, g, H = o.stage_gather(pos[sample], np.asarray(np.float32(Phi_ref), np.float64))
+    assert relmax(out[:, 0], phi) < TOL_MESH
+    assert relmax(out[:, 1:4], g) < TOL_MESH
+    assert relmax(out[:, 4:10], sym6(H)) < TOL_MESH
+    plan.close()
+
+
+def test_262k_pair_term_at_sampled_ions(gb, frame262k):
+    fr, cfg, pos, q, mu = frame262k
+    plan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=fr.n)
+    out, _ = plan.pair(_c(pos), _c(q), _c(mu))
+    sample = np.random.default_rng(8).choice(fr.n, 48, replace=False)
+    o = O2.PMEOracle(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"])
+    pairs = _sampled_pairs(pos, fr.box[0, 0], cfg["rcut"], sample)
+    phi, g, H = o._derivs(lambda P: o.pair_potential(P, pos, q, mu, pairs), pos)
+    got = out.cpu().numpy()[sample]
+    assert relmax(got[:, 0], phi[sample]) < TOL_MESH
+    assert relmax(got[:, 1:4], g[sample]) < TOL_MESH
+    assert relmax(got[:, 4:10], sym6(H[sample])) < TOL_MESH
+    plan.close()
+
+
+def test_262k_backward_properties(gb, frame262k):
+    fr, cfg, pos, q, mu = frame262k
+    n = fr.n
+    plan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=n)
+    P, Q, MU = _c(pos), _c(q), _c(mu)
+    zero3, zero1 = torch.zeros((n, 3), device="cuda"), torch.zeros(n, device="cuda")
+    f64 = lambda x: torch.tensor([x], dtype=torch.float64, device="cuda")
+    # energy-only cotangent: the gradient of E, i.e. (-force, phi, -field) of the forward
+    fw = plan.forward(P, Q, MU)
+    gp, gq, gm = plan.backward(P, Q, MU, f64(1.0), zero3, zero1, zero3)
+    assert relrmse(gp.cpu().numpy(), -fw["force"].cpu().numpy()) < 1e-6
+    assert relrmse(gq.cpu().numpy(), fw["phi"].cpu().numpy()) < 1e-6
+    assert relrmse(gm.cpu().numpy(), -fw["field"].cpu().numpy()) < 1e-6
+    # force cotangents v and w: grad_pos = -H v; the Hessian of E is symmetric, so
+    # w . (H v) = v . (H w)
+    rng = np.random.default_rng(9)
+    v = torch.tensor(np.float32(rng.normal(size=(n, 3))), device="cuda")
+    w = torch.tensor(np.float32(rng.normal(size=(n, 3))), device="cuda")
+    Hv = plan.backward(P, Q, MU, f64(0.0), v, zero1, zero3)[0].double()
+    Hw = plan.backward(P, Q, MU, f64(0.0), w, zero1, zero3)[0].double()
+    a = float((w.double() * Hv).sum())
+    b = float((v.double() * Hw).sum())
+    scale = float(w.double().norm() * Hv.norm())
+    assert abs(a - b) < 1e-5 * scale
+    plan.close()
