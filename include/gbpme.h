@@ -253,7 +253,9 @@ long long pme_launch_count(void);
  * stage + PME_STAGES_PER_PASS * pass, pass 0 = forward, 1 = backward, with stage
  * 0 sort, 1 spread, 2 FFT R2C, 3 influence, 4 FFT C2R, 5 gather, 6 pair (all of it),
  * 7 combine (with the forward's energy reduction), 8 pair evaluation from the hit lists
- * alone (a part of stage 6). At most 4096 stage executions are recorded between two reads. */
+ * alone (a part of stage 6). At most 4096 stage executions are recorded between two reads.
+ * While the timers are on, each timed stage is also an NVTX range named "fwd.spread" etc.,
+ * for timeline profilers. */
 #define PME_STAGES_PER_PASS 9
 #define PME_NUM_STAGES 18
 int pme_profile_enable(pme_plan_t plan, int enable);
