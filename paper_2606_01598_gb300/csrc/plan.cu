@@ -312,11 +312,17 @@ static void free_plan(pme_plan_t p) {
   delete p;
 }
 
+// A failed allocation is reported as PME_ERR_NOMEM and its error is cleared from the runtime,
+// so that later launch checks (of this or another plan) do not mistake it for their own.
 template <typename T>
 static int dalloc(pme_plan_t p, T** ptr, size_t count) {
   *ptr = nullptr;
-  return check_cuda(p, cudaMalloc(reinterpret_cast<void**>(ptr), sizeof(T) * std::max<size_t>(count, 1)),
-                    "cudaMalloc");
+  const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), sizeof(T) * std::max<size_t>(count, 1));
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+  }
+  return check_cuda(p, e, "cudaMalloc");
 }
 
 // Count / start arrays of the sort: n + 1 entries padded to a multiple of 4 (the scan moves
