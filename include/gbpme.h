@@ -27,11 +27,9 @@
  *     float32, q/phi [n] float32, field_grad [n][6] float32 ordered xx, yy, zz, xy, xz, yz.
  *   - Outputs are WRITTEN, never accumulated into.
  *   - Pointers to per-ion arrays and to energies may be device pointers or host pointers
- *     (pinned or pageable); the library asks the CUDA runtime which one it is. Pinned host
- *     memory that the device can address (unified addressing) is read and written in place
- *     by the kernels; other host arrays are staged through plan-owned device buffers with
- *     cudaMemcpyAsync on the call's stream. Host outputs are complete when the stream is
- *     synchronised, and host inputs must not change until then.
+ *     (pinned or pageable); the library asks the CUDA runtime which one it is and stages
+ *     host arrays through plan-owned device buffers with cudaMemcpyAsync on the call's
+ *     stream. Host outputs are complete when the stream is synchronised.
  *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.
  *     Calls are asynchronous on that stream. A plan must not be used by two calls that
  *     overlap in time (its scratch buffers are shared); use one plan per stream.

@@ -166,28 +166,6 @@ static bool frame_geometry(Geometry& g, const double* box, double rcut, bool pai
 
 // ---- host-pointer staging ------------------------------------------------------------------
 
-// Where a caller's array lives: device (or managed) memory; pinned host memory the device can
-// address directly (with unified addressing, through the device-side address the runtime
-// reports: the kernels then read and write it in place, over NVLink-C2C on Grace systems);
-// or other host memory, which is staged through plan-owned device buffers.
-enum class Where { kDevice, kMappedHost, kHost };
-
-static Where classify(const void* ptr, const void** dev_ptr) {
-  *dev_ptr = ptr;
-  if (!ptr) return Where::kDevice;
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
-    cudaGetLastError();
-    return Where::kHost;
-  }
-  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return Where::kDevice;
-  if (at.type == cudaMemoryTypeHost && at.devicePointer) {
-    *dev_ptr = at.devicePointer;
-    return Where::kMappedHost;
-  }
-  return Where::kHost;
-}
-
 static bool is_device_pointer(const void* ptr) {
   if (!ptr) return true;
   cudaPointerAttributes at;
@@ -214,15 +192,12 @@ struct Staging {
     size_t bytes;
   };
   std::vector<Pending> outs;
-  bool staged = false;   // some argument is copied through the staging buffers
+  bool staged = false;   // some argument is a host pointer
 
   Staging(pme_plan_t p_, cudaStream_t s_, int n_) : p(p_), s(s_), n(n_) {}
 
   const float* in(const float* ptr, int width, int slot) {
-    const void* dp;
-    const Where w = classify(ptr, &dp);
-    if (w == Where::kDevice) return ptr;
-    if (w == Where::kMappedHost) return static_cast<const float*>(dp);
+    if (!ptr || is_device_pointer(ptr)) return ptr;
     staged = true;
     float* d = p->stage_f + size_t(slot) * p->max_ions;
     const size_t bytes = sizeof(float) * size_t(width) * n;
@@ -233,10 +208,7 @@ struct Staging {
   // count doubles (per-frame energies / cotangents / virials); slot 0 = outputs, 1 = inputs,
   // 2 = virials (9 per frame)
   const double* in_d(const double* ptr, int count, int slot) {
-    const void* dp;
-    const Where w = classify(ptr, &dp);
-    if (w == Where::kDevice) return ptr;
-    if (w == Where::kMappedHost) return static_cast<const double*>(dp);
+    if (!ptr || is_device_pointer(ptr)) return ptr;
     staged = true;
     double* d = p->stage_d + size_t(slot) * p->nframes;
     if (status == PME_OK)
@@ -245,20 +217,14 @@ struct Staging {
     return d;
   }
   float* out(float* ptr, int width, int slot) {
-    const void* dp;
-    const Where w = classify(ptr, &dp);
-    if (w == Where::kDevice) return ptr;
-    if (w == Where::kMappedHost) return const_cast<float*>(static_cast<const float*>(dp));
+    if (!ptr || is_device_pointer(ptr)) return ptr;
     staged = true;
     float* d = p->stage_f + size_t(slot) * p->max_ions;
     outs.push_back({ptr, d, sizeof(float) * size_t(width) * n});
     return d;
   }
   double* out_d(double* ptr, int count, int slot) {
-    const void* dp;
-    const Where w = classify(ptr, &dp);
-    if (w == Where::kDevice) return ptr;
-    if (w == Where::kMappedHost) return const_cast<double*>(static_cast<const double*>(dp));
+    if (!ptr || is_device_pointer(ptr)) return ptr;
     staged = true;
     double* d = p->stage_d + size_t(slot) * p->nframes;
     outs.push_back({ptr, d, sizeof(double) * count});
