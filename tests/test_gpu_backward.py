@@ -105,10 +105,21 @@ def test_backward_host_pointer_path(gb):
     c = lambda x: torch.tensor(np.float32(x), device="cuda")
     gE = torch.tensor([0.3], dtype=torch.float64)
     d = plan.backward(c(pos), c(q), c(mu), gE.cuda(), c(gF), c(gphi), c(gfield))
+    # pinned and pageable host arrays, both staged through the plan's buffers
     h = plan.backward(*(c(x).cpu().pin_memory() for x in (pos, q, mu)), gE.pin_memory(),
                       *(c(x).cpu().pin_memory() for x in (gF, gphi, gfield)))
     for x, y in zip(d, h):
         assert torch.equal(x.cpu(), y)
+    pg = plan.backward(*(c(x).cpu() for x in (pos, q, mu)), gE,
+                       *(c(x).cpu() for x in (gF, gphi, gfield)))
+    for x, y in zip(d, pg):
+        assert torch.equal(x.cpu(), y)
+    # and the forward the same way
+    fd = plan.forward(c(pos), c(q), c(mu))
+    for hx in ((c(x).cpu().pin_memory() for x in (pos, q, mu)), (c(x).cpu() for x in (pos, q, mu))):
+        fh = plan.forward(*hx)
+        for k in fd:
+            assert torch.equal(fd[k].cpu(), fh[k]), k
 
 
 @pytest.mark.parametrize("name", list(CASES))
