@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(kConvPlaneThreads) k_conv_c2r(ConvArgs a) {
   plane_setup(a, F, csm, twz, twy, b0, b1);
   const int np = (Ny + 1) >> 1, Zs = Nz | 1, Sw = pc * Nzh;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const float rnz = 1.f / float(Nz), rny = 1.f / float(Ny), rnzh = 1.f / float(Nzh), rnp = 1.f / float(np);
+  const float rny = 1.f / float(Ny), rnzh = 1.f / float(Nzh), rnp = 1.f / float(np);
   const float2* src = a.spec + (copy ? F.tspec_off : F.spec_off) + size_t(x0) * Ny * Nzh;
   const int total = pc * Ny * Nzh;
   for (int t0 = threadIdx.x; t0 < total; t0 += kLoadBatch * blockDim.x) {
