@@ -371,7 +371,7 @@ class PMEOracle:
         E, parts = self.energy(pos_t, q_t, mu_t, pairs, parts=True)
         gr, gq, gm = torch.autograd.grad(E, (pos_t, q_t, mu_t))
         out = dict(energy=float(E.detach()), force=(-gr).numpy(), phi=gq.numpy(), field=(-gm).numpy())
-        out.update({k: float(v) for k, v in parts.items()})
+        out.update({k: float(v.detach()) if torch.is_tensor(v) else float(v) for k, v in parts.items()})
         if field_grad:
             out["field_grad"] = self.field_gradient(np.asarray(pos, np.float64), np.asarray(q, np.float64),
                                                     np.asarray(mu_t.detach().numpy()), pairs)
