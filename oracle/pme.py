@@ -36,6 +36,13 @@ paper's outputs), is evaluated from its definition by central differences of the
 and pinned against a term-by-term evaluation and the scaling identity
 tr W = E_qq + 2 E_qmu + 3 E_mumu of the exact (O1) Ewald sum.
 
+Point quadrupoles (an extension: the paper names the rank-2 channel as future work) enter
+the spread as Theta : grad grad W, the pair term through the quadrupole contractions of
+grad^2..grad^4 psi, and the self energy through the quadrupole parts of the Gaussian-cloud
+self interaction (readings stated in oracle/quadrupole.py); their pins are in
+tests/test_oracle_quadrupole.py (against O1Q, the charge-cluster limit on the mesh, and
+mesh refinement).
+
 Pins (tests/test_oracle_pme.py): agreement with O1 within the mesh error, which falls with
 mesh refinement and with order and is larger without deconvolution; the two forms of Eq.
 energy_recip; the dipole as the limit of a charge pair; exact invariance under whole-mesh-
@@ -207,8 +214,13 @@ class PMEOracle:
             out.append((idx, w, dw))
         return out
 
-    def mesh_density(self, pos, q, mu):
-        """rho_mesh of Eq. charge_dipole_assign as a flat torch tensor [Nx*Ny*Nz]."""
+    def mesh_density(self, pos, q, mu, theta=None):
+        """rho_mesh of Eq. charge_dipole_assign as a flat torch tensor [Nx*Ny*Nz].
+
+        With theta ([n,3,3] symmetric point quadrupoles, the rank-2 extension) each ion also
+        adds Theta : grad grad W, the second derivative of its weights with respect to its
+        position: sum_ab Theta'_ab d_a d_b W in mesh coordinates, with
+        Theta'_ab = N_a N_b (C^-T Theta C^-1)_ab."""
         Nx, Ny, Nz = self.N
         (ix, wx, dx), (iy, wy, dy), (iz, wz, dz) = self._stencils(pos)
         dmu = (mu @ _t(self.Cinv)) * _t(np.array(self.N, np.float64))   # N_a (mu . C^-1_{:a})
@@ -216,6 +228,22 @@ class PMEOracle:
                + dmu[:, 0, None, None, None] * dx[:, :, None, None] * wy[:, None, :, None] * wz[:, None, None, :]
                + dmu[:, 1, None, None, None] * wx[:, :, None, None] * dy[:, None, :, None] * wz[:, None, None, :]
                + dmu[:, 2, None, None, None] * wx[:, :, None, None] * wy[:, None, :, None] * dz[:, None, None, :])
+        if theta is not None:
+            s = pos @ _t(self.Cinv)
+            x = s * _t(np.array(self.N, np.float64))
+            d2 = [bspline.stencil_weights(self.p, x[:, a], 2)[1] for a in range(3)]
+            G = _t(self.Cinv * np.array(self.N, np.float64)[None, :])   # G[alpha, a] = N_a C^-1[alpha, a]
+            Tp = torch.einsum("ka,ikl,lb->iab", G, theta, G)
+            one = [wx, wy, wz]
+            der1 = [dx, dy, dz]
+            for a in range(3):
+                for b in range(3):
+                    f = []
+                    for c in range(3):
+                        order = (a == c) + (b == c)
+                        f.append(one[c] if order == 0 else (der1[c] if order == 1 else d2[c]))
+                    val = val + Tp[:, a, b, None, None, None] * (
+                        f[0][:, :, None, None] * f[1][:, None, :, None] * f[2][:, None, None, :])
         flat = (ix[:, :, None, None] * Ny + iy[:, None, :, None]) * Nz + iz[:, None, None, :]
         rho = torch.zeros(Nx * Ny * Nz, dtype=f64)
         return rho.index_put((flat.reshape(-1),), val.reshape(-1), accumulate=True)
@@ -255,7 +283,7 @@ class PMEOracle:
             B.append(((2 * l - 1) * B[-1] + (2 * alpha * alpha) ** l * ex / (alpha * SQRT_PI)) / r2)
         return B
 
-    def pair_energy(self, pos, q, mu, pairs=None):
+    def pair_energy(self, pos, q, mu, pairs=None, theta=None):
         if pairs is None:
             pairs = self._pairs(pos.detach().numpy())
         i, j, sh = pairs
@@ -263,21 +291,50 @@ class PMEOracle:
         j = torch.as_tensor(j)
         r = pos[i] - pos[j] + _t(sh)
         r2 = (r * r).sum(-1)
-        B0, B1, B2 = self._bfuncs(r2, self.alpha, 2)
+        B = self._bfuncs(r2, self.alpha, 2 if theta is None else 4)
+        B0, B1, B2 = B[:3]
         mir = (mu[i] * r).sum(-1)
         mjr = (mu[j] * r).sum(-1)
         u = (q[i] * q[j] * B0 + (q[i] * mjr - q[j] * mir) * B1
              + (mu[i] * mu[j]).sum(-1) * B1 - mir * mjr * B2)
+        if theta is not None:
+            # quadrupole terms of (q_i + mu_i.grad + Th_i:grad grad)(q_j - mu_j.grad + Th_j:grad grad)
+            # psi, each a contraction of grad^n psi written out with the B_l:
+            #   A : grad^2 psi         = -tr A B1 + (r.A.r) B2
+            #   m . grad^3 psi : A     = (tr A (m.r) + 2 m.A.r) B2 - (r.A.r)(m.r) B3
+            #   A : grad^4 psi : C     = (tr A tr C + 2 A:C) B2
+            #                            - (tr A (r.C.r) + tr C (r.A.r) + 4 (A r).(C r)) B3
+            #                            + (r.A.r)(r.C.r) B4
+            B3, B4 = B[3], B[4]
+            Ti, Tj = theta[i], theta[j]
+            tri = torch.einsum("paa->p", Ti)
+            trj = torch.einsum("paa->p", Tj)
+            Tir = torch.einsum("pab,pb->pa", Ti, r)
+            Tjr = torch.einsum("pab,pb->pa", Tj, r)
+            rTir = (Tir * r).sum(-1)
+            rTjr = (Tjr * r).sum(-1)
+            u = u + (q[i] * (-trj * B1 + rTjr * B2) + q[j] * (-tri * B1 + rTir * B2))
+            u = u + ((trj * mir + 2 * (mu[i] * Tjr).sum(-1)) * B2 - rTjr * mir * B3)
+            u = u - ((tri * mjr + 2 * (mu[j] * Tir).sum(-1)) * B2 - rTir * mjr * B3)
+            u = u + ((tri * trj + 2 * (Ti * Tj).sum((-1, -2))) * B2
+                     - (tri * rTjr + trj * rTir + 4 * (Tir * Tjr).sum(-1)) * B3 + rTir * rTjr * B4)
         return 0.5 * u.sum()
 
     # -- total energy -------------------------------------------------------------------
-    def energy(self, pos, q, mu, pairs=None, parts=False):
-        rho = self.mesh_density(pos, q, mu)
+    def energy(self, pos, q, mu, pairs=None, parts=False, theta=None):
+        quad = {} if theta is None else dict(theta=theta)
+        rho = self.mesh_density(pos, q, mu, **quad)
         E_rec = self.recip_energy(rho)
-        E_pair = self.pair_energy(pos, q, mu, pairs) if self.include_pair else pos.sum() * 0.0
+        E_pair = self.pair_energy(pos, q, mu, pairs, **quad) if self.include_pair else pos.sum() * 0.0
         a = self.alpha
         E_self = (-(a / SQRT_PI) * (q * q).sum() - (2 * a ** 3 / (3 * SQRT_PI)) * (mu * mu).sum()) \
             if self.include_self else q.sum() * 0.0
+        if theta is not None and self.include_self:
+            # quadrupole parts of -1/2 sum_i [L_i L_i' erf(alpha r)/r] at r -> 0, from
+            # erf(x)/x = (2/sqrt(pi))(1 - x^2/3 + x^4/10 - ...)
+            tr = torch.einsum("iaa->i", theta)
+            E_self = E_self - (a / SQRT_PI) * (-(4 * a * a / 3) * (q * tr).sum()
+                                                + (4 * a ** 4 / 5) * ((tr * tr).sum() + 2 * (theta * theta).sum()))
         Q = q.sum()
         E_bg = (-math.pi * Q * Q / (2 * self.V * a * a)) if self.include_bg else Q * 0.0
         E = self.k * (E_rec + E_pair + E_self + E_bg)
@@ -377,6 +434,24 @@ class PMEOracle:
                                                     np.asarray(mu_t.detach().numpy()), pairs)
         return out
 
+    def evaluate_quad(self, pos, q, mu, theta, *, pairs=None):
+        """Energy and per-ion derivatives with point quadrupoles theta [n,3,3] (numpy float64):
+        force = -dE/dr, phi = dE/dq, field = -dE/dmu, field_grad = -dE/dTheta, the symmetric
+        matrix G with dE = -G : dTheta for every symmetric dTheta (it reduces to the field
+        gradient of all other sources when theta = 0)."""
+        pos_t = _t(pos).requires_grad_(True)
+        q_t = _t(q).requires_grad_(True)
+        mu_t = _t(np.zeros_like(pos) if mu is None else mu).requires_grad_(True)
+        th_t = _t(theta).requires_grad_(True)
+        if pairs is None and self.include_pair:
+            pairs = self._pairs(np.asarray(pos, np.float64))
+        E, parts = self.energy(pos_t, q_t, mu_t, pairs, parts=True, theta=th_t)
+        gr, gq, gm, gt = torch.autograd.grad(E, (pos_t, q_t, mu_t, th_t))
+        out = dict(energy=float(E.detach()), force=(-gr).numpy(), phi=gq.numpy(),
+                   field=(-gm).numpy(), field_grad=(-0.5 * (gt + gt.transpose(1, 2))).numpy())
+        out.update({k: float(v.detach()) for k, v in parts.items()})
+        return out
+
     def hvp(self, pos, q, mu, g_energy, g_force, g_phi, g_field, pairs=None):
         """Vector-Jacobian product of (pos, q, mu) -> (E, force, phi, field) with the given
         cotangents, by double backward. Returns (grad_pos, grad_q, grad_mu) as numpy."""
@@ -393,9 +468,10 @@ class PMEOracle:
         return a.numpy(), b.numpy(), c.numpy()
 
     # -- stage-level helpers (per-kernel parity) ------------------------------------------
-    def stage_mesh(self, pos, q, mu) -> np.ndarray:
+    def stage_mesh(self, pos, q, mu, theta=None) -> np.ndarray:
         with torch.no_grad():
-            return self.mesh_density(_t(pos), _t(q), _t(mu)).reshape(self.N).numpy()
+            th = None if theta is None else _t(theta)
+            return self.mesh_density(_t(pos), _t(q), _t(mu), th).reshape(self.N).numpy()
 
     def stage_solve(self, rho: np.ndarray):
         """Returns (Phi mesh, E_recip) for a given mesh density (no coulomb_k factor)."""

@@ -113,3 +113,63 @@ def test_wrong_real_space_field_sign_is_caught(monkeypatch):
         return E, phi, -field, fg
     monkeypatch.setattr(ewald, "real_space", bad)
     _fails(TE.test_derivatives_central_differences)
+
+
+# ---- the quadrupole extension (O1Q and O2 with theta) ---------------------------------
+
+import test_oracle_quadrupole as TQ  # noqa: E402
+from oracle import quadrupole as O1Q  # noqa: E402
+
+
+@pytest.fixture
+def small_quad():
+    fr = W.rocksalt(1, 5.64, jitter=0.25, mu_sigma=0.1, seed=21)
+    return fr, W.quadrupoles(fr.n, 0.1, seed=22)
+
+
+def test_quadrupole_self_factor_is_caught(monkeypatch, small_quad):
+    # Theta:Theta with weight 1 instead of 2 in the Gaussian-cloud self energy
+    orig = O1Q.self_energy
+
+    def bad(q, mu, theta, alpha):
+        E, dq, dmu, dT = orig(q, mu, theta, alpha)
+        c = alpha / math.sqrt(math.pi) * (4 * alpha ** 4 / 5)
+        return E + c * np.sum(theta * theta), dq, dmu, dT + 2 * c * theta
+    monkeypatch.setattr(O1Q, "self_energy", bad)
+    _fails(TQ.test_alpha_independence_with_quadrupoles, small_quad)
+
+
+def test_quadrupole_sign_in_structure_factor_is_caught(monkeypatch):
+    # +Theta:kk instead of -Theta:kk in S(k)
+    orig = O1Q.reciprocal
+    monkeypatch.setattr(O1Q, "reciprocal",
+                        lambda pos, q, mu, th, *a, **k: orig(pos, q, mu, -th, *a, **k))
+    _fails(TQ.test_quadrupole_is_limit_of_charge_cluster)
+
+
+def test_quadrupole_mesh_factor_is_caught(monkeypatch):
+    # the mesh sees 2 Theta (a missing 1/2 in the second-moment convention)
+    orig = O2.PMEOracle.mesh_density
+
+    def bad(self, pos, q, mu, theta=None):
+        return orig(self, pos, q, mu, None if theta is None else 2 * theta)
+    monkeypatch.setattr(O2.PMEOracle, "mesh_density", bad)
+    _fails(TQ.test_o2_converges_to_o1q_with_mesh_refinement)
+
+
+def test_quadrupole_pair_cross_sign_is_caught(monkeypatch, small_quad):
+    # mu_j - Theta_i cross term with the wrong sign: the pair energy then sees -mu for
+    # sources j in the Theta_i contraction only
+    orig = O2.PMEOracle.pair_energy
+
+    def bad(self, pos, q, mu, pairs=None, theta=None):
+        if theta is None:
+            return orig(self, pos, q, mu, pairs)
+        e_full = orig(self, pos, q, mu, pairs, theta)
+        e_mu0 = orig(self, pos, q, mu * 0, pairs, theta)
+        e_th0 = orig(self, pos, q, mu, pairs, None)
+        e_both0 = orig(self, pos, q, mu * 0, pairs, None)
+        # flip the whole mu-theta coupling
+        return e_full - 2 * (e_full - e_mu0 - e_th0 + e_both0)
+    monkeypatch.setattr(O2.PMEOracle, "pair_energy", bad)
+    _fails(TQ.test_o2_pair_term_matches_o1q_real_space, small_quad)

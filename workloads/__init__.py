@@ -15,6 +15,7 @@ and value distributions:
                      Gaussian jitter shifted to zero net charge, Gaussian dipoles.
 * ``uneven_frames`` -- a batch of molten-NaCl frames whose ion counts are uniform in
                      [64, 1024], each box scaled so the density stays fixed.
+* ``quadrupoles`` -- Gaussian symmetric point quadrupoles for the rank-2 channel.
 
 Units: Angstrom for lengths, elementary charges for q, e*Angstrom for dipoles.
 All arrays are float64 numpy arrays; callers cast as they need.
@@ -184,6 +185,14 @@ def uneven_frames(n_frames: int = 256, n_min: int = 64, n_max: int = 1024,
         fr = molten_nacl(n, seed=seed * 1000 + f)
         out.append(FrameSpec(frame=fr, spacing=spacing, order=orders[f % len(orders)]))
     return out
+
+
+def quadrupoles(n: int, sigma: float = 0.05, seed: int = 55) -> np.ndarray:
+    """Random symmetric point quadrupoles [n, 3, 3] (e*Angstrom^2): each independent entry
+    of the upper triangle drawn from N(0, sigma^2), mirrored below the diagonal."""
+    rng = np.random.default_rng(seed)
+    A = rng.normal(0.0, sigma, size=(n, 3, 3))
+    return np.triu(A) + np.transpose(np.triu(A, 1), (0, 2, 1))
 
 
 def tangent(n: int, scale: float = 1.0, seed: int = 77):
