@@ -187,6 +187,27 @@ int pme_forward_virial(pme_plan_t plan, void* stream, int n, const float* pos, c
                        const float* mu, double* energy, float* force, float* phi, float* field,
                        float* field_grad, double* virial);
 
+/* Forward with point quadrupoles: the rank-2 multipole channel the paper's concluding
+ * section names as the next extension of its PME layer (an extension beyond the paper's
+ * equations; the readings below are the library's). Each ion carries a symmetric Cartesian
+ * quadrupole Theta, theta [n][6] float32 = (xx, yy, zz, xy, xz, yz), not made traceless,
+ * entering the multipole operator q + mu . grad + Theta : grad grad: the energy of an ion in a
+ * potential phi is q phi + mu . grad phi + Theta : grad grad phi, and a cluster of charges q_c
+ * at offsets d_c with zero net charge and dipole has Theta = 1/2 sum_c q_c d_c d_c. The mesh
+ * density adds Theta : grad grad W (second derivatives of the spline weights, the derivative
+ * terms of Eq. charge_dipole_assign taken one order further), the pair term adds the
+ * quadrupole contractions of grad^2..grad^5 erfc(alpha r)/r, and the self energy adds the
+ * quadrupole parts of the Gaussian-cloud self interaction
+ *   -(alpha/sqrt(pi)) [-(4 alpha^2/3) q tr Theta + (4 alpha^4/5)((tr Theta)^2 + 2 Theta:Theta)].
+ * Outputs as pme_forward, except field_grad = -dE/dTheta (the symmetric matrix G with
+ * dE = -G : dTheta for symmetric dTheta; equal to pme_forward's field gradient when Theta = 0)
+ * and force = -dE/dr including Theta : grad^3 phi. Single-frame plans with recip_method 0;
+ * no CUDA graph, no virial and no backward (a later pme_backward recomputes from its own
+ * inputs). Pointers follow pme_forward's host/device rule. theta may be NULL only when n = 0. */
+int pme_forward_quad(pme_plan_t plan, void* stream, int n, const float* pos, const float* q,
+                     const float* mu, const float* theta, double* energy, float* force, float* phi,
+                     float* field, float* field_grad);
+
 /* ---- batched frames ----------------------------------------------------------------------
  * One plan over F frames stored back to back in the per-ion arrays: frame f owns ions
  * [offsets[f], offsets[f+1]) (offsets[0] = 0, host array of F+1), with its own box

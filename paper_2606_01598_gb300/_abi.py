@@ -42,6 +42,7 @@ _SIGS = {
     "pme_sync_status": (c_int, [c_void_p, c_void_p]),
     "pme_forward": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 8),
     "pme_forward_virial": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 9),
+    "pme_forward_quad": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 9),
     "pme_backward": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 10),
     "pme_spread": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 4),
     "pme_solve": (c_int, [c_void_p, c_void_p] + [c_void_p] * 3),

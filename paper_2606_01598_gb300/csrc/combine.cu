@@ -13,9 +13,19 @@
 // block of kRedItem ions), and the item of each frame that finishes last adds the item sums,
 // the frame's reciprocal-space partials and the background energy in a fixed order.
 //
+// With point quadrupoles Theta (the rank-2 channel; in.theta non-null) the forward also adds
+// the quadrupole self terms: with c5 = 8 alpha^5 / (5 sqrt(pi)),
+//   phi        += k c tr Theta
+//   field_grad  = k (-hess phi_mesh - hess phi_pair - c q I + c5 (tr Theta I + 2 Theta))
+//                                                                      (= -dE/dTheta)
+//   force       = -k (q grad phi + (hess phi) mu + Theta : grad^3 phi)    (mesh + pair parts)
+// and the per-ion energy 1/2 Theta : hess phi_pair + c q tr Theta
+// - (4 alpha^5 / (5 sqrt(pi))) ((tr Theta)^2 + 2 Theta : Theta).
+//
 // Backward, per ion: grad = k (mesh part + pair part) + the self and background terms of
 // the g_E-weighted gradient and of the Hessian-vector product.
 #include <algorithm>
+#include <cmath>
 
 #include "kernels.h"
 
@@ -49,6 +59,11 @@ struct CombineArgs {
   float alpha;
   double e_self_q;    // alpha / sqrt(pi)
   double e_self_mu;   // 2 alpha^3 / (3 sqrt(pi))
+  // quadrupoles (forward; null: none)
+  const float* qout;  // [n][8]: Theta : grad^3 phi of the mesh at 0..2, of the pair term at 4..6
+  float self_c5;      // 8 alpha^5 / (5 sqrt(pi))
+  double e_self_t1;   // 4 alpha^3 / (3 sqrt(pi))
+  double e_self_t2;   // 4 alpha^5 / (5 sqrt(pi))
   // frame energies (forward; energy_out null: not wanted)
   double* energy_out;
   const double* recip_parts;
@@ -107,7 +122,33 @@ __global__ void __launch_bounds__(kCombThreads) k_combine_forward(CombineArgs a)
     const float F0 = qi * fld[0] + fg[0] * mu[0] + fg[3] * mu[1] + fg[4] * mu[2];
     const float F1 = qi * fld[1] + fg[3] * mu[0] + fg[1] * mu[1] + fg[5] * mu[2];
     const float F2 = qi * fld[2] + fg[4] * mu[0] + fg[5] * mu[1] + fg[2] * mu[2];
-    if (a.phi) a.phi[i] = ph;
+    float F0q = 0.f, F1q = 0.f, F2q = 0.f;
+    float ph_q = ph;
+    if (a.in.theta) {
+      const float* th = a.in.theta + size_t(i) * 6;
+      const float T[6] = {th[0], th[1], th[2], th[3], th[4], th[5]};
+      const float trT = T[0] + T[1] + T[2];
+      ph_q = ph + k * a.self_c * trT;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) fg[c] += k * a.self_c5 * ((c < 3 ? trT : 0.f) + 2.f * T[c]);
+      float g[3], H[6], t3[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        g[c] = v[1 + c] + w[1 + c];
+        t3[c] = (a.with_mesh ? a.qout[size_t(i) * 8 + c] : 0.f) + (a.with_pair ? a.qout[size_t(i) * 8 + 4 + c] : 0.f);
+      }
+#pragma unroll
+      for (int c = 0; c < 6; ++c) H[c] = v[4 + c] + w[4 + c];
+      F0q = -k * (qi * g[0] + H[0] * mu[0] + H[3] * mu[1] + H[4] * mu[2] + t3[0]);
+      F1q = -k * (qi * g[1] + H[3] * mu[0] + H[1] * mu[1] + H[5] * mu[2] + t3[1]);
+      F2q = -k * (qi * g[2] + H[4] * mu[0] + H[5] * mu[1] + H[2] * mu[2] + t3[2]);
+      const double TW = double(T[0]) * w[4] + double(T[1]) * w[5] + double(T[2]) * w[6] +
+                        2.0 * (double(T[3]) * w[7] + double(T[4]) * w[8] + double(T[5]) * w[9]);
+      const double TT = double(T[0]) * T[0] + double(T[1]) * T[1] + double(T[2]) * T[2] +
+                        2.0 * (double(T[3]) * T[3] + double(T[4]) * T[4] + double(T[5]) * T[5]);
+      e_i += 0.5 * TW + a.e_self_t1 * double(qi) * trT - a.e_self_t2 * (double(trT) * trT + 2.0 * TT);
+    }
+    if (a.phi) a.phi[i] = ph_q;
     if (a.field) {
       a.field[3 * i] = fld[0];
       a.field[3 * i + 1] = fld[1];
@@ -118,14 +159,14 @@ __global__ void __launch_bounds__(kCombThreads) k_combine_forward(CombineArgs a)
       for (int c = 0; c < 6; ++c) a.field_grad[6 * i + c] = fg[c];
     }
     if (a.force) {
-      a.force[3 * i] = F0;
-      a.force[3 * i + 1] = F1;
-      a.force[3 * i + 2] = F2;
+      a.force[3 * i] = a.in.theta ? F0q : F0;
+      a.force[3 * i + 1] = a.in.theta ? F1q : F1;
+      a.force[3 * i + 2] = a.in.theta ? F2q : F2;
     }
     const double mu2 = double(mu[0]) * mu[0] + double(mu[1]) * mu[1] + double(mu[2]) * mu[2];
-    e_i = 0.5 * (double(qi) * w[0] + double(mu[0]) * w[1] + double(mu[1]) * w[2] +
-                 double(mu[2]) * w[3]) -
-          a.e_self_q * double(qi) * qi - a.e_self_mu * mu2;
+    e_i += 0.5 * (double(qi) * w[0] + double(mu[0]) * w[1] + double(mu[1]) * w[2] +
+                  double(mu[2]) * w[3]) -
+           a.e_self_q * double(qi) * qi - a.e_self_mu * mu2;
     if (a.virial_out) {
 #pragma unroll
       for (int r = 0; r < 3; ++r)
@@ -246,6 +287,9 @@ CombineArgs base_args(pme_plan_t p, const IonInputs& in) {
   a.with_bg = p->opts.include_background ? 1 : 0;
   a.e_self_q = self ? al / sp : 0.0;
   a.e_self_mu = self ? 2.0 * al * al * al / (3.0 * sp) : 0.0;
+  a.self_c5 = self ? float(8.0 * std::pow(al, 5) / (5.0 * sp)) : 0.f;
+  a.e_self_t1 = self ? 4.0 * al * al * al / (3.0 * sp) : 0.0;
+  a.e_self_t2 = self ? 4.0 * std::pow(al, 5) / (5.0 * sp) : 0.0;
   return a;
 }
 
@@ -253,8 +297,10 @@ CombineArgs base_args(pme_plan_t p, const IonInputs& in) {
 
 int launch_combine_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool with_mesh,
                            bool with_pair, float* force, float* phi, float* field,
-                           float* field_grad, double* energy, int recip_kind, double* virial) {
+                           float* field_grad, double* energy, int recip_kind, double* virial,
+                           const float* quad_out) {
   CombineArgs a = base_args(p, in);
+  a.qout = quad_out;
   a.mesh_out = p->mesh_out;
   a.pair_out = p->pair_out;
   a.with_mesh = with_mesh;

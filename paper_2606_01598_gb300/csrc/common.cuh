@@ -239,6 +239,8 @@ struct pme_plan_s {
   gbpme::PairRecords pr;
   float* mesh_out;           // [max_ions][10] per-ion mesh results (caller order)
   float* pair_out;           // [max_ions][10] per-ion pair results
+  float* quad_out = nullptr; // [max_ions][8] quadrupole forward: Theta : grad^3 phi of the mesh
+                             // (0..2) and of the pair term (4..6); single-frame plans
   double* epart;             // reciprocal energy partials, one per influence (or k) block
   double* eitem;             // [items] per-ion energy partials
   // pair lists recorded by the forward for a backward on the same positions
@@ -260,7 +262,7 @@ struct pme_plan_s {
   int* ecount;               // [frames] energy items finished (reset by the last one)
   int* flags;                // device error flags
   // host-pointer staging
-  float* stage_f;            // device staging for host arrays, 34 floats per ion
+  float* stage_f;            // device staging for host arrays, 40 floats per ion
   double* stage_d;           // [2 frames + 2]
   cudaStream_t side;
   cudaEvent_t ev_fork, ev_join;

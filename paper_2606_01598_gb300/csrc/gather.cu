@@ -12,7 +12,10 @@
 // z-column, scales them by its own z-weights, and the group sums the moments with warp
 // shuffles. Forward mode keeps orders <= 2 (potential, gradient, Hessian). Tangent mode
 // (backward pass) keeps orders <= 3 of Phi and <= 2 of the tangent potential dPhi and
-// evaluates the mesh part of the Hessian-vector product in mesh coordinates.
+// evaluates the mesh part of the Hessian-vector product in mesh coordinates. Quadrupole mode
+// (the rank-2 channel) writes the forward outputs and, from the orders-3 moments, the
+// contraction Theta_i : grad^3 phi that the force on a point quadrupole needs:
+// sum_ab Theta_ab d_a d_b d_c phi = (D v)_c with v_k = sum_ij Theta'_ij M_ijk, Theta' = D^T Theta D.
 #include "kernels.h"
 
 namespace gbpme {
@@ -29,6 +32,8 @@ struct GatherArgs {
   const float* mesh;      // Phi of frame f at mesh_off, d Phi at tmesh_off
   const double* g_energy; // per frame
   float* out;
+  const float* theta;     // quadrupole mode: Theta [caller index][6] (xx yy zz xy xz yz)
+  float* qout;            // quadrupole mode: Theta : grad^3 phi at [caller index * 8 + 0..2]
   int t_lo, t_hi;         // sorted positions of this launch
 };
 
@@ -45,9 +50,11 @@ __device__ __forceinline__ void apply_D(const float* D, const float x[3], float 
   for (int a = 0; a < 3; ++a) y[a] = D[a * 3 + 0] * x[0] + D[a * 3 + 1] * x[1] + D[a * 3 + 2] * x[2];
 }
 
-template <int P, bool TAN, bool BATCH>
+// MODE: 0 forward, 1 tangent, 2 quadrupole forward
+template <int P, int MODE, bool BATCH>
 __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
-  constexpr int DM = TAN ? 3 : 2;
+  constexpr bool TAN = MODE == 1;
+  constexpr int DM = MODE == 0 ? 2 : 3;
   const int gid = a.t_lo + (blockIdx.x * blockDim.x + threadIdx.x) / kGroup;
   const int l = threadIdx.x & (kGroup - 1);
   const bool valid = gid < a.t_hi;
@@ -134,7 +141,41 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
   const float m200 = MOM(2, 0, 0), m020 = MOM(0, 2, 0), m002 = MOM(0, 0, 2);
   const float m110 = MOM(1, 1, 0), m101 = MOM(1, 0, 1), m011 = MOM(0, 1, 1);
   if (!TAN) {
+    float m3[10];   // quadrupole mode: 300 030 003 210 201 120 021 102 012 111
+    if constexpr (MODE == 2) {
+      m3[0] = MOM(3, 0, 0); m3[1] = MOM(0, 3, 0); m3[2] = MOM(0, 0, 3);
+      m3[3] = MOM(2, 1, 0); m3[4] = MOM(2, 0, 1); m3[5] = MOM(1, 2, 0);
+      m3[6] = MOM(0, 2, 1); m3[7] = MOM(1, 0, 2); m3[8] = MOM(0, 1, 2);
+      m3[9] = MOM(1, 1, 1);
+    }
     if (!valid || l != 0) return;
+    if constexpr (MODE == 2) {
+      const float* th = a.theta + size_t(m.w) * 6;
+      const float T[3][3] = {{th[0], th[3], th[4]}, {th[3], th[1], th[5]}, {th[4], th[5], th[2]}};
+      float TD[3][3], Tp[3][3];   // Theta D, D^T Theta D
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          TD[r][c] = T[r][0] * g.D[0 * 3 + c] + T[r][1] * g.D[1 * 3 + c] + T[r][2] * g.D[2 * 3 + c];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          Tp[r][c] = g.D[0 * 3 + r] * TD[0][c] + g.D[1 * 3 + r] * TD[1][c] + g.D[2 * 3 + r] * TD[2][c];
+      const float sxy = Tp[0][1] + Tp[1][0], sxz = Tp[0][2] + Tp[2][0], syz = Tp[1][2] + Tp[2][1];
+      // v_k = sum_ij Theta'_ij M_ijk
+      float v[3];
+      v[0] = Tp[0][0] * m3[0] + Tp[1][1] * m3[5] + Tp[2][2] * m3[7] + sxy * m3[3] + sxz * m3[4] + syz * m3[9];
+      v[1] = Tp[0][0] * m3[3] + Tp[1][1] * m3[1] + Tp[2][2] * m3[8] + sxy * m3[5] + sxz * m3[9] + syz * m3[6];
+      v[2] = Tp[0][0] * m3[4] + Tp[1][1] * m3[6] + Tp[2][2] * m3[2] + sxy * m3[9] + sxz * m3[7] + syz * m3[8];
+      float tr[3];
+      apply_D(g.D, v, tr);
+      float* qo = a.qout + size_t(m.w) * 8;
+      qo[0] = tr[0];
+      qo[1] = tr[1];
+      qo[2] = tr[2];
+    }
     const float gx[3] = {m100, m010, m001};
     const float Hx[3][3] = {{m200, m110, m101}, {m110, m020, m011}, {m101, m011, m002}};
     float gr[3];
@@ -235,9 +276,9 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
 #undef TMOM
 }
 
-template <bool TAN, bool BATCH>
+template <int MODE, bool BATCH>
 int launch_t(pme_plan_t p, cudaStream_t s, int n, const float* mesh, const double* g_energy,
-             float* out) {
+             float* out, const float* theta = nullptr, float* qout = nullptr) {
   GatherArgs a;
   a.one = p->frames_h[0];
   a.maps = p->maps;
@@ -245,6 +286,8 @@ int launch_t(pme_plan_t p, cudaStream_t s, int n, const float* mesh, const doubl
   a.mesh = mesh;
   a.g_energy = g_energy;
   a.out = out;
+  a.theta = theta;
+  a.qout = qout;
   for (int gi = 0; gi < p->nogroups; ++gi) {
     const OrderGroup& G = p->ogroups[gi];
     a.t_lo = BATCH ? G.sorted_lo : 0;
@@ -252,13 +295,13 @@ int launch_t(pme_plan_t p, cudaStream_t s, int n, const float* mesh, const doubl
     const int grid = int((size_t(a.t_hi - a.t_lo) * kGroup + kGatherThreads - 1) / kGatherThreads);
     if (grid <= 0) continue;
     switch (G.order) {
-      case 1: k_gather<1, TAN, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
-      case 2: k_gather<2, TAN, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
-      case 3: k_gather<3, TAN, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
-      case 4: k_gather<4, TAN, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
-      case 5: k_gather<5, TAN, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
-      case 6: k_gather<6, TAN, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
-      case 7: k_gather<7, TAN, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
+      case 1: k_gather<1, MODE, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
+      case 2: k_gather<2, MODE, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
+      case 3: k_gather<3, MODE, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
+      case 4: k_gather<4, MODE, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
+      case 5: k_gather<5, MODE, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
+      case 6: k_gather<6, MODE, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
+      case 7: k_gather<7, MODE, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
       default: return set_error(p, PME_ERR_ARG, "spline order out of range");
     }
     count_launch();
@@ -273,10 +316,16 @@ int launch_t(pme_plan_t p, cudaStream_t s, int n, const float* mesh, const doubl
 int launch_gather(pme_plan_t p, cudaStream_t s, int n, const float* mesh, bool tangent,
                   const double* g_energy, float* out) {
   if (p->batch)
-    return tangent ? launch_t<true, true>(p, s, n, mesh, g_energy, out)
-                   : launch_t<false, true>(p, s, n, mesh, nullptr, out);
-  return tangent ? launch_t<true, false>(p, s, n, mesh, g_energy, out)
-                 : launch_t<false, false>(p, s, n, mesh, nullptr, out);
+    return tangent ? launch_t<1, true>(p, s, n, mesh, g_energy, out)
+                   : launch_t<0, true>(p, s, n, mesh, nullptr, out);
+  return tangent ? launch_t<1, false>(p, s, n, mesh, g_energy, out)
+                 : launch_t<0, false>(p, s, n, mesh, nullptr, out);
+}
+
+int launch_gather_quad(pme_plan_t p, cudaStream_t s, int n, const float* mesh, const float* theta,
+                       float* out, float* qout) {
+  if (p->batch) return set_error(p, PME_ERR_UNSUPPORTED, "quadrupoles need a single-frame plan");
+  return launch_t<2, false>(p, s, n, mesh, nullptr, out, theta, qout);
 }
 
 }  // namespace gbpme

@@ -15,6 +15,7 @@ struct IonInputs {
   const float* gforce;  // [n][3] or null: dr = -g_force
   const float* gphi;    // [n] or null:    dq = g_phi
   const float* gfield;  // [n][3] or null: dmu = -g_field
+  const float* theta;   // [n][6] point quadrupoles (xx yy zz xy xz yz) or null (forward only)
   int n;
 };
 
@@ -36,6 +37,9 @@ int launch_input_check(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool w
 // keep_rho (tangent pass, nullable): *keep_rho == 0 means rho is in place from the forward on
 // the same inputs; only d rho is formed and written.
 int launch_spread(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh, const int* keep_rho = nullptr);
+// Quadrupole forward (single-frame plans): rho of charges, dipoles and point quadrupoles
+// theta [caller index][6] into mesh + mesh_off.
+int launch_spread_quad(pme_plan_t p, cudaStream_t s, const float* theta, float* mesh);
 
 // influence.cu: in-place G C / V multiply of every frame's spectrum (and tangent spectrum)
 // and the float64 energy partials (one per block, blocks grouped by frame).
@@ -79,6 +83,13 @@ int launch_conv_inverse(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh,
 //   tangent: out[orig][8]  = mesh part of (grad_r (3), grad_q, grad_mu (3)) of the backward
 int launch_gather(pme_plan_t p, cudaStream_t s, int n, const float* mesh, bool tangent,
                   const double* g_energy, float* out);
+// Quadrupole forward: the forward layout in out, and Theta_i : grad^3 phi at qout[orig][0..2].
+int launch_gather_quad(pme_plan_t p, cudaStream_t s, int n, const float* mesh, const float* theta,
+                       float* out, float* qout);
+
+// quad.cu: real-space pair term with point quadrupoles (single-frame plans): the forward
+// layout of the pair potential of every source in out, Theta_i : grad^3 phi at qout[orig][4..6].
+int launch_pair_quad(pme_plan_t p, cudaStream_t s, int n, const float* theta, float* out, float* qout);
 
 // pair.cu: real-space erfc pair term over the cell list, same output layouts as gather.
 // The fused pass; skip (nullable): return at once when *skip == 0.
@@ -97,10 +108,12 @@ int launch_pair_listed(pme_plan_t p, cudaStream_t s, int n, bool tangent, const 
 // energies of this pass (recip_kind as there).
 // virial (nullable, needs energy): also the frame virials [9] per frame from the plan's
 // k-space sums (vpart) and per-ion pair virials (pvir).
+// With in.theta the quadrupole terms are added (quad_out: the gather's and the pair
+// kernel's Theta : grad^3 phi; no virial).
 int launch_combine_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool with_mesh,
                            bool with_pair, float* force, float* phi, float* field,
                            float* field_grad, double* energy, int recip_kind,
-                           double* virial = nullptr);
+                           double* virial = nullptr, const float* quad_out = nullptr);
 int launch_combine_backward(pme_plan_t p, cudaStream_t s, const IonInputs& in,
                             const double* g_energy, float* grad_pos, float* grad_q,
                             float* grad_mu);

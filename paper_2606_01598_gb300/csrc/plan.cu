@@ -178,7 +178,7 @@ static bool is_device_pointer(const void* ptr) {
 
 enum StageSlot {
   kPos = 0, kQ = 3, kMu = 4, kGF = 7, kGPhi = 10, kGField = 11, kOF = 14, kOPhi = 17,
-  kOField = 18, kOFG = 21, kOGPos = 27, kOGQ = 30, kOGMu = 31, kStageFloats = 34
+  kOField = 18, kOFG = 21, kOGPos = 27, kOGQ = 30, kOGMu = 31, kTheta = 34, kStageFloats = 40
 };
 
 struct Staging {
@@ -285,7 +285,7 @@ static void free_plan(pme_plan_t p) {
                   p->plist, p->plist_cnt, p->in_saved, p->in_flags, p->vpart,
                   p->pvir, p->vitem, p->gtab, p->sb.t_bidx, p->sb.t_bfq,
                   p->sb.t_bdm, p->sb.t_cidx, p->sb.t_cfq, p->sb.t_cmu, p->conv_tw,
-                  p->conv_planes1};
+                  p->conv_planes1, p->quad_out};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int g = 0; g < p->nfgroups; ++g) {
@@ -629,6 +629,7 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
   A(&p->pr.dr, ni);
   A(&p->mesh_out, ni * 10);
   A(&p->pair_out, ni * 10);
+  if (single) A(&p->quad_out, ni * 8);
   A(&p->e_ion, ni);
   A(&p->epart, size_t(p->total_blocks) + 1);
   A(&p->flags, 1);
@@ -1323,6 +1324,59 @@ int pme_forward_virial(pme_plan_t p, void* stream, int n, const float* pos, cons
   float* fg_out = sg.out(field_grad, 6, kOFG);
   if (sg.status) return sg.status;
   if ((st = run_forward(p, s, in, e_out, f_out, p_out, fl_out, fg_out, v_out))) return st;
+  return sg.finish();
+}
+
+// Forward with point quadrupoles (the rank-2 channel): sort, quadrupole spread, the mesh
+// convolution, quadrupole gather, the quadrupole pair kernel, combine. Runs directly (no
+// graph) and leaves nothing for a backward to reuse.
+static int run_forward_quad(pme_plan_t p, cudaStream_t s, const IonInputs& in, double* e_out,
+                            float* f_out, float* p_out, float* fl_out, float* fg_out) {
+  const int n = in.n;
+  const bool pair = p->opts.include_pair != 0;
+  int st;
+  p->fwd_n = -1;
+  p->fwd_lists = false;
+  if ((st = launch_sort(p, s, in, false, true, pair, nullptr))) return st;
+  const bool fork = pair && n > 0;
+  cudaStream_t ps = p->opts.overlap_pair ? p->side : s;
+  if (fork) {
+    if (p->opts.overlap_pair && (st = fork_side(p, s))) return st;
+    if ((st = launch_pair_quad(p, ps, n, in.theta, p->pair_out, p->quad_out))) return st;
+  }
+  if ((st = launch_spread_quad(p, s, in.theta, p->rho))) return st;
+  if ((st = fft_forward(p, s, false))) return st;
+  if ((st = multiply_influence(p, s, false, nullptr))) return st;
+  if ((st = fft_inverse(p, s, false))) return st;
+  if ((st = launch_gather_quad(p, s, n, p->phi, in.theta, p->mesh_out, p->quad_out))) return st;
+  if (fork && p->opts.overlap_pair && (st = join_side(p, s))) return st;
+  return launch_combine_forward(p, s, in, true, fork, f_out, p_out, fl_out, fg_out, e_out, 1, nullptr,
+                                p->quad_out);
+}
+
+int pme_forward_quad(pme_plan_t p, void* stream, int n, const float* pos, const float* q,
+                     const float* mu, const float* theta, double* energy, float* force, float* phi,
+                     float* field, float* field_grad) {
+  int st = check_common(p, n, pos, q);
+  if (st) return st;
+  if (n > 0 && !theta) return set_error(p, PME_ERR_ARG, "theta is NULL");
+  if (p->opts.recip_method != 0)
+    return set_error(p, PME_ERR_UNSUPPORTED, "quadrupoles need the particle-mesh method (recip_method 0)");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Staging sg(p, s, n);
+  IonInputs in{};
+  in.pos = sg.in(pos, 3, kPos);
+  in.q = sg.in(q, 1, kQ);
+  in.mu = sg.in(mu, 3, kMu);
+  in.theta = sg.in(theta, 6, kTheta);
+  in.n = n;
+  double* e_out = sg.out_d(energy, 1, 0);
+  float* f_out = sg.out(force, 3, kOF);
+  float* p_out = sg.out(phi, 1, kOPhi);
+  float* fl_out = sg.out(field, 3, kOField);
+  float* fg_out = sg.out(field_grad, 6, kOFG);
+  if (sg.status) return sg.status;
+  if ((st = run_forward_quad(p, s, in, e_out, f_out, p_out, fl_out, fg_out))) return st;
   return sg.finish();
 }
 

@@ -25,6 +25,10 @@
 //   d rho = sum_i [dq_i + (dmu_i + q_i dr_i) . grad + (mu_i . grad)(dr_i . grad)] W(x_i - m)
 // (gradients with respect to the source position), the directional derivative of rho_mesh
 // along the cotangent direction.
+//
+// Quadrupole mode spreads rho of charges, dipoles and point quadrupoles Theta_i (the rank-2
+// channel), sum_i [q_i + mu_i . grad + Theta_i : grad grad] W(x_i - m): the tangent mode's
+// record layout with (q, mu, Theta) in place of (dq, d', mu (x) dr), written to rho.
 #include "kernels.h"
 
 namespace gbpme {
@@ -42,6 +46,7 @@ constexpr int SL = 2 * NT;                // listed (overlapping) ions held befo
 constexpr int kMaxCand = kMaxCandPerDim * kMaxCandPerDim * kMaxCandPerDim;
 
 struct SpreadArgs {
+  const float* theta;   // quadrupole mode: Theta [caller index][6] (xx yy zz xy xz yz)
   FrameDesc one;
   FrameMaps maps;
   int key_lo;           // first global brick of this launch
@@ -91,8 +96,10 @@ __device__ __forceinline__ int up_dist(int a, int b, int n) {
   return d < 0 ? d + n : d;
 }
 
-template <int P, bool TAN, bool BATCH>
+// MODE: 0 forward, 1 tangent, 2 quadrupole forward
+template <int P, int MODE, bool BATCH>
 __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
+  constexpr bool TAN = MODE != 0;   // record layout with second derivatives
   using RC = Rec<TAN>;
   constexpr int DW = RC::DW;                      // weight derivative orders kept
 
@@ -119,7 +126,7 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
   const int b0x = bx * BX, b0y = by * BY, b0z = bz * BZ;
   const int ex = min(BX, g.N[0] - b0x), ey = min(BY, g.N[1] - b0y), ez = min(BZ, g.N[2] - b0z);
   const int Nx = g.N[0], Ny = g.N[1], Nz = g.N[2];
-  const bool with_rho = !TAN || !a.keep_rho || *a.keep_rho != 0;
+  const bool with_rho = MODE == 0 || (MODE == 1 && (!a.keep_rho || *a.keep_rho != 0));
 
   // ---- (1) candidate source bricks: product of the per-axis lists, in a fixed order ----
   const int* ct = a.cand + F.cand_off;
@@ -221,7 +228,35 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
         for (int k = 0; k < BX * RC::NXV; ++k) rec[RC::XOFF + k] = 0.f;
         const float q = fq.w, mx = dm.x, my = dm.y, mz = dm.z;
         float c4 = 0.f, c5 = 0.f, c6 = 0.f, c7 = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
-        if (TAN) {
+        // quadrupole mode: Theta' = D^T Theta D (mesh coordinates) as xx, 2 xy, yy, 2 xz, 2 yz, zz
+        float t_xx = 0.f, t_xy = 0.f, t_yy = 0.f, t_xz = 0.f, t_yz = 0.f, t_zz = 0.f;
+        if (MODE == 2) {
+          const float* th = a.theta + size_t(a.mr.idx[src].w) * 6;
+          const float T[3][3] = {{th[0], th[3], th[4]}, {th[3], th[1], th[5]}, {th[4], th[5], th[2]}};
+          const float* D = F.g.D;
+          float TD[3][3];   // Theta D
+#pragma unroll
+          for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              TD[r][c] = T[r][0] * D[0 * 3 + c] + T[r][1] * D[1 * 3 + c] + T[r][2] * D[2 * 3 + c];
+          float Tp[3][3];   // D^T Theta D
+#pragma unroll
+          for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              Tp[r][c] = D[0 * 3 + r] * TD[0][c] + D[1 * 3 + r] * TD[1][c] + D[2 * 3 + r] * TD[2][c];
+          c4 = q;
+          c5 = mx;
+          c6 = my;
+          c7 = mz;
+          t_xx = Tp[0][0];
+          t_yy = Tp[1][1];
+          t_zz = Tp[2][2];
+          t_xy = Tp[0][1] + Tp[1][0];
+          t_xz = Tp[0][2] + Tp[2][0];
+          t_yz = Tp[1][2] + Tp[2][1];
+        } else if (TAN) {
           const float4 tq = a.mr.tq[src];
           const float4 tt = a.mr.tt[src];
           c4 = tq.x;
@@ -240,7 +275,15 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
           if (X < BX) {
             const float w0 = w[0][j], w1 = w[1][j];
             float* e = rec + RC::XOFF + X * RC::NXV;
-            if (TAN) {
+            if (MODE == 2) {
+              const float w2 = w[DW - 1][j];
+              e[0] = c4 * w0 + c5 * w1 + t_xx * w2;
+              e[1] = c6 * w0 + t_xy * w1;
+              e[2] = t_yy * w0;
+              e[3] = c7 * w0 + t_xz * w1;
+              e[4] = t_yz * w0;
+              e[5] = t_zz * w0;
+            } else if (TAN) {
               const float w2 = w[DW - 1][j];
               e[0] = c4 * w0 + c5 * w1 + mx * tx * w2;
               e[1] = c6 * w0 + (mx * ty + my * tx) * w1;
@@ -377,7 +420,7 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
   if (X < ex && Y < ey) {
     const size_t off = (size_t(gx) * Ny + gy) * Nz + zs0;
     float* rho = a.mesh + F.mesh_off + off;
-    float* drho = a.mesh + F.tmesh_off + off;
+    float* drho = a.mesh + (MODE == 2 ? F.mesh_off : F.tmesh_off) + off;
     const int nz = min(ZS, ez - seg * ZS);
 #pragma unroll
     for (int z = 0; z < ZS; ++z)
@@ -389,27 +432,28 @@ __global__ void __launch_bounds__(NT) k_spread(SpreadArgs a) {
 }
 
 // One instantiation's launch; the first use on a device raises its dynamic shared-memory limit.
-template <int P, bool TAN, bool BATCH>
+template <int P, int MODE, bool BATCH>
 int launch_order(pme_plan_t p, cudaStream_t s, int grid, const SpreadArgs& a) {
-  constexpr int bytes = spread_smem_bytes<P, TAN>();
+  constexpr int bytes = spread_smem_bytes<P, MODE != 0>();
   static int done_mask = 0;   // devices 0..31 already configured (idempotent if raced)
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 32 || !(done_mask & (1 << dev))) {
-    const int st = check_cuda(p, cudaFuncSetAttribute(k_spread<P, TAN, BATCH>,
+    const int st = check_cuda(p, cudaFuncSetAttribute(k_spread<P, MODE, BATCH>,
                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
                               "cudaFuncSetAttribute");
     if (st) return st;
     if (dev < 32) done_mask |= 1 << dev;
   }
-  k_spread<P, TAN, BATCH><<<grid, NT, bytes, s>>>(a);
+  k_spread<P, MODE, BATCH><<<grid, NT, bytes, s>>>(a);
   return PME_OK;
 }
 
-template <bool TAN, bool BATCH>
-int launch_t(pme_plan_t p, cudaStream_t s, float* mesh, const int* keep_rho) {
+template <int MODE, bool BATCH>
+int launch_t(pme_plan_t p, cudaStream_t s, float* mesh, const int* keep_rho, const float* theta = nullptr) {
   SpreadArgs a;
-  a.keep_rho = TAN ? keep_rho : nullptr;
+  a.theta = theta;
+  a.keep_rho = MODE == 1 ? keep_rho : nullptr;
   a.one = p->frames_h[0];
   a.maps = p->maps;
   a.mr = p->mr;
@@ -423,13 +467,13 @@ int launch_t(pme_plan_t p, cudaStream_t s, float* mesh, const int* keep_rho) {
     a.key_lo = G.brick_lo;
     int st = PME_OK;
     switch (G.order) {
-      case 1: st = launch_order<1, TAN, BATCH>(p, s, grid, a); break;
-      case 2: st = launch_order<2, TAN, BATCH>(p, s, grid, a); break;
-      case 3: st = launch_order<3, TAN, BATCH>(p, s, grid, a); break;
-      case 4: st = launch_order<4, TAN, BATCH>(p, s, grid, a); break;
-      case 5: st = launch_order<5, TAN, BATCH>(p, s, grid, a); break;
-      case 6: st = launch_order<6, TAN, BATCH>(p, s, grid, a); break;
-      case 7: st = launch_order<7, TAN, BATCH>(p, s, grid, a); break;
+      case 1: st = launch_order<1, MODE, BATCH>(p, s, grid, a); break;
+      case 2: st = launch_order<2, MODE, BATCH>(p, s, grid, a); break;
+      case 3: st = launch_order<3, MODE, BATCH>(p, s, grid, a); break;
+      case 4: st = launch_order<4, MODE, BATCH>(p, s, grid, a); break;
+      case 5: st = launch_order<5, MODE, BATCH>(p, s, grid, a); break;
+      case 6: st = launch_order<6, MODE, BATCH>(p, s, grid, a); break;
+      case 7: st = launch_order<7, MODE, BATCH>(p, s, grid, a); break;
       default: return set_error(p, PME_ERR_ARG, "spline order out of range");
     }
     if (st) return st;
@@ -448,8 +492,13 @@ void spread_brick_shape(int shape[3]) {
 
 int launch_spread(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh, const int* keep_rho) {
   if (p->batch)
-    return tangent ? launch_t<true, true>(p, s, mesh, keep_rho) : launch_t<false, true>(p, s, mesh, keep_rho);
-  return tangent ? launch_t<true, false>(p, s, mesh, keep_rho) : launch_t<false, false>(p, s, mesh, keep_rho);
+    return tangent ? launch_t<1, true>(p, s, mesh, keep_rho) : launch_t<0, true>(p, s, mesh, keep_rho);
+  return tangent ? launch_t<1, false>(p, s, mesh, keep_rho) : launch_t<0, false>(p, s, mesh, keep_rho);
+}
+
+int launch_spread_quad(pme_plan_t p, cudaStream_t s, const float* theta, float* mesh) {
+  if (p->batch) return set_error(p, PME_ERR_UNSUPPORTED, "quadrupoles need a single-frame plan");
+  return launch_t<2, false>(p, s, mesh, nullptr, theta);
 }
 
 }  // namespace gbpme

@@ -256,6 +256,42 @@ class Plan:
                 torch.cuda.current_stream(self.device).synchronize()
         return out
 
+    def forward_quad(self, pos, q, mu, theta, *, energy=True, force=True, phi=True, field=True,
+                     field_grad=True):
+        """Forward with point quadrupoles theta [n, 6] (xx, yy, zz, xy, xz, yz) or [n, 3, 3]
+        (pme_forward_quad): field_grad is then -dE/dTheta. Returns a dict of tensors."""
+        dev = pos.device if isinstance(pos, torch.Tensor) else torch.device("cpu")
+        on_dev = dev.type == "cuda"
+        if theta is not None and tuple(theta.shape[-2:]) == (3, 3):
+            t = torch.as_tensor(theta)
+            theta = torch.stack([t[:, 0, 0], t[:, 1, 1], t[:, 2, 2], t[:, 0, 1], t[:, 0, 2], t[:, 1, 2]], 1)
+        pos = _f32(pos, dev)
+        q = _f32(q, dev)
+        mu = _f32(mu, dev)
+        theta = _f32(theta, dev)
+        n = int(pos.shape[0])
+        alloc = dict(device=dev, pin_memory=True) if not on_dev else dict(device=dev)
+        out = {}
+        if energy:
+            out["energy"] = torch.empty(1, dtype=torch.float64, **alloc)
+        if force:
+            out["force"] = torch.empty((n, 3), dtype=torch.float32, **alloc)
+        if phi:
+            out["phi"] = torch.empty(n, dtype=torch.float32, **alloc)
+        if field:
+            out["field"] = torch.empty((n, 3), dtype=torch.float32, **alloc)
+        if field_grad:
+            out["field_grad"] = torch.empty((n, 6), dtype=torch.float32, **alloc)
+        with _on_device(self.device):
+            st = self.lib.pme_forward_quad(self.handle, _stream_handle(self.device), n, _ptr(pos), _ptr(q),
+                                           _ptr(mu), _ptr(theta), _ptr(out.get("energy")),
+                                           _ptr(out.get("force")), _ptr(out.get("phi")),
+                                           _ptr(out.get("field")), _ptr(out.get("field_grad")))
+            self._check(st, "pme_forward_quad")
+            if not on_dev:
+                torch.cuda.current_stream(self.device).synchronize()
+        return out
+
     def backward(self, pos, q, mu=None, g_energy=None, g_force=None, g_phi=None, g_field=None):
         """Vector-Jacobian product of (pos, q, mu) -> (E, force, phi, field)."""
         dev = pos.device if isinstance(pos, torch.Tensor) else torch.device("cpu")

@@ -1,0 +1,134 @@
+"""Parity of pme_forward_quad (charges, dipoles and point quadrupoles: the rank-2 channel)
+against the FP64 oracle O2 with quadrupoles on the same mesh, and of the total against the
+explicit Ewald sum with quadrupoles (O1Q) within the mesh error the oracle itself shows."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import pme as O2
+from oracle import quadrupole as O1Q
+
+from gpu_util import TOL_E, TOL_F, f32, prepared, relrmse, sym6
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2606_01598_gb300 as g
+    return g
+
+
+CASES = {
+    # rock-salt 4x4x4, 512 ions, 32^3, p = 4, rcut 10: the pair term loops over images
+    "rocksalt512": lambda: (W.rocksalt(4, 5.64, jitter=0.1, mu_sigma=0.05, seed=1000),
+                            (32, 32, 32), 4, 0.30, 10.0),
+    # molten NaCl 4096 ions, 64^3, p = 6, rcut 9: several pair cells per axis
+    "nacl4096": lambda: (W.molten_nacl(4096, L=51.0, seed=1001), (64, 64, 64), 6, 0.30, 9.0),
+    # 64 ions in a 12.7 A box: one pair cell per axis, every image inside rcut
+    "nacl64": lambda: (W.molten_nacl(64, seed=1002), (16, 16, 16), 4, 0.30, 9.0),
+    # ragged mesh, odd order
+    "nacl1000_ragged": lambda: (W.molten_nacl(1000, seed=77), (27, 30, 25), 5, 0.35, 8.0),
+}
+
+
+def _ebar(ref):
+    return TOL_E * sum(abs(ref[k]) for k in ("e_recip", "e_pair", "e_self", "e_bg"))
+
+
+def _inputs(name, sigma=0.1):
+    fr, mesh, p, a, rc = CASES[name]()
+    pos, q, mu = prepared(fr)
+    th = f32(W.quadrupoles(fr.n, sigma, seed=300))
+    return fr, mesh, p, a, rc, pos, q, mu, th
+
+
+def _gpu(gb, fr, mesh, p, a, rc, pos, q, mu, th, **kw):
+    plan = gb.Plan(fr.box, mesh, p, a, rc, max_ions=max(1024, len(q)), **kw)
+    t = [torch.tensor(np.float32(x), device="cuda") for x in (pos, q, mu, th)]
+    out = plan.forward_quad(*t)
+    return plan, {k: v.cpu().numpy().astype(np.float64) for k, v in out.items()}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_quad_forward_matches_plain_pme(gb, name):
+    fr, mesh, p, a, rc, pos, q, mu, th = _inputs(name)
+    _, got = _gpu(gb, fr, mesh, p, a, rc, pos, q, mu, th)
+    ref = O2.PMEOracle(fr.box, mesh, p, a, rc).evaluate_quad(pos, q, mu, th)
+    assert abs(got["energy"][0] - ref["energy"]) < _ebar(ref)
+    assert relrmse(got["force"], ref["force"]) < TOL_F
+    assert relrmse(got["phi"], ref["phi"]) < TOL_F
+    assert relrmse(got["field"], ref["field"]) < TOL_F
+    assert relrmse(got["field_grad"], sym6(ref["field_grad"])) < TOL_F
+
+
+def test_quad_options(gb):
+    # no pair term, no self/background, eV units: each toggles the same way as O2
+    base = _inputs("nacl1000_ragged")
+    fr, mesh, p, a, rc, pos, q, mu, th = base
+    for kw in (dict(include_pair=False), dict(include_self=False, include_background=False),
+               dict(coulomb_k=14.3996454784), dict(deconvolution=False)):
+        _, got = _gpu(gb, *base, **kw)
+        ref = O2.PMEOracle(fr.box, mesh, p, a, rc, **kw).evaluate_quad(pos, q, mu, th)
+        assert abs(got["energy"][0] - ref["energy"]) < _ebar(ref), kw
+        assert relrmse(got["force"], ref["force"]) < TOL_F, kw
+        assert relrmse(got["field_grad"], sym6(ref["field_grad"])) < TOL_F, kw
+
+
+def test_quad_vs_explicit_ewald(gb):
+    # the GPU's discretisation error against O1Q equals the oracle's own to within float32
+    fr, mesh, p, a, rc, pos, q, mu, th = _inputs("nacl64")
+    _, got = _gpu(gb, fr, (24, 24, 24), 6, a, rc, pos, q, mu, th)
+    ref = O2.PMEOracle(fr.box, (24, 24, 24), 6, a, rc).evaluate_quad(pos, q, mu, th)
+    ew = O1Q.ewald(pos, q, mu, O1Q.sym_from6(th), fr.box, a, rcut=rc)
+    e_pme = abs(ref["energy"] - ew["energy"])
+    assert abs(got["energy"][0] - ew["energy"]) <= 1.1 * e_pme + TOL_E * abs(ew["energy"])
+    f_pme = relrmse(ref["force"], ew["force"])
+    assert relrmse(got["force"], ew["force"]) <= 1.1 * f_pme + TOL_F
+    g_pme = relrmse(sym6(ref["field_grad"]), O1Q.to6(ew["field_grad"]))
+    assert relrmse(got["field_grad"], O1Q.to6(ew["field_grad"])) <= 1.1 * g_pme + TOL_F
+
+
+def test_quad_zero_theta_equals_plain_forward(gb):
+    fr, mesh, p, a, rc, pos, q, mu, _ = _inputs("nacl4096")
+    plan, got = _gpu(gb, fr, mesh, p, a, rc, pos, q, mu, np.zeros((fr.n, 6)))
+    t = [torch.tensor(np.float32(x), device="cuda") for x in (pos, q, mu)]
+    out = {k: v.cpu().numpy().astype(np.float64) for k, v in plan.forward(*t, field_grad=True).items()}
+    assert abs(got["energy"][0] - out["energy"][0]) < 1e-6 * abs(out["energy"][0])
+    for k in ("force", "phi", "field", "field_grad"):
+        assert relrmse(got[k], out[k]) < 1e-6, k
+
+
+def test_quad_deterministic_and_host_pointers(gb):
+    fr, mesh, p, a, rc, pos, q, mu, th = _inputs("nacl1000_ragged")
+    plan = gb.Plan(fr.box, mesh, p, a, rc, max_ions=1024)
+    t = [torch.tensor(np.float32(x), device="cuda") for x in (pos, q, mu, th)]
+    o1 = plan.forward_quad(*t)
+    o2 = plan.forward_quad(*t)
+    for k in o1:
+        assert torch.equal(o1[k], o2[k]), k
+    o3 = plan.forward_quad(*[x.cpu() for x in t])
+    for k in o1:
+        assert torch.equal(o1[k].cpu(), o3[k]), k
+    # a plain forward and backward after a quadrupole forward recompute from their inputs
+    f = plan.forward(*t[:3])
+    ref = O2.PMEOracle(fr.box, mesh, p, a, rc).evaluate(pos, q, mu, field_grad=False)
+    assert relrmse(f["force"].cpu().numpy(), ref["force"]) < TOL_F
+    gp, gq, gm = plan.backward(*t[:3], g_energy=1.0)
+    assert relrmse(-gp.cpu().numpy(), ref["force"]) < TOL_F
+
+
+def test_quad_refusals(gb):
+    fr, mesh, p, a, rc, pos, q, mu, th = _inputs("nacl64")
+    t = [torch.tensor(np.float32(x), device="cuda") for x in (pos, q, mu, th)]
+    plan = gb.Plan(fr.box, mesh, p, a, rc, max_ions=1024, recip_method="ewald")
+    with pytest.raises(gb.PMEError) as e:
+        plan.forward_quad(*t)
+    assert e.value.status == 5   # PME_ERR_UNSUPPORTED
+    plan = gb.Plan(fr.box, mesh, p, a, rc, max_ions=1024)
+    with pytest.raises(gb.PMEError) as e:
+        plan.forward_quad(*t[:3], None)
+    assert e.value.status == 1   # PME_ERR_ARG
