@@ -7,7 +7,7 @@ Hessian-vector product a force-matching loss needs) on one 32768-ion molten-NaCl
 in HBM. The metric is ion-evaluations per second: ions / (t_forward + t_backward).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--fft auto|cufft|own] [--batch] [--crossover] [--no-extras]
+                  [--fft auto|cufft|own] [--batch] [--crossover] [--quad] [--no-extras]
 
 The timed steps repeat the same calls, so after the first two they replay the plan's recorded
 pass graphs, as any caller's repeated calls do. --fft picks the transforms of the mesh
@@ -73,6 +73,11 @@ def stage_bytes(stage: str, N: int, M: int, Mh: int) -> float:
 # rcut are not counted. The same counts apply to the list-driven evaluation kernel alone
 # (stage pair_eval), which evaluates exactly the pairs inside rcut.
 PAIR_FLOPS = {"fwd.pair": 80.0, "bwd.pair": 450.0, "fwd.pair_eval": 80.0, "bwd.pair_eval": 450.0}
+# Quadrupole pair kernel (csrc/quad.cu), same counting: radial functions B0..B5, the
+# quadrupole products B r, A r and their contractions, phi, grad phi, the 6-component Hessian
+# and the 3-component Theta_i : grad^3 phi: 380 per pair inside rcut.
+QUAD_PAIR_FLOPS = 380.0
+QUAD_METRIC = "PME q+mu+Theta fwd Mion-evals/s @32k ions"
 # Stages timed as one kernel of this library (the roofline's dominant kernel is picked among
 # them; sort and pair are several kernels each, cuFFT is a library call).
 SINGLE_KERNEL_STAGES = ("spread", "influence", "gather", "combine", "pair_eval")
@@ -625,6 +630,90 @@ def run_ours(args):
     return 0
 
 
+def run_quad(args):
+    """Forward with point quadrupoles (pme_forward_quad, the rank-2 channel) on the benchmark
+    frame, quadrupoles Gaussian with sigma 0.1 e A^2 per independent entry; the plain forward
+    (pme_forward, field gradient on) on the same frame beside it. One JSON line: the quadrupole
+    forward's rate, per-stage times of a serialised pass, the dominant kernel's roofline."""
+    import numpy as np
+    import torch
+
+    fr, cfg = build_frame(args.workload)
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2606_01598_gb300 as gb
+    import workloads as W
+
+    n = fr.n
+    c = lambda x: torch.tensor(np.float32(x), device=dev)
+    pos, q, mu = c(fr.pos), c(fr.q), c(fr.mu)
+    th = c(W.quadrupoles(n, 0.1, seed=300).reshape(n, 9)[:, [0, 4, 8, 1, 2, 5]])
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    plan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=n, device=dev, fft=FFT)
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid).replace("GPU-", "")
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    l0 = gb.launch_count()
+    t_quad = time_steps(torch, lambda: plan.forward_quad(pos, q, mu, th), args.steps, args.warmup, dev, flush)
+    launches = (gb.launch_count() - l0) // (args.steps + args.warmup)
+    t_plain = time_steps(torch, lambda: plan.forward(pos, q, mu, field_grad=True), args.steps, args.warmup,
+                         dev, flush)
+    splan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=n, device=dev,
+                    fft=FFT, overlap_pair=False)
+    for _ in range(args.warmup):
+        splan.forward_quad(pos, q, mu, th)
+    splan.profile(True)
+    s_ms = time_steps(torch, lambda: splan.forward_quad(pos, q, mu, th), args.steps, 0, dev, flush)
+    stages = splan.profile_read()
+    splan.profile(False)
+    splan.close()
+    clocks = sampler.stop()
+    M = int(np.prod(cfg["mesh"]))
+    Mh = cfg["mesh"][0] * cfg["mesh"][1] * (cfg["mesh"][2] // 2 + 1)
+    ppi = pairs_per_ion(n, abs(float(np.linalg.det(fr.box))), cfg["rcut"])
+    peak, peak_kind = load_peaks()
+    kernels = {k: v for k, v in stages.items() if k.split(".")[1] in ("pair", "spread", "gather", "influence")}
+    dom = max(kernels, key=lambda k: kernels[k][0])
+    avg_ms = stages[dom][0] / stages[dom][1]
+    if dom == "fwd.pair":
+        fl = n * ppi * QUAD_PAIR_FLOPS
+        ach = fl / (avg_ms / 1e3) / 1e12
+        roof = {"kernel": "k_pair_quad", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
+                "avg_launch_ms": avg_ms, "flops_per_launch": fl}
+    else:
+        # quadrupole mode reads 24 more bytes per ion (Theta) than the forward tables count
+        by = stage_bytes(dom, n, M, Mh) + (24 * n if dom in ("fwd.spread", "fwd.gather") else 0)
+        ach = by / (avg_ms / 1e3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": None, "peak_source": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)",
+                "avg_launch_ms": avg_ms, "bytes_per_launch": by}
+    cfgd = dict(config_dict(cfg, fr, 1), transforms=plan.fft_kind, theta_sigma=0.1)
+    cfgd["workload"] = cfgd["workload"].replace("charges+dipoles, fwd+bwd (HVP)",
+                                                "charges+dipoles+quadrupoles, forward")
+    line = {
+        "metric": QUAD_METRIC, "value": n / t_quad / 1e3, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_quad, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": cfgd,
+        "plain_forward_ms": t_plain,
+        "serial_ms_per_step": s_ms,
+        "stage_ms": {k: round(v[0] / v[1], 5) for k, v in sorted(stages.items())},
+        "roofline": roof,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    plan.close()
+    print(json.dumps(line))
+    return 0
+
+
 def run_crossover(args):
     """Ewald-vs-PME forward timing (energy + forces) on molten-NaCl frames of growing size at
     the same density; one JSON line with the median frame times and the force difference."""
@@ -790,6 +879,7 @@ def main():
                     help="skip the plain-PyTorch comparator and the 16-frame roofline")
     ap.add_argument("--crossover", action="store_true", help="Ewald vs PME timing sweep")
     ap.add_argument("--batch", action="store_true", help="uneven batch vs per-frame loop")
+    ap.add_argument("--quad", action="store_true", help="forward with point quadrupoles")
     ap.add_argument("--frames", type=int, default=256)
     ap.add_argument("--fft", default="auto", choices=["auto", "cufft", "own"],
                     help="transforms of the mesh convolution (pme_opts.fft)")
@@ -798,6 +888,8 @@ def main():
     FFT = args.fft
     if args.batch:
         return run_batch(args)
+    if args.quad:
+        return run_quad(args)
     if args.crossover:
         return run_crossover(args)
     if args.warmup < 3 and args.impl == "ours":

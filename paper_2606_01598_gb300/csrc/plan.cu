@@ -1335,23 +1335,41 @@ static int run_forward_quad(pme_plan_t p, cudaStream_t s, const IonInputs& in, d
   const int n = in.n;
   const bool pair = p->opts.include_pair != 0;
   int st;
+  int t;
   p->fwd_n = -1;
   p->fwd_lists = false;
+  t = prof_begin(p, 0, s);
   if ((st = launch_sort(p, s, in, false, true, pair, nullptr))) return st;
+  prof_end(p, t, s);
   const bool fork = pair && n > 0;
   cudaStream_t ps = p->opts.overlap_pair ? p->side : s;
   if (fork) {
     if (p->opts.overlap_pair && (st = fork_side(p, s))) return st;
+    t = prof_begin(p, 6, ps);
     if ((st = launch_pair_quad(p, ps, n, in.theta, p->pair_out, p->quad_out))) return st;
+    prof_end(p, t, ps);
   }
+  t = prof_begin(p, 1, s);
   if ((st = launch_spread_quad(p, s, in.theta, p->rho))) return st;
+  prof_end(p, t, s);
+  t = prof_begin(p, 2, s);
   if ((st = fft_forward(p, s, false))) return st;
+  prof_end(p, t, s);
+  t = prof_begin(p, 3, s);
   if ((st = multiply_influence(p, s, false, nullptr))) return st;
+  prof_end(p, t, s);
+  t = prof_begin(p, 4, s);
   if ((st = fft_inverse(p, s, false))) return st;
+  prof_end(p, t, s);
+  t = prof_begin(p, 5, s);
   if ((st = launch_gather_quad(p, s, n, p->phi, in.theta, p->mesh_out, p->quad_out))) return st;
+  prof_end(p, t, s);
   if (fork && p->opts.overlap_pair && (st = join_side(p, s))) return st;
-  return launch_combine_forward(p, s, in, true, fork, f_out, p_out, fl_out, fg_out, e_out, 1, nullptr,
-                                p->quad_out);
+  t = prof_begin(p, 7, s);
+  st = launch_combine_forward(p, s, in, true, fork, f_out, p_out, fl_out, fg_out, e_out, 1, nullptr,
+                              p->quad_out);
+  prof_end(p, t, s);
+  return st;
 }
 
 int pme_forward_quad(pme_plan_t p, void* stream, int n, const float* pos, const float* q,
