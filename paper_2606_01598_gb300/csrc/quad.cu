@@ -17,12 +17,17 @@
 //                    + Ar (2 c B2 + 2 dr B3 - 2 tr B B3 + 2 rBr B4) + Br (-2 tr A B3 + 2 rAr B4)
 //                    + d (-tr A B2 + rAr B3) - 2 B2 A d - 4 B3 (B A r + A B r)
 //
-// Work split: one thread per ion in pair-cell order. It visits every offset o in
-// [-kimg, kimg]^3 of the cell grid (each offset is one periodic image of the cell it wraps to,
-// so every image inside rcut is seen once, also for boxes with few cells) and every ion of
-// that cell, forming r = (f_i - f_j - o) H from the in-cell offsets. Sums run in a fixed
-// order, so the result is reproducible. Output in caller order: out[10] = phi, grad phi,
-// grad^2 phi (xx yy zz xy xz yz); qout[4..6] = A : grad^3 phi.
+// Work split: one warp per ion (pair-cell order). The warp walks the neighbouring cells: the
+// (2 kimg + 1)^2 (x, y) columns, each the contiguous run of the 2 kimg + 1 z-cells around the
+// ion's cell (one or two ranges at the periodic wrap; the z offset of a candidate follows from
+// its own cell), or, when an axis has too few cells for distinct offsets, every offset of the
+// [-kimg, kimg]^3 cube on its own (each then one periodic image of the cell it wraps to). The
+// lanes test 32 candidates at a time, forming r = (f_i - f_j - o) H from the in-cell offsets,
+// and append the hits inside rcut, in order, to the warp's shared-memory list (ballot +
+// popc); each time the list holds 32 hits all lanes evaluate one each. Per-lane sums are
+// reduced with warp shuffles in a fixed order, so the result is reproducible. Output in
+// caller order: out[10] = phi, grad phi, grad^2 phi (xx yy zz xy xz yz); qout[4..6] =
+// A : grad^3 phi.
 #include <cmath>
 
 #include "kernels.h"
@@ -58,111 +63,174 @@ __device__ __forceinline__ void mul(const Sym& A, float x, float y, float z, flo
   oz = A.xz * x + A.yz * y + A.zz * z;
 }
 
+struct QuadAcc {
+  float phi = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+  float hxx = 0.f, hyy = 0.f, hzz = 0.f, hxy = 0.f, hxz = 0.f, hyz = 0.f;
+  float tx = 0.f, ty = 0.f, tz = 0.f;
+};
+
+// One pair: source j at displacement r from the field point with quadrupole A (trace trA).
+__device__ __forceinline__ void quad_pair(const QuadPairArgs& a, const Sym& A, float trA, int j, float rx,
+                                          float ry, float rz, QuadAcc& S) {
+  const float al = a.alpha;
+  const float r2 = rx * rx + ry * ry + rz * rz;
+  const float rinv = rsqrtf(r2);
+  const float rinv2 = rinv * rinv;
+  const float ex = expf(-al * al * r2);
+  const float B0 = erfcf(al * r2 * rinv) * rinv;
+  const float B1 = (B0 + a.c[1] * ex) * rinv2;
+  const float B2 = (3.f * B1 + a.c[2] * ex) * rinv2;
+  const float B3 = (5.f * B2 + a.c[3] * ex) * rinv2;
+  const float B4 = (7.f * B3 + a.c[4] * ex) * rinv2;
+  const float B5 = (9.f * B4 + a.c[5] * ex) * rinv2;
+  const float4 mj = a.pr.mu[j];
+  const float c = mj.w, dx = mj.x, dy = mj.y, dz = mj.z;
+  const Sym Bm = load_sym(a.theta + size_t(a.pr.idx[j].w) * 6);
+  const float trB = Bm.xx + Bm.yy + Bm.zz;
+  float Brx, Bry, Brz, Arx, Ary, Arz;
+  mul(Bm, rx, ry, rz, Brx, Bry, Brz);
+  mul(A, rx, ry, rz, Arx, Ary, Arz);
+  const float dr = dx * rx + dy * ry + dz * rz;
+  const float rBr = Brx * rx + Bry * ry + Brz * rz;
+  const float rAr = Arx * rx + Ary * ry + Arz * rz;
+  // potential, gradient, Hessian
+  const float sI = -c * B1 - dr * B2 + trB * B2 - rBr * B3;
+  const float srr = c * B2 + dr * B3 - trB * B3 + rBr * B4;
+  S.phi += c * B0 + dr * B1 - trB * B1 + rBr * B2;
+  S.gx += sI * rx + B1 * dx + 2.f * B2 * Brx;
+  S.gy += sI * ry + B1 * dy + 2.f * B2 * Bry;
+  S.gz += sI * rz + B1 * dz + 2.f * B2 * Brz;
+  S.hxx += sI + srr * rx * rx - 2.f * B2 * dx * rx - 4.f * B3 * Brx * rx + 2.f * B2 * Bm.xx;
+  S.hyy += sI + srr * ry * ry - 2.f * B2 * dy * ry - 4.f * B3 * Bry * ry + 2.f * B2 * Bm.yy;
+  S.hzz += sI + srr * rz * rz - 2.f * B2 * dz * rz - 4.f * B3 * Brz * rz + 2.f * B2 * Bm.zz;
+  S.hxy += srr * rx * ry - B2 * (dx * ry + rx * dy) - 2.f * B3 * (Brx * ry + rx * Bry) + 2.f * B2 * Bm.xy;
+  S.hxz += srr * rx * rz - B2 * (dx * rz + rx * dz) - 2.f * B3 * (Brx * rz + rx * Brz) + 2.f * B2 * Bm.xz;
+  S.hyz += srr * ry * rz - B2 * (dy * rz + ry * dz) - 2.f * B3 * (Bry * rz + ry * Brz) + 2.f * B2 * Bm.yz;
+  // A : grad^3 phi
+  const float AB = A.xx * Bm.xx + A.yy * Bm.yy + A.zz * Bm.zz + 2.f * (A.xy * Bm.xy + A.xz * Bm.xz + A.yz * Bm.yz);
+  const float Ard = Arx * dx + Ary * dy + Arz * dz;
+  const float ArBr = Arx * Brx + Ary * Bry + Arz * Brz;
+  float Adx, Ady, Adz, BArx, BAry, BArz, ABrx, ABry, ABrz;
+  mul(A, dx, dy, dz, Adx, Ady, Adz);
+  mul(Bm, Arx, Ary, Arz, BArx, BAry, BArz);
+  mul(A, Brx, Bry, Brz, ABrx, ABry, ABrz);
+  const float s_r = c * trA * B2 - c * rAr * B3 + trA * dr * B3 + 2.f * Ard * B3 - rAr * dr * B4 -
+                    (trA * trB + 2.f * AB) * B3 + (trA * rBr + trB * rAr + 4.f * ArBr) * B4 - rAr * rBr * B5;
+  const float s_Ar = 2.f * c * B2 + 2.f * dr * B3 - 2.f * trB * B3 + 2.f * rBr * B4;
+  const float s_Br = -2.f * trA * B3 + 2.f * rAr * B4;
+  const float s_d = -trA * B2 + rAr * B3;
+  S.tx += s_r * rx + s_Ar * Arx + s_Br * Brx + s_d * dx - 2.f * B2 * Adx - 4.f * B3 * (BArx + ABrx);
+  S.ty += s_r * ry + s_Ar * Ary + s_Br * Bry + s_d * dy - 2.f * B2 * Ady - 4.f * B3 * (BAry + ABry);
+  S.tz += s_r * rz + s_Ar * Arz + s_Br * Brz + s_d * dz - 2.f * B2 * Adz - 4.f * B3 * (BArz + ABrz);
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+constexpr int kWarps = kQuadThreads / 32;
+constexpr int kHitCap = 64;   // < 32 carried over + 32 appended per test round
+
 __global__ void __launch_bounds__(kQuadThreads) k_pair_quad(QuadPairArgs a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
+  __shared__ float4 s_hit[kWarps][kHitCap];   // r (x, y, z), source j (int bits)
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kWarps + wid;
+  if (i >= a.n) return;   // warp-uniform
+  float4* hits = s_hit[wid];
   const Geometry& g = a.g;
   const int4 ci = a.pr.idx[i];
   const float4 fi = a.pr.fq[i];
   const Sym A = load_sym(a.theta + size_t(ci.w) * 6);
   const float trA = A.xx + A.yy + A.zz;
   const float rc2 = g.rcut2;
-  const float al = a.alpha;
-  float phi = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-  float hxx = 0.f, hyy = 0.f, hzz = 0.f, hxy = 0.f, hxz = 0.f, hyz = 0.f;
-  float tx = 0.f, ty = 0.f, tz = 0.f;
   const int kx = g.kimg[0], ky = g.kimg[1], kz = g.kimg[2];
   const int ncx = g.ncell[0], ncy = g.ncell[1], ncz = g.ncell[2];
-  for (int ox = -kx; ox <= kx; ++ox) {
-    int cx = (ci.x + ox) % ncx;
+  const bool zrun = ncz >= 2 * kz + 1;
+  const int nzs = zrun ? 1 : 2 * kz + 1;
+  const int nseg = (2 * kx + 1) * (2 * ky + 1) * nzs;
+  QuadAcc S;
+  int nh = 0;   // hits in the list (the same in every lane)
+  for (int sg = 0; sg < nseg; ++sg) {
+    const int ozs = zrun ? 0 : (sg % nzs) - kz;
+    const int t = sg / nzs;
+    const int oy = (t % (2 * ky + 1)) - ky;
+    const int ox = (t / (2 * ky + 1)) - kx;
+    int cx = (ci.x + ox) % ncx, cy = (ci.y + oy) % ncy;
     if (cx < 0) cx += ncx;
-    for (int oy = -ky; oy <= ky; ++oy) {
-      int cy = (ci.y + oy) % ncy;
-      if (cy < 0) cy += ncy;
-      for (int oz = -kz; oz <= kz; ++oz) {
-        int cz = (ci.z + oz) % ncz;
-        if (cz < 0) cz += ncz;
-        const int key = a.cell_off + (cx * ncy + cy) * ncz + cz;
-        const int lo = a.start_c[key], hi = a.start_c[key + 1];
-        const bool self_cell = ox == 0 && oy == 0 && oz == 0;
-        for (int j = lo; j < hi; ++j) {
-          if (self_cell && j == i) continue;
-          const float4 fj = a.pr.fq[j];
-          const float ux = fi.x - fj.x - float(ox), uy = fi.y - fj.y - float(oy), uz = fi.z - fj.z - float(oz);
-          const float rx = ux * g.H[0] + uy * g.H[3] + uz * g.H[6];
-          const float ry = ux * g.H[1] + uy * g.H[4] + uz * g.H[7];
-          const float rz = ux * g.H[2] + uy * g.H[5] + uz * g.H[8];
-          const float r2 = rx * rx + ry * ry + rz * rz;
-          if (!(r2 < rc2)) continue;
-          const float rinv = rsqrtf(r2);
-          const float rinv2 = rinv * rinv;
-          const float ex = expf(-al * al * r2);
-          const float B0 = erfcf(al * r2 * rinv) * rinv;
-          const float B1 = (B0 + a.c[1] * ex) * rinv2;
-          const float B2 = (3.f * B1 + a.c[2] * ex) * rinv2;
-          const float B3 = (5.f * B2 + a.c[3] * ex) * rinv2;
-          const float B4 = (7.f * B3 + a.c[4] * ex) * rinv2;
-          const float B5 = (9.f * B4 + a.c[5] * ex) * rinv2;
-          const float4 mj = a.pr.mu[j];
-          const float c = mj.w, dx = mj.x, dy = mj.y, dz = mj.z;
-          const Sym Bm = load_sym(a.theta + size_t(a.pr.idx[j].w) * 6);
-          const float trB = Bm.xx + Bm.yy + Bm.zz;
-          float Brx, Bry, Brz, Arx, Ary, Arz;
-          mul(Bm, rx, ry, rz, Brx, Bry, Brz);
-          mul(A, rx, ry, rz, Arx, Ary, Arz);
-          const float dr = dx * rx + dy * ry + dz * rz;
-          const float rBr = Brx * rx + Bry * ry + Brz * rz;
-          const float rAr = Arx * rx + Ary * ry + Arz * rz;
-          // potential, gradient, Hessian
-          const float sI = -c * B1 - dr * B2 + trB * B2 - rBr * B3;
-          const float srr = c * B2 + dr * B3 - trB * B3 + rBr * B4;
-          phi += c * B0 + dr * B1 - trB * B1 + rBr * B2;
-          gx += sI * rx + B1 * dx + 2.f * B2 * Brx;
-          gy += sI * ry + B1 * dy + 2.f * B2 * Bry;
-          gz += sI * rz + B1 * dz + 2.f * B2 * Brz;
-          hxx += sI + srr * rx * rx - 2.f * B2 * dx * rx - 4.f * B3 * Brx * rx + 2.f * B2 * Bm.xx;
-          hyy += sI + srr * ry * ry - 2.f * B2 * dy * ry - 4.f * B3 * Bry * ry + 2.f * B2 * Bm.yy;
-          hzz += sI + srr * rz * rz - 2.f * B2 * dz * rz - 4.f * B3 * Brz * rz + 2.f * B2 * Bm.zz;
-          hxy += srr * rx * ry - B2 * (dx * ry + rx * dy) - 2.f * B3 * (Brx * ry + rx * Bry) + 2.f * B2 * Bm.xy;
-          hxz += srr * rx * rz - B2 * (dx * rz + rx * dz) - 2.f * B3 * (Brx * rz + rx * Brz) + 2.f * B2 * Bm.xz;
-          hyz += srr * ry * rz - B2 * (dy * rz + ry * dz) - 2.f * B3 * (Bry * rz + ry * Brz) + 2.f * B2 * Bm.yz;
-          // A : grad^3 phi
-          const float AB = A.xx * Bm.xx + A.yy * Bm.yy + A.zz * Bm.zz +
-                           2.f * (A.xy * Bm.xy + A.xz * Bm.xz + A.yz * Bm.yz);
-          const float Ard = Arx * dx + Ary * dy + Arz * dz;
-          const float ArBr = Arx * Brx + Ary * Bry + Arz * Brz;
-          float Adx, Ady, Adz, BArx, BAry, BArz, ABrx, ABry, ABrz;
-          mul(A, dx, dy, dz, Adx, Ady, Adz);
-          mul(Bm, Arx, Ary, Arz, BArx, BAry, BArz);
-          mul(A, Brx, Bry, Brz, ABrx, ABry, ABrz);
-          const float s_r = c * trA * B2 - c * rAr * B3 + trA * dr * B3 + 2.f * Ard * B3 - rAr * dr * B4 -
-                            (trA * trB + 2.f * AB) * B3 + (trA * rBr + trB * rAr + 4.f * ArBr) * B4 -
-                            rAr * rBr * B5;
-          const float s_Ar = 2.f * c * B2 + 2.f * dr * B3 - 2.f * trB * B3 + 2.f * rBr * B4;
-          const float s_Br = -2.f * trA * B3 + 2.f * rAr * B4;
-          const float s_d = -trA * B2 + rAr * B3;
-          tx += s_r * rx + s_Ar * Arx + s_Br * Brx + s_d * dx - 2.f * B2 * Adx - 4.f * B3 * (BArx + ABrx);
-          ty += s_r * ry + s_Ar * Ary + s_Br * Bry + s_d * dy - 2.f * B2 * Ady - 4.f * B3 * (BAry + ABry);
-          tz += s_r * rz + s_Ar * Arz + s_Br * Brz + s_d * dz - 2.f * B2 * Adz - 4.f * B3 * (BArz + ABrz);
+    if (cy < 0) cy += ncy;
+    const int row = a.cell_off + (cx * ncy + cy) * ncz;
+    int loA, lenA, loB = 0, lenB = 0;
+    if (zrun) {
+      const int z0 = ci.z - kz, z1 = ci.z + kz;
+      if (z0 < 0) {
+        loA = a.start_c[row + z0 + ncz]; lenA = a.start_c[row + ncz] - loA;
+        loB = a.start_c[row]; lenB = a.start_c[row + z1 + 1] - loB;
+      } else if (z1 >= ncz) {
+        loA = a.start_c[row + z0]; lenA = a.start_c[row + ncz] - loA;
+        loB = a.start_c[row]; lenB = a.start_c[row + z1 - ncz + 1] - loB;
+      } else {
+        loA = a.start_c[row + z0]; lenA = a.start_c[row + z1 + 1] - loA;
+      }
+    } else {
+      int cz = (ci.z + ozs) % ncz;
+      if (cz < 0) cz += ncz;
+      loA = a.start_c[row + cz]; lenA = a.start_c[row + cz + 1] - loA;
+    }
+    const int len = lenA + lenB;
+    for (int base = 0; base < len; base += 32) {
+      const int k = base + lane;
+      bool hit = false;
+      float rx = 0.f, ry = 0.f, rz = 0.f;
+      int j = 0;
+      if (k < len) {
+        j = k < lenA ? loA + k : loB + (k - lenA);
+        const float4 fj = a.pr.fq[j];
+        int oz = ozs;
+        if (zrun) {
+          oz = __float_as_int(fj.w) - ci.z;
+          if (oz > kz) oz -= ncz;
+          else if (oz < -kz) oz += ncz;
         }
+        const float ux = fi.x - fj.x - float(ox), uy = fi.y - fj.y - float(oy), uz = fi.z - fj.z - float(oz);
+        rx = ux * g.H[0] + uy * g.H[3] + uz * g.H[6];
+        ry = ux * g.H[1] + uy * g.H[4] + uz * g.H[7];
+        rz = ux * g.H[2] + uy * g.H[5] + uz * g.H[8];
+        const float r2 = rx * rx + ry * ry + rz * rz;
+        hit = r2 < rc2 && !(j == i && ox == 0 && oy == 0 && oz == 0);
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, hit);
+      if (hit) hits[nh + __popc(bal & ((1u << lane) - 1u))] = make_float4(rx, ry, rz, __int_as_float(j));
+      nh += __popc(bal);
+      __syncwarp();
+      if (nh >= 32) {
+        const float4 h = hits[lane];
+        quad_pair(a, A, trA, __float_as_int(h.w), h.x, h.y, h.z, S);
+        __syncwarp();
+        if (lane < nh - 32) hits[lane] = hits[32 + lane];
+        nh -= 32;
+        __syncwarp();
       }
     }
   }
-  float* o = a.out + size_t(ci.w) * 10;
-  o[0] = phi;
-  o[1] = gx;
-  o[2] = gy;
-  o[3] = gz;
-  o[4] = hxx;
-  o[5] = hyy;
-  o[6] = hzz;
-  o[7] = hxy;
-  o[8] = hxz;
-  o[9] = hyz;
-  float* qo = a.qout + size_t(ci.w) * 8;
-  qo[4] = tx;
-  qo[5] = ty;
-  qo[6] = tz;
+  if (lane < nh) {
+    const float4 h = hits[lane];
+    quad_pair(a, A, trA, __float_as_int(h.w), h.x, h.y, h.z, S);
+  }
+  const float v[13] = {warp_sum_f(S.phi), warp_sum_f(S.gx), warp_sum_f(S.gy), warp_sum_f(S.gz),
+                       warp_sum_f(S.hxx), warp_sum_f(S.hyy), warp_sum_f(S.hzz), warp_sum_f(S.hxy),
+                       warp_sum_f(S.hxz), warp_sum_f(S.hyz), warp_sum_f(S.tx), warp_sum_f(S.ty),
+                       warp_sum_f(S.tz)};
+  if (lane == 0) {
+    float* o = a.out + size_t(ci.w) * 10;
+#pragma unroll
+    for (int c = 0; c < 10; ++c) o[c] = v[c];
+    float* qo = a.qout + size_t(ci.w) * 8;
+    qo[4] = v[10];
+    qo[5] = v[11];
+    qo[6] = v[12];
+  }
 }
 
 }  // namespace
@@ -182,7 +250,7 @@ int launch_pair_quad(pme_plan_t p, cudaStream_t s, int n, const float* theta, fl
   a.alpha = float(p->alpha);
   const double al = p->alpha;
   for (int l = 0; l < 6; ++l) a.c[l] = float(std::pow(2.0 * al * al, l) / (al * std::sqrt(kPi)));
-  const int grid = (n + kQuadThreads - 1) / kQuadThreads;
+  const int grid = (n + kWarps - 1) / kWarps;
   k_pair_quad<<<grid, kQuadThreads, 0, s>>>(a);
   count_launch();
   return check_launch(p, "k_pair_quad");
