@@ -148,36 +148,12 @@ __global__ void __launch_bounds__(kQuadThreads) k_pair_quad(QuadPairArgs a) {
   const int kx = g.kimg[0], ky = g.kimg[1], kz = g.kimg[2];
   const int ncx = g.ncell[0], ncy = g.ncell[1], ncz = g.ncell[2];
   const bool zrun = ncz >= 2 * kz + 1;
-  const int nzs = zrun ? 1 : 2 * kz + 1;
-  const int nseg = (2 * kx + 1) * (2 * ky + 1) * nzs;
   QuadAcc S;
   int nh = 0;   // hits in the list (the same in every lane)
-  for (int sg = 0; sg < nseg; ++sg) {
-    const int ozs = zrun ? 0 : (sg % nzs) - kz;
-    const int t = sg / nzs;
-    const int oy = (t % (2 * ky + 1)) - ky;
-    const int ox = (t / (2 * ky + 1)) - kx;
-    int cx = (ci.x + ox) % ncx, cy = (ci.y + oy) % ncy;
-    if (cx < 0) cx += ncx;
-    if (cy < 0) cy += ncy;
-    const int row = a.cell_off + (cx * ncy + cy) * ncz;
-    int loA, lenA, loB = 0, lenB = 0;
-    if (zrun) {
-      const int z0 = ci.z - kz, z1 = ci.z + kz;
-      if (z0 < 0) {
-        loA = a.start_c[row + z0 + ncz]; lenA = a.start_c[row + ncz] - loA;
-        loB = a.start_c[row]; lenB = a.start_c[row + z1 + 1] - loB;
-      } else if (z1 >= ncz) {
-        loA = a.start_c[row + z0]; lenA = a.start_c[row + ncz] - loA;
-        loB = a.start_c[row]; lenB = a.start_c[row + z1 - ncz + 1] - loB;
-      } else {
-        loA = a.start_c[row + z0]; lenA = a.start_c[row + z1 + 1] - loA;
-      }
-    } else {
-      int cz = (ci.z + ozs) % ncz;
-      if (cz < 0) cz += ncz;
-      loA = a.start_c[row + cz]; lenA = a.start_c[row + cz + 1] - loA;
-    }
+  // test the candidates of one or two contiguous ranges of the cell order against ion i, with
+  // the cell offset (ox, oy) of the range's column folded into (fxo, fyo) and, outside z-runs,
+  // the z offset in ozs
+  auto visit = [&](int loA, int lenA, int loB, int lenB, float fxo, float fyo, int ozs, bool zero_xy) {
     const int len = lenA + lenB;
     for (int base = 0; base < len; base += 32) {
       const int k = base + lane;
@@ -193,12 +169,12 @@ __global__ void __launch_bounds__(kQuadThreads) k_pair_quad(QuadPairArgs a) {
           if (oz > kz) oz -= ncz;
           else if (oz < -kz) oz += ncz;
         }
-        const float ux = fi.x - fj.x - float(ox), uy = fi.y - fj.y - float(oy), uz = fi.z - fj.z - float(oz);
+        const float ux = fxo - fj.x, uy = fyo - fj.y, uz = fi.z - float(oz) - fj.z;
         rx = ux * g.H[0] + uy * g.H[3] + uz * g.H[6];
         ry = ux * g.H[1] + uy * g.H[4] + uz * g.H[7];
         rz = ux * g.H[2] + uy * g.H[5] + uz * g.H[8];
         const float r2 = rx * rx + ry * ry + rz * rz;
-        hit = r2 < rc2 && !(j == i && ox == 0 && oy == 0 && oz == 0);
+        hit = r2 < rc2 && !(j == i && zero_xy && oz == 0);
       }
       const unsigned bal = __ballot_sync(0xffffffffu, hit);
       if (hit) hits[nh + __popc(bal & ((1u << lane) - 1u))] = make_float4(rx, ry, rz, __int_as_float(j));
@@ -213,6 +189,41 @@ __global__ void __launch_bounds__(kQuadThreads) k_pair_quad(QuadPairArgs a) {
         __syncwarp();
       }
     }
+  };
+  // neighbour columns; cell indices advance with a wrap test instead of a division
+  int cx = ((ci.x - kx) % ncx + ncx) % ncx;
+  const int cy0 = ((ci.y - ky) % ncy + ncy) % ncy;
+  const int cz0 = ((ci.z - kz) % ncz + ncz) % ncz;
+  for (int ox = -kx; ox <= kx; ++ox) {
+    const float fxo = fi.x - float(ox);
+    int cy = cy0;
+    for (int oy = -ky; oy <= ky; ++oy) {
+      const float fyo = fi.y - float(oy);
+      const int row = a.cell_off + (cx * ncy + cy) * ncz;
+      const bool zero_xy = ox == 0 && oy == 0;
+      if (zrun) {
+        const int z0 = ci.z - kz, z1 = ci.z + kz;
+        if (z0 < 0) {
+          const int loA = a.start_c[row + z0 + ncz], loB = a.start_c[row];
+          visit(loA, a.start_c[row + ncz] - loA, loB, a.start_c[row + z1 + 1] - loB, fxo, fyo, 0, zero_xy);
+        } else if (z1 >= ncz) {
+          const int loA = a.start_c[row + z0], loB = a.start_c[row];
+          visit(loA, a.start_c[row + ncz] - loA, loB, a.start_c[row + z1 - ncz + 1] - loB, fxo, fyo, 0, zero_xy);
+        } else {
+          const int loA = a.start_c[row + z0];
+          visit(loA, a.start_c[row + z1 + 1] - loA, 0, 0, fxo, fyo, 0, zero_xy);
+        }
+      } else {
+        int cz = cz0;
+        for (int oz = -kz; oz <= kz; ++oz) {
+          const int loA = a.start_c[row + cz];
+          visit(loA, a.start_c[row + cz + 1] - loA, 0, 0, fxo, fyo, oz, zero_xy);
+          cz = cz + 1 == ncz ? 0 : cz + 1;
+        }
+      }
+      cy = cy + 1 == ncy ? 0 : cy + 1;
+    }
+    cx = cx + 1 == ncx ? 0 : cx + 1;
   }
   if (lane < nh) {
     const float4 h = hits[lane];
