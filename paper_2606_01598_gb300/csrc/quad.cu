@@ -17,17 +17,18 @@
 //                    + Ar (2 c B2 + 2 dr B3 - 2 tr B B3 + 2 rBr B4) + Br (-2 tr A B3 + 2 rAr B4)
 //                    + d (-tr A B2 + rAr B3) - 2 B2 A d - 4 B3 (B A r + A B r)
 //
-// Work split: one warp per ion (pair-cell order). The warp walks the neighbouring cells: the
+// Work split: one warp per ion (pair-cell order). The neighbouring cells are the
 // (2 kimg + 1)^2 (x, y) columns, each the contiguous run of the 2 kimg + 1 z-cells around the
-// ion's cell (one or two ranges at the periodic wrap; the z offset of a candidate follows from
-// its own cell), or, when an axis has too few cells for distinct offsets, every offset of the
+// ion's cell (one or two ranges at the periodic wrap; a candidate's z offset follows from its
+// own cell), or, when an axis has too few cells for distinct offsets, every offset of the
 // [-kimg, kimg]^3 cube on its own (each then one periodic image of the cell it wraps to). The
-// lanes test 32 candidates at a time, forming r = (f_i - f_j - o) H from the in-cell offsets,
-// and append the hits inside rcut, in order, to the warp's shared-memory list (ballot +
-// popc); each time the list holds 32 hits all lanes evaluate one each. Per-lane sums are
-// reduced with warp shuffles in a fixed order, so the result is reproducible. Output in
-// caller order: out[10] = phi, grad phi, grad^2 phi (xx yy zz xy xz yz); qout[4..6] =
-// A : grad^3 phi.
+// lanes describe 32 such segments at a time and a warp scan lays their candidates out as one
+// dense stream in shared memory; the lanes test 32 candidates at a time, forming
+// r = (f_i - f_j - o) H from the in-cell offsets, and append the hits inside rcut, in order, to
+// the warp's hit list (ballot + popc); each time the list holds 32 hits all lanes evaluate one
+// each. Per-lane sums are reduced with warp shuffles in a fixed order, so the result is
+// reproducible. Output in caller order: out[10] = phi, grad phi, grad^2 phi (xx yy zz xy xz
+// yz); qout[4..6] = A : grad^3 phi.
 #include <cmath>
 
 #include "kernels.h"
@@ -132,9 +133,12 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 
 constexpr int kWarps = kQuadThreads / 32;
 constexpr int kHitCap = 64;   // < 32 carried over + 32 appended per test round
+constexpr int kCandCap = 512; // candidates listed per warp at a time
+constexpr int kSegShift = 27; // candidate entry: (segment lane << 27) | sorted index
 
 __global__ void __launch_bounds__(kQuadThreads) k_pair_quad(QuadPairArgs a) {
   __shared__ float4 s_hit[kWarps][kHitCap];   // r (x, y, z), source j (int bits)
+  __shared__ unsigned s_cand[kWarps][kCandCap];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * kWarps + wid;
   if (i >= a.n) return;   // warp-uniform
@@ -150,80 +154,107 @@ __global__ void __launch_bounds__(kQuadThreads) k_pair_quad(QuadPairArgs a) {
   const bool zrun = ncz >= 2 * kz + 1;
   QuadAcc S;
   int nh = 0;   // hits in the list (the same in every lane)
-  // test the candidates of one or two contiguous ranges of the cell order against ion i, with
-  // the cell offset (ox, oy) of the range's column folded into (fxo, fyo) and, outside z-runs,
-  // the z offset in ozs
-  auto visit = [&](int loA, int lenA, int loB, int lenB, float fxo, float fyo, int ozs, bool zero_xy) {
-    const int len = lenA + lenB;
-    for (int base = 0; base < len; base += 32) {
-      const int k = base + lane;
-      bool hit = false;
-      float rx = 0.f, ry = 0.f, rz = 0.f;
-      int j = 0;
-      if (k < len) {
-        j = k < lenA ? loA + k : loB + (k - lenA);
-        const float4 fj = a.pr.fq[j];
-        int oz = ozs;
-        if (zrun) {
-          oz = __float_as_int(fj.w) - ci.z;
-          if (oz > kz) oz -= ncz;
-          else if (oz < -kz) oz += ncz;
-        }
-        const float ux = fxo - fj.x, uy = fyo - fj.y, uz = fi.z - float(oz) - fj.z;
-        rx = ux * g.H[0] + uy * g.H[3] + uz * g.H[6];
-        ry = ux * g.H[1] + uy * g.H[4] + uz * g.H[7];
-        rz = ux * g.H[2] + uy * g.H[5] + uz * g.H[8];
-        const float r2 = rx * rx + ry * ry + rz * rz;
-        hit = r2 < rc2 && !(j == i && zero_xy && oz == 0);
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, hit);
-      if (hit) hits[nh + __popc(bal & ((1u << lane) - 1u))] = make_float4(rx, ry, rz, __int_as_float(j));
-      nh += __popc(bal);
-      __syncwarp();
-      if (nh >= 32) {
-        const float4 h = hits[lane];
-        quad_pair(a, A, trA, __float_as_int(h.w), h.x, h.y, h.z, S);
-        __syncwarp();
-        if (lane < nh - 32) hits[lane] = hits[32 + lane];
-        nh -= 32;
-        __syncwarp();
-      }
-    }
-  };
-  // neighbour columns; cell indices advance with a wrap test instead of a division
-  int cx = ((ci.x - kx) % ncx + ncx) % ncx;
-  const int cy0 = ((ci.y - ky) % ncy + ncy) % ncy;
-  const int cz0 = ((ci.z - kz) % ncz + ncz) % ncz;
-  for (int ox = -kx; ox <= kx; ++ox) {
-    const float fxo = fi.x - float(ox);
-    int cy = cy0;
-    for (int oy = -ky; oy <= ky; ++oy) {
-      const float fyo = fi.y - float(oy);
+  unsigned* cand = s_cand[wid];
+  const int nzs = zrun ? 1 : 2 * kz + 1;
+  const int nseg = (2 * kx + 1) * (2 * ky + 1) * nzs;
+  for (int g0 = 0; g0 < nseg; g0 += 32) {
+    // lane l describes segment g0 + l: one or two contiguous ranges of the cell order, with
+    // the segment's cell offset folded into (fxo, fyo) and, outside z-runs, its z offset
+    const int sidx = g0 + lane;
+    int loA = 0, lenA = 0, loB = 0, lenB = 0, ozs = 0, zxy = 0;
+    float fxo = 0.f, fyo = 0.f;
+    if (sidx < nseg) {
+      ozs = zrun ? 0 : (sidx % nzs) - kz;
+      const int t = sidx / nzs;
+      const int oy = (t % (2 * ky + 1)) - ky;
+      const int ox = (t / (2 * ky + 1)) - kx;
+      int cx = (ci.x + ox) % ncx, cy = (ci.y + oy) % ncy;
+      if (cx < 0) cx += ncx;
+      if (cy < 0) cy += ncy;
+      fxo = fi.x - float(ox);
+      fyo = fi.y - float(oy);
+      zxy = ox == 0 && oy == 0;
       const int row = a.cell_off + (cx * ncy + cy) * ncz;
-      const bool zero_xy = ox == 0 && oy == 0;
       if (zrun) {
         const int z0 = ci.z - kz, z1 = ci.z + kz;
         if (z0 < 0) {
-          const int loA = a.start_c[row + z0 + ncz], loB = a.start_c[row];
-          visit(loA, a.start_c[row + ncz] - loA, loB, a.start_c[row + z1 + 1] - loB, fxo, fyo, 0, zero_xy);
+          loA = a.start_c[row + z0 + ncz]; lenA = a.start_c[row + ncz] - loA;
+          loB = a.start_c[row]; lenB = a.start_c[row + z1 + 1] - loB;
         } else if (z1 >= ncz) {
-          const int loA = a.start_c[row + z0], loB = a.start_c[row];
-          visit(loA, a.start_c[row + ncz] - loA, loB, a.start_c[row + z1 - ncz + 1] - loB, fxo, fyo, 0, zero_xy);
+          loA = a.start_c[row + z0]; lenA = a.start_c[row + ncz] - loA;
+          loB = a.start_c[row]; lenB = a.start_c[row + z1 - ncz + 1] - loB;
         } else {
-          const int loA = a.start_c[row + z0];
-          visit(loA, a.start_c[row + z1 + 1] - loA, 0, 0, fxo, fyo, 0, zero_xy);
+          loA = a.start_c[row + z0]; lenA = a.start_c[row + z1 + 1] - loA;
         }
       } else {
-        int cz = cz0;
-        for (int oz = -kz; oz <= kz; ++oz) {
-          const int loA = a.start_c[row + cz];
-          visit(loA, a.start_c[row + cz + 1] - loA, 0, 0, fxo, fyo, oz, zero_xy);
-          cz = cz + 1 == ncz ? 0 : cz + 1;
+        int cz = (ci.z + ozs) % ncz;
+        if (cz < 0) cz += ncz;
+        loA = a.start_c[row + cz]; lenA = a.start_c[row + cz + 1] - loA;
+      }
+    }
+    // segments back to back: one dense candidate stream
+    const int len = lenA + lenB;
+    int pre = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, pre, o);
+      if (lane >= o) pre += u;
+    }
+    const int total = __shfl_sync(0xffffffffu, pre, 31);
+    for (int piece = 0; piece < total; piece += kCandCap) {
+      const int npc = min(kCandCap, total - piece);
+      {
+        const int first = pre - len;
+        const int lo = max(first, piece), hi = min(pre, piece + kCandCap);
+        for (int q = lo; q < hi; ++q) {
+          const int off = q - first;
+          cand[q - piece] = (unsigned(lane) << kSegShift) | unsigned(off < lenA ? loA + off : loB + (off - lenA));
         }
       }
-      cy = cy + 1 == ncy ? 0 : cy + 1;
+      __syncwarp();
+      for (int base = 0; base < npc; base += 32) {
+        const int k = base + lane;
+        const bool valid = k < npc;
+        const unsigned e = valid ? cand[k] : 0u;
+        const int src = int(e >> kSegShift);
+        const float sfx = __shfl_sync(0xffffffffu, fxo, src);
+        const float sfy = __shfl_sync(0xffffffffu, fyo, src);
+        const int soz = __shfl_sync(0xffffffffu, ozs, src);
+        const int szxy = __shfl_sync(0xffffffffu, zxy, src);
+        bool hit = false;
+        float rx = 0.f, ry = 0.f, rz = 0.f;
+        int j = 0;
+        if (valid) {
+          j = int(e & ((1u << kSegShift) - 1u));
+          const float4 fj = a.pr.fq[j];
+          int oz = soz;
+          if (zrun) {
+            oz = __float_as_int(fj.w) - ci.z;
+            if (oz > kz) oz -= ncz;
+            else if (oz < -kz) oz += ncz;
+          }
+          const float ux = sfx - fj.x, uy = sfy - fj.y, uz = fi.z - float(oz) - fj.z;
+          rx = ux * g.H[0] + uy * g.H[3] + uz * g.H[6];
+          ry = ux * g.H[1] + uy * g.H[4] + uz * g.H[7];
+          rz = ux * g.H[2] + uy * g.H[5] + uz * g.H[8];
+          const float r2 = rx * rx + ry * ry + rz * rz;
+          hit = r2 < rc2 && !(j == i && szxy && oz == 0);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        if (hit) hits[nh + __popc(bal & ((1u << lane) - 1u))] = make_float4(rx, ry, rz, __int_as_float(j));
+        nh += __popc(bal);
+        __syncwarp();
+        if (nh >= 32) {
+          const float4 h = hits[lane];
+          quad_pair(a, A, trA, __float_as_int(h.w), h.x, h.y, h.z, S);
+          __syncwarp();
+          if (lane < nh - 32) hits[lane] = hits[32 + lane];
+          nh -= 32;
+          __syncwarp();
+        }
+      }
+      __syncwarp();
     }
-    cx = cx + 1 == ncx ? 0 : cx + 1;
   }
   if (lane < nh) {
     const float4 h = hits[lane];
@@ -249,6 +280,7 @@ __global__ void __launch_bounds__(kQuadThreads) k_pair_quad(QuadPairArgs a) {
 int launch_pair_quad(pme_plan_t p, cudaStream_t s, int n, const float* theta, float* out, float* qout) {
   if (p->batch) return set_error(p, PME_ERR_UNSUPPORTED, "quadrupoles need a single-frame plan");
   if (n <= 0) return PME_OK;
+  if (n >= (1 << 27)) return set_error(p, PME_ERR_UNSUPPORTED, "quadrupole pair term: more than 2^27 ions");
   QuadPairArgs a;
   a.g = p->g;
   a.pr = p->pr;
