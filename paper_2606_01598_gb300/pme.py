@@ -509,6 +509,35 @@ class PMEEnergy(torch.autograd.Function):
         return None, g * dEdr, g * dEdq, g * dEdmu
 
 
+class PMEQuadEnergy(torch.autograd.Function):
+    """Total energy with point quadrupoles theta [n, 6] (xx, yy, zz, xy, xz, yz), through
+    pme_forward_quad. Differentiable once: the gradients are -force, phi, -field and, for the
+    six independent entries of theta, -field_grad with the off-diagonal entries doubled (each
+    appears twice in the symmetric tensor). There is no second derivative (no quadrupole
+    backward pass): differentiating the gradients raises."""
+
+    @staticmethod
+    def forward(ctx, plan, pos, q, mu, theta):
+        out = plan.forward_quad(pos.detach(), q.detach(), mu.detach(), theta.detach())
+        ctx.save_for_backward(out["force"], out["phi"], out["field"], out["field_grad"])
+        return out["energy"].reshape(())
+
+    @staticmethod
+    @torch.autograd.function.once_differentiable
+    def backward(ctx, gE):
+        F, phi, field, fg = ctx.saved_tensors
+        g = gE.to(torch.float32)
+        w = torch.tensor([1.0, 1.0, 1.0, 2.0, 2.0, 2.0], dtype=fg.dtype, device=fg.device)
+        return None, -g * F, g * phi, -g * field, -g * fg * w
+
+
+def pme_quad_energy(plan: Plan, pos, q, mu, theta):
+    """Energy with point quadrupoles (theta [n, 6]); first derivatives only."""
+    if mu is None:
+        mu = torch.zeros_like(pos)
+    return PMEQuadEnergy.apply(plan, pos, q, mu, theta)
+
+
 def pme_energy(plan: Plan, pos, q, mu=None):
     if mu is None:
         mu = torch.zeros_like(pos)

@@ -132,3 +132,59 @@ def test_quad_refusals(gb):
     with pytest.raises(gb.PMEError) as e:
         plan.forward_quad(*t[:3], None)
     assert e.value.status == 1   # PME_ERR_ARG
+
+
+def test_quad_triclinic_cell(gb):
+    # a sheared cell: the mesh sees Theta through D^T Theta D, which a transposed D would
+    # leave unchanged in a cubic box
+    box = np.array([[14.0, 0.0, 0.0], [3.0, 13.5, 0.0], [-2.0, 1.5, 15.0]])
+    rng = np.random.default_rng(41)
+    n = 96
+    pos = f32(rng.uniform(size=(n, 3)) @ box)
+    q = rng.normal(size=n)
+    q = f32(q - q.mean())
+    mu = f32(rng.normal(0, 0.05, size=(n, 3)))
+    th = f32(W.quadrupoles(n, 0.1, seed=42))
+    mesh, p, a, rc = (28, 27, 30), 6, 0.35, 6.5
+    plan = gb.Plan(box, mesh, p, a, rc, max_ions=1024)
+    t = [torch.tensor(np.float32(x), device="cuda") for x in (pos, q, mu, th)]
+    got = {k: v.cpu().numpy().astype(np.float64) for k, v in plan.forward_quad(*t).items()}
+    ref = O2.PMEOracle(box, mesh, p, a, rc).evaluate_quad(pos, q, mu, th)
+    assert abs(got["energy"][0] - ref["energy"]) < _ebar(ref)
+    assert relrmse(got["force"], ref["force"]) < TOL_F
+    assert relrmse(got["field_grad"], sym6(ref["field_grad"])) < TOL_F
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4, 5, 7])
+def test_quad_spline_orders(gb, order):
+    fr, mesh, _, a, rc, pos, q, mu, th = _inputs("nacl64")
+    _, got = _gpu(gb, fr, mesh, order, a, rc, pos, q, mu, th)
+    ref = O2.PMEOracle(fr.box, mesh, order, a, rc).evaluate_quad(pos, q, mu, th)
+    assert abs(got["energy"][0] - ref["energy"]) < _ebar(ref)
+    assert relrmse(got["force"], ref["force"]) < TOL_F
+    assert relrmse(got["field_grad"], sym6(ref["field_grad"])) < TOL_F
+
+
+def test_quad_energy_autograd(gb):
+    # first derivatives of pme_quad_energy are the forward's outputs; the energy is quadratic
+    # in (q, mu, Theta), so a central difference along Theta is exact up to rounding
+    fr, mesh, p, a, rc, pos, q, mu, th = _inputs("nacl1000_ragged")
+    plan = gb.Plan(fr.box, mesh, p, a, rc, max_ions=1024)
+    th6 = sym6(th)
+    t = [torch.tensor(np.float32(x), device="cuda", requires_grad=True) for x in (pos, q, mu, th6)]
+    E = gb.pme_quad_energy(plan, *t)
+    gpos, gq, gmu, gth = torch.autograd.grad(E, t)
+    out = plan.forward_quad(*[x.detach() for x in t])
+    assert torch.equal(gpos, -out["force"])
+    assert torch.equal(gq, out["phi"])
+    rng = np.random.default_rng(43)
+    d = torch.tensor(np.float32(rng.normal(size=th6.shape)), device="cuda")
+    h = 0.05
+    ep = plan.forward_quad(t[0].detach(), t[1].detach(), t[2].detach(), t[3].detach() + h * d)["energy"].item()
+    em = plan.forward_quad(t[0].detach(), t[1].detach(), t[2].detach(), t[3].detach() - h * d)["energy"].item()
+    fd = (ep - em) / (2 * h)
+    ad = float((gth.double() * d.double()).sum())
+    assert abs(fd - ad) < 1e-3 * abs(ad) + 2e-5 * abs(E.item()) / h
+    with pytest.raises(RuntimeError):
+        gg = torch.autograd.grad(gb.pme_quad_energy(plan, *t), t[0], create_graph=True)[0]
+        torch.autograd.grad(gg.sum(), t[0])
