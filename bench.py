@@ -78,6 +78,27 @@ PAIR_FLOPS = {"fwd.pair": 80.0, "bwd.pair": 450.0, "fwd.pair_eval": 80.0, "bwd.p
 # and the 3-component Theta_i : grad^3 phi: 380 per pair inside rcut.
 QUAD_PAIR_FLOPS = 380.0
 QUAD_METRIC = "PME q+mu+Theta fwd Mion-evals/s @32k ions"
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each kernel from one
+# ncu capture of the same kernels on the same workload (cold cache: ncu flushes the caches
+# before each replay); the summaries, with their commands, are under profiles/.
+MEASURED_TRAFFIC = {
+    "fwd.pair_eval": (52.047104e6 + 0.142848e6, "profiles/k_spread_gather_pair_nacl32k.md"),
+    "bwd.pair_eval": (53.097728e6 + 0.274176e6, "profiles/k_spread_gather_pair_nacl32k.md"),
+    "fwd.spread": (1.611264e6, "profiles/k_spread_gather_pair_nacl32k.md"),
+    "bwd.spread": (2.666752e6, "profiles/k_spread_gather_pair_nacl32k.md"),
+    "fwd.gather": (9.455360e6, "profiles/k_spread_gather_pair_nacl32k.md"),
+    "bwd.gather": (19.428608e6, "profiles/k_spread_gather_pair_nacl32k.md"),
+    "quad.pair": (21.713631e9 * 111.744e-6, "profiles/k_pair_quad_nacl32k.md"),
+}
+
+
+def traffic_of(stage: str, workload: str):
+    """(bytes per launch, source) when a capture of this kernel on this workload exists."""
+    if workload != "nacl32k" or stage not in MEASURED_TRAFFIC:
+        return None, None
+    return MEASURED_TRAFFIC[stage]
+
+
 # Stages timed as one kernel of this library (the roofline's dominant kernel is picked among
 # them; sort and pair are several kernels each, cuFFT is a library call).
 SINGLE_KERNEL_STAGES = ("spread", "influence", "gather", "combine", "pair_eval")
@@ -587,17 +608,20 @@ def run_ours(args):
 
         def roofline(stage):
             avg_ms = stages[stage][0] / stages[stage][1]
+            tr, tr_src = traffic_of(stage, args.workload)
             if stage in PAIR_FLOPS:
                 fl = n * ppi * PAIR_FLOPS[stage]
                 ach = fl / (avg_ms / 1e3) / 1e12
                 return {"kernel": stage, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
-                        "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                        "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": tr,
+                        "traffic_source": tr_src,
                         "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
                         "avg_launch_ms": avg_ms, "flops_per_launch": fl}
             by = stage_bytes(stage, n, M, Mh)
             ach = by / (avg_ms / 1e3) / 1e9
             return {"kernel": stage, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                    "frac": ach / peak, "traffic": None, "peak_source": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)",
+                    "frac": ach / peak, "traffic": tr, "traffic_source": tr_src,
+                    "peak_source": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)",
                     "avg_launch_ms": avg_ms, "bytes_per_launch": by}
 
         roof = roofline(dom) if dom is not None else None
@@ -683,8 +707,9 @@ def run_quad(args):
     if dom == "fwd.pair":
         fl = n * ppi * QUAD_PAIR_FLOPS
         ach = fl / (avg_ms / 1e3) / 1e12
+        tr, tr_src = traffic_of("quad.pair", args.workload)
         roof = {"kernel": "k_pair_quad", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": tr, "traffic_source": tr_src,
                 "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
                 "avg_launch_ms": avg_ms, "flops_per_launch": fl}
     else:
