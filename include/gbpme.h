@@ -201,9 +201,10 @@ int pme_forward_virial(pme_plan_t plan, void* stream, int n, const float* pos, c
  *   -(alpha/sqrt(pi)) [-(4 alpha^2/3) q tr Theta + (4 alpha^4/5)((tr Theta)^2 + 2 Theta:Theta)].
  * Outputs as pme_forward, except field_grad = -dE/dTheta (the symmetric matrix G with
  * dE = -G : dTheta for symmetric dTheta; equal to pme_forward's field gradient when Theta = 0)
- * and force = -dE/dr including Theta : grad^3 phi. Single-frame plans with recip_method 0;
- * no CUDA graph, no virial and no backward (a later pme_backward recomputes from its own
- * inputs). Pointers follow pme_forward's host/device rule. theta may be NULL only when n = 0. */
+ * and force = -dE/dr including Theta : grad^3 phi. Plans with recip_method 0 (batched plans:
+ * pme_batch_forward_quad); no CUDA graph, no virial and no backward (a later pme_backward
+ * recomputes from its own inputs). Pointers follow pme_forward's host/device rule. theta may
+ * be NULL only when n = 0. */
 int pme_forward_quad(pme_plan_t plan, void* stream, int n, const float* pos, const float* q,
                      const float* mu, const float* theta, double* energy, float* force, float* phi,
                      float* field, float* field_grad);
@@ -234,6 +235,11 @@ int pme_batch_forward(pme_plan_t plan, void* stream, const float* pos, const flo
 int pme_batch_forward_virial(pme_plan_t plan, void* stream, const float* pos, const float* q,
                              const float* mu, double* energy, float* force, float* phi,
                              float* field, float* field_grad, double* virial);
+
+/* As pme_forward_quad for every frame: theta [offsets[F]][6], energy [F] float64. */
+int pme_batch_forward_quad(pme_plan_t plan, void* stream, const float* pos, const float* q,
+                           const float* mu, const float* theta, double* energy, float* force,
+                           float* phi, float* field, float* field_grad);
 
 /* As pme_backward for every frame; g_energy is [F] float64 (one cotangent per frame). */
 int pme_batch_backward(pme_plan_t plan, void* stream, const float* pos, const float* q,

@@ -57,6 +57,7 @@ _SIGS = {
     "pme_batch_frames": (c_int, [c_void_p]),
     "pme_batch_forward": (c_int, [c_void_p, c_void_p] + [c_void_p] * 8),
     "pme_batch_forward_virial": (c_int, [c_void_p, c_void_p] + [c_void_p] * 9),
+    "pme_batch_forward_quad": (c_int, [c_void_p, c_void_p] + [c_void_p] * 9),
     "pme_batch_backward": (c_int, [c_void_p, c_void_p] + [c_void_p] * 10),
 }
 

@@ -324,7 +324,7 @@ int launch_gather(pme_plan_t p, cudaStream_t s, int n, const float* mesh, bool t
 
 int launch_gather_quad(pme_plan_t p, cudaStream_t s, int n, const float* mesh, const float* theta,
                        float* out, float* qout) {
-  if (p->batch) return set_error(p, PME_ERR_UNSUPPORTED, "quadrupoles need a single-frame plan");
+  if (p->batch) return launch_t<2, true>(p, s, n, mesh, nullptr, out, theta, qout);
   return launch_t<2, false>(p, s, n, mesh, nullptr, out, theta, qout);
 }
 

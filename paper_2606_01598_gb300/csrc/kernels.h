@@ -37,8 +37,8 @@ int launch_input_check(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool w
 // keep_rho (tangent pass, nullable): *keep_rho == 0 means rho is in place from the forward on
 // the same inputs; only d rho is formed and written.
 int launch_spread(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh, const int* keep_rho = nullptr);
-// Quadrupole forward (single-frame plans): rho of charges, dipoles and point quadrupoles
-// theta [caller index][6] into mesh + mesh_off.
+// Quadrupole forward: rho of charges, dipoles and point quadrupoles theta [caller index][6]
+// into mesh + mesh_off of every frame.
 int launch_spread_quad(pme_plan_t p, cudaStream_t s, const float* theta, float* mesh);
 
 // influence.cu: in-place G C / V multiply of every frame's spectrum (and tangent spectrum)
@@ -87,8 +87,8 @@ int launch_gather(pme_plan_t p, cudaStream_t s, int n, const float* mesh, bool t
 int launch_gather_quad(pme_plan_t p, cudaStream_t s, int n, const float* mesh, const float* theta,
                        float* out, float* qout);
 
-// quad.cu: real-space pair term with point quadrupoles (single-frame plans): the forward
-// layout of the pair potential of every source in out, Theta_i : grad^3 phi at qout[orig][4..6].
+// quad.cu: real-space pair term with point quadrupoles (every frame): the forward layout of
+// the pair potential of every source in out, Theta_i : grad^3 phi at qout[orig][4..6].
 int launch_pair_quad(pme_plan_t p, cudaStream_t s, int n, const float* theta, float* out, float* qout);
 
 // pair.cu: real-space erfc pair term over the cell list, same output layouts as gather.

@@ -629,7 +629,7 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
   A(&p->pr.dr, ni);
   A(&p->mesh_out, ni * 10);
   A(&p->pair_out, ni * 10);
-  if (single) A(&p->quad_out, ni * 8);
+  A(&p->quad_out, ni * 8);
   A(&p->e_ion, ni);
   A(&p->epart, size_t(p->total_blocks) + 1);
   A(&p->flags, 1);
@@ -1327,9 +1327,9 @@ int pme_forward_virial(pme_plan_t p, void* stream, int n, const float* pos, cons
   return sg.finish();
 }
 
-// Forward with point quadrupoles (the rank-2 channel): sort, quadrupole spread, the mesh
-// convolution, quadrupole gather, the quadrupole pair kernel, combine. Runs directly (no
-// graph) and leaves nothing for a backward to reuse.
+// Forward with point quadrupoles (the rank-2 channel) over every frame of the plan: sort,
+// quadrupole spread, the mesh convolution, quadrupole gather, the quadrupole pair kernel,
+// combine. Runs directly (no graph) and leaves nothing for a backward to reuse.
 static int run_forward_quad(pme_plan_t p, cudaStream_t s, const IonInputs& in, double* e_out,
                             float* f_out, float* p_out, float* fl_out, float* fg_out) {
   const int n = in.n;
@@ -1389,6 +1389,33 @@ int pme_forward_quad(pme_plan_t p, void* stream, int n, const float* pos, const 
   in.theta = sg.in(theta, 6, kTheta);
   in.n = n;
   double* e_out = sg.out_d(energy, 1, 0);
+  float* f_out = sg.out(force, 3, kOF);
+  float* p_out = sg.out(phi, 1, kOPhi);
+  float* fl_out = sg.out(field, 3, kOField);
+  float* fg_out = sg.out(field_grad, 6, kOFG);
+  if (sg.status) return sg.status;
+  if ((st = run_forward_quad(p, s, in, e_out, f_out, p_out, fl_out, fg_out))) return st;
+  return sg.finish();
+}
+
+static int check_batch(pme_plan_t p, const float* pos, const float* q);
+
+int pme_batch_forward_quad(pme_plan_t p, void* stream, const float* pos, const float* q,
+                           const float* mu, const float* theta, double* energy, float* force,
+                           float* phi, float* field, float* field_grad) {
+  int st = check_batch(p, pos, q);
+  if (st) return st;
+  const int n = p->frame_offsets[p->nframes];
+  if (n > 0 && !theta) return set_error(p, PME_ERR_ARG, "theta is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Staging sg(p, s, n);
+  IonInputs in{};
+  in.pos = sg.in(pos, 3, kPos);
+  in.q = sg.in(q, 1, kQ);
+  in.mu = sg.in(mu, 3, kMu);
+  in.theta = sg.in(theta, 6, kTheta);
+  in.n = n;
+  double* e_out = sg.out_d(energy, p->nframes, 0);
   float* f_out = sg.out(force, 3, kOF);
   float* p_out = sg.out(phi, 1, kOPhi);
   float* fl_out = sg.out(field, 3, kOField);

@@ -1,4 +1,4 @@
-// Real-space pair term with point quadrupoles: the rank-2 channel of the multipole operator
+// Real-space pair term with point quadrupoles (every frame of the plan): the rank-2 channel of the multipole operator
 // L_i = q_i + mu_i . grad + Theta_i : grad grad (an extension; the paper names quadrupolar
 // channels as future work).
 //
@@ -40,14 +40,14 @@ namespace {
 constexpr int kQuadThreads = 128;
 
 struct QuadPairArgs {
-  Geometry g;
+  FrameDesc one;
+  FrameMaps maps;
   PairRecords pr;
   const int* start_c;
   const float* theta;   // [caller index][6]
   float* out;           // [caller index][10]
   float* qout;          // [caller index][8], this kernel writes 4..6
   int n;
-  int cell_off;         // first global cell key of the frame
   float alpha;
   float c[6];           // (2 alpha^2)^l / (alpha sqrt(pi)), l = 1..5 at c[l]
 };
@@ -136,6 +136,7 @@ constexpr int kHitCap = 64;   // < 32 carried over + 32 appended per test round
 constexpr int kCandCap = 512; // candidates listed per warp at a time
 constexpr int kSegShift = 27; // candidate entry: (segment lane << 27) | sorted index
 
+template <bool BATCH>
 __global__ void __launch_bounds__(kQuadThreads) k_pair_quad(QuadPairArgs a) {
   __shared__ float4 s_hit[kWarps][kHitCap];   // r (x, y, z), source j (int bits)
   __shared__ unsigned s_cand[kWarps][kCandCap];
@@ -143,7 +144,8 @@ __global__ void __launch_bounds__(kQuadThreads) k_pair_quad(QuadPairArgs a) {
   const int i = blockIdx.x * kWarps + wid;
   if (i >= a.n) return;   // warp-uniform
   float4* hits = s_hit[wid];
-  const Geometry& g = a.g;
+  const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, BATCH ? a.maps.sorted_frame[i] : 0);
+  const Geometry& g = F.g;
   const int4 ci = a.pr.idx[i];
   const float4 fi = a.pr.fq[i];
   const Sym A = load_sym(a.theta + size_t(ci.w) * 6);
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(kQuadThreads) k_pair_quad(QuadPairArgs a) {
       fxo = fi.x - float(ox);
       fyo = fi.y - float(oy);
       zxy = ox == 0 && oy == 0;
-      const int row = a.cell_off + (cx * ncy + cy) * ncz;
+      const int row = F.cell_off + (cx * ncy + cy) * ncz;
       if (zrun) {
         const int z0 = ci.z - kz, z1 = ci.z + kz;
         if (z0 < 0) {
@@ -278,23 +280,23 @@ __global__ void __launch_bounds__(kQuadThreads) k_pair_quad(QuadPairArgs a) {
 }  // namespace
 
 int launch_pair_quad(pme_plan_t p, cudaStream_t s, int n, const float* theta, float* out, float* qout) {
-  if (p->batch) return set_error(p, PME_ERR_UNSUPPORTED, "quadrupoles need a single-frame plan");
   if (n <= 0) return PME_OK;
   if (n >= (1 << 27)) return set_error(p, PME_ERR_UNSUPPORTED, "quadrupole pair term: more than 2^27 ions");
   QuadPairArgs a;
-  a.g = p->g;
+  a.one = p->frames_h[0];
+  a.maps = p->maps;
   a.pr = p->pr;
   a.start_c = p->sb.start_c;
   a.theta = theta;
   a.out = out;
   a.qout = qout;
   a.n = n;
-  a.cell_off = p->frames_h[0].cell_off;
   a.alpha = float(p->alpha);
   const double al = p->alpha;
   for (int l = 0; l < 6; ++l) a.c[l] = float(std::pow(2.0 * al * al, l) / (al * std::sqrt(kPi)));
   const int grid = (n + kWarps - 1) / kWarps;
-  k_pair_quad<<<grid, kQuadThreads, 0, s>>>(a);
+  if (p->batch) k_pair_quad<true><<<grid, kQuadThreads, 0, s>>>(a);
+  else k_pair_quad<false><<<grid, kQuadThreads, 0, s>>>(a);
   count_launch();
   return check_launch(p, "k_pair_quad");
 }

@@ -497,7 +497,7 @@ int launch_spread(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh, const
 }
 
 int launch_spread_quad(pme_plan_t p, cudaStream_t s, const float* theta, float* mesh) {
-  if (p->batch) return set_error(p, PME_ERR_UNSUPPORTED, "quadrupoles need a single-frame plan");
+  if (p->batch) return launch_t<2, true>(p, s, mesh, nullptr, theta);
   return launch_t<2, false>(p, s, mesh, nullptr, theta);
 }
 

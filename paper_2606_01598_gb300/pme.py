@@ -446,6 +446,39 @@ class BatchPlan(Plan):
                 torch.cuda.current_stream(self.device).synchronize()
         return out
 
+    def forward_quad(self, pos, q, mu, theta, *, energy=True, force=True, phi=True, field=True,
+                     field_grad=True):
+        """pme_batch_forward_quad: every frame with point quadrupoles theta [n, 6] (xx, yy, zz,
+        xy, xz, yz) or [n, 3, 3]; energy [F]; field_grad = -dE/dTheta."""
+        dev = pos.device if isinstance(pos, torch.Tensor) else torch.device("cpu")
+        on_dev = dev.type == "cuda"
+        if theta is not None and tuple(theta.shape[-2:]) == (3, 3):
+            t = torch.as_tensor(theta)
+            theta = torch.stack([t[:, 0, 0], t[:, 1, 1], t[:, 2, 2], t[:, 0, 1], t[:, 0, 2], t[:, 1, 2]], 1)
+        pos, q, mu, theta = (_f32(t, dev) for t in (pos, q, mu, theta))
+        n = self.n
+        alloc = dict(device=dev, pin_memory=True) if not on_dev else dict(device=dev)
+        out = {}
+        if energy:
+            out["energy"] = torch.empty(self.nframes, dtype=torch.float64, **alloc)
+        if force:
+            out["force"] = torch.empty((n, 3), dtype=torch.float32, **alloc)
+        if phi:
+            out["phi"] = torch.empty(n, dtype=torch.float32, **alloc)
+        if field:
+            out["field"] = torch.empty((n, 3), dtype=torch.float32, **alloc)
+        if field_grad:
+            out["field_grad"] = torch.empty((n, 6), dtype=torch.float32, **alloc)
+        with _on_device(self.device):
+            st = self.lib.pme_batch_forward_quad(self.handle, _stream_handle(self.device), _ptr(pos), _ptr(q),
+                                                 _ptr(mu), _ptr(theta), _ptr(out.get("energy")),
+                                                 _ptr(out.get("force")), _ptr(out.get("phi")),
+                                                 _ptr(out.get("field")), _ptr(out.get("field_grad")))
+            self._check(st, "pme_batch_forward_quad")
+            if not on_dev:
+                torch.cuda.current_stream(self.device).synchronize()
+        return out
+
     def backward(self, pos, q, mu=None, g_energy=None, g_force=None, g_phi=None, g_field=None):
         dev = pos.device if isinstance(pos, torch.Tensor) else torch.device("cpu")
         on_dev = dev.type == "cuda"

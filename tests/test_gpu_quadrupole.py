@@ -188,3 +188,35 @@ def test_quad_energy_autograd(gb):
     with pytest.raises(RuntimeError):
         gg = torch.autograd.grad(gb.pme_quad_energy(plan, *t), t[0], create_graph=True)[0]
         torch.autograd.grad(gg.sum(), t[0])
+
+
+def test_quad_batch_matches_single_frames(gb):
+    specs = W.uneven_frames(n_frames=8, seed=1003)
+    frames = [sp.frame for sp in specs]
+    meshes = [gb.mesh_dims(fr.box, sp.spacing, rule=1, strategy=1, clamp=(16, 48)) for fr, sp in zip(frames, specs)]
+    orders = [sp.order for sp in specs]
+    offsets = np.concatenate([[0], np.cumsum([fr.n for fr in frames])]).astype(np.int64)
+    pos = np.concatenate([f32(fr.pos) for fr in frames])
+    q = np.concatenate([f32(fr.q) for fr in frames])
+    mu = np.concatenate([f32(fr.mu) for fr in frames])
+    th = sym6(f32(W.quadrupoles(len(q), 0.1, seed=44)))
+    c = lambda x: torch.tensor(np.float32(x), device="cuda")
+    bp = gb.BatchPlan([fr.box for fr in frames], meshes, orders, offsets, 0.30, 9.0)
+    out = bp.forward_quad(c(pos), c(q), c(mu), c(th))
+    for f, fr in enumerate(frames):
+        lo, hi = offsets[f], offsets[f + 1]
+        sp = gb.Plan(fr.box, meshes[f], orders[f], 0.30, 9.0, max_ions=max(fr.n, 64), fft=bp.fft_kind)
+        ref = sp.forward_quad(c(pos[lo:hi]), c(q[lo:hi]), c(mu[lo:hi]), c(th[lo:hi]))
+        e = ref["energy"].item()
+        assert abs(out["energy"][f].item() - e) < 1e-6 * abs(e), f
+        for k in ("force", "phi", "field", "field_grad"):
+            assert relrmse(out[k][lo:hi].cpu().numpy(), ref[k].cpu().numpy()) < 1e-6, (f, k)
+        sp.close()
+    # one frame against the oracle
+    f = 3
+    lo, hi = offsets[f], offsets[f + 1]
+    o = O2.PMEOracle(frames[f].box, meshes[f], orders[f], 0.30, 9.0).evaluate_quad(
+        pos[lo:hi], q[lo:hi], mu[lo:hi], O1Q.sym_from6(th[lo:hi]))
+    assert abs(out["energy"][f].item() - o["energy"]) < _ebar(o)
+    assert relrmse(out["force"][lo:hi].cpu().numpy(), o["force"]) < TOL_F
+    assert relrmse(out["field_grad"][lo:hi].cpu().numpy(), sym6(o["field_grad"])) < TOL_F
