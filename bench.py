@@ -88,7 +88,6 @@ MEASURED_TRAFFIC = {
     "bwd.spread": (2.666752e6, "profiles/k_spread_gather_pair_nacl32k.md"),
     "fwd.gather": (9.455360e6, "profiles/k_spread_gather_pair_nacl32k.md"),
     "bwd.gather": (19.428608e6, "profiles/k_spread_gather_pair_nacl32k.md"),
-    "quad.pair": (21.713631e9 * 111.744e-6, "profiles/k_pair_quad_nacl32k.md"),
 }
 
 
@@ -701,14 +700,18 @@ def run_quad(args):
     Mh = cfg["mesh"][0] * cfg["mesh"][1] * (cfg["mesh"][2] // 2 + 1)
     ppi = pairs_per_ion(n, abs(float(np.linalg.det(fr.box))), cfg["rcut"])
     peak, peak_kind = load_peaks()
-    kernels = {k: v for k, v in stages.items() if k.split(".")[1] in ("pair", "spread", "gather", "influence")}
+    # single kernels: the list-driven pair evaluation (with hit lists) or the cell walk, spread,
+    # gather, influence
+    single = ("pair_eval", "spread", "gather", "influence") if "fwd.pair_eval" in stages else \
+        ("pair", "spread", "gather", "influence")
+    kernels = {k: v for k, v in stages.items() if k.split(".")[1] in single}
     dom = max(kernels, key=lambda k: kernels[k][0])
     avg_ms = stages[dom][0] / stages[dom][1]
-    if dom == "fwd.pair":
+    if dom in ("fwd.pair", "fwd.pair_eval"):
         fl = n * ppi * QUAD_PAIR_FLOPS
         ach = fl / (avg_ms / 1e3) / 1e12
-        tr, tr_src = traffic_of("quad.pair", args.workload)
-        roof = {"kernel": "k_pair_quad", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+        tr, tr_src = traffic_of("quad." + dom.split(".")[1], args.workload)
+        roof = {"kernel": "k_pair_quad_listed" if dom == "fwd.pair_eval" else "k_pair_quad", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": tr, "traffic_source": tr_src,
                 "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
                 "avg_launch_ms": avg_ms, "flops_per_launch": fl}

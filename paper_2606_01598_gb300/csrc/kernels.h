@@ -89,7 +89,12 @@ int launch_gather_quad(pme_plan_t p, cudaStream_t s, int n, const float* mesh, c
 
 // quad.cu: real-space pair term with point quadrupoles (every frame): the forward layout of
 // the pair potential of every source in out, Theta_i : grad^3 phi at qout[orig][4..6].
-int launch_pair_quad(pme_plan_t p, cudaStream_t s, int n, const float* theta, float* out, float* qout);
+// skip (nullable): return at once when *skip == 0 (the hit lists hold).
+int launch_pair_quad(pme_plan_t p, cudaStream_t s, int n, const float* theta, float* out, float* qout,
+                     const int* skip = nullptr);
+// The same from the plan's hit lists (runs only when *flag == 0).
+int launch_pair_quad_listed(pme_plan_t p, cudaStream_t s, int n, const float* theta, float* out,
+                            float* qout, const int* flag);
 
 // pair.cu: real-space erfc pair term over the cell list, same output layouts as gather.
 // The fused pass; skip (nullable): return at once when *skip == 0.

@@ -1346,7 +1346,17 @@ static int run_forward_quad(pme_plan_t p, cudaStream_t s, const IonInputs& in, d
   if (fork) {
     if (p->opts.overlap_pair && (st = fork_side(p, s))) return st;
     t = prof_begin(p, 6, ps);
-    if ((st = launch_pair_quad(p, ps, n, in.theta, p->pair_out, p->quad_out))) return st;
+    if (p->plist) {
+      // hit lists from the list pass, evaluated per ion; the cell walk only if one overflowed
+      if ((st = launch_pair_build(p, ps, n, p->cache_bad))) return st;
+      if ((st = launch_pair_quad(p, ps, n, in.theta, p->pair_out, p->quad_out, p->cache_bad))) return st;
+      const int te = prof_begin(p, 8, ps);
+      if ((st = launch_pair_quad_listed(p, ps, n, in.theta, p->pair_out, p->quad_out, p->cache_bad)))
+        return st;
+      prof_end(p, te, ps);
+    } else if ((st = launch_pair_quad(p, ps, n, in.theta, p->pair_out, p->quad_out))) {
+      return st;
+    }
     prof_end(p, t, ps);
   }
   t = prof_begin(p, 1, s);

@@ -29,6 +29,10 @@
 // each. Per-lane sums are reduced with warp shuffles in a fixed order, so the result is
 // reproducible. Output in caller order: out[10] = phi, grad phi, grad^2 phi (xx yy zz xy xz
 // yz); qout[4..6] = A : grad^3 phi.
+//
+// When the plan keeps pair-hit lists, the forward builds them with the charge-dipole list pass
+// (k_pair_build: the ions of a cell share one candidate stream) and k_pair_quad_listed
+// evaluates each ion's list; the cell-walking kernel then runs only if a list overflowed.
 #include <cmath>
 
 #include "kernels.h"
@@ -49,6 +53,13 @@ struct QuadPairArgs {
   float* qout;          // [caller index][8], this kernel writes 4..6
   int n;
   float alpha;
+  // hit lists of the list pass (k_pair_build): per ion (r, j) in stream order, list_cnt hits
+  // or -1 when more than list_cap; flag = that pass's overflow flag: the list-driven kernel
+  // runs when *flag == 0, the cell-walking kernel when *flag != 0 (or flag null)
+  const float4* list;
+  const int* list_cnt;
+  int list_cap;
+  const int* flag;
   float c[6];           // (2 alpha^2)^l / (alpha sqrt(pi)), l = 1..5 at c[l]
 };
 
@@ -140,6 +151,7 @@ template <bool BATCH>
 __global__ void __launch_bounds__(kQuadThreads) k_pair_quad(QuadPairArgs a) {
   __shared__ float4 s_hit[kWarps][kHitCap];   // r (x, y, z), source j (int bits)
   __shared__ unsigned s_cand[kWarps][kCandCap];
+  if (a.flag && *a.flag == 0) return;   // the lists hold: the list-driven kernel does the work
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * kWarps + wid;
   if (i >= a.n) return;   // warp-uniform
@@ -277,11 +289,40 @@ __global__ void __launch_bounds__(kQuadThreads) k_pair_quad(QuadPairArgs a) {
   }
 }
 
-}  // namespace
+// The same sums from the hit lists of the list pass: one warp per ion, lane l takes hits
+// l, l + 32, ... in order; shuffle reduction in a fixed order.
+template <bool BATCH>
+__global__ void __launch_bounds__(kQuadThreads) k_pair_quad_listed(QuadPairArgs a) {
+  if (*a.flag != 0) return;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kWarps + wid;
+  if (i >= a.n) return;   // warp-uniform
+  const int4 ci = a.pr.idx[i];
+  const Sym A = load_sym(a.theta + size_t(ci.w) * 6);
+  const float trA = A.xx + A.yy + A.zz;
+  QuadAcc S;
+  const int c = a.list_cnt[i];
+  const float4* li = a.list + size_t(i) * a.list_cap;
+  for (int k = lane; k < c; k += 32) {
+    const float4 h = li[k];
+    quad_pair(a, A, trA, __float_as_int(h.w), h.x, h.y, h.z, S);
+  }
+  const float v[13] = {warp_sum_f(S.phi), warp_sum_f(S.gx), warp_sum_f(S.gy), warp_sum_f(S.gz),
+                       warp_sum_f(S.hxx), warp_sum_f(S.hyy), warp_sum_f(S.hzz), warp_sum_f(S.hxy),
+                       warp_sum_f(S.hxz), warp_sum_f(S.hyz), warp_sum_f(S.tx), warp_sum_f(S.ty),
+                       warp_sum_f(S.tz)};
+  if (lane == 0) {
+    float* o = a.out + size_t(ci.w) * 10;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) o[k] = v[k];
+    float* qo = a.qout + size_t(ci.w) * 8;
+    qo[4] = v[10];
+    qo[5] = v[11];
+    qo[6] = v[12];
+  }
+}
 
-int launch_pair_quad(pme_plan_t p, cudaStream_t s, int n, const float* theta, float* out, float* qout) {
-  if (n <= 0) return PME_OK;
-  if (n >= (1 << 27)) return set_error(p, PME_ERR_UNSUPPORTED, "quadrupole pair term: more than 2^27 ions");
+QuadPairArgs quad_args(pme_plan_t p, int n, const float* theta, float* out, float* qout, const int* flag) {
   QuadPairArgs a;
   a.one = p->frames_h[0];
   a.maps = p->maps;
@@ -294,6 +335,31 @@ int launch_pair_quad(pme_plan_t p, cudaStream_t s, int n, const float* theta, fl
   a.alpha = float(p->alpha);
   const double al = p->alpha;
   for (int l = 0; l < 6; ++l) a.c[l] = float(std::pow(2.0 * al * al, l) / (al * std::sqrt(kPi)));
+  a.list = p->plist;
+  a.list_cnt = p->plist_cnt;
+  a.list_cap = p->plist_cap;
+  a.flag = flag;
+  return a;
+}
+
+}  // namespace
+
+int launch_pair_quad_listed(pme_plan_t p, cudaStream_t s, int n, const float* theta, float* out,
+                            float* qout, const int* flag) {
+  if (n <= 0) return PME_OK;
+  const QuadPairArgs a = quad_args(p, n, theta, out, qout, flag);
+  const int grid = (n + kWarps - 1) / kWarps;
+  if (p->batch) k_pair_quad_listed<true><<<grid, kQuadThreads, 0, s>>>(a);
+  else k_pair_quad_listed<false><<<grid, kQuadThreads, 0, s>>>(a);
+  count_launch();
+  return check_launch(p, "k_pair_quad_listed");
+}
+
+int launch_pair_quad(pme_plan_t p, cudaStream_t s, int n, const float* theta, float* out, float* qout,
+                     const int* skip) {
+  if (n <= 0) return PME_OK;
+  if (n >= (1 << 27)) return set_error(p, PME_ERR_UNSUPPORTED, "quadrupole pair term: more than 2^27 ions");
+  const QuadPairArgs a = quad_args(p, n, theta, out, qout, skip);
   const int grid = (n + kWarps - 1) / kWarps;
   if (p->batch) k_pair_quad<true><<<grid, kQuadThreads, 0, s>>>(a);
   else k_pair_quad<false><<<grid, kQuadThreads, 0, s>>>(a);

@@ -220,3 +220,37 @@ def test_quad_batch_matches_single_frames(gb):
     assert abs(out["energy"][f].item() - o["energy"]) < _ebar(o)
     assert relrmse(out["force"][lo:hi].cpu().numpy(), o["force"]) < TOL_F
     assert relrmse(out["field_grad"][lo:hi].cpu().numpy(), sym6(o["field_grad"])) < TOL_F
+
+
+def test_quad_pair_lists_disabled_and_overflowing(gb):
+    # without hit lists (a plan whose lists would exceed 1 GiB) the cell-walking kernel does the
+    # pair term; with lists the list-driven one does; a clustered frame overflows the lists and
+    # falls back to the cell walk. All agree with each other and with the oracle.
+    fr, mesh, p, a, rc, pos, q, mu, th = _inputs("nacl1000_ragged")
+    c = lambda x: torch.tensor(np.float32(x), device="cuda")
+    outs = []
+    for max_ions in (1024, 1 << 18):
+        plan = gb.Plan(fr.box, mesh, p, a, rc, max_ions=max_ions)
+        outs.append({k: v.cpu().numpy() for k, v in plan.forward_quad(c(pos), c(q), c(mu), c(th)).items()})
+        plan.close()
+    assert abs(outs[0]["energy"][0] - outs[1]["energy"][0]) < 1e-6 * abs(outs[1]["energy"][0])
+    for k in ("force", "phi", "field", "field_grad"):
+        assert relrmse(outs[0][k], outs[1][k]) < 1e-6, k
+    rng = np.random.default_rng(45)
+    box = np.diag([40.0, 40.0, 40.0])
+    pts = []
+    while len(pts) < 200:
+        x = rng.uniform(-7.0, 7.0, 3)
+        if np.linalg.norm(x) < 7.0 and all(np.linalg.norm(x - y) > 1.0 for y in pts):
+            pts.append(x)
+    pc = f32(20.0 + np.array(pts))
+    qc = f32(np.where(np.arange(200) % 2 == 0, 0.5, -0.5))
+    muc = f32(rng.normal(0, 0.05, (200, 3)))
+    thc = f32(W.quadrupoles(200, 0.1, seed=46))
+    plan = gb.Plan(box, (40, 40, 40), 6, 0.30, 9.0, max_ions=1024)
+    out = plan.forward_quad(c(pc), c(qc), c(muc), c(thc))
+    ref = O2.PMEOracle(box, (40, 40, 40), 6, 0.30, 9.0).evaluate_quad(pc, qc, muc, thc)
+    assert abs(out["energy"].item() - ref["energy"]) < _ebar(ref)
+    assert relrmse(out["force"].cpu().numpy(), ref["force"]) < TOL_F
+    assert relrmse(out["field_grad"].cpu().numpy(), sym6(ref["field_grad"])) < TOL_F
+    plan.close()
