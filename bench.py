@@ -73,7 +73,7 @@ def stage_bytes(stage: str, N: int, M: int, Mh: int) -> float:
 # rcut are not counted. The same counts apply to the list-driven evaluation kernel alone
 # (stage pair_eval), which evaluates exactly the pairs inside rcut.
 PAIR_FLOPS = {"fwd.pair": 80.0, "bwd.pair": 450.0, "fwd.pair_eval": 80.0, "bwd.pair_eval": 450.0}
-# Quadrupole pair kernel (csrc/quad.cu), same counting: radial functions B0..B5, the
+# Quadrupole pair kernels (csrc/quad.cu), same counting: radial functions B0..B5, the
 # quadrupole products B r, A r and their contractions, phi, grad phi, the 6-component Hessian
 # and the 3-component Theta_i : grad^3 phi: 380 per pair inside rcut.
 QUAD_PAIR_FLOPS = 380.0
@@ -88,6 +88,7 @@ MEASURED_TRAFFIC = {
     "bwd.spread": (2.666752e6, "profiles/k_spread_gather_pair_nacl32k.md"),
     "fwd.gather": (9.455360e6, "profiles/k_spread_gather_pair_nacl32k.md"),
     "bwd.gather": (19.428608e6, "profiles/k_spread_gather_pair_nacl32k.md"),
+    "quad.pair_eval": (52.838656e6 + 0.348672e6, "profiles/k_pair_quad_nacl32k.md"),
 }
 
 
