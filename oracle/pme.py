@@ -467,6 +467,24 @@ class PMEOracle:
         a, b, c = torch.autograd.grad(L, (pos_t, q_t, mu_t))
         return a.numpy(), b.numpy(), c.numpy()
 
+    def hvp_quad(self, pos, q, mu, theta, g_energy, g_force, g_phi, g_field, pairs=None):
+        """The same vector-Jacobian product with point quadrupoles theta [n,3,3] (cotangents on
+        E, force, phi and field; none on -dE/dTheta), by double backward. Returns (grad_pos,
+        grad_q, grad_mu, grad_theta) as numpy; grad_theta is the symmetric matrix G with
+        dL = G : dTheta for symmetric dTheta."""
+        pos_t = _t(pos).requires_grad_(True)
+        q_t = _t(q).requires_grad_(True)
+        mu_t = _t(mu).requires_grad_(True)
+        th_t = _t(theta).requires_grad_(True)
+        if pairs is None and self.include_pair:
+            pairs = self._pairs(np.asarray(pos, np.float64))
+        E = self.energy(pos_t, q_t, mu_t, pairs, theta=th_t)
+        gr, gq, gm = torch.autograd.grad(E, (pos_t, q_t, mu_t), create_graph=True)
+        L = (float(g_energy) * E - (gr * _t(g_force)).sum() + (gq * _t(g_phi)).sum()
+             - (gm * _t(g_field)).sum())
+        a, b, c, d = torch.autograd.grad(L, (pos_t, q_t, mu_t, th_t))
+        return a.numpy(), b.numpy(), c.numpy(), (0.5 * (d + d.transpose(1, 2))).numpy()
+
     # -- stage-level helpers (per-kernel parity) ------------------------------------------
     def stage_mesh(self, pos, q, mu, theta=None) -> np.ndarray:
         with torch.no_grad():

@@ -227,3 +227,41 @@ def test_o2_translation_by_whole_mesh_cells(small):
     assert abs(r0["energy"] - r1["energy"]) < 1e-12 * abs(r0["energy"])
     assert np.allclose(r0["force"], r1["force"], atol=1e-11)
     assert np.allclose(r0["field_grad"], r1["field_grad"], atol=1e-11)
+
+
+def test_o2_quad_hvp_central_differences(small):
+    # the force-matching backward with quadrupoles (the VJP a later GPU backward is checked
+    # against): central differences of L = gE E - gF.F + gphi.phi - gfield.field
+    fr, T = small
+    o = pme.PMEOracle(fr.box, (16, 16, 16), 6, 0.45, 5.0)
+    gF, gphi, gfield = W.tangent(fr.n, seed=47)
+    gE = 0.7
+    a, b, c, d = o.hvp_quad(fr.pos, fr.q, fr.mu, T, gE, gF, gphi, gfield)
+
+    def L(pos=fr.pos, q=fr.q, mu=fr.mu, th=T):
+        r = o.evaluate_quad(pos, q, mu, th)
+        return (gE * r["energy"] + (gF * r["force"]).sum() + (gphi * r["phi"]).sum()
+                + (gfield * r["field"]).sum())
+
+    h = 1e-5
+    for i, cc in [(1, 0), (4, 2), (7, 1)]:
+        dd = np.zeros_like(fr.pos)
+        dd[i, cc] = h
+        assert abs((L(pos=fr.pos + dd) - L(pos=fr.pos - dd)) / (2 * h) - a[i, cc]) < 1e-7
+        assert abs((L(mu=fr.mu + dd) - L(mu=fr.mu - dd)) / (2 * h) - c[i, cc]) < 1e-7
+        dq = np.zeros(fr.n)
+        dq[i] = h
+        assert abs((L(q=fr.q + dq) - L(q=fr.q - dq)) / (2 * h) - b[i]) < 1e-7
+    for i, p_, q_ in [(2, 0, 0), (5, 1, 2)]:
+        dT = np.zeros_like(T)
+        dT[i, p_, q_] += h
+        if p_ != q_:
+            dT[i, q_, p_] += h
+        fd = (L(th=T + dT) - L(th=T - dT)) / (2 * h)
+        assert abs(fd - (1.0 if p_ == q_ else 2.0) * d[i, p_, q_]) < 1e-7
+    # with only the energy cotangent it is the gradient
+    z = np.zeros_like(fr.pos)
+    a0, b0, c0, d0 = o.hvp_quad(fr.pos, fr.q, fr.mu, T, 2.0, z, np.zeros(fr.n), z)
+    r = o.evaluate_quad(fr.pos, fr.q, fr.mu, T)
+    assert np.allclose(a0, -2.0 * r["force"], atol=1e-12)
+    assert np.allclose(d0, -2.0 * r["field_grad"], atol=1e-12)
