@@ -17,7 +17,8 @@
  *   E_background -pi Q^2 / (2 V alpha^2), Q = sum q (zero for neutral frames).
  *
  * and its derivatives, and the vector-Jacobian product (adjoint) of those derivatives that
- * a force-matching loss (Eq. loss) needs.
+ * a force-matching loss (Eq. loss) needs. pme_forward_quad / pme_batch_forward_quad add point
+ * quadrupoles (the rank-2 channel; forward only), documented at their declarations.
  *
  * Conventions
  *   - Lengths in the caller's unit (Angstrom in the tests), charges in e, dipoles in e*length.
