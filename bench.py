@@ -684,7 +684,8 @@ def run_quad(args):
     sampler.start()
     l0 = gb.launch_count()
     t_quad = time_steps(torch, lambda: plan.forward_quad(pos, q, mu, th), args.steps, args.warmup, dev, flush)
-    launches = (gb.launch_count() - l0) // (args.steps + args.warmup)
+    # kernels of this library inside the timed steps (the same per call)
+    launches = (gb.launch_count() - l0) // (args.steps + args.warmup) * args.steps
     t_plain = time_steps(torch, lambda: plan.forward(pos, q, mu, field_grad=True), args.steps, args.warmup,
                          dev, flush)
     splan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=n, device=dev,
