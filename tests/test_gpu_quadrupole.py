@@ -254,3 +254,21 @@ def test_quad_pair_lists_disabled_and_overflowing(gb):
     assert relrmse(out["force"].cpu().numpy(), ref["force"]) < TOL_F
     assert relrmse(out["field_grad"].cpu().numpy(), sym6(ref["field_grad"])) < TOL_F
     plan.close()
+
+
+def test_quad_empty_and_single_ion(gb):
+    fr, mesh, p, a, rc, pos, q, mu, th = _inputs("nacl64")
+    plan = gb.Plan(fr.box, mesh, p, a, rc, max_ions=1024)
+    e = torch.zeros((0, 3), device="cuda")
+    out = plan.forward_quad(e, torch.zeros(0, device="cuda"), e, torch.zeros((0, 6), device="cuda"))
+    assert out["energy"].item() == 0.0 and out["force"].shape == (0, 3)
+    # one neutral ion carrying only a quadrupole: its energy is the interaction with its own
+    # periodic images (mesh + pair) plus the cloud self term
+    p1 = np.array([[3.1, 4.7, 5.9]])
+    t1 = np.array([[[0.3, 0.05, -0.1], [0.05, -0.2, 0.07], [-0.1, 0.07, 0.15]]])
+    z = np.zeros((1, 3))
+    c = lambda x: torch.tensor(np.float32(x), device="cuda")
+    got = plan.forward_quad(c(p1), c(np.zeros(1)), c(z), c(f32(t1)))
+    ref = O2.PMEOracle(fr.box, mesh, p, a, rc).evaluate_quad(f32(p1), np.zeros(1), z, f32(t1))
+    assert abs(got["energy"].item() - ref["energy"]) < _ebar(ref) + 1e-7
+    assert np.allclose(got["field_grad"].cpu().numpy(), sym6(ref["field_grad"]), rtol=1e-4, atol=1e-6)
