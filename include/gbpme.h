@@ -55,7 +55,7 @@ typedef enum {
                                1..7, alpha <= 0, singular box, mesh dimension < order ... */
   PME_ERR_CUDA = 2,         /* a CUDA runtime call or kernel launch failed */
   PME_ERR_CUFFT = 3,        /* a cuFFT call failed */
-  PME_ERR_NONFINITE = 4,    /* a NaN or Inf appeared in pos, q or mu (device flag) */
+  PME_ERR_NONFINITE = 4,    /* a NaN or Inf appeared in pos, q, mu or theta (device flag) */
   PME_ERR_UNSUPPORTED = 5,  /* option combination not implemented (e.g. finite surface eps) */
   PME_ERR_TIMEOUT = 6,      /* a bounded device-side wait expired */
   PME_ERR_NOMEM = 7         /* device allocation failed at plan creation */

@@ -1263,7 +1263,7 @@ int pme_sync_status(pme_plan_t p, void* stream) {
   if ((st = check_cuda(p, cudaMemcpy(&flags, p->flags, sizeof(int), cudaMemcpyDeviceToHost), "read flags")))
     return st;
   if (flags) cudaMemset(p->flags, 0, sizeof(int));
-  if (flags & kFlagNonFinite) return set_error(p, PME_ERR_NONFINITE, "non-finite value in pos, q or mu");
+  if (flags & kFlagNonFinite) return set_error(p, PME_ERR_NONFINITE, "non-finite value in pos, q, mu or theta");
   if (flags & kFlagTimeout) return set_error(p, PME_ERR_TIMEOUT, "device wait timed out");
   if (flags & kFlagVirialLost)
     return set_error(p, PME_ERR_UNSUPPORTED,

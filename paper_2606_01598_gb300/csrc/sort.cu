@@ -134,6 +134,10 @@ k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int tangent, 
     }
     bool ok = isfinite(rx) && isfinite(ry) && isfinite(rz) && isfinite(qi);
     if (in.mu) ok = ok && isfinite(in.mu[3 * i]) && isfinite(in.mu[3 * i + 1]) && isfinite(in.mu[3 * i + 2]);
+    if (in.theta) {
+#pragma unroll
+      for (int a = 0; a < 6; ++a) ok = ok && isfinite(in.theta[6 * i + a]);
+    }
     if (!ok) atomicOr(flags, kFlagNonFinite);
     double s[3];
     frac_coords(g, rx, ry, rz, s);

@@ -272,3 +272,21 @@ def test_quad_empty_and_single_ion(gb):
     ref = O2.PMEOracle(fr.box, mesh, p, a, rc).evaluate_quad(f32(p1), np.zeros(1), z, f32(t1))
     assert abs(got["energy"].item() - ref["energy"]) < _ebar(ref) + 1e-7
     assert np.allclose(got["field_grad"].cpu().numpy(), sym6(ref["field_grad"]), rtol=1e-4, atol=1e-6)
+
+
+def test_quad_nonfinite_theta_is_flagged(gb):
+    # a NaN quadrupole is reported as PME_ERR_NONFINITE (4) by the next status check (the
+    # kernels index nothing by Theta, so nothing faults); the plan then keeps working
+    fr, mesh, p, a, rc, pos, q, mu, th = _inputs("nacl1000_ragged")
+    plan = gb.Plan(fr.box, mesh, p, a, rc, max_ions=1024)
+    c = lambda x: torch.tensor(np.float32(x), device="cuda")
+    bad = np.array(th)
+    bad[11, 1, 2] = np.nan
+    plan.forward_quad(c(pos), c(q), c(mu), c(bad))
+    with pytest.raises(gb.PMEError) as e:
+        plan.sync_status()
+    assert e.value.status == 4
+    out = plan.forward_quad(c(pos), c(q), c(mu), c(th))
+    plan.sync_status()
+    ref = O2.PMEOracle(fr.box, mesh, p, a, rc).evaluate_quad(pos, q, mu, th)
+    assert abs(out["energy"].item() - ref["energy"]) < _ebar(ref)
