@@ -290,3 +290,14 @@ def test_quad_nonfinite_theta_is_flagged(gb):
     plan.sync_status()
     ref = O2.PMEOracle(fr.box, mesh, p, a, rc).evaluate_quad(pos, q, mu, th)
     assert abs(out["energy"].item() - ref["energy"]) < _ebar(ref)
+
+
+def test_quad_without_dipoles(gb):
+    # mu = NULL is the same as zero dipoles, bit for bit
+    fr, mesh, p, a, rc, pos, q, mu, th = _inputs("nacl1000_ragged")
+    plan = gb.Plan(fr.box, mesh, p, a, rc, max_ions=1024)
+    c = lambda x: torch.tensor(np.float32(x), device="cuda")
+    o1 = plan.forward_quad(c(pos), c(q), None, c(th))
+    o2 = plan.forward_quad(c(pos), c(q), c(np.zeros_like(mu)), c(th))
+    for k in o1:
+        assert torch.equal(o1[k], o2[k]), k
