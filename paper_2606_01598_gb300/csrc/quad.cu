@@ -1,6 +1,6 @@
-// Real-space pair term with point quadrupoles (every frame of the plan): the rank-2 channel of the multipole operator
-// L_i = q_i + mu_i . grad + Theta_i : grad grad (an extension; the paper names quadrupolar
-// channels as future work).
+// Real-space pair term with point quadrupoles (every frame of the plan): the rank-2 channel of
+// the multipole operator L_i = q_i + mu_i . grad + Theta_i : grad grad (an extension; the paper
+// names quadrupolar channels as future work).
 //
 // For a source j = (c, d, B) = (q_j, mu_j, Theta_j) at r = r_i - r_j + n, the potential at i
 // is phi = (c - d . grad + B : grad grad) psi(r), psi = erfc(alpha r)/r. With the radial
