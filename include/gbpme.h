@@ -298,26 +298,31 @@ int pme_profile_read(pme_plan_t plan, double* ms, long long* calls);
  * framework that has already reserved the whole device for its own memory pool (so a new
  * cudaMalloc fails), or a simulation loop that must not allocate or free because
  * cudaMalloc / cudaFree can synchronise the device. It computes the same rho_mesh as
- * pme_spread (same kernels, same ordering, bitwise the same result) but needs no plan and
- * allocates nothing: all of its sort scratch lives in ONE static device array of
+ * pme_spread with the same kernels in the same order, so the result is bitwise that of a
+ * plan's pme_spread with the same box, mesh and order, but it needs no plan and allocates
+ * nothing: all of its sort scratch lives in ONE static device array of
  * PME_NOALLOC_SCRATCH_BYTES bytes inside the library, which every GPU that loads the library
  * keeps until the process exits.
  *   box[9], mesh[3], order: as for pme_plan_create. pos [n][3], q [n], mu [n][3] (may be NULL)
  *     and rho [Nx][Ny][Nz] are DEVICE pointers owned by the caller; rho is written.
+ *   status (DEVICE pointer to one int, may be NULL): written on the stream after the spread,
+ *     PME_ERR_NONFINITE when pos, q or mu held a NaN or Inf (rho is then not meaningful),
+ *     PME_OK otherwise. The return value cannot report this: it is known only on the device.
  *   Limits: 0 <= n <= PME_NOALLOC_MAX_IONS and order <= mesh[a] <= PME_NOALLOC_MAX_MESH;
  *     anything larger returns PME_ERR_ARG without touching the device.
  *   The first call on a device looks up the device address of the array (with that device
  *     current) and caches it; make that first call before any stream capture on the device.
- *   Every call uses the same array and leaves its contents behind; the counters that must
- *     start at zero are cleared on the call's stream at the start of each call. Calls whose
- *     execution overlaps on the GPU (other streams, other host threads) race on the array and
- *     give wrong results: serialise them.
+ *   Every call uses the same array and leaves its contents behind; what must start at zero
+ *     (counters, the error flag) and the candidate-brick table are rewritten on the call's
+ *     stream at the start of each call, by kernels and a memset (nothing is copied from host
+ *     memory). Calls whose execution overlaps on the GPU (other streams, other host threads)
+ *     race on the array and give wrong results: serialise them.
  *   Returns PME_OK, PME_ERR_ARG, PME_ERR_UNSUPPORTED or PME_ERR_CUDA. */
 #define PME_NOALLOC_MAX_IONS 32768
 #define PME_NOALLOC_MAX_MESH 128
 #define PME_NOALLOC_SCRATCH_BYTES 2396672
 int pme_spread_noalloc(void* stream, const double box[9], const int mesh[3], int order, int n,
-                       const float* pos, const float* q, const float* mu, float* rho);
+                       const float* pos, const float* q, const float* mu, float* rho, int* status);
 
 #ifdef __cplusplus
 }

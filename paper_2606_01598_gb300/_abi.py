@@ -51,7 +51,7 @@ _SIGS = {
     "pme_launch_count": (ctypes.c_longlong, []),
     "pme_profile_enable": (c_int, [c_void_p, c_int]),
     "pme_profile_read": (c_int, [c_void_p, c_double_p, ctypes.POINTER(ctypes.c_longlong)]),
-    "pme_spread_noalloc": (c_int, [c_void_p, c_double_p, c_int_p, c_int, c_int] + [c_void_p] * 4),
+    "pme_spread_noalloc": (c_int, [c_void_p, c_double_p, c_int_p, c_int, c_int] + [c_void_p] * 5),
     "pme_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int_p, c_double_p, c_int_p, c_int_p,
                                  c_double, c_double, ctypes.POINTER(PMEOpts)]),
     "pme_batch_frames": (c_int, [c_void_p]),

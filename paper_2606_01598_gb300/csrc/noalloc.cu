@@ -11,6 +11,9 @@
 // The array lives in this translation unit. Host code cannot use its name as a device
 // address, so the first call on each device asks the runtime for the address with
 // cudaGetSymbolAddress (with that device current) and caches it; later calls reuse it.
+// Everything a call writes into the array is formed on the device, on the call's stream (the
+// candidate-brick table by a small kernel, the counters by the sort's own clearing), so no
+// call copies from host memory.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -92,30 +95,52 @@ bool na_invert(const double* a, double* inv, double* det_out) {
   return true;
 }
 
-// Source bricks along one axis whose ions' stencils reach each brick (same rule as the plan).
-bool na_candidates(int N, int B, int P, int nb, int* tab) {
-  for (int b = 0; b < nb; ++b) {
-    const int b0 = b * B, ext = std::min(B, N - b0);
-    int list[kMaxCandPerDim + 1], cnt = 0;
-    if (ext + P - 1 >= N) {
-      if (nb > kMaxCandPerDim) return false;
-      for (int k = 0; k < nb; ++k) list[cnt++] = k;
-    } else {
-      for (int m = b0 - P + 1; m <= b0 + ext - 1; ++m) {
-        const int bi = (((m % N) + N) % N) / B;
-        bool seen = false;
-        for (int k = 0; k < cnt; ++k) seen = seen || list[k] == bi;
-        if (!seen) {
-          if (cnt == kMaxCandPerDim) return false;
-          list[cnt++] = bi;
-        }
-      }
-    }
-    int* row = tab + b * (1 + kMaxCandPerDim);
-    row[0] = cnt;
-    for (int k = 0; k < cnt; ++k) row[1 + k] = list[k];
+// Source bricks along one axis whose ions' stencils reach brick b (the plan's rule): every
+// brick when the brick and its stencil reach cover the axis, else the bricks holding the
+// stencil origins m0 in [b0 - P + 1, b0 + ext - 1], wrapped. Returns the count, or -1 when
+// more than kMaxCandPerDim bricks would be needed. Host and device share this one routine.
+__host__ __device__ inline int na_candidate_row(int N, int B, int P, int nb, int b, int* list) {
+  const int b0 = b * B, ext = (N - b0 < B) ? N - b0 : B;
+  int cnt = 0;
+  if (ext + P - 1 >= N) {
+    if (nb > kMaxCandPerDim) return -1;
+    for (int k = 0; k < nb; ++k) list[cnt++] = k;
+    return cnt;
   }
-  return true;
+  for (int m = b0 - P + 1; m <= b0 + ext - 1; ++m) {
+    const int bi = (((m % N) + N) % N) / B;
+    bool seen = false;
+    for (int k = 0; k < cnt; ++k) seen = seen || list[k] == bi;
+    if (!seen) {
+      if (cnt == kMaxCandPerDim) return -1;
+      list[cnt++] = bi;
+    }
+  }
+  return cnt;
+}
+
+struct NaAxes {
+  int N[3], B[3], nb[3];
+};
+
+// One thread per (axis, brick row) of the table [3][max_nb][1 + kMaxCandPerDim]; rows past an
+// axis's brick count are zeroed. The host has checked that no row overflows.
+__global__ void k_na_candidates(NaAxes ax, int P, int max_nb, int* tab) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * max_nb) return;
+  const int a = t / max_nb, b = t - a * max_nb;
+  int* row = tab + t * (1 + kMaxCandPerDim);
+  int list[kMaxCandPerDim];
+  int cnt = 0;
+  if (b < ax.nb[a]) cnt = na_candidate_row(ax.N[a], ax.B[a], P, ax.nb[a], b, list);
+  if (cnt < 0) cnt = 0;
+  row[0] = cnt;
+  for (int k = 0; k < kMaxCandPerDim; ++k) row[1 + k] = k < cnt ? list[k] : 0;
+}
+
+// *out = PME_ERR_NONFINITE when the sort flagged a NaN or Inf input, PME_OK otherwise.
+__global__ void k_na_status(const int* flags, int* out) {
+  if (threadIdx.x == 0) *out = (*flags & kFlagNonFinite) ? PME_ERR_NONFINITE : PME_OK;
 }
 
 }  // namespace
@@ -126,7 +151,7 @@ using namespace gbpme;
 
 extern "C" int pme_spread_noalloc(void* stream, const double box[9], const int mesh[3], int order,
                                   int n, const float* pos, const float* q, const float* mu,
-                                  float* rho) {
+                                  float* rho, int* status) {
   if (!box || !mesh || !rho || order < 1 || order > kMaxOrder) return PME_ERR_ARG;
   if (n < 0 || n > kNaMaxIons) return PME_ERR_ARG;     // beyond the fixed scratch
   if (n > 0 && (!pos || !q)) return PME_ERR_ARG;
@@ -173,11 +198,15 @@ extern "C" int pme_spread_noalloc(void* stream, const double box[9], const int m
   v.max_ions = kNaMaxIons;
   v.nogroups = 1;
   v.ogroups[0] = OrderGroup{order, 0, fd.nbricks, 0, n};
-  int cand[3 * kNaMaxNb * (1 + kMaxCandPerDim)];
-  std::memset(cand, 0, sizeof(cand));
-  for (int a = 0; a < 3; ++a)
-    if (!na_candidates(mesh[a], g.brick[a], order, g.nb[a], cand + a * fd.max_nb * (1 + kMaxCandPerDim)))
-      return PME_ERR_UNSUPPORTED;
+  NaAxes ax{};
+  for (int a = 0; a < 3; ++a) {
+    ax.N[a] = mesh[a];
+    ax.B[a] = g.brick[a];
+    ax.nb[a] = g.nb[a];
+    int list[kMaxCandPerDim];
+    for (int b = 0; b < g.nb[a]; ++b)   // host check only; the table is formed on the device
+      if (na_candidate_row(mesh[a], g.brick[a], order, g.nb[a], b, list) < 0) return PME_ERR_UNSUPPORTED;
+  }
   v.sb.key_b = reinterpret_cast<int*>(base + kOffKeyB);
   v.sb.key_c = reinterpret_cast<int*>(base + kOffKeyC);
   v.sb.slot_b = reinterpret_cast<int*>(base + kOffSlotB);
@@ -199,10 +228,10 @@ extern "C" int pme_spread_noalloc(void* stream, const double box[9], const int m
   v.mr.tt = nullptr;
   v.cand = reinterpret_cast<int*>(base + kOffCand);
   v.flags = reinterpret_cast<int*>(base + kOffFlags);
-  // the candidate table and the error flag are per call: rewrite / clear them first
-  if (cudaMemcpyAsync(v.cand, cand, sizeof(int) * 3 * fd.max_nb * (1 + kMaxCandPerDim),
-                      cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return PME_ERR_CUDA;
+  // the candidate table and the error flag are per call: form / clear them on the stream
+  k_na_candidates<<<1, 3 * kNaMaxNb, 0, s>>>(ax, order, fd.max_nb, v.cand);
+  count_launch();
+  if (cudaGetLastError() != cudaSuccess) return PME_ERR_CUDA;
   if (cudaMemsetAsync(v.flags, 0, sizeof(int), s) != cudaSuccess) return PME_ERR_CUDA;
   IonInputs in{};
   in.pos = pos;
@@ -214,5 +243,11 @@ extern "C" int pme_spread_noalloc(void* stream, const double box[9], const int m
   if (st) return st;
   const int rc = launch_spread(&v, s, false, rho);   // the frame's rho sits at offset 0
   v.frames_h = nullptr;                               // host views only: nothing to release
-  return rc;
+  if (rc) return rc;
+  if (status) {
+    k_na_status<<<1, 32, 0, s>>>(v.flags, status);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return PME_ERR_CUDA;
+  }
+  return PME_OK;
 }

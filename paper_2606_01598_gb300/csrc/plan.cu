@@ -1382,6 +1382,18 @@ static int run_forward_quad(pme_plan_t p, cudaStream_t s, const IonInputs& in, d
   return st;
 }
 
+// The quadrupole density Theta : grad grad W is continuous in r only when the second
+// derivative of W is, i.e. for spline order p >= 4 (for p <= 3 it jumps at mesh points and
+// the third derivative vanishes between them): below that the mesh energy is not a smooth
+// function of the positions and Theta : grad^3 phi is not its gradient, so those orders are
+// refused.
+static int check_quad_orders(pme_plan_t p) {
+  for (int f = 0; f < p->nframes; ++f)
+    if (p->frames_h[f].g.order < 4)
+      return set_error(p, PME_ERR_UNSUPPORTED, "quadrupoles need spline order >= 4 in every frame");
+  return PME_OK;
+}
+
 int pme_forward_quad(pme_plan_t p, void* stream, int n, const float* pos, const float* q,
                      const float* mu, const float* theta, double* energy, float* force, float* phi,
                      float* field, float* field_grad) {
@@ -1390,6 +1402,7 @@ int pme_forward_quad(pme_plan_t p, void* stream, int n, const float* pos, const 
   if (n > 0 && !theta) return set_error(p, PME_ERR_ARG, "theta is NULL");
   if (p->opts.recip_method != 0)
     return set_error(p, PME_ERR_UNSUPPORTED, "quadrupoles need the particle-mesh method (recip_method 0)");
+  if ((st = check_quad_orders(p))) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Staging sg(p, s, n);
   IonInputs in{};
@@ -1417,6 +1430,7 @@ int pme_batch_forward_quad(pme_plan_t p, void* stream, const float* pos, const f
   if (st) return st;
   const int n = p->frame_offsets[p->nframes];
   if (n > 0 && !theta) return set_error(p, PME_ERR_ARG, "theta is NULL");
+  if ((st = check_quad_orders(p))) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Staging sg(p, s, n);
   IonInputs in{};

@@ -75,11 +75,13 @@ def mesh_dims(box, spacing: float, rule: int = 0, strategy: int = 1, clamp=(0, 0
     return [m[0], m[1], m[2]]
 
 
-def spread_noalloc(box, mesh, order: int, pos, q, mu=None):
+def spread_noalloc(box, mesh, order: int, pos, q, mu=None, status=None):
     """pme_spread_noalloc: the mesh density without a plan and without any device allocation
     (for callers that cannot allocate; see include/gbpme.h). Device tensors in; rho is
     allocated here by torch only because this helper returns a new tensor -- callers that
-    cannot allocate pass their own output through the C ABI."""
+    cannot allocate pass their own output through the C ABI. status: optional int32 device
+    tensor of one element, set on the stream to 4 (PME_ERR_NONFINITE) when an input held a NaN
+    or Inf, else 0."""
     lib = _abi.load()
     dev = pos.device
     pos, q, mu = (_f32(t, dev) for t in (pos, q, mu))
@@ -91,7 +93,8 @@ def spread_noalloc(box, mesh, order: int, pos, q, mu=None):
     m = (ctypes.c_int * 3)(*[int(x) for x in mesh])
     with torch.cuda.device(dev):
         st = lib.pme_spread_noalloc(_stream_handle(dev), b, m, int(order), int(pos.shape[0]),
-                                    _ptr(pos), _ptr(q), _ptr(mu), _ptr(rho))
+                                    _ptr(pos), _ptr(q), _ptr(mu), _ptr(rho),
+                                    None if status is None else _ptr(status))
     if st:
         raise PMEError(st, "pme_spread_noalloc")
     return rho

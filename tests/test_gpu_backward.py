@@ -8,7 +8,7 @@ import torch
 import workloads as W
 from oracle import pme as O2
 
-from gpu_util import TOL_E, TOL_F, TOL_HVP, f32, prepared, relrmse
+from gpu_util import TOL_E, TOL_F, TOL_HVP, check_energy, f32, prepared, relrmse
 
 pytestmark = pytest.mark.gpu
 
@@ -187,8 +187,9 @@ def test_pair_lists_disabled_and_overflowing_paths(gb):
     plan = gb.Plan(box, (40, 40, 40), 6, 0.30, 9.0, max_ions=1024)
     out = plan.forward(c(pc), c(qc), c(muc))
     ref = O2.PMEOracle(box, (40, 40, 40), 6, 0.30, 9.0).evaluate(pc, qc, muc, field_grad=False)
-    scale = sum(abs(ref[k]) for k in ("e_recip", "e_pair", "e_self", "e_bg"))
-    assert abs(out["energy"].item() - ref["energy"]) < TOL_E * scale
+    # alternating +-0.5 charges packed in a ball: E is a small remainder of E_recip and E_self
+    # (float64 on both sides), so the bar is on the float32 parts
+    check_energy(out["energy"].item(), ref, cancel=True)
     assert relrmse(out["force"].cpu().numpy(), ref["force"]) < TOL_F
     gFc, gphic, gfieldc = (f32(x) for x in W.tangent(200, seed=37))
     got = plan.backward(c(pc), c(qc), c(muc), gE, c(gFc), c(gphic), c(gfieldc))

@@ -265,3 +265,23 @@ def test_o2_quad_hvp_central_differences(small):
     r = o.evaluate_quad(fr.pos, fr.q, fr.mu, T)
     assert np.allclose(a0, -2.0 * r["force"], atol=1e-12)
     assert np.allclose(d0, -2.0 * r["field_grad"], atol=1e-12)
+
+
+def test_o2_quad_forces_are_energy_gradient_at_order4(small):
+    # at p = 4 the quadrupole density uses the second spline derivative, which is continuous:
+    # the mesh energy is then continuous with kinks only where an ion crosses a spline knot,
+    # and away from them the force (with Theta : grad^3 phi) is -dE/dr; central differences
+    # with a step far below any ion's distance to a knot check it
+    fr, T = small
+    o = pme.PMEOracle(fr.box, (16, 16, 16), 4, 0.45, 5.0)
+    r = o.evaluate_quad(fr.pos, fr.q, fr.mu, T)
+    h = 1e-6
+    x = fr.pos @ np.linalg.inv(fr.box) * 16.0          # mesh coordinates
+    for i, c in [(0, 0), (2, 1), (5, 2), (7, 0)]:
+        # knots of the order-4 stencil are at integer mesh coordinates
+        assert np.abs(x[i] - np.round(x[i])).min() > 1e-3
+        d = np.zeros_like(fr.pos)
+        d[i, c] = h
+        ep = o.evaluate_quad(fr.pos + d, fr.q, fr.mu, T)["energy"]
+        em = o.evaluate_quad(fr.pos - d, fr.q, fr.mu, T)["energy"]
+        assert abs((ep - em) / (2 * h) + r["force"][i, c]) < 1e-6 * max(1.0, abs(r["force"][i, c]))
