@@ -59,7 +59,11 @@ def solve_dipoles(oracle: O2.PMEOracle, pos, q, a, *, omega: float = 0.5, tol: f
 
 
 def polarisation_energy(mu, a):
-    return float(np.sum(np.sum(np.asarray(mu) ** 2, axis=1) / (2.0 * np.asarray(a))))
+    """sum_i |mu_i|^2 / (2 a_i); an ion with a_i = 0 carries no induced dipole and no term."""
+    a = np.asarray(a, np.float64)
+    m2 = np.sum(np.asarray(mu) ** 2, axis=1)
+    pol = a > 0
+    return float(np.sum(m2[pol] / (2.0 * a[pol])))
 
 
 def label(frame, mesh=(32, 32, 32), order: int = 4, alpha: float = 0.30, rcut: float = 9.0,

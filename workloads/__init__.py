@@ -222,3 +222,54 @@ def workload(name: str):
     cfg = {k: v for k, v in w.items() if k != "gen"}
     return fr, cfg
 
+
+
+# ---- the learned charge/dipole network: seeded parameters and training frames ---------
+
+NET_SCALARS, NET_VECTORS, NET_RADIAL, NET_LAYERS = 32, 16, 8, 2
+# (name, shape, stored as bfloat16?) in the order of the flat parameter vector; the shapes
+# are (fan_in, fan_out) for the channel-mixing matrices
+NET_LAYOUT = (
+    [("emb", (2, NET_SCALARS), False)]
+    + [item for t in range(NET_LAYERS) for item in (
+        (f"WA{t}", (NET_SCALARS, NET_SCALARS + NET_VECTORS), True),
+        (f"WB{t}", (NET_VECTORS, 2 * NET_VECTORS), True),
+        (f"WR{t}", (NET_RADIAL, NET_SCALARS + 3 * NET_VECTORS), False),
+        (f"WU{t}", (NET_SCALARS + NET_VECTORS, NET_SCALARS + NET_VECTORS), True),
+        (f"WY{t}", (2 * NET_VECTORS, NET_VECTORS), True))]
+    + [("Wh", (NET_SCALARS, 2 * NET_SCALARS), True), ("bh", (2 * NET_SCALARS,), False),
+       ("wq", (NET_SCALARS,), False), ("bq", (1,), False),
+       ("wE", (NET_SCALARS,), False), ("bE", (1,), False),
+       ("wmu", (NET_VECTORS,), False)]
+)
+
+
+def to_bf16(x) -> np.ndarray:
+    """Round to the nearest bfloat16 value (ties to even), returned as float64."""
+    f = np.asarray(x, np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def net_params(seed: int = 2024) -> dict:
+    """Gaussian initial parameters of the network, sigma = 1/sqrt(fan_in) for every weight
+    matrix (the embedding table and the radial weights included), biases zero. The
+    channel-mixing matrices are rounded to bfloat16 (the precision they are stored in);
+    everything else is float32. Returns float64 arrays by name."""
+    rng = np.random.default_rng(seed)
+    out = {}
+    for name, shape, bf16 in NET_LAYOUT:
+        if name.startswith("b"):
+            v = np.zeros(shape)
+        else:
+            v = rng.normal(0.0, 1.0 / math.sqrt(shape[0]), size=shape)
+        out[name] = to_bf16(v) if bf16 else np.asarray(np.float32(v), np.float64)
+    return out
+
+
+def training_frames(n_frames: int = 32, n: int = 512, seed: int = 1003) -> list[Frame]:
+    """Molten-NaCl frames of the learned-charge task: n ions each at ~1.5 g/cm^3
+    (L = 25.5 A for 512 ions), species set; charges and dipoles are not used (the teacher
+    assigns them)."""
+    return [molten_nacl(n, seed=seed * 1000 + f) for f in range(n_frames)]
