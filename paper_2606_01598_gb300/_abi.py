@@ -15,6 +15,7 @@ c_double_p = ctypes.POINTER(ctypes.c_double)
 c_int_p = ctypes.POINTER(ctypes.c_int)
 
 HEADER = os.path.join(ROOT, "include", "gbpme.h")
+HEADERS = [HEADER, os.path.join(ROOT, "include", "gbnet.h")]
 
 STATUS = {0: "PME_OK", 1: "PME_ERR_ARG", 2: "PME_ERR_CUDA", 3: "PME_ERR_CUFFT",
           4: "PME_ERR_NONFINITE", 5: "PME_ERR_UNSUPPORTED", 6: "PME_ERR_TIMEOUT",
@@ -59,6 +60,23 @@ _SIGS = {
     "pme_batch_forward_virial": (c_int, [c_void_p, c_void_p] + [c_void_p] * 9),
     "pme_batch_forward_quad": (c_int, [c_void_p, c_void_p] + [c_void_p] * 9),
     "pme_batch_backward": (c_int, [c_void_p, c_void_p] + [c_void_p] * 10),
+    # the learned charge/dipole network (include/gbnet.h)
+    "gbnet_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int]),
+    "gbnet_destroy": (c_int, [c_void_p]),
+    "gbnet_last_error": (ctypes.c_char_p, [c_void_p]),
+    "gbnet_set_frames": (c_int, [c_void_p, c_void_p, c_int, c_int_p, c_double_p, c_void_p]),
+    "gbnet_set_params": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "gbnet_get_params": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "gbnet_forward": (c_int, [c_void_p, c_void_p] + [c_void_p] * 4),
+    "gbnet_backward": (c_int, [c_void_p, c_void_p] + [c_void_p] * 5),
+    "gbnet_loss_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_double,
+                                c_void_p, c_void_p, c_void_p, c_int]),
+    "gbnet_adam": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_double, c_double, c_double]),
+    "gbnet_train_step": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_double,
+                                 c_double, c_void_p]),
+    "gbnet_mix": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
+    "gbnet_sync_status": (c_int, [c_void_p, c_void_p]),
+    "gbnet_last_launches": (ctypes.c_longlong, [c_void_p]),
 }
 
 NOALLOC_MAX_IONS = 32768
@@ -72,10 +90,13 @@ _LIB = None
 
 
 def header_functions() -> list[str]:
-    """Names of every function the public header declares."""
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(pme_[a-z_]+)\s*\(", src)))
+    """Names of every function the public headers declare."""
+    names = set()
+    for h in HEADERS:
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names.update(re.findall(r"\b((?:pme|gbnet)_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 def load():
