@@ -102,13 +102,25 @@ def traffic_of(stage: str, workload: str):
 # Stages timed as one kernel of this library (the roofline's dominant kernel is picked among
 # them; sort and pair are several kernels each, cuFFT is a library call).
 SINGLE_KERNEL_STAGES = ("spread", "influence", "gather", "combine", "pair_eval")
-# FP32 peak for the ALU bound: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def pairs_per_ion(n: int, volume: float, rcut: float) -> float:
-    """Expected partners inside rcut at uniform density (the molten-NaCl generator's)."""
-    return (n - 1) / volume * 4.0 / 3.0 * math.pi * rcut ** 3
+def fp32_peak(dev, sm_max_mhz):
+    """FP32 peak for the ALU bound: the device's SM count x 128 FP32 lanes x 2 flop (FMA) x
+    the maximum SM clock nvidia-smi reported during the run (2070 MHz if none)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = sm_max_mhz or 2070.0
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, f"derived: {sms} SM x 128 FP32 lanes x 2 x {mhz:.0f} MHz"
+
+
+def pair_hits(pos, box, rcut):
+    """Ordered pairs (i, j) within rcut over the periodic images of an orthorhombic box: the
+    number of pair evaluations one list pass makes (each pair is evaluated from both ions)."""
+    import numpy as np
+    from scipy.spatial import cKDTree
+    L = np.diag(np.asarray(box, np.float64))
+    t = cKDTree(np.mod(np.asarray(pos, np.float64), L), boxsize=L)
+    return 2 * len(t.query_pairs(rcut, output_type="ndarray"))
 
 
 def load_peaks():
@@ -207,27 +219,52 @@ def build_frame(name: str):
 
 
 def cpu_baseline(fr, cfg, max_seconds: float = 20.0, max_steps: int = 5):
-    """Time the float64 oracle (plain PME, autograd double backward) as it stands."""
+    """Time the float64 oracles as they stand on this machine's host cores: O2 (plain PME,
+    autograd double backward) fwd + bwd on the benchmark frame on every core this process may
+    use (os.sched_getaffinity) and on one core, and O1 (explicit Ewald, the method PME
+    replaces) forward on a 1024-ion frame of the same density at the benchmark's alpha and
+    cutoffs (|k| <= 2 alpha sqrt(ln 1e8)). Bounded samples, about 30 s in all."""
     import numpy as np
     import torch
+    from oracle import ewald as O1
     from oracle import pme as O2
     import workloads as W
     pos, q, mu = (np.asarray(np.float32(x), np.float64) for x in (fr.pos, fr.q, fr.mu))
     gF, gphi, gfield = W.tangent(fr.n, seed=99)
     o = O2.PMEOracle(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"])
-    steps, t0 = 0, time.perf_counter()
-    while True:
-        o.evaluate(pos, q, mu, field_grad=False)
-        o.hvp(pos, q, mu, 0.5, gF, gphi, gfield)
-        steps += 1
+    threads0 = torch.get_num_threads()
+    cores = len(os.sched_getaffinity(0))
+
+    def o2_rate(nthreads, budget, cap):
+        torch.set_num_threads(nthreads)
+        steps, t0 = 0, time.perf_counter()
+        while True:
+            o.evaluate(pos, q, mu, field_grad=False)
+            o.hvp(pos, q, mu, 0.5, gF, gphi, gfield)
+            steps += 1
+            if time.perf_counter() - t0 >= budget or steps >= cap:
+                break
         el = time.perf_counter() - t0
-        if el >= max_seconds * 0.5 or steps >= max_steps:
-            break
-    el = time.perf_counter() - t0
-    return {"value": fr.n * steps / el / 1e6, "unit": UNIT, "cores": torch.get_num_threads(),
-            "kind": "oracle",
-            "sample": f"{steps} full fwd+bwd step(s) of the {fr.n}-ion frame (float64 torch CPU, "
-                      f"{el:.1f} s)"}
+        return fr.n * steps / el / 1e6, steps, el
+
+    v_all, s_all, e_all = o2_rate(cores, max_seconds * 0.25, max_steps)
+    v_one, s_one, e_one = o2_rate(1, 1.0, 1)
+    torch.set_num_threads(cores)
+    f1 = W.molten_nacl(1024, seed=6024)
+    p1, q1, m1 = (np.asarray(np.float32(x), np.float64) for x in (f1.pos, f1.q, f1.mu))
+    t0 = time.perf_counter()
+    O1.ewald(p1, q1, m1, f1.box, cfg["alpha"], rcut=cfg["rcut"], kmax=2 * cfg["alpha"] * math.sqrt(math.log(1e8)))
+    e_o1 = time.perf_counter() - t0
+    torch.set_num_threads(threads0)
+    return {"value": v_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{s_all} full fwd+bwd step(s) of the {fr.n}-ion frame (O2, float64 torch CPU, "
+                      f"{e_all:.1f} s on {cores} threads)",
+            "one_core": {"value": v_one, "unit": UNIT, "cores": 1,
+                         "sample": f"{s_one} fwd+bwd step of the {fr.n}-ion frame ({e_one:.1f} s)"},
+            "explicit_ewald_o1": {"value": 1024 / e_o1 / 1e6, "unit": "Mion-evals/s (forward)",
+                                  "cores": cores, "sample": f"forward (energy, forces, phi, field) of a 1024-ion "
+                                  f"molten-NaCl frame, alpha {cfg['alpha']}, rcut {cfg['rcut']}, |k| <= 2 alpha "
+                                  f"sqrt(ln 1e8) ({e_o1:.1f} s)"}}
 
 
 def run_reference(args):
@@ -242,6 +279,7 @@ def run_reference(args):
     pos, q, mu = (np.asarray(np.float32(x), np.float64) for x in (fr.pos, fr.q, fr.mu))
     gF, gphi, gfield = W.tangent(fr.n, seed=99)
     o = O2.PMEOracle(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"])
+    torch.set_num_threads(len(os.sched_getaffinity(0)))
 
     def step():
         o.evaluate(pos, q, mu, field_grad=False)
@@ -261,7 +299,7 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_dict(cfg, fr, ws),
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
-                         "sample": f"each step one full fwd+bwd of the {fr.n}-ion frame"},
+                         "sample": f"each step one full fwd+bwd of the {fr.n}-ion frame (O2, float64 torch CPU)"},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -483,6 +521,109 @@ def batch16_rooflines(gb, fr, cfg, dev, steps):
     return {"frames": F, "ions_per_frame": n, "peak_gbs": peak, "peak_source": kind, "stages": out}
 
 
+def train_bench(gb, dev, steps):
+    """The learned-charge training step of the fourth workload: 32 molten-NaCl frames of 512
+    ions (L = 25.5 A), the 2-layer network and the batched PME (mesh 32^3, order 4, alpha 0.30,
+    rcut 9 A); one step = the loss of Eq. loss, its parameter gradient (forward-over-reverse
+    through the network and the PME's Hessian-vector product) and the Adam update, in one call
+    (gbnet_train_step). Beside it the plain per-frame form: the same step as a loop of
+    single-frame calls (one network handle and one single-frame PME plan per frame) with the
+    gradient accumulated, then one Adam update and the parameters copied back to every
+    per-frame handle. Targets are synthetic (random energies and forces: the step's cost does
+    not depend on them); the two forms give the same gradient (gradient_rel_diff), hence the
+    same training trajectory and force accuracy."""
+    import numpy as np
+    import torch
+    import workloads as W
+
+    frames = W.training_frames(32, 512, seed=1003)
+    F = len(frames)
+    offsets = np.concatenate([[0], np.cumsum([fr.n for fr in frames])])
+    N = int(offsets[-1])
+    rng = np.random.default_rng(11)
+    c = lambda x: torch.tensor(np.float32(x), device=dev)
+    pos = c(np.concatenate([fr.pos for fr in frames]))
+    species = np.concatenate([fr.species for fr in frames])
+    boxes = [fr.box for fr in frames]
+    e_ref = torch.tensor(rng.normal(-80.0, 5.0, size=F), device=dev)
+    f_ref = c(rng.normal(0.0, 0.2, size=(N, 3)))
+    params = W.net_params(seed=2024)
+    pme_kw = dict(device=dev, fft=FFT)
+    net = gb.Net(N, F, device=dev)
+    net.set_frames(offsets, boxes, species)
+    net.set_params(params)
+    bp = gb.BatchPlan(boxes, [(32, 32, 32)] * F, [4] * F, offsets, 0.30, 9.0, **pme_kw)
+    lr = 1e-3
+    loss = torch.empty(3, dtype=torch.float64, device=dev)
+    # the first step's gradient of both forms, from the same parameters
+    _, _, g_batch = net.loss_grad(bp, pos, e_ref, f_ref, 1.0, 1.0)
+    singles = []
+    for f, fr in enumerate(frames):
+        lo, hi = int(offsets[f]), int(offsets[f + 1])
+        n1 = gb.Net(fr.n, 1, device=dev)
+        n1.set_frames([0, fr.n], [fr.box], fr.species)
+        n1.set_params(params)
+        b1 = gb.BatchPlan([fr.box], [(32, 32, 32)], [4], [0, fr.n], 0.30, 9.0, **pme_kw)
+        singles.append((n1, b1, lo, hi, fr.n, f))
+    g_loop = torch.zeros_like(g_batch)
+
+    def loop_grad(g):
+        # lambda_e / F and lambda_f N_f / N reproduce the batch normalisation of Eq. loss
+        for n1, b1, lo, hi, nf, f in singles:
+            n1.loss_grad(b1, pos[lo:hi], e_ref[f:f + 1], f_ref[lo:hi], 1.0 / F, nf / N, grad=g, accumulate=True)
+
+    loop_grad(g_loop)
+    gdiff = float((g_loop - g_batch).norm() / g_batch.norm())
+    pbuf = torch.empty(gb.net.NUM_PARAMS, dtype=torch.float32, device=dev)
+
+    def per_frame_step():
+        g_loop.zero_()
+        loop_grad(g_loop)
+        singles[0][0].adam(g_loop, lr)
+        pbuf.copy_(singles[0][0].get_params())
+        for n1, *_ in singles[1:]:
+            n1.set_params_device(pbuf)
+
+    def batched_step():
+        net.train_step(bp, pos, e_ref, f_ref, 1.0, 1.0, lr, loss)
+
+    for _ in range(3):
+        batched_step()
+    torch.cuda.synchronize(dev)
+    k = max(5, steps)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = gb.launch_count()
+    a.record()
+    for _ in range(k):
+        batched_step()
+    b.record()
+    torch.cuda.synchronize(dev)
+    launches = (gb.launch_count() - l0) // k
+    t_batch = a.elapsed_time(b) / k
+    for _ in range(2):
+        per_frame_step()
+    torch.cuda.synchronize(dev)
+    kl = max(2, k // 4)
+    a.record()
+    for _ in range(kl):
+        per_frame_step()
+    b.record()
+    torch.cuda.synchronize(dev)
+    t_loop = a.elapsed_time(b) / kl
+    net.sync_status()
+    for n1, b1, *_ in singles:
+        n1.close()
+        b1.close()
+    net.close()
+    bp.close()
+    return {"workload": "32 molten-NaCl frames x 512 ions (L = 25.5 A), 2-layer net (32 scalar + 16 vector "
+                        "channels, 8 Bessel, 5 A), PME mesh 32^3 order 4 alpha 0.30 rcut 9 A",
+            "batched_ms_per_step": t_batch, "per_frame_ms_per_step": t_loop,
+            "speedup_batched_vs_per_frame": t_loop / t_batch,
+            "ions_per_s_batched": N / (t_batch / 1e3), "kernel_launches_per_step": int(launches),
+            "gradient_rel_diff_batched_vs_per_frame": gdiff, "steps": k}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -588,11 +729,12 @@ def run_ours(args):
     h2d = 2 * (12 + 4 + 12) * n + (12 + 4 + 12) * n + 8
     d2h = 8 + (12 + 4 + 12) * n + (12 + 4 + 12) * n
     clocks = sampler.stop()
-    plain = b16 = vir = None
+    plain = b16 = vir = train = None
     if rank == 0 and not args.no_extras:
         plain = vs_plain(gb, fr, cfg, dev, pos, q, mu, gE, gF, gphi, gfield, flush, args.steps)
         vir = virial_cost(gb, fr, cfg, dev, pos, q, mu, flush, args.steps)
         b16 = batch16_rooflines(gb, fr, cfg, dev, args.steps)
+        train = train_bench(gb, dev, args.steps)
 
     if rank == 0:
         # ---- roofline of the dominant kernel (stage timers of the timed region) ------------
@@ -603,19 +745,19 @@ def run_ours(args):
             ours.update({k: v for k, v in stages.items() if k.endswith(".pair")})
         dom = max(ours, key=lambda k: ours[k][0]) if ours else None
         peak, peak_kind = load_peaks()
-        vol = abs(float(np.linalg.det(fr.box)))
-        ppi = pairs_per_ion(n, vol, cfg["rcut"])
+        fpeak, fpeak_src = fp32_peak(dev, clocks.get("sm_max_mhz"))
+        hits = pair_hits(fr.pos, fr.box, cfg["rcut"])
 
         def roofline(stage):
             avg_ms = stages[stage][0] / stages[stage][1]
             tr, tr_src = traffic_of(stage, args.workload)
             if stage in PAIR_FLOPS:
-                fl = n * ppi * PAIR_FLOPS[stage]
+                fl = hits * PAIR_FLOPS[stage]
                 ach = fl / (avg_ms / 1e3) / 1e12
-                return {"kernel": stage, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
-                        "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": tr,
-                        "traffic_source": tr_src,
-                        "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
+                return {"kernel": stage, "bound": "alu", "achieved": ach, "peak": fpeak,
+                        "unit": "TFLOP/s", "frac": ach / fpeak, "traffic": tr,
+                        "traffic_source": tr_src, "peak_source": fpeak_src,
+                        "pair_hits_per_launch": hits,
                         "avg_launch_ms": avg_ms, "flops_per_launch": fl}
             by = stage_bytes(stage, n, M, Mh)
             ach = by / (avg_ms / 1e3) / 1e9
@@ -632,7 +774,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(config_dict(cfg, fr, ws), transforms=plan.fft_kind),
+            "config": config_dict(cfg, fr, ws),
+            "transforms": plan.fft_kind,
             "roofline": roof,
             "stage_ms": per_stage,
             "serial_ms_per_step": s_ms,
@@ -642,6 +785,7 @@ def run_ours(args):
             "mesh_rooflines_batch16": b16,
             "vs_plain": plain,
             "virial": vir,
+            "train": train,
             "cpu_baseline": cpu,
             "e2e": {"value": e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e_ms},
@@ -700,8 +844,9 @@ def run_quad(args):
     clocks = sampler.stop()
     M = int(np.prod(cfg["mesh"]))
     Mh = cfg["mesh"][0] * cfg["mesh"][1] * (cfg["mesh"][2] // 2 + 1)
-    ppi = pairs_per_ion(n, abs(float(np.linalg.det(fr.box))), cfg["rcut"])
+    hits = pair_hits(fr.pos, fr.box, cfg["rcut"])
     peak, peak_kind = load_peaks()
+    fpeak, fpeak_src = fp32_peak(dev, clocks.get("sm_max_mhz"))
     # single kernels: the list-driven pair evaluation (with hit lists) or the cell walk, spread,
     # gather, influence
     single = ("pair_eval", "spread", "gather", "influence") if "fwd.pair_eval" in stages else \
@@ -710,12 +855,12 @@ def run_quad(args):
     dom = max(kernels, key=lambda k: kernels[k][0])
     avg_ms = stages[dom][0] / stages[dom][1]
     if dom in ("fwd.pair", "fwd.pair_eval"):
-        fl = n * ppi * QUAD_PAIR_FLOPS
+        fl = hits * QUAD_PAIR_FLOPS
         ach = fl / (avg_ms / 1e3) / 1e12
         tr, tr_src = traffic_of("quad." + dom.split(".")[1], args.workload)
-        roof = {"kernel": "k_pair_quad_listed" if dom == "fwd.pair_eval" else "k_pair_quad", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": tr, "traffic_source": tr_src,
-                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
+        roof = {"kernel": "k_pair_quad_listed" if dom == "fwd.pair_eval" else "k_pair_quad", "bound": "alu",
+                "achieved": ach, "peak": fpeak, "unit": "TFLOP/s", "frac": ach / fpeak, "traffic": tr,
+                "traffic_source": tr_src, "peak_source": fpeak_src, "pair_hits_per_launch": hits,
                 "avg_launch_ms": avg_ms, "flops_per_launch": fl}
     else:
         # quadrupole mode reads 24 more bytes per ion (Theta) than the forward tables count
@@ -724,14 +869,14 @@ def run_quad(args):
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "traffic": None, "peak_source": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)",
                 "avg_launch_ms": avg_ms, "bytes_per_launch": by}
-    cfgd = dict(config_dict(cfg, fr, 1), transforms=plan.fft_kind, theta_sigma=0.1)
+    cfgd = dict(config_dict(cfg, fr, 1), theta_sigma=0.1)
     cfgd["workload"] = cfgd["workload"].replace("charges+dipoles, fwd+bwd (HVP)",
                                                 "charges+dipoles+quadrupoles, forward")
     line = {
         "metric": QUAD_METRIC, "value": n / t_quad / 1e3, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_quad, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": cfgd,
+        "config": cfgd, "transforms": plan.fft_kind,
         "plain_forward_ms": t_plain,
         "serial_ms_per_step": s_ms,
         "stage_ms": {k: round(v[0] / v[1], 5) for k, v in sorted(stages.items())},

@@ -25,6 +25,9 @@ constexpr int kRedItem = 128;
 // launch bookkeeping
 // ----------------------------------------------------------------------------------------
 void count_launch();
+// Streaming multiprocessors of the current device (queried once per device; grids of the
+// grid-stride kernels are sized in multiples of it).
+int device_sm_count();
 
 // ----------------------------------------------------------------------------------------
 // geometry shared by all kernels of one plan (passed by value)

@@ -22,7 +22,6 @@ namespace gbpme {
 namespace {
 
 constexpr int kInflThreads = 256;
-constexpr int kInflMaxBlocks = 152 * 4;
 
 // Neumaier-compensated float accumulation (sum s, running correction c)
 __device__ __forceinline__ void comp_add(float& s, float& c, float v) {
@@ -254,7 +253,7 @@ int launch_influence_tables(pme_plan_t p, cudaStream_t s) {
   for (int f = 0; f < p->nframes; ++f) {
     const FrameDesc& F = p->frames_h[f];
     const long long Mh = (long long)F.g.N[0] * F.g.N[1] * (F.g.N[2] / 2 + 1);
-    const int grid = int(std::min<long long>((Mh + kInflThreads - 1) / kInflThreads, 152 * 8));
+    const int grid = int(std::min<long long>((Mh + kInflThreads - 1) / kInflThreads, 8LL * device_sm_count()));
     k_gc_table<<<grid, kInflThreads, 0, s>>>(F, p->dconv_all, inv4a2, p->gtab);
     const int st = check_launch(p, "k_gc_table");
     if (st) return st;
@@ -267,7 +266,7 @@ int launch_p3m_tables(pme_plan_t p, cudaStream_t s) {
   for (int f = 0; f < p->nframes; ++f) {
     const FrameDesc& F = p->frames_h[f];
     const long long Mh = (long long)F.g.N[0] * F.g.N[1] * (F.g.N[2] / 2 + 1);
-    const int grid = int(std::min<long long>((Mh + kInflThreads - 1) / kInflThreads, 152 * 8));
+    const int grid = int(std::min<long long>((Mh + kInflThreads - 1) / kInflThreads, 8LL * device_sm_count()));
     k_p3m_table<<<grid, kInflThreads, 0, s>>>(F, inv4a2, p->gtab);
     const int st = check_launch(p, "k_p3m_table");
     if (st) return st;
@@ -278,7 +277,8 @@ int launch_p3m_tables(pme_plan_t p, cudaStream_t s) {
 int influence_blocks(const Geometry& g) {
   const long long Mh = (long long)g.N[0] * g.N[1] * (g.N[2] / 2 + 1);
   const long long want = (Mh + kInflThreads - 1) / kInflThreads;
-  return int(want < kInflMaxBlocks ? (want > 0 ? want : 1) : kInflMaxBlocks);
+  const long long cap = 4LL * device_sm_count();
+  return int(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
 int launch_influence(pme_plan_t p, cudaStream_t s, cufftComplex* spec, bool tangent,

@@ -25,6 +25,17 @@ namespace gbpme {
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+int device_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
 int set_error(pme_plan_t plan, int status, const std::string& what) {
   if (plan) plan->last_error = what;
   return status;

@@ -443,7 +443,7 @@ int launch_sort_t(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangen
 int launch_input_check(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool with_lists) {
   int st = check_cuda(p, cudaMemsetAsync(p->in_flags, 0, 2 * sizeof(int), s), "memset");
   if (st || in.n == 0) return st;
-  const int grid = std::min(152 * 4, (3 * in.n + 255) / 256);
+  const int grid = std::min(4 * device_sm_count(), (3 * in.n + 255) / 256);
   k_input_check<<<grid, 256, 0, s>>>(in.n, in, p->in_saved, p->max_ions, with_lists ? p->plist_cnt : nullptr,
                                       p->in_diff, p->cache_bad);
   count_launch();

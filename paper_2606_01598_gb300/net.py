@@ -111,6 +111,11 @@ class Net:
             self._check(self.lib.gbnet_set_params(self.handle, self._s(), _ptr(t)), "gbnet_set_params")
             torch.cuda.current_stream(self.device).synchronize()
 
+    def set_params_device(self, t: torch.Tensor):
+        """Copy parameters from a float32 device tensor on the call's stream (no host sync)."""
+        with torch.cuda.device(self.device):
+            self._check(self.lib.gbnet_set_params(self.handle, self._s(), _ptr(t)), "gbnet_set_params")
+
     def get_params(self) -> torch.Tensor:
         t = torch.empty(NUM_PARAMS, dtype=torch.float32, device=self.device)
         with torch.cuda.device(self.device):
