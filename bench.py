@@ -467,10 +467,11 @@ def virial_cost(gb, fr, cfg, dev, pos, q, mu, flush, steps):
     return {"forward_ms": t_f, "forward_with_virial_ms": t_v, "steps": k}
 
 
-def batch16_rooflines(gb, fr, cfg, dev, steps):
+def batch16_rooflines(gb, fr, cfg, dev, steps, brick=None):
     """Spread / gather / influence rooflines over 16 frames of the 32k workload in one batched
     launch per stage (working set well above L2). The frames are translated, axis-permuted
-    copies of the benchmark frame: same statistics, different ion-to-brick layouts."""
+    copies of the benchmark frame: same statistics, different ion-to-brick layouts. brick: the
+    spread's brick shape (None: the default)."""
     import numpy as np
     import torch
     import workloads as W
@@ -492,7 +493,7 @@ def batch16_rooflines(gb, fr, cfg, dev, steps):
     gF, gphi, gfield = (torch.tensor(np.float32(x), device=dev) for x in W.tangent(F * n, seed=17))
     gE = torch.full((F,), 0.5, dtype=torch.float64, device=dev)
     bp = gb.BatchPlan([fr.box] * F, [cfg["mesh"]] * F, [cfg["order"]] * F, offsets, cfg["alpha"], cfg["rcut"],
-                      device=dev, fft=FFT, overlap_pair=False)
+                      device=dev, fft=FFT, overlap_pair=False, brick=brick)
     for _ in range(2):
         bp.forward(P, Qv, MU)
         bp.backward(P, Qv, MU, gE, gF, gphi, gfield)
@@ -518,7 +519,23 @@ def batch16_rooflines(gb, fr, cfg, dev, steps):
         ach = by / (avg / 1e3) / 1e9
         out[stage] = {"avg_launch_ms": round(avg, 5), "bytes_per_launch": by, "achieved": round(ach, 1),
                       "frac": round(ach / peak, 4)}
-    return {"frames": F, "ions_per_frame": n, "peak_gbs": peak, "peak_source": kind, "stages": out}
+    return {"frames": F, "ions_per_frame": n, "peak_gbs": peak, "peak_source": kind,
+            "brick": list(brick) if brick else [8, 8, 16], "stages": out}
+
+
+def brick_sweep_batch16(gb, fr, cfg, dev, steps):
+    """The 16-frame roofline of the spread for every built brick shape: the batched plans are
+    not tuned, so the sweep shows each shape's spread over the batch; the line reports the
+    default shape's full table and the fastest shape's."""
+    sweep = {}
+    for sh in gb.pme.SPREAD_SHAPES:
+        r = batch16_rooflines(gb, fr, cfg, dev, max(3, steps // 2), brick=sh)
+        sweep["x".join(map(str, sh))] = r
+    spread_ms = lambda r: r["stages"]["fwd.spread"]["avg_launch_ms"] + r["stages"]["bwd.spread"]["avg_launch_ms"]
+    best = min(sweep, key=lambda k: spread_ms(sweep[k]))
+    return sweep["8x8x16"], sweep[best], {k: {s_: v["frac"] for s_, v in r["stages"].items()
+                                             if s_.endswith("spread") or s_.endswith("gather")}
+                                         for k, r in sweep.items()}
 
 
 def train_bench(gb, dev, steps):
@@ -645,6 +662,9 @@ def run_ours(args):
     import workloads as W
 
     n = fr.n
+    # the brick autotuner's table for this frame (the plan below takes its cached choice)
+    _, tune_times = gb.autotune_brick(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], n, device=dev)
+    tune_ms = {"x".join(map(str, k)): (None if v is None else round(v, 4)) for k, v in tune_times.items()}
     plan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=n, device=dev, fft=FFT)
     c = lambda x: torch.tensor(np.float32(x), device=dev)
     pos, q, mu = c(fr.pos), c(fr.q), c(fr.mu)
@@ -692,7 +712,7 @@ def run_ours(args):
     # ---- per-kernel times: the same K steps with the pair term on the call's stream ---------
     # (stage events then bracket one kernel at a time; the overlapped run above is the value)
     splan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=n,
-                    device=dev, fft=FFT, overlap_pair=False)
+                    device=dev, fft=FFT, overlap_pair=False, brick=plan.brick)
 
     def sstep():
         splan.forward(pos, q, mu, energy=True, force=True, phi=True, field=True)
@@ -729,11 +749,11 @@ def run_ours(args):
     h2d = 2 * (12 + 4 + 12) * n + (12 + 4 + 12) * n + 8
     d2h = 8 + (12 + 4 + 12) * n + (12 + 4 + 12) * n
     clocks = sampler.stop()
-    plain = b16 = vir = train = None
+    plain = b16 = b16_best = b16_sweep = vir = train = None
     if rank == 0 and not args.no_extras:
         plain = vs_plain(gb, fr, cfg, dev, pos, q, mu, gE, gF, gphi, gfield, flush, args.steps)
         vir = virial_cost(gb, fr, cfg, dev, pos, q, mu, flush, args.steps)
-        b16 = batch16_rooflines(gb, fr, cfg, dev, args.steps)
+        b16, b16_best, b16_sweep = brick_sweep_batch16(gb, fr, cfg, dev, args.steps)
         train = train_bench(gb, dev, args.steps)
 
     if rank == 0:
@@ -783,6 +803,10 @@ def run_ours(args):
                                    "avg_launch_ms": round(v["avg_launch_ms"], 5)}
                                for k, v in mesh_kernels.items()},
             "mesh_rooflines_batch16": b16,
+            "mesh_rooflines_batch16_best_brick": b16_best,
+            "batch16_brick_sweep_frac": b16_sweep,
+            "brick": list(plan.brick),
+            "brick_autotune_ms": tune_ms,
             "vs_plain": plain,
             "virial": vir,
             "train": train,

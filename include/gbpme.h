@@ -73,7 +73,11 @@ typedef struct {
   int include_self;        /* 1: self terms (default) */
   int include_background;  /* 1: neutralising background term (default) */
   int max_ions;            /* capacity; default 1<<18, at most 1<<27 (PME_ERR_UNSUPPORTED) */
-  int brick[3];            /* spread/gather brick edge in mesh points; 0 = automatic */
+  int brick[3];            /* spread brick edge in mesh points, x y z: one of the built shapes
+                              8x8x16 (the default), 8x8x32, 16x8x16, 16x16x16, 4x8x16
+                              (PME_ERR_UNSUPPORTED otherwise); {0,0,0} = automatic: the
+                              autotuner's choice when opts.autotune is set (single-frame
+                              plans), the default shape otherwise */
   int overlap_pair;        /* 1: run the pair term on a plan-owned side stream, concurrently
                               with the mesh stages (default); 0: everything on the call's
                               stream, one stage after the other (per-kernel timing) */
@@ -99,7 +103,15 @@ typedef struct {
                               (PME_ERR_UNSUPPORTED where they do not apply). With the own
                               transforms the stage timers' "FFT R2C" and "FFT C2R" stages are
                               the z/y passes and "influence" includes the x transforms */
-  int reserved[4];
+  int autotune;            /* 1 (default): with brick {0,0,0}, pme_plan_create times every
+                              built brick shape once for this (device, mesh, order, max_ions
+                              rounded up to a power of two) on synthetic uniform ions -- the
+                              forward + backward of the mesh part, CUDA events, median of 5 --
+                              and keeps the fastest (the default shape unless another is more
+                              than 2 % faster); the choice is cached for the process (and in the
+                              file named by the environment variable GBPME_TUNE_CACHE, if set).
+                              0: no tuning. Batched plans are not tuned. */
+  int reserved[3];
 } pme_opts;
 
 void pme_opts_default(pme_opts* opts);
@@ -128,6 +140,9 @@ int pme_plan_destroy(pme_plan_t plan);
  * (Stockham transforms in shared memory, the x transform fused with the influence multiply),
  * 1 for cuFFT. */
 int pme_plan_fft_kind(pme_plan_t plan, int* kind);
+
+/* The spread brick shape the plan uses (explicit, tuned or default): brick[3] = x, y, z edges. */
+int pme_plan_brick(pme_plan_t plan, int brick[3]);
 
 /* Text of the last error recorded on the plan (never NULL). */
 const char* pme_last_error(pme_plan_t plan);
@@ -271,6 +286,17 @@ int pme_gather(pme_plan_t plan, void* stream, int n, const float* pos, const flo
 int pme_pair(pme_plan_t plan, void* stream, int n, const float* pos, const float* q,
              const float* mu, float* out, double* e_pair);
 
+/* The brick autotuner on its own (what pme_plan_create does with opts.autotune): times the
+ * forward + backward of the mesh part (pair term off) of a plan with each built brick shape on
+ * n_ions synthetic uniform ions in `box` and writes the fastest shape to brick_out[3] and, if
+ * ms_out is not NULL, the median milliseconds of each shape in the order 8x8x16, 8x8x32,
+ * 16x8x16, 16x16x16, 4x8x16 (a negative value: that shape does not fit this mesh and order).
+ * opts (may be NULL) supplies the remaining options. Allocates its own device buffers and
+ * temporary plans on the current device; uses the process-wide cache. No counterpart in the
+ * paper (its kernels are PyTorch operations with no launch parameters to choose). */
+int pme_autotune_brick(const double box[9], const int mesh[3], int order, double alpha, double rcut,
+                       int n_ions, const pme_opts* opts, int brick_out[3], double* ms_out);
+
 /* Number of the library's own kernels launched since the library was loaded (cuFFT's
  * kernels are not counted). */
 long long pme_launch_count(void);
@@ -299,7 +325,8 @@ int pme_profile_read(pme_plan_t plan, double* ms, long long* calls);
  * cudaMalloc fails), or a simulation loop that must not allocate or free because
  * cudaMalloc / cudaFree can synchronise the device. It computes the same rho_mesh as
  * pme_spread with the same kernels in the same order, so the result is bitwise that of a
- * plan's pme_spread with the same box, mesh and order, but it needs no plan and allocates
+ * plan's pme_spread with the same box, mesh and order and the default brick (8 x 8 x 16, which
+ * this entry point always uses), but it needs no plan and allocates
  * nothing: all of its sort scratch lives in ONE static device array of
  * PME_NOALLOC_SCRATCH_BYTES bytes inside the library, which every GPU that loads the library
  * keeps until the process exits.

@@ -27,7 +27,7 @@ class PMEOpts(ctypes.Structure):
                 ("include_pair", c_int), ("include_self", c_int), ("include_background", c_int),
                 ("max_ions", c_int), ("brick", c_int * 3), ("overlap_pair", c_int),
                 ("recip_method", c_int), ("ewald_kmax", c_double), ("influence_kind", c_int),
-                ("fft", c_int), ("reserved", c_int * 4)]
+                ("fft", c_int), ("autotune", c_int), ("reserved", c_int * 3)]
 
 
 _SIGS = {
@@ -38,6 +38,7 @@ _SIGS = {
     "pme_plan_set_box": (c_int, [c_void_p, c_double_p]),
     "pme_plan_destroy": (c_int, [c_void_p]),
     "pme_plan_fft_kind": (c_int, [c_void_p, c_int_p]),
+    "pme_plan_brick": (c_int, [c_void_p, c_int_p]),
     "pme_last_error": (ctypes.c_char_p, [c_void_p]),
     "pme_status_string": (ctypes.c_char_p, [c_int]),
     "pme_sync_status": (c_int, [c_void_p, c_void_p]),
@@ -50,6 +51,8 @@ _SIGS = {
     "pme_gather": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 3),
     "pme_pair": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 5),
     "pme_launch_count": (ctypes.c_longlong, []),
+    "pme_autotune_brick": (c_int, [c_double_p, c_int_p, c_int, c_double, c_double, c_int,
+                                   ctypes.POINTER(PMEOpts), c_int_p, c_double_p]),
     "pme_profile_enable": (c_int, [c_void_p, c_int]),
     "pme_profile_read": (c_int, [c_void_p, c_double_p, ctypes.POINTER(ctypes.c_longlong)]),
     "pme_spread_noalloc": (c_int, [c_void_p, c_double_p, c_int_p, c_int, c_int] + [c_void_p] * 5),

@@ -56,7 +56,26 @@ int launch_p3m_tables(pme_plan_t p, cudaStream_t s);
 // Fill every frame's influence table for the plan's kind (G C for kind 0, P3M for kind 1):
 // plan creation and set_box; the multiply passes read it.
 int launch_influence_tables(pme_plan_t p, cudaStream_t s);
-void spread_brick_shape(int shape[3]);
+void spread_brick_shape(int shape[3]);   // the default brick
+// Brick shapes the spread kernels are built for (the autotuner chooses among them).
+constexpr int kNumSpreadShapes = 5;
+constexpr int kSpreadShapes[kNumSpreadShapes][3] = {{8, 8, 16}, {8, 8, 32}, {16, 8, 16}, {16, 16, 16}, {4, 8, 16}};
+bool spread_shape_supported(const int shape[3]);
+// tune.cu: the brick autotuner (pme_autotune_brick); use_cache: answer from the cache when the
+// key is known (ms_out then stays untouched)
+int autotune_brick(const double box[9], const int mesh[3], int order, double alpha, double rcut, int n,
+                   const pme_opts& base, int out[3], double* ms_out, bool use_cache);
+// one launcher per brick shape (spread.cu, spread_shapes_*.cu); mode 0 forward, 1 tangent,
+// 2 quadrupole forward
+#define GBPME_SPREAD_SHAPE(tag)                                                                      \
+  int launch_spread_##tag(pme_plan_t p, cudaStream_t s, int mode, float* mesh, const int* keep_rho, \
+                          const float* theta);
+GBPME_SPREAD_SHAPE(8x8x16)
+GBPME_SPREAD_SHAPE(8x8x32)
+GBPME_SPREAD_SHAPE(16x8x16)
+GBPME_SPREAD_SHAPE(16x16x16)
+GBPME_SPREAD_SHAPE(4x8x16)
+#undef GBPME_SPREAD_SHAPE
 
 // conv.cu: the mesh convolution by hand-written transforms (meshes whose axes are all
 // 2,3,5-smooth and at most kConvMaxLen long, planes within shared memory).

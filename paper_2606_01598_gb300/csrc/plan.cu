@@ -423,6 +423,11 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
   if (p->max_ions > (1 << 27)) return set_error(p, PME_ERR_UNSUPPORTED, "more than 2^27 ions in one plan");
   int brick[3];
   spread_brick_shape(brick);
+  if (p->opts.brick[0] > 0 || p->opts.brick[1] > 0 || p->opts.brick[2] > 0) {
+    if (!spread_shape_supported(p->opts.brick))
+      return set_error(p, PME_ERR_UNSUPPORTED, "brick shape not among the built ones");
+    for (int a = 0; a < 3; ++a) brick[a] = p->opts.brick[a];
+  }
   // the mesh convolution runs on the hand-written transforms when the options ask for them,
   // every axis of every frame is 2,3,5-smooth and short enough, and a plane (pass A / C) and
   // a pass-B tile fit in shared memory
@@ -1106,6 +1111,7 @@ void pme_opts_default(pme_opts* o) {
   o->overlap_pair = 1;
   o->recip_method = 0;
   o->ewald_kmax = 0.0;
+  o->autotune = 1;
 }
 
 const char* pme_status_string(int s) {
@@ -1170,6 +1176,13 @@ int pme_plan_create(pme_plan_t* out, const double box[9], const int mesh[3], int
   if (opts) p->opts = *opts;
   else pme_opts_default(&p->opts);
   int st = validate_opts(p, alpha, rcut);
+  // automatic brick: the autotuner's (cached) choice for this mesh, order and capacity
+  if (st == PME_OK && p->opts.autotune && p->opts.recip_method == 0 && p->opts.brick[0] == 0 &&
+      p->opts.brick[1] == 0 && p->opts.brick[2] == 0 && order >= 1 && order <= kMaxOrder) {
+    int b[3];
+    if (autotune_brick(box, mesh, order, alpha, rcut, p->opts.max_ions, p->opts, b, nullptr, true) == PME_OK)
+      for (int a = 0; a < 3; ++a) p->opts.brick[a] = b[a];
+  }
   if (st == PME_OK) {
     p->max_ions = p->opts.max_ions;
     FrameInput fi{box, {mesh[0], mesh[1], mesh[2]}, order, 0, p->max_ions};
@@ -1220,6 +1233,12 @@ int pme_batch_create(pme_plan_t* out, int nframes, const int* offsets, const dou
 }
 
 int pme_batch_frames(pme_plan_t p) { return p ? p->nframes : 0; }
+
+int pme_plan_brick(pme_plan_t p, int brick[3]) {
+  if (!p || !brick) return PME_ERR_ARG;
+  for (int a = 0; a < 3; ++a) brick[a] = p->frames_h[0].g.brick[a];
+  return PME_OK;
+}
 
 int pme_plan_set_box(pme_plan_t p, const double box[9]) {
   if (!p || !box) return PME_ERR_ARG;

@@ -1,0 +1,12 @@
+// Spread kernels of the 16 x 16 x 16 brick (one of the shapes the brick autotuner
+// chooses among; the kernel is the template of spread_impl.cuh).
+#include "spread_impl.cuh"
+
+namespace gbpme {
+
+int launch_spread_16x16x16(pme_plan_t p, cudaStream_t s, int mode, float* mesh, const int* keep_rho,
+                           const float* theta) {
+  return launch_spread_shape<Shape<16, 16, 16>>(p, s, mode, mesh, keep_rho, theta);
+}
+
+}  // namespace gbpme

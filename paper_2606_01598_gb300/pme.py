@@ -100,6 +100,35 @@ def spread_noalloc(box, mesh, order: int, pos, q, mu=None, status=None):
     return rho
 
 
+def _set_brick(opts, brick, autotune):
+    if brick is not None:
+        b = [int(x) for x in brick]
+        if len(b) != 3:
+            raise ValueError("brick is three edges (x, y, z)")
+        opts.brick[0], opts.brick[1], opts.brick[2] = b
+    opts.autotune = int(bool(autotune))
+
+
+SPREAD_SHAPES = [(8, 8, 16), (8, 8, 32), (16, 8, 16), (16, 16, 16), (4, 8, 16)]
+
+
+def autotune_brick(box, mesh, order: int, alpha: float, rcut: float, n_ions: int, device=None):
+    """pme_autotune_brick: the fastest brick shape for this mesh, order and ion count, and the
+    median forward + backward milliseconds of every built shape (None where it does not apply)."""
+    lib = _abi.load()
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    b = (ctypes.c_double * 9)(*np.asarray(box, np.float64).reshape(9))
+    m = (ctypes.c_int * 3)(*[int(x) for x in mesh])
+    out = (ctypes.c_int * 3)()
+    ms = (ctypes.c_double * len(SPREAD_SHAPES))()
+    with torch.cuda.device(dev):
+        st = lib.pme_autotune_brick(b, m, int(order), float(alpha), float(rcut), int(n_ions), None, out, ms)
+    if st:
+        raise PMEError(st, "pme_autotune_brick")
+    times = {sh: (ms[k] if ms[k] >= 0 else None) for k, sh in enumerate(SPREAD_SHAPES)}
+    return (out[0], out[1], out[2]), times
+
+
 def launch_count() -> int:
     return int(_abi.load().pme_launch_count())
 
@@ -115,7 +144,8 @@ class Plan:
                  coulomb_k: float = 1.0, include_pair: bool = True, include_self: bool = True,
                  include_background: bool = True, max_ions: int = 1 << 18,
                  overlap_pair: bool = True, recip_method: str = "mesh", ewald_kmax: float = 0.0,
-                 influence: str = "deconvolution", fft: str = "auto", device=None):
+                 influence: str = "deconvolution", fft: str = "auto", brick=None, autotune: bool = True,
+                 device=None):
         if not torch.cuda.is_available():
             raise RuntimeError("gbpme needs a CUDA device; there is no CPU fallback")
         self.lib = _abi.load()
@@ -146,6 +176,7 @@ class Plan:
         opts.fft = _FFT_KINDS[fft]
         opts.recip_method = 0 if recip_method == "mesh" else 1
         opts.ewald_kmax = float(ewald_kmax)
+        _set_brick(opts, brick, autotune)
         self.box = np.asarray(box, np.float64).reshape(3, 3).copy()
         self.mesh = tuple(int(x) for x in mesh)
         self.order = int(order)
@@ -162,8 +193,14 @@ class Plan:
         if st:
             raise PMEError(st, "pme_plan_create")
         self.handle = h
+        self.brick = self._brick()
 
     # -- helpers ---------------------------------------------------------------------------
+    def _brick(self):
+        b = (ctypes.c_int * 3)()
+        self._check(self.lib.pme_plan_brick(self.handle, b), "pme_plan_brick")
+        return (b[0], b[1], b[2])
+
     def _check(self, st, where):
         if st:
             raise PMEError(st, where, self.lib.pme_last_error(self.handle).decode())
@@ -367,7 +404,7 @@ class BatchPlan(Plan):
                  influence_power: float = 1.0, deconvolution: bool = True,
                  coulomb_k: float = 1.0, include_pair: bool = True, include_self: bool = True,
                  include_background: bool = True, overlap_pair: bool = True,
-                 influence: str = "deconvolution", fft: str = "auto", device=None):
+                 influence: str = "deconvolution", fft: str = "auto", brick=None, device=None):
         if not torch.cuda.is_available():
             raise RuntimeError("gbpme needs a CUDA device; there is no CPU fallback")
         self.lib = _abi.load()
@@ -391,6 +428,7 @@ class BatchPlan(Plan):
         opts.include_self = int(bool(include_self))
         opts.include_background = int(bool(include_background))
         opts.overlap_pair = int(bool(overlap_pair))
+        _set_brick(opts, brick, False)
         boxes = np.asarray(boxes, np.float64).reshape(-1, 9)
         meshes = np.asarray(meshes, np.int32).reshape(-1, 3)
         orders = np.asarray(orders, np.int32).reshape(-1)
@@ -413,6 +451,7 @@ class BatchPlan(Plan):
         if st:
             raise PMEError(st, "pme_batch_create")
         self.handle = h
+        self.brick = self._brick()
 
     def forward(self, pos, q, mu=None, *, energy=True, force=True, phi=True, field=True,
                 field_grad=False, virial=False):

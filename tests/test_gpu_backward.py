@@ -162,7 +162,8 @@ def test_pair_lists_disabled_and_overflowing_paths(gb):
     args = (c(pos), c(q), c(mu), gE, c(gF), c(gphi), c(gfield))
     outs = []
     for max_ions in (1024, 1 << 18):
-        plan = gb.Plan(fr.box, mesh, p, a, rc, max_ions=max_ions)
+        # one brick for both (the automatic choice is tuned per capacity)
+        plan = gb.Plan(fr.box, mesh, p, a, rc, max_ions=max_ions, brick=(8, 8, 16))
         f = plan.forward(*args[:3], field_grad=True)
         b = plan.backward(*args)
         outs.append((f, b))

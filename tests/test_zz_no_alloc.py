@@ -4,9 +4,9 @@ that must not allocate because allocation can synchronise the device).
 
 It is called through the C ABI several times in a row -- on different inputs, so later calls
 also show that the shared static scratch carries nothing over -- and each result must equal
-pme_spread of a plan with the same box, mesh and order bit for bit (the header promises the
-same kernels in the same order), and match the float64 oracle's mesh density within the mesh
-tolerance of the other parity tests. The largest case fills the fixed scratch: 32768 ions on a
+pme_spread of a plan with the same box, mesh, order and brick (8 x 8 x 16) bit for bit (the
+header promises the same kernels in the same order), and match the float64 oracle's mesh
+density within the mesh tolerance of the other parity tests. The largest case fills the fixed scratch: 32768 ions on a
 128^3 mesh (the largest candidate-brick table). A NaN input is reported through the optional
 device status word. Sizes beyond the fixed scratch must be rejected. The file name makes pytest
 collect it last."""
@@ -53,7 +53,7 @@ def test_noalloc_spread_equals_plan_spread_in_a_row(gb):
     for fr, mesh, order in cases:   # calls in a row on the shared scratch
         pos64, q64, mu64 = prepared(fr)
         pos, q, mu = (torch.tensor(np.float32(x), device="cuda") for x in (pos64, q64, mu64))
-        plan = gb.Plan(fr.box, mesh, order, 0.30, 9.0, max_ions=max(4096, fr.n))
+        plan = gb.Plan(fr.box, mesh, order, 0.30, 9.0, max_ions=max(4096, fr.n), brick=(8, 8, 16))
         ref = plan.spread(pos, q, mu)
         rho = torch.full(mesh, float("nan"), dtype=torch.float32, device="cuda")
         st = _noalloc(lib, fr.box, mesh, order, pos, q, mu, rho, status)
@@ -82,7 +82,7 @@ def test_noalloc_reports_nonfinite_input(gb):
     assert _noalloc(lib, fr.box, (24, 24, 24), 4, pos, q, mu, rho, status) == 0
     torch.cuda.synchronize()
     assert status.item() == 0
-    plan = gb.Plan(fr.box, (24, 24, 24), 4, 0.30, 9.0, max_ions=1024)
+    plan = gb.Plan(fr.box, (24, 24, 24), 4, 0.30, 9.0, max_ions=1024, brick=(8, 8, 16))
     assert torch.equal(rho, plan.spread(pos, q, mu))
     plan.close()
 
