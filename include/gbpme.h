@@ -58,7 +58,8 @@ typedef enum {
   PME_ERR_NONFINITE = 4,    /* a NaN or Inf appeared in pos, q, mu or theta (device flag) */
   PME_ERR_UNSUPPORTED = 5,  /* option combination not implemented (e.g. finite surface eps) */
   PME_ERR_TIMEOUT = 6,      /* a bounded device-side wait expired */
-  PME_ERR_NOMEM = 7         /* device allocation failed at plan creation */
+  PME_ERR_NOMEM = 7,        /* device allocation failed at plan creation */
+  PME_ERR_BOUNDS = 8        /* index-checking build only: a kernel's index check failed */
 } pme_status;
 
 typedef struct pme_plan_s* pme_plan_t;
@@ -296,6 +297,18 @@ int pme_pair(pme_plan_t plan, void* stream, int n, const float* pos, const float
  * paper (its kernels are PyTorch operations with no launch parameters to choose). */
 int pme_autotune_brick(const double box[9], const int mesh[3], int order, double alpha, double rcut,
                        int n_ions, const pme_opts* opts, int brick_out[3], double* ms_out);
+
+/* Index-checking build. Compiled with -DGBPME_BOUNDS (libgbpme_bounds.so, built on request),
+ * the sort, spread, gather, pair-list and combine kernels test every array index they derive
+ * (sorted slots, mesh offsets, pair-list slots and partner indices) against its array's size
+ * before the access; a failed test skips the access and sets a device flag -- it never traps,
+ * so the context stays usable. pme_sync_status then reports PME_ERR_BOUNDS.
+ * pme_bounds_flags() returns and clears the flags of all kernels (bit 0 spread, 1 gather,
+ * 2 pair, 3 combine, 4 sort; always 0 in the normal build) and pme_bounds_checking() tells
+ * which build is loaded (1 = index-checking). No counterpart in the paper: a debugging aid
+ * for memory races and indexing errors, in place of compute-sanitizer. */
+int pme_bounds_flags(void);
+int pme_bounds_checking(void);
 
 /* Number of the library's own kernels launched since the library was loaded (cuFFT's
  * kernels are not counted). */

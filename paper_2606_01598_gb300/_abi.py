@@ -19,7 +19,7 @@ HEADERS = [HEADER, os.path.join(ROOT, "include", "gbnet.h")]
 
 STATUS = {0: "PME_OK", 1: "PME_ERR_ARG", 2: "PME_ERR_CUDA", 3: "PME_ERR_CUFFT",
           4: "PME_ERR_NONFINITE", 5: "PME_ERR_UNSUPPORTED", 6: "PME_ERR_TIMEOUT",
-          7: "PME_ERR_NOMEM"}
+          7: "PME_ERR_NOMEM", 8: "PME_ERR_BOUNDS"}
 
 
 class PMEOpts(ctypes.Structure):
@@ -51,6 +51,8 @@ _SIGS = {
     "pme_gather": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 3),
     "pme_pair": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 5),
     "pme_launch_count": (ctypes.c_longlong, []),
+    "pme_bounds_flags": (c_int, []),
+    "pme_bounds_checking": (c_int, []),
     "pme_autotune_brick": (c_int, [c_double_p, c_int_p, c_int, c_double, c_double, c_int,
                                    ctypes.POINTER(PMEOpts), c_int_p, c_double_p]),
     "pme_profile_enable": (c_int, [c_void_p, c_int]),
@@ -103,11 +105,12 @@ def header_functions() -> list[str]:
 
 
 def load():
-    """Load libgbpme.so (built in-tree). Raises if it is missing: there is no fallback."""
+    """Load libgbpme.so (built in-tree), or with GBPME_BOUNDS=1 in the environment the
+    index-checking libgbpme_bounds.so. Raises if it is missing: there is no fallback."""
     global _LIB
     if _LIB is not None:
         return _LIB
-    path = lib_path()
+    path = lib_path(os.environ.get("GBPME_BOUNDS") == "1")
     if not os.path.exists(path):
         raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
                            "(the CUDA library is required; there is no CPU fallback)")

@@ -32,8 +32,11 @@ def find_nvcc() -> str:
     raise RuntimeError("nvcc not found (set CUDA_HOME)")
 
 
-def lib_path() -> str:
-    return os.path.join(LIBDIR, LIBNAME)
+BOUNDS_LIBNAME = "libgbpme_bounds.so"
+
+
+def lib_path(bounds: bool = False) -> str:
+    return os.path.join(LIBDIR, BOUNDS_LIBNAME if bounds else LIBNAME)
 
 
 def _sources():
@@ -52,13 +55,15 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile and link the library; returns the path of the shared object."""
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, bounds: bool = False) -> str:
+    """Compile and link the library; returns the path of the shared object. bounds: the
+    index-checking variant (-DGBPME_BOUNDS, libgbpme_bounds.so, objects in _build/bounds)."""
     nvcc = find_nvcc()
     cuda_home = os.path.dirname(os.path.dirname(nvcc))
-    os.makedirs(BUILD, exist_ok=True)
+    bdir = os.path.join(BUILD, "bounds") if bounds else BUILD
+    os.makedirs(bdir, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
-    out = lib_path()
+    out = lib_path(bounds)
     headers = [d for d in _deps() if not d.endswith(".cu")]
     if not force and not _stale(out, _deps()):
         return out
@@ -66,9 +71,11 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
                      "-I", os.path.join(ROOT, "include"), "-I", CSRC]
     if ptxas_info:
         cflags += ["-Xptxas", "-v"]
+    if bounds:
+        cflags += ["-DGBPME_BOUNDS"]
 
     def compile_one(src: str):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         if force or _stale(obj, [src] + headers):
             cmd = [nvcc, "-c", src, "-o", obj] + cflags
             r = subprocess.run(cmd, capture_output=True, text=True)
@@ -93,4 +100,5 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv,
+                bounds="--bounds" in sys.argv))

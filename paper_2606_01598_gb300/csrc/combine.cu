@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kCombThreads) k_combine_forward(CombineArgs a)
   const int i = lo + int(threadIdx.x);
   double e_i = 0.0;
   float vi[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // virial terms of ion i
-  if (i < hi) {
+  if (i < hi && index_ok(i, a.in.n)) {
     const float bg = bg_factor(a, F);
     float qi = a.in.q[i];
     float mu[3] = {0.f, 0.f, 0.f};
@@ -363,5 +363,7 @@ int launch_pair_energy(pme_plan_t p, cudaStream_t s, int n, const IonInputs& in,
   return check_launch(p, "k_pair_energy");
 }
 
+
+GBPME_BOUNDS_READER(bounds_hit_combine)
 
 }  // namespace gbpme

@@ -480,4 +480,49 @@ constexpr int kFlagNonFinite = 1;
 constexpr int kFlagTimeout = 2;
 constexpr int kFlagVirialLost = 4;   // a virial pass fell back to the fused pair kernel
 
+// ----------------------------------------------------------------------------------------
+// index-checking build (compiled with -DGBPME_BOUNDS): index_ok(i, n) tests 0 <= i < n before
+// a kernel touches element i of an array of n; a failed test records a bit in a device word of
+// the translation unit and the access is skipped (no trap, no fault). Each translation unit
+// provides a reader (GBPME_BOUNDS_READER) that returns and clears its word; in a normal build
+// index_ok is always true and the readers return 0.
+// ----------------------------------------------------------------------------------------
+#ifdef GBPME_BOUNDS
+namespace {
+__device__ int g_bounds_hit;
+}
+__device__ __forceinline__ bool index_ok(long long i, long long n) {
+  if (i >= 0 && i < n) return true;
+  atomicOr(&g_bounds_hit, 1);
+  return false;
+}
+#define GBPME_BOUNDS_READER(fn)                                                   \
+  int fn() {                                                                      \
+    int v = 0;                                                                    \
+    if (cudaMemcpyFromSymbol(&v, g_bounds_hit, sizeof(int)) != cudaSuccess) {    \
+      cudaGetLastError();                                                         \
+      return 0;                                                                   \
+    }                                                                             \
+    if (v) {                                                                      \
+      const int z = 0;                                                            \
+      cudaMemcpyToSymbol(g_bounds_hit, &z, sizeof(int));                          \
+    }                                                                             \
+    return v;                                                                     \
+  }
+#else
+__device__ __forceinline__ bool index_ok(long long, long long) { return true; }
+#define GBPME_BOUNDS_READER(fn) \
+  int fn() { return 0; }
+#endif
+// readers of the translation units with checks (0 in normal builds)
+int bounds_hit_spread();
+int bounds_hit_spread_8x8x32();
+int bounds_hit_spread_16x8x16();
+int bounds_hit_spread_16x16x16();
+int bounds_hit_spread_4x8x16();
+int bounds_hit_gather();
+int bounds_hit_pair();
+int bounds_hit_combine();
+int bounds_hit_sort();
+
 }  // namespace gbpme

@@ -110,11 +110,12 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
         int y = m.y + jy;
         if (y >= Ny) y -= Ny;
         const size_t off = (size_t(x) * Ny + y) * Nz + z;
-        const float v = __ldg(phi_mesh + off);
+        const bool in_mesh = index_ok((long long)off, (long long)g.N[0] * Ny * Nz);
+        const float v = in_mesh ? __ldg(phi_mesh + off) : 0.f;
 #pragma unroll
         for (int b = 0; b <= DM; ++b) r[b] += v * wy[b][jy];
         if (TAN) {
-          const float dv = __ldg(dphi_mesh + off);
+          const float dv = in_mesh ? __ldg(dphi_mesh + off) : 0.f;
 #pragma unroll
           for (int b = 0; b < 3; ++b) rt[b] += dv * wy[b][jy];
         }
@@ -327,5 +328,7 @@ int launch_gather_quad(pme_plan_t p, cudaStream_t s, int n, const float* mesh, c
   if (p->batch) return launch_t<2, true>(p, s, n, mesh, nullptr, out, theta, qout);
   return launch_t<2, false>(p, s, n, mesh, nullptr, out, theta, qout);
 }
+
+GBPME_BOUNDS_READER(bounds_hit_gather)
 
 }  // namespace gbpme

@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_build(PairArgs a, int* ov
                          !(self_cell && j == __float_as_int(fi.w));
         const unsigned bal = __ballot_sync(0xffffffffu, hit);
         const int k = cnt[s] + __popc(bal & lane_lt);
-        if (hit && k < cap)
+        if (hit && k < cap && index_ok(k, cap))
           a.list[size_t(i0 + s) * cap + k] = make_float4(r.x, r.y, r.z, __int_as_float(j));
         cnt[s] += __popc(bal);
       }
@@ -609,7 +609,9 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_listed(PairArgs a, int n)
   const int c = a.list_cnt[i];
   const float4* li = a.list + size_t(i) * a.list_cap;
   for (int k = lane; k < c; k += 32) {
+    if (!index_ok(k, a.list_cap)) break;
     const float4 h = li[k];
+    if (!index_ok(__float_as_int(h.w), n)) continue;
     interact<TAN>(a, I, __float_as_int(h.w), mk(h.x, h.y, h.z), A, VIR ? vir : nullptr);
   }
   if (VIR) {
@@ -761,5 +763,7 @@ int launch_pair_listed(pme_plan_t p, cudaStream_t s, int n, bool tangent, const 
   count_launch();
   return check_launch(p, "k_pair_listed");
 }
+
+GBPME_BOUNDS_READER(bounds_hit_pair)
 
 }  // namespace gbpme

@@ -1124,6 +1124,7 @@ const char* pme_status_string(int s) {
     case PME_ERR_UNSUPPORTED: return "unsupported option";
     case PME_ERR_TIMEOUT: return "device wait timed out";
     case PME_ERR_NOMEM: return "out of device memory";
+    case PME_ERR_BOUNDS: return "index check failed";
     default: return "unknown status";
   }
 }
@@ -1298,7 +1299,28 @@ int pme_sync_status(pme_plan_t p, void* stream) {
   if (flags & kFlagVirialLost)
     return set_error(p, PME_ERR_UNSUPPORTED,
                      "virial: a pair-hit list overflowed, so the pair part of the virial is missing");
+  if (pme_bounds_flags()) return set_error(p, PME_ERR_BOUNDS, "an index check failed (index-checking build)");
   return PME_OK;
+}
+
+int pme_bounds_flags(void) {
+  int v = 0;
+  v |= bounds_hit_spread() ? 1 : 0;
+  v |= (bounds_hit_spread_8x8x32() | bounds_hit_spread_16x8x16() | bounds_hit_spread_16x16x16() |
+        bounds_hit_spread_4x8x16()) ? 1 : 0;
+  v |= bounds_hit_gather() ? 2 : 0;
+  v |= bounds_hit_pair() ? 4 : 0;
+  v |= bounds_hit_combine() ? 8 : 0;
+  v |= bounds_hit_sort() ? 16 : 0;
+  return v;
+}
+
+int pme_bounds_checking(void) {
+#ifdef GBPME_BOUNDS
+  return 1;
+#else
+  return 0;
+#endif
 }
 
 int pme_forward(pme_plan_t p, void* stream, int n, const float* pos, const float* q,

@@ -213,8 +213,14 @@ __global__ void __launch_bounds__(kSortThreads)
 k_scatter(int n, SortBuffers sb, int need_mesh, int need_pair, const int* reuse) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || (reuse && *reuse == 0)) return;
-  if (need_mesh) sb.perm_b[sb.start_b[sb.key_b[i]] + sb.slot_b[i]] = i;
-  if (need_pair) sb.perm_c[sb.start_c[sb.key_c[i]] + sb.slot_c[i]] = i;
+  if (need_mesh) {
+    const int d = sb.start_b[sb.key_b[i]] + sb.slot_b[i];
+    if (index_ok(d, n)) sb.perm_b[d] = i;
+  }
+  if (need_pair) {
+    const int d = sb.start_c[sb.key_c[i]] + sb.slot_c[i];
+    if (index_ok(d, n)) sb.perm_c[d] = i;
+  }
 }
 
 __device__ __forceinline__ int stable_rank(const int* perm, int seg_lo, int seg_hi, int self,
@@ -252,6 +258,7 @@ k_rank_records(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, Mesh
     const int k = sb.key_c[i];
     dest = stable_rank(sb.perm_c, sb.start_c[k], sb.start_c[k + 1], i, t);
   }
+  if (!index_ok(i, n) || !index_ok(dest, n)) return;
   const int f = BATCH ? maps.ion_frame[i] : 0;
   const FrameDesc& F = frame_at<BATCH>(one, maps, f);
   const Geometry& g = F.g;
@@ -456,5 +463,7 @@ int launch_sort(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangent,
   return p->batch ? launch_sort_t<true>(p, s, in, tangent, need_mesh, need_pair, reuse, save)
                   : launch_sort_t<false>(p, s, in, tangent, need_mesh, need_pair, reuse, save);
 }
+
+GBPME_BOUNDS_READER(bounds_hit_sort)
 
 }  // namespace gbpme

@@ -406,9 +406,10 @@ __global__ void __launch_bounds__(SH::NT) k_spread(SpreadArgs a) {
     float* rho = a.mesh + F.mesh_off + off;
     float* drho = a.mesh + (MODE == 2 ? F.mesh_off : F.tmesh_off) + off;
     const int nz = min(ZS, ez - seg * ZS);
+    const long long M = (long long)Nx * Ny * Nz;
 #pragma unroll
     for (int z = 0; z < ZS; ++z)
-      if (z < nz) {
+      if (z < nz && index_ok((long long)(off + z), M)) {
         if (with_rho) rho[z] = acc[z];
         if (TAN) drho[z] = dacc[z];
       }

@@ -9,4 +9,6 @@ int launch_spread_16x16x16(pme_plan_t p, cudaStream_t s, int mode, float* mesh, 
   return launch_spread_shape<Shape<16, 16, 16>>(p, s, mode, mesh, keep_rho, theta);
 }
 
+GBPME_BOUNDS_READER(bounds_hit_spread_16x16x16)
+
 }  // namespace gbpme

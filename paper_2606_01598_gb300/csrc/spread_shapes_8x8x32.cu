@@ -9,4 +9,6 @@ int launch_spread_8x8x32(pme_plan_t p, cudaStream_t s, int mode, float* mesh, co
   return launch_spread_shape<Shape<8, 8, 32>>(p, s, mode, mesh, keep_rho, theta);
 }
 
+GBPME_BOUNDS_READER(bounds_hit_spread_8x8x32)
+
 }  // namespace gbpme

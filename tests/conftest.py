@@ -17,3 +17,21 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def root():
     return ROOT
+
+
+def pytest_sessionfinish(session, exitstatus):
+    """Under the index-checking build (GBPME_BOUNDS=1) write which build ran and the kernels'
+    index-check flags to the file named by GBPME_BOUNDS_REPORT."""
+    path = os.environ.get("GBPME_BOUNDS_REPORT")
+    if not path or os.environ.get("GBPME_BOUNDS") != "1":
+        return
+    import json
+    try:
+        import paper_2606_01598_gb300 as g
+        lib = g.load_library()
+        rep = {"checking": int(lib.pme_bounds_checking()), "flags": int(lib.pme_bounds_flags()),
+               "exitstatus": int(exitstatus)}
+    except Exception as e:  # reported, the outer test fails on it
+        rep = {"error": str(e)}
+    with open(path, "w") as f:
+        json.dump(rep, f)

@@ -25,8 +25,9 @@ def test_every_header_symbol_is_exported(lib):
 
 
 def test_status_strings(lib):
-    for s in range(8):
+    for s in range(9):
         assert lib.pme_status_string(s)
+    assert lib.pme_bounds_checking() == 0 and lib.pme_bounds_flags() == 0
     assert lib.pme_last_error(None) == b"null plan"
 
 
