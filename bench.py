@@ -854,6 +854,12 @@ def run_quad(args):
     t_quad = time_steps(torch, lambda: plan.forward_quad(pos, q, mu, th), args.steps, args.warmup, dev, flush)
     # kernels of this library inside the timed steps (the same per call)
     launches = (gb.launch_count() - l0) // (args.steps + args.warmup) * args.steps
+    # forward + backward (Hessian-vector product) with quadrupoles: the force-matching step
+    gF, gphi, gfield = (torch.tensor(np.float32(x), device=dev) for x in W.tangent(n, seed=99))
+    gE = torch.tensor([0.5], dtype=torch.float64, device=dev)
+    t_qfb = time_steps(torch, lambda: (plan.forward_quad(pos, q, mu, th),
+                                       plan.backward_quad(pos, q, mu, th, gE, gF, gphi, gfield)),
+                       args.steps, args.warmup, dev, flush)
     t_plain = time_steps(torch, lambda: plan.forward(pos, q, mu, field_grad=True), args.steps, args.warmup,
                          dev, flush)
     splan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=n, device=dev,
@@ -902,6 +908,8 @@ def run_quad(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": cfgd, "transforms": plan.fft_kind,
         "plain_forward_ms": t_plain,
+        "quad_fwd_bwd_ms": t_qfb,
+        "quad_fwd_bwd_Mion_evals_per_s": n / t_qfb / 1e3,
         "serial_ms_per_step": s_ms,
         "stage_ms": {k: round(v[0] / v[1], 5) for k, v in sorted(stages.items())},
         "roofline": roof,

@@ -17,8 +17,8 @@
  *   E_background -pi Q^2 / (2 V alpha^2), Q = sum q (zero for neutral frames).
  *
  * and its derivatives, and the vector-Jacobian product (adjoint) of those derivatives that
- * a force-matching loss (Eq. loss) needs. pme_forward_quad / pme_batch_forward_quad add point
- * quadrupoles (the rank-2 channel; forward only), documented at their declarations.
+ * a force-matching loss (Eq. loss) needs. pme_forward_quad / pme_backward_quad and their batch
+ * forms add point quadrupoles (the rank-2 channel), documented at their declarations.
  *
  * Conventions
  *   - Lengths in the caller's unit (Angstrom in the tests), charges in e, dipoles in e*length.
@@ -219,12 +219,31 @@ int pme_forward_virial(pme_plan_t plan, void* stream, int n, const float* pos, c
  * Outputs as pme_forward, except field_grad = -dE/dTheta (the symmetric matrix G with
  * dE = -G : dTheta for symmetric dTheta; equal to pme_forward's field gradient when Theta = 0)
  * and force = -dE/dr including Theta : grad^3 phi. Plans with recip_method 0 (batched plans:
- * pme_batch_forward_quad); no CUDA graph, no virial and no backward (a later pme_backward
- * recomputes from its own inputs). Pointers follow pme_forward's host/device rule. theta may
+ * pme_batch_forward_quad); no CUDA graph and no virial; the backward is pme_backward_quad. Pointers follow pme_forward's host/device rule. theta may
  * be NULL only when n = 0. */
 int pme_forward_quad(pme_plan_t plan, void* stream, int n, const float* pos, const float* q,
                      const float* mu, const float* theta, double* energy, float* force, float* phi,
                      float* field, float* field_grad);
+
+/* Backward with point quadrupoles: the vector-Jacobian product of the map
+ * (pos, q, mu, theta) -> (E, force, phi, field) of pme_forward_quad for cotangents g_energy [1]
+ * float64, g_force [n][3], g_phi [n], g_field [n][3] (each may be NULL = zero; there is no
+ * cotangent on the -dE/dTheta output):
+ *   grad = g_E dE + H v  in (r, q, mu, Theta),  v = (-g_force, g_phi, -g_field, 0),
+ * with H the Hessian of E. grad_theta [n][6] (xx, yy, zz, xy, xz, yz) is the symmetric matrix G
+ * with dL = G : dTheta for symmetric dTheta. This is the double backward through the forces
+ * that a force-matching loss (Eq. loss) needs when the quadrupole channel is trained: the mesh
+ * part spreads the tangent density (Theta : grad grad)(dr . grad) W with third spline
+ * derivatives and gathers Phi to fourth and d Phi to third order; the pair part evaluates the
+ * quadrupole pair sums in dual numbers (value and directional derivative). Needs spline order
+ * >= 4 and, with the pair term, the plan's pair-hit lists (PME_ERR_UNSUPPORTED otherwise; a
+ * list that overflows at run time is reported by pme_sync_status as PME_ERR_UNSUPPORTED).
+ * Recomputes everything from its own inputs (no reuse of a forward, no CUDA graph). Pointers
+ * follow pme_forward's host/device rule; outputs may be NULL. */
+int pme_backward_quad(pme_plan_t plan, void* stream, int n, const float* pos, const float* q,
+                      const float* mu, const float* theta, const double* g_energy,
+                      const float* g_force, const float* g_phi, const float* g_field,
+                      float* grad_pos, float* grad_q, float* grad_mu, float* grad_theta);
 
 /* ---- batched frames ----------------------------------------------------------------------
  * One plan over F frames stored back to back in the per-ion arrays: frame f owns ions
@@ -257,6 +276,12 @@ int pme_batch_forward_virial(pme_plan_t plan, void* stream, const float* pos, co
 int pme_batch_forward_quad(pme_plan_t plan, void* stream, const float* pos, const float* q,
                            const float* mu, const float* theta, double* energy, float* force,
                            float* phi, float* field, float* field_grad);
+
+/* As pme_backward_quad for every frame: theta [offsets[F]][6], g_energy [F] float64. */
+int pme_batch_backward_quad(pme_plan_t plan, void* stream, const float* pos, const float* q,
+                            const float* mu, const float* theta, const double* g_energy,
+                            const float* g_force, const float* g_phi, const float* g_field,
+                            float* grad_pos, float* grad_q, float* grad_mu, float* grad_theta);
 
 /* As pme_backward for every frame; g_energy is [F] float64 (one cotangent per frame). */
 int pme_batch_backward(pme_plan_t plan, void* stream, const float* pos, const float* q,

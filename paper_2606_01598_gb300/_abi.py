@@ -46,6 +46,8 @@ _SIGS = {
     "pme_forward_virial": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 9),
     "pme_forward_quad": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 9),
     "pme_backward": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 10),
+    "pme_backward_quad": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 12),
+    "pme_batch_backward_quad": (c_int, [c_void_p, c_void_p] + [c_void_p] * 12),
     "pme_spread": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 4),
     "pme_solve": (c_int, [c_void_p, c_void_p] + [c_void_p] * 3),
     "pme_gather": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 3),

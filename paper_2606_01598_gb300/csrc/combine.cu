@@ -259,6 +259,80 @@ __global__ void __launch_bounds__(kCombThreads) k_combine_backward(CombineArgs a
   }
 }
 
+// Quadrupole Hessian-vector product, per ion: from the mesh and pair parts' 13 gathered values
+// and their tangents (out[26]: phi, grad phi, grad^2 phi, Theta : grad^3 phi), the gradient of
+// E in (r, q, mu, Theta) and its directional derivative along v = (dr, dq, dmu) = (-g_force,
+// g_phi, -g_field), grad = g_E dE + d(dE):
+//   dE/dr     = k (q g + H mu + t3)
+//   dE/dq     = k (phi - c_phi q - bg Q + c tr Theta)
+//   dE/dmu    = k (g - c mu)
+//   dE/dTheta = k (H + c q I - c5 (tr Theta I + 2 Theta))
+// (c_phi = 2 alpha / sqrt(pi), c = 4 alpha^3 / (3 sqrt(pi)), c5 = 8 alpha^5 / (5 sqrt(pi)), bg =
+// pi / (V alpha^2)), and their tangents k (dq g + q dg + dH mu + H dmu + dt3),
+// k (dphi - c_phi dq - bg dQ), k (dg - c dmu), k (dH + c dq I).
+template <bool BATCH>
+__global__ void __launch_bounds__(kCombThreads) k_combine_backward_quad(CombineArgs a, const float* qm,
+                                                                      const float* qp, float* grad_theta) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.in.n) return;
+  const int f = BATCH ? a.maps.ion_frame[i] : 0;
+  const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, f);
+  const float bg = bg_factor(a, F);
+  const float qi = a.in.q[i];
+  float mu[3] = {0.f, 0.f, 0.f}, dmu[3] = {0.f, 0.f, 0.f};
+  if (a.in.mu)
+    for (int c = 0; c < 3; ++c) mu[c] = a.in.mu[3 * i + c];
+  if (a.in.gfield)
+    for (int c = 0; c < 3; ++c) dmu[c] = -a.in.gfield[3 * i + c];
+  const float dq = a.in.gphi ? a.in.gphi[i] : 0.f;
+  const float gE = a.g_energy ? float(a.g_energy[f]) : 0.f;
+  float v[26];
+#pragma unroll
+  for (int t = 0; t < 26; ++t) v[t] = qm[size_t(i) * 26 + t] + (a.with_pair ? qp[size_t(i) * 26 + t] : 0.f);
+  const float* P = v;          // phi, g (3), H (6: xx yy zz xy xz yz), t3 (3)
+  const float* T = v + 13;     // their tangents
+  const float* th = a.in.theta + size_t(i) * 6;
+  const float trT = th[0] + th[1] + th[2];
+  const float Q = float(a.qsum[2 * f]), dQ = float(a.qsum[2 * f + 1]);
+  const float k = a.k;
+  // H mu and dH mu, H dmu (symmetric 6-vectors)
+  auto hv = [](const float* H, const float* x, float* y) {
+    y[0] = H[0] * x[0] + H[3] * x[1] + H[4] * x[2];
+    y[1] = H[3] * x[0] + H[1] * x[1] + H[5] * x[2];
+    y[2] = H[4] * x[0] + H[5] * x[1] + H[2] * x[2];
+  };
+  float Hm[3], dHm[3], Hdm[3];
+  hv(P + 4, mu, Hm);
+  hv(T + 4, mu, dHm);
+  hv(P + 4, dmu, Hdm);
+  if (a.grad_pos) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float Er = qi * P[1 + c] + Hm[c] + P[10 + c];
+      const float dEr = dq * P[1 + c] + qi * T[1 + c] + dHm[c] + Hdm[c] + T[10 + c];
+      a.grad_pos[3 * i + c] = k * (gE * Er + dEr);
+    }
+  }
+  if (a.grad_q) {
+    const float Eq = P[0] - a.self_phi * qi - bg * Q + a.self_c * trT;
+    const float dEq = T[0] - a.self_phi * dq - bg * dQ;
+    a.grad_q[i] = k * (gE * Eq + dEq);
+  }
+  if (a.grad_mu) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a.grad_mu[3 * i + c] = k * (gE * (P[1 + c] - a.self_c * mu[c]) + T[1 + c] - a.self_c * dmu[c]);
+  }
+  if (grad_theta) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const float diag = c < 3 ? 1.f : 0.f;
+      const float Et = P[4 + c] + a.self_c * qi * diag - a.self_c5 * (trT * diag + 2.f * th[c]);
+      const float dEt = T[4 + c] + a.self_c * dq * diag;
+      grad_theta[6 * i + c] = k * (gE * Et + dEt);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kCombThreads)
 k_pair_energy(int n, const float* q, const float* mu, const float* pair_out, double* e_ion) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -352,6 +426,24 @@ int launch_combine_backward(pme_plan_t p, cudaStream_t s, const IonInputs& in,
   else k_combine_backward<false><<<grid, kCombThreads, 0, s>>>(a);
   count_launch();
   return check_launch(p, "k_combine_backward");
+}
+
+int launch_combine_backward_quad(pme_plan_t p, cudaStream_t s, const IonInputs& in, const double* g_energy,
+                                 const float* qmesh, const float* qpair, float* grad_pos, float* grad_q,
+                                 float* grad_mu, float* grad_theta) {
+  CombineArgs a = base_args(p, in);
+  a.with_mesh = 1;
+  a.with_pair = p->opts.include_pair != 0;
+  a.g_energy = g_energy;
+  a.grad_pos = grad_pos;
+  a.grad_q = grad_q;
+  a.grad_mu = grad_mu;
+  const int grid = (in.n + kCombThreads - 1) / kCombThreads;
+  if (grid == 0) return PME_OK;
+  if (p->batch) k_combine_backward_quad<true><<<grid, kCombThreads, 0, s>>>(a, qmesh, qpair, grad_theta);
+  else k_combine_backward_quad<false><<<grid, kCombThreads, 0, s>>>(a, qmesh, qpair, grad_theta);
+  count_launch();
+  return check_launch(p, "k_combine_backward_quad");
 }
 
 int launch_pair_energy(pme_plan_t p, cudaStream_t s, int n, const IonInputs& in,

@@ -242,6 +242,8 @@ struct pme_plan_s {
   gbpme::PairRecords pr;
   float* mesh_out;           // [max_ions][10] per-ion mesh results (caller order)
   float* pair_out;           // [max_ions][10] per-ion pair results
+  float* qb_mesh = nullptr;  // [max_ions][26] quadrupole backward: mesh values and tangents
+  float* qb_pair = nullptr;  // [max_ions][26] the same for the pair term
   float* quad_out = nullptr; // [max_ions][8] quadrupole forward: Theta : grad^3 phi of the mesh
                              // (0..2) and of the pair term (4..6); single-frame plans
   double* epart;             // reciprocal energy partials, one per influence (or k) block
@@ -351,7 +353,11 @@ __device__ __forceinline__ void spline_weights(float f, float (&w)[DMAX + 1][P])
     if constexpr (DMAX >= 3)
       w[3][j] = lv[3][i] - 3.f * ((i >= 1) ? lv[3][i - 1] : 0.f) +
                 3.f * ((i >= 2) ? lv[3][i - 2] : 0.f) - ((i >= 3) ? lv[3][i - 3] : 0.f);
+    if constexpr (DMAX >= 4)
+      w[4][j] = lv[4][i] - 4.f * ((i >= 1) ? lv[4][i - 1] : 0.f) + 6.f * ((i >= 2) ? lv[4][i - 2] : 0.f) -
+                4.f * ((i >= 3) ? lv[4][i - 3] : 0.f) + ((i >= 4) ? lv[4][i - 4] : 0.f);
   }
+  static_assert(DMAX <= 4, "derivatives up to order 4");
 }
 
 // Fractional coordinate s = r C^{-1} wrapped into [0,1), in float64.
@@ -479,6 +485,7 @@ __device__ __forceinline__ void item_range(const FrameDesc& F, int item, int& lo
 constexpr int kFlagNonFinite = 1;
 constexpr int kFlagTimeout = 2;
 constexpr int kFlagVirialLost = 4;   // a virial pass fell back to the fused pair kernel
+constexpr int kFlagQuadLost = 16;    // a quadrupole backward found an overflowed pair-hit list
 
 // ----------------------------------------------------------------------------------------
 // index-checking build (compiled with -DGBPME_BOUNDS): index_ok(i, n) tests 0 <= i < n before

@@ -277,6 +277,229 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
 #undef TMOM
 }
 
+// Quadrupole Hessian-vector product, mesh part: for each ion the 13 gathered quantities of the
+// quadrupole forward -- phi, grad phi, grad^2 phi and Theta_i : grad^3 phi -- and their
+// directional derivatives along the ion's displacement dr and the tangent mesh d Phi (the
+// potential of d rho): with t = D^T dr, M the moments of Phi and N those of d Phi (mesh
+// coordinates),
+//   d phi = N_0 + M_1 . t,  d grad phi = D (N_1 + M_2 t),  d grad^2 phi = D (N_2 + M_3[t]) D^T,
+//   d (Theta : grad^3 phi) = D (Theta' : N_3 + Theta' : M_4[t]),  Theta' = D^T Theta D,
+// which needs the moments of Phi up to order 4 and of d Phi up to order 3. Output
+// out[caller index][26]: the 13 values, then their 13 tangents.
+template <int P, bool BATCH>
+__global__ void __launch_bounds__(kGatherThreads) k_gather_qdual(GatherArgs a) {
+  const int gid = a.t_lo + (blockIdx.x * blockDim.x + threadIdx.x) / kGroup;
+  const int l = threadIdx.x & (kGroup - 1);
+  const bool valid = gid < a.t_hi;
+  const int ion = valid ? gid : a.t_lo;
+  const int frame = BATCH ? a.maps.sorted_frame[ion] : 0;
+  const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, frame);
+  const Geometry& g = F.g;
+  const float* phi_mesh = a.mesh + F.mesh_off;
+  const float* dphi_mesh = a.mesh + F.tmesh_off;
+  const int4 m = a.mr.idx[ion];
+  const float4 fq = a.mr.fq[ion];
+  float wx[5][P], wy[5][P], wzall[5][P];
+  spline_weights<P, 4>(fq.x, wx);
+  spline_weights<P, 4>(fq.y, wy);
+  spline_weights<P, 4>(fq.z, wzall);
+  const bool act = valid && (l < P);
+  float wz[5];
+#pragma unroll
+  for (int c = 0; c <= 4; ++c) {
+    float v = 0.f;
+#pragma unroll
+    for (int j = 0; j < P; ++j) v = (j == l) ? wzall[c][j] : v;
+    wz[c] = act ? v : 0.f;
+  }
+  int z = m.z + l;
+  if (z >= g.N[2]) z -= g.N[2];
+  const int Ny = g.N[1], Nz = g.N[2];
+  const long long Mtot = (long long)g.N[0] * Ny * Nz;
+  float S[5][5], T[4][4];   // S[a][b]: sum over (jx, jy) of Phi W_x^(a) W_y^(b), a + b <= 4
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j < 5; ++j) S[i][j] = 0.f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) T[i][j] = 0.f;
+  if (act) {
+#pragma unroll
+    for (int jx = 0; jx < P; ++jx) {
+      int x = m.x + jx;
+      if (x >= g.N[0]) x -= g.N[0];
+      float r[5], rt[4];
+#pragma unroll
+      for (int b = 0; b < 5; ++b) r[b] = 0.f;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) rt[b] = 0.f;
+#pragma unroll
+      for (int jy = 0; jy < P; ++jy) {
+        int y = m.y + jy;
+        if (y >= Ny) y -= Ny;
+        const size_t off = (size_t(x) * Ny + y) * Nz + z;
+        const bool in_mesh = index_ok((long long)off, Mtot);
+        const float v = in_mesh ? __ldg(phi_mesh + off) : 0.f;
+        const float dv = in_mesh ? __ldg(dphi_mesh + off) : 0.f;
+#pragma unroll
+        for (int b = 0; b < 5; ++b) r[b] += v * wy[b][jy];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) rt[b] += dv * wy[b][jy];
+      }
+#pragma unroll
+      for (int ia = 0; ia < 5; ++ia)
+#pragma unroll
+        for (int ib = 0; ib < 5; ++ib)
+          if (ia + ib <= 4) S[ia][ib] += r[ib] * wx[ia][jx];
+#pragma unroll
+      for (int ia = 0; ia < 4; ++ia)
+#pragma unroll
+        for (int ib = 0; ib < 4; ++ib)
+          if (ia + ib <= 3) T[ia][ib] += rt[ib] * wx[ia][jx];
+    }
+  }
+  // moments M[a][b][c] (a + b + c <= 4) and N[a][b][c] (<= 3), reduced over the z-lanes
+  float M[5][5][5], N[4][4][4];
+#pragma unroll
+  for (int ia = 0; ia < 5; ++ia)
+#pragma unroll
+    for (int ib = 0; ib < 5; ++ib)
+#pragma unroll
+      for (int ic = 0; ic < 5; ++ic) M[ia][ib][ic] = (ia + ib + ic <= 4) ? group_sum(S[ia][ib] * wz[ic]) : 0.f;
+#pragma unroll
+  for (int ia = 0; ia < 4; ++ia)
+#pragma unroll
+    for (int ib = 0; ib < 4; ++ib)
+#pragma unroll
+      for (int ic = 0; ic < 4; ++ic) N[ia][ib][ic] = (ia + ib + ic <= 3) ? group_sum(T[ia][ib] * wz[ic]) : 0.f;
+  if (!valid || l != 0) return;
+  const float4 tt = a.mr.tt[ion];
+  const float tv[3] = {tt.x, tt.y, tt.z};
+  // Theta' = D^T Theta D
+  const float* th = a.theta + size_t(m.w) * 6;
+  const float Th[3][3] = {{th[0], th[3], th[4]}, {th[3], th[1], th[5]}, {th[4], th[5], th[2]}};
+  float TD[3][3], Tp[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      TD[r][c] = Th[r][0] * g.D[0 * 3 + c] + Th[r][1] * g.D[1 * 3 + c] + Th[r][2] * g.D[2 * 3 + c];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      Tp[r][c] = g.D[0 * 3 + r] * TD[0][c] + g.D[1 * 3 + r] * TD[1][c] + g.D[2 * 3 + r] * TD[2][c];
+  // moment of a multi-index given as axis list: e1 = unit steps
+  auto mom = [&](int i0, int i1, int i2) { return M[i0][i1][i2]; };
+  auto nmom = [&](int i0, int i1, int i2) { return N[i0][i1][i2]; };
+  (void)mom;
+  (void)nmom;
+  // first-, second-, third-order tensors in mesh coordinates
+  const int e[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  float m1[3], n1[3], m2[3][3], n2[3][3], m2t[3], m3t[3][3], n3th[3], m4t[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    m1[i] = M[e[i][0]][e[i][1]][e[i][2]];
+    n1[i] = N[e[i][0]][e[i][1]][e[i][2]];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      m2[i][j] = M[e[i][0] + e[j][0]][e[i][1] + e[j][1]][e[i][2] + e[j][2]];
+      n2[i][j] = N[e[i][0] + e[j][0]][e[i][1] + e[j][1]][e[i][2] + e[j][2]];
+    }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float s2 = 0.f, s3 = 0.f, s4 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      s2 += m2[i][j] * tv[j];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int a0 = e[i][0] + e[j][0] + e[k][0], a1 = e[i][1] + e[j][1] + e[k][1], a2 = e[i][2] + e[j][2] + e[k][2];
+        // Theta'_jk N_jki and Theta'_jk sum_l M_jkil t_l
+        s3 += Tp[j][k] * N[a0][a1][a2];
+        float s = 0.f;
+#pragma unroll
+        for (int l2 = 0; l2 < 3; ++l2) s += M[a0 + e[l2][0]][a1 + e[l2][1]][a2 + e[l2][2]] * tv[l2];
+        s4 += Tp[j][k] * s;
+      }
+    }
+    m2t[i] = s2;
+    n3th[i] = s3;
+    m4t[i] = s4;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        s += M[e[i][0] + e[j][0] + e[k][0]][e[i][1] + e[j][1] + e[k][1]][e[i][2] + e[j][2] + e[k][2]] * tv[k];
+      m3t[i][j] = s;
+    }
+  // Theta' : M_3 (the forward's third-order contraction)
+  float v3[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        s += Tp[j][k] * M[e[i][0] + e[j][0] + e[k][0]][e[i][1] + e[j][1] + e[k][1]][e[i][2] + e[j][2] + e[k][2]];
+    v3[i] = s;
+  }
+  // r-space: vectors D x, matrices D X D^T
+  float gr[3], dgr[3], t3r[3], dt3r[3];
+  {
+    float a1[3], a2[3], a3[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      a1[i] = n1[i] + m2t[i];
+      a2[i] = n3th[i] + m4t[i];
+      a3[i] = m1[i];
+    }
+    apply_D(g.D, a3, gr);
+    apply_D(g.D, a1, dgr);
+    apply_D(g.D, v3, t3r);
+    apply_D(g.D, a2, dt3r);
+  }
+  float Hr[3][3], dHr[3][3];
+#pragma unroll
+  for (int pass = 0; pass < 2; ++pass) {
+    float X[3][3], XD[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) X[i][j] = pass == 0 ? m2[i][j] : n2[i][j] + m3t[i][j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) XD[i][b] = X[i][0] * g.D[b * 3 + 0] + X[i][1] * g.D[b * 3 + 1] + X[i][2] * g.D[b * 3 + 2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const float v = g.D[i * 3 + 0] * XD[0][b] + g.D[i * 3 + 1] * XD[1][b] + g.D[i * 3 + 2] * XD[2][b];
+        if (pass == 0) Hr[i][b] = v;
+        else dHr[i][b] = v;
+      }
+  }
+  const float dphi = N[0][0][0] + m1[0] * tv[0] + m1[1] * tv[1] + m1[2] * tv[2];
+  float* o = a.out + size_t(m.w) * 26;
+  const float vals[26] = {M[0][0][0], gr[0], gr[1], gr[2], Hr[0][0], Hr[1][1], Hr[2][2], Hr[0][1], Hr[0][2], Hr[1][2],
+                          t3r[0], t3r[1], t3r[2],
+                          dphi, dgr[0], dgr[1], dgr[2], dHr[0][0], dHr[1][1], dHr[2][2], dHr[0][1], dHr[0][2],
+                          dHr[1][2], dt3r[0], dt3r[1], dt3r[2]};
+#pragma unroll
+  for (int k = 0; k < 26; ++k) o[k] = vals[k];
+}
+
 template <int MODE, bool BATCH>
 int launch_t(pme_plan_t p, cudaStream_t s, int n, const float* mesh, const double* g_energy,
              float* out, const float* theta = nullptr, float* qout = nullptr) {
@@ -327,6 +550,42 @@ int launch_gather_quad(pme_plan_t p, cudaStream_t s, int n, const float* mesh, c
                        float* out, float* qout) {
   if (p->batch) return launch_t<2, true>(p, s, n, mesh, nullptr, out, theta, qout);
   return launch_t<2, false>(p, s, n, mesh, nullptr, out, theta, qout);
+}
+
+int launch_gather_qdual(pme_plan_t p, cudaStream_t s, int n, const float* mesh, const float* theta, float* out) {
+  GatherArgs a;
+  a.one = p->frames_h[0];
+  a.maps = p->maps;
+  a.mr = p->mr;
+  a.mesh = mesh;
+  a.g_energy = nullptr;
+  a.out = out;
+  a.theta = theta;
+  a.qout = nullptr;
+  for (int gi = 0; gi < p->nogroups; ++gi) {
+    const OrderGroup& G = p->ogroups[gi];
+    a.t_lo = p->batch ? G.sorted_lo : 0;
+    a.t_hi = p->batch ? G.sorted_hi : n;
+    const int grid = int((size_t(a.t_hi - a.t_lo) * kGroup + kGatherThreads - 1) / kGatherThreads);
+    if (grid <= 0) continue;
+#define GBPME_QDUAL(PP)                                                                   \
+  case PP:                                                                                \
+    if (p->batch) k_gather_qdual<PP, true><<<grid, kGatherThreads, 0, s>>>(a);            \
+    else k_gather_qdual<PP, false><<<grid, kGatherThreads, 0, s>>>(a);                    \
+    break;
+    switch (G.order) {
+      GBPME_QDUAL(4)
+      GBPME_QDUAL(5)
+      GBPME_QDUAL(6)
+      GBPME_QDUAL(7)
+      default: return set_error(p, PME_ERR_UNSUPPORTED, "quadrupole backward: spline order below 4");
+    }
+#undef GBPME_QDUAL
+    count_launch();
+    const int st = check_launch(p, "k_gather_qdual");
+    if (st) return st;
+  }
+  return PME_OK;
 }
 
 GBPME_BOUNDS_READER(bounds_hit_gather)

@@ -40,6 +40,9 @@ int launch_spread(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh, const
 // Quadrupole forward: rho of charges, dipoles and point quadrupoles theta [caller index][6]
 // into mesh + mesh_off of every frame.
 int launch_spread_quad(pme_plan_t p, cudaStream_t s, const float* theta, float* mesh);
+// Quadrupole Hessian-vector product: the tangent density d rho of charges, dipoles and
+// quadrupoles along (dr, dq, dmu) into mesh + tmesh_off of every frame.
+int launch_spread_quad_tangent(pme_plan_t p, cudaStream_t s, const float* theta, float* mesh);
 
 // influence.cu: in-place G C / V multiply of every frame's spectrum (and tangent spectrum)
 // and the float64 energy partials (one per block, blocks grouped by frame).
@@ -102,6 +105,10 @@ int launch_conv_inverse(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh,
 //   tangent: out[orig][8]  = mesh part of (grad_r (3), grad_q, grad_mu (3)) of the backward
 int launch_gather(pme_plan_t p, cudaStream_t s, int n, const float* mesh, bool tangent,
                   const double* g_energy, float* out);
+// Quadrupole Hessian-vector product, mesh part: the 13 gathered values of the quadrupole
+// forward and their tangents along (dr, d Phi) at out[orig][26] (Phi at mesh_off, d Phi at
+// tmesh_off of mesh).
+int launch_gather_qdual(pme_plan_t p, cudaStream_t s, int n, const float* mesh, const float* theta, float* out);
 // Quadrupole forward: the forward layout in out, and Theta_i : grad^3 phi at qout[orig][0..2].
 int launch_gather_quad(pme_plan_t p, cudaStream_t s, int n, const float* mesh, const float* theta,
                        float* out, float* qout);
@@ -111,6 +118,9 @@ int launch_gather_quad(pme_plan_t p, cudaStream_t s, int n, const float* mesh, c
 // skip (nullable): return at once when *skip == 0 (the hit lists hold).
 int launch_pair_quad(pme_plan_t p, cudaStream_t s, int n, const float* theta, float* out, float* qout,
                      const int* skip = nullptr);
+// Quadrupole Hessian-vector product: the 13 per-ion pair sums and their tangents along
+// (dr, dq, dmu) from the hit lists, out[caller index][26] (runs only when *flag == 0).
+int launch_pair_quad_dual(pme_plan_t p, cudaStream_t s, int n, const float* theta, float* out, const int* flag);
 // The same from the plan's hit lists (runs only when *flag == 0).
 int launch_pair_quad_listed(pme_plan_t p, cudaStream_t s, int n, const float* theta, float* out,
                             float* qout, const int* flag);
@@ -138,6 +148,11 @@ int launch_combine_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, bo
                            bool with_pair, float* force, float* phi, float* field,
                            float* field_grad, double* energy, int recip_kind,
                            double* virial = nullptr, const float* quad_out = nullptr);
+// Quadrupole Hessian-vector product: grads in (r, q, mu, Theta) from the mesh and pair parts'
+// 26-value dual outputs (qmesh, qpair: [n][26]).
+int launch_combine_backward_quad(pme_plan_t p, cudaStream_t s, const IonInputs& in, const double* g_energy,
+                                 const float* qmesh, const float* qpair, float* grad_pos, float* grad_q,
+                                 float* grad_mu, float* grad_theta);
 int launch_combine_backward(pme_plan_t p, cudaStream_t s, const IonInputs& in,
                             const double* g_energy, float* grad_pos, float* grad_q,
                             float* grad_mu);

@@ -30,9 +30,20 @@
 #include <string>
 #include <vector>
 
+#include "dual.cuh"
 #include "net.cuh"
 
 namespace gbnet {
+
+using gbpme::Dual;
+using gbpme::rcpT;
+using gbpme::sqrtT;
+using gbpme::sincosT;
+using gbpme::sigmoidT;
+using gbpme::siluT;
+using gbpme::dsiluT;
+using gbpme::shfl_xor;
+using gbpme::warp_sum;
 
 namespace {
 
@@ -73,58 +84,6 @@ __host__ __device__ constexpr MixW mix_w(int w) {
                                 : MixW{oLayer0 + (w / 4) * kLayerSize + oWY, 2 * V, V});
 }
 
-// ---------------------------------------------------------------------------------------
-// Dual numbers
-// ---------------------------------------------------------------------------------------
-struct Dual {
-  float v, d;
-  __device__ __forceinline__ Dual() {}
-  __device__ __forceinline__ Dual(float x) : v(x), d(0.f) {}
-  __device__ __forceinline__ Dual(float x, float y) : v(x), d(y) {}
-};
-__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
-__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
-__device__ __forceinline__ Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
-__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.v * b.d + a.d * b.v); }
-__device__ __forceinline__ Dual operator*(float s, Dual a) { return Dual(s * a.v, s * a.d); }
-__device__ __forceinline__ Dual operator*(Dual a, float s) { return Dual(s * a.v, s * a.d); }
-__device__ __forceinline__ Dual operator+(Dual a, float s) { return Dual(a.v + s, a.d); }
-__device__ __forceinline__ Dual operator+(float s, Dual a) { return Dual(a.v + s, a.d); }
-__device__ __forceinline__ Dual operator-(float s, Dual a) { return Dual(s - a.v, -a.d); }
-__device__ __forceinline__ Dual& operator+=(Dual& a, Dual b) { a.v += b.v; a.d += b.d; return a; }
-__device__ __forceinline__ Dual& operator-=(Dual& a, Dual b) { a.v -= b.v; a.d -= b.d; return a; }
-
-__device__ __forceinline__ float rcpT(float a) { return 1.f / a; }
-__device__ __forceinline__ Dual rcpT(Dual a) { const float r = 1.f / a.v; return Dual(r, -a.d * r * r); }
-__device__ __forceinline__ float sqrtT(float a) { return sqrtf(a); }
-__device__ __forceinline__ Dual sqrtT(Dual a) { const float s = sqrtf(a.v); return Dual(s, 0.5f * a.d / s); }
-__device__ __forceinline__ void sincosT(float a, float& s, float& c) { sincosf(a, &s, &c); }
-__device__ __forceinline__ void sincosT(Dual a, Dual& s, Dual& c) {
-  float sv, cv;
-  sincosf(a.v, &sv, &cv);
-  s = Dual(sv, cv * a.d);
-  c = Dual(cv, -sv * a.d);
-}
-__device__ __forceinline__ float sigmoidT(float a) { return 1.f / (1.f + expf(-a)); }
-__device__ __forceinline__ Dual sigmoidT(Dual a) {
-  const float s = 1.f / (1.f + expf(-a.v));
-  return Dual(s, a.d * s * (1.f - s));
-}
-template <typename T> __device__ __forceinline__ T siluT(T x) { return x * sigmoidT(x); }
-// d silu / dx = s (1 + x (1 - s)), s = sigmoid(x)
-template <typename T> __device__ __forceinline__ T dsiluT(T x) {
-  const T s = sigmoidT(x);
-  return s * (1.f + x * (1.f - s));
-}
-__device__ __forceinline__ float shfl_xor(float x, int o) { return __shfl_xor_sync(0xffffffffu, x, o); }
-__device__ __forceinline__ Dual shfl_xor(Dual x, int o) {
-  return Dual(__shfl_xor_sync(0xffffffffu, x.v, o), __shfl_xor_sync(0xffffffffu, x.d, o));
-}
-template <typename T> __device__ __forceinline__ T warp_sum(T x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += shfl_xor(x, o);
-  return x;
-}
 template <typename T> __device__ __forceinline__ T mk(float v, float d);
 template <> __device__ __forceinline__ float mk<float>(float v, float) { return v; }
 template <> __device__ __forceinline__ Dual mk<Dual>(float v, float d) { return Dual(v, d); }
@@ -941,7 +900,7 @@ __global__ void k_adam(int np, float* __restrict__ P, float* __restrict__ m, flo
 // =========================================================================================
 // host side
 // =========================================================================================
-using gbnet::Dual;
+using gbpme::Dual;
 using gbnet::NetFrame;
 
 struct gbnet_s {

@@ -189,7 +189,7 @@ static bool is_device_pointer(const void* ptr) {
 
 enum StageSlot {
   kPos = 0, kQ = 3, kMu = 4, kGF = 7, kGPhi = 10, kGField = 11, kOF = 14, kOPhi = 17,
-  kOField = 18, kOFG = 21, kOGPos = 27, kOGQ = 30, kOGMu = 31, kTheta = 34, kStageFloats = 40
+  kOField = 18, kOFG = 21, kOGPos = 27, kOGQ = 30, kOGMu = 31, kTheta = 34, kOGTheta = 40, kStageFloats = 46
 };
 
 struct Staging {
@@ -646,6 +646,8 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
   A(&p->mesh_out, ni * 10);
   A(&p->pair_out, ni * 10);
   A(&p->quad_out, ni * 8);
+  A(&p->qb_mesh, ni * 26);
+  A(&p->qb_pair, ni * 26);
   A(&p->e_ion, ni);
   A(&p->epart, size_t(p->total_blocks) + 1);
   A(&p->flags, 1);
@@ -1299,6 +1301,9 @@ int pme_sync_status(pme_plan_t p, void* stream) {
   if (flags & kFlagVirialLost)
     return set_error(p, PME_ERR_UNSUPPORTED,
                      "virial: a pair-hit list overflowed, so the pair part of the virial is missing");
+  if (flags & kFlagQuadLost)
+    return set_error(p, PME_ERR_UNSUPPORTED,
+                     "quadrupole backward: a pair-hit list overflowed, so the pair part is missing");
   if (pme_bounds_flags()) return set_error(p, PME_ERR_BOUNDS, "an index check failed (index-checking build)");
   return PME_OK;
 }
@@ -1499,6 +1504,107 @@ int pme_batch_forward_quad(pme_plan_t p, void* stream, const float* pos, const f
   if (sg.status) return sg.status;
   if ((st = run_forward_quad(p, s, in, e_out, f_out, p_out, fl_out, fg_out))) return st;
   return sg.finish();
+}
+
+// Backward with point quadrupoles: the Hessian-vector product along v = (dr, dq, dmu) plus
+// g_E times the gradient, in (r, q, mu, Theta). The mesh part spreads rho (with Theta) and the
+// tangent density d rho (third spline derivatives), transforms both, and gathers the 13
+// quadrupole-forward values with their tangents (moments of Phi to order 4, of d Phi to 3);
+// the pair part evaluates the same 13 sums in dual numbers over the hit lists; the combine
+// assembles the gradients and their tangents with the self and background terms.
+static int run_backward_quad(pme_plan_t p, cudaStream_t s, const IonInputs& in, const double* gE,
+                             float* o_pos, float* o_q, float* o_mu, float* o_theta) {
+  const int n = in.n;
+  if (n == 0) return PME_OK;
+  const bool pair = p->opts.include_pair != 0;
+  constexpr int B = PME_STAGES_PER_PASS;
+  int st, t;
+  p->fwd_n = -1;   // nothing of this pass is reused by a later call
+  p->fwd_lists = false;
+  t = prof_begin(p, B + 0, s);
+  if ((st = launch_sort(p, s, in, true, true, pair, nullptr))) return st;
+  prof_end(p, t, s);
+  cudaStream_t ps = p->opts.overlap_pair ? p->side : s;
+  if (pair) {
+    if (p->opts.overlap_pair && (st = fork_side(p, s))) return st;
+    t = prof_begin(p, B + 6, ps);
+    if ((st = launch_pair_build(p, ps, n, p->cache_bad))) return st;
+    if ((st = launch_pair_quad_dual(p, ps, n, in.theta, p->qb_pair, p->cache_bad))) return st;
+    prof_end(p, t, ps);
+  }
+  t = prof_begin(p, B + 1, s);
+  if ((st = launch_spread_quad(p, s, in.theta, p->rho))) return st;
+  if ((st = launch_spread_quad_tangent(p, s, in.theta, p->rho))) return st;
+  prof_end(p, t, s);
+  t = prof_begin(p, B + 2, s);
+  if ((st = fft_forward(p, s, true))) return st;
+  prof_end(p, t, s);
+  t = prof_begin(p, B + 3, s);
+  if ((st = multiply_influence(p, s, true, nullptr))) return st;
+  prof_end(p, t, s);
+  t = prof_begin(p, B + 4, s);
+  if ((st = fft_inverse(p, s, true))) return st;
+  prof_end(p, t, s);
+  t = prof_begin(p, B + 5, s);
+  if ((st = launch_gather_qdual(p, s, n, p->phi, in.theta, p->qb_mesh))) return st;
+  prof_end(p, t, s);
+  if (pair && p->opts.overlap_pair && (st = join_side(p, s))) return st;
+  t = prof_begin(p, B + 7, s);
+  st = launch_combine_backward_quad(p, s, in, gE, p->qb_mesh, p->qb_pair, o_pos, o_q, o_mu, o_theta);
+  prof_end(p, t, s);
+  return st;
+}
+
+static int backward_quad_common(pme_plan_t p, void* stream, int n, const float* pos, const float* q,
+                                const float* mu, const float* theta, const double* g_energy,
+                                const float* g_force, const float* g_phi, const float* g_field,
+                                float* grad_pos, float* grad_q, float* grad_mu, float* grad_theta, int nE) {
+  int st;
+  if (n > 0 && !theta) return set_error(p, PME_ERR_ARG, "theta is NULL");
+  if ((st = check_quad_orders(p))) return st;
+  if (p->opts.include_pair && !p->plist)
+    return set_error(p, PME_ERR_UNSUPPORTED, "the quadrupole backward needs the plan's pair-hit lists");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Staging sg(p, s, n);
+  IonInputs in{};
+  in.pos = sg.in(pos, 3, kPos);
+  in.q = sg.in(q, 1, kQ);
+  in.mu = sg.in(mu, 3, kMu);
+  in.theta = sg.in(theta, 6, kTheta);
+  in.gforce = sg.in(g_force, 3, kGF);
+  in.gphi = sg.in(g_phi, 1, kGPhi);
+  in.gfield = sg.in(g_field, 3, kGField);
+  in.n = n;
+  const double* gE = sg.in_d(g_energy, nE, 1);
+  float* o_pos = sg.out(grad_pos, 3, kOGPos);
+  float* o_q = sg.out(grad_q, 1, kOGQ);
+  float* o_mu = sg.out(grad_mu, 3, kOGMu);
+  float* o_th = sg.out(grad_theta, 6, kOGTheta);
+  if (sg.status) return sg.status;
+  if ((st = run_backward_quad(p, s, in, gE, o_pos, o_q, o_mu, o_th))) return st;
+  return sg.finish();
+}
+
+int pme_backward_quad(pme_plan_t p, void* stream, int n, const float* pos, const float* q, const float* mu,
+                      const float* theta, const double* g_energy, const float* g_force, const float* g_phi,
+                      const float* g_field, float* grad_pos, float* grad_q, float* grad_mu, float* grad_theta) {
+  int st = check_common(p, n, pos, q);
+  if (st) return st;
+  if (p->opts.recip_method != 0)
+    return set_error(p, PME_ERR_UNSUPPORTED, "quadrupoles need the particle-mesh method (recip_method 0)");
+  return backward_quad_common(p, stream, n, pos, q, mu, theta, g_energy, g_force, g_phi, g_field, grad_pos,
+                              grad_q, grad_mu, grad_theta, 1);
+}
+
+int pme_batch_backward_quad(pme_plan_t p, void* stream, const float* pos, const float* q, const float* mu,
+                            const float* theta, const double* g_energy, const float* g_force,
+                            const float* g_phi, const float* g_field, float* grad_pos, float* grad_q,
+                            float* grad_mu, float* grad_theta) {
+  int st = check_batch(p, pos, q);
+  if (st) return st;
+  const int n = p->frame_offsets[p->nframes];
+  return backward_quad_common(p, stream, n, pos, q, mu, theta, g_energy, g_force, g_phi, g_field, grad_pos,
+                              grad_q, grad_mu, grad_theta, p->nframes);
 }
 
 int pme_backward(pme_plan_t p, void* stream, int n, const float* pos, const float* q,

@@ -35,6 +35,7 @@
 // evaluates each ion's list; the cell-walking kernel then runs only if a list overflowed.
 #include <cmath>
 
+#include "dual.cuh"
 #include "kernels.h"
 
 namespace gbpme {
@@ -69,71 +70,82 @@ struct Sym {
 
 __device__ __forceinline__ Sym load_sym(const float* t) { return Sym{t[0], t[1], t[2], t[3], t[4], t[5]}; }
 
-__device__ __forceinline__ void mul(const Sym& A, float x, float y, float z, float& ox, float& oy, float& oz) {
+template <typename T>
+__device__ __forceinline__ void mul(const Sym& A, T x, T y, T z, T& ox, T& oy, T& oz) {
   ox = A.xx * x + A.xy * y + A.xz * z;
   oy = A.xy * x + A.yy * y + A.yz * z;
   oz = A.xz * x + A.yz * y + A.zz * z;
 }
 
+template <typename T>
 struct QuadAcc {
-  float phi = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-  float hxx = 0.f, hyy = 0.f, hzz = 0.f, hxy = 0.f, hxz = 0.f, hyz = 0.f;
-  float tx = 0.f, ty = 0.f, tz = 0.f;
+  T phi = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+  T hxx = 0.f, hyy = 0.f, hzz = 0.f, hxy = 0.f, hxz = 0.f, hyz = 0.f;
+  T tx = 0.f, ty = 0.f, tz = 0.f;
 };
 
-// One pair: source j at displacement r from the field point with quadrupole A (trace trA).
-__device__ __forceinline__ void quad_pair(const QuadPairArgs& a, const Sym& A, float trA, int j, float rx,
-                                          float ry, float rz, QuadAcc& S) {
+// One pair: source j = (c, d, B) at displacement r from the field point with quadrupole A
+// (trace trA). Written once over the scalar type T: float for the forward; Dual for the
+// Hessian-vector product, where r, c and d carry their tangents along (dr, dq, dmu) and every
+// output its directional derivative (the quadrupoles have none).
+template <typename T>
+__device__ __forceinline__ void quad_pair(const QuadPairArgs& a, const Sym& A, float trA, int j, T rx, T ry, T rz,
+                                          T c, T dx, T dy, T dz, QuadAcc<T>& S) {
   const float al = a.alpha;
-  const float r2 = rx * rx + ry * ry + rz * rz;
-  const float rinv = rsqrtf(r2);
-  const float rinv2 = rinv * rinv;
-  const float ex = expf(-al * al * r2);
-  const float B0 = erfcf(al * r2 * rinv) * rinv;
-  const float B1 = (B0 + a.c[1] * ex) * rinv2;
-  const float B2 = (3.f * B1 + a.c[2] * ex) * rinv2;
-  const float B3 = (5.f * B2 + a.c[3] * ex) * rinv2;
-  const float B4 = (7.f * B3 + a.c[4] * ex) * rinv2;
-  const float B5 = (9.f * B4 + a.c[5] * ex) * rinv2;
-  const float4 mj = a.pr.mu[j];
-  const float c = mj.w, dx = mj.x, dy = mj.y, dz = mj.z;
+  const T r2 = rx * rx + ry * ry + rz * rz;
+  const T rinv = rsqrtT(r2);
+  const T rinv2 = rinv * rinv;
+  const T ex = expT(-(al * al) * r2);
+  const T B0 = erfcT(al * (r2 * rinv)) * rinv;
+  const T B1 = (B0 + a.c[1] * ex) * rinv2;
+  const T B2 = (3.f * B1 + a.c[2] * ex) * rinv2;
+  const T B3 = (5.f * B2 + a.c[3] * ex) * rinv2;
+  const T B4 = (7.f * B3 + a.c[4] * ex) * rinv2;
+  const T B5 = (9.f * B4 + a.c[5] * ex) * rinv2;
   const Sym Bm = load_sym(a.theta + size_t(a.pr.idx[j].w) * 6);
   const float trB = Bm.xx + Bm.yy + Bm.zz;
-  float Brx, Bry, Brz, Arx, Ary, Arz;
+  T Brx, Bry, Brz, Arx, Ary, Arz;
   mul(Bm, rx, ry, rz, Brx, Bry, Brz);
   mul(A, rx, ry, rz, Arx, Ary, Arz);
-  const float dr = dx * rx + dy * ry + dz * rz;
-  const float rBr = Brx * rx + Bry * ry + Brz * rz;
-  const float rAr = Arx * rx + Ary * ry + Arz * rz;
+  const T dr = dx * rx + dy * ry + dz * rz;
+  const T rBr = Brx * rx + Bry * ry + Brz * rz;
+  const T rAr = Arx * rx + Ary * ry + Arz * rz;
   // potential, gradient, Hessian
-  const float sI = -c * B1 - dr * B2 + trB * B2 - rBr * B3;
-  const float srr = c * B2 + dr * B3 - trB * B3 + rBr * B4;
+  const T sI = -(c * B1) - dr * B2 + trB * B2 - rBr * B3;
+  const T srr = c * B2 + dr * B3 - trB * B3 + rBr * B4;
   S.phi += c * B0 + dr * B1 - trB * B1 + rBr * B2;
   S.gx += sI * rx + B1 * dx + 2.f * B2 * Brx;
   S.gy += sI * ry + B1 * dy + 2.f * B2 * Bry;
   S.gz += sI * rz + B1 * dz + 2.f * B2 * Brz;
-  S.hxx += sI + srr * rx * rx - 2.f * B2 * dx * rx - 4.f * B3 * Brx * rx + 2.f * B2 * Bm.xx;
-  S.hyy += sI + srr * ry * ry - 2.f * B2 * dy * ry - 4.f * B3 * Bry * ry + 2.f * B2 * Bm.yy;
-  S.hzz += sI + srr * rz * rz - 2.f * B2 * dz * rz - 4.f * B3 * Brz * rz + 2.f * B2 * Bm.zz;
-  S.hxy += srr * rx * ry - B2 * (dx * ry + rx * dy) - 2.f * B3 * (Brx * ry + rx * Bry) + 2.f * B2 * Bm.xy;
-  S.hxz += srr * rx * rz - B2 * (dx * rz + rx * dz) - 2.f * B3 * (Brx * rz + rx * Brz) + 2.f * B2 * Bm.xz;
-  S.hyz += srr * ry * rz - B2 * (dy * rz + ry * dz) - 2.f * B3 * (Bry * rz + ry * Brz) + 2.f * B2 * Bm.yz;
+  S.hxx += sI + srr * rx * rx - 2.f * B2 * dx * rx - 4.f * B3 * Brx * rx + 2.f * Bm.xx * B2;
+  S.hyy += sI + srr * ry * ry - 2.f * B2 * dy * ry - 4.f * B3 * Bry * ry + 2.f * Bm.yy * B2;
+  S.hzz += sI + srr * rz * rz - 2.f * B2 * dz * rz - 4.f * B3 * Brz * rz + 2.f * Bm.zz * B2;
+  S.hxy += srr * rx * ry - B2 * (dx * ry + rx * dy) - 2.f * B3 * (Brx * ry + rx * Bry) + 2.f * Bm.xy * B2;
+  S.hxz += srr * rx * rz - B2 * (dx * rz + rx * dz) - 2.f * B3 * (Brx * rz + rx * Brz) + 2.f * Bm.xz * B2;
+  S.hyz += srr * ry * rz - B2 * (dy * rz + ry * dz) - 2.f * B3 * (Bry * rz + ry * Brz) + 2.f * Bm.yz * B2;
   // A : grad^3 phi
   const float AB = A.xx * Bm.xx + A.yy * Bm.yy + A.zz * Bm.zz + 2.f * (A.xy * Bm.xy + A.xz * Bm.xz + A.yz * Bm.yz);
-  const float Ard = Arx * dx + Ary * dy + Arz * dz;
-  const float ArBr = Arx * Brx + Ary * Bry + Arz * Brz;
-  float Adx, Ady, Adz, BArx, BAry, BArz, ABrx, ABry, ABrz;
+  const T Ard = Arx * dx + Ary * dy + Arz * dz;
+  const T ArBr = Arx * Brx + Ary * Bry + Arz * Brz;
+  T Adx, Ady, Adz, BArx, BAry, BArz, ABrx, ABry, ABrz;
   mul(A, dx, dy, dz, Adx, Ady, Adz);
   mul(Bm, Arx, Ary, Arz, BArx, BAry, BArz);
   mul(A, Brx, Bry, Brz, ABrx, ABry, ABrz);
-  const float s_r = c * trA * B2 - c * rAr * B3 + trA * dr * B3 + 2.f * Ard * B3 - rAr * dr * B4 -
-                    (trA * trB + 2.f * AB) * B3 + (trA * rBr + trB * rAr + 4.f * ArBr) * B4 - rAr * rBr * B5;
-  const float s_Ar = 2.f * c * B2 + 2.f * dr * B3 - 2.f * trB * B3 + 2.f * rBr * B4;
-  const float s_Br = -2.f * trA * B3 + 2.f * rAr * B4;
-  const float s_d = -trA * B2 + rAr * B3;
+  const T s_r = trA * (c * B2) - c * rAr * B3 + trA * (dr * B3) + 2.f * (Ard * B3) - rAr * dr * B4 -
+                (trA * trB + 2.f * AB) * B3 + (trA * rBr + trB * rAr + 4.f * ArBr) * B4 - rAr * rBr * B5;
+  const T s_Ar = 2.f * (c * B2) + 2.f * (dr * B3) - (2.f * trB) * B3 + 2.f * (rBr * B4);
+  const T s_Br = -(2.f * trA) * B3 + 2.f * (rAr * B4);
+  const T s_d = -trA * B2 + rAr * B3;
   S.tx += s_r * rx + s_Ar * Arx + s_Br * Brx + s_d * dx - 2.f * B2 * Adx - 4.f * B3 * (BArx + ABrx);
   S.ty += s_r * ry + s_Ar * Ary + s_Br * Bry + s_d * dy - 2.f * B2 * Ady - 4.f * B3 * (BAry + ABry);
   S.tz += s_r * rz + s_Ar * Arz + s_Br * Brz + s_d * dz - 2.f * B2 * Adz - 4.f * B3 * (BArz + ABrz);
+}
+
+// forward call: the source's charge and dipole from the pair records
+__device__ __forceinline__ void quad_pair(const QuadPairArgs& a, const Sym& A, float trA, int j, float rx, float ry,
+                                          float rz, QuadAcc<float>& S) {
+  const float4 mj = a.pr.mu[j];
+  quad_pair<float>(a, A, trA, j, rx, ry, rz, mj.w, mj.x, mj.y, mj.z, S);
 }
 
 __device__ __forceinline__ float warp_sum_f(float v) {
@@ -166,7 +178,7 @@ __global__ void __launch_bounds__(kQuadThreads) k_pair_quad(QuadPairArgs a) {
   const int kx = g.kimg[0], ky = g.kimg[1], kz = g.kimg[2];
   const int ncx = g.ncell[0], ncy = g.ncell[1], ncz = g.ncell[2];
   const bool zrun = ncz >= 2 * kz + 1;
-  QuadAcc S;
+  QuadAcc<float> S;
   int nh = 0;   // hits in the list (the same in every lane)
   unsigned* cand = s_cand[wid];
   const int nzs = zrun ? 1 : 2 * kz + 1;
@@ -300,7 +312,7 @@ __global__ void __launch_bounds__(kQuadThreads) k_pair_quad_listed(QuadPairArgs 
   const int4 ci = a.pr.idx[i];
   const Sym A = load_sym(a.theta + size_t(ci.w) * 6);
   const float trA = A.xx + A.yy + A.zz;
-  QuadAcc S;
+  QuadAcc<float> S;
   const int c = a.list_cnt[i];
   const float4* li = a.list + size_t(i) * a.list_cap;
   for (int k = lane; k < c; k += 32) {
@@ -320,6 +332,54 @@ __global__ void __launch_bounds__(kQuadThreads) k_pair_quad_listed(QuadPairArgs 
     qo[5] = v[11];
     qo[6] = v[12];
   }
+}
+
+// Tangent of the per-ion pair sums along (dr, dq, dmu) (the quadrupole Hessian-vector
+// product): the list-driven evaluation in dual numbers. For hit (j, r = r_i - r_j + n) the
+// displacement's tangent is dr_i - dr_j and the source's charge and dipole carry dq_j and
+// dmu_j = d'_j - q_j dr_j (the pair records hold d' = dmu + q dr). Output in caller order:
+// out[26] = the 13 sums (phi, grad phi, grad^2 phi, A : grad^3 phi) and their 13 tangents.
+// Needs the hit lists (runs when *flag == 0; the caller reports a lost list otherwise).
+template <bool BATCH>
+__global__ void __launch_bounds__(kQuadThreads) k_pair_quad_dual(QuadPairArgs a) {
+  if (*a.flag != 0) return;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kWarps + wid;
+  if (i >= a.n) return;   // warp-uniform
+  const int4 ci = a.pr.idx[i];
+  const Sym A = load_sym(a.theta + size_t(ci.w) * 6);
+  const float trA = A.xx + A.yy + A.zz;
+  const float4 dri = a.pr.dr[i];
+  QuadAcc<Dual> S;
+  const int c = a.list_cnt[i];
+  const float4* li = a.list + size_t(i) * a.list_cap;
+  for (int k = lane; k < c; k += 32) {
+    if (!index_ok(k, a.list_cap)) break;
+    const float4 h = li[k];
+    const int j = __float_as_int(h.w);
+    if (!index_ok(j, a.n)) continue;
+    const float4 mj = a.pr.mu[j], tj = a.pr.tq[j], drj = a.pr.dr[j];
+    const Dual rx(h.x, dri.x - drj.x), ry(h.y, dri.y - drj.y), rz(h.z, dri.z - drj.z);
+    const Dual cj(mj.w, tj.x);
+    const Dual dx(mj.x, tj.y - mj.w * drj.x), dy(mj.y, tj.z - mj.w * drj.y), dz(mj.z, tj.w - mj.w * drj.z);
+    quad_pair<Dual>(a, A, trA, j, rx, ry, rz, cj, dx, dy, dz, S);
+  }
+  const Dual v[13] = {S.phi, S.gx, S.gy, S.gz, S.hxx, S.hyy, S.hzz, S.hxy, S.hxz, S.hyz, S.tx, S.ty, S.tz};
+  float o[26];
+#pragma unroll
+  for (int k = 0; k < 13; ++k) {
+    o[k] = warp_sum_f(v[k].v);
+    o[13 + k] = warp_sum_f(v[k].d);
+  }
+  if (lane == 0) {
+    float* out = a.out + size_t(ci.w) * 26;
+#pragma unroll
+    for (int k = 0; k < 26; ++k) out[k] = o[k];
+  }
+}
+
+__global__ void k_flag_if_set(const int* cond, int* flags, int bit) {
+  if (threadIdx.x == 0 && *cond != 0) atomicOr(flags, bit);
 }
 
 QuadPairArgs quad_args(pme_plan_t p, int n, const float* theta, float* out, float* qout, const int* flag) {
@@ -353,6 +413,21 @@ int launch_pair_quad_listed(pme_plan_t p, cudaStream_t s, int n, const float* th
   else k_pair_quad_listed<false><<<grid, kQuadThreads, 0, s>>>(a);
   count_launch();
   return check_launch(p, "k_pair_quad_listed");
+}
+
+int launch_pair_quad_dual(pme_plan_t p, cudaStream_t s, int n, const float* theta, float* out, const int* flag) {
+  if (n <= 0) return PME_OK;
+  const QuadPairArgs a = quad_args(p, n, theta, out, nullptr, flag);
+  const int grid = (n + kWarps - 1) / kWarps;
+  if (p->batch) k_pair_quad_dual<true><<<grid, kQuadThreads, 0, s>>>(a);
+  else k_pair_quad_dual<false><<<grid, kQuadThreads, 0, s>>>(a);
+  count_launch();
+  int st = check_launch(p, "k_pair_quad_dual");
+  if (st) return st;
+  // an overflowed list leaves the pair part out: flag it for pme_sync_status
+  k_flag_if_set<<<1, 32, 0, s>>>(flag, p->flags, kFlagQuadLost);
+  count_launch();
+  return check_launch(p, "k_flag_if_set");
 }
 
 int launch_pair_quad(pme_plan_t p, cudaStream_t s, int n, const float* theta, float* out, float* qout,

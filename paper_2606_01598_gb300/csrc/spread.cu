@@ -71,6 +71,10 @@ int launch_spread_quad(pme_plan_t p, cudaStream_t s, const float* theta, float* 
   return dispatch(p, s, 2, mesh, nullptr, theta);
 }
 
+int launch_spread_quad_tangent(pme_plan_t p, cudaStream_t s, const float* theta, float* mesh) {
+  return dispatch(p, s, 3, mesh, nullptr, theta);
+}
+
 GBPME_BOUNDS_READER(bounds_hit_spread)
 
 }  // namespace gbpme

@@ -39,7 +39,9 @@ struct SpreadArgs {
   const int* keep_rho;
 };
 
-// Shared-memory record of one staged ion (floats), DW = weight-derivative orders kept:
+// Shared-memory record of one staged ion (floats), DW = weight-derivative orders kept
+// (quadrupole tangent mode: orders 0..3, the x table holding per column the ten sums
+// u_(ny,nz) = sum_nx C_(nx,ny,nz) W_x^(nx) for ny + nz <= 3, the y table W_y^(0..3)):
 //   [ZOFF, ...)  z windows: for segment g and order d, 8 floats at ZOFF + g ZSEG + 8 d (ZSEG
 //                = 8 DW, plus 4 in the forward record: the four segments of one ion start in
 //                different banks)
@@ -52,25 +54,33 @@ struct SpreadArgs {
 //   [YOFF, ...)  per brick row Y, the y weights wy0, wy1 (and wy2), NYV floats
 // The stride is a multiple of 4 with an odd quotient, so 16-byte reads of different ions
 // spread over the banks.
-template <class SH, bool TAN>
+template <class SH, int RK>
 struct Rec {
   static constexpr int BX = SH::BX, BY = SH::BY, NSEG = SH::NSEG;
-  static constexpr int DW = TAN ? 3 : 2;
+  static constexpr bool TAN = RK != 0;
+  static constexpr int DW = RK == 0 ? 2 : (RK == 1 ? 3 : 4);
   static constexpr int ZOFF = 0;
-  static constexpr int ZSEG = DW * ZS + (TAN ? 0 : 4);   // 64 B apart would share banks
+  static constexpr int ZSEG = DW * ZS + (RK == 0 ? 4 : 0);   // 64 B apart would share banks
   static constexpr int XOFF = NSEG * ZSEG;
-  static constexpr int NXV = TAN ? 9 : 4;
+  static constexpr int NXV = RK == 0 ? 4 : (RK == 1 ? 9 : 10);
   static constexpr int YOFF = XOFF + BX * NXV;
-  static constexpr int NYV = TAN ? 3 : 2;
+  static constexpr int NYV = DW;
   static constexpr int LEN = YOFF + BY * NYV;
   static constexpr int STR = ((LEN + 3) / 4) % 2 == 0 ? (LEN + 3) / 4 * 4 + 4 : (LEN + 3) / 4 * 4;
 };
 
-template <class SH, int P, bool TAN>
-constexpr int spread_smem_bytes() {
-  return SH::CAP * Rec<SH, TAN>::STR * 4 + SH::SL * (4 + 8);
+// record kind of a mode: 0 forward (orders <= 1), 1 tangent / quadrupole forward (<= 2),
+// 2 quadrupole tangent (<= 3)
+template <int MODE>
+__host__ __device__ constexpr int rec_kind() {
+  return MODE == 0 ? 0 : (MODE == 3 ? 2 : 1);
 }
-static_assert(spread_smem_bytes<Shape<16, 16, 16>, 7, true>() <= 200 * 1024, "staging fits in shared memory");
+
+template <class SH, int P, int RK>
+constexpr int spread_smem_bytes() {
+  return SH::CAP * Rec<SH, RK>::STR * 4 + SH::SL * (4 + 8);
+}
+static_assert(spread_smem_bytes<Shape<16, 16, 16>, 7, 2>() <= 200 * 1024, "staging fits in shared memory");
 
 // distance from a to b going up the periodic axis of length n (a, b in [0, n))
 __device__ __forceinline__ int up_dist(int a, int b, int n) {
@@ -78,13 +88,13 @@ __device__ __forceinline__ int up_dist(int a, int b, int n) {
   return d < 0 ? d + n : d;
 }
 
-// MODE: 0 forward, 1 tangent, 2 quadrupole forward
+// MODE: 0 forward, 1 tangent, 2 quadrupole forward, 3 quadrupole tangent (d rho only)
 template <class SH, int P, int MODE, bool BATCH>
 __global__ void __launch_bounds__(SH::NT) k_spread(SpreadArgs a) {
   constexpr int BX = SH::BX, BY = SH::BY, BZ = SH::BZ, NSEG = SH::NSEG, NT = SH::NT, CAP = SH::CAP,
                 NW = SH::NW, SL = SH::SL;
-  constexpr bool TAN = MODE != 0;   // record layout with second derivatives
-  using RC = Rec<SH, TAN>;
+  constexpr bool TAN = MODE != 0;   // a second accumulator (d rho, or rho of the quadrupole modes)
+  using RC = Rec<SH, rec_kind<MODE>()>;
   constexpr int DW = RC::DW;                      // weight derivative orders kept
 
   extern __shared__ __align__(16) float dyn[];
@@ -214,6 +224,54 @@ __global__ void __launch_bounds__(SH::NT) k_spread(SpreadArgs a) {
         float c4 = 0.f, c5 = 0.f, c6 = 0.f, c7 = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
         // quadrupole mode: Theta' = D^T Theta D (mesh coordinates) as xx, 2 xy, yy, 2 xz, 2 yz, zz
         float t_xx = 0.f, t_xy = 0.f, t_yy = 0.f, t_xz = 0.f, t_yz = 0.f, t_zz = 0.f;
+        // quadrupole tangent mode: coefficients C_(nx,ny,nz) of d rho (mesh coordinates)
+        float C[4][4][4];
+        if (MODE == 3) {
+#pragma unroll
+          for (int i0 = 0; i0 < 4; ++i0)
+#pragma unroll
+            for (int i1 = 0; i1 < 4; ++i1)
+#pragma unroll
+              for (int i2 = 0; i2 < 4; ++i2) C[i0][i1][i2] = 0.f;
+          const float4 tq = a.mr.tq[src];
+          const float4 tt = a.mr.tt[src];
+          const float t0 = tt.x, t1 = tt.y, t2 = tt.z;
+          const float* th = a.theta + size_t(a.mr.idx[src].w) * 6;
+          const float T[3][3] = {{th[0], th[3], th[4]}, {th[3], th[1], th[5]}, {th[4], th[5], th[2]}};
+          const float* D = F.g.D;
+          float TD[3][3], Tp[3][3];
+#pragma unroll
+          for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              TD[r][c] = T[r][0] * D[0 * 3 + c] + T[r][1] * D[1 * 3 + c] + T[r][2] * D[2 * 3 + c];
+#pragma unroll
+          for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              Tp[r][c] = D[0 * 3 + r] * TD[0][c] + D[1 * 3 + r] * TD[1][c] + D[2 * 3 + r] * TD[2][c];
+          // dq W + d' . grad W + (mu' . grad)(t . grad) W + (Theta' : grad grad)(t . grad) W
+          C[0][0][0] = tq.x;
+          C[1][0][0] = tq.y;
+          C[0][1][0] = tq.z;
+          C[0][0][1] = tq.w;
+          C[2][0][0] = mx * t0;
+          C[0][2][0] = my * t1;
+          C[0][0][2] = mz * t2;
+          C[1][1][0] = mx * t1 + my * t0;
+          C[1][0][1] = mx * t2 + mz * t0;
+          C[0][1][1] = my * t2 + mz * t1;
+          C[3][0][0] = Tp[0][0] * t0;
+          C[0][3][0] = Tp[1][1] * t1;
+          C[0][0][3] = Tp[2][2] * t2;
+          C[2][1][0] = Tp[0][0] * t1 + 2.f * Tp[0][1] * t0;
+          C[2][0][1] = Tp[0][0] * t2 + 2.f * Tp[0][2] * t0;
+          C[1][2][0] = Tp[1][1] * t0 + 2.f * Tp[0][1] * t1;
+          C[0][2][1] = Tp[1][1] * t2 + 2.f * Tp[1][2] * t1;
+          C[1][0][2] = Tp[2][2] * t0 + 2.f * Tp[0][2] * t2;
+          C[0][1][2] = Tp[2][2] * t1 + 2.f * Tp[1][2] * t2;
+          C[1][1][1] = 2.f * (Tp[0][1] * t2 + Tp[0][2] * t1 + Tp[1][2] * t0);
+        }
         if (MODE == 2) {
           const float* th = a.theta + size_t(a.mr.idx[src].w) * 6;
           const float T[3][3] = {{th[0], th[3], th[4]}, {th[3], th[1], th[5]}, {th[4], th[5], th[2]}};
@@ -259,7 +317,20 @@ __global__ void __launch_bounds__(SH::NT) k_spread(SpreadArgs a) {
           if (X < BX) {
             const float w0 = w[0][j], w1 = w[1][j];
             float* e = rec + RC::XOFF + X * RC::NXV;
-            if (MODE == 2) {
+            if (MODE == 3) {
+              // u_(ny,nz) = sum_nx C_(nx,ny,nz) W_x^(nx), order (ny,nz): 00 10 01 20 11 02 30 21 12 03
+              const float w2 = w[2][j], w3 = w[DW - 1][j];
+              e[0] = C[0][0][0] * w0 + C[1][0][0] * w1 + C[2][0][0] * w2 + C[3][0][0] * w3;
+              e[1] = C[0][1][0] * w0 + C[1][1][0] * w1 + C[2][1][0] * w2;
+              e[2] = C[0][0][1] * w0 + C[1][0][1] * w1 + C[2][0][1] * w2;
+              e[3] = C[0][2][0] * w0 + C[1][2][0] * w1;
+              e[4] = C[0][1][1] * w0 + C[1][1][1] * w1;
+              e[5] = C[0][0][2] * w0 + C[1][0][2] * w1;
+              e[6] = C[0][3][0] * w0;
+              e[7] = C[0][2][1] * w0;
+              e[8] = C[0][1][2] * w0;
+              e[9] = C[0][0][3] * w0;
+            } else if (MODE == 2) {
               const float w2 = w[DW - 1][j];
               e[0] = c4 * w0 + c5 * w1 + t_xx * w2;
               e[1] = c6 * w0 + t_xy * w1;
@@ -365,7 +436,22 @@ __global__ void __launch_bounds__(SH::NT) k_spread(SpreadArgs a) {
           bits &= bits - 1;
           const float* rec = sw + t * RC::STR;
           const float4* wz = reinterpret_cast<const float4*>(rec + zo);
-          if (TAN) {
+          if (MODE == 3) {
+            const float* xe = rec + xo;
+            const float4 ye = *reinterpret_cast<const float4*>(rec + yo);
+            const float A0 = xe[0] * ye.x + xe[1] * ye.y + xe[3] * ye.z + xe[6] * ye.w;
+            const float A1 = xe[2] * ye.x + xe[4] * ye.y + xe[7] * ye.z;
+            const float A2 = xe[5] * ye.x + xe[8] * ye.y;
+            const float A3 = xe[9] * ye.x;
+#pragma unroll
+            for (int z = 0; z < ZS; z += 4) {
+              const float4 w0 = wz[z / 4], w1 = wz[2 + z / 4], w2 = wz[4 + z / 4], w3 = wz[6 + z / 4];
+              dacc[z] += A0 * w0.x + A1 * w1.x + A2 * w2.x + A3 * w3.x;
+              dacc[z + 1] += A0 * w0.y + A1 * w1.y + A2 * w2.y + A3 * w3.y;
+              dacc[z + 2] += A0 * w0.z + A1 * w1.z + A2 * w2.z + A3 * w3.z;
+              dacc[z + 3] += A0 * w0.w + A1 * w1.w + A2 * w2.w + A3 * w3.w;
+            }
+          } else if (TAN) {
             const float* xe = rec + xo;
             const float* ye = rec + yo;
             const float wy0 = ye[0], wy1 = ye[1], wy2 = ye[2];
@@ -419,7 +505,7 @@ __global__ void __launch_bounds__(SH::NT) k_spread(SpreadArgs a) {
 // One instantiation's launch; the first use on a device raises its dynamic shared-memory limit.
 template <class SH, int P, int MODE, bool BATCH>
 int launch_order(pme_plan_t p, cudaStream_t s, int grid, const SpreadArgs& a) {
-  constexpr int bytes = spread_smem_bytes<SH, P, MODE != 0>();
+  constexpr int bytes = spread_smem_bytes<SH, P, rec_kind<MODE>()>();
   static int done_mask = 0;   // devices 0..31 already configured (idempotent if raced)
   int dev = 0;
   cudaGetDevice(&dev);
@@ -476,10 +562,12 @@ int launch_spread_shape(pme_plan_t p, cudaStream_t s, int mode, float* mesh, con
   if (p->batch) {
     if (mode == 0) return launch_t<SH, 0, true>(p, s, mesh, keep_rho);
     if (mode == 1) return launch_t<SH, 1, true>(p, s, mesh, keep_rho);
+    if (mode == 3) return launch_t<SH, 3, true>(p, s, mesh, nullptr, theta);
     return launch_t<SH, 2, true>(p, s, mesh, nullptr, theta);
   }
   if (mode == 0) return launch_t<SH, 0, false>(p, s, mesh, keep_rho);
   if (mode == 1) return launch_t<SH, 1, false>(p, s, mesh, keep_rho);
+  if (mode == 3) return launch_t<SH, 3, false>(p, s, mesh, nullptr, theta);
   return launch_t<SH, 2, false>(p, s, mesh, nullptr, theta);
 }
 

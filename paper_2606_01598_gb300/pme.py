@@ -359,6 +359,41 @@ class Plan:
                 torch.cuda.current_stream(self.device).synchronize()
         return gp, gq, gm
 
+    def backward_quad(self, pos, q, mu, theta, g_energy=None, g_force=None, g_phi=None, g_field=None):
+        """pme_backward_quad: vector-Jacobian product of (pos, q, mu, theta) -> (E, force, phi,
+        field) of the quadrupole forward. Returns (grad_pos, grad_q, grad_mu, grad_theta [n, 6],
+        the symmetric matrix with dL = G : dTheta)."""
+        return self._backward_quad(pos, q, mu, theta, g_energy, g_force, g_phi, g_field, 1,
+                                   self.lib.pme_backward_quad, True)
+
+    def _backward_quad(self, pos, q, mu, theta, g_energy, g_force, g_phi, g_field, nE, fn, single):
+        dev = pos.device if isinstance(pos, torch.Tensor) else torch.device("cpu")
+        on_dev = dev.type == "cuda"
+        if theta is not None and tuple(theta.shape[-2:]) == (3, 3):
+            t = torch.as_tensor(theta)
+            theta = torch.stack([t[:, 0, 0], t[:, 1, 1], t[:, 2, 2], t[:, 0, 1], t[:, 0, 2], t[:, 1, 2]], 1)
+        pos, q, mu, theta, g_force, g_phi, g_field = (_f32(t, dev) for t in (pos, q, mu, theta, g_force, g_phi,
+                                                                             g_field))
+        if g_energy is not None:
+            g_energy = torch.as_tensor(g_energy, dtype=torch.float64).reshape(nE).to(dev).contiguous()
+        n = int(pos.shape[0])
+        alloc = dict(device=dev, pin_memory=True) if not on_dev else dict(device=dev)
+        gp = torch.empty((n, 3), dtype=torch.float32, **alloc)
+        gq = torch.empty(n, dtype=torch.float32, **alloc)
+        gm = torch.empty((n, 3), dtype=torch.float32, **alloc)
+        gt = torch.empty((n, 6), dtype=torch.float32, **alloc)
+        args = (_ptr(pos), _ptr(q), _ptr(mu), _ptr(theta), _ptr(g_energy), _ptr(g_force), _ptr(g_phi),
+                _ptr(g_field), _ptr(gp), _ptr(gq), _ptr(gm), _ptr(gt))
+        with _on_device(self.device):
+            if single:
+                st = fn(self.handle, _stream_handle(self.device), n, *args)
+            else:
+                st = fn(self.handle, _stream_handle(self.device), *args)
+            self._check(st, "pme_backward_quad" if single else "pme_batch_backward_quad")
+            if not on_dev:
+                torch.cuda.current_stream(self.device).synchronize()
+        return gp, gq, gm, gt
+
     # -- stage-level entry points (device tensors) -------------------------------------------
     def spread(self, pos, q, mu=None):
         pos, q, mu = (_f32(t, self.device) for t in (pos, q, mu))
@@ -541,6 +576,11 @@ class BatchPlan(Plan):
                 torch.cuda.current_stream(self.device).synchronize()
         return gp, gq, gm
 
+    def backward_quad(self, pos, q, mu, theta, g_energy=None, g_force=None, g_phi=None, g_field=None):
+        """pme_batch_backward_quad: as Plan.backward_quad for every frame (g_energy [F])."""
+        return self._backward_quad(pos, q, mu, theta, g_energy, g_force, g_phi, g_field, self.nframes,
+                                   self.lib.pme_batch_backward_quad, False)
+
 
 # ------------------------------------------------------------------------------------------
 # autograd
@@ -584,30 +624,59 @@ class PMEEnergy(torch.autograd.Function):
         return None, g * dEdr, g * dEdq, g * dEdmu
 
 
+_W6 = (1.0, 1.0, 1.0, 2.0, 2.0, 2.0)   # independent entries of a symmetric 3x3: off-diagonals twice
+
+
+class _PMEQuadGrad(torch.autograd.Function):
+    """(pos, q, mu, theta6) -> (dE/dr, dE/dq, dE/dmu, dE/dtheta6); its VJP along cotangents on the
+    first three is the quadrupole Hessian-vector product (pme_backward_quad). A cotangent on
+    dE/dtheta6 (a loss on -dE/dTheta) is not supported and raises."""
+
+    @staticmethod
+    def forward(ctx, plan, pos, q, mu, theta, dEdr, dEdq, dEdmu, dEdt):
+        ctx.plan = plan
+        ctx.save_for_backward(pos, q, mu, theta)
+        return dEdr.clone(), dEdq.clone(), dEdmu.clone(), dEdt.clone()
+
+    @staticmethod
+    def backward(ctx, v_r, v_q, v_mu, v_t):
+        pos, q, mu, theta = ctx.saved_tensors
+        if v_t is not None and bool((v_t != 0).any()):
+            raise RuntimeError("no second derivative through dE/dTheta (pme_backward_quad takes no "
+                               "cotangent on -dE/dTheta)")
+        z = lambda t, like: torch.zeros_like(like) if t is None else t
+        v_r, v_q, v_mu = z(v_r, pos), z(v_q, q), z(v_mu, mu)
+        gp, gq, gm, gt = ctx.plan.backward_quad(pos.detach(), q.detach(), mu.detach(), theta.detach(), None,
+                                                -v_r.detach(), v_q.detach(), -v_mu.detach())
+        w = torch.tensor(_W6, dtype=gt.dtype, device=gt.device)
+        return None, gp, gq, gm, gt * w, None, None, None, None
+
+
 class PMEQuadEnergy(torch.autograd.Function):
     """Total energy with point quadrupoles theta [n, 6] (xx, yy, zz, xy, xz, yz), through
-    pme_forward_quad. Differentiable once: the gradients are -force, phi, -field and, for the
-    six independent entries of theta, -field_grad with the off-diagonal entries doubled (each
-    appears twice in the symmetric tensor). There is no second derivative (no quadrupole
-    backward pass): differentiating the gradients raises."""
+    pme_forward_quad. The gradients are -force, phi, -field and, for the six independent
+    entries of theta, -field_grad with the off-diagonal entries doubled (each appears twice in
+    the symmetric tensor). Twice differentiable through the force, phi and field gradients
+    (pme_backward_quad): a force-matching loss trains the quadrupole channel."""
 
     @staticmethod
     def forward(ctx, plan, pos, q, mu, theta):
         out = plan.forward_quad(pos.detach(), q.detach(), mu.detach(), theta.detach())
-        ctx.save_for_backward(out["force"], out["phi"], out["field"], out["field_grad"])
+        ctx.plan = plan
+        ctx.save_for_backward(pos, q, mu, theta, out["force"], out["phi"], out["field"], out["field_grad"])
         return out["energy"].reshape(())
 
     @staticmethod
-    @torch.autograd.function.once_differentiable
     def backward(ctx, gE):
-        F, phi, field, fg = ctx.saved_tensors
+        pos, q, mu, theta, F, phi, field, fg = ctx.saved_tensors
+        w = torch.tensor(_W6, dtype=fg.dtype, device=fg.device)
+        dEdr, dEdq, dEdmu, dEdt = _PMEQuadGrad.apply(ctx.plan, pos, q, mu, theta, -F, phi, -field, -fg * w)
         g = gE.to(torch.float32)
-        w = torch.tensor([1.0, 1.0, 1.0, 2.0, 2.0, 2.0], dtype=fg.dtype, device=fg.device)
-        return None, -g * F, g * phi, -g * field, -g * fg * w
+        return None, g * dEdr, g * dEdq, g * dEdmu, g * dEdt
 
 
 def pme_quad_energy(plan: Plan, pos, q, mu, theta):
-    """Energy with point quadrupoles (theta [n, 6]); first derivatives only."""
+    """Energy with point quadrupoles (theta [n, 6]); twice differentiable through the forces."""
     if mu is None:
         mu = torch.zeros_like(pos)
     return PMEQuadEnergy.apply(plan, pos, q, mu, theta)

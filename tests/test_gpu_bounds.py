@@ -23,7 +23,11 @@ def test_parity_cases_under_index_checks(root, tmp_path):
     r = subprocess.run([sys.executable, "-c", "import __graft_entry__ as g; g.build()"], cwd=root, env=env,
                        capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stderr[-2000:]
-    r = subprocess.run([sys.executable, "-m", "pytest", *FILES, "-m", "gpu", "-q", "-x", "-p", "no:cacheprovider"],
+    # tests that assert bitwise equality between two different kernels (hit-list vs cell-walk
+    # pair term) are left out: the index checks change the code the compiler generates for one
+    # of them, so their rounding may differ in the last bit under this build
+    r = subprocess.run([sys.executable, "-m", "pytest", *FILES, "-m", "gpu", "-q", "-x", "-p", "no:cacheprovider",
+                        "-k", "not bitwise"],
                        cwd=root, env=env, capture_output=True, text=True, timeout=1800)
     tail = (r.stdout + r.stderr)[-3000:]
     print(tail)

@@ -15,7 +15,7 @@ import torch
 import workloads as W
 from oracle import pme as O2
 
-from gpu_util import TOL_E, TOL_F, TOL_HVP, TOL_MESH, check_energy, f32, prepared, relmax, relrmse, sym6
+from gpu_util import TOL_E, TOL_F, TOL_HVP, TOL_MESH, check, check_energy, f32, prepared, relmax, relrmse, sym6
 
 pytestmark = pytest.mark.gpu
 
@@ -66,6 +66,25 @@ def test_32k_backward_matches_double_backward(gb, frame32k):
     ref = o.hvp(pos, q, mu, 0.5, gF, gphi, gfield)
     for g_, r_ in zip(got, ref):
         assert relrmse(g_.cpu().numpy(), r_) < TOL_HVP
+    plan.close()
+
+
+def test_32k_quad_backward_matches_double_backward(gb, frame32k):
+    # the quadrupole backward (pme_backward_quad) at the benchmark configuration, point
+    # quadrupoles sigma 0.1 e A^2, against the oracle's double backward with quadrupoles
+    fr, cfg = frame32k
+    pos, q, mu = prepared(fr)
+    th = f32(W.quadrupoles(fr.n, 0.1, seed=300))
+    th6 = sym6(th)
+    gF, gphi, gfield = (f32(x) for x in W.tangent(fr.n, seed=99))
+    plan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=fr.n)
+    got = plan.backward_quad(_c(pos), _c(q), _c(mu), _c(th6), torch.tensor([0.5], dtype=torch.float64, device="cuda"),
+                             _c(gF), _c(gphi), _c(gfield))
+    plan.sync_status()
+    ref = O2.PMEOracle(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"]).hvp_quad(
+        pos, q, mu, th, 0.5, gF, gphi, gfield)
+    for g_, r_, nm in zip(got, (ref[0], ref[1], ref[2], sym6(ref[3])), ("pos", "q", "mu", "theta")):
+        check(f"32k hvp_quad {nm} (rel RMSE)", relrmse(g_.cpu().numpy(), r_), TOL_HVP)
     plan.close()
 
 

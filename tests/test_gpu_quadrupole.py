@@ -9,7 +9,7 @@ import workloads as W
 from oracle import pme as O2
 from oracle import quadrupole as O1Q
 
-from gpu_util import TOL_E, TOL_F, check, check_energy, f32, prepared, relrmse, sym6
+from gpu_util import TOL_E, TOL_F, TOL_HVP, check, check_energy, f32, prepared, relrmse, sym6
 
 pytestmark = pytest.mark.gpu
 
@@ -213,9 +213,106 @@ def test_quad_energy_autograd(gb):
     fd = (ep - em) / (2 * h)
     ad = float((gth.double() * d.double()).sum())
     assert abs(fd - ad) < 1e-3 * abs(ad) + 2e-5 * abs(E.item()) / h
+    # twice differentiable through the forces: a force-matching loss L = sum (F - F0) . w
+    # differentiated by autograd equals the oracle's double backward
+    F0 = np.float32(np.random.default_rng(3).normal(size=(len(pos), 3)))
+    E = gb.pme_quad_energy(plan, *t)
+    (gp1,) = torch.autograd.grad(E, t[0], create_graph=True)
+    L = ((-gp1 - torch.tensor(F0, device="cuda")) ** 2).sum()
+    gg = torch.autograd.grad(L, t)
+    ref = O2.PMEOracle(fr.box, mesh, p, a, rc).hvp_quad(pos, q, mu, th, 0.0,
+                                                        2 * ((-gp1).detach().double().cpu().numpy() - F0),
+                                                        np.zeros(len(pos)), np.zeros((len(pos), 3)))
+    w6 = np.array([1.0, 1.0, 1.0, 2.0, 2.0, 2.0])
+    for g_, r_, nm in zip(gg, (ref[0], ref[1], ref[2], sym6(ref[3]) * w6), ("pos", "q", "mu", "theta")):
+        check(f"double backward {nm} (rel RMSE)", relrmse(g_.cpu().numpy(), r_), TOL_HVP)
+    # a loss on -dE/dTheta has no second derivative here
     with pytest.raises(RuntimeError):
-        gg = torch.autograd.grad(gb.pme_quad_energy(plan, *t), t[0], create_graph=True)[0]
-        torch.autograd.grad(gg.sum(), t[0])
+        gt1 = torch.autograd.grad(gb.pme_quad_energy(plan, *t), t[3], create_graph=True)[0]
+        torch.autograd.grad((gt1 ** 2).sum(), t[0])
+
+
+QB_CASES = ["rocksalt512", "nacl4096", "nacl64", "nacl1000_ragged"]
+
+
+@pytest.mark.parametrize("name", QB_CASES)
+def test_quad_backward_matches_oracle(gb, name):
+    # pme_backward_quad: g_E dE + H v in (r, q, mu, Theta) against the oracle's double backward
+    fr, mesh, p, a, rc, pos, q, mu, th = _inputs(name)
+    plan = gb.Plan(fr.box, mesh, p, a, rc, max_ions=max(1024, len(q)))
+    gF, gphi, gfield = (f32(x) for x in W.tangent(fr.n, seed=17))
+    c = lambda x: torch.tensor(np.float32(x), device="cuda")
+    got = plan.backward_quad(c(pos), c(q), c(mu), c(sym6(th)), torch.tensor([0.6], dtype=torch.float64, device="cuda"),
+                             c(gF), c(gphi), c(gfield))
+    plan.sync_status()
+    ref = O2.PMEOracle(fr.box, mesh, p, a, rc).hvp_quad(pos, q, mu, th, 0.6, gF, gphi, gfield)
+    for g_, r_, nm in zip(got, (ref[0], ref[1], ref[2], sym6(ref[3])), ("pos", "q", "mu", "theta")):
+        check(f"hvp_quad {nm} (rel RMSE)", relrmse(g_.cpu().numpy(), r_), TOL_HVP)
+    plan.close()
+
+
+def test_quad_backward_options_triclinic_and_batch(gb):
+    c = lambda x: torch.tensor(np.float32(x), device="cuda")
+    # options: no pair term, eV units, no self / background
+    fr, mesh, p, a, rc, pos, q, mu, th = _inputs("nacl1000_ragged")
+    gF, gphi, gfield = (f32(x) for x in W.tangent(fr.n, seed=19))
+    for kw in (dict(include_pair=False), dict(coulomb_k=14.3996454784),
+               dict(include_self=False, include_background=False)):
+        plan = gb.Plan(fr.box, mesh, p, a, rc, max_ions=1024, **kw)
+        got = plan.backward_quad(c(pos), c(q), c(mu), c(sym6(th)), torch.tensor([0.3], dtype=torch.float64,
+                                                                              device="cuda"),
+                                 c(gF), c(gphi), c(gfield))
+        ref = O2.PMEOracle(fr.box, mesh, p, a, rc, **kw).hvp_quad(pos, q, mu, th, 0.3, gF, gphi, gfield)
+        for g_, r_, nm in zip(got, (ref[0], ref[1], ref[2], sym6(ref[3])), ("pos", "q", "mu", "theta")):
+            check(f"hvp_quad {kw} {nm}", relrmse(g_.cpu().numpy(), r_), TOL_HVP)
+        plan.close()
+    # triclinic cell
+    box = np.array([[26.0, 0.0, 0.0], [3.0, 25.0, 0.0], [-2.0, 1.5, 27.0]])
+    rng = np.random.default_rng(4)
+    f2 = W.molten_nacl(512, seed=9)
+    p2 = f32(rng.uniform(size=(512, 3)) @ box)
+    _, q2, m2 = prepared(f2)
+    t2 = f32(W.quadrupoles(512, 0.1, seed=31))
+    g2 = [f32(x) for x in W.tangent(512, seed=21)]
+    plan = gb.Plan(box, (24, 24, 25), 6, 0.35, 6.0, max_ions=1024)
+    got = plan.backward_quad(c(p2), c(q2), c(m2), c(sym6(t2)), torch.tensor([0.2], dtype=torch.float64, device="cuda"),
+                             *[c(x) for x in g2])
+    ref = O2.PMEOracle(box, (24, 24, 25), 6, 0.35, 6.0).hvp_quad(p2, q2, m2, t2, 0.2, *g2)
+    for g_, r_, nm in zip(got, (ref[0], ref[1], ref[2], sym6(ref[3])), ("pos", "q", "mu", "theta")):
+        check(f"hvp_quad triclinic {nm}", relrmse(g_.cpu().numpy(), r_), TOL_HVP)
+    plan.close()
+    # an uneven batch (orders 4 and 6) against single-frame plans and the oracle
+    specs = W.uneven_frames(n_frames=5, seed=1007)
+    frames = [sp.frame for sp in specs]
+    meshes = [gb.mesh_dims(f_.box, sp.spacing, rule=1, strategy=1, clamp=(16, 48)) for f_, sp in zip(frames, specs)]
+    orders = [sp.order for sp in specs]
+    offsets = np.concatenate([[0], np.cumsum([f_.n for f_ in frames])]).astype(np.int64)
+    P = np.concatenate([f32(f_.pos) for f_ in frames])
+    Qv = np.concatenate([f32(f_.q) for f_ in frames])
+    MU = np.concatenate([f32(f_.mu) for f_ in frames])
+    TH = f32(W.quadrupoles(len(Qv), 0.1, seed=45))
+    gFb, gpb, gfb = (f32(x) for x in W.tangent(len(Qv), seed=23))
+    gE = np.linspace(0.1, 0.5, len(frames))
+    bp = gb.BatchPlan([f_.box for f_ in frames], meshes, orders, offsets, 0.30, 9.0)
+    got = bp.backward_quad(c(P), c(Qv), c(MU), c(sym6(TH)), torch.tensor(gE, device="cuda"), c(gFb), c(gpb), c(gfb))
+    bp.sync_status()
+    for f, f_ in enumerate(frames):
+        lo, hi = offsets[f], offsets[f + 1]
+        ref = O2.PMEOracle(f_.box, meshes[f], orders[f], 0.30, 9.0).hvp_quad(
+            P[lo:hi], Qv[lo:hi], MU[lo:hi], TH[lo:hi], gE[f], gFb[lo:hi], gpb[lo:hi], gfb[lo:hi])
+        for g_, r_, nm in zip(got, (ref[0], ref[1], ref[2], sym6(ref[3])), ("pos", "q", "mu", "theta")):
+            check(f"hvp_quad batch frame {f} {nm}", relrmse(g_[lo:hi].cpu().numpy(), r_), TOL_HVP)
+    bp.close()
+
+
+def test_quad_backward_refusals(gb):
+    fr, mesh, p, a, rc, pos, q, mu, th = _inputs("nacl64")
+    c = lambda x: torch.tensor(np.float32(x), device="cuda")
+    plan = gb.Plan(fr.box, mesh, 3, a, rc, max_ions=1024)
+    with pytest.raises(gb.PMEError) as e:
+        plan.backward_quad(c(pos), c(q), c(mu), c(sym6(th)), None, c(pos), c(q), c(mu))
+    assert e.value.status == 5
+    plan.close()
 
 
 def test_quad_batch_matches_single_frames(gb):
