@@ -3,7 +3,9 @@
 Each CUDA translation unit under ``csrc/`` is compiled in parallel to an object file under
 ``_build/`` and linked into ``lib/libgbpme.so`` against cuFFT (the only library call on the
 path: the two 3D transforms) with the CUDA runtime linked statically. Up-to-date outputs are
-reused unless ``force`` is set.
+reused unless ``force`` is set. The pair-term unit is compiled without implicit multiply-add
+contraction (its multiply-adds are written out), so that its fused and list-driven kernels
+round identically.
 """
 from __future__ import annotations
 
@@ -20,6 +22,9 @@ BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "lib")
 LIBNAME = "libgbpme.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# per-unit flags: no implicit contraction where two kernels must round the same expressions
+# identically
+UNIT_FLAGS = {"pair.cu": ["-fmad=false"]}
 
 
 def find_nvcc() -> str:
@@ -77,7 +82,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, 
     def compile_one(src: str):
         obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         if force or _stale(obj, [src] + headers):
-            cmd = [nvcc, "-c", src, "-o", obj] + cflags
+            cmd = [nvcc, "-c", src, "-o", obj] + cflags + UNIT_FLAGS.get(os.path.basename(src), [])
             r = subprocess.run(cmd, capture_output=True, text=True)
             if r.returncode != 0:
                 raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

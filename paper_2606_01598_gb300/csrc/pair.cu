@@ -34,6 +34,12 @@
 // of the tangent sources (dq_j, dmu_j + q_j dr_j, mu_j (x) dr_j) up to second derivatives;
 // every term is linear in the per-pair contributions, so each lane folds its pairs straight
 // into the seven outputs before the reduction.
+//
+// Rounding: this file is compiled with -fmad=false, so a multiply and an add fuse only where
+// fmaf_ below says so. The fused and the list-driven kernels inline the same pair expressions
+// into different code; with contraction left to the compiler, the two could round a term
+// differently (the choice depends on the surrounding code), and the two paths would no longer
+// agree bit for bit.
 #include "kernels.h"
 
 namespace gbpme {
@@ -75,7 +81,8 @@ struct V3 {
   float x, y, z;
 };
 __device__ __forceinline__ V3 mk(float x, float y, float z) { return V3{x, y, z}; }
-__device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float fmaf_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float dot(V3 a, V3 b) { return fmaf_(a.x, b.x, fmaf_(a.y, b.y, a.z * b.z)); }
 __device__ __forceinline__ V3 operator+(V3 a, V3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
 __device__ __forceinline__ V3 operator*(float s, V3 a) { return mk(s * a.x, s * a.y, s * a.z); }
 __device__ __forceinline__ void acc(V3& a, V3 b) { a.x += b.x; a.y += b.y; a.z += b.z; }
@@ -121,48 +128,52 @@ __device__ __forceinline__ void interact(const PairArgs& a, const Ion& I, int j,
   const float alpha = a.alpha;
   const float ex = expf(-alpha * alpha * r2);
   const float B0 = erfcf(alpha * rr) * rinv;
-  const float B1 = (B0 + a.c1 * ex) * rinv2;
-  const float B2 = (3.f * B1 + a.c2 * ex) * rinv2;
-  const float B3 = (5.f * B2 + a.c3 * ex) * rinv2;
+  const float B1 = fmaf_(a.c1, ex, B0) * rinv2;
+  const float B2 = fmaf_(a.c2, ex, 3.f * B1) * rinv2;
+  const float B3 = fmaf_(a.c3, ex, 5.f * B2) * rinv2;
   const float4 mj4 = a.pr.mu[j];
   const V3 d = mk(mj4.x, mj4.y, mj4.z);
   const float c = mj4.w;
-  const float dr_ = dot(d, r);
-  const float phi = c * B0 + dr_ * B1;
-  // grad phi = c g1 - g2(d) = -(c B1 + (d.r) B2) r + B1 d
-  const V3 gphi = (-c * B1 - dr_ * B2) * r + B1 * d;
+  const float rd = dot(d, r);
+  const float phi = fmaf_(c, B0, rd * B1);
+  // grad phi = c g1 - g2(d) = -(c B1 + (d.r) B2) r + B1 d = al r + B1 d
+  const float al = -fmaf_(c, B1, rd * B2);
+  const V3 gphi = mk(fmaf_(al, r.x, B1 * d.x), fmaf_(al, r.y, B1 * d.y), fmaf_(al, r.z, B1 * d.z));
+  // s_rr = c B2 + (d.r) B3, the coefficient of r r in grad grad phi
+  const float s_rr = fmaf_(c, B2, rd * B3);
   if constexpr (!TAN) {
     A.phi += phi;
     acc(A.g, gphi);
     // grad grad phi = c (-I B1 + r r B2) - [(I (d.r) + r d + d r) B2 - r r (d.r) B3]
-    const float s_rr = c * B2 + dr_ * B3;
-    const float s_I = -c * B1 - dr_ * B2;
+    //               = al I + s_rr r r - B2 (r d + d r)
+    const V3 u = s_rr * r, b = B2 * d;
     float h[6];
-    h[0] = s_I + s_rr * r.x * r.x - 2.f * B2 * d.x * r.x;
-    h[1] = s_I + s_rr * r.y * r.y - 2.f * B2 * d.y * r.y;
-    h[2] = s_I + s_rr * r.z * r.z - 2.f * B2 * d.z * r.z;
-    h[3] = s_rr * r.x * r.y - B2 * (r.x * d.y + d.x * r.y);
-    h[4] = s_rr * r.x * r.z - B2 * (r.x * d.z + d.x * r.z);
-    h[5] = s_rr * r.y * r.z - B2 * (r.y * d.z + d.y * r.z);
+    h[0] = fmaf_(fmaf_(-2.f, b.x, u.x), r.x, al);
+    h[1] = fmaf_(fmaf_(-2.f, b.y, u.y), r.y, al);
+    h[2] = fmaf_(fmaf_(-2.f, b.z, u.z), r.z, al);
+    h[3] = fmaf_(u.x, r.y, -fmaf_(r.x, b.y, b.x * r.y));
+    h[4] = fmaf_(u.x, r.z, -fmaf_(r.x, b.z, b.x * r.z));
+    h[5] = fmaf_(u.y, r.z, -fmaf_(r.y, b.z, b.y * r.z));
 #pragma unroll
     for (int k = 0; k < 6; ++k) A.h[k] += h[k];
     if (vir) {
       const V3 m = I.mu;
-      const float Fx = -(I.q * gphi.x + h[0] * m.x + h[3] * m.y + h[4] * m.z);
-      const float Fy = -(I.q * gphi.y + h[3] * m.x + h[1] * m.y + h[5] * m.z);
-      const float Fz = -(I.q * gphi.z + h[4] * m.x + h[5] * m.y + h[2] * m.z);
-      vir[0] += 0.5f * Fx * r.x;
-      vir[1] += 0.5f * Fx * r.y;
-      vir[2] += 0.5f * Fx * r.z;
-      vir[3] += 0.5f * Fy * r.x;
-      vir[4] += 0.5f * Fy * r.y;
-      vir[5] += 0.5f * Fy * r.z;
-      vir[6] += 0.5f * Fz * r.x;
-      vir[7] += 0.5f * Fz * r.y;
-      vir[8] += 0.5f * Fz * r.z;
+      const float Fx = -fmaf_(I.q, gphi.x, fmaf_(h[0], m.x, fmaf_(h[3], m.y, h[4] * m.z)));
+      const float Fy = -fmaf_(I.q, gphi.y, fmaf_(h[3], m.x, fmaf_(h[1], m.y, h[5] * m.z)));
+      const float Fz = -fmaf_(I.q, gphi.z, fmaf_(h[4], m.x, fmaf_(h[5], m.y, h[2] * m.z)));
+      const float hx = 0.5f * Fx, hy = 0.5f * Fy, hz = 0.5f * Fz;
+      vir[0] = fmaf_(hx, r.x, vir[0]);
+      vir[1] = fmaf_(hx, r.y, vir[1]);
+      vir[2] = fmaf_(hx, r.z, vir[2]);
+      vir[3] = fmaf_(hy, r.x, vir[3]);
+      vir[4] = fmaf_(hy, r.y, vir[4]);
+      vir[5] = fmaf_(hy, r.z, vir[5]);
+      vir[6] = fmaf_(hz, r.x, vir[6]);
+      vir[7] = fmaf_(hz, r.y, vir[7]);
+      vir[8] = fmaf_(hz, r.z, vir[8]);
     }
   } else {
-    const float B4 = (7.f * B3 + a.c4 * ex) * rinv2;
+    const float B4 = fmaf_(a.c4, ex, 7.f * B3) * rinv2;
     const float4 tj = a.pr.tq[j];
     const float4 drj4 = a.pr.dr[j];
     const float cp = tj.x;                       // tangent charge of j
@@ -172,53 +183,61 @@ __device__ __forceinline__ void interact(const PairArgs& a, const Ion& I, int j,
     // Every term below is a contraction of grad^k psi (k <= 4) with the vectors r, d = mu_j,
     // d', dr_j, mu_i, dr_i, w_i; it is written as a combination of those vectors with scalar
     // coefficients built from their dot products:
-    //   H(u)      = (grad grad phi) u            = alpha u + (ru s_rr - B2 du) r - B2 ru d
+    //   H(u)      = (grad grad phi) u            = al u + (ru s_rr - B2 du) r - B2 ru d
     //   T3        = (grad^3 phi)[mu_i, dr_i]
     //   gdphi     = grad of the potential of the tangent sources (cp, d', mu_j (x) dr_j)
     //   Hdmu      = (grad grad dphi) mu_i
-    // with alpha = -(c B1 + rd B2), s_rr = c B2 + rd B3 (the coefficients of g2 / g3 / g4
+    // with al = -(c B1 + rd B2), s_rr = c B2 + rd B3 (the coefficients of g2 / g3 / g4
     // contractions of the header, expanded).
-    const float rd = dr_, rm = dot(r, m), rt = dot(r, t), rw = dot(r, w);
+    const float rm = dot(r, m), rt = dot(r, t), rw = dot(r, w);
     const float rdp = dot(r, dp), rdj = dot(r, drj);
     const float d_t = dot(d, t), d_w = dot(d, w), d_m = dot(d, m), m_t = dot(m, t);
     const float dp_m = dot(dp, m), dj_m = dot(drj, m), d_dj = dot(d, drj);
-    const float al = -c * B1 - rd * B2;          // gphi = al r + B1 d
-    const float s_rr = c * B2 + rd * B3;
-    const float dphi = cp * B0 + (rdp - d_dj) * B1 + rd * rdj * B2;
-    const float gd_r = -cp * B1 - rdp * B2 + d_dj * B2 - rd * rdj * B3;   // gdphi = gd_r r + B1 d'
-                                                                          //   + B2 rdj d + B2 rd dr_j
+    const float rd_rdj = rd * rdj;
+    // dphi = cp B0 + (rdp - d_dj) B1 + rd rdj B2
+    const float dphi = fmaf_(cp, B0, fmaf_(rdp - d_dj, B1, rd_rdj * B2));
+    // gdphi = gd_r r + B1 d' + B2 rdj d + B2 rd dr_j, gd_r = -cp B1 + (d_dj - rdp) B2 - rd rdj B3;
+    // gd_r is also the coefficient of m in Hdmu
+    const float gd_r = fmaf_(-cp, B1, fmaf_(d_dj - rdp, B2, -(rd_rdj * B3)));
     // T3 on m, t, d, r
-    const float T_m = c * B2 * rt - B2 * d_t + B3 * rd * rt;
-    const float T_t = c * B2 * rm - B2 * d_m + B3 * rd * rm;
-    const float T_d = -B2 * m_t + B3 * rm * rt;
-    const float T_r = c * B2 * m_t - c * rm * rt * B3 + B3 * (d_m * rt + d_t * rm + m_t * rd) - B4 * rd * rm * rt;
-    // Hdmu on m, r, d', d, dr_j
-    const float D_m = -cp * B1 - B2 * rdp + B2 * d_dj - B3 * rd * rdj;
-    const float D_r = cp * rm * B2 - B2 * dp_m + rdp * rm * B3 - B3 * (d_dj * rm + d_m * rdj + dj_m * rd) +
-                      B4 * rd * rdj * rm;
-    const float D_dp = -B2 * rm;
-    const float D_d = B2 * dj_m - B3 * rdj * rm;
-    const float D_dj = B2 * d_m - B3 * rd * rm;
+    const float T_m = fmaf_(s_rr, rt, -(B2 * d_t));
+    const float T_t = fmaf_(s_rr, rm, -(B2 * d_m));
+    const float rm_rt = rm * rt;
+    const float T_d = fmaf_(B3, rm_rt, -(B2 * m_t));
+    // T_r = c B2 m_t + B3 (d_m rt + d_t rm + m_t rd - c rm rt) - B4 rd rm rt
+    const float T_in = fmaf_(d_m, rt, fmaf_(d_t, rm, fmaf_(m_t, rd, -(c * rm_rt))));
+    const float T_r = fmaf_(c * B2, m_t, fmaf_(B3, T_in, -(B4 * rd * rm_rt)));
+    // Hdmu on r, d', d, dr_j:
+    // D_r = B2 (cp rm - dp_m) + B3 ((rdp - d_dj) rm - d_m rdj - dj_m rd) + B4 rd rdj rm
+    const float D_in = fmaf_(rdp - d_dj, rm, -fmaf_(d_m, rdj, dj_m * rd));
+    const float D_r = fmaf_(B2, fmaf_(cp, rm, -dp_m), fmaf_(B3, D_in, B4 * rd_rdj * rm));
+    const float D_dp = -(B2 * rm);
+    const float D_d = fmaf_(B2, dj_m, -(B3 * rdj * rm));
+    const float D_dj = fmaf_(B2, d_m, -(B3 * rd * rm));
     // grad_q = gE phi + dphi + gphi . dr_i
-    A.gq += I.gE * phi + dphi + al * rt + B1 * d_t;
+    A.gq += fmaf_(I.gE, phi, fmaf_(al, rt, fmaf_(B1, d_t, dphi)));
     // grad_mu = gE gphi + gdphi + H(dr_i)
     {
-      const float cr = I.gE * al + gd_r + (rt * s_rr - B2 * d_t);
-      const float cd = I.gE * B1 + B2 * rdj - B2 * rt;
+      const float cr = fmaf_(I.gE, al, gd_r + T_m);
+      const float cd = fmaf_(I.gE, B1, B2 * (rdj - rt));
       const float cdp = B1, cdj = B2 * rd, ct = al;
-      acc(A.gm, cr * r + cd * d + cdp * dp + cdj * drj + ct * t);
+      A.gm.x += fmaf_(cr, r.x, fmaf_(cd, d.x, fmaf_(cdp, dp.x, fmaf_(cdj, drj.x, ct * t.x))));
+      A.gm.y += fmaf_(cr, r.y, fmaf_(cd, d.y, fmaf_(cdp, dp.y, fmaf_(cdj, drj.y, ct * t.y))));
+      A.gm.z += fmaf_(cr, r.z, fmaf_(cd, d.z, fmaf_(cdp, dp.z, fmaf_(cdj, drj.z, ct * t.z))));
     }
     // grad_r = (gE q + dq) gphi + H(w_i) + q gdphi + Hdmu + T3
     {
-      const float k1 = I.gE * I.q + I.dq;
-      const float cr = k1 * al + (rw * s_rr - B2 * d_w) + I.q * gd_r + D_r + T_r;
-      const float cd = k1 * B1 - B2 * rw + I.q * B2 * rdj + D_d + T_d;
+      const float k1 = fmaf_(I.gE, I.q, I.dq);
+      const float cr = fmaf_(k1, al, fmaf_(rw, s_rr, fmaf_(-B2, d_w, fmaf_(I.q, gd_r, D_r + T_r))));
+      const float cd = fmaf_(k1, B1, fmaf_(B2, fmaf_(I.q, rdj, -rw), D_d + T_d));
       const float cw = al;
-      const float cdp = I.q * B1 + D_dp;
-      const float cdj = I.q * B2 * rd + D_dj;
-      const float cm = D_m + T_m;
+      const float cdp = fmaf_(I.q, B1, D_dp);
+      const float cdj = fmaf_(I.q * B2, rd, D_dj);
+      const float cm = gd_r + T_m;
       const float ct = T_t;
-      acc(A.gr, cr * r + cd * d + cw * w + cdp * dp + cdj * drj + cm * m + ct * t);
+      A.gr.x += fmaf_(cr, r.x, fmaf_(cd, d.x, fmaf_(cw, w.x, fmaf_(cdp, dp.x, fmaf_(cdj, drj.x, fmaf_(cm, m.x, ct * t.x))))));
+      A.gr.y += fmaf_(cr, r.y, fmaf_(cd, d.y, fmaf_(cw, w.y, fmaf_(cdp, dp.y, fmaf_(cdj, drj.y, fmaf_(cm, m.y, ct * t.y))))));
+      A.gr.z += fmaf_(cr, r.z, fmaf_(cd, d.z, fmaf_(cw, w.z, fmaf_(cdp, dp.z, fmaf_(cdj, drj.z, fmaf_(cm, m.z, ct * t.z))))));
     }
   }
 }
