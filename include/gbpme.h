@@ -96,14 +96,18 @@ typedef struct {
                               pme_forward_virial reports PME_ERR_UNSUPPORTED */
   int fft;                 /* transforms of the mesh convolution. The library's own apply when
                               every mesh axis of every frame is 2,3,5-smooth and at most 256
-                              long and a mesh plane fits in one block's shared memory.
-                              0 (default): automatic, the library's own for batched plans
-                              whose meshes have no axis above 64 points (one launch per pass
-                              for all frames; faster there on GB300), cuFFT otherwise.
+                              long and a mesh plane fits in one block's shared memory; when
+                              every axis of every frame is 64 or 128 points they run as
+                              power-of-two kernels (compile-time four-step transforms).
+                              0 (default): automatic, the library's own when every frame's
+                              mesh takes the power-of-two kernels, or for batched plans whose
+                              meshes have no axis above 64 points (one launch per pass for
+                              all frames; faster there on GB300), cuFFT otherwise.
                               1: always cuFFT. 2: always the library's own
-                              (PME_ERR_UNSUPPORTED where they do not apply). With the own
-                              transforms the stage timers' "FFT R2C" and "FFT C2R" stages are
-                              the z/y passes and "influence" includes the x transforms */
+                              (PME_ERR_UNSUPPORTED where they do not apply). 3: the library's
+                              own without the power-of-two kernels. With the own transforms
+                              the stage timers' "FFT R2C" and "FFT C2R" stages are the z/y
+                              passes and "influence" includes the x transforms */
   int autotune;            /* 1 (default): with brick {0,0,0}, pme_plan_create times every
                               built brick shape once for this (device, mesh, order, max_ions
                               rounded up to a power of two) on synthetic uniform ions -- the
@@ -139,7 +143,7 @@ int pme_plan_destroy(pme_plan_t plan);
 
 /* Which transforms the plan's mesh convolution uses: *kind = 0 for the library's own
  * (Stockham transforms in shared memory, the x transform fused with the influence multiply),
- * 1 for cuFFT. */
+ * 1 for cuFFT, 2 for the library's own power-of-two kernels (every axis 64 or 128). */
 int pme_plan_fft_kind(pme_plan_t plan, int* kind);
 
 /* The spread brick shape the plan uses (explicit, tuned or default): brick[3] = x, y, z edges. */

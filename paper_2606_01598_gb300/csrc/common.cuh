@@ -212,6 +212,7 @@ struct pme_plan_s {
   gbpme::FFTGroup* fgroups = nullptr;
   // hand-written transforms (every axis 2,3,5-smooth and short enough): no cuFFT plans
   bool conv = false;
+  bool conv_p2 = false;                    // every axis 64 or 128: the power-of-two kernels
   float2* conv_tw = nullptr;               // twiddle tables
   int2* conv_planes1 = nullptr;            // batched plans: pass A / C block -> (frame, plane)
   int2* conv_planes2 = nullptr;            //   the same with the tangent meshes

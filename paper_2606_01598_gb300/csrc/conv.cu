@@ -547,6 +547,404 @@ __global__ void __launch_bounds__(kConvBThreads) k_conv_x(ConvArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Power-of-two path: meshes whose every axis is 64 or 128 points. The same three passes, the
+// same layouts and the same energy (and virial) partials per pass-B block as the kernels
+// above, but each 1D transform of length L = 8 B (B = 8 or 16) is the four-step split of
+// Bailey (J. Supercomputing 4, 1990) done in registers with one shared-memory exchange:
+//   step 1, for each t < B: the 8-point DFT over m of x[t + B m], times w_L^(t k1), written
+//           to slot t + B k1;
+//   step 2, for each k1 < 8: the B-point DFT over t of slots t + B k1, which is X[k1 + 8 k2].
+// The loads from global memory feed step 1 of the first transform of a pass directly, and
+// step 2 of its last transform stores to global memory directly; the real-pair separation of
+// the R2C (and the Hermitian extension of the C2R) is folded into the loads of the y (z) step
+// 1, and the influence multiply into the forward x step 2. A pass is four steps with three
+// barriers. Lengths, strides and index arithmetic are compile-time constants; the twiddles
+// w_L^j are read from the plan's table (float64-built) through the read-only cache.
+// ---------------------------------------------------------------------------------------
+constexpr int kP2PlaneThreads = 1024;
+
+// 16-point DFT in registers: 4 x 4 with the twiddles w16^(n1 k1) between the two radix-4
+// steps; output in natural order.
+template <bool INV>
+__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+  const float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f, h = 0.70710678118654752f;
+  float2 t[4][4];
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) {
+    float2 a0 = v[n1], a1 = v[n1 + 4], a2 = v[n1 + 8], a3 = v[n1 + 12];
+    dft4<INV>(a0, a1, a2, a3);
+    t[n1][0] = a0;
+    t[n1][1] = a1;
+    t[n1][2] = a2;
+    t[n1][3] = a3;
+  }
+  // forward twiddles w16^j = (cos, -sin)(2 pi j / 16); the inverse takes their conjugates
+  const float sg = INV ? -1.f : 1.f;
+  auto tw = [&](float2 a, float wr, float wi) {   // a (wr + i sg wi)
+    const float wj = sg * wi;
+    return make_float2(a.x * wr - a.y * wj, a.x * wj + a.y * wr);
+  };
+  t[1][1] = tw(t[1][1], c1, -s1);   // j = 1
+  t[1][2] = tw(t[1][2], h, -h);     // j = 2
+  t[1][3] = tw(t[1][3], s1, -c1);   // j = 3
+  t[2][1] = tw(t[2][1], h, -h);     // j = 2
+  t[2][2] = rot<INV>(t[2][2]);      // j = 4
+  t[2][3] = tw(t[2][3], -h, -h);    // j = 6
+  t[3][1] = tw(t[3][1], s1, -c1);   // j = 3
+  t[3][2] = tw(t[3][2], -h, -h);    // j = 6
+  t[3][3] = tw(t[3][3], -c1, s1);   // j = 9
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    float2 b0 = t[0][k1], b1 = t[1][k1], b2 = t[2][k1], b3 = t[3][k1];
+    dft4<INV>(b0, b1, b2, b3);
+    v[k1] = b0;
+    v[k1 + 4] = b1;
+    v[k1 + 8] = b2;
+    v[k1 + 12] = b3;
+  }
+}
+
+template <int B, bool INV>
+__device__ __forceinline__ void dft_b(float2 (&u)[B]) {
+  if constexpr (B == 16) dft16<INV>(u);
+  else dft<B, INV>(u);
+}
+
+// step 1 on v[m] = x[t + B m]: the 8-point DFT and the twiddles w_L^(t k1) (tw: forward table)
+template <bool INV>
+__device__ __forceinline__ void p2_step1(float2 (&v)[8], int t, const float2* __restrict__ tw) {
+  dft<8, INV>(v);
+#pragma unroll
+  for (int k = 1; k < 8; ++k) {
+    float2 w = __ldg(tw + t * k);
+    if (INV) w.y = -w.y;
+    v[k] = cmul(v[k], w);
+  }
+}
+
+// Shared-memory float2 entries of one pass A / C plane block: the padded row lines Z
+// [NY / 2][NZ + 8] (slot p of a line at p + p / BZ) and a second buffer of the same size
+// (A: the z spectra in natural order; C: the half spectra after the y transform), with the
+// y-step buffer [NY][NZ / 2 + 1] sharing the first one.
+template <int NY, int NZ>
+constexpr int p2_plane_entries() {
+  return 2 * (NY / 2) * (NZ + 8);
+}
+
+template <int NY, int NZ>
+__device__ __forceinline__ void r2c_plane_p2(const float* __restrict__ src, float2* __restrict__ dst,
+                                             const float2* __restrict__ tz, const float2* __restrict__ ty,
+                                             float2* sm) {
+  constexpr int NP = NY / 2, LS = NZ + 8, NZH = NZ / 2 + 1, BZ = NZ / 8, BY = NY / 8;
+  static_assert(NY * NZH <= NP * LS, "the y buffer fits in the row buffer");
+  static_assert(NP * BZ <= kP2PlaneThreads && NP * 8 <= kP2PlaneThreads && NZH * 8 <= kP2PlaneThreads,
+                "steps 1 (z) and 2 hold one item per thread");
+  float2* Z = sm;              // z step 1 output (padded); then the y step 1 output S [NY][NZH]
+  float2* Z2 = sm + NP * LS;   // z spectra, natural order, row stride LS
+  float2* S = Z;
+  const int tid = threadIdx.x;
+  // z step 1: complex row p = rows 2p (real) and 2p + 1 (imaginary), read from global memory
+  if (tid < NP * BZ) {
+    const int pr = tid / BZ, t = tid - pr * BZ;
+    const float* r0 = src + (2 * pr) * NZ + t;
+    float2 v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = make_float2(r0[BZ * m], r0[NZ + BZ * m]);
+    p2_step1<false>(v, t, tz);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) Z[pr * LS + t + BZ * k + k] = v[k];
+  }
+  __syncthreads();
+  // z step 2
+  if (tid < NP * 8) {
+    const int pr = tid >> 3, k1 = tid & 7;
+    float2 u[BZ];
+#pragma unroll
+    for (int t = 0; t < BZ; ++t) u[t] = Z[pr * LS + t + (BZ + 1) * k1];
+    dft_b<BZ, false>(u);
+#pragma unroll
+    for (int k2 = 0; k2 < BZ; ++k2) Z2[pr * LS + k1 + 8 * k2] = u[k2];
+  }
+  __syncthreads();
+  // y step 1 on the real rows' half spectra: row 2p is (Z_k + conj Z_{N-k}) / 2, row 2p + 1
+  // is (Z_k - conj Z_{N-k}) / 2i, with Z the spectrum of complex row p
+  for (int it = tid; it < BY * NZH; it += blockDim.x) {
+    const int t = it / NZH, kz = it - t * NZH;
+    const int km = (NZ - kz) & (NZ - 1);
+    float2 v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int y = t + BY * m;
+      const float2 zk = Z2[(y >> 1) * LS + kz], zm = Z2[(y >> 1) * LS + km];
+      v[m] = (y & 1) ? make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x))
+                     : make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+    }
+    p2_step1<false>(v, t, ty);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) S[(t + BY * k) * NZH + kz] = v[k];
+  }
+  __syncthreads();
+  // y step 2, straight to the plane's [ky][kz] block of the spectrum
+  if (tid < 8 * NZH) {
+    const int k1 = tid / NZH, kz = tid - k1 * NZH;
+    float2 u[BY];
+#pragma unroll
+    for (int t = 0; t < BY; ++t) u[t] = S[(t + BY * k1) * NZH + kz];
+    dft_b<BY, false>(u);
+#pragma unroll
+    for (int k2 = 0; k2 < BY; ++k2) dst[(k1 + 8 * k2) * NZH + kz] = u[k2];
+  }
+}
+
+template <int NY, int NZ>
+__device__ __forceinline__ void c2r_plane_p2(const float2* __restrict__ src, float* __restrict__ dst,
+                                             const float2* __restrict__ tz, const float2* __restrict__ ty,
+                                             float2* sm) {
+  constexpr int NP = NY / 2, LS = NZ + 8, NZH = NZ / 2 + 1, BZ = NZ / 8, BY = NY / 8;
+  float2* S = sm;              // y step 1 output [NY][NZH]; then the z step 1 output (padded)
+  float2* S2 = sm + NP * LS;   // half spectra after the y transform [NY][NZH]
+  float2* Z = S;
+  const int tid = threadIdx.x;
+  // y step 1, read from the plane's [ky][kz] block
+  for (int it = tid; it < BY * NZH; it += blockDim.x) {
+    const int t = it / NZH, kz = it - t * NZH;
+    float2 v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = src[(t + BY * m) * NZH + kz];
+    p2_step1<true>(v, t, ty);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) S[(t + BY * k) * NZH + kz] = v[k];
+  }
+  __syncthreads();
+  // y step 2
+  if (tid < 8 * NZH) {
+    const int k1 = tid / NZH, kz = tid - k1 * NZH;
+    float2 u[BY];
+#pragma unroll
+    for (int t = 0; t < BY; ++t) u[t] = S[(t + BY * k1) * NZH + kz];
+    dft_b<BY, true>(u);
+#pragma unroll
+    for (int k2 = 0; k2 < BY; ++k2) S2[(k1 + 8 * k2) * NZH + kz] = u[k2];
+  }
+  __syncthreads();
+  // z step 1 on complex row p = (half row 2p) + i (half row 2p + 1), extended by Hermitian
+  // symmetry (the n_z = 0 and Nyquist entries of a real row's spectrum are real)
+  if (tid < NP * BZ) {
+    const int pr = tid / BZ, t = tid - pr * BZ;
+    const float2* ra = S2 + (2 * pr) * NZH;
+    const float2* rb = ra + NZH;
+    float2 v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int k = t + BZ * m;
+      float2 A, Bv;
+      if (k < NZH) {
+        A = ra[k];
+        Bv = rb[k];
+        if (k == 0 || 2 * k == NZ) {
+          A.y = 0.f;
+          Bv.y = 0.f;
+        }
+      } else {
+        A = ra[NZ - k];
+        Bv = rb[NZ - k];
+        A.y = -A.y;
+        Bv.y = -Bv.y;
+      }
+      v[m] = make_float2(A.x - Bv.y, A.y + Bv.x);
+    }
+    p2_step1<true>(v, t, tz);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) Z[pr * LS + t + BZ * k + k] = v[k];
+  }
+  __syncthreads();
+  // z step 2: real parts to row 2p, imaginary parts to row 2p + 1
+  if (tid < NP * 8) {
+    const int pr = tid >> 3, k1 = tid & 7;
+    float2 u[BZ];
+#pragma unroll
+    for (int t = 0; t < BZ; ++t) u[t] = Z[pr * LS + t + (BZ + 1) * k1];
+    dft_b<BZ, true>(u);
+    float* r0 = dst + (2 * pr) * NZ + k1;
+#pragma unroll
+    for (int k2 = 0; k2 < BZ; ++k2) {
+      r0[8 * k2] = u[k2].x;
+      r0[NZ + 8 * k2] = u[k2].y;
+    }
+  }
+}
+
+template <bool BATCH>
+__global__ void __launch_bounds__(kP2PlaneThreads, 1) k_conv_r2c_p2(ConvArgs a) {
+  extern __shared__ __align__(16) float2 csm[];
+  int copy, x0, pc;
+  const FrameDesc& F = plane_block<BATCH>(a, copy, x0, pc);
+  if (copy == 0 && a.keep && *a.keep == 0) return;   // rho's spectrum is not needed again
+  const int Ny = F.g.N[1], Nz = F.g.N[2];
+  const float* src = a.mesh + (copy ? F.tmesh_off : F.mesh_off) + size_t(x0) * Ny * Nz;
+  float2* dst = a.spec + (copy ? F.tspec_off : F.spec_off) + size_t(x0) * Ny * (Nz / 2 + 1);
+  const float2* tz = a.tw + F.tw_off[2];
+  const float2* ty = a.tw + F.tw_off[1];
+  if (Ny == 128 && Nz == 128) r2c_plane_p2<128, 128>(src, dst, tz, ty, csm);
+  else if (Ny == 128) r2c_plane_p2<128, 64>(src, dst, tz, ty, csm);
+  else if (Nz == 128) r2c_plane_p2<64, 128>(src, dst, tz, ty, csm);
+  else r2c_plane_p2<64, 64>(src, dst, tz, ty, csm);
+}
+
+template <bool BATCH>
+__global__ void __launch_bounds__(kP2PlaneThreads, 1) k_conv_c2r_p2(ConvArgs a) {
+  extern __shared__ __align__(16) float2 csm[];
+  int copy, x0, pc;
+  const FrameDesc& F = plane_block<BATCH>(a, copy, x0, pc);
+  if (copy == 0 && a.keep && *a.keep == 0) return;   // the forward's Phi stays in place
+  const int Ny = F.g.N[1], Nz = F.g.N[2];
+  const float2* src = a.spec + (copy ? F.tspec_off : F.spec_off) + size_t(x0) * Ny * (Nz / 2 + 1);
+  float* dst = a.mesh + (copy ? F.tmesh_off : F.mesh_off) + size_t(x0) * Ny * Nz;
+  const float2* tz = a.tw + F.tw_off[2];
+  const float2* ty = a.tw + F.tw_off[1];
+  if (Ny == 128 && Nz == 128) c2r_plane_p2<128, 128>(src, dst, tz, ty, csm);
+  else if (Ny == 128) c2r_plane_p2<128, 64>(src, dst, tz, ty, csm);
+  else if (Nz == 128) c2r_plane_p2<64, 128>(src, dst, tz, ty, csm);
+  else c2r_plane_p2<64, 64>(src, dst, tz, ty, csm);
+}
+
+// Pass B tile of NC columns (KW = 16 of the spectrum, then, in a tangent pass that also
+// keeps rho's, the same 16 of the tangent spectrum): forward x transform, influence multiply
+// with the energy (and virial) sums, inverse x transform. nrho = the leading rho columns.
+constexpr int kP2Cols = 16;
+
+template <int NX, int NC, bool VIR>
+__device__ __forceinline__ void x_tile_p2(const ConvArgs& a, const FrameDesc& F, int c0, int nrho, float2* sm) {
+  constexpr int BX = NX / 8;
+  static_assert(NC * 8 <= kConvBThreads, "one step-2 item per thread");
+  const Geometry& g = F.g;
+  const int N1 = g.N[1], N2 = g.N[2], Nzh = N2 / 2 + 1;
+  const int ncols = N1 * Nzh;
+  float2* T = sm;             // step 1 outputs [x][c], row stride NC
+  float2* T2 = sm + NX * NC;  // step 2 outputs
+  const float2* tw = a.tw + F.tw_off[0];
+  const int tid = threadIdx.x;
+  // column c of the tile: spectrum column c0 + c (rho), or c0 + c - nrho of the tangent one
+  auto col_ptr = [&](int c) { return c < nrho ? a.spec + F.spec_off + c0 + c : a.spec + F.tspec_off + c0 + (c - nrho); };
+  // forward step 1 from global memory
+  for (int it = tid; it < BX * NC; it += blockDim.x) {
+    const int t = it / NC, c = it - t * NC;
+    const float2* cp = col_ptr(c);
+    float2 v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = cp[size_t(t + BX * m) * ncols];
+    p2_step1<false>(v, t, tw);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) T[(t + BX * k) * NC + c] = v[k];
+  }
+  __syncthreads();
+  // forward step 2, natural order into T2
+  if (tid < 8 * NC) {
+    const int k1 = tid / NC, c = tid - k1 * NC;
+    float2 u[BX];
+#pragma unroll
+    for (int t = 0; t < BX; ++t) u[t] = T[(t + BX * k1) * NC + c];
+    dft_b<BX, false>(u);
+#pragma unroll
+    for (int k2 = 0; k2 < BX; ++k2) T2[(k1 + 8 * k2) * NC + c] = u[k2];
+  }
+  __syncthreads();
+  // inverse step 1, its inputs multiplied by G C / V first (the energy and virial sums over
+  // the rho columns)
+  float e = 0.f, ec = 0.f;
+  float sv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, sc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const float* cx = a.dconv + F.dconv_off;
+  for (int it = tid; it < BX * NC; it += blockDim.x) {
+    const int t = it / NC, c = it - t * NC;
+    const bool rho_col = c < nrho;
+    const int col = c0 + (rho_col ? c : c - nrho);
+    int iy, iz;
+    split_rc(col, Nzh, 1.f / float(Nzh), iy, iz);
+    const float ny = float(iy <= N1 / 2 ? iy : iy - N1);
+    const float nz = float(iz);
+    const float wz = (iz == 0 || (2 * iz == N2)) ? 1.f : 2.f;
+    float gcv[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int ix = t + BX * m;
+      gcv[m] = a.gtab ? __ldg(a.gtab + F.gtab_off + size_t(ix) * ncols + col) : 0.f;
+    }
+    float2 v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int ix = t + BX * m;
+      const float nx = float(ix <= NX / 2 ? ix : ix - NX);
+      const float kx = nx * g.bk[0] + ny * g.bk[3] + nz * g.bk[6];
+      const float kyv = nx * g.bk[1] + ny * g.bk[4] + nz * g.bk[7];
+      const float kz = nx * g.bk[2] + ny * g.bk[5] + nz * g.bk[8];
+      const float k2v = kx * kx + kyv * kyv + kz * kz;
+      float gc = gcv[m];
+      if (!a.gtab && k2v > 0.f)
+        gc = 12.566370614359172f * expf(-k2v * a.inv4a2) / k2v * cx[ix] * cx[NX + iy] * cx[NX + N1 + iz];
+      const float2 x = T2[ix * NC + c];
+      if (rho_col) {
+        const float eg = wz * gc * (x.x * x.x + x.y * x.y);
+        comp_add(e, ec, eg);
+        if (VIR && k2v > 0.f) {
+          const float tt = eg * (1.f / k2v + a.inv4a2);
+          comp_add(sv[0], sc[0], tt * kx * kx);
+          comp_add(sv[1], sc[1], tt * kyv * kyv);
+          comp_add(sv[2], sc[2], tt * kz * kz);
+          comp_add(sv[3], sc[3], tt * kx * kyv);
+          comp_add(sv[4], sc[4], tt * kx * kz);
+          comp_add(sv[5], sc[5], tt * kyv * kz);
+        }
+      }
+      const float fac = gc * g.inv_volume;
+      v[m] = make_float2(x.x * fac, x.y * fac);
+    }
+    p2_step1<true>(v, t, tw);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) T[(t + BX * k) * NC + c] = v[k];
+  }
+  __syncthreads();
+  // inverse step 2, straight to the spectrum
+  if (tid < 8 * NC) {
+    const int k1 = tid / NC, c = tid - k1 * NC;
+    float2 u[BX];
+#pragma unroll
+    for (int t = 0; t < BX; ++t) u[t] = T[(t + BX * k1) * NC + c];
+    dft_b<BX, true>(u);
+    float2* cp = col_ptr(c);
+#pragma unroll
+    for (int k2 = 0; k2 < BX; ++k2) cp[size_t(k1 + 8 * k2) * ncols] = u[k2];
+  }
+  __shared__ double wsum[kConvBThreads / 32];
+  const double et = block_comp_sum(e, ec, wsum);
+  if (threadIdx.x == 0) a.partials[blockIdx.x] = et;
+  if (VIR) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const double vt = block_comp_sum(sv[c], sc[c], wsum);
+      if (threadIdx.x == 0) a.vparts[6 * blockIdx.x + c] = vt;
+    }
+  }
+}
+
+template <bool BATCH, bool VIR>
+__global__ void __launch_bounds__(kConvBThreads) k_conv_x_p2(ConvArgs a) {
+  extern __shared__ __align__(16) float2 csm[];
+  const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, BATCH ? a.maps.blk_frame[blockIdx.x] : 0);
+  const int c0 = (blockIdx.x - F.infl_blk_off) * kP2Cols;
+  // tangent pass on the forward's inputs: rho's columns are not needed again
+  const bool rho_cols = !(a.tangent && a.keep && *a.keep == 0);
+  const int nrho = rho_cols ? kP2Cols : 0;
+  const bool two = a.tangent && rho_cols;
+  if (F.g.N[0] == 128) {
+    if (two) x_tile_p2<128, 2 * kP2Cols, VIR>(a, F, c0, nrho, csm);
+    else x_tile_p2<128, kP2Cols, VIR>(a, F, c0, nrho, csm);
+  } else {
+    if (two) x_tile_p2<64, 2 * kP2Cols, VIR>(a, F, c0, nrho, csm);
+    else x_tile_p2<64, kP2Cols, VIR>(a, F, c0, nrho, csm);
+  }
+}
+
 ConvArgs conv_args(pme_plan_t p) {
   ConvArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -579,6 +977,18 @@ int set_smem(pme_plan_t p, K kernel, unsigned& done_mask) {
 }
 
 }  // namespace
+
+bool conv_p2_ok(const int N[3]) {
+  for (int a = 0; a < 3; ++a)
+    if (N[a] != 64 && N[a] != 128) return false;
+  return true;
+}
+
+size_t conv_p2_plane_smem(const int N[3]) {
+  return size_t(2 * (N[1] / 2) * (N[2] + 8)) * sizeof(float2);
+}
+
+size_t conv_p2_x_smem(const int N[3]) { return size_t(2 * N[0] * 2 * kP2Cols) * sizeof(float2); }
 
 bool conv_axis_ok(int L) {
   if (L < 1 || L > kConvMaxLen) return false;
@@ -637,6 +1047,19 @@ int launch_conv_forward(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh,
                             : (tangent ? 2 : 1) * ((F0.g.N[0] + F0.conv_pp - 1) / F0.conv_pp);
   a.planes = tangent ? p->conv_planes2 : p->conv_planes1;
   int st;
+  if (p->conv_p2) {
+    if (p->batch) {
+      static unsigned done = 0;
+      if ((st = set_smem(p, k_conv_r2c_p2<true>, done))) return st;
+      k_conv_r2c_p2<true><<<grid, kP2PlaneThreads, p->conv_smem_plane, s>>>(a);
+    } else {
+      static unsigned done = 0;
+      if ((st = set_smem(p, k_conv_r2c_p2<false>, done))) return st;
+      k_conv_r2c_p2<false><<<grid, kP2PlaneThreads, p->conv_smem_plane, s>>>(a);
+    }
+    count_launch();
+    return check_launch(p, "k_conv_r2c_p2");
+  }
   if (p->batch) {
     static unsigned done = 0;
     if ((st = set_smem(p, k_conv_r2c<true>, done))) return st;
@@ -661,6 +1084,19 @@ int launch_conv_inverse(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh,
                             : (tangent ? 2 : 1) * ((F0.g.N[0] + F0.conv_pp - 1) / F0.conv_pp);
   a.planes = tangent ? p->conv_planes2 : p->conv_planes1;
   int st;
+  if (p->conv_p2) {
+    if (p->batch) {
+      static unsigned done = 0;
+      if ((st = set_smem(p, k_conv_c2r_p2<true>, done))) return st;
+      k_conv_c2r_p2<true><<<grid, kP2PlaneThreads, p->conv_smem_plane, s>>>(a);
+    } else {
+      static unsigned done = 0;
+      if ((st = set_smem(p, k_conv_c2r_p2<false>, done))) return st;
+      k_conv_c2r_p2<false><<<grid, kP2PlaneThreads, p->conv_smem_plane, s>>>(a);
+    }
+    count_launch();
+    return check_launch(p, "k_conv_c2r_p2");
+  }
   if (p->batch) {
     static unsigned done = 0;
     if ((st = set_smem(p, k_conv_c2r<true>, done))) return st;
@@ -691,6 +1127,23 @@ int launch_conv_influence(pme_plan_t p, cudaStream_t s, bool tangent, double* pa
     if ((st = set_smem(p, k_conv_x<B, V>, done))) return st;             \
     k_conv_x<B, V><<<grid, kConvBThreads, smem, s>>>(a);                 \
   } while (0)
+#define GB_CONV_X_P2(B, V)                                               \
+  do {                                                                   \
+    static unsigned done = 0;                                            \
+    if ((st = set_smem(p, k_conv_x_p2<B, V>, done))) return st;          \
+    k_conv_x_p2<B, V><<<grid, kConvBThreads, smem, s>>>(a);              \
+  } while (0)
+  if (p->conv_p2) {
+    if (p->batch) {
+      if (vparts) GB_CONV_X_P2(true, true);
+      else GB_CONV_X_P2(true, false);
+    } else {
+      if (vparts) GB_CONV_X_P2(false, true);
+      else GB_CONV_X_P2(false, false);
+    }
+    count_launch();
+    return check_launch(p, "k_conv_x_p2");
+  }
   if (p->batch) {
     if (vparts) GB_CONV_X(true, true);
     else GB_CONV_X(true, false);
@@ -699,6 +1152,7 @@ int launch_conv_influence(pme_plan_t p, cudaStream_t s, bool tangent, double* pa
     else GB_CONV_X(false, false);
   }
 #undef GB_CONV_X
+#undef GB_CONV_X_P2
   count_launch();
   return check_launch(p, "k_conv_x");
 }

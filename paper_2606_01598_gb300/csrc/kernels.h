@@ -87,6 +87,11 @@ GBPME_SPREAD_SHAPE(4x8x16)
 //   inverse: C2R of the spectra into mesh (Phi, and d Phi)
 constexpr int kConvMaxLen = 256;
 bool conv_axis_ok(int L);
+// the power-of-two kernels: every axis 64 or 128 points; their shared memory per plane block
+// (pass A / C, kP2PlaneThreads threads) and per pass-B block
+bool conv_p2_ok(const int N[3]);
+size_t conv_p2_plane_smem(const int N[3]);
+size_t conv_p2_x_smem(const int N[3]);
 void conv_tiles(const int N[3], int* ntile, int* cols);
 int conv_planes_per_block(const int N[3]);
 size_t conv_plane_cap(const int N[3]);

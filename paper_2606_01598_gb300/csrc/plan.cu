@@ -396,11 +396,19 @@ struct FrameInput {
 // cuFFT on batches of 16-48 point meshes and lose to it at 128^3, where the spectrum stays in
 // L2 and cuFFT's per-point cost is lower. The axis lengths and shared-memory sizes are
 // checked by the caller.
+// Meshes whose every axis is 64 or 128 points take the power-of-two kernels (compile-time
+// four-step transforms), which beat cuFFT on GB300 for single frames too (a 128^3 R2C pass in
+// a fraction of cuFFT's three kernels), so the automatic choice takes them whenever every
+// frame qualifies.
 constexpr int kConvAutoMaxAxis = 64;
 
 static bool conv_wanted(const pme_plan_s* p, bool single, const std::vector<FrameInput>& fin) {
-  if (p->opts.fft == 2) return true;
-  if (p->opts.fft != 0 || single) return false;
+  if (p->opts.fft == 2 || p->opts.fft == 3) return true;
+  if (p->opts.fft != 0) return false;
+  bool p2 = true;
+  for (const FrameInput& f : fin) p2 = p2 && conv_p2_ok(f.mesh);
+  if (p2) return true;
+  if (single) return false;
   for (const FrameInput& f : fin)
     for (int a = 0; a < 3; ++a)
       if (f.mesh[a] > kConvAutoMaxAxis) return false;
@@ -441,8 +449,20 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
       smem_x = std::max(smem_x, conv_x_smem(fin[f].mesh));
       biggest = std::max(biggest, conv_plane_cap(fin[f].mesh));
     }
-    if (conv) {
+    // the power-of-two kernels when every frame qualifies (fft = 3 keeps the general ones)
+    bool p2 = conv && p->opts.fft != 3;
+    for (int f = 0; f < F && p2; ++f) p2 = conv_p2_ok(fin[f].mesh);
+    if (p2) {
+      smem_x = 0;
+      for (int f = 0; f < F; ++f) {
+        smem_plane = std::max(smem_plane, conv_p2_plane_smem(fin[f].mesh));
+        smem_x = std::max(smem_x, conv_p2_x_smem(fin[f].mesh));
+      }
+    }
+    if (conv && !p2) {
       for (int f = 0; f < F; ++f) smem_plane = std::max(smem_plane, conv_plane_smem(fin[f].mesh, cap));
+    }
+    if (conv) {
       int dev = 0, optin = 0;
       cudaGetDevice(&dev);
       if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
@@ -451,9 +471,10 @@ static int build_plan(pme_plan_s* p, const std::vector<FrameInput>& fin, double 
       }
       conv = smem_plane + 1024 <= size_t(optin) && smem_x + 1024 <= size_t(optin);
     }
-    if (!conv && p->opts.fft == 2)
-      return set_error(p, PME_ERR_UNSUPPORTED, "fft = 2: a mesh the library's transforms do not take");
+    if (!conv && (p->opts.fft == 2 || p->opts.fft == 3))
+      return set_error(p, PME_ERR_UNSUPPORTED, "fft = 2 / 3: a mesh the library's transforms do not take");
     p->conv = conv;
+    p->conv_p2 = conv && p2;
     p->conv_cap = int(cap);
     p->conv_smem_plane = smem_plane;
     p->conv_smem_x = smem_x;
@@ -1089,7 +1110,7 @@ static int validate_opts(pme_plan_s* p, double alpha, double rcut) {
   if (!(p->opts.influence_power >= 0.0)) return set_error(p, PME_ERR_ARG, "influence_power < 0");
   if (p->opts.recip_method < 0 || p->opts.recip_method > 1) return set_error(p, PME_ERR_ARG, "recip_method");
   if (p->opts.influence_kind < 0 || p->opts.influence_kind > 1) return set_error(p, PME_ERR_ARG, "influence_kind");
-  if (p->opts.fft < 0 || p->opts.fft > 2) return set_error(p, PME_ERR_ARG, "fft");
+  if (p->opts.fft < 0 || p->opts.fft > 3) return set_error(p, PME_ERR_ARG, "fft");
   p->opts_kmax = p->opts.ewald_kmax > 0.0 ? p->opts.ewald_kmax : 2.0 * alpha * std::sqrt(std::log(1e8));
   return PME_OK;
 }
@@ -1283,7 +1304,7 @@ int pme_plan_destroy(pme_plan_t p) {
 
 int pme_plan_fft_kind(pme_plan_t p, int* kind) {
   if (!p || !kind) return PME_ERR_ARG;
-  *kind = p->conv ? 0 : 1;
+  *kind = p->conv ? (p->conv_p2 ? 2 : 0) : 1;
   return PME_OK;
 }
 

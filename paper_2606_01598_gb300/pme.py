@@ -133,7 +133,7 @@ def launch_count() -> int:
     return int(_abi.load().pme_launch_count())
 
 
-_FFT_KINDS = {"auto": 0, "cufft": 1, "own": 2}
+_FFT_KINDS = {"auto": 0, "cufft": 1, "own": 2, "own-general": 3}
 
 
 class Plan:
@@ -172,7 +172,7 @@ class Plan:
             raise ValueError("influence is 'deconvolution' or 'p3m'")
         opts.influence_kind = 0 if influence == "deconvolution" else 1
         if fft not in _FFT_KINDS:
-            raise ValueError("fft is 'auto', 'cufft' or 'own'")
+            raise ValueError("fft is 'auto', 'cufft', 'own' or 'own-general'")
         opts.fft = _FFT_KINDS[fft]
         opts.recip_method = 0 if recip_method == "mesh" else 1
         opts.ewald_kmax = float(ewald_kmax)
@@ -223,10 +223,18 @@ class Plan:
 
     @property
     def fft_kind(self) -> str:
-        """'own' (the library's transforms) or 'cufft' (pme_plan_fft_kind)."""
+        """'own' (the library's transforms, general or power-of-two kernels) or 'cufft'
+        (pme_plan_fft_kind)."""
         k = ctypes.c_int(-1)
         self._check(self.lib.pme_plan_fft_kind(self.handle, ctypes.byref(k)), "pme_plan_fft_kind")
-        return "own" if k.value == 0 else "cufft"
+        return "cufft" if k.value == 1 else "own"
+
+    @property
+    def fft_kernels(self) -> str:
+        """'general', 'power-of-two' (the library's own) or 'cufft' (pme_plan_fft_kind)."""
+        k = ctypes.c_int()
+        self._check(self.lib.pme_plan_fft_kind(self.handle, ctypes.byref(k)), "pme_plan_fft_kind")
+        return {0: "general", 1: "cufft", 2: "power-of-two"}[k.value]
 
     def sync_status(self):
         with _on_device(self.device):
@@ -458,7 +466,7 @@ class BatchPlan(Plan):
             raise ValueError("influence is 'deconvolution' or 'p3m'")
         opts.influence_kind = 0 if influence == "deconvolution" else 1
         if fft not in _FFT_KINDS:
-            raise ValueError("fft is 'auto', 'cufft' or 'own'")
+            raise ValueError("fft is 'auto', 'cufft', 'own' or 'own-general'")
         opts.fft = _FFT_KINDS[fft]
         opts.include_self = int(bool(include_self))
         opts.include_background = int(bool(include_background))
