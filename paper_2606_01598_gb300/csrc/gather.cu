@@ -50,14 +50,45 @@ __device__ __forceinline__ void apply_D(const float* D, const float x[3], float 
   for (int a = 0; a < 3; ++a) y[a] = D[a * 3 + 0] * x[0] + D[a * 3 + 1] * x[1] + D[a * 3 + 2] * x[2];
 }
 
+// Lanes per ion of k_gather: P (one per stencil z-offset), 32 / P ions per warp (the last
+// 32 mod P lanes idle).
+template <int P>
+__host__ __device__ constexpr int gather_ions_per_warp() {
+  return 32 / P;
+}
+
+// Sum over the P lanes of a group (lane l of the group holds v); valid in lane 0 of the group.
+template <int P>
+__device__ __forceinline__ float group_sum_p(float v, int l) {
+#pragma unroll
+  for (int off = 1; off < P; off <<= 1) {
+    const float t = __shfl_down_sync(0xffffffffu, v, off);
+    if ((l & (2 * off - 1)) == 0 && l + off < P) v += t;
+  }
+  return v;
+}
+
+// Per-group weight tables in shared memory: [axis][stencil index][order], orders padded to
+// 4; the groups of a warp lie an odd number of 16-byte units apart, so that the same entry of
+// every group falls in distinct banks.
+template <int P>
+__host__ __device__ constexpr int gather_tab_floats() {
+  return 4 * ((3 * P + 1) | 1);
+}
+
 // MODE: 0 forward, 1 tangent, 2 quadrupole forward
 template <int P, int MODE, bool BATCH>
 __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
   constexpr bool TAN = MODE == 1;
   constexpr int DM = MODE == 0 ? 2 : 3;
-  const int gid = a.t_lo + (blockIdx.x * blockDim.x + threadIdx.x) / kGroup;
-  const int l = threadIdx.x & (kGroup - 1);
-  const bool valid = gid < a.t_hi;
+  constexpr int IPW = gather_ions_per_warp<P>();
+  constexpr int TABF = gather_tab_floats<P>();
+  static_assert(DM <= 3, "orders fit the table");
+  __shared__ __align__(16) float tabs[kGatherThreads / 32][IPW][TABF];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int grp = lane / P, l = lane - grp * P;
+  const int gid = a.t_lo + (blockIdx.x * (kGatherThreads / 32) + wid) * IPW + grp;
+  const bool valid = grp < IPW && gid < a.t_hi;
   const int ion = valid ? gid : a.t_lo;
   const int frame = BATCH ? a.maps.sorted_frame[ion] : 0;
   const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, frame);
@@ -66,22 +97,57 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
   const float* dphi_mesh = a.mesh + F.tmesh_off;
   const int4 m = a.mr.idx[ion];
   const float4 fq = a.mr.fq[ion];
-  float wx[DM + 1][P], wy[DM + 1][P], wzall[DM + 1][P];
-  spline_weights<P, DM>(fq.x, wx);
-  spline_weights<P, DM>(fq.y, wy);
-  spline_weights<P, DM>(fq.z, wzall);
-  const bool act = valid && (l < P);
-  float wz[DM + 1];
+  // the weights of each axis once per ion: lanes 0, 1, 2 of the group take x, y, z and put
+  // them in the group's table
+  float* tab = tabs[wid][grp < IPW ? grp : 0];
+  auto put = [&](int ax, const float (&w)[DM + 1][P]) {
 #pragma unroll
-  for (int c = 0; c <= DM; ++c) {
-    float v = 0.f;
+    for (int j = 0; j < P; ++j)
+      *reinterpret_cast<float4*>(tab + (ax * P + j) * 4) =
+          make_float4(w[0][j], w[1][j], w[2][j], DM >= 3 ? w[DM][j] : 0.f);
+  };
+  if constexpr (P >= 3) {
+    const float f = l == 0 ? fq.x : (l == 1 ? fq.y : fq.z);
+    float w[DM + 1][P];
+    spline_weights<P, DM>(f, w);
+    if (valid && l < 3) put(l, w);
+  } else {   // fewer than three lanes: lane 0 forms all three
 #pragma unroll
-    for (int j = 0; j < P; ++j) v = (j == l) ? wzall[c][j] : v;
-    wz[c] = act ? v : 0.f;
+    for (int ax = 0; ax < 3; ++ax) {
+      float w[DM + 1][P];
+      spline_weights<P, DM>(ax == 0 ? fq.x : (ax == 1 ? fq.y : fq.z), w);
+      if (valid && l == 0) put(ax, w);
+    }
   }
+  __syncwarp();
+  const bool act = valid;
+  float wz[DM + 1];
+  {
+    const float4 t = *reinterpret_cast<const float4*>(tab + (2 * P + l) * 4);
+    const float tz[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int c = 0; c <= DM; ++c) wz[c] = act ? tz[c] : 0.f;
+  }
+  float wy[P][DM + 1];
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    const float4 t = *reinterpret_cast<const float4*>(tab + (1 * P + j) * 4);
+    const float ty[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int c = 0; c <= DM; ++c) wy[j][c] = ty[c];
+  }
+  const int Nx = g.N[0], Ny = g.N[1], Nz = g.N[2];
   int z = m.z + l;
-  if (z >= g.N[2]) z -= g.N[2];
-  const int Ny = g.N[1], Nz = g.N[2];
+  if (z >= Nz) z -= Nz;
+  int yo[P];
+#pragma unroll
+  for (int jy = 0; jy < P; ++jy) {
+    int y = m.y + jy;
+    if (y >= Ny) y -= Ny;
+    yo[jy] = y * Nz + z;
+  }
+  const int plane = Ny * Nz;
+  const long long Mtot = (long long)Nx * plane;
 
   // S[a][b]: sum over (jx, jy) of Phi * W^(a)_x * W^(b)_y for this lane's z, a + b <= DM
   float S[DM + 1][DM + 1];
@@ -99,7 +165,8 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
 #pragma unroll
     for (int jx = 0; jx < P; ++jx) {
       int x = m.x + jx;
-      if (x >= g.N[0]) x -= g.N[0];
+      if (x >= Nx) x -= Nx;
+      const int xo = x * plane;
       float r[DM + 1], rt[3];
 #pragma unroll
       for (int b = 0; b <= DM; ++b) r[b] = 0.f;
@@ -107,36 +174,36 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
       for (int b = 0; b < 3; ++b) rt[b] = 0.f;
 #pragma unroll
       for (int jy = 0; jy < P; ++jy) {
-        int y = m.y + jy;
-        if (y >= Ny) y -= Ny;
-        const size_t off = (size_t(x) * Ny + y) * Nz + z;
-        const bool in_mesh = index_ok((long long)off, (long long)g.N[0] * Ny * Nz);
+        const int off = xo + yo[jy];
+        const bool in_mesh = index_ok((long long)off, Mtot);
         const float v = in_mesh ? __ldg(phi_mesh + off) : 0.f;
 #pragma unroll
-        for (int b = 0; b <= DM; ++b) r[b] += v * wy[b][jy];
+        for (int b = 0; b <= DM; ++b) r[b] += v * wy[jy][b];
         if (TAN) {
           const float dv = in_mesh ? __ldg(dphi_mesh + off) : 0.f;
 #pragma unroll
-          for (int b = 0; b < 3; ++b) rt[b] += dv * wy[b][jy];
+          for (int b = 0; b < 3; ++b) rt[b] += dv * wy[jy][b];
         }
       }
+      const float4 t = *reinterpret_cast<const float4*>(tab + jx * 4);
+      const float wxj[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
       for (int ia = 0; ia <= DM; ++ia)
 #pragma unroll
         for (int ib = 0; ib <= DM; ++ib)
-          if (ia + ib <= DM) S[ia][ib] += r[ib] * wx[ia][jx];
+          if (ia + ib <= DM) S[ia][ib] += r[ib] * wxj[ia];
       if (TAN) {
 #pragma unroll
         for (int ia = 0; ia < 3; ++ia)
 #pragma unroll
           for (int ib = 0; ib < 3; ++ib)
-            if (ia + ib <= 2) T[ia][ib] += rt[ib] * wx[ia][jx];
+            if (ia + ib <= 2) T[ia][ib] += rt[ib] * wxj[ia];
       }
     }
   }
   // moments M_abc, reduced over the group's z-lanes
-#define MOM(ia, ib, ic) group_sum(S[ia][ib] * wz[ic])
-#define TMOM(ia, ib, ic) group_sum(T[ia][ib] * wz[ic])
+#define MOM(ia, ib, ic) group_sum_p<P>(S[ia][ib] * wz[ic], l)
+#define TMOM(ia, ib, ic) group_sum_p<P>(T[ia][ib] * wz[ic], l)
   const float m000 = MOM(0, 0, 0);
   const float m100 = MOM(1, 0, 0), m010 = MOM(0, 1, 0), m001 = MOM(0, 0, 1);
   const float m200 = MOM(2, 0, 0), m020 = MOM(0, 2, 0), m002 = MOM(0, 0, 2);
@@ -516,18 +583,27 @@ int launch_t(pme_plan_t p, cudaStream_t s, int n, const float* mesh, const doubl
     const OrderGroup& G = p->ogroups[gi];
     a.t_lo = BATCH ? G.sorted_lo : 0;
     a.t_hi = BATCH ? G.sorted_hi : n;
-    const int grid = int((size_t(a.t_hi - a.t_lo) * kGroup + kGatherThreads - 1) / kGatherThreads);
-    if (grid <= 0) continue;
+    const size_t nion = size_t(a.t_hi - a.t_lo);
+    if (nion == 0) continue;
+    // blocks of kGatherThreads / 32 warps, gather_ions_per_warp<P>() ions per warp
+#define GBPME_GATHER(PP)                                                                        \
+  case PP: {                                                                                    \
+    const size_t per_block = size_t(kGatherThreads / 32) * gather_ions_per_warp<PP>();          \
+    const int grid = int((nion + per_block - 1) / per_block);                                   \
+    k_gather<PP, MODE, BATCH><<<grid, kGatherThreads, 0, s>>>(a);                               \
+    break;                                                                                      \
+  }
     switch (G.order) {
-      case 1: k_gather<1, MODE, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
-      case 2: k_gather<2, MODE, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
-      case 3: k_gather<3, MODE, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
-      case 4: k_gather<4, MODE, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
-      case 5: k_gather<5, MODE, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
-      case 6: k_gather<6, MODE, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
-      case 7: k_gather<7, MODE, BATCH><<<grid, kGatherThreads, 0, s>>>(a); break;
+      GBPME_GATHER(1)
+      GBPME_GATHER(2)
+      GBPME_GATHER(3)
+      GBPME_GATHER(4)
+      GBPME_GATHER(5)
+      GBPME_GATHER(6)
+      GBPME_GATHER(7)
       default: return set_error(p, PME_ERR_ARG, "spline order out of range");
     }
+#undef GBPME_GATHER
     count_launch();
     int st = check_launch(p, "k_gather");
     if (st) return st;
