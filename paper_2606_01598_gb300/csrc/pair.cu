@@ -13,8 +13,9 @@
 // (the contractions of grad^k psi). The potential at i of source j is q_j psi - mu_j . grad psi.
 //
 // Work split: one warp per pair cell (cells at least rcut/2 wide, so a partner is at most
-// kimg = ceil(rcut / cell width) cells away per axis); the warp handles the cell's ions
-// kSlots at a time, and they share one candidate stream. The candidates are the
+// kimg = ceil(rcut / cell width) cells away per axis); the warp handles the cell's ions a few
+// at a time (four in the fused pass, eight in the list pass), and they share one candidate
+// stream. The candidates are the
 // (2 kimg + 1)^2 neighbouring (x, y) cell columns, each holding the contiguous run of the
 // 2 kimg + 1 z-cells around the cell (one or two ranges at the periodic wrap); when an axis
 // has too few cells for distinct offsets, each offset is its own segment and stands for its
@@ -518,10 +519,10 @@ __global__ void __launch_bounds__(kPairThreads) k_pair(PairArgs a) {
       bool any_full = false;
 #pragma unroll
       for (int s = 0; s < kSlots; ++s) {
+        if (s >= ni) break;   // uniform per warp
         const float4 fi = s_fi[w][s];
         const V3 r = cell_to_r<ORTHO>(g, fi.x + bx, fi.y + by, fi.z + bz);
-        const bool hit = valid && s < ni && dot(r, r) < g.rcut2 &&
-                         !(self_cell && j == __float_as_int(fi.w));
+        const bool hit = valid && dot(r, r) < g.rcut2 && !(self_cell && j == __float_as_int(fi.w));
         const unsigned bal = __ballot_sync(0xffffffffu, hit);
         if (hit) s_hit[w][s][cnt[s] + __popc(bal & lane_lt)] = make_float4(r.x, r.y, r.z, __int_as_float(j));
         cnt[s] += __popc(bal);
@@ -558,8 +559,13 @@ __global__ void __launch_bounds__(kPairThreads) k_pair(PairArgs a) {
 // List pass: one warp per pair cell walks the same candidate stream and writes every ion's
 // hits (r, j), in stream order, to its list in global memory; list_cnt = hits, or -1 (and
 // *overflow = 1) when an ion has more than list_cap.
+// (ions of a cell sharing one candidate stream in the list pass: up to eight, so that most
+// cells walk their stream once; slots past the cell's last ion are skipped, warp-uniformly)
+constexpr int kBuildSlots = 8;
+
 template <bool BATCH, bool ORTHO>
 __global__ void __launch_bounds__(kPairThreads) k_pair_build(PairArgs a, int* overflow) {
+  constexpr int kSlots = kBuildSlots;
   __shared__ float4 s_fi[kPairWarps][kSlots];
   __shared__ unsigned s_cand[kPairWarps][kCandCap];
   __shared__ int s_code[kPairWarps][32];
@@ -589,10 +595,10 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_build(PairArgs a, int* ov
                     [&](bool valid, int j, float bx, float by, float bz, bool self_cell) {
 #pragma unroll
       for (int s = 0; s < kSlots; ++s) {
+        if (s >= ni) break;   // uniform per warp
         const float4 fi = s_fi[w][s];
         const V3 r = cell_to_r<ORTHO>(g, fi.x + bx, fi.y + by, fi.z + bz);
-        const bool hit = valid && s < ni && dot(r, r) < g.rcut2 &&
-                         !(self_cell && j == __float_as_int(fi.w));
+        const bool hit = valid && dot(r, r) < g.rcut2 && !(self_cell && j == __float_as_int(fi.w));
         const unsigned bal = __ballot_sync(0xffffffffu, hit);
         const int k = cnt[s] + __popc(bal & lane_lt);
         if (hit && k < cap && index_ok(k, cap))
