@@ -8,10 +8,14 @@ in HBM. The metric is ion-evaluations per second: ions / (t_forward + t_backward
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--fft auto|cufft|own] [--batch] [--crossover] [--quad] [--no-extras]
+                  [--profile-driver]
 
 The timed steps repeat the same calls, so after the first two they replay the plan's recorded
 pass graphs, as any caller's repeated calls do. --fft picks the transforms of the mesh
-convolution (the automatic choice is cuFFT for this single frame).
+convolution (the automatic choice, for this single 128^3 frame, is the library's power-of-two
+kernels). --profile-driver runs only W + K untimed steps of one plan with the default brick
+(no tuner, no timers, no JSON line; with --quad, forward_quad calls): the command the ncu
+summaries under profiles/ were captured from.
 
 With N > 1 (launched by torch.distributed.run) every rank runs an independent replica of the
 step on its own GPU ("replicas only": a single frame does not shard); value is the sum of the
@@ -82,13 +86,13 @@ QUAD_METRIC = "PME q+mu+Theta fwd Mion-evals/s @32k ions"
 # ncu capture of the same kernels on the same workload (cold cache: ncu flushes the caches
 # before each replay); the summaries, with their commands, are under profiles/.
 MEASURED_TRAFFIC = {
-    "fwd.pair_eval": (52.047104e6 + 0.142848e6, "profiles/k_spread_gather_pair_nacl32k.md"),
-    "bwd.pair_eval": (53.097728e6 + 0.274176e6, "profiles/k_spread_gather_pair_nacl32k.md"),
-    "fwd.spread": (1.611264e6, "profiles/k_spread_gather_pair_nacl32k.md"),
-    "bwd.spread": (2.666752e6, "profiles/k_spread_gather_pair_nacl32k.md"),
-    "fwd.gather": (9.455360e6, "profiles/k_spread_gather_pair_nacl32k.md"),
-    "bwd.gather": (19.428608e6, "profiles/k_spread_gather_pair_nacl32k.md"),
-    "quad.pair_eval": (52.838656e6 + 0.348672e6, "profiles/k_pair_quad_nacl32k.md"),
+    "fwd.pair_eval": (52.047360e6 + 0.122624e6, "profiles/k_spread_gather_pair_nacl32k.md"),
+    "bwd.pair_eval": (53.099520e6 + 0.201216e6, "profiles/k_spread_gather_pair_nacl32k.md"),
+    "fwd.spread": (1.611520e6 + 0.000000e6, "profiles/k_spread_gather_pair_nacl32k.md"),
+    "bwd.spread": (2.667008e6 + 0.000000e6, "profiles/k_spread_gather_pair_nacl32k.md"),
+    "fwd.gather": (9.451520e6 + 0.000000e6, "profiles/k_spread_gather_pair_nacl32k.md"),
+    "bwd.gather": (19.423744e6 + 0.000000e6, "profiles/k_spread_gather_pair_nacl32k.md"),
+    "quad.pair_eval": (52.838144e6 + 0.163840e6, "profiles/k_pair_quad_nacl32k.md"),
 }
 
 
@@ -1074,6 +1078,39 @@ def run_batch(args):
     return 0
 
 
+def run_profile_driver(args):
+    """W + K steps of the timed step (or of forward_quad with --quad) on one plan with the
+    default 8x8x16 brick: the fixed launch sequence the ncu summaries count launches in."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2606_01598_gb300 as gb
+    import workloads as W
+
+    fr, cfg = build_frame(args.workload)
+    dev = torch.device("cuda", 0)
+    n = fr.n
+    plan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=n, device=dev,
+                   fft=FFT, brick=(8, 8, 16))
+    c = lambda x: torch.tensor(np.float32(x), device=dev)
+    pos, q, mu = c(fr.pos), c(fr.q), c(fr.mu)
+    if args.quad:
+        th = c(W.quadrupoles(n, 0.1, seed=300).reshape(n, 9)[:, [0, 4, 8, 1, 2, 5]])
+        for _ in range(args.warmup + args.steps):
+            plan.forward_quad(pos, q, mu, th)
+    else:
+        gF, gphi, gfield = (c(x) for x in W.tangent(n, seed=99))
+        gE = torch.tensor([0.5], dtype=torch.float64, device=dev)
+        for _ in range(args.warmup + args.steps):
+            plan.forward(pos, q, mu, energy=True, force=True, phi=True, field=True)
+            plan.backward(pos, q, mu, gE, gF, gphi, gfield)
+    torch.cuda.synchronize(dev)
+    plan.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1090,9 +1127,13 @@ def main():
     ap.add_argument("--frames", type=int, default=256)
     ap.add_argument("--fft", default="auto", choices=["auto", "cufft", "own"],
                     help="transforms of the mesh convolution (pme_opts.fft)")
+    ap.add_argument("--profile-driver", action="store_true",
+                    help="untimed W + K steps of one plan (default brick), for ncu captures")
     args = ap.parse_args()
     global FFT
     FFT = args.fft
+    if args.profile_driver:
+        return run_profile_driver(args)
     if args.batch:
         return run_batch(args)
     if args.quad:
