@@ -14,7 +14,8 @@ The timed steps repeat the same calls, so after the first two they replay the pl
 pass graphs, as any caller's repeated calls do. --fft picks the transforms of the mesh
 convolution (the automatic choice, for this single 128^3 frame, is the library's power-of-two
 kernels). --profile-driver runs only W + K untimed steps of one plan with the default brick
-(no tuner, no timers, no JSON line; with --quad, forward_quad calls): the command the ncu
+(no tuner, no timers, no JSON line; with --quad, forward_quad calls; with --train, the learned
+network's forward + backward on the 32 x 512-ion training batch): the command the ncu
 summaries under profiles/ were captured from.
 
 With N > 1 (launched by torch.distributed.run) every rank runs an independent replica of the
@@ -1089,8 +1090,23 @@ def run_profile_driver(args):
     import paper_2606_01598_gb300 as gb
     import workloads as W
 
-    fr, cfg = build_frame(args.workload)
     dev = torch.device("cuda", 0)
+    if args.train:
+        # the learned network on the 32 x 512-ion training batch: W + K forward + backward
+        frames = W.training_frames(32, 512, seed=1003)
+        offsets = np.concatenate([[0], np.cumsum([f.n for f in frames])])
+        N = int(offsets[-1])
+        net = gb.Net(N, len(frames), device=dev)
+        net.set_frames(offsets, [f.box for f in frames], np.concatenate([f.species for f in frames]))
+        net.set_params(W.net_params(seed=2024))
+        pos = torch.tensor(np.float32(np.concatenate([f.pos for f in frames])), device=dev)
+        for _ in range(args.warmup + args.steps):
+            out = net.forward(pos)
+            net.backward(out["q"], out["mu"], torch.ones(len(frames), dtype=torch.float64, device=dev))
+        torch.cuda.synchronize(dev)
+        net.close()
+        return 0
+    fr, cfg = build_frame(args.workload)
     n = fr.n
     plan = gb.Plan(fr.box, cfg["mesh"], cfg["order"], cfg["alpha"], cfg["rcut"], max_ions=n, device=dev,
                    fft=FFT, brick=(8, 8, 16))
@@ -1129,6 +1145,8 @@ def main():
                     help="transforms of the mesh convolution (pme_opts.fft)")
     ap.add_argument("--profile-driver", action="store_true",
                     help="untimed W + K steps of one plan (default brick), for ncu captures")
+    ap.add_argument("--train", action="store_true",
+                    help="with --profile-driver: the learned network's forward + backward instead")
     args = ap.parse_args()
     global FFT
     FFT = args.fft
