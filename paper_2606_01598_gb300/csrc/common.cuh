@@ -48,7 +48,23 @@ struct Geometry {
   float bk[9];        // reciprocal basis, rows b_r = 2 pi C^{-T}: bk[r*3+c] = 2 pi cinv[c*3+r]
   float inv_volume;   // 1 / V
   float bg_fac;       // pi / (V alpha^2), the background potential per unit net charge
+  // K = diag-scaled C^{-1} as float pairs hi + lo (K[a*3+b] = N_b cinv[a*3+b] for the mesh,
+  // ncell_b cinv[a*3+b] for the pair cells): mesh and cell coordinates in compensated float32
+  float kmh[9], kml[9], kch[9], kcl[9];
 };
+
+// Fill the compensated-float32 copies of N_b C^{-1} and ncell_b C^{-1} (after cinv, N, ncell).
+inline void geometry_split(Geometry& g) {
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      const double km = double(g.N[b]) * g.cinv[a * 3 + b];
+      const double kc = double(g.ncell[b]) * g.cinv[a * 3 + b];
+      g.kmh[a * 3 + b] = float(km);
+      g.kml[a * 3 + b] = float(km - double(float(km)));
+      g.kch[a * 3 + b] = float(kc);
+      g.kcl[a * 3 + b] = float(kc - double(float(kc)));
+    }
+}
 
 // Per-ion records in brick (mesh) order.
 struct MeshRecords {
@@ -386,6 +402,85 @@ __device__ __forceinline__ void stencil_origin(double s, int N, int order, int& 
   if (m >= N) m -= N;
   m0 = m;
   f = fr;
+}
+
+// Scaled coordinate x_b = sum_a r_a K[a][b] (K = kh + kl) as hi + lo in float32: exact
+// products by fused multiply-add error terms, the sum by the two-sum of Knuth (TAOCP vol. 2,
+// 4.2.2), so x is carried to about 2^-45 of |x| -- the float64 result rounded to float32 within
+// one unit in the last place -- without the float64 pipe.
+__device__ __forceinline__ void scaled_coord(const float* kh, const float* kl, float rx, float ry, float rz,
+                                             int b, float& hi, float& lo) {
+  const float r[3] = {rx, ry, rz};
+  float s = 0.f, e = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float k = kh[a * 3 + b];
+    const float p = r[a] * k;
+    const float pe = fmaf(r[a], k, -p);
+    const float t = s + p;
+    const float bb = t - s;
+    const float te = (s - (t - bb)) + (p - bb);
+    s = t;
+    e += te + fmaf(r[a], kl[a * 3 + b], pe);
+  }
+  hi = s;
+  lo = e;
+}
+
+// Integer part m and fraction f in [0,1) of hi + lo + c (c a multiple of 1/2); false when the
+// value is not finite or too large for the float path (|hi| >= 2^22).
+__device__ __forceinline__ bool split_coord(float hi, float lo, float c, int& m, float& f) {
+  if (!(fabsf(hi) < 4194304.f) || !(fabsf(lo) < 1.f)) return false;
+  const float yh = hi + c;
+  const float bb = yh - hi;
+  const float yl = lo + ((hi - (yh - bb)) + (c - bb));
+  const float fl = floorf(yh);
+  float fr = (yh - fl) + yl;
+  int k = int(fl);
+  if (fr < 0.f) {
+    fr += 1.f;
+    k -= 1;
+  } else if (fr >= 1.f) {
+    fr -= 1.f;
+    k += 1;
+  }
+  if (fr >= 1.f) {
+    fr = 0.f;
+    k += 1;
+  }
+  m = k;
+  f = fr;
+  return true;
+}
+
+// First stencil point m0 (wrapped) and offset f along axis b from the position, in float32
+// (stencil_origin of frac_coords' s to float32 rounding); false: use the float64 path.
+__device__ __forceinline__ bool stencil_origin_f(const Geometry& g, float rx, float ry, float rz, int b, int& m0,
+                                                 float& f) {
+  float hi, lo;
+  scaled_coord(g.kmh, g.kml, rx, ry, rz, b, hi, lo);
+  int m;
+  if (!split_coord(hi, lo, 1.f - 0.5f * float(g.order), m, f)) return false;
+  const int N = g.N[b];
+  m %= N;
+  if (m < 0) m += N;
+  m0 = m;
+  return true;
+}
+
+// Pair cell and in-cell offset along axis b from the position, in float32; false: use the
+// float64 path.
+__device__ __forceinline__ bool cell_origin_f(const Geometry& g, float rx, float ry, float rz, int b, int& c,
+                                              float& f) {
+  float hi, lo;
+  scaled_coord(g.kch, g.kcl, rx, ry, rz, b, hi, lo);
+  int m;
+  if (!split_coord(hi, lo, 0.f, m, f)) return false;
+  const int nc = g.ncell[b];
+  m %= nc;
+  if (m < 0) m += nc;
+  c = m;
+  return true;
 }
 
 // Pair cell and in-cell offset of fractional coordinate s along one axis.

@@ -179,6 +179,7 @@ extern "C" int pme_spread_noalloc(void* stream, const double box[9], const int m
     g.ncell[a] = 1;
     g.kimg[a] = 0;
   }
+  geometry_split(g);
   g.order = order;
   g.alpha = 1.f;
   g.rcut2 = 0.f;

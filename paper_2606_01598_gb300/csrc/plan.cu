@@ -171,6 +171,7 @@ static bool frame_geometry(Geometry& g, const double* box, double rcut, bool pai
   }
   for (int b = 0; b < 3; ++b)
     for (int c = 0; c < 3; ++c) g.H[b * 3 + c] = float(box[b * 3 + c] / g.ncell[b]);
+  geometry_split(g);
   *ncells = nc_tot;
   return true;
 }

@@ -139,14 +139,25 @@ k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int tangent, 
       for (int a = 0; a < 6; ++a) ok = ok && isfinite(in.theta[6 * i + a]);
     }
     if (!ok) atomicOr(flags, kFlagNonFinite);
-    double s[3];
-    frac_coords(g, rx, ry, rz, s);
+    // mesh and cell coordinates in compensated float32 (GB300's float64 rate is a small
+    // fraction of its float32 rate); positions beyond the float path's range, or not finite,
+    // take the float64 path
     int m0[3], c[3];
     float fb[3], fc[3];
+    bool fast = true;
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      stencil_origin(s[b], g.N[b], g.order, m0[b], fb[b]);
-      cell_origin(s[b], g.ncell[b], c[b], fc[b]);
+      fast = fast && stencil_origin_f(g, rx, ry, rz, b, m0[b], fb[b]);
+      fast = fast && cell_origin_f(g, rx, ry, rz, b, c[b], fc[b]);
+    }
+    if (!fast) {
+      double s[3];
+      frac_coords(g, rx, ry, rz, s);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        stencil_origin(s[b], g.N[b], g.order, m0[b], fb[b]);
+        cell_origin(s[b], g.ncell[b], c[b], fc[b]);
+      }
     }
     const int kb = F.brick_off + ((m0[0] / g.brick[0]) * g.nb[1] + m0[1] / g.brick[1]) * g.nb[2] +
                    m0[2] / g.brick[2];
@@ -333,13 +344,24 @@ k_rank_records(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, Mesh
     }
     return;
   }
+  // the binning pass's coordinates: compensated float32, float64 where that does not apply
   double s[3];
-  frac_coords(g, rx, ry, rz, s);
+  bool fast = true;
+  int m0[3], cc[3];
+  float fm[3], fcl[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    if (mesh_side) fast = fast && stencil_origin_f(g, rx, ry, rz, b, m0[b], fm[b]);
+    else fast = fast && cell_origin_f(g, rx, ry, rz, b, cc[b], fcl[b]);
+  }
+  if (!fast) frac_coords(g, rx, ry, rz, s);
   if (mesh_side) {
-    int m0[3];
     float fr[3];
 #pragma unroll
-    for (int b = 0; b < 3; ++b) stencil_origin(s[b], g.N[b], g.order, m0[b], fr[b]);
+    for (int b = 0; b < 3; ++b) {
+      if (fast) fr[b] = fm[b];
+      else stencil_origin(s[b], g.N[b], g.order, m0[b], fr[b]);
+    }
     float pm[3], pd[3], pt[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
@@ -358,7 +380,14 @@ k_rank_records(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, Mesh
     int c[3];
     float fr[3];
 #pragma unroll
-    for (int b = 0; b < 3; ++b) cell_origin(s[b], g.ncell[b], c[b], fr[b]);
+    for (int b = 0; b < 3; ++b) {
+      if (fast) {
+        c[b] = cc[b];
+        fr[b] = fcl[b];
+      } else {
+        cell_origin(s[b], g.ncell[b], c[b], fr[b]);
+      }
+    }
     pr.idx[dest] = make_int4(c[0], c[1], c[2], i);
     pr.fq[dest] = make_float4(fr[0], fr[1], fr[2], __int_as_float(c[2]));
     pr.mu[dest] = make_float4(mu[0], mu[1], mu[2], qi);
