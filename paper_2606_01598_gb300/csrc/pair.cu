@@ -41,6 +41,8 @@
 // into different code; with contraction left to the compiler, the two could round a term
 // differently (the choice depends on the surrounding code), and the two paths would no longer
 // agree bit for bit.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace gbpme {
@@ -459,100 +461,101 @@ __global__ void __launch_bounds__(kPairThreads) k_pair(PairArgs a) {
   __shared__ unsigned s_cand[kPairWarps][kCandCap];     // candidate stream of the segment group
   __shared__ int s_code[kPairWarps][32];                // packed (ox, oy, oz) of each segment
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int cidx = blockIdx.x * kPairWarps + w;
-  if (cidx >= a.ncells) return;   // uniform per warp
   if (a.cache_bad && *a.cache_bad == 0) return;
-  if (a.vir_lost && cidx == 0 && lane == 0) atomicOr(a.vir_lost, kFlagVirialLost);
-  const int cell = a.cell_lo + cidx;
-  const int c_lo = a.start_c[cell], c_hi = a.start_c[cell + 1];
-  if (c_lo == c_hi) return;
-  const int frame = BATCH ? a.maps.sorted_frame[c_lo] : 0;
-  const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, frame);
-  const Geometry& g = F.g;
-  const CellCtx cc = cell_ctx(g, cell - F.cell_off, F.cell_off);
-  const unsigned lane_lt = (1u << lane) - 1u;
-  const float gE = (TAN && a.g_energy) ? float(a.g_energy[frame]) : 0.f;
+  if (a.vir_lost && blockIdx.x == 0 && w == 0 && lane == 0) atomicOr(a.vir_lost, kFlagVirialLost);
+  // grid-stride over the cells (the launch may be capped: as a fallback it mostly exits here)
+  for (int cidx = blockIdx.x * kPairWarps + w; cidx < a.ncells; cidx += gridDim.x * kPairWarps) {
+    const int cell = a.cell_lo + cidx;
+    const int c_lo = a.start_c[cell], c_hi = a.start_c[cell + 1];
+    if (c_lo == c_hi) continue;   // uniform per warp
+    const int frame = BATCH ? a.maps.sorted_frame[c_lo] : 0;
+    const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, frame);
+    const Geometry& g = F.g;
+    const CellCtx cc = cell_ctx(g, cell - F.cell_off, F.cell_off);
+    const unsigned lane_lt = (1u << lane) - 1u;
+    const float gE = (TAN && a.g_energy) ? float(a.g_energy[frame]) : 0.f;
 
-  for (int i0 = c_lo; i0 < c_hi; i0 += kSlots) {
-    const int ni = min(kSlots, c_hi - i0);
-    if (lane < ni) {
-      const float4 f = a.pr.fq[i0 + lane];
-      s_fi[w][lane] = make_float4(f.x, f.y, f.z, __int_as_float(i0 + lane));
-    }
+    for (int i0 = c_lo; i0 < c_hi; i0 += kSlots) {
+      const int ni = min(kSlots, c_hi - i0);
+      if (lane < ni) {
+        const float4 f = a.pr.fq[i0 + lane];
+        s_fi[w][lane] = make_float4(f.x, f.y, f.z, __int_as_float(i0 + lane));
+      }
 #pragma unroll
-    for (int s = 0; s < kSlots; ++s)
+      for (int s = 0; s < kSlots; ++s)
 #pragma unroll
-      for (int k = 0; k < NA; ++k) s_acc[w][s][k][lane] = 0.f;
-    __syncwarp();
-    int cnt[kSlots];     // hits waiting per slot (< 64)
+        for (int k = 0; k < NA; ++k) s_acc[w][s][k][lane] = 0.f;
+      __syncwarp();
+      int cnt[kSlots];     // hits waiting per slot (< 64)
 #pragma unroll
-    for (int s = 0; s < kSlots; ++s) cnt[s] = 0;
-    unsigned cnts = 0;   // the same, packed 8 bits per slot, for the flush loop
+      for (int s = 0; s < kSlots; ++s) cnt[s] = 0;
+      unsigned cnts = 0;   // the same, packed 8 bits per slot, for the flush loop
 
-    // Evaluate, for every slot, its waiting hits in whole 32-wide chunks (all of them when
-    // `last`), keeping the remainder at the front of the list.
-    auto flush = [&](bool last) {
-      for (int s = 0; s < ni; ++s) {
-        const int c = int((cnts >> (8 * s)) & 0xffu);
-        const int upto = last ? c : (c & ~31);
-        if (upto == 0) continue;   // uniform
-        const Ion I = load_ion<TAN>(a, i0 + s, gE);
-        Acc<TAN> A;
-        float* ap = &s_acc[w][s][0][lane];
-        acc_load<TAN>(A, ap);
-        for (int k = lane; k < upto; k += 32) {
-          const float4 h = s_hit[w][s][k];
-          interact<TAN>(a, I, __float_as_int(h.w), mk(h.x, h.y, h.z), A);
+      // Evaluate, for every slot, its waiting hits in whole 32-wide chunks (all of them when
+      // `last`), keeping the remainder at the front of the list.
+      auto flush = [&](bool last) {
+        for (int s = 0; s < ni; ++s) {
+          const int c = int((cnts >> (8 * s)) & 0xffu);
+          const int upto = last ? c : (c & ~31);
+          if (upto == 0) continue;   // uniform
+          const Ion I = load_ion<TAN>(a, i0 + s, gE);
+          Acc<TAN> A;
+          float* ap = &s_acc[w][s][0][lane];
+          acc_load<TAN>(A, ap);
+          for (int k = lane; k < upto; k += 32) {
+            const float4 h = s_hit[w][s][k];
+            interact<TAN>(a, I, __float_as_int(h.w), mk(h.x, h.y, h.z), A);
+          }
+          acc_store<TAN>(A, ap);
+          __syncwarp();
+          const int rest = c - upto;
+          if (lane < rest)   // [0, rest) and [upto, c) do not overlap: upto >= 32 > rest
+            s_hit[w][s][lane] = s_hit[w][s][upto + lane];
+          __syncwarp();
+          cnts = (cnts & ~(0xffu << (8 * s))) | (unsigned(rest) << (8 * s));
         }
-        acc_store<TAN>(A, ap);
-        __syncwarp();
-        const int rest = c - upto;
-        if (lane < rest)   // [0, rest) and [upto, c) do not overlap: upto >= 32 > rest
-          s_hit[w][s][lane] = s_hit[w][s][upto + lane];
-        __syncwarp();
-        cnts = (cnts & ~(0xffu << (8 * s))) | (unsigned(rest) << (8 * s));
-      }
-    };
+      };
 
-    walk_candidates(a, cc, s_cand[w], s_code[w], lane,
-                    [&](bool valid, int j, float bx, float by, float bz, bool self_cell) {
-      bool any_full = false;
+      walk_candidates(a, cc, s_cand[w], s_code[w], lane,
+                      [&](bool valid, int j, float bx, float by, float bz, bool self_cell) {
+        bool any_full = false;
 #pragma unroll
-      for (int s = 0; s < kSlots; ++s) {
-        if (s >= ni) break;   // uniform per warp
-        const float4 fi = s_fi[w][s];
-        const V3 r = cell_to_r<ORTHO>(g, fi.x + bx, fi.y + by, fi.z + bz);
-        const bool hit = valid && dot(r, r) < g.rcut2 && !(self_cell && j == __float_as_int(fi.w));
-        const unsigned bal = __ballot_sync(0xffffffffu, hit);
-        if (hit) s_hit[w][s][cnt[s] + __popc(bal & lane_lt)] = make_float4(r.x, r.y, r.z, __int_as_float(j));
-        cnt[s] += __popc(bal);
-        any_full |= cnt[s] >= 32;
-      }
-      if (any_full) {
-        __syncwarp();
-        cnts = pack_counts(cnt);
-        flush(false);
-        unpack_counts(cnts, cnt);
-      }
-    });
-    __syncwarp();
-    cnts = pack_counts(cnt);
-    flush(true);
+        for (int s = 0; s < kSlots; ++s) {
+          if (s >= ni) break;   // uniform per warp
+          const float4 fi = s_fi[w][s];
+          const V3 r = cell_to_r<ORTHO>(g, fi.x + bx, fi.y + by, fi.z + bz);
+          const bool hit = valid && dot(r, r) < g.rcut2 && !(self_cell && j == __float_as_int(fi.w));
+          const unsigned bal = __ballot_sync(0xffffffffu, hit);
+          if (hit) s_hit[w][s][cnt[s] + __popc(bal & lane_lt)] = make_float4(r.x, r.y, r.z, __int_as_float(j));
+          cnt[s] += __popc(bal);
+          any_full |= cnt[s] >= 32;
+        }
+        if (any_full) {
+          __syncwarp();
+          cnts = pack_counts(cnt);
+          flush(false);
+          unpack_counts(cnts, cnt);
+        }
+      });
+      __syncwarp();
+      cnts = pack_counts(cnt);
+      flush(true);
 
-    for (int s = 0; s < ni; ++s) {
-      const int orig = a.pr.idx[i0 + s].w;
-      const float* ap = &s_acc[w][s][0][0];
-      float v[NA];
+      for (int s = 0; s < ni; ++s) {
+        const int orig = a.pr.idx[i0 + s].w;
+        const float* ap = &s_acc[w][s][0][0];
+        float v[NA];
 #pragma unroll
-      for (int k = 0; k < NA; ++k) v[k] = warp_sum(ap[32 * k + lane]);
-      if (lane == 0) {
-        float* o = a.out + size_t(orig) * (TAN ? 8 : 10);
+        for (int k = 0; k < NA; ++k) v[k] = warp_sum(ap[32 * k + lane]);
+        if (lane == 0) {
+          float* o = a.out + size_t(orig) * (TAN ? 8 : 10);
 #pragma unroll
-        for (int k = 0; k < NA; ++k) o[k] = v[k];
-        if (TAN) o[7] = 0.f;
+          for (int k = 0; k < NA; ++k) o[k] = v[k];
+          if (TAN) o[7] = 0.f;
+        }
       }
+      __syncwarp();
     }
-    __syncwarp();
   }
 }
 
@@ -736,8 +739,11 @@ int launch_pair(pme_plan_t p, cudaStream_t s, int n, bool tangent, const IonInpu
   PairArgs a = pair_args(p, g_energy, out);
   a.cache_bad = skip;
   if (virial && !tangent) a.vir_lost = p->flags;
-  const int grid = (a.ncells + kPairWarps - 1) / kPairWarps;
+  int grid = (a.ncells + kPairWarps - 1) / kPairWarps;
   if (grid == 0) return PME_OK;
+  // as the fallback of the list path (skip non-null) it normally exits at once: a small grid
+  // keeps that cheap; the cells are walked grid-stride when it does run
+  if (skip) grid = std::min(grid, 2 * device_sm_count());
   const bool ortho = plan_ortho(p);
   if (p->batch) {
     if (tangent) launch_k<true, true>(ortho, grid, s, a);

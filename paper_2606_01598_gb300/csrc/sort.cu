@@ -238,7 +238,8 @@ __device__ __forceinline__ int stable_rank(const int* perm, int seg_lo, int seg_
                                            int fallback) {
   if (seg_hi - seg_lo > kRankMaxSegment) return fallback;
   int r = 0;
-  for (int u = seg_lo; u < seg_hi; ++u) r += (perm[u] < self) ? 1 : 0;
+#pragma unroll 8
+  for (int u = seg_lo; u < seg_hi; ++u) r += (perm[u] < self) ? 1 : 0;   // eight loads in flight
   return seg_lo + r;
 }
 

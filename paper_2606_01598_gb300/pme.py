@@ -129,6 +129,24 @@ def autotune_brick(box, mesh, order: int, alpha: float, rcut: float, n_ions: int
     return (out[0], out[1], out[2]), times
 
 
+def _outputs(want, given, alloc, dev):
+    # the output tensors of a call: fresh ones, or the caller's, checked against what the call
+    # writes (a wrong buffer would be overwritten past its end by the library)
+    out = {}
+    for k, spec in want.items():
+        if spec is None:
+            continue
+        shape, dtype = spec
+        t = None if given is None else given.get(k)
+        if t is None:
+            t = torch.empty(shape, dtype=dtype, **alloc)
+        elif (tuple(t.shape) != tuple(shape) or t.dtype != dtype or not t.is_contiguous()
+              or t.device.type != dev.type):
+            raise ValueError(f"output '{k}': expected a contiguous {dtype} tensor of shape {shape} on {dev}")
+        out[k] = t
+    return out
+
+
 def launch_count() -> int:
     return int(_abi.load().pme_launch_count())
 
@@ -264,10 +282,16 @@ class Plan:
 
     # -- full passes -----------------------------------------------------------------------
     def forward(self, pos, q, mu=None, *, energy=True, force=True, phi=True, field=True,
-                field_grad=False, virial=False):
+                field_grad=False, virial=False, out=None, sync=True):
         """Energy and derivatives (and, with virial=True, the 3x3 virial -dE/d strain; see
         pme_forward_virial). Device tensors stay on the device; CPU tensors are passed as
-        host pointers (the library stages them). Returns a dict of tensors."""
+        host pointers (the library stages them). Returns a dict of tensors.
+
+        out: optional dict of preallocated output tensors (the keys asked for, with the shapes
+        and dtypes this method would allocate, on the inputs' device; pinned host memory for
+        host calls), written instead of fresh ones. sync=False skips the stream synchronisation
+        after a host call: host outputs are then complete only once the current stream has been
+        synchronised (by a later call with sync=True, for instance)."""
         dev = pos.device if isinstance(pos, torch.Tensor) else torch.device("cpu")
         on_dev = dev.type == "cuda"
         pos = _f32(pos, dev)
@@ -276,20 +300,13 @@ class Plan:
         n = int(pos.shape[0])
         pin = (not on_dev)
         alloc = dict(device=dev, pin_memory=pin) if pin else dict(device=dev)
-        out = {}
-        if energy:
-            out["energy"] = torch.empty(1, dtype=torch.float64, **alloc)
-        if force:
-            out["force"] = torch.empty((n, 3), dtype=torch.float32, **alloc)
-        if phi:
-            out["phi"] = torch.empty(n, dtype=torch.float32, **alloc)
-        if field:
-            out["field"] = torch.empty((n, 3), dtype=torch.float32, **alloc)
-        if field_grad:
-            out["field_grad"] = torch.empty((n, 6), dtype=torch.float32, **alloc)
-        if virial:
-            out.setdefault("energy", torch.empty(1, dtype=torch.float64, **alloc))
-            out["virial"] = torch.empty((3, 3), dtype=torch.float64, **alloc)
+        want = {"energy": ((1,), torch.float64) if (energy or virial) else None,
+                "force": ((n, 3), torch.float32) if force else None,
+                "phi": ((n,), torch.float32) if phi else None,
+                "field": ((n, 3), torch.float32) if field else None,
+                "field_grad": ((n, 6), torch.float32) if field_grad else None,
+                "virial": ((3, 3), torch.float64) if virial else None}
+        out = _outputs(want, out, alloc, dev)
         with _on_device(self.device):
             args = (self.handle, _stream_handle(self.device), n, _ptr(pos), _ptr(q),
                     _ptr(mu), _ptr(out.get("energy")), _ptr(out.get("force")),
@@ -300,7 +317,7 @@ class Plan:
             else:
                 st = self.lib.pme_forward(*args)
                 self._check(st, "pme_forward")
-            if not on_dev:
+            if not on_dev and sync:
                 torch.cuda.current_stream(self.device).synchronize()
         return out
 
@@ -340,8 +357,11 @@ class Plan:
                 torch.cuda.current_stream(self.device).synchronize()
         return out
 
-    def backward(self, pos, q, mu=None, g_energy=None, g_force=None, g_phi=None, g_field=None):
-        """Vector-Jacobian product of (pos, q, mu) -> (E, force, phi, field)."""
+    def backward(self, pos, q, mu=None, g_energy=None, g_force=None, g_phi=None, g_field=None, *,
+                 out=None, sync=True):
+        """Vector-Jacobian product of (pos, q, mu) -> (E, force, phi, field). out: optional
+        preallocated (grad_pos [n, 3], grad_q [n], grad_mu [n, 3]) float32 tensors; sync as for
+        forward."""
         dev = pos.device if isinstance(pos, torch.Tensor) else torch.device("cpu")
         on_dev = dev.type == "cuda"
         pos = _f32(pos, dev)
@@ -355,15 +375,15 @@ class Plan:
             g_energy = g_energy.to(dev).contiguous()
         n = int(pos.shape[0])
         alloc = dict(device=dev, pin_memory=True) if not on_dev else dict(device=dev)
-        gp = torch.empty((n, 3), dtype=torch.float32, **alloc)
-        gq = torch.empty(n, dtype=torch.float32, **alloc)
-        gm = torch.empty((n, 3), dtype=torch.float32, **alloc)
+        want = {"gp": ((n, 3), torch.float32), "gq": ((n,), torch.float32), "gm": ((n, 3), torch.float32)}
+        o = _outputs(want, None if out is None else dict(zip(("gp", "gq", "gm"), out)), alloc, dev)
+        gp, gq, gm = o["gp"], o["gq"], o["gm"]
         with _on_device(self.device):
             st = self.lib.pme_backward(self.handle, _stream_handle(self.device), n, _ptr(pos), _ptr(q),
                                        _ptr(mu), _ptr(g_energy), _ptr(g_force), _ptr(g_phi),
                                        _ptr(g_field), _ptr(gp), _ptr(gq), _ptr(gm))
             self._check(st, "pme_backward")
-            if not on_dev:
+            if not on_dev and sync:
                 torch.cuda.current_stream(self.device).synchronize()
         return gp, gq, gm
 

@@ -106,6 +106,25 @@ def test_forward_deterministic_and_host_pointer_path(gb):
     o4 = plan.forward(*[x.cpu() for x in t], field_grad=True)
     for k in o1:
         assert torch.equal(o1[k].cpu(), o4[k]), k
+    # the caller's pinned output buffers, the forward not synchronised: its outputs are complete
+    # once the backward that follows on the same stream has synchronised
+    n = len(q)
+    fo = {k: torch.empty_like(v.cpu()).pin_memory() for k, v in o1.items()}
+    bo = tuple(torch.empty(s, dtype=torch.float32).pin_memory() for s in [(n, 3), (n,), (n, 3)])
+    rng = np.random.default_rng(3)
+    cot = [torch.tensor(np.float32(rng.normal(size=sh))) for sh in [(n, 3), (n,), (n, 3)]]
+    gE = torch.tensor([0.4], dtype=torch.float64)
+    ref_b = plan.backward(*t, gE.cuda(), *[c.cuda() for c in cot])
+    for _ in range(2):   # the second pair of calls replays the recorded pass graphs
+        o5 = plan.forward(*h, field_grad=True, out=fo, sync=False)
+        b5 = plan.backward(*h, gE.pin_memory(), *[c.pin_memory() for c in cot], out=bo, sync=True)
+        assert all(o5[k] is fo[k] for k in fo) and all(x is y for x, y in zip(b5, bo))
+        for k in o1:
+            assert torch.equal(o1[k].cpu(), fo[k]), k
+        for x, y in zip(ref_b, bo):
+            assert torch.equal(x.cpu(), y)
+    with pytest.raises(ValueError):
+        plan.forward(*h, out={"force": torch.empty((n, 2)).pin_memory()})
 
 
 def test_charges_only_and_empty(gb):
