@@ -188,10 +188,54 @@ static bool is_device_pointer(const void* ptr) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Where a caller pointer lives: 0 device (or managed) memory, 1 pinned host memory the device
+// can address (*dev: that address), 2 other host memory.
+static int pointer_kind(const void* ptr, const void** dev) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return 2;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return 0;
+  if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+    *dev = at.devicePointer;
+    return 1;
+  }
+  return 2;
+}
+
 enum StageSlot {
   kPos = 0, kQ = 3, kMu = 4, kGF = 7, kGPhi = 10, kGField = 11, kOF = 14, kOPhi = 17,
   kOField = 18, kOFG = 21, kOGPos = 27, kOGQ = 30, kOGMu = 31, kTheta = 34, kOGTheta = 40, kStageFloats = 46
 };
+
+// The arrays of one staging direction moved by a single kernel (pinned host memory is
+// addressable by the device): lengths in floats (float64 arrays count two per value).
+constexpr int kMaxStageCopies = 12;
+struct StageCopies {
+  const float* src[kMaxStageCopies];
+  float* dst[kMaxStageCopies];
+  long long len[kMaxStageCopies];
+  int count;
+};
+
+__global__ void __launch_bounds__(256) k_stage_copy(StageCopies c) {
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int k = 0; k < c.count; ++k) {   // uniform
+    const float* src = c.src[k];
+    float* dst = c.dst[k];
+    const long long len = c.len[k];
+    if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0) {
+      const long long n4 = len / 4;
+      for (long long i = t0; i < n4; i += stride)
+        reinterpret_cast<float4*>(dst)[i] = reinterpret_cast<const float4*>(src)[i];
+      for (long long i = 4 * n4 + t0; i < len; i += stride) dst[i] = src[i];
+    } else {
+      for (long long i = t0; i < len; i += stride) dst[i] = src[i];
+    }
+  }
+}
 
 struct Staging {
   pme_plan_t p;
@@ -203,18 +247,53 @@ struct Staging {
     const void* dev;
     size_t bytes;
   };
-  std::vector<Pending> outs;
+  std::vector<Pending> outs;   // pageable host outputs (copied with cudaMemcpyAsync)
+  StageCopies in_k{}, out_k{};   // pinned host arrays (moved by k_stage_copy)
   bool staged = false;   // some argument is a host pointer
 
   Staging(pme_plan_t p_, cudaStream_t s_, int n_) : p(p_), s(s_), n(n_) {}
+
+  // one host input of `bytes` into device staging d: by the copy kernel when pinned (and
+  // there is room in its table), else by cudaMemcpyAsync
+  void stage_in(const void* ptr, void* d, size_t bytes) {
+    const void* dp = nullptr;
+    if (bytes % 4 == 0 && in_k.count < kMaxStageCopies && pointer_kind(ptr, &dp) == 1) {
+      in_k.src[in_k.count] = static_cast<const float*>(dp);
+      in_k.dst[in_k.count] = static_cast<float*>(d);
+      in_k.len[in_k.count] = (long long)(bytes / 4);
+      ++in_k.count;
+      return;
+    }
+    if (bytes && status == PME_OK)
+      status = check_cuda(p, cudaMemcpyAsync(d, ptr, bytes, cudaMemcpyHostToDevice, s), "stage input");
+  }
+  void stage_out(void* ptr, const void* d, size_t bytes) {
+    const void* dp = nullptr;
+    if (bytes % 4 == 0 && out_k.count < kMaxStageCopies && pointer_kind(ptr, &dp) == 1) {
+      out_k.src[out_k.count] = static_cast<const float*>(d);
+      out_k.dst[out_k.count] = const_cast<float*>(static_cast<const float*>(dp));
+      out_k.len[out_k.count] = (long long)(bytes / 4);
+      ++out_k.count;
+      return;
+    }
+    outs.push_back({ptr, d, bytes});
+  }
+  int launch_copies(const StageCopies& c) {
+    long long total = 0;
+    for (int k = 0; k < c.count; ++k) total += c.len[k];
+    if (total == 0 || status != PME_OK) return status;
+    const long long want = (total / 4 + 255) / 256;
+    const int grid = int(std::max(1LL, std::min<long long>(want, 4LL * device_sm_count())));
+    k_stage_copy<<<grid, 256, 0, s>>>(c);
+    count_launch();
+    return status = check_launch(p, "k_stage_copy");
+  }
 
   const float* in(const float* ptr, int width, int slot) {
     if (!ptr || is_device_pointer(ptr)) return ptr;
     staged = true;
     float* d = p->stage_f + size_t(slot) * p->max_ions;
-    const size_t bytes = sizeof(float) * size_t(width) * n;
-    if (bytes && status == PME_OK)
-      status = check_cuda(p, cudaMemcpyAsync(d, ptr, bytes, cudaMemcpyHostToDevice, s), "stage input");
+    stage_in(ptr, d, sizeof(float) * size_t(width) * n);
     return d;
   }
   // count doubles (per-frame energies / cotangents / virials); slot 0 = outputs, 1 = inputs,
@@ -223,26 +302,32 @@ struct Staging {
     if (!ptr || is_device_pointer(ptr)) return ptr;
     staged = true;
     double* d = p->stage_d + size_t(slot) * p->nframes;
-    if (status == PME_OK)
-      status = check_cuda(p, cudaMemcpyAsync(d, ptr, sizeof(double) * count, cudaMemcpyHostToDevice, s),
-                          "stage input");
+    stage_in(ptr, d, sizeof(double) * count);
     return d;
   }
   float* out(float* ptr, int width, int slot) {
     if (!ptr || is_device_pointer(ptr)) return ptr;
     staged = true;
     float* d = p->stage_f + size_t(slot) * p->max_ions;
-    outs.push_back({ptr, d, sizeof(float) * size_t(width) * n});
+    stage_out(ptr, d, sizeof(float) * size_t(width) * n);
     return d;
   }
   double* out_d(double* ptr, int count, int slot) {
     if (!ptr || is_device_pointer(ptr)) return ptr;
     staged = true;
     double* d = p->stage_d + size_t(slot) * p->nframes;
-    outs.push_back({ptr, d, sizeof(double) * count});
+    stage_out(ptr, d, sizeof(double) * count);
     return d;
   }
+  // after every in() / out(): the pinned inputs' copy kernel, and the status so far
+  int ready() {
+    if (status == PME_OK && in_k.count) launch_copies(in_k);
+    in_k.count = 0;
+    return status;
+  }
   int finish() {
+    if (status == PME_OK && out_k.count) launch_copies(out_k);
+    out_k.count = 0;
     for (auto& o : outs) {
       if (status != PME_OK) break;
       if (o.bytes)
@@ -1367,7 +1452,7 @@ int pme_forward(pme_plan_t p, void* stream, int n, const float* pos, const float
   float* p_out = sg.out(phi, 1, kOPhi);
   float* fl_out = sg.out(field, 3, kOField);
   float* fg_out = sg.out(field_grad, 6, kOFG);
-  if (sg.status) return sg.status;
+  if ((st = sg.ready())) return st;
   const PassKey key = make_key({0ull, (unsigned long long)n, ptr_bits(in.pos), ptr_bits(in.q), ptr_bits(in.mu),
                                 ptr_bits(e_out), ptr_bits(f_out), ptr_bits(p_out), ptr_bits(fl_out),
                                 ptr_bits(fg_out)});
@@ -1401,7 +1486,7 @@ int pme_forward_virial(pme_plan_t p, void* stream, int n, const float* pos, cons
   float* p_out = sg.out(phi, 1, kOPhi);
   float* fl_out = sg.out(field, 3, kOField);
   float* fg_out = sg.out(field_grad, 6, kOFG);
-  if (sg.status) return sg.status;
+  if ((st = sg.ready())) return st;
   if ((st = run_forward(p, s, in, e_out, f_out, p_out, fl_out, fg_out, v_out))) return st;
   return sg.finish();
 }
@@ -1495,7 +1580,7 @@ int pme_forward_quad(pme_plan_t p, void* stream, int n, const float* pos, const 
   float* p_out = sg.out(phi, 1, kOPhi);
   float* fl_out = sg.out(field, 3, kOField);
   float* fg_out = sg.out(field_grad, 6, kOFG);
-  if (sg.status) return sg.status;
+  if ((st = sg.ready())) return st;
   if ((st = run_forward_quad(p, s, in, e_out, f_out, p_out, fl_out, fg_out))) return st;
   return sg.finish();
 }
@@ -1523,7 +1608,7 @@ int pme_batch_forward_quad(pme_plan_t p, void* stream, const float* pos, const f
   float* p_out = sg.out(phi, 1, kOPhi);
   float* fl_out = sg.out(field, 3, kOField);
   float* fg_out = sg.out(field_grad, 6, kOFG);
-  if (sg.status) return sg.status;
+  if ((st = sg.ready())) return st;
   if ((st = run_forward_quad(p, s, in, e_out, f_out, p_out, fl_out, fg_out))) return st;
   return sg.finish();
 }
@@ -1602,7 +1687,7 @@ static int backward_quad_common(pme_plan_t p, void* stream, int n, const float* 
   float* o_q = sg.out(grad_q, 1, kOGQ);
   float* o_mu = sg.out(grad_mu, 3, kOGMu);
   float* o_th = sg.out(grad_theta, 6, kOGTheta);
-  if (sg.status) return sg.status;
+  if ((st = sg.ready())) return st;
   if ((st = run_backward_quad(p, s, in, gE, o_pos, o_q, o_mu, o_th))) return st;
   return sg.finish();
 }
@@ -1651,7 +1736,7 @@ int pme_backward(pme_plan_t p, void* stream, int n, const float* pos, const floa
   float* o_pos = sg.out(grad_pos, 3, kOGPos);
   float* o_q = sg.out(grad_q, 1, kOGQ);
   float* o_mu = sg.out(grad_mu, 3, kOGMu);
-  if (sg.status) return sg.status;
+  if ((st = sg.ready())) return st;
   const PassKey key = make_key({1ull, (unsigned long long)n, ptr_bits(in.pos), ptr_bits(in.q), ptr_bits(in.mu),
                                 ptr_bits(gE), ptr_bits(in.gforce), ptr_bits(in.gphi), ptr_bits(in.gfield),
                                 ptr_bits(o_pos), ptr_bits(o_q), ptr_bits(o_mu),
@@ -1686,7 +1771,7 @@ int pme_batch_forward(pme_plan_t p, void* stream, const float* pos, const float*
   float* p_out = sg.out(phi, 1, kOPhi);
   float* fl_out = sg.out(field, 3, kOField);
   float* fg_out = sg.out(field_grad, 6, kOFG);
-  if (sg.status) return sg.status;
+  if ((st = sg.ready())) return st;
   const PassKey key = make_key({0ull, (unsigned long long)n, ptr_bits(in.pos), ptr_bits(in.q), ptr_bits(in.mu),
                                 ptr_bits(e_out), ptr_bits(f_out), ptr_bits(p_out), ptr_bits(fl_out),
                                 ptr_bits(fg_out)});
@@ -1720,7 +1805,7 @@ int pme_batch_forward_virial(pme_plan_t p, void* stream, const float* pos, const
   float* p_out = sg.out(phi, 1, kOPhi);
   float* fl_out = sg.out(field, 3, kOField);
   float* fg_out = sg.out(field_grad, 6, kOFG);
-  if (sg.status) return sg.status;
+  if ((st = sg.ready())) return st;
   if ((st = run_forward(p, s, in, e_out, f_out, p_out, fl_out, fg_out, v_out))) return st;
   return sg.finish();
 }
@@ -1745,7 +1830,7 @@ int pme_batch_backward(pme_plan_t p, void* stream, const float* pos, const float
   float* o_pos = sg.out(grad_pos, 3, kOGPos);
   float* o_q = sg.out(grad_q, 1, kOGQ);
   float* o_mu = sg.out(grad_mu, 3, kOGMu);
-  if (sg.status) return sg.status;
+  if ((st = sg.ready())) return st;
   const PassKey key = make_key({1ull, (unsigned long long)n, ptr_bits(in.pos), ptr_bits(in.q), ptr_bits(in.mu),
                                 ptr_bits(gE), ptr_bits(in.gforce), ptr_bits(in.gphi), ptr_bits(in.gfield),
                                 ptr_bits(o_pos), ptr_bits(o_q), ptr_bits(o_mu),
