@@ -86,6 +86,7 @@ __device__ __forceinline__ float bg_factor(const CombineArgs& a, const FrameDesc
 
 template <bool BATCH>
 __global__ void __launch_bounds__(kCombThreads) k_combine_forward(CombineArgs a) {
+  pdl_begin();
   static_assert(kRedItem == kCombThreads, "one ion per thread");
   const int item = blockIdx.x;
   const int f = BATCH ? a.maps.item_frame[item] : 0;
@@ -218,6 +219,7 @@ __global__ void __launch_bounds__(kCombThreads) k_combine_forward(CombineArgs a)
 
 template <bool BATCH>
 __global__ void __launch_bounds__(kCombThreads) k_combine_backward(CombineArgs a) {
+  pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.in.n) return;
   const int f = BATCH ? a.maps.ion_frame[i] : 0;
@@ -402,8 +404,8 @@ int launch_combine_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, bo
     a.one.nitems = std::max(1, (in.n + kRedItem - 1) / kRedItem);
     items = a.one.nitems;
   }
-  if (p->batch) k_combine_forward<true><<<items, kCombThreads, 0, s>>>(a);
-  else k_combine_forward<false><<<items, kCombThreads, 0, s>>>(a);
+  if (p->batch) pdl_launch(k_combine_forward<true>, items, kCombThreads, 0, s, a);
+  else pdl_launch(k_combine_forward<false>, items, kCombThreads, 0, s, a);
   count_launch();
   return check_launch(p, "k_combine_forward");
 }
@@ -422,8 +424,8 @@ int launch_combine_backward(pme_plan_t p, cudaStream_t s, const IonInputs& in,
   a.grad_mu = grad_mu;
   const int grid = (in.n + kCombThreads - 1) / kCombThreads;
   if (grid == 0) return PME_OK;
-  if (p->batch) k_combine_backward<true><<<grid, kCombThreads, 0, s>>>(a);
-  else k_combine_backward<false><<<grid, kCombThreads, 0, s>>>(a);
+  if (p->batch) pdl_launch(k_combine_backward<true>, grid, kCombThreads, 0, s, a);
+  else pdl_launch(k_combine_backward<false>, grid, kCombThreads, 0, s, a);
   count_launch();
   return check_launch(p, "k_combine_backward");
 }

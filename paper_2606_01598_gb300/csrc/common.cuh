@@ -29,6 +29,33 @@ void count_launch();
 // grid-stride kernels are sized in multiples of it).
 int device_sm_count();
 
+// Programmatic dependent launch (sm_90 and later): a kernel launched with pdl_launch may be
+// scheduled while the previous kernel of its stream is finishing; it must call pdl_begin()
+// before touching global memory. pdl_begin waits until the preceding grids have completed and
+// their memory is visible (griddepcontrol.wait), then lets the next grid be scheduled
+// (griddepcontrol.launch_dependents), so consecutive kernels of a pass overlap only in their
+// launch and scheduling, never in their memory accesses. Outside such a launch both are no-ops.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ----------------------------------------------------------------------------------------
 // geometry shared by all kernels of one plan (passed by value)
 // ----------------------------------------------------------------------------------------

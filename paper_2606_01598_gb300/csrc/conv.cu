@@ -286,6 +286,7 @@ __device__ __forceinline__ const FrameDesc& plane_block(const ConvArgs& a, int& 
 //      all planes side by side, so one transform along y covers them)
 template <bool BATCH>
 __global__ void __launch_bounds__(kConvPlaneThreads) k_conv_r2c(ConvArgs a) {
+  pdl_begin();
   extern __shared__ __align__(16) float2 csm[];
   int copy, x0, pc;
   const FrameDesc& F = plane_block<BATCH>(a, copy, x0, pc);
@@ -362,6 +363,7 @@ __global__ void __launch_bounds__(kConvPlaneThreads) k_conv_r2c(ConvArgs a) {
 
 template <bool BATCH>
 __global__ void __launch_bounds__(kConvPlaneThreads) k_conv_c2r(ConvArgs a) {
+  pdl_begin();
   extern __shared__ __align__(16) float2 csm[];
   int copy, x0, pc;
   const FrameDesc& F = plane_block<BATCH>(a, copy, x0, pc);
@@ -443,6 +445,7 @@ __global__ void __launch_bounds__(kConvPlaneThreads) k_conv_c2r(ConvArgs a) {
 
 template <bool BATCH, bool VIR>
 __global__ void __launch_bounds__(kConvBThreads) k_conv_x(ConvArgs a) {
+  pdl_begin();
   extern __shared__ __align__(16) float2 csm[];
   const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, BATCH ? a.maps.blk_frame[blockIdx.x] : 0);
   const Geometry& g = F.g;
@@ -777,6 +780,7 @@ __device__ __forceinline__ void c2r_plane_p2(const float2* __restrict__ src, flo
 
 template <bool BATCH>
 __global__ void __launch_bounds__(kP2PlaneThreads, 1) k_conv_r2c_p2(ConvArgs a) {
+  pdl_begin();
   extern __shared__ __align__(16) float2 csm[];
   int copy, x0, pc;
   const FrameDesc& F = plane_block<BATCH>(a, copy, x0, pc);
@@ -794,6 +798,7 @@ __global__ void __launch_bounds__(kP2PlaneThreads, 1) k_conv_r2c_p2(ConvArgs a) 
 
 template <bool BATCH>
 __global__ void __launch_bounds__(kP2PlaneThreads, 1) k_conv_c2r_p2(ConvArgs a) {
+  pdl_begin();
   extern __shared__ __align__(16) float2 csm[];
   int copy, x0, pc;
   const FrameDesc& F = plane_block<BATCH>(a, copy, x0, pc);
@@ -929,6 +934,7 @@ __device__ __forceinline__ void x_tile_p2(const ConvArgs& a, const FrameDesc& F,
 
 template <bool BATCH, bool VIR>
 __global__ void __launch_bounds__(kConvBThreads) k_conv_x_p2(ConvArgs a) {
+  pdl_begin();
   extern __shared__ __align__(16) float2 csm[];
   const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, BATCH ? a.maps.blk_frame[blockIdx.x] : 0);
   const int c0 = (blockIdx.x - F.infl_blk_off) * kP2Cols;
@@ -1051,11 +1057,11 @@ int launch_conv_forward(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh,
     if (p->batch) {
       static unsigned done = 0;
       if ((st = set_smem(p, k_conv_r2c_p2<true>, done))) return st;
-      k_conv_r2c_p2<true><<<grid, kP2PlaneThreads, p->conv_smem_plane, s>>>(a);
+      pdl_launch(k_conv_r2c_p2<true>, grid, kP2PlaneThreads, p->conv_smem_plane, s, a);
     } else {
       static unsigned done = 0;
       if ((st = set_smem(p, k_conv_r2c_p2<false>, done))) return st;
-      k_conv_r2c_p2<false><<<grid, kP2PlaneThreads, p->conv_smem_plane, s>>>(a);
+      pdl_launch(k_conv_r2c_p2<false>, grid, kP2PlaneThreads, p->conv_smem_plane, s, a);
     }
     count_launch();
     return check_launch(p, "k_conv_r2c_p2");
@@ -1063,11 +1069,11 @@ int launch_conv_forward(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh,
   if (p->batch) {
     static unsigned done = 0;
     if ((st = set_smem(p, k_conv_r2c<true>, done))) return st;
-    k_conv_r2c<true><<<grid, p->conv_threads, p->conv_smem_plane, s>>>(a);
+    pdl_launch(k_conv_r2c<true>, grid, p->conv_threads, p->conv_smem_plane, s, a);
   } else {
     static unsigned done = 0;
     if ((st = set_smem(p, k_conv_r2c<false>, done))) return st;
-    k_conv_r2c<false><<<grid, p->conv_threads, p->conv_smem_plane, s>>>(a);
+    pdl_launch(k_conv_r2c<false>, grid, p->conv_threads, p->conv_smem_plane, s, a);
   }
   count_launch();
   return check_launch(p, "k_conv_r2c");
@@ -1088,11 +1094,11 @@ int launch_conv_inverse(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh,
     if (p->batch) {
       static unsigned done = 0;
       if ((st = set_smem(p, k_conv_c2r_p2<true>, done))) return st;
-      k_conv_c2r_p2<true><<<grid, kP2PlaneThreads, p->conv_smem_plane, s>>>(a);
+      pdl_launch(k_conv_c2r_p2<true>, grid, kP2PlaneThreads, p->conv_smem_plane, s, a);
     } else {
       static unsigned done = 0;
       if ((st = set_smem(p, k_conv_c2r_p2<false>, done))) return st;
-      k_conv_c2r_p2<false><<<grid, kP2PlaneThreads, p->conv_smem_plane, s>>>(a);
+      pdl_launch(k_conv_c2r_p2<false>, grid, kP2PlaneThreads, p->conv_smem_plane, s, a);
     }
     count_launch();
     return check_launch(p, "k_conv_c2r_p2");
@@ -1100,11 +1106,11 @@ int launch_conv_inverse(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh,
   if (p->batch) {
     static unsigned done = 0;
     if ((st = set_smem(p, k_conv_c2r<true>, done))) return st;
-    k_conv_c2r<true><<<grid, p->conv_threads, p->conv_smem_plane, s>>>(a);
+    pdl_launch(k_conv_c2r<true>, grid, p->conv_threads, p->conv_smem_plane, s, a);
   } else {
     static unsigned done = 0;
     if ((st = set_smem(p, k_conv_c2r<false>, done))) return st;
-    k_conv_c2r<false><<<grid, p->conv_threads, p->conv_smem_plane, s>>>(a);
+    pdl_launch(k_conv_c2r<false>, grid, p->conv_threads, p->conv_smem_plane, s, a);
   }
   count_launch();
   return check_launch(p, "k_conv_c2r");
@@ -1125,13 +1131,13 @@ int launch_conv_influence(pme_plan_t p, cudaStream_t s, bool tangent, double* pa
   do {                                                                   \
     static unsigned done = 0;                                            \
     if ((st = set_smem(p, k_conv_x<B, V>, done))) return st;             \
-    k_conv_x<B, V><<<grid, kConvBThreads, smem, s>>>(a);                 \
+    pdl_launch(k_conv_x<B, V>, grid, kConvBThreads, smem, s, a);                 \
   } while (0)
 #define GB_CONV_X_P2(B, V)                                               \
   do {                                                                   \
     static unsigned done = 0;                                            \
     if ((st = set_smem(p, k_conv_x_p2<B, V>, done))) return st;          \
-    k_conv_x_p2<B, V><<<grid, kConvBThreads, smem, s>>>(a);              \
+    pdl_launch(k_conv_x_p2<B, V>, grid, kConvBThreads, smem, s, a);              \
   } while (0)
   if (p->conv_p2) {
     if (p->batch) {

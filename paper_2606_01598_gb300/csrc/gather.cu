@@ -79,6 +79,7 @@ __host__ __device__ constexpr int gather_tab_floats() {
 // MODE: 0 forward, 1 tangent, 2 quadrupole forward
 template <int P, int MODE, bool BATCH>
 __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
+  pdl_begin();
   constexpr bool TAN = MODE == 1;
   constexpr int DM = MODE == 0 ? 2 : 3;
   constexpr int IPW = gather_ions_per_warp<P>();
@@ -590,7 +591,7 @@ int launch_t(pme_plan_t p, cudaStream_t s, int n, const float* mesh, const doubl
   case PP: {                                                                                    \
     const size_t per_block = size_t(kGatherThreads / 32) * gather_ions_per_warp<PP>();          \
     const int grid = int((nion + per_block - 1) / per_block);                                   \
-    k_gather<PP, MODE, BATCH><<<grid, kGatherThreads, 0, s>>>(a);                               \
+    pdl_launch(k_gather<PP, MODE, BATCH>, grid, kGatherThreads, 0, s, a);                               \
     break;                                                                                      \
   }
     switch (G.order) {

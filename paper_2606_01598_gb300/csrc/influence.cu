@@ -36,6 +36,7 @@ template <bool BATCH, bool VIR>
 __global__ void __launch_bounds__(kInflThreads)
 k_influence(FrameDesc one, FrameMaps maps, float2* spec, int tangent, const float* dconv,
             float inv4a2, double* partials, double* vparts, const float* gtab) {
+  pdl_begin();
   const FrameDesc& F = frame_at<BATCH>(one, maps, BATCH ? maps.blk_frame[blockIdx.x] : 0);
   const Geometry& g = F.g;
   const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2];
@@ -136,6 +137,7 @@ __global__ void __launch_bounds__(kEnergyThreads)
 k_energy_final(FrameDesc one, FrameMaps maps, const double* parts, int recip_kind,
                const double* e_ion, const double* qsum, int with_bg, double alpha, double scale,
                double* eitem, int* ecount, double* out) {
+  pdl_begin();
   const int item = blockIdx.x;
   const int f = BATCH ? maps.item_frame[item] : 0;
   const FrameDesc& F = frame_at<BATCH>(one, maps, f);
@@ -289,11 +291,11 @@ int launch_influence(pme_plan_t p, cudaStream_t s, cufftComplex* spec, bool tang
   const int grid = p->batch ? p->total_blocks : one.infl_nblk;
   const int tg = tangent ? 1 : 0;
   if (p->batch) {
-    if (vparts) k_influence<true, true><<<grid, kInflThreads, 0, s>>>(one, p->maps, sp, tg, p->dconv_all, inv4a2, partials, vparts, p->gtab);
-    else k_influence<true, false><<<grid, kInflThreads, 0, s>>>(one, p->maps, sp, tg, p->dconv_all, inv4a2, partials, vparts, p->gtab);
+    if (vparts) pdl_launch(k_influence<true, true>, grid, kInflThreads, 0, s, one, p->maps, sp, tg, p->dconv_all, inv4a2, partials, vparts, p->gtab);
+    else pdl_launch(k_influence<true, false>, grid, kInflThreads, 0, s, one, p->maps, sp, tg, p->dconv_all, inv4a2, partials, vparts, p->gtab);
   } else {
-    if (vparts) k_influence<false, true><<<grid, kInflThreads, 0, s>>>(one, p->maps, sp, tg, p->dconv_all, inv4a2, partials, vparts, p->gtab);
-    else k_influence<false, false><<<grid, kInflThreads, 0, s>>>(one, p->maps, sp, tg, p->dconv_all, inv4a2, partials, vparts, p->gtab);
+    if (vparts) pdl_launch(k_influence<false, true>, grid, kInflThreads, 0, s, one, p->maps, sp, tg, p->dconv_all, inv4a2, partials, vparts, p->gtab);
+    else pdl_launch(k_influence<false, false>, grid, kInflThreads, 0, s, one, p->maps, sp, tg, p->dconv_all, inv4a2, partials, vparts, p->gtab);
   }
   count_launch();
   return check_launch(p, "k_influence");
@@ -310,11 +312,11 @@ int launch_energy_final(pme_plan_t p, cudaStream_t s, const double* parts, int r
   const double* e_ion = with_ions ? p->e_ion : nullptr;
   const int items = p->batch ? p->total_items : one.nitems;
   if (p->batch)
-    k_energy_final<true><<<items, kEnergyThreads, 0, s>>>(one, p->maps, parts, recip_kind, e_ion, p->sb.qsum,
+    pdl_launch(k_energy_final<true>, items, kEnergyThreads, 0, s, one, p->maps, parts, recip_kind, e_ion, p->sb.qsum,
                                                           with_bg ? 1 : 0, p->alpha, scale, p->eitem,
                                                           p->ecount, out);
   else
-    k_energy_final<false><<<items, kEnergyThreads, 0, s>>>(one, p->maps, parts, recip_kind, e_ion, p->sb.qsum,
+    pdl_launch(k_energy_final<false>, items, kEnergyThreads, 0, s, one, p->maps, parts, recip_kind, e_ion, p->sb.qsum,
                                                            with_bg ? 1 : 0, p->alpha, scale, p->eitem,
                                                            p->ecount, out);
   count_launch();

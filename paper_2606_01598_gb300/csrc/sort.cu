@@ -104,6 +104,7 @@ template <bool BATCH>
 __global__ void __launch_bounds__(kSortThreads)
 k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int tangent, int* flags,
       int nbricks, int ncells, const int* reuse, float* save, int ld) {
+  pdl_begin();
   static_assert(kRedItem == kSortThreads, "one ion per thread");
   const int item = blockIdx.x;
   const int f = BATCH ? maps.item_frame[item] : 0;
@@ -215,6 +216,7 @@ k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int tangent, 
 // Segment starts from the final counts: block 0 scans the brick counts, block 1 the cell
 // counts (1024 threads each). Skipped on reuse.
 __global__ void __launch_bounds__(1024) k_scan(SortBuffers sb, int nbricks, int ncells, const int* reuse) {
+  pdl_begin();
   if (reuse && *reuse == 0) return;
   if (blockIdx.x == 0) block_exclusive_scan(sb.count_b, sb.start_b, nbricks);
   else block_exclusive_scan(sb.count_c, sb.start_c, ncells);
@@ -222,6 +224,7 @@ __global__ void __launch_bounds__(1024) k_scan(SortBuffers sb, int nbricks, int 
 
 __global__ void __launch_bounds__(kSortThreads)
 k_scatter(int n, SortBuffers sb, int need_mesh, int need_pair, const int* reuse) {
+  pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || (reuse && *reuse == 0)) return;
   if (need_mesh) {
@@ -247,6 +250,7 @@ template <bool BATCH>
 __global__ void __launch_bounds__(kSortThreads)
 k_rank_records(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, MeshRecords mr,
                PairRecords pr, int tangent, int need_mesh, int need_pair, const int* reuse) {
+  pdl_begin();
   const int n = in.n;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   const bool mesh_side = t < n;
@@ -403,6 +407,7 @@ k_rank_records(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, Mesh
 __global__ void __launch_bounds__(256)
 k_input_check(int n, IonInputs in, const float* saved, int ld, const int* list_cnt, int* in_diff,
               int* cache_bad) {
+  pdl_begin();
   bool same = true, lists = true;
   const int stride = gridDim.x * blockDim.x;
   const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -446,7 +451,7 @@ int launch_sort_t(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangen
   }
   {
     const int items = BATCH ? p->total_items : one.nitems;
-    k_bin<BATCH><<<items, kSortThreads, 0, s>>>(one, p->maps, in, p->sb, tangent ? 1 : 0, p->flags,
+    pdl_launch(k_bin<BATCH>, items, kSortThreads, 0, s, one, p->maps, in, p->sb, tangent ? 1 : 0, p->flags,
                                                 p->total_bricks, p->total_cells, reuse, save,
                                                 p->max_ions);
     count_launch();
@@ -454,7 +459,7 @@ int launch_sort_t(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangen
       p->counts_clean = false;
       return st;
     }
-    k_scan<<<2, 1024, 0, s>>>(p->sb, p->total_bricks, p->total_cells, reuse);
+    pdl_launch(k_scan, 2, 1024, 0, s, p->sb, p->total_bricks, p->total_cells, reuse);
     count_launch();
     if ((st = check_launch(p, "k_scan"))) {
       p->counts_clean = false;
@@ -462,11 +467,11 @@ int launch_sort_t(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool tangen
     }
   }
   if (nblk > 0) {
-    k_scatter<<<nblk, kSortThreads, 0, s>>>(n, p->sb, need_mesh ? 1 : 0, need_pair ? 1 : 0, reuse);
+    pdl_launch(k_scatter, nblk, kSortThreads, 0, s, n, p->sb, need_mesh ? 1 : 0, need_pair ? 1 : 0, reuse);
     count_launch();
     if ((st = check_launch(p, "k_scatter"))) return st;
     const int nblk2 = (2 * n + kSortThreads - 1) / kSortThreads;
-    k_rank_records<BATCH><<<nblk2, kSortThreads, 0, s>>>(one, p->maps, in, p->sb, p->mr, p->pr,
+    pdl_launch(k_rank_records<BATCH>, nblk2, kSortThreads, 0, s, one, p->maps, in, p->sb, p->mr, p->pr,
                                                          tangent ? 1 : 0, need_mesh ? 1 : 0,
                                                          need_pair ? 1 : 0, reuse);
     count_launch();
@@ -481,7 +486,7 @@ int launch_input_check(pme_plan_t p, cudaStream_t s, const IonInputs& in, bool w
   int st = check_cuda(p, cudaMemsetAsync(p->in_flags, 0, 2 * sizeof(int), s), "memset");
   if (st || in.n == 0) return st;
   const int grid = std::min(4 * device_sm_count(), (3 * in.n + 255) / 256);
-  k_input_check<<<grid, 256, 0, s>>>(in.n, in, p->in_saved, p->max_ions, with_lists ? p->plist_cnt : nullptr,
+  pdl_launch(k_input_check, grid, 256, 0, s, in.n, in, p->in_saved, p->max_ions, with_lists ? p->plist_cnt : nullptr,
                                       p->in_diff, p->cache_bad);
   count_launch();
   return check_launch(p, "k_input_check");

@@ -91,6 +91,7 @@ __device__ __forceinline__ int up_dist(int a, int b, int n) {
 // MODE: 0 forward, 1 tangent, 2 quadrupole forward, 3 quadrupole tangent (d rho only)
 template <class SH, int P, int MODE, bool BATCH>
 __global__ void __launch_bounds__(SH::NT) k_spread(SpreadArgs a) {
+  pdl_begin();
   constexpr int BX = SH::BX, BY = SH::BY, BZ = SH::BZ, NSEG = SH::NSEG, NT = SH::NT, CAP = SH::CAP,
                 NW = SH::NW, SL = SH::SL;
   constexpr bool TAN = MODE != 0;   // a second accumulator (d rho, or rho of the quadrupole modes)
@@ -516,7 +517,7 @@ int launch_order(pme_plan_t p, cudaStream_t s, int grid, const SpreadArgs& a) {
     if (st) return st;
     if (dev < 32) done_mask |= 1 << dev;
   }
-  k_spread<SH, P, MODE, BATCH><<<grid, SH::NT, bytes, s>>>(a);
+  pdl_launch(k_spread<SH, P, MODE, BATCH>, grid, SH::NT, bytes, s, a);
   return PME_OK;
 }
 
