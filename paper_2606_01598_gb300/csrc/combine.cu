@@ -94,7 +94,8 @@ __global__ void __launch_bounds__(kCombThreads) k_combine_forward(CombineArgs a)
   int lo, hi;
   item_range(F, item, lo, hi);
   const int i = lo + int(threadIdx.x);
-  double e_i = 0.0;
+  double e_i = 0.0;   // quadrupole terms (float64)
+  float e_f = 0.f;    // pair and self terms
   float vi[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // virial terms of ion i
   if (i < hi && index_ok(i, a.in.n)) {
     const float bg = bg_factor(a, F);
@@ -164,10 +165,11 @@ __global__ void __launch_bounds__(kCombThreads) k_combine_forward(CombineArgs a)
       a.force[3 * i + 1] = a.in.theta ? F1q : F1;
       a.force[3 * i + 2] = a.in.theta ? F2q : F2;
     }
-    const double mu2 = double(mu[0]) * mu[0] + double(mu[1]) * mu[1] + double(mu[2]) * mu[2];
-    e_i += 0.5 * (double(qi) * w[0] + double(mu[0]) * w[1] + double(mu[1]) * w[2] +
-                  double(mu[2]) * w[3]) -
-           a.e_self_q * double(qi) * qi - a.e_self_mu * mu2;
+    // the ion's pair and self energy in float32 (float64 across the block's warps below; the
+    // per-ion float64 arithmetic kept the float64 pipe a third busy)
+    const float mu2 = mu[0] * mu[0] + mu[1] * mu[1] + mu[2] * mu[2];
+    e_f = 0.5f * (qi * w[0] + mu[0] * w[1] + mu[1] * w[2] + mu[2] * w[3]) - float(a.e_self_q) * qi * qi -
+          float(a.e_self_mu) * mu2;
     if (a.virial_out) {
 #pragma unroll
       for (int r = 0; r < 3; ++r)
@@ -184,7 +186,7 @@ __global__ void __launch_bounds__(kCombThreads) k_combine_forward(CombineArgs a)
     }
   }
   if (!a.energy_out) return;   // uniform
-  const double e_item = block_sum_d(e_i);
+  const double e_item = block_sum_f(e_f) + (a.in.theta ? block_sum_d(e_i) : 0.0);
   if (threadIdx.x == 0) a.eitem[item] = e_item;
   if (!last_item_done(a.ecount + f, F.nitems)) return;
   double rp = a.recip_kind ? strided_sum_d(a.recip_parts + F.infl_blk_off, F.infl_nblk) : 0.0;
