@@ -219,8 +219,6 @@ __global__ void __launch_bounds__(SH::NT) k_spread(SpreadArgs a) {
         float* rec = sw + tid * RC::STR;
         float w[DW][P];
         spline_weights<P, DW - 1>(fq.x, w);
-#pragma unroll
-        for (int k = 0; k < BX * RC::NXV; ++k) rec[RC::XOFF + k] = 0.f;
         const float q = fq.w, mx = dm.x, my = dm.y, mz = dm.z;
         float c4 = 0.f, c5 = 0.f, c6 = 0.f, c7 = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
         // quadrupole mode: Theta' = D^T Theta D (mesh coordinates) as xx, 2 xy, yy, 2 xz, 2 yz, zz
@@ -310,7 +308,9 @@ __global__ void __launch_bounds__(SH::NT) k_spread(SpreadArgs a) {
           ty = tt.y;
           tz = tt.z;
         }
-        // stencil index j sits in brick column (j - rx) mod Nx
+        // stencil index j sits in brick column (j - rx) mod Nx. Only the columns (and rows) the
+        // ion's stencil covers are written: the accumulation reads an entry only for an ion
+        // whose coverage bit of that column (row) is set
 #pragma unroll
         for (int j = 0; j < P; ++j) {
           int X = j - rx;
@@ -356,8 +356,6 @@ __global__ void __launch_bounds__(SH::NT) k_spread(SpreadArgs a) {
           }
         }
         spline_weights<P, DW - 1>(fq.y, w);
-#pragma unroll
-        for (int k = 0; k < BY * RC::NYV; ++k) rec[RC::YOFF + k] = 0.f;
 #pragma unroll
         for (int j = 0; j < P; ++j) {
           int Yr = j - ry;
