@@ -219,50 +219,6 @@ __global__ void __launch_bounds__(kCombThreads) k_combine_forward(CombineArgs a)
   }
 }
 
-template <bool BATCH>
-__global__ void __launch_bounds__(kCombThreads) k_combine_backward(CombineArgs a) {
-  pdl_begin();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.in.n) return;
-  const int f = BATCH ? a.maps.ion_frame[i] : 0;
-  const FrameDesc& F = frame_at<BATCH>(a.one, a.maps, f);
-  const float bg = bg_factor(a, F);
-  const float qi = a.in.q[i];
-  float mu[3] = {0.f, 0.f, 0.f}, dmu[3] = {0.f, 0.f, 0.f};
-  if (a.in.mu) {
-    mu[0] = a.in.mu[3 * i];
-    mu[1] = a.in.mu[3 * i + 1];
-    mu[2] = a.in.mu[3 * i + 2];
-  }
-  if (a.in.gfield) {
-    dmu[0] = -a.in.gfield[3 * i];
-    dmu[1] = -a.in.gfield[3 * i + 1];
-    dmu[2] = -a.in.gfield[3 * i + 2];
-  }
-  const float dq = a.in.gphi ? a.in.gphi[i] : 0.f;
-  const float gE = a.g_energy ? float(a.g_energy[f]) : 0.f;
-  float v[8], w[8];
-#pragma unroll
-  for (int t = 0; t < 8; ++t) {
-    v[t] = a.with_mesh ? a.mesh_out[size_t(i) * 8 + t] : 0.f;
-    w[t] = a.with_pair ? a.pair_out[size_t(i) * 8 + t] : 0.f;
-  }
-  const float Q = float(a.qsum[2 * f]), dQ = float(a.qsum[2 * f + 1]);
-  const float k = a.k;
-  if (a.grad_pos) {
-    a.grad_pos[3 * i] = k * (v[0] + w[0]);
-    a.grad_pos[3 * i + 1] = k * (v[1] + w[1]);
-    a.grad_pos[3 * i + 2] = k * (v[2] + w[2]);
-  }
-  if (a.grad_q)
-    a.grad_q[i] = k * (v[3] + w[3] - a.self_phi * (gE * qi + dq) - bg * (gE * Q + dQ));
-  if (a.grad_mu) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-      a.grad_mu[3 * i + c] = k * (v[4 + c] + w[4 + c] - a.self_c * (gE * mu[c] + dmu[c]));
-  }
-}
-
 // Quadrupole Hessian-vector product, per ion: from the mesh and pair parts' 13 gathered values
 // and their tangents (out[26]: phi, grad phi, grad^2 phi, Theta : grad^3 phi), the gradient of
 // E in (r, q, mu, Theta) and its directional derivative along v = (dr, dq, dmu) = (-g_force,
@@ -412,24 +368,24 @@ int launch_combine_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, bo
   return check_launch(p, "k_combine_forward");
 }
 
-int launch_combine_backward(pme_plan_t p, cudaStream_t s, const IonInputs& in,
-                            const double* g_energy, float* grad_pos, float* grad_q,
-                            float* grad_mu) {
-  CombineArgs a = base_args(p, in);
-  a.mesh_out = p->mesh_out;
-  a.pair_out = p->pair_out;
-  a.with_mesh = 1;
-  a.with_pair = p->opts.include_pair != 0;
-  a.g_energy = g_energy;
-  a.grad_pos = grad_pos;
-  a.grad_q = grad_q;
-  a.grad_mu = grad_mu;
-  const int grid = (in.n + kCombThreads - 1) / kCombThreads;
-  if (grid == 0) return PME_OK;
-  if (p->batch) pdl_launch(k_combine_backward<true>, grid, kCombThreads, 0, s, a);
-  else pdl_launch(k_combine_backward<false>, grid, kCombThreads, 0, s, a);
-  count_launch();
-  return check_launch(p, "k_combine_backward");
+BackwardFinish backward_finish_args(pme_plan_t p, const IonInputs& in, float* grad_pos, float* grad_q,
+                                    float* grad_mu) {
+  const CombineArgs a = base_args(p, in);
+  BackwardFinish f = {};
+  f.pair_out = p->opts.include_pair ? p->pair_out : nullptr;
+  f.q = in.q;
+  f.mu = in.mu;
+  f.gphi = in.gphi;
+  f.gfield = in.gfield;
+  f.qsum = a.qsum;
+  f.grad_pos = grad_pos;
+  f.grad_q = grad_q;
+  f.grad_mu = grad_mu;
+  f.k = a.k;
+  f.self_phi = a.self_phi;
+  f.self_c = a.self_c;
+  f.with_bg = a.with_bg;
+  return f;
 }
 
 int launch_combine_backward_quad(pme_plan_t p, cudaStream_t s, const IonInputs& in, const double* g_energy,

@@ -35,6 +35,8 @@ struct GatherArgs {
   const float* theta;     // quadrupole mode: Theta [caller index][6] (xx yy zz xy xz yz)
   float* qout;            // quadrupole mode: Theta : grad^3 phi at [caller index * 8 + 0..2]
   int t_lo, t_hi;         // sorted positions of this launch
+  int finish;             // tangent mode: write the backward's gradients (fin), not out
+  BackwardFinish fin;
 };
 
 __device__ __forceinline__ float group_sum(float v) {
@@ -331,15 +333,52 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs a) {
     apply_D(g.D, xm, gm);
     // grad_q = gE phi + dphi + g . t
     const float gq = gE * m000 + t000 + gx[0] * tv[0] + gx[1] * tv[1] + gx[2] * tv[2];
-    float* o = a.out + size_t(m.w) * 8;
-    o[0] = gr[0];
-    o[1] = gr[1];
-    o[2] = gr[2];
-    o[3] = gq;
-    o[4] = gm[0];
-    o[5] = gm[1];
-    o[6] = gm[2];
-    o[7] = 0.f;
+    if (a.finish) {
+      // the backward's final assembly: mesh part + pair part, self and background terms,
+      // coulomb_k
+      const BackwardFinish& fn = a.fin;
+      const int i = m.w;
+      const float v[7] = {gr[0], gr[1], gr[2], gq, gm[0], gm[1], gm[2]};
+      float w[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (fn.pair_out) {
+#pragma unroll
+        for (int c = 0; c < 7; ++c) w[c] = fn.pair_out[size_t(i) * 8 + c];
+      }
+      const float qi = fn.q[i];
+      float mu_i[3] = {0.f, 0.f, 0.f}, dmu[3] = {0.f, 0.f, 0.f};
+      if (fn.mu) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) mu_i[c] = fn.mu[3 * i + c];
+      }
+      if (fn.gfield) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dmu[c] = -fn.gfield[3 * i + c];
+      }
+      const float dqi = fn.gphi ? fn.gphi[i] : 0.f;
+      const float bg = fn.with_bg ? g.bg_fac : 0.f;
+      const float Q = float(fn.qsum[2 * frame]), dQ = float(fn.qsum[2 * frame + 1]);
+      const float k = fn.k;
+      if (fn.grad_pos) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) fn.grad_pos[3 * i + c] = k * (v[c] + w[c]);
+      }
+      if (fn.grad_q) fn.grad_q[i] = k * (v[3] + w[3] - fn.self_phi * (gE * qi + dqi) - bg * (gE * Q + dQ));
+      if (fn.grad_mu) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          fn.grad_mu[3 * i + c] = k * (v[4 + c] + w[4 + c] - fn.self_c * (gE * mu_i[c] + dmu[c]));
+      }
+    } else {
+      float* o = a.out + size_t(m.w) * 8;
+      o[0] = gr[0];
+      o[1] = gr[1];
+      o[2] = gr[2];
+      o[3] = gq;
+      o[4] = gm[0];
+      o[5] = gm[1];
+      o[6] = gm[2];
+      o[7] = 0.f;
+    }
   }
 #undef MOM
 #undef TMOM
@@ -570,7 +609,8 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather_qdual(GatherArgs a) {
 
 template <int MODE, bool BATCH>
 int launch_t(pme_plan_t p, cudaStream_t s, int n, const float* mesh, const double* g_energy,
-             float* out, const float* theta = nullptr, float* qout = nullptr) {
+             float* out, const float* theta = nullptr, float* qout = nullptr,
+             const BackwardFinish* fin = nullptr) {
   GatherArgs a;
   a.one = p->frames_h[0];
   a.maps = p->maps;
@@ -580,6 +620,8 @@ int launch_t(pme_plan_t p, cudaStream_t s, int n, const float* mesh, const doubl
   a.out = out;
   a.theta = theta;
   a.qout = qout;
+  a.finish = fin ? 1 : 0;
+  a.fin = fin ? *fin : BackwardFinish{};
   for (int gi = 0; gi < p->nogroups; ++gi) {
     const OrderGroup& G = p->ogroups[gi];
     a.t_lo = BATCH ? G.sorted_lo : 0;
@@ -623,6 +665,12 @@ int launch_gather(pme_plan_t p, cudaStream_t s, int n, const float* mesh, bool t
                  : launch_t<0, false>(p, s, n, mesh, nullptr, out);
 }
 
+int launch_gather_finish(pme_plan_t p, cudaStream_t s, int n, const float* mesh, const double* g_energy,
+                         const BackwardFinish& fin) {
+  if (p->batch) return launch_t<1, true>(p, s, n, mesh, g_energy, nullptr, nullptr, nullptr, &fin);
+  return launch_t<1, false>(p, s, n, mesh, g_energy, nullptr, nullptr, nullptr, &fin);
+}
+
 int launch_gather_quad(pme_plan_t p, cudaStream_t s, int n, const float* mesh, const float* theta,
                        float* out, float* qout) {
   if (p->batch) return launch_t<2, true>(p, s, n, mesh, nullptr, out, theta, qout);
@@ -639,6 +687,8 @@ int launch_gather_qdual(pme_plan_t p, cudaStream_t s, int n, const float* mesh, 
   a.out = out;
   a.theta = theta;
   a.qout = nullptr;
+  a.finish = 0;
+  a.fin = BackwardFinish{};
   for (int gi = 0; gi < p->nogroups; ++gi) {
     const OrderGroup& G = p->ogroups[gi];
     a.t_lo = p->batch ? G.sorted_lo : 0;

@@ -105,11 +105,35 @@ int launch_conv_influence(pme_plan_t p, cudaStream_t s, bool tangent, double* pa
                           double* vparts = nullptr, const int* keep = nullptr);
 int launch_conv_inverse(pme_plan_t p, cudaStream_t s, bool tangent, float* mesh, const int* keep = nullptr);
 
+// The backward pass's final per-ion assembly (the pair term's tangent sums, the self and
+// background terms, coulomb_k), done in the tangent gather's epilogue so that the backward
+// needs no separate combine launch.
+struct BackwardFinish {
+  const float* pair_out;   // [n][8] tangent pair sums in caller order (null: no pair term)
+  const float* q;          // [n]
+  const float* mu;         // [n][3] or null
+  const float* gphi;       // [n] or null: dq
+  const float* gfield;     // [n][3] or null: dmu = -g_field
+  const double* qsum;      // Q, dQ per frame
+  float* grad_pos;         // [n][3] or null
+  float* grad_q;           // [n] or null
+  float* grad_mu;          // [n][3] or null
+  float k, self_phi, self_c;
+  int with_bg;
+};
+// combine.cu: the constants and pointers of the assembly for these inputs and outputs.
+BackwardFinish backward_finish_args(pme_plan_t p, const IonInputs& in, float* grad_pos, float* grad_q,
+                                    float* grad_mu);
+
 // gather.cu: per-ion interpolation of the potential mesh(es).
 //   forward: out[orig][10] = phi, dphi/dr (3), d2phi/drdr (6)
 //   tangent: out[orig][8]  = mesh part of (grad_r (3), grad_q, grad_mu (3)) of the backward
 int launch_gather(pme_plan_t p, cudaStream_t s, int n, const float* mesh, bool tangent,
                   const double* g_energy, float* out);
+// Tangent gather that also does the backward's final assembly (fin) and writes the gradients
+// in place of the mesh part; the pair term's results must be complete when it runs.
+int launch_gather_finish(pme_plan_t p, cudaStream_t s, int n, const float* mesh, const double* g_energy,
+                         const BackwardFinish& fin);
 // Quadrupole Hessian-vector product, mesh part: the 13 gathered values of the quadrupole
 // forward and their tangents along (dr, d Phi) at out[orig][26] (Phi at mesh_off, d Phi at
 // tmesh_off of mesh).
@@ -158,9 +182,6 @@ int launch_combine_forward(pme_plan_t p, cudaStream_t s, const IonInputs& in, bo
 int launch_combine_backward_quad(pme_plan_t p, cudaStream_t s, const IonInputs& in, const double* g_energy,
                                  const float* qmesh, const float* qpair, float* grad_pos, float* grad_q,
                                  float* grad_mu, float* grad_theta);
-int launch_combine_backward(pme_plan_t p, cudaStream_t s, const IonInputs& in,
-                            const double* g_energy, float* grad_pos, float* grad_q,
-                            float* grad_mu);
 // ewald.cu: explicit Ewald reciprocal sum (structure factor, then per-ion potential
 // derivatives in the gather's [n][10] layout); energy partials sum A |S|^2 over the half space.
 int ewald_build_kvectors(pme_plan_t p, std::vector<int4>& kn, std::vector<float4>& kv);

@@ -1179,12 +1179,12 @@ static int run_backward(pme_plan_t p, cudaStream_t s, const IonInputs& in, const
   t = prof_begin(p, B + 4, s);
   if ((st = fft_inverse(p, s, true, keep))) return st;
   prof_end(p, t, s);
-  t = prof_begin(p, B + 5, s);
-  if ((st = launch_gather(p, s, n, p->phi, true, gE, p->mesh_out))) return st;
-  prof_end(p, t, s);
+  // the pair term (side stream) has long finished by now: join first, so that the tangent
+  // gather also does the final per-ion assembly (no separate combine launch)
   if (pair && p->opts.overlap_pair && (st = join_side(p, s))) return st;
-  t = prof_begin(p, B + 7, s);
-  if ((st = launch_combine_backward(p, s, in, gE, o_pos, o_q, o_mu))) return st;
+  t = prof_begin(p, B + 5, s);
+  const BackwardFinish fin = backward_finish_args(p, in, o_pos, o_q, o_mu);
+  if ((st = launch_gather_finish(p, s, n, p->phi, gE, fin))) return st;
   prof_end(p, t, s);
   return PME_OK;
 }
