@@ -87,12 +87,12 @@ QUAD_METRIC = "PME q+mu+Theta fwd Mion-evals/s @32k ions"
 # ncu capture of the same kernels on the same workload (cold cache: ncu flushes the caches
 # before each replay); the summaries, with their commands, are under profiles/.
 MEASURED_TRAFFIC = {
-    "fwd.pair_eval": (52.047360e6 + 0.122624e6, "profiles/k_spread_gather_pair_nacl32k.md"),
-    "bwd.pair_eval": (53.099520e6 + 0.201216e6, "profiles/k_spread_gather_pair_nacl32k.md"),
+    "fwd.pair_eval": (52.048384e6 + 0.132352e6, "profiles/k_spread_gather_pair_nacl32k.md"),
+    "bwd.pair_eval": (53.100288e6 + 0.196864e6, "profiles/k_spread_gather_pair_nacl32k.md"),
     "fwd.spread": (1.611520e6 + 0.000000e6, "profiles/k_spread_gather_pair_nacl32k.md"),
-    "bwd.spread": (2.667008e6 + 0.000000e6, "profiles/k_spread_gather_pair_nacl32k.md"),
-    "fwd.gather": (9.451520e6 + 0.000000e6, "profiles/k_spread_gather_pair_nacl32k.md"),
-    "bwd.gather": (19.423744e6 + 0.000000e6, "profiles/k_spread_gather_pair_nacl32k.md"),
+    "bwd.spread": (2.666752e6 + 0.000000e6, "profiles/k_spread_gather_pair_nacl32k.md"),
+    "fwd.gather": (9.452032e6 + 0.000000e6, "profiles/k_spread_gather_pair_nacl32k.md"),
+    "bwd.gather": (21.523200e6 + 0.000000e6, "profiles/k_spread_gather_pair_nacl32k.md"),
     "quad.pair_eval": (52.838144e6 + 0.163840e6, "profiles/k_pair_quad_nacl32k.md"),
 }
 
