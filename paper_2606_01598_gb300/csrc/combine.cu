@@ -189,10 +189,12 @@ __global__ void __launch_bounds__(kCombThreads) k_combine_forward(CombineArgs a)
   const double e_item = block_sum_f(e_f) + (a.in.theta ? block_sum_d(e_i) : 0.0);
   if (threadIdx.x == 0) a.eitem[item] = e_item;
   if (!last_item_done(a.ecount + f, F.nitems)) return;
-  double rp = a.recip_kind ? strided_sum_d(a.recip_parts + F.infl_blk_off, F.infl_nblk) : 0.0;
-  double ep = strided_sum_d(a.eitem + F.item_off, F.nitems);
-  rp = block_sum_d(rp);
-  ep = block_sum_d(ep);
+  // the frame's reciprocal and per-item partials, both sums at once (the last block's float64
+  // chain is what this kernel's duration is made of)
+  double rp, ep;
+  strided_sum2_d(a.recip_parts + F.infl_blk_off, a.recip_kind ? F.infl_nblk : 0, 1, a.eitem + F.item_off,
+                 F.nitems, 1, rp, ep);
+  block_sum2_d(rp, ep);
   double W[9], S[6];
   if (a.virial_out) {
 #pragma unroll
@@ -202,11 +204,11 @@ __global__ void __launch_bounds__(kCombThreads) k_combine_forward(CombineArgs a)
   }
   if (threadIdx.x == 0) {
     const double V = F.g.volume;
-    const double coef = a.recip_kind == 1 ? 0.5 / V : (a.recip_kind == 2 ? 4.0 * kPi / V : 0.0);
+    const double coef = a.recip_kind == 1 ? F.g.e_mesh_coef : (a.recip_kind == 2 ? F.g.e_ewald_coef : 0.0);
     double e_bg = 0.0;
     if (a.with_bg) {
       const double Q = a.qsum[2 * f];
-      e_bg = -kPi * Q * Q / (2.0 * V * double(a.alpha) * double(a.alpha));
+      e_bg = -(Q * Q) * F.g.e_bg_coef;
     }
     a.energy_out[f] = a.kd * (coef * rp + ep + e_bg);
     if (a.virial_out) {

@@ -75,6 +75,10 @@ struct Geometry {
   float bk[9];        // reciprocal basis, rows b_r = 2 pi C^{-T}: bk[r*3+c] = 2 pi cinv[c*3+r]
   float inv_volume;   // 1 / V
   float bg_fac;       // pi / (V alpha^2), the background potential per unit net charge
+  // energy coefficients (host float64, so that the last block of an energy sum divides nothing):
+  // 1 / (2V) of the mesh sum, 4 pi / V of the explicit Ewald sum, pi / (2 V alpha^2) of the
+  // background term -pi Q^2 / (2 V alpha^2)
+  double e_mesh_coef, e_ewald_coef, e_bg_coef;
   // K = diag-scaled C^{-1} as float pairs hi + lo (K[a*3+b] = N_b cinv[a*3+b] for the mesh,
   // ncell_b cinv[a*3+b] for the pair cells): mesh and cell coordinates in compensated float32
   float kmh[9], kml[9], kch[9], kcl[9];
@@ -526,20 +530,60 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// Largest butterfly offset of the second level of a block sum over nw warp partials held in
+// lanes 0 .. nw-1 (zeros above): the levels at and above the smallest power of two >= nw only
+// add zeros to those lanes, so the tree may start below it and still add the same terms in the
+// same order as the full five-level tree.
+__device__ __forceinline__ int partial_tree_top(int nw) {
+  int o = 1;
+  while (o < nw) o <<= 1;
+  return o >> 1;
+}
+
 // Block-wide float64 sum (blockDim.x a multiple of 32, <= 1024). Result valid in thread 0.
 __device__ __forceinline__ double block_sum_d(double v) {
   __shared__ double part[32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = int(blockDim.x >> 5);
   v = warp_sum_d(v);
   __syncthreads();
   if (lane == 0) part[wid] = v;
   __syncthreads();
   double r = 0.0;
   if (wid == 0) {
-    r = (lane < int(blockDim.x >> 5)) ? part[lane] : 0.0;
-    r = warp_sum_d(r);
+    r = (lane < nw) ? part[lane] : 0.0;
+    for (int o = partial_tree_top(nw); o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
   }
   return r;
+}
+
+// Two block-wide float64 sums at once, each exactly as block_sum_d forms it; their shuffle
+// trees are interleaved and share one pair of barriers (GB300's float64 latency makes two
+// trees in sequence cost twice one). Results valid in thread 0.
+__device__ __forceinline__ void block_sum2_d(double& a, double& b) {
+  __shared__ double part2[2][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = int(blockDim.x >> 5);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  __syncthreads();
+  if (lane == 0) {
+    part2[0][wid] = a;
+    part2[1][wid] = b;
+  }
+  __syncthreads();
+  double ra = 0.0, rb = 0.0;
+  if (wid == 0) {
+    ra = (lane < nw) ? part2[0][lane] : 0.0;
+    rb = (lane < nw) ? part2[1][lane] : 0.0;
+    for (int o = partial_tree_top(nw); o > 0; o >>= 1) {
+      ra += __shfl_xor_sync(0xffffffffu, ra, o);
+      rb += __shfl_xor_sync(0xffffffffu, rb, o);
+    }
+  }
+  a = ra;
+  b = rb;
 }
 
 // Two-level deterministic sum, second level: after thread 0 has stored its block's partial,
@@ -582,20 +626,68 @@ __device__ __forceinline__ double block_sum_f(float v) {
   return r;
 }
 
-// sum_{k = threadIdx.x; k < n; k += blockDim.x} src[k * stride] in that order, with eight loads
-// in flight at a time (the plain loop waits for each load before the next one). __ldcg reads
-// partials other blocks wrote in the same launch.
+// Two such sums at once, each exactly as block_sum_f forms it (interleaved trees, one pair of
+// barriers). Results valid in thread 0.
+__device__ __forceinline__ void block_sum2_f(float va, float vb, double& ra, double& rb) {
+  __shared__ double wpart2[2][32];
+  float ca = 0.f, cb = 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float a2 = __shfl_xor_sync(0xffffffffu, va, o), b2 = __shfl_xor_sync(0xffffffffu, vb, o);
+    const float ca2 = __shfl_xor_sync(0xffffffffu, ca, o), cb2 = __shfl_xor_sync(0xffffffffu, cb, o);
+    const float ta = va + a2, tb = vb + b2;
+    ca += ca2 + (fabsf(va) >= fabsf(a2) ? (va - ta) + a2 : (a2 - ta) + va);
+    cb += cb2 + (fabsf(vb) >= fabsf(b2) ? (vb - tb) + b2 : (b2 - tb) + vb);
+    va = ta;
+    vb = tb;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    wpart2[0][threadIdx.x >> 5] = double(va) + double(ca);
+    wpart2[1][threadIdx.x >> 5] = double(vb) + double(cb);
+  }
+  __syncthreads();
+  ra = 0.0;
+  rb = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+      ra += wpart2[0][w];
+      rb += wpart2[1][w];
+    }
+}
+
+// Sum of src[k * stride] over k = threadIdx.x, threadIdx.x + T, ... < n (T = blockDim.x): eight
+// loads in flight at a time (the plain loop waits for each load before the next one), each
+// round of eight added as a balanced tree (three dependent float64 adds, not eight) before it
+// joins the running sum; a fixed order for a given n and block size. __ldcg reads partials
+// other blocks wrote in the same launch.
+__device__ __forceinline__ double strided_round(const double* src, int n, int stride, int k0, int T) {
+  double v[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) v[u] = (k0 + u * T < n) ? __ldcg(src + size_t(k0 + u * T) * stride) : 0.0;
+  return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+}
+
 __device__ __forceinline__ double strided_sum_d(const double* src, int n, int stride = 1) {
   double acc = 0.0;
   const int T = blockDim.x;
-  for (int k0 = threadIdx.x; k0 < n; k0 += 8 * T) {
-    double v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = (k0 + u * T < n) ? __ldcg(src + size_t(k0 + u * T) * stride) : 0.0;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) acc += v[u];
-  }
+  for (int k0 = threadIdx.x; k0 < n; k0 += 8 * T) acc += strided_round(src, n, stride, k0, T);
   return acc;
+}
+
+// Two such sums at once (the loads of both in flight together); each equals what
+// strided_sum_d returns for it.
+__device__ __forceinline__ void strided_sum2_d(const double* a_src, int na, int sa, const double* b_src, int nb,
+                                               int sb, double& a, double& b) {
+  a = 0.0;
+  b = 0.0;
+  const int T = blockDim.x, n = max(na, nb);
+  for (int k0 = threadIdx.x; k0 < n; k0 += 8 * T) {
+    const double ra = strided_round(a_src, na, sa, k0, T);
+    const double rb = strided_round(b_src, nb, sb, k0, T);
+    if (k0 < na) a += ra;
+    if (k0 < nb) b += rb;
+  }
 }
 
 // Ion range [lo, hi) of reduction item `item` of frame F.

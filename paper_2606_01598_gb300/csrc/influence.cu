@@ -149,10 +149,9 @@ k_energy_final(FrameDesc one, FrameMaps maps, const double* parts, int recip_kin
   b = block_sum_d(b);
   if (threadIdx.x == 0) eitem[item] = b;
   if (!last_item_done(ecount + f, F.nitems)) return;
-  double a = recip_kind ? strided_sum_d(parts + F.infl_blk_off, F.infl_nblk) : 0.0;
-  double e = strided_sum_d(eitem + F.item_off, F.nitems);
-  a = block_sum_d(a);
-  e = block_sum_d(e);
+  double a, e;
+  strided_sum2_d(parts + F.infl_blk_off, recip_kind ? F.infl_nblk : 0, 1, eitem + F.item_off, F.nitems, 1, a, e);
+  block_sum2_d(a, e);
   if (threadIdx.x == 0) {
     const double V = F.g.volume;
     const double coef = recip_kind == 1 ? 0.5 / V : (recip_kind == 2 ? 4.0 * kPi / V : 0.0);

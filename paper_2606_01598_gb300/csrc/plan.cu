@@ -156,6 +156,9 @@ static bool frame_geometry(Geometry& g, const double* box, double rcut, bool pai
     for (int c = 0; c < 3; ++c) g.bk[r * 3 + c] = float(2.0 * kPi * inv[c * 3 + r]);
   g.inv_volume = float(1.0 / g.volume);
   g.bg_fac = float(kPi / (g.volume * double(g.alpha) * double(g.alpha)));
+  g.e_mesh_coef = 0.5 / g.volume;
+  g.e_ewald_coef = 4.0 * kPi / g.volume;
+  g.e_bg_coef = kPi / (2.0 * g.volume * double(g.alpha) * double(g.alpha));
   // pair cells at least rcut/2 wide (at least one per axis); a candidate cell lies at most
   // kimg = ceil(rcut / cell width) cells away along each axis. When an axis has fewer than
   // 2 kimg + 1 cells the offsets wrap onto the same cells again: each offset then stands for

@@ -192,16 +192,16 @@ k_bin(FrameDesc one, FrameMaps maps, IonInputs in, SortBuffers sb, int tangent, 
     qb = (tangent && in.gphi) ? in.gphi[i] : 0.f;
   }
   if (sb.qcount) {
-    const double A = block_sum_f(qa), B = block_sum_f(qb);
+    double A, B;
+    block_sum2_f(qa, qb, A, B);
     if (threadIdx.x == 0) {
       sb.qpart[2 * item] = A;
       sb.qpart[2 * item + 1] = B;
     }
     if (last_item_done(sb.qcount + f, F.nitems)) {
-      double a = strided_sum_d(sb.qpart + 2 * F.item_off, F.nitems, 2);
-      double b = strided_sum_d(sb.qpart + 2 * F.item_off + 1, F.nitems, 2);
-      a = block_sum_d(a);
-      b = block_sum_d(b);
+      double a, b;
+      strided_sum2_d(sb.qpart + 2 * F.item_off, F.nitems, 2, sb.qpart + 2 * F.item_off + 1, F.nitems, 2, a, b);
+      block_sum2_d(a, b);
       if (threadIdx.x == 0) {
         sb.qsum[2 * f] = a;
         sb.qsum[2 * f + 1] = b;
