@@ -173,3 +173,113 @@ def test_quadrupole_pair_cross_sign_is_caught(monkeypatch, small_quad):
         return e_full - 2 * (e_full - e_mu0 - e_th0 + e_both0)
     monkeypatch.setattr(O2.PMEOracle, "pair_energy", bad)
     _fails(TQ.test_o2_pair_term_matches_o1q_real_space, small_quad)
+
+
+# ---- the learned network O4 and the polarisable teacher O3 -----------------------------
+
+import test_oracle_net as TN  # noqa: E402
+import test_oracle_teacher as TT  # noqa: E402
+from oracle import net as N  # noqa: E402
+from oracle import teacher as T  # noqa: E402
+
+
+def _net_params():
+    # as the network pins' fixture: seeded weights with non-zero biases
+    p = W.net_params(seed=11)
+    rng = np.random.default_rng(3)
+    for k in ("bh", "bq", "bE"):
+        p[k] = rng.normal(0, 0.3, size=p[k].shape)
+    return p
+
+
+@pytest.fixture
+def net_frame():
+    return W.molten_nacl(64, seed=21)
+
+
+def test_dropped_charge_neutralisation_is_caught(monkeypatch, net_frame):
+    # the charge head without its per-frame mean subtraction
+    def bad(hs, hv, params):
+        H = hs @ params["Wh"] + params["bh"]
+        qt = N.silu(H[:, :N.S]) @ params["wq"] + params["bq"][0]
+        _, mu, Ei = orig(hs, hv, params)
+        return qt, mu, Ei
+    orig = N.readout
+    monkeypatch.setattr(N, "readout", bad)
+    _fails(TN.test_neutral_charges, net_frame, _net_params())
+
+
+def test_dipole_head_bias_is_caught(monkeypatch, net_frame):
+    # a constant vector added to every dipole: not equivariant
+    orig = N.readout
+
+    def bad(hs, hv, params):
+        q, mu, Ei = orig(hs, hv, params)
+        return q, mu + torch.tensor([0.01, 0.0, 0.0], dtype=torch.float64), Ei
+    monkeypatch.setattr(N, "readout", bad)
+    _fails(TN.test_rotation_equivariance, net_frame, _net_params())
+
+
+def test_dropped_periodic_images_is_caught(monkeypatch, net_frame):
+    # the edge list without the neighbours that are periodic images
+    orig = N.edges
+
+    def bad(pos, box, rc=N.RC):
+        i, j, sh = orig(pos, box, rc)
+        keep = ~np.abs(sh).max(axis=1).astype(bool) if len(sh) else np.zeros(0, bool)
+        return i[keep], j[keep], sh[keep]
+    monkeypatch.setattr(N, "edges", bad)
+    _fails(TN.test_supercell_replica_is_extensive, net_frame, _net_params())
+
+
+def test_wrong_envelope_coefficient_is_caught(monkeypatch):
+    monkeypatch.setattr(N, "envelope", lambda x: 1.0 - 21.0 * x ** 5 + 34.0 * x ** 6 - 15.0 * x ** 7)
+    _fails(TN.test_bessel_basis_orthonormal_and_envelope)
+
+
+def test_wrong_bessel_normalisation_is_caught(monkeypatch):
+    orig = N.radial_basis
+    monkeypatch.setattr(N, "radial_basis", lambda r: orig(r) / math.sqrt(2.0))
+    _fails(TN.test_bessel_basis_orthonormal_and_envelope)
+
+
+def test_model_force_sign_is_caught(monkeypatch):
+    orig = N.Model.forces
+
+    def bad(self, pos, species, params):
+        r = orig(self, pos, species, params)
+        r["force"] = -r["force"]
+        return r
+    monkeypatch.setattr(N.Model, "forces", bad)
+    _fails(TN.test_forces_central_differences, _net_params())
+
+
+def test_polarisation_energy_factor_is_caught(monkeypatch):
+    # |mu|^2 / a instead of |mu|^2 / (2a): the energy is no longer stationary at mu = a E
+    orig = T.polarisation_energy
+    monkeypatch.setattr(T, "polarisation_energy", lambda mu, a: 2.0 * orig(mu, a))
+    _fails(TT.test_self_consistency_and_stationarity, W.molten_nacl(32, seed=13))
+
+
+def test_loose_dipole_convergence_is_caught(monkeypatch):
+    # mixing stopped at a residual of 1e-4
+    orig = T.solve_dipoles
+
+    def bad(oracle, pos, q, a, **kw):
+        kw["tol"] = 1e-4
+        return orig(oracle, pos, q, a, **kw)
+    monkeypatch.setattr(T, "solve_dipoles", bad)
+    _fails(TT.test_self_consistency_and_stationarity, W.molten_nacl(32, seed=13))
+
+
+def test_teacher_forces_without_dipoles_are_caught(monkeypatch):
+    # forces taken from the charges alone, the induced dipoles left out
+    orig = T.label
+
+    def bad(frame, mesh=(32, 32, 32), order=4, alpha=0.30, rcut=9.0, **kw):
+        lab = orig(frame, mesh=mesh, order=order, alpha=alpha, rcut=rcut, **kw)
+        o = O2.PMEOracle(frame.box, mesh, order, alpha, rcut)
+        lab["force"] = o.evaluate(frame.pos, lab["q"], np.zeros_like(frame.pos), field_grad=False)["force"]
+        return lab
+    monkeypatch.setattr(T, "label", bad)
+    _fails(TT.test_hellmann_feynman_forces, W.molten_nacl(32, seed=13))

@@ -1,6 +1,6 @@
 """Pins of the network oracle O4 (oracle/net.py) against what symmetry and calculus fix:
-rotation equivariance, translation / permutation invariance, locality of a 2-layer net with a
-5 A cutoff, neutral charges, a vanishing dipole in a symmetric environment, the Bessel basis'
+rotation equivariance, translation / permutation invariance, extensivity under a supercell
+replica (periodic images), locality of a 2-layer net with a 5 A cutoff, neutral charges, a vanishing dipole in a symmetric environment, the Bessel basis'
 orthonormality and the envelope's closed form, forces and the force-matching gradient against
 central differences."""
 import math
@@ -59,6 +59,23 @@ def test_translation_and_permutation(frame, params):
     q2, mu2, e2 = _pred(frame.pos[perm], frame.species[perm], frame.box, params)
     assert np.allclose(q2, q0[perm], atol=1e-12) and np.allclose(mu2, mu0[perm], atol=1e-12)
     assert abs(e2 - e0) < 1e-10 * abs(e0)
+
+
+def test_supercell_replica_is_extensive(frame, params):
+    # a periodic frame and its 2 x 1 x 1 replica are the same material: the replica's charges
+    # and dipoles are the frame's, twice over, and its short-range energy is twice the frame's;
+    # in the 12.7 A cell many 5 A neighbours are periodic images, so a lost image shows
+    box2 = frame.box.copy()
+    box2[0] = 2.0 * frame.box[0]
+    pos2 = np.vstack([frame.pos, frame.pos + frame.box[0]])
+    sp2 = np.concatenate([frame.species, frame.species])
+    q0, mu0, e0 = _pred(frame.pos, frame.species, frame.box, params)
+    q1, mu1, e1 = _pred(pos2, sp2, box2, params)
+    assert np.allclose(q1, np.concatenate([q0, q0]), atol=1e-12)
+    assert np.allclose(mu1, np.vstack([mu0, mu0]), atol=1e-12)
+    assert abs(e1 - 2.0 * e0) < 1e-10 * abs(e0)
+    _, _, sh = N.edges(frame.pos, frame.box)
+    assert np.abs(sh).max(axis=1).astype(bool).mean() > 0.2   # the check is not vacuous
 
 
 def test_neutral_charges(frame, params):
