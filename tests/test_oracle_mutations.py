@@ -283,3 +283,26 @@ def test_teacher_forces_without_dipoles_are_caught(monkeypatch):
         return lab
     monkeypatch.setattr(T, "label", bad)
     _fails(TT.test_hellmann_feynman_forces, W.molten_nacl(32, seed=13))
+
+
+# ---- the virial (O2) -------------------------------------------------------------------
+
+import test_oracle_virial as TV  # noqa: E402
+
+
+def test_virial_without_background_is_caught(monkeypatch):
+    # the term-by-term virial missing E_bg I (invisible on a neutral frame)
+    orig = O2.PMEOracle.virial_terms
+
+    def bad(self, pos, q, mu):
+        Q = float(np.sum(q))
+        return orig(self, pos, q, mu) + self.k * math.pi * Q * Q / (2 * self.V * self.alpha ** 2) * np.eye(3)
+    monkeypatch.setattr(O2.PMEOracle, "virial_terms", bad)
+    _fails(TV.test_virial_definition_matches_terms_charged)
+
+
+def test_transposed_strain_is_caught(monkeypatch):
+    # the cell strained by (I + eps^T): W comes out transposed, which fixed dipoles make visible
+    orig = O2.PMEOracle.strained
+    monkeypatch.setattr(O2.PMEOracle, "strained", lambda self, eps: orig(self, np.asarray(eps).T))
+    _fails(TV.test_virial_definition_matches_terms_cubic, True)

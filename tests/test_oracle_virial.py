@@ -2,7 +2,8 @@
 and lattice vectors r -> (I + eps) r with the dipoles held fixed.
 
 Pins: the definition (central differences of the energy under strain) against the term-by-term
-evaluation, in a cubic and a triclinic cell, with and without dipoles; and the scaling
+evaluation, in a cubic and a triclinic cell, with and without dipoles, and with a net charge
+(the background term); and the scaling
 identity of the exact Ewald sum (O1): under r -> (1 + l) r the charge-charge, charge-dipole
 and dipole-dipole energies scale as 1/L, 1/L^2 and 1/L^3, so
 tr W = E_qq + 2 E_qmu + 3 E_mumu for a neutral frame, which O2 meets once its mesh and
@@ -33,6 +34,19 @@ def test_virial_definition_matches_terms_cubic(dipoles):
         assert np.abs(Wd - Wd.T).max() > 1e-3 * np.abs(Wd).max()
     else:
         assert np.abs(Wd - Wd.T).max() < 1e-8 * np.abs(Wd).max()
+
+
+def test_virial_definition_matches_terms_charged():
+    # a frame with net charge Q: the neutralising background -pi Q^2 / (2 V alpha^2) scales as
+    # 1/V and adds E_bg I to the virial (zero on the neutral frames above)
+    fr = W.molten_nacl(96, seed=17)
+    q = fr.q.copy()
+    q[:3] += 0.4
+    o = O2.PMEOracle(fr.box, (20, 20, 20), 6, 0.35, 7.0)
+    Wd = o.virial(fr.pos, q, fr.mu)
+    assert _rel(Wd, o.virial_terms(fr.pos, q, fr.mu)) < 1e-8
+    e_bg = np.pi * q.sum() ** 2 / (2 * o.V * 0.35 ** 2)
+    assert e_bg > 1e-3 * np.abs(Wd).max()     # the check is not vacuous
 
 
 def test_virial_definition_matches_terms_triclinic():
