@@ -306,3 +306,18 @@ def test_transposed_strain_is_caught(monkeypatch):
     orig = O2.PMEOracle.strained
     monkeypatch.setattr(O2.PMEOracle, "strained", lambda self, eps: orig(self, np.asarray(eps).T))
     _fails(TV.test_virial_definition_matches_terms_cubic, True)
+
+
+def test_background_sign_in_pme_is_caught(monkeypatch):
+    # O2's neutralising background with the wrong sign (invisible on a neutral frame)
+    orig = O2.PMEOracle.energy
+
+    def bad(self, pos, q, mu, pairs=None, parts=False, theta=None):
+        E, P = orig(self, pos, q, mu, pairs, parts=True, theta=theta)
+        E = E - 2.0 * P["e_bg"]
+        if parts:
+            P = dict(P, e_bg=-P["e_bg"])
+            return E, P
+        return E
+    monkeypatch.setattr(O2.PMEOracle, "energy", bad)
+    _fails(TP.test_charged_frame_matches_ewald_with_background)
