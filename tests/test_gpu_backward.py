@@ -25,6 +25,10 @@ CASES = {
     "nacl512_p6": lambda: (W.molten_nacl(512, seed=201), (32, 32, 32), 6, 0.30, 9.0),
     "nacl64_images_p5": lambda: (W.molten_nacl(64, seed=202), (16, 16, 16), 5, 0.30, 9.0),
     "nacl1000_ragged_p7": lambda: (W.molten_nacl(1000, seed=203), (27, 30, 25), 7, 0.35, 8.0),
+    # net charge +1: the background enters the gradient (-pi Q / (V alpha^2) in dE/dq) as well
+    # as the Hessian-vector product
+    "nacl512_charged_p6": lambda: (W.with_net_charge(W.molten_nacl(512, seed=204), 1.0, 8), (32, 32, 32), 6,
+                                   0.30, 9.0),
 }
 
 

@@ -33,6 +33,8 @@ CASES = {
     "nacl64": lambda: (W.molten_nacl(64, seed=1002), (16, 16, 16), 4, 0.30, 9.0),
     # ragged mesh, odd order, 1000 ions
     "nacl1000_ragged": lambda: (W.molten_nacl(1000, seed=77), (27, 30, 25), 5, 0.35, 8.0),
+    # net charge +1 (on the first eight ions): the neutralising background acts
+    "nacl512_charged": lambda: (W.with_net_charge(W.molten_nacl(512, seed=1003), 1.0, 8), (32, 32, 32), 6, 0.30, 9.0),
 }
 
 

@@ -147,6 +147,13 @@ def molten_nacl(n: int, L: float | None = None, min_sep: float = 2.2, q0: float 
     return Frame(pos=pos, q=q, mu=mu, box=np.eye(3) * L, species=species)
 
 
+def with_net_charge(fr: Frame, Q: float, k: int) -> Frame:
+    """The frame with Q / k added to the charges of its first k ions (net charge Q)."""
+    q = np.array(fr.q, np.float64)
+    q[:k] += Q / k
+    return Frame(pos=fr.pos, q=q, mu=fr.mu, box=fr.box, species=fr.species)
+
+
 def charged_dimer(sep: float = 8.0, L: float = 30.0, mu_sigma: float = 0.05,
                   seed: int = 1005) -> Frame:
     """Two small ion clusters of opposite total charge in a cubic box (a stand-in for the
