@@ -321,3 +321,28 @@ def test_background_sign_in_pme_is_caught(monkeypatch):
         return E
     monkeypatch.setattr(O2.PMEOracle, "energy", bad)
     _fails(TP.test_charged_frame_matches_ewald_with_background)
+
+
+# ---- the mesh-size rules ---------------------------------------------------------------
+
+import test_oracle_meshdims as TM  # noqa: E402
+from oracle import meshdims  # noqa: E402
+
+
+def test_mesh_target_from_box_columns_is_caught(monkeypatch):
+    # the lengths of the box's columns taken for those of its lattice vectors
+    orig = meshdims.target
+    monkeypatch.setattr(meshdims, "target",
+                        lambda box, spacing, rule="paper": orig(np.asarray(box).T, spacing, rule))
+    _fails(TM.test_mesh_dims_follow_the_lattice_vectors)
+
+
+def test_smooth_size_below_target_is_caught(monkeypatch):
+    # the largest smooth size <= target instead of the smallest >= target
+    def bad(n):
+        n = max(1, int(n))
+        while not meshdims.is_smooth(n):
+            n -= 1
+        return n
+    monkeypatch.setattr(meshdims, "next_smooth", bad)
+    _fails(TM.test_strategies_against_enumeration)
