@@ -56,7 +56,6 @@ struct CombineArgs {
   float self_phi;     // 2 alpha / sqrt(pi)     (0 when self terms are off)
   float self_c;       // 4 alpha^3 / (3 sqrt(pi))
   int with_bg;        // background term on
-  float alpha;
   double e_self_q;    // alpha / sqrt(pi)
   double e_self_mu;   // 2 alpha^3 / (3 sqrt(pi))
   // quadrupoles (forward; null: none)
@@ -313,7 +312,6 @@ CombineArgs base_args(pme_plan_t p, const IonInputs& in) {
   a.in = in;
   a.qsum = p->sb.qsum;
   a.e_ion = p->e_ion;
-  a.alpha = float(p->alpha);
   a.k = float(p->opts.coulomb_k);
   const double sp = 1.7724538509055160273;
   const double al = p->alpha;
