@@ -120,10 +120,14 @@ def fp32_peak(dev, sm_max_mhz):
 
 def pair_hits(pos, box, rcut):
     """Ordered pairs (i, j) within rcut over the periodic images of an orthorhombic box: the
-    number of pair evaluations one list pass makes (each pair is evaluated from both ions)."""
+    number of pair evaluations one list pass makes (each pair is evaluated from both ions).
+    The periodic tree sees the nearest image of each pair only, so rcut must stay below half
+    of every box edge (then no pair has a second image within rcut)."""
     import numpy as np
     from scipy.spatial import cKDTree
     L = np.diag(np.asarray(box, np.float64))
+    if not rcut < 0.5 * L.min():
+        raise ValueError(f"pair_hits: rcut {rcut} not below half the shortest box edge {L.min()}")
     t = cKDTree(np.mod(np.asarray(pos, np.float64), L), boxsize=L)
     return 2 * len(t.query_pairs(rcut, output_type="ndarray"))
 
