@@ -516,6 +516,7 @@ int launch_order(pme_plan_t p, cudaStream_t s, int grid, const SpreadArgs& a) {
     if (dev < 32) done_mask |= 1 << dev;
   }
   pdl_launch(k_spread<SH, P, MODE, BATCH>, grid, SH::NT, bytes, s, a);
+  count_launch();
   return PME_OK;
 }
 
