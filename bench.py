@@ -316,7 +316,7 @@ def run_reference(args):
 
 
 def config_dict(cfg, fr, ws):
-    return {"workload": f"molten-NaCl {fr.n} ions, L={fr.box[0, 0]:.1f} A, mesh "
+    return {"workload": f"{cfg.get('desc', 'molten-NaCl')} {fr.n} ions, L={fr.box[0, 0]:.1f} A, mesh "
                         f"{'x'.join(map(str, cfg['mesh']))}, order {cfg['order']}, alpha {cfg['alpha']}, "
                         f"rcut {cfg['rcut']}, charges+dipoles, fwd+bwd (HVP)",
             "ions": fr.n, "mesh": list(cfg["mesh"]), "order": cfg["order"], "alpha": cfg["alpha"],

@@ -212,13 +212,13 @@ def tangent(n: int, scale: float = 1.0, seed: int = 77):
 # Named workloads: mesh/order/alpha/rcut settings that go with each generator.
 WORKLOADS = {
     "rocksalt512": dict(gen=lambda: rocksalt(4, 5.64, jitter=0.1, mu_sigma=0.05, seed=1000),
-                        mesh=(32, 32, 32), order=4, alpha=0.30, rcut=10.0),
+                        mesh=(32, 32, 32), order=4, alpha=0.30, rcut=10.0, desc="rock-salt NaCl"),
     "nacl4096": dict(gen=lambda: molten_nacl(4096, L=51.0, seed=1001),
-                     mesh=(64, 64, 64), order=6, alpha=0.30, rcut=9.0),
+                     mesh=(64, 64, 64), order=6, alpha=0.30, rcut=9.0, desc="molten-NaCl"),
     "nacl32k": dict(gen=lambda: molten_nacl(32768, L=102.0, seed=1004),
-                    mesh=(128, 128, 128), order=6, alpha=0.30, rcut=9.0),
+                    mesh=(128, 128, 128), order=6, alpha=0.30, rcut=9.0, desc="molten-NaCl"),
     "nacl262k": dict(gen=lambda: molten_nacl(262144, L=204.0, seed=1014),
-                     mesh=(256, 256, 256), order=6, alpha=0.30, rcut=9.0),
+                     mesh=(256, 256, 256), order=6, alpha=0.30, rcut=9.0, desc="molten-NaCl"),
 }
 
 
