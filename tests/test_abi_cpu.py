@@ -1,5 +1,7 @@
 """Host-side checks of the C ABI that need no GPU: the library loads, exports every function
-the public header declares, and its host-only mesh-size rule agrees with the oracle's."""
+the public header declares, every ctypes signature has the prototype's number of parameters,
+the ctypes mirror of pme_opts has the C compiler's layout of the header's struct, and the
+host-only mesh-size rule agrees with the oracle's."""
 import ctypes
 
 import numpy as np
@@ -59,3 +61,51 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.pme_plan_destroy(None) == 1
     assert lib.pme_forward(None, None, 0, *([None] * 8)) == 1
     assert lib.pme_backward(None, None, 0, *([None] * 10)) == 1
+
+
+def _prototypes():
+    """name -> number of parameters, from every prototype the public headers declare."""
+    import re
+
+    import paper_2606_01598_gb300._abi as A
+    out = {}
+    for h in A.HEADERS:
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        src = re.sub(r"^\s*#.*$", "", src, flags=re.M)
+        for name, args in re.findall(r"\b((?:pme|gbnet)_[a-z_0-9]+)\s*\(([^()]*)\)\s*;", src, flags=re.S):
+            args = " ".join(args.split())
+            out[name] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_ctypes_signatures_match_the_header_prototypes():
+    # a ctypes signature with a parameter more or fewer than the C prototype would pass
+    # shifted arguments to the library
+    import paper_2606_01598_gb300._abi as A
+    protos = _prototypes()
+    assert set(protos) == set(A.header_functions())
+    wrong = {n: (len(A._SIGS[n][1]), k) for n, k in protos.items() if len(A._SIGS[n][1]) != k}
+    assert not wrong, wrong
+
+
+def test_opts_struct_layout_matches_the_header(tmp_path):
+    # the ctypes mirror of pme_opts against the C compiler's layout of the header's struct
+    import shutil
+    import subprocess
+
+    import paper_2606_01598_gb300._abi as A
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = [f[0] for f in A.PMEOpts._fields_]
+    prog = tmp_path / "layout.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gbpme.h"\nint main(void) {\n'
+                    '  printf("%zu\\n", sizeof(pme_opts));\n'
+                    + "".join(f'  printf("%zu\\n", offsetof(pme_opts, {n}));\n' for n in names)
+                    + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    inc = __import__("os").path.dirname(A.HEADER)
+    subprocess.run([cc, "-std=c99", "-I", inc, str(prog), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got[0] == ctypes.sizeof(A.PMEOpts)
+    assert got[1:] == [getattr(A.PMEOpts, n).offset for n in names]
