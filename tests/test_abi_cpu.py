@@ -109,3 +109,47 @@ def test_opts_struct_layout_matches_the_header(tmp_path):
     got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
     assert got[0] == ctypes.sizeof(A.PMEOpts)
     assert got[1:] == [getattr(A.PMEOpts, n).offset for n in names]
+
+
+def _c_kind(decl):
+    d = " ".join(decl.split())
+    if "*" in d or "[" in d or d.endswith("_t") or " pme_plan_t" in d or d.startswith("pme_plan_t") \
+            or d.startswith("gbnet_t"):
+        return "ptr"
+    if "double" in d:
+        return "f64"
+    if "float" in d:
+        return "f32"
+    if "long long" in d:
+        return "i64"
+    if "int" in d or "size_t" in d:
+        return "i32" if "size_t" not in d else "i64"
+    return "?" + d
+
+
+def _ctypes_kind(t):
+    if t is None:
+        return "void"
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or hasattr(t, "_type_") and isinstance(t._type_, type):
+        return "ptr"
+    return {ctypes.c_double: "f64", ctypes.c_float: "f32", ctypes.c_int: "i32", ctypes.c_longlong: "i64",
+            ctypes.c_size_t: "i64"}.get(t, "?" + repr(t))
+
+
+def test_ctypes_parameter_kinds_match_the_header():
+    # pointer / float64 / float32 / integer class of each parameter (a double passed where the
+    # prototype has an int, or the reverse, lands in the wrong register)
+    import re
+
+    import paper_2606_01598_gb300._abi as A
+    bad = {}
+    for h in A.HEADERS:
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        src = re.sub(r"^\s*#.*$", "", src, flags=re.M)
+        for name, args in re.findall(r"\b((?:pme|gbnet)_[a-z_0-9]+)\s*\(([^()]*)\)\s*;", src, flags=re.S):
+            args = " ".join(args.split())
+            c = [] if args in ("", "void") else [_c_kind(a) for a in args.split(",")]
+            py = [_ctypes_kind(t) for t in A._SIGS[name][1]]
+            if c != py:
+                bad[name] = (c, py)
+    assert not bad, bad
