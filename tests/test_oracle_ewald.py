@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from oracle import ewald
+from oracle import ewald, pme
 
 
 def _golden(root):
@@ -28,6 +28,41 @@ def test_rocksalt_madelung(root):
     # zero forces and equal potentials magnitude on a perfect lattice
     assert np.abs(r["force"]).max() < 1e-10
     assert np.allclose(np.abs(r["phi"]), np.abs(r["phi"][0]), rtol=1e-10)
+
+
+def _golden_file(root, name):
+    vals = {}
+    with open(os.path.join(root, "tests", "golden", name)) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals
+
+
+_FCC = [(0, 0, 0), (0.5, 0.5, 0), (0.5, 0, 0.5), (0, 0.5, 0.5)]
+CRYSTALS = {
+    # golden file, fractional basis of the cubic cell, charges, nearest-neighbour distance / a
+    "cscl": ("madelung_cscl.txt", [(0, 0, 0), (0.5, 0.5, 0.5)], [1, -1], np.sqrt(3) / 2),
+    "zincblende": ("madelung_zincblende.txt", _FCC + [(x + 0.25, y + 0.25, z + 0.25) for x, y, z in _FCC],
+                   [1] * 4 + [-1] * 4, np.sqrt(3) / 4),
+}
+
+
+@pytest.mark.parametrize("name", list(CRYSTALS))
+def test_other_crystal_madelung_constants(root, name):
+    # two more structures with tabulated Madelung constants: body-centred (CsCl) and
+    # tetrahedral (zinc blende) coordination; O1 is exact, O2 carries its mesh error
+    fname, basis, charges, r0a = CRYSTALS[name]
+    g = _golden_file(root, fname)
+    fr = W.cubic_crystal(basis, charges, int(g["ncell"]), g["a"])
+    ref = -fr.n * g["M"] / (2 * r0a * g["a"])
+    r = ewald.ewald(fr.pos, fr.q, fr.mu, fr.box, 0.5)
+    assert abs(r["energy"] - ref) / abs(ref) < 1e-8
+    assert np.abs(r["force"]).max() < 1e-10
+    o2 = pme.PMEOracle(fr.box, (48, 48, 48), 6, 0.7, 0.49 * fr.box[0, 0]).evaluate(
+        fr.pos, fr.q, fr.mu, field_grad=False)
+    assert abs(o2["energy"] - ref) / abs(ref) < 1e-5
 
 
 def test_alpha_independence_charges_and_dipoles():

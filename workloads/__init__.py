@@ -147,6 +147,17 @@ def molten_nacl(n: int, L: float | None = None, min_sep: float = 2.2, q0: float 
     return Frame(pos=pos, q=q, mu=mu, box=np.eye(3) * L, species=species)
 
 
+def cubic_crystal(basis, charges, ncell: int, a: float) -> Frame:
+    """ncell^3 cubic cells of edge a, each holding ions of the given charges at the fractional
+    positions ``basis`` (a perfect crystal; no dipoles)."""
+    cells = np.array([(i, j, k) for i in range(ncell) for j in range(ncell) for k in range(ncell)], np.float64)
+    b = np.asarray(basis, np.float64)
+    pos = ((cells[:, None, :] + b[None, :, :]) * a).reshape(-1, 3)
+    q = np.tile(np.asarray(charges, np.float64), len(cells))
+    species = (q < 0).astype(np.int64)
+    return Frame(pos=pos, q=q, mu=np.zeros_like(pos), box=np.eye(3) * (ncell * a), species=species)
+
+
 def with_net_charge(fr: Frame, Q: float, k: int) -> Frame:
     """The frame with Q / k added to the charges of its first k ions (net charge Q)."""
     q = np.array(fr.q, np.float64)
