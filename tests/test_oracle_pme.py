@@ -219,3 +219,27 @@ def test_charged_frame_matches_ewald_with_background():
     assert np.abs(r["phi"] - ref["phi"]).max() < 1e-5
     assert np.abs(r["force"] - ref["force"]).max() < 1e-5
     assert abs(ref["e_bg"]) > 3e-5 * abs(ref["energy"])      # the check is not vacuous
+
+
+def test_parallel_dipole_lattice_closed_form():
+    # identical parallel dipoles on a simple cubic lattice: the spherical vacuum sum over the
+    # other dipoles vanishes by cubic symmetry (Lorentz), so with conducting boundaries (the
+    # Ewald form) each site feels the field (4 pi / 3) M / V and E = -2 pi |M|^2 / (3 V), M the
+    # total dipole; the forces and field gradients vanish. O1 is exact; O2's error falls with
+    # the mesh at about the order of the spline
+    fr = W.cubic_crystal([(0, 0, 0)], [0.0], 6, 3.0)
+    mu = np.tile(np.array([0.1, 0.2, -0.05]), (fr.n, 1))
+    V = abs(np.linalg.det(fr.box))
+    M = mu.sum(0)
+    e_ref = -2 * math.pi * (M @ M) / (3 * V)
+    f_ref = (4 * math.pi / 3) * M / V
+    r = ewald.ewald(fr.pos, fr.q, mu, fr.box, 0.5)
+    assert abs(r["energy"] - e_ref) < 1e-12 * abs(e_ref)
+    assert np.abs(r["field"] - f_ref).max() < 1e-12 * np.abs(f_ref).max()
+    assert np.abs(r["force"]).max() < 1e-14 and np.abs(r["field_grad"]).max() < 1e-12
+    errs = []
+    for mesh in ((36, 36, 36), (48, 48, 48)):
+        o = pme.PMEOracle(fr.box, mesh, 6, 0.5, 8.9).evaluate(fr.pos, fr.q, mu, field_grad=False)
+        errs.append(abs(o["energy"] - e_ref) / abs(e_ref))
+        assert np.abs(o["field"] - f_ref).max() < 2 * errs[-1] * np.abs(f_ref).max() + 1e-12
+    assert errs[1] < 2e-5 and errs[0] / errs[1] > (48 / 36) ** 5
