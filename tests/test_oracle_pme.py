@@ -243,3 +243,26 @@ def test_parallel_dipole_lattice_closed_form():
         errs.append(abs(o["energy"] - e_ref) / abs(e_ref))
         assert np.abs(o["field"] - f_ref).max() < 2 * errs[-1] * np.abs(f_ref).max() + 1e-12
     assert errs[1] < 2e-5 and errs[0] / errs[1] > (48 / 36) ** 5
+
+
+def test_stage_helpers_compose_to_the_evaluation():
+    # the stage helpers the per-kernel GPU tests compare against (mesh density, solve, gather,
+    # pair) reassemble, with the self and background terms of the Ewald split, the potential,
+    # field and energy that evaluate() takes from autograd of the total energy
+    fr = W.with_net_charge(W.molten_nacl(64, seed=31), 0.2, 4)
+    a = 0.35
+    o = pme.PMEOracle(fr.box, (20, 18, 16), 5, a, 6.0)
+    rho = o.stage_mesh(fr.pos, fr.q, fr.mu)
+    Phi, e_rec = o.stage_solve(rho)
+    phi_m, g_m, _ = o.stage_gather(fr.pos, Phi)
+    e_pair, phi_p, g_p, _ = o.stage_pair(fr.pos, fr.q, fr.mu)
+    ev = o.evaluate(fr.pos, fr.q, fr.mu, field_grad=False)
+    Q = fr.q.sum()
+    V = abs(np.linalg.det(fr.box))
+    phi = phi_m + phi_p - 2 * a / math.sqrt(math.pi) * fr.q - math.pi * Q / (V * a * a)
+    field = -(g_m + g_p) + 4 * a ** 3 / (3 * math.sqrt(math.pi)) * fr.mu
+    e_self = -a / math.sqrt(math.pi) * (fr.q ** 2).sum() - 2 * a ** 3 / (3 * math.sqrt(math.pi)) * (fr.mu ** 2).sum()
+    e_bg = -math.pi * Q * Q / (2 * V * a * a)
+    assert np.abs(phi - ev["phi"]).max() < 1e-12 * np.abs(ev["phi"]).max()
+    assert np.abs(field - ev["field"]).max() < 1e-12 * np.abs(ev["field"]).max()
+    assert abs(e_rec + e_pair + e_self + e_bg - ev["energy"]) < 1e-12 * abs(ev["energy"])
